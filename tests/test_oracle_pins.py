@@ -1,0 +1,428 @@
+"""Pins of the CPU oracle against closed forms, invariants and brute force.
+
+Each test checks one oracle function against something other than the oracle
+itself: a textbook closed form, an exact identity the paper states (Sec. 3,
+Sec. 4), a brute-force construction written differently, or a dense direct
+solve.  They are chosen so that a dropped term, a wrong sign or index, or a
+transposed operand anywhere in the oracle fails at least one of them.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle import cgs_oracle as O
+from paper_2606_20496_b300 import meshes
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _kron_q1(hx, hy, hz):
+    """Q1 box-element stiffness as a Kronecker sum of 1D stiffness/mass."""
+    K = lambda h: np.array([[1.0, -1.0], [-1.0, 1.0]]) / h
+    M = lambda h: h * np.array([[1 / 3, 1 / 6], [1 / 6, 1 / 3]])
+    return (np.kron(M(hz), np.kron(M(hy), K(hx))) + np.kron(M(hz), np.kron(K(hy), M(hx)))
+            + np.kron(K(hz), np.kron(M(hy), M(hx))))
+
+
+def _corners(lo, h):
+    return np.array([[lo[0] + (k & 1) * h[0], lo[1] + ((k >> 1) & 1) * h[1],
+                      lo[2] + ((k >> 2) & 1) * h[2]] for k in range(8)])
+
+
+# --------------------------------------------------------------------------
+# element matrices
+# --------------------------------------------------------------------------
+
+def test_unit_cube_element_matches_golden():
+    gold = np.loadtxt(os.path.join(GOLDEN, "q1_unit_cube.txt")) / 12.0
+    A, _ = O.element_matrices(_corners([0, 0, 0], [1, 1, 1]), np.arange(8)[None, :])
+    np.testing.assert_allclose(A[0], gold, atol=1e-15)
+
+
+@pytest.mark.parametrize("h", [(1.0, 1.0, 1.0), (0.3, 2.0, 0.7), (1e-2, 1.0, 1.0)])
+def test_box_element_matches_kronecker_closed_form(h):
+    A, _ = O.element_matrices(_corners([0.2, -1.0, 3.0], h), np.arange(8)[None, :])
+    ref = _kron_q1(*h)
+    np.testing.assert_allclose(A[0], ref, rtol=1e-13, atol=1e-13 * np.abs(ref).max())
+
+
+def _ref_integrals():
+    """1D integrals over [-1,1] of the linear basis l_0=(1-x)/2, l_1=(1+x)/2."""
+    mass = np.array([[2 / 3, 1 / 3], [1 / 3, 2 / 3]])
+    s = np.array([-0.5, 0.5])                      # l_s'
+    dl_l = np.outer(s, [1.0, 1.0])                 # int l_i' l_j = s_i * 1
+    dl_dl = 2.0 * np.outer(s, s)                   # int l_i' l_j'
+    return mass, dl_l, dl_dl
+
+
+def test_affine_element_matches_exact_integral():
+    """For x = B xi + c the stiffness is |det B| sum_ab (B^-1 B^-T)_ab K^ab with
+    K^ab_ij = int d_a l_i d_b l_j over the reference cube (exact 1D products)."""
+    rng = np.random.default_rng(7)
+    B = np.eye(3) * 0.5 + 0.2 * rng.standard_normal((3, 3))
+    assert np.linalg.det(B) > 0
+    c = rng.standard_normal(3)
+    xi = np.array([[2 * (k & 1) - 1, 2 * ((k >> 1) & 1) - 1, 2 * ((k >> 2) & 1) - 1] for k in range(8)], float)
+    X = xi @ B.T + c
+    mass, dl_l, dl_dl = _ref_integrals()
+    bits = [[(k >> d) & 1 for d in range(3)] for k in range(8)]
+    G = np.linalg.inv(B) @ np.linalg.inv(B).T
+    ref = np.zeros((8, 8))
+    for i in range(8):
+        for j in range(8):
+            tot = 0.0
+            for a in range(3):
+                for b in range(3):
+                    prod = 1.0
+                    for d in range(3):
+                        si, sj = bits[i][d], bits[j][d]
+                        if d == a and d == b:
+                            prod *= dl_dl[si, sj]
+                        elif d == a:
+                            prod *= dl_l[si, sj]
+                        elif d == b:
+                            prod *= dl_l[sj, si]
+                        else:
+                            prod *= mass[si, sj]
+                    tot += G[a, b] * prod
+            ref[i, j] = np.linalg.det(B) * tot
+    A, _ = O.element_matrices(X, np.arange(8)[None, :])
+    np.testing.assert_allclose(A[0], ref, rtol=1e-12, atol=1e-13 * np.abs(ref).max())
+
+
+def test_element_matrix_invariants_on_distorted_elements():
+    m, _ = meshes.workload_cube8()
+    A, min_det = O.element_matrices(m.xyz, m.conn)
+    assert min_det > 0
+    np.testing.assert_allclose(A, np.swapaxes(A, 1, 2), atol=1e-16)
+    assert np.abs(A.sum(axis=2)).max() < 1e-15 * np.abs(A).max() * 8
+    # rigid rotation leaves A^e unchanged; uniform scaling by s multiplies it by s (3D)
+    rng = np.random.default_rng(3)
+    Q, _ = np.linalg.qr(rng.standard_normal((3, 3)))
+    if np.linalg.det(Q) < 0:
+        Q[:, 0] *= -1
+    Ar, _ = O.element_matrices(m.xyz @ Q.T + 1.5, m.conn)
+    As, _ = O.element_matrices(2.5 * m.xyz, m.conn)
+    np.testing.assert_allclose(Ar, A, atol=1e-13)
+    np.testing.assert_allclose(As, 2.5 * A, atol=1e-13)
+
+
+@pytest.mark.parametrize("wl", ["cube8", "cube_deformed", "cylinder"])
+def test_patch_test_linear_fields(wl):
+    """int grad phi_i . grad u dV = 0 at interior vertices for linear u, on
+    distorted trilinear meshes (2x2x2 Gauss integrates this exactly)."""
+    if wl == "cube8":
+        m, _ = meshes.workload_cube8()
+    elif wl == "cube_deformed":
+        m = meshes.cube(6, deform=True, permute_seed=4)
+    else:
+        m = meshes.cylinder(4, 16, 4, grading=1.2, aspect=5.0, boxes=(2, 2, 2))
+    Ae, _ = O.element_matrices(m.xyz, m.conn)
+    A = O.assemble(m.conn.astype(np.int64), Ae, m.nv)
+    interior = ~O.dirichlet_mask(m.conn, m.nv)
+    rng = np.random.default_rng(11)
+    g = rng.standard_normal(3)
+    u = m.xyz @ g + 0.7
+    y = A @ u
+    assert np.abs(y[interior]).max() < 1e-12 * np.abs(A.data).max() * np.abs(u).max()
+    # constants are in the null space everywhere
+    assert np.abs(A @ np.ones(m.nv)).max() < 1e-13 * np.abs(A.data).max()
+
+
+def test_assembled_free_block_is_spd_and_27_point_on_uniform_mesh():
+    n = 4
+    m = meshes.cube(n)
+    P = O.Problem(m.xyz, m.conn, m.part, (2, 2, 2))
+    Ad = P.A.toarray()
+    np.testing.assert_allclose(Ad, Ad.T, atol=1e-15)
+    assert np.linalg.eigvalsh(Ad).min() > 0
+    # the assembled uniform-grid stencil: centre 8h/3, faces 0, edges -h/6, corners -h/12
+    h = 1.0 / n
+    c = 2 + (n + 1) * (2 + (n + 1) * 2)
+    row = P.A_full[[c], :].toarray()[0]
+    assert row[c] == pytest.approx(8 * h / 3, rel=1e-13)
+    for di in (-1, 0, 1):
+        for dj in (-1, 0, 1):
+            for dk in (-1, 0, 1):
+                nz = abs(di) + abs(dj) + abs(dk)
+                if nz == 0:
+                    continue
+                v = c + di + (n + 1) * (dj + (n + 1) * dk)
+                expect = {1: 0.0, 2: -h / 6, 3: -h / 12}[nz]
+                assert row[v] == pytest.approx(expect, abs=1e-15)
+
+
+# --------------------------------------------------------------------------
+# Dirichlet set, subdomains
+# --------------------------------------------------------------------------
+
+def test_dirichlet_mask_cube_and_cylinder():
+    m = meshes.cube((3, 4, 5), perturb=0.1, seed=1)
+    d = O.dirichlet_mask(m.conn, m.nv)
+    i = np.arange(m.nv) % 4
+    j = (np.arange(m.nv) // 4) % 5
+    k = np.arange(m.nv) // 20
+    expect = (i == 0) | (i == 3) | (j == 0) | (j == 4) | (k == 0) | (k == 5)
+    np.testing.assert_array_equal(d, expect)
+    c = meshes.cylinder(3, 8, 2, grading=1.1, aspect=3.0, boxes=(2, 2, 2))
+    d = O.dirichlet_mask(c.conn, c.nv)
+    ir = np.arange(c.nv) % 4
+    iz = np.arange(c.nv) // (4 * 8)
+    np.testing.assert_array_equal(d, (ir == 0) | (ir == 3) | (iz == 0) | (iz == 2))
+
+
+def test_subdomain_restriction_matches_structured_brute_force():
+    """R_p of a 2^3 block grown by one element layer = free vertices strictly
+    inside the grown block's vertex range (structured mesh, any perturbation)."""
+    dims = (6, 5, 7)
+    m = meshes.cube(dims, perturb=0.1, seed=2)
+    P = O.Problem(m.xyz, m.conn, m.part, (2, 2, 2))
+    nvx, nvy = dims[0] + 1, dims[1] + 1
+    vid = np.arange(m.nv)
+    vi, vj, vk = vid % nvx, (vid // nvx) % nvy, vid // (nvx * nvy)
+    nb = [-(-d // 2) for d in dims]
+    for p in range(len(P.sub_idx)):
+        bi, bj, bk = p % nb[0], (p // nb[0]) % nb[1], p // (nb[0] * nb[1])
+        ok = np.ones(m.nv, bool)
+        for v, b, d in ((vi, bi, dims[0]), (vj, bj, dims[1]), (vk, bk, dims[2])):
+            lo = max(2 * b - 1, 0)
+            hi = min(2 * b + 2 + 1, d)
+            ok &= (v > lo) & (v < hi)
+        expect = np.flatnonzero(ok & ~P.dir)
+        np.testing.assert_array_equal(P.sub_idx[p], expect)
+
+
+def test_local_solve_satisfies_interior_equations():
+    """y = A_p^{-1} R_p r extended by zero solves (A R_p^T y)_i = r_i on R_p:
+    A_p is the principal submatrix of A (Sec. 3)."""
+    m, b = meshes.workload_cube8()
+    P = O.Problem(m.xyz, m.conn, m.part, m.boxes)
+    r = np.where(P.dir, 0.0, b)
+    for p in (0, 5, 21, 63):
+        idx = P.sub_idx[p]
+        ext = np.zeros(m.nv)
+        ext[idx] = P.local_solve_one(p, r)
+        np.testing.assert_allclose(P.apply_A(ext)[idx], r[idx], atol=1e-12)
+    # the batched (grouped Cholesky) path gives the same sum as one-by-one solves
+    tot = np.zeros(m.nv)
+    for p in range(len(P.sub_idx)):
+        tot[P.sub_idx[p]] += P.local_solve_one(p, r)
+    np.testing.assert_allclose(P.local_solves(r, weighted=False), tot, atol=1e-12)
+    w = tot.copy()
+    w[P.mult > 0] /= P.mult[P.mult > 0]
+    np.testing.assert_allclose(P.local_solves(r, weighted=True), w, atol=1e-12)
+
+
+# --------------------------------------------------------------------------
+# box coarse space
+# --------------------------------------------------------------------------
+
+def _trilinear(c, X):
+    x, y, z = X[:, 0], X[:, 1], X[:, 2]
+    return (c[0] + c[1] * x + c[2] * y + c[3] * z + c[4] * x * y + c[5] * y * z
+            + c[6] * x * z + c[7] * x * y * z)
+
+
+def _box_vertex_xyz(P):
+    nb = P.box_b + 1
+    a = P.box_active
+    ijk = np.stack([a % nb[0], (a // nb[0]) % nb[1], a // (nb[0] * nb[1])], axis=1)
+    return P.box_lo + ijk * P.box_H
+
+
+@pytest.mark.parametrize("wl", ["cube8", "cube_deformed", "cylinder"])
+def test_interpolation_reproduces_trilinear_fields(wl):
+    if wl == "cube8":
+        m, _ = meshes.workload_cube8()
+    elif wl == "cube_deformed":
+        m = meshes.cube(10, deform=True, permute_seed=4, boxes=(3, 4, 3))
+    else:
+        m = meshes.cylinder(6, 24, 6, grading=1.1, aspect=4.0, boxes=(4, 4, 3))
+    P = O.Problem(m.xyz, m.conn, m.part, m.boxes)
+    c = np.random.default_rng(5).standard_normal(8)
+    z = P.interp(_trilinear(c, _box_vertex_xyz(P)))
+    f = _trilinear(c, m.xyz)
+    free = ~P.dir
+    np.testing.assert_allclose(z[free], f[free], rtol=1e-13, atol=1e-13 * np.abs(f).max())
+    assert np.all(z[P.dir] == 0)
+
+
+def test_restriction_is_transpose_of_interpolation():
+    m = meshes.cube((7, 5, 6), perturb=0.15, seed=9, boxes=(3, 2, 3))
+    P = O.Problem(m.xyz, m.conn, m.part, m.boxes)
+    rng = np.random.default_rng(1)
+    u = rng.standard_normal(P.nr)
+    s = np.where(P.dir, 0.0, rng.standard_normal(m.nv))
+    assert P.interp(u) @ s == pytest.approx(u @ P.restrict(s), rel=1e-13)
+
+
+def _vertex_based_J(P):
+    """J_ij = Phi_j(x_i) from each free node's bounding box (Sec. 4, the
+    vertex-oriented construction), as a dense (n_free, n_r) matrix."""
+    nb = P.box_b + 1
+    col = -np.ones(int(np.prod(nb)), int)
+    col[P.box_active] = np.arange(P.nr)
+    J = np.zeros((P.free.size, P.nr))
+    for row, v in enumerate(P.free):
+        t = (P.xyz[v] - P.box_lo) / P.box_H
+        cell = np.clip(np.floor(t).astype(int), 0, P.box_b - 1)
+        f = t - cell
+        for m in range(8):
+            bit = [(m >> d) & 1 for d in range(3)]
+            w = np.prod([f[d] if bit[d] else 1 - f[d] for d in range(3)])
+            g = cell + bit
+            gid = g[0] + nb[0] * (g[1] + nb[1] * g[2])
+            if abs(w) > 0:
+                assert col[gid] >= 0
+                J[row, col[gid]] += w
+    return J
+
+
+def test_galerkin_equality_on_box_aligned_mesh():
+    """When element planes align with box planes J_L is continuous and the
+    cell-wise assembly (Eq. Aij) equals the Galerkin A_r = J^T A J."""
+    m = meshes.cube(8, boxes=(4, 2, 4))
+    P = O.Problem(m.xyz, m.conn, m.part, m.boxes)
+    J = _vertex_based_J(P)
+    np.testing.assert_allclose(P.Ar, J.T @ P.A.toarray() @ J, atol=1e-14 * np.abs(P.Ar).max() * 10)
+
+
+def test_boxes_equal_to_elements_give_exact_inverse():
+    n = 4
+    m = meshes.cube(n, boxes=(n, n, n))
+    P = O.Problem(m.xyz, m.conn, m.part, m.boxes)
+    assert P.nr == P.free.size
+    np.testing.assert_allclose(P.Ar, P.A.toarray(), atol=1e-14)
+    r = np.where(P.dir, 0.0, np.random.default_rng(2).standard_normal(m.nv))
+    np.testing.assert_allclose(P.box_correction(r), P.to_full(np.linalg.solve(P.A.toarray(), r[P.free])),
+                               atol=1e-12)
+
+
+def test_hybrid_residual_is_orthogonal_to_coarse_space_when_galerkin():
+    """With A_r = J~^T A J~ the coarse step of Eq. asm2 is an A-orthogonal
+    projection: J~^T (r - A z) = 0 for z = M r (hybrid)."""
+    m = meshes.cube(8, boxes=(2, 4, 2), perturb=0.0)
+    P = O.Problem(m.xyz, m.conn, m.part, m.boxes)
+    r = np.where(P.dir, 0.0, np.random.default_rng(4).standard_normal(m.nv))
+    z = P.apply_M(r, "hybrid")
+    res = P.restrict(r - P.apply_A(z))
+    assert np.abs(res).max() < 1e-12 * np.abs(P.restrict(r)).max()
+
+
+def test_reduced_space_count_golden():
+    gold = json.load(open(os.path.join(GOLDEN, "reduced_space_counts.json")))
+    b = tuple(gold["boxes"])
+    m = meshes.cube((14, 14, 24), perturb=0.1, seed=3, boxes=b)
+    P = O.Problem(m.xyz, m.conn, m.part, m.boxes)
+    assert P.nr == gold["nominal_nr"]
+    c = meshes.cylinder(6, 32, 24, grading=1.0, aspect=6.0, boxes=b)
+    Pc = O.Problem(c.xyz, c.conn, c.part, c.boxes)
+    assert Pc.nr < gold["nominal_nr"]
+    nb = np.array(b) + 1
+    a = Pc.box_active
+    i, j = a % nb[0], (a // nb[0]) % nb[1]
+    corner = ((i == 0) | (i == b[0])) & ((j == 0) | (j == b[1]))
+    assert not corner.any()
+
+
+def test_reduced_matrix_spd_and_coarse_solve_exact():
+    m, _ = meshes.workload_cube8()
+    P = O.Problem(m.xyz, m.conn, m.part, m.boxes)
+    np.testing.assert_allclose(P.Ar, P.Ar.T, atol=1e-15)
+    assert np.linalg.eigvalsh(P.Ar).min() > 0
+    rr = np.random.default_rng(0).standard_normal(P.nr)
+    np.testing.assert_allclose(P.Ar @ P.coarse_solve(rr), rr, atol=1e-11)
+
+
+# --------------------------------------------------------------------------
+# preconditioners and iteration
+# --------------------------------------------------------------------------
+
+def _dense_M(P, form):
+    cols = []
+    for j in P.free:
+        e = np.zeros(P.nv)
+        e[j] = 1.0
+        cols.append(P.apply_M(e, form)[P.free])
+    return np.array(cols).T
+
+
+def test_additive_preconditioner_symmetric_positive_definite():
+    m = meshes.cube(4, perturb=0.15, seed=0, boxes=(2, 2, 2))
+    P = O.Problem(m.xyz, m.conn, m.part, m.boxes)
+    M = _dense_M(P, "additive")
+    assert np.abs(M - M.T).max() < 1e-14 * np.abs(M).max()
+    assert np.linalg.eigvalsh(0.5 * (M + M.T)).min() > 0
+
+
+def test_single_subdomain_hybrid_is_exact():
+    m = meshes.cube(4, perturb=0.15, seed=0, boxes=(2, 2, 2))
+    part = np.zeros(m.ne, dtype=np.int32)
+    P = O.Problem(m.xyz, m.conn, part, m.boxes)
+    r = np.where(P.dir, 0.0, np.random.default_rng(8).standard_normal(m.nv))
+    exact = P.to_full(np.linalg.solve(P.A.toarray(), r[P.free]))
+    np.testing.assert_allclose(P.apply_M(r, "hybrid"), exact, atol=1e-12)
+    x, its, relres, ok = P.solve(r, rtol=1e-12)
+    assert ok and its == 1 and relres < 1e-12
+
+
+@pytest.mark.parametrize("form", ["hybrid", "additive"])
+def test_pcg_matches_dense_direct_solve(form):
+    m, b = meshes.workload_cube8()
+    P = O.Problem(m.xyz, m.conn, m.part, m.boxes)
+    x, its, relres, ok = P.solve(b, rtol=1e-13, form=form)
+    exact = P.to_full(np.linalg.solve(P.A.toarray(), b[P.free]))
+    assert ok and relres < 1e-12
+    assert np.linalg.norm(x - exact) / np.linalg.norm(exact) < 1e-11
+
+
+def test_zero_rhs_gives_zero_solution():
+    m, _ = meshes.workload_cube8()
+    P = O.Problem(m.xyz, m.conn, m.part, m.boxes)
+    x, its, relres, ok = P.solve(np.zeros(m.nv))
+    assert ok and its == 0 and not x.any()
+
+
+@pytest.mark.parametrize("n", [8, 16])
+def test_both_halves_needed_and_hybrid_beats_additive(n):
+    """Sec. 5: ASM_2 needs both the local and the box part; Sec. 3: the
+    multiplicative form takes fewer iterations than the additive one."""
+    m = meshes.cube(n, perturb=0.15, seed=0, boxes=(n // 2,) * 3 if n == 8 else (8, 8, 8))
+    b = meshes.rhs(m.nv, 1)
+    P = O.Problem(m.xyz, m.conn, m.part, m.boxes)
+    its = {f: P.solve(b, 1e-8, maxit=400, form=f) for f in ("hybrid", "additive", "local", "box")}
+    assert its["hybrid"][3] and its["additive"][3] and its["local"][3]
+    assert not its["box"][3]
+    assert its["hybrid"][1] < its["additive"][1]
+    assert its["hybrid"][1] < its["local"][1]
+
+
+def test_flexible_cg_equals_textbook_pcg_for_symmetric_preconditioner():
+    """With a symmetric M the Polak-Ribiere beta of flexible CG equals the
+    Fletcher-Reeves beta of textbook PCG in exact arithmetic, so the iterates
+    agree to rounding; a wrong beta or alpha breaks this."""
+    m, b = meshes.workload_cube8()
+    P = O.Problem(m.xyz, m.conn, m.part, m.boxes)
+    bb = np.where(P.dir, 0.0, b)
+    M = lambda r: P.apply_M(r, "additive")
+    for k in (1, 2, 5, 8):
+        x_f, its, _, _ = O.fcg(P.apply_A, M, bb, 0.0, k)
+        assert its == k
+        # textbook PCG (Hestenes-Stiefel with z = M r, beta = r1.z1 / r0.z0)
+        x = np.zeros_like(bb)
+        r = bb.copy()
+        z = M(r)
+        p = z.copy()
+        rz = r @ z
+        for _ in range(k):
+            q = P.apply_A(p)
+            a = rz / (p @ q)
+            x += a * p
+            r -= a * q
+            z = M(r)
+            rz_new = r @ z
+            p = z + (rz_new / rz) * p
+            rz = rz_new
+        np.testing.assert_allclose(x_f, x, rtol=1e-9, atol=1e-9 * np.abs(x).max())
