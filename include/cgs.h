@@ -1,0 +1,191 @@
+/*
+ * cgs.h -- C ABI of the B300 coarse-grid Schwarz solver.
+ *
+ * The library solves the N=1 element-vertex Poisson system A u = b of a pMG
+ * pressure preconditioner with flexible PCG preconditioned by the two-level
+ * overlapping Schwarz method of "Coarse Solvers for Exascale Solution of
+ * Poisson Problems" (Ratnayaka, Fischer, Olson):
+ *
+ *   local part   l = sum_p R~_p^T A_p^{-1} R_p r            (Sec. 3, Eq. asm1)
+ *   box part     B_C s = J~ A_r^{-1} J~^T s,  J~ = W Q^T J_L  (Sec. 4)
+ *   hybrid       z = l + B_C (r - A l)                      (Eq. asm2)
+ *   additive     z = sum_p R_p^T A_p^{-1} R_p r + B_C r     (Eq. asm)
+ *
+ * Conventions shared by every call
+ *   - Meshes are trilinear hexahedra.  conn[8*e + k] is the vertex of local
+ *     corner k = a + 2b + 4c, (a,b,c) in {0,1}^3 of the reference cube
+ *     (lexicographic; Sec. 1).  xyz[3*v + d] is coordinate d of vertex v.
+ *   - Vectors are float64 arrays of length nv in the caller's vertex order.
+ *     Entries at Dirichlet vertices are ignored on input and written 0 on
+ *     output.
+ *   - "device" pointers are CUDA device (or managed) memory on the mesh's
+ *     device; "host" pointers are ordinary CPU memory.  The library never
+ *     keeps a caller pointer beyond the call.
+ *   - stream is a cudaStream_t passed as void*; NULL means the legacy default
+ *     stream.  Calls are stream-ordered: they enqueue work and return without
+ *     waiting unless the description says otherwise.  A mesh owns its scratch
+ *     vectors, so two calls on the same mesh must not overlap on the GPU.
+ *   - Every call returns a cgs_status; nothing is thrown across the ABI.
+ *     cgs_last_error() returns a message for the calling thread's last error.
+ */
+#ifndef CGS_H
+#define CGS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cgs_ctx cgs_ctx;
+typedef struct cgs_mesh cgs_mesh;
+
+typedef enum {
+    CGS_OK = 0,
+    CGS_ERR_INVALID_ARG = 1,   /* null pointer, negative size, bad parameter   */
+    CGS_ERR_INVALID_MESH = 2,  /* index out of range, Jacobian <= 0            */
+    CGS_ERR_NOT_SPD = 3,       /* a local A_p or the reduced A_r not SPD       */
+    CGS_ERR_NO_CONVERGENCE = 4,/* maxit reached before the tolerance           */
+    CGS_ERR_BREAKDOWN = 5,     /* p.q <= 0, r.z <= 0 or a NaN in the iteration */
+    CGS_ERR_OOM = 6,           /* device allocation failed                     */
+    CGS_ERR_ADMISSION = 7,     /* setup would exceed the context's HBM budget  */
+    CGS_ERR_TIMEOUT = 8,       /* a bounded device-side wait expired           */
+    CGS_ERR_CUDA = 9           /* any other CUDA runtime error                 */
+} cgs_status;
+
+typedef enum {
+    CGS_FP64 = 0,        /* every step in float64 (the plain form)                   */
+    CGS_FP32_BULK = 1,   /* local solves, inner A apply, J~ and J~^T in float32;
+                            reduced solve, outer A p, residual and dots in float64   */
+    CGS_FP16_LOCAL = 2   /* as CGS_FP32_BULK, local inverses stored in float16 with
+                            one float32 scale per subdomain                          */
+} cgs_precision;
+
+typedef enum {
+    CGS_HYBRID = 0,      /* ASM_1 then ASM_2 (Eqs. asm1, asm2), W_ov-weighted local sum */
+    CGS_ADDITIVE = 1     /* Eq. asm with R~_p = R_p (symmetric)                         */
+} cgs_form;
+
+typedef struct {
+    int box[3];            /* b_x, b_y, b_z: box cells per axis over the bounding box
+                              (Sec. 4); each >= 1                                       */
+    double box_margin;     /* bounding box grown by this fraction of its extent, >= 0  */
+    int overlap_layers;    /* delta: element layers added to each Omega_p (Sec. 3), >= 0 */
+    cgs_precision prec;
+    cgs_form form;
+} cgs_params;
+
+typedef struct {
+    int64_t nv, ne;        /* vertices, elements                                      */
+    int64_t n_free;        /* non-Dirichlet vertices                                  */
+    int64_t n_sub;         /* subdomains (max elem_part + 1)                          */
+    int64_t n_r;           /* active box vertices (reduced-space unknowns, Sec. 4)    */
+    int64_t max_sub_dofs;  /* largest m_p = |R_p|                                     */
+    int64_t sum_sub_dofs;  /* sum_p m_p                                               */
+    size_t footprint_bytes;/* device memory held by the mesh                          */
+    double setup_seconds;  /* host wall time of cgs_mesh_setup                        */
+    int64_t kernel_launches; /* CUDA kernels this mesh has launched so far           */
+} cgs_mesh_info_t;
+
+/* Kernel classes reported by the profiler. */
+typedef enum {
+    CGS_K_APPLY_A64 = 0,   /* y += A x, float64 (outer product A p, FP64 inner apply) */
+    CGS_K_APPLY_A32 = 1,   /* s -= A l, float32 inner apply                           */
+    CGS_K_LOCAL = 2,       /* local solves                                            */
+    CGS_K_RESTRICT = 3,    /* r_r = J~^T s                                            */
+    CGS_K_COARSE = 4,      /* u_r = A_r^{-1} r_r                                      */
+    CGS_K_INTERP = 5,      /* z += J~ u_r                                             */
+    CGS_K_PCG_XR = 6,      /* x, r update and ||r||                                   */
+    CGS_K_PCG_DOTS = 7,    /* z.r, z.q                                                */
+    CGS_K_PCG_P = 8,       /* p = z + beta p                                          */
+    CGS_K_OTHER = 9,       /* fills, copies, init, final residual                     */
+    CGS_K_COUNT = 10
+} cgs_kernel_class;
+
+/* ---- context --------------------------------------------------------------
+ * cgs_create: binds to CUDA device `device`; hbm_budget_bytes caps the sum of
+ * footprints of the context's live meshes (0 = no cap).  *ctx owned by the
+ * caller until cgs_destroy, which must come after every cgs_mesh_free.      */
+cgs_status cgs_create(cgs_ctx** ctx, int device, size_t hbm_budget_bytes);
+cgs_status cgs_destroy(cgs_ctx* ctx);
+size_t cgs_ctx_bytes_in_use(const cgs_ctx* ctx);
+
+/* ---- setup (Sec. 3 and Sec. 4) ---------------------------------------------
+ * Builds everything the solve needs from host arrays, which are copied:
+ *   xyz       host, nv*3 float64
+ *   conn      host, ne*8 int32, entries in [0, nv)
+ *   dirichlet host, nv uint8 (nonzero = homogeneous Dirichlet vertex), or NULL:
+ *             every vertex of a boundary face (a face of exactly one element)
+ *   elem_part host, ne int32 subdomain id per element (Omega_p), ids in
+ *             [0, n_sub); NULL puts every element in one subdomain
+ *   params    host; NULL = 4x4x4 boxes, margin 0, delta 1, FP64, hybrid
+ * Host work: element matrices (2x2x2 Gauss), Dirichlet set, grown subdomains
+ * and the explicit inverses of A_p = R_p A R_p^T (Cholesky, float64), box
+ * grid, centroid cells, active box vertices, A_r by cell assembly (Eq. Aij)
+ * and its inverse (float64).  Then one upload to the device.  Synchronous.
+ * Errors: INVALID_ARG, INVALID_MESH (index out of range, Jacobian <= 0 at a
+ * quadrature point, empty mesh), NOT_SPD, ADMISSION, OOM, CUDA.  On error
+ * *out is NULL and nothing stays allocated.                                 */
+cgs_status cgs_mesh_setup(cgs_ctx* ctx, const double* xyz, int64_t nv,
+                          const int32_t* conn, int64_t ne,
+                          const uint8_t* dirichlet, const int32_t* elem_part,
+                          const cgs_params* params, cgs_mesh** out);
+cgs_status cgs_mesh_free(cgs_mesh* mesh);
+cgs_status cgs_mesh_info(const cgs_mesh* mesh, cgs_mesh_info_t* info);
+/* Switch the preconditioner form of an existing mesh (no new data needed). */
+cgs_status cgs_mesh_set_form(cgs_mesh* mesh, cgs_form form);
+/* Host copies of setup results, for checking: dirichlet (nv uint8),
+ * box_active (n_r int64 lexicographic box-vertex ids (i + (b_x+1)(j + (b_y+1)k)),
+ * sub_ptr (n_sub+1 int64) and sub_idx (sum_sub_dofs int32 ascending vertex ids).
+ * Any output pointer may be NULL.  Synchronous.                             */
+cgs_status cgs_mesh_export(const cgs_mesh* mesh, uint8_t* dirichlet, int64_t* box_active,
+                           int64_t* sub_ptr, int32_t* sub_idx);
+
+/* ---- hot-path steps, device vectors, stream-ordered -------------------------
+ * cgs_apply_A: y = A x, A = Q^T A_L Q (Sec. 3), float64.  x, y device, nv.  */
+cgs_status cgs_apply_A(cgs_mesh* mesh, const double* x, double* y, void* stream);
+/* cgs_apply_local: l = sum_p R_p^T A_p^{-1} R_p r (Eq. asm1), weighted by
+ * W_ov = 1/multiplicity when `weighted` != 0.  Mesh precision.              */
+cgs_status cgs_apply_local(cgs_mesh* mesh, const double* r, double* l, int weighted, void* stream);
+/* cgs_restrict: r_r = J_L^T Q W s (Sec. 4); s device nv, r_r device n_r.     */
+cgs_status cgs_restrict(cgs_mesh* mesh, const double* s, double* rr, void* stream);
+/* cgs_coarse_solve: u_r = A_r^{-1} r_r, float64; device n_r vectors.        */
+cgs_status cgs_coarse_solve(cgs_mesh* mesh, const double* rr, double* ur, void* stream);
+/* cgs_interp: z = W Q^T J_L u_r (Sec. 4); u_r device n_r, z device nv.       */
+cgs_status cgs_interp(cgs_mesh* mesh, const double* ur, double* z, void* stream);
+/* cgs_apply_preconditioner: z = M r in the mesh's form and precision.       */
+cgs_status cgs_apply_preconditioner(cgs_mesh* mesh, const double* r, double* z, void* stream);
+
+/* ---- solve ----------------------------------------------------------------
+ * cgs_solve: flexible PCG (Polak-Ribiere beta, x0 = 0) on A x = b for nrhs
+ * right-hand sides stored back to back (b[k*nv ...]); stops when the
+ * recursive residual satisfies ||r|| <= rtol ||b|| or after maxit products
+ * A p.  b, x device.  iters[k] = products A p used, relres[k] = true
+ * ||b - A x|| / ||b|| (0 when b = 0), both host arrays of nrhs, always
+ * written.  Synchronous (waits for the stream).  Returns NO_CONVERGENCE or
+ * BREAKDOWN for the first right-hand side that failed; the others are still
+ * solved.                                                                   */
+cgs_status cgs_solve(cgs_mesh* mesh, const double* b, double* x, int nrhs, double rtol,
+                     int maxit, int* iters, double* relres, void* stream);
+/* cgs_solve_host: as cgs_solve with b and x in HOST memory; copies them to
+ * and from the device inside the call (pinned memory makes this faster).    */
+cgs_status cgs_solve_host(cgs_mesh* mesh, const double* b_host, double* x_host, int nrhs,
+                          double rtol, int maxit, int* iters, double* relres, void* stream);
+
+/* ---- profiling --------------------------------------------------------------
+ * cgs_profile_enable: when on, every kernel the mesh launches is bracketed by
+ * CUDA events recorded on its launching stream (adds host cost per launch).
+ * cgs_profile_read: waits for the device, then writes per kernel class the
+ * summed event time in milliseconds (ms[CGS_K_COUNT]) and the launch count
+ * (launches[CGS_K_COUNT]) since the last read, and resets them.            */
+cgs_status cgs_profile_enable(cgs_mesh* mesh, int enable);
+cgs_status cgs_profile_read(cgs_mesh* mesh, double* ms, int64_t* launches);
+
+const char* cgs_status_string(cgs_status s);
+const char* cgs_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CGS_H */

@@ -1,0 +1,264 @@
+"""Thin Python binding of the C ABI in include/cgs.h (argument marshalling only).
+
+Every function keeps the C name.  Device vectors are passed as CUDA tensors
+(float64, contiguous) or raw device addresses; host arrays as numpy arrays.
+All computation happens in libcgs.so; if the library is missing this module
+raises on import of the library instead of falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libcgs.so")
+
+OK, ERR_INVALID_ARG, ERR_INVALID_MESH, ERR_NOT_SPD, ERR_NO_CONVERGENCE, ERR_BREAKDOWN, ERR_OOM, \
+    ERR_ADMISSION, ERR_TIMEOUT, ERR_CUDA = range(10)
+PREC = {"fp64": 0, "fp32": 1, "fp16": 2}
+FORM = {"hybrid": 0, "additive": 1}
+
+# every symbol include/cgs.h declares
+EXPORTS = (
+    "cgs_create", "cgs_destroy", "cgs_ctx_bytes_in_use", "cgs_mesh_setup", "cgs_mesh_free", "cgs_mesh_info",
+    "cgs_mesh_set_form", "cgs_mesh_export", "cgs_apply_A", "cgs_apply_local", "cgs_restrict",
+    "cgs_coarse_solve", "cgs_interp", "cgs_apply_preconditioner", "cgs_solve", "cgs_solve_host",
+    "cgs_profile_enable", "cgs_profile_read", "cgs_status_string", "cgs_last_error",
+)
+KERNEL_CLASSES = ("apply_A64", "apply_A32", "local", "restrict", "coarse", "interp", "pcg_xr", "pcg_dots",
+                  "pcg_p", "other")
+
+
+class CGSError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        super().__init__(f"{where}: status {status} ({msg})")
+        self.status = status
+
+
+class Params(C.Structure):
+    _fields_ = [("box", C.c_int * 3), ("box_margin", C.c_double), ("overlap_layers", C.c_int),
+                ("prec", C.c_int), ("form", C.c_int)]
+
+
+class MeshInfo(C.Structure):
+    _fields_ = [("nv", C.c_int64), ("ne", C.c_int64), ("n_free", C.c_int64), ("n_sub", C.c_int64),
+                ("n_r", C.c_int64), ("max_sub_dofs", C.c_int64), ("sum_sub_dofs", C.c_int64),
+                ("footprint_bytes", C.c_size_t), ("setup_seconds", C.c_double),
+                ("kernel_launches", C.c_int64)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libcgs.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} not built: run `python -m paper_2606_20496_b300.build`")
+    lib = C.CDLL(path)
+    P, I64, I32, D = C.c_void_p, C.c_int64, C.c_int, C.c_double
+    sig = {
+        "cgs_create": ([C.POINTER(P), I32, C.c_size_t], I32),
+        "cgs_destroy": ([P], I32),
+        "cgs_ctx_bytes_in_use": ([P], C.c_size_t),
+        "cgs_mesh_setup": ([P, P, I64, P, I64, P, P, C.POINTER(Params), C.POINTER(P)], I32),
+        "cgs_mesh_free": ([P], I32),
+        "cgs_mesh_info": ([P, C.POINTER(MeshInfo)], I32),
+        "cgs_mesh_set_form": ([P, I32], I32),
+        "cgs_mesh_export": ([P, P, P, P, P], I32),
+        "cgs_apply_A": ([P, P, P, P], I32),
+        "cgs_apply_local": ([P, P, P, I32, P], I32),
+        "cgs_restrict": ([P, P, P, P], I32),
+        "cgs_coarse_solve": ([P, P, P, P], I32),
+        "cgs_interp": ([P, P, P, P], I32),
+        "cgs_apply_preconditioner": ([P, P, P, P], I32),
+        "cgs_solve": ([P, P, P, I32, D, I32, P, P, P], I32),
+        "cgs_solve_host": ([P, P, P, I32, D, I32, P, P, P], I32),
+        "cgs_profile_enable": ([P, I32], I32),
+        "cgs_profile_read": ([P, P, P], I32),
+        "cgs_status_string": ([I32], C.c_char_p),
+        "cgs_last_error": ([], C.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = lib
+    return lib
+
+
+def _ptr(a):
+    """Address of a CUDA tensor, a numpy array, an int address or None."""
+    if a is None:
+        return None
+    if isinstance(a, int):
+        return a
+    if isinstance(a, np.ndarray):
+        if not a.flags.c_contiguous:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr()
+    raise TypeError(type(a))
+
+
+def _stream(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except ImportError:
+            pass
+        return None
+    return stream if isinstance(stream, int) else stream.cuda_stream
+
+
+def _check(status: int, where: str, allow=()):
+    if status != OK and status not in allow:
+        lib = load()
+        raise CGSError(status, where, lib.cgs_last_error().decode())
+    return status
+
+
+def status_string(status: int) -> str:
+    return load().cgs_status_string(status).decode()
+
+
+# ---------------------------------------------------------------------------
+# C-named wrappers
+# ---------------------------------------------------------------------------
+
+def cgs_create(device: int = 0, hbm_budget_bytes: int = 0):
+    ctx = C.c_void_p()
+    _check(load().cgs_create(C.byref(ctx), device, hbm_budget_bytes), "cgs_create")
+    return ctx
+
+
+def cgs_destroy(ctx):
+    _check(load().cgs_destroy(ctx), "cgs_destroy")
+
+
+def cgs_ctx_bytes_in_use(ctx) -> int:
+    return int(load().cgs_ctx_bytes_in_use(ctx))
+
+
+def cgs_mesh_setup(ctx, xyz, conn, dirichlet=None, elem_part=None, boxes=(4, 4, 4), margin=0.0, overlap=1,
+                   prec="fp64", form="hybrid"):
+    xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+    conn = np.ascontiguousarray(conn, dtype=np.int32)
+    d = None if dirichlet is None else np.ascontiguousarray(dirichlet, dtype=np.uint8)
+    part = None if elem_part is None else np.ascontiguousarray(elem_part, dtype=np.int32)
+    prm = Params((C.c_int * 3)(*[int(b) for b in boxes]), float(margin), int(overlap), PREC[prec], FORM[form])
+    mesh = C.c_void_p()
+    st = load().cgs_mesh_setup(ctx, _ptr(xyz), xyz.shape[0], _ptr(conn), conn.shape[0], _ptr(d), _ptr(part),
+                               C.byref(prm), C.byref(mesh))
+    _check(st, "cgs_mesh_setup")
+    return mesh
+
+
+def cgs_mesh_free(mesh):
+    _check(load().cgs_mesh_free(mesh), "cgs_mesh_free")
+
+
+def cgs_mesh_info(mesh) -> dict:
+    info = MeshInfo()
+    _check(load().cgs_mesh_info(mesh, C.byref(info)), "cgs_mesh_info")
+    return {f: getattr(info, f) for f, _ in MeshInfo._fields_}
+
+
+def cgs_mesh_set_form(mesh, form: str):
+    _check(load().cgs_mesh_set_form(mesh, FORM[form]), "cgs_mesh_set_form")
+
+
+def cgs_mesh_export(mesh) -> dict:
+    info = cgs_mesh_info(mesh)
+    out = {"dirichlet": np.zeros(info["nv"], np.uint8), "box_active": np.zeros(info["n_r"], np.int64),
+           "sub_ptr": np.zeros(info["n_sub"] + 1, np.int64), "sub_idx": np.zeros(info["sum_sub_dofs"], np.int32)}
+    _check(load().cgs_mesh_export(mesh, *(_ptr(out[k]) for k in ("dirichlet", "box_active", "sub_ptr", "sub_idx"))),
+           "cgs_mesh_export")
+    return out
+
+
+def cgs_apply_A(mesh, x, y, stream=None):
+    _check(load().cgs_apply_A(mesh, _ptr(x), _ptr(y), _stream(stream)), "cgs_apply_A")
+
+
+def cgs_apply_local(mesh, r, l, weighted=True, stream=None):
+    _check(load().cgs_apply_local(mesh, _ptr(r), _ptr(l), int(bool(weighted)), _stream(stream)), "cgs_apply_local")
+
+
+def cgs_restrict(mesh, s, rr, stream=None):
+    _check(load().cgs_restrict(mesh, _ptr(s), _ptr(rr), _stream(stream)), "cgs_restrict")
+
+
+def cgs_coarse_solve(mesh, rr, ur, stream=None):
+    _check(load().cgs_coarse_solve(mesh, _ptr(rr), _ptr(ur), _stream(stream)), "cgs_coarse_solve")
+
+
+def cgs_interp(mesh, ur, z, stream=None):
+    _check(load().cgs_interp(mesh, _ptr(ur), _ptr(z), _stream(stream)), "cgs_interp")
+
+
+def cgs_apply_preconditioner(mesh, r, z, stream=None):
+    _check(load().cgs_apply_preconditioner(mesh, _ptr(r), _ptr(z), _stream(stream)), "cgs_apply_preconditioner")
+
+
+def cgs_solve(mesh, b, x, nrhs=1, rtol=1e-8, maxit=1000, stream=None, allow=(ERR_NO_CONVERGENCE, ERR_BREAKDOWN)):
+    """Returns (status, iters ndarray, relres ndarray)."""
+    iters = np.zeros(nrhs, np.int32)
+    relres = np.zeros(nrhs, np.float64)
+    st = load().cgs_solve(mesh, _ptr(b), _ptr(x), nrhs, float(rtol), int(maxit), _ptr(iters), _ptr(relres),
+                          _stream(stream))
+    _check(st, "cgs_solve", allow)
+    return st, iters, relres
+
+
+def cgs_solve_host(mesh, b, x, nrhs=1, rtol=1e-8, maxit=1000, stream=None,
+                   allow=(ERR_NO_CONVERGENCE, ERR_BREAKDOWN)):
+    """b, x host numpy float64 arrays (pinned tensors work too)."""
+    iters = np.zeros(nrhs, np.int32)
+    relres = np.zeros(nrhs, np.float64)
+    st = load().cgs_solve_host(mesh, _ptr(b), _ptr(x), nrhs, float(rtol), int(maxit), _ptr(iters),
+                               _ptr(relres), _stream(stream))
+    _check(st, "cgs_solve_host", allow)
+    return st, iters, relres
+
+
+def cgs_profile_enable(mesh, enable=True):
+    _check(load().cgs_profile_enable(mesh, int(bool(enable))), "cgs_profile_enable")
+
+
+def cgs_profile_read(mesh) -> dict:
+    """{kernel class: (milliseconds, launches)} since the last read."""
+    ms = np.zeros(len(KERNEL_CLASSES), np.float64)
+    n = np.zeros(len(KERNEL_CLASSES), np.int64)
+    _check(load().cgs_profile_read(mesh, _ptr(ms), _ptr(n)), "cgs_profile_read")
+    return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(KERNEL_CLASSES)}
+
+
+class Mesh:
+    """Owning handle around cgs_mesh_setup / cgs_mesh_free."""
+
+    def __init__(self, ctx, xyz, conn, part=None, boxes=(4, 4, 4), dirichlet=None, margin=0.0, overlap=1,
+                 prec="fp64", form="hybrid"):
+        self.handle = cgs_mesh_setup(ctx, xyz, conn, dirichlet, part, boxes, margin, overlap, prec, form)
+        self.info = cgs_mesh_info(self.handle)
+        self.prec = prec
+
+    def free(self):
+        if self.handle is not None:
+            cgs_mesh_free(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.free()

@@ -1,0 +1,96 @@
+// Internal declarations shared by the host setup, the CUDA kernels and the
+// C ABI.  Not installed; the public interface is include/cgs.h.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include "../../include/cgs.h"
+
+namespace cgs {
+
+// Number of stored entries of a symmetric 8x8 element matrix.
+constexpr int kUpper = 36;   // upper triangle including the diagonal, (i <= j)
+constexpr int kOff = 28;     // strict upper triangle (i < j); diagonal = -row sum
+constexpr int kPackAlign = 8;  // packed inverses start on multiples of 8 entries
+
+// Everything the host setup produces, in the layout the device uses.
+struct HostSetup {
+    int64_t nv = 0, ne = 0, n_free = 0, n_sub = 0, nr = 0;
+    int64_t max_m = 0, sum_m = 0;
+    // elements in device order (sorted by centroid cell, then subdomain, then id)
+    std::vector<int32_t> elem_order;   // device slot -> caller element id
+    std::vector<int32_t> conn;         // ne*8, vertex id, or ~v for a Dirichlet vertex
+    std::vector<double> a36;           // SoA [kUpper][ne] element matrices, float64
+    std::vector<float> a28;            // SoA [kOff][ne] off-diagonals, float32
+    std::vector<uint8_t> dir;          // nv, 1 = Dirichlet
+    std::vector<double> invcnt;        // nv, 1 / (elements at the vertex)
+    std::vector<double> wov;           // nv, 1 / (subdomains holding the vertex), 0 if none
+    // subdomains, in caller order
+    std::vector<int64_t> sub_ptr;      // n_sub+1
+    std::vector<int32_t> sub_idx;      // sum_m, ascending vertex ids per subdomain
+    std::vector<int64_t> inv_ptr;      // n_sub+1, offsets (entries) of packed inverses
+    std::vector<double> inv;           // packed lower triangle, row-major, float64
+    // box coarse space
+    int b[3] = {1, 1, 1};
+    double lo[3] = {0, 0, 0}, H[3] = {1, 1, 1};
+    std::vector<int32_t> cell;         // ne (device order), lexicographic cell id
+    std::vector<int32_t> cell_cols;    // ncell*8, active column of each cell corner or -1
+    std::vector<int64_t> box_active;   // nr, lexicographic box-vertex ids
+    std::vector<double> ar_inv;        // nr*nr, A_r^{-1}, full symmetric, float64
+    double seconds = 0.0;
+};
+
+// Host setup (setup.cpp).  Returns CGS_OK or an error with a message in err.
+cgs_status host_setup(const double* xyz, int64_t nv, const int32_t* conn, int64_t ne,
+                      const uint8_t* dirichlet, const int32_t* elem_part,
+                      const cgs_params& prm, HostSetup& out, std::string& err);
+
+// Device-resident mesh data (api.cu allocates, kernels.cu reads).
+struct DevMesh {
+    int64_t nv = 0, ne = 0, n_sub = 0, nr = 0;
+    int b[3] = {1, 1, 1};
+    double lo[3] = {0, 0, 0}, H[3] = {1, 1, 1};
+    float lof[3] = {0, 0, 0}, Hf[3] = {1, 1, 1};
+    const int32_t* conn = nullptr;     // ne*8 (int4 x2 per element)
+    const double* a36 = nullptr;       // [36][ne]
+    const float* a28 = nullptr;        // [28][ne]
+    const double2* xyzw = nullptr;     // 2*nv: (x, y), (z, 1/count) per vertex, float64
+    const float4* xyzwf = nullptr;     // nv: same, float32
+    const int32_t* cell = nullptr;     // ne
+    const int32_t* cell_cols = nullptr;// ncell*8
+    // subdomains grouped by size class for the warp kernels
+    const int32_t* sub_ptr = nullptr;  // n_sub+1 (int32 offsets into sub_idx)
+    const int32_t* sub_idx = nullptr;
+    const int64_t* inv_ptr = nullptr;  // n_sub+1
+    const double* inv64 = nullptr;
+    const float* inv32 = nullptr;
+    const __half* inv16 = nullptr;
+    const float* inv16_scale = nullptr;// n_sub
+    const double* wov64 = nullptr;     // nv
+    const float* wov32 = nullptr;      // nv
+    const double* ar_inv = nullptr;    // nr*nr
+    int max_m = 0;
+};
+
+// Device scalars of one PCG solve (kernels.cu).
+struct SolveScalars {
+    double bnorm2;     // ||b||^2
+    double tol2;       // (rtol ||b||)^2
+    double rho;        // r.z of the current iterate
+    double pq;         // p.A p
+    double alpha, beta;
+    double rr;         // ||r||^2 after the update
+    double zr, zq;     // z.r and z.q for the next direction
+    int iters;
+    int maxit;
+    int done;          // 1 = stop (converged, failed or maxit)
+    int status;        // cgs_status of the solve
+    unsigned int ticket[4];  // block-completion counters of the fused reductions
+};
+
+}  // namespace cgs

@@ -1,0 +1,545 @@
+// Host setup of the two-level Schwarz coarse solver: everything that is built
+// once per mesh and then kept resident on the device.
+//
+//   element matrices   a^e_ij = int grad l_i . grad l_j dV, trilinear map,
+//                      2x2x2 Gauss-Legendre (Sec. 3)
+//   Dirichlet set      vertices of faces owned by one element (homogeneous
+//                      Dirichlet, Sec. 3), unless the caller gives a mask
+//   subdomains         Omega_p grown by delta layers of vertex-sharing
+//                      elements; R_p = free vertices whose elements all lie in
+//                      the grown set ("interior to the extended subdomain",
+//                      Sec. 3); A_p = R_p A R_p^T and its explicit inverse
+//   box coarse space   bounding box split in b_x*b_y*b_z cells; each element
+//                      belongs to the cell holding its centroid; J_L evaluates
+//                      the cell's trilinear hats at the element's vertices
+//                      (rows of Dirichlet vertices zero); active box vertices
+//                      are the corners of occupied cells with a nonzero column
+//                      (Sec. 4); A_r = sum_e J_e^T A^e J_e cell by cell
+//                      (Eq. Aij) and its inverse.
+//
+// The device keeps explicit inverses instead of sparse Cholesky factors (the
+// paper's CHOLMOD and XX^T): a GEMV with a 27..64-dof inverse is one coalesced
+// stream per subdomain, where a triangular solve would be two dependent sweeps.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+
+#include <omp.h>
+
+#include "internal.h"
+
+namespace cgs {
+namespace {
+
+constexpr int kMaxSubDofs = 16384;
+
+// Stiffness of one trilinear hexahedron, 2x2x2 Gauss points (weights 1).
+// Returns the smallest Jacobian determinant met at a quadrature point.
+double hex_stiffness(const double X[8][3], double A[8][8]) {
+    const double g = 1.0 / std::sqrt(3.0);
+    double min_det = 1e300;
+    for (int i = 0; i < 8; ++i)
+        for (int j = 0; j < 8; ++j) A[i][j] = 0.0;
+    for (int q = 0; q < 8; ++q) {
+        double xi[3];
+        for (int d = 0; d < 3; ++d) xi[d] = ((q >> d) & 1) ? g : -g;
+        // reference gradients dN[k][a]
+        double dN[8][3];
+        for (int k = 0; k < 8; ++k) {
+            double s[3], f[3];
+            for (int d = 0; d < 3; ++d) {
+                s[d] = ((k >> d) & 1) ? 1.0 : -1.0;
+                f[d] = 1.0 + s[d] * xi[d];
+            }
+            dN[k][0] = 0.125 * s[0] * f[1] * f[2];
+            dN[k][1] = 0.125 * s[1] * f[0] * f[2];
+            dN[k][2] = 0.125 * s[2] * f[0] * f[1];
+        }
+        // Jacobian J[d][a] = dx_d / dxi_a
+        double J[3][3] = {{0}};
+        for (int k = 0; k < 8; ++k)
+            for (int d = 0; d < 3; ++d)
+                for (int a = 0; a < 3; ++a) J[d][a] += X[k][d] * dN[k][a];
+        // cofactors: inverse(J)[a][d] = C[d][a] / det
+        double C[3][3];
+        C[0][0] = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+        C[0][1] = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+        C[0][2] = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+        C[1][0] = J[0][2] * J[2][1] - J[0][1] * J[2][2];
+        C[1][1] = J[0][0] * J[2][2] - J[0][2] * J[2][0];
+        C[1][2] = J[0][1] * J[2][0] - J[0][0] * J[2][1];
+        C[2][0] = J[0][1] * J[1][2] - J[0][2] * J[1][1];
+        C[2][1] = J[0][2] * J[1][0] - J[0][0] * J[1][2];
+        C[2][2] = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+        const double det = J[0][0] * C[0][0] + J[0][1] * C[0][1] + J[0][2] * C[0][2];
+        min_det = std::min(min_det, det);
+        if (!(det > 0.0)) continue;
+        // physical gradients B[k][d] = sum_a dN[k][a] * inv(J)[a][d]
+        double B[8][3];
+        for (int k = 0; k < 8; ++k)
+            for (int d = 0; d < 3; ++d)
+                B[k][d] = (dN[k][0] * C[d][0] + dN[k][1] * C[d][1] + dN[k][2] * C[d][2]) / det;
+        for (int i = 0; i < 8; ++i)
+            for (int j = i; j < 8; ++j)
+                A[i][j] += det * (B[i][0] * B[j][0] + B[i][1] * B[j][1] + B[i][2] * B[j][2]);
+    }
+    for (int i = 0; i < 8; ++i)
+        for (int j = 0; j < i; ++j) A[i][j] = A[j][i];
+    return min_det;
+}
+
+inline double dot(const double* a, const double* b, int n) {
+    double s = 0.0;
+    for (int k = 0; k < n; ++k) s += a[k] * b[k];
+    return s;
+}
+
+// Explicit inverse of an SPD n x n row-major matrix `a` (destroyed) through
+// its Cholesky factor: a = L L^T, Y = L^{-1}, inv = Y^T Y.  Returns false if
+// a pivot is not positive.  `threads` > 1 parallelises the three O(n^3/6)
+// sweeps.
+bool spd_inverse(double* a, int n, double* inv, int threads) {
+    for (int j = 0; j < n; ++j) {
+        double* Lj = a + (size_t)j * n;
+        const double d = Lj[j] - dot(Lj, Lj, j);
+        if (!(d > 0.0) || !std::isfinite(d)) return false;
+        const double ljj = std::sqrt(d);
+        Lj[j] = ljj;
+#pragma omp parallel for schedule(static) num_threads(threads) if (threads > 1 && n - j > 64)
+        for (int i = j + 1; i < n; ++i) {
+            double* Li = a + (size_t)i * n;
+            Li[j] = (Li[j] - dot(Li, Lj, j)) / ljj;
+        }
+    }
+    // columns of Y = L^{-1}, column c stored contiguously in Y[c*n + i], i >= c
+    std::vector<double> Y((size_t)n * n, 0.0);
+#pragma omp parallel for schedule(dynamic, 8) num_threads(threads) if (threads > 1)
+    for (int c = 0; c < n; ++c) {
+        double* y = Y.data() + (size_t)c * n;
+        y[c] = 1.0 / a[(size_t)c * n + c];
+        for (int i = c + 1; i < n; ++i) {
+            const double* Li = a + (size_t)i * n;
+            double s = 0.0;
+            for (int k = c; k < i; ++k) s += Li[k] * y[k];
+            y[i] = -s / Li[i];
+        }
+    }
+    // inv[i][j] = sum_{k >= max(i,j)} Y[k][i] Y[k][j]
+#pragma omp parallel for schedule(dynamic, 8) num_threads(threads) if (threads > 1)
+    for (int i = 0; i < n; ++i) {
+        const double* yi = Y.data() + (size_t)i * n;
+        for (int j = 0; j <= i; ++j) {
+            const double* yj = Y.data() + (size_t)j * n;
+            const double v = dot(yi + i, yj + i, n - i);
+            inv[(size_t)i * n + j] = v;
+            inv[(size_t)j * n + i] = v;
+        }
+    }
+    return true;
+}
+
+// Upper-triangle slot of the pair (i, j), i <= j, in the 36-entry layout.
+inline int upper_slot(int i, int j) { return i * 8 - i * (i - 1) / 2 + (j - i); }
+// Strict-upper slot of (i, j), i < j, in the 28-entry layout.
+inline int off_slot(int i, int j) { return i * 7 - i * (i - 1) / 2 + (j - i - 1); }
+
+}  // namespace
+
+cgs_status host_setup(const double* xyz, int64_t nv, const int32_t* conn, int64_t ne,
+                      const uint8_t* dirichlet, const int32_t* elem_part,
+                      const cgs_params& prm, HostSetup& S, std::string& err) {
+    const auto t0 = std::chrono::steady_clock::now();
+    const int nthreads = std::max(1, omp_get_max_threads());
+    if (!xyz || !conn || nv <= 0 || ne <= 0) {
+        err = "empty mesh or null input";
+        return nv <= 0 || ne <= 0 ? CGS_ERR_INVALID_MESH : CGS_ERR_INVALID_ARG;
+    }
+    if (nv >= INT32_MAX || ne >= INT32_MAX / 8) {
+        err = "mesh too large for 32-bit indices";
+        return CGS_ERR_INVALID_ARG;
+    }
+    for (int d = 0; d < 3; ++d)
+        if (prm.box[d] < 1 || prm.box[d] > 4096) {
+            err = "box counts must lie in [1, 4096]";
+            return CGS_ERR_INVALID_ARG;
+        }
+    if (prm.overlap_layers < 0 || !(prm.box_margin >= 0.0)) {
+        err = "negative overlap or margin";
+        return CGS_ERR_INVALID_ARG;
+    }
+    for (int64_t i = 0; i < ne * 8; ++i)
+        if (conn[i] < 0 || conn[i] >= nv) {
+            err = "connectivity index out of range at entry " + std::to_string(i);
+            return CGS_ERR_INVALID_MESH;
+        }
+    int64_t n_sub = 1;
+    if (elem_part) {
+        int64_t mx = -1;
+        for (int64_t e = 0; e < ne; ++e) {
+            if (elem_part[e] < 0) {
+                err = "negative subdomain id";
+                return CGS_ERR_INVALID_ARG;
+            }
+            mx = std::max<int64_t>(mx, elem_part[e]);
+        }
+        n_sub = mx + 1;
+    }
+    S.nv = nv;
+    S.ne = ne;
+    S.n_sub = n_sub;
+
+    // ---- element matrices ---------------------------------------------------
+    std::vector<double> Ae((size_t)ne * 64);
+    double min_det = 1e300;
+#pragma omp parallel for schedule(static) reduction(min : min_det)
+    for (int64_t e = 0; e < ne; ++e) {
+        double X[8][3];
+        for (int k = 0; k < 8; ++k)
+            for (int d = 0; d < 3; ++d) X[k][d] = xyz[(size_t)conn[e * 8 + k] * 3 + d];
+        double A[8][8];
+        min_det = std::min(min_det, hex_stiffness(X, A));
+        std::memcpy(&Ae[(size_t)e * 64], A, sizeof(A));
+    }
+    if (!(min_det > 0.0)) {
+        err = "element with non-positive Jacobian at a quadrature point";
+        return CGS_ERR_INVALID_MESH;
+    }
+
+    // ---- Dirichlet set ------------------------------------------------------
+    S.dir.assign(nv, 0);
+    if (dirichlet) {
+        for (int64_t v = 0; v < nv; ++v) S.dir[v] = dirichlet[v] ? 1 : 0;
+    } else {
+        struct Face { int32_t v[4]; };
+        std::vector<Face> faces((size_t)ne * 6);
+        for (int64_t e = 0; e < ne; ++e) {
+            for (int d = 0; d < 3; ++d)
+                for (int side = 0; side < 2; ++side) {
+                    Face f;
+                    int n = 0;
+                    for (int k = 0; k < 8; ++k)
+                        if (((k >> d) & 1) == side) f.v[n++] = conn[e * 8 + k];
+                    std::sort(f.v, f.v + 4);
+                    faces[(size_t)e * 6 + d * 2 + side] = f;
+                }
+        }
+        auto less = [](const Face& a, const Face& b) {
+            return std::lexicographical_compare(a.v, a.v + 4, b.v, b.v + 4);
+        };
+        std::sort(faces.begin(), faces.end(), less);
+        for (size_t i = 0; i < faces.size();) {
+            size_t j = i + 1;
+            while (j < faces.size() && std::equal(faces[i].v, faces[i].v + 4, faces[j].v)) ++j;
+            if (j - i == 1)
+                for (int k = 0; k < 4; ++k) S.dir[faces[i].v[k]] = 1;
+            i = j;
+        }
+    }
+    S.n_free = 0;
+    for (int64_t v = 0; v < nv; ++v) S.n_free += !S.dir[v];
+
+    // ---- vertex -> element adjacency, element counts --------------------------
+    std::vector<int64_t> v2e_ptr(nv + 1, 0);
+    for (int64_t i = 0; i < ne * 8; ++i) v2e_ptr[conn[i] + 1]++;
+    for (int64_t v = 0; v < nv; ++v) v2e_ptr[v + 1] += v2e_ptr[v];
+    std::vector<int32_t> v2e(ne * 8);
+    {
+        std::vector<int64_t> fill(v2e_ptr.begin(), v2e_ptr.end() - 1);
+        for (int64_t e = 0; e < ne; ++e)
+            for (int k = 0; k < 8; ++k) {
+                const int32_t v = conn[e * 8 + k];
+                // an element listing one vertex twice is degenerate (caught by det)
+                v2e[fill[v]++] = (int32_t)e;
+            }
+    }
+    S.invcnt.assign(nv, 0.0);
+    for (int64_t v = 0; v < nv; ++v) {
+        const int64_t c = v2e_ptr[v + 1] - v2e_ptr[v];
+        S.invcnt[v] = c > 0 ? 1.0 / (double)c : 0.0;
+    }
+
+    // ---- subdomains: grow, select R_p, invert A_p -------------------------
+    std::vector<int64_t> part_ptr(n_sub + 1, 0);
+    std::vector<int32_t> part_el(ne);
+    for (int64_t e = 0; e < ne; ++e) part_ptr[(elem_part ? elem_part[e] : 0) + 1]++;
+    for (int64_t p = 0; p < n_sub; ++p) part_ptr[p + 1] += part_ptr[p];
+    {
+        std::vector<int64_t> fill(part_ptr.begin(), part_ptr.end() - 1);
+        for (int64_t e = 0; e < ne; ++e) part_el[fill[elem_part ? elem_part[e] : 0]++] = (int32_t)e;
+    }
+    std::vector<std::vector<int32_t>> sub_sets(n_sub);
+    std::vector<std::vector<double>> sub_inv(n_sub);
+    bool not_spd = false, too_big = false;
+#pragma omp parallel
+    {
+        std::vector<int32_t> estamp(ne, -1), vcount(nv, 0), vpos(nv, -1);
+        std::vector<int32_t> grown, frontier, touched;
+        std::vector<double> Ap;
+#pragma omp for schedule(dynamic, 16)
+        for (int64_t p = 0; p < n_sub; ++p) {
+            grown.assign(part_el.begin() + part_ptr[p], part_el.begin() + part_ptr[p + 1]);
+            for (int32_t e : grown) estamp[e] = (int32_t)p;
+            size_t layer_begin = 0;
+            for (int layer = 0; layer < prm.overlap_layers; ++layer) {
+                const size_t layer_end = grown.size();
+                for (size_t i = layer_begin; i < layer_end; ++i) {
+                    const int32_t e = grown[i];
+                    for (int k = 0; k < 8; ++k) {
+                        const int32_t v = conn[(int64_t)e * 8 + k];
+                        for (int64_t t = v2e_ptr[v]; t < v2e_ptr[v + 1]; ++t) {
+                            const int32_t f = v2e[t];
+                            if (estamp[f] != (int32_t)p) {
+                                estamp[f] = (int32_t)p;
+                                grown.push_back(f);
+                            }
+                        }
+                    }
+                }
+                layer_begin = layer_end;
+            }
+            // vertices all of whose elements are in the grown set
+            touched.clear();
+            for (int32_t e : grown)
+                for (int k = 0; k < 8; ++k) {
+                    const int32_t v = conn[(int64_t)e * 8 + k];
+                    if (vcount[v]++ == 0) touched.push_back(v);
+                }
+            std::vector<int32_t>& R = sub_sets[p];
+            R.clear();
+            for (int32_t v : touched)
+                if (!S.dir[v] && vcount[v] == v2e_ptr[v + 1] - v2e_ptr[v]) R.push_back(v);
+            for (int32_t v : touched) vcount[v] = 0;
+            std::sort(R.begin(), R.end());
+            const int m = (int)R.size();
+            if (m > kMaxSubDofs) {
+#pragma omp atomic write
+                too_big = true;
+                continue;
+            }
+            if (m == 0) continue;
+            for (int i = 0; i < m; ++i) vpos[R[i]] = i;
+            Ap.assign((size_t)m * m, 0.0);
+            for (int32_t e : grown) {
+                const double* A = &Ae[(size_t)e * 64];
+                int loc[8];
+                for (int k = 0; k < 8; ++k) loc[k] = vpos[conn[(int64_t)e * 8 + k]];
+                for (int k = 0; k < 8; ++k) {
+                    if (loc[k] < 0) continue;
+                    for (int l = 0; l < 8; ++l)
+                        if (loc[l] >= 0) Ap[(size_t)loc[k] * m + loc[l]] += A[k * 8 + l];
+                }
+            }
+            for (int i = 0; i < m; ++i) vpos[R[i]] = -1;
+            std::vector<double> full((size_t)m * m);
+            if (!spd_inverse(Ap.data(), m, full.data(), 1)) {
+#pragma omp atomic write
+                not_spd = true;
+                continue;
+            }
+            std::vector<double>& pk = sub_inv[p];
+            pk.resize((size_t)m * (m + 1) / 2);
+            size_t o = 0;
+            for (int i = 0; i < m; ++i)
+                for (int j = 0; j <= i; ++j) pk[o++] = full[(size_t)i * m + j];
+        }
+    }
+    if (too_big) {
+        err = "a subdomain has more than 16384 dofs";
+        return CGS_ERR_INVALID_ARG;
+    }
+    if (not_spd) {
+        err = "a local matrix A_p is not SPD";
+        return CGS_ERR_NOT_SPD;
+    }
+    S.sub_ptr.assign(n_sub + 1, 0);
+    S.inv_ptr.assign(n_sub + 1, 0);
+    S.max_m = 0;
+    for (int64_t p = 0; p < n_sub; ++p) {
+        const int64_t m = (int64_t)sub_sets[p].size();
+        S.sub_ptr[p + 1] = S.sub_ptr[p] + m;
+        const int64_t sz = m * (m + 1) / 2;
+        S.inv_ptr[p + 1] = S.inv_ptr[p] + (sz + kPackAlign - 1) / kPackAlign * kPackAlign;
+        S.max_m = std::max(S.max_m, m);
+    }
+    S.sum_m = S.sub_ptr[n_sub];
+    if (S.sum_m >= INT32_MAX) {
+        err = "too many subdomain dofs for 32-bit offsets";
+        return CGS_ERR_INVALID_ARG;
+    }
+    S.sub_idx.resize(S.sum_m);
+    S.inv.assign(S.inv_ptr[n_sub], 0.0);
+    S.wov.assign(nv, 0.0);
+    std::vector<int32_t> mult(nv, 0);
+    for (int64_t p = 0; p < n_sub; ++p) {
+        std::copy(sub_sets[p].begin(), sub_sets[p].end(), S.sub_idx.begin() + S.sub_ptr[p]);
+        std::copy(sub_inv[p].begin(), sub_inv[p].end(), S.inv.begin() + S.inv_ptr[p]);
+        for (int32_t v : sub_sets[p]) mult[v]++;
+    }
+    for (int64_t v = 0; v < nv; ++v) S.wov[v] = mult[v] ? 1.0 / mult[v] : 0.0;
+    sub_sets.clear();
+    sub_inv.clear();
+
+    // ---- box grid and centroid cells ----------------------------------------
+    double lo[3], hi[3];
+    for (int d = 0; d < 3; ++d) {
+        lo[d] = 1e300;
+        hi[d] = -1e300;
+    }
+    for (int64_t v = 0; v < nv; ++v)
+        for (int d = 0; d < 3; ++d) {
+            lo[d] = std::min(lo[d], xyz[v * 3 + d]);
+            hi[d] = std::max(hi[d], xyz[v * 3 + d]);
+        }
+    for (int d = 0; d < 3; ++d) {
+        const double ext = hi[d] - lo[d];
+        lo[d] -= prm.box_margin * ext;
+        hi[d] += prm.box_margin * ext;
+        S.b[d] = prm.box[d];
+        S.lo[d] = lo[d];
+        S.H[d] = (hi[d] - lo[d]) / S.b[d];
+        if (!(S.H[d] > 0.0)) S.H[d] = 1.0;
+    }
+    const int bx = S.b[0], by = S.b[1], bz = S.b[2];
+    const int64_t ncell = (int64_t)bx * by * bz;
+    const int64_t nbv = (int64_t)(bx + 1) * (by + 1) * (bz + 1);
+    std::vector<int32_t> ecell(ne);
+    for (int64_t e = 0; e < ne; ++e) {
+        int c[3];
+        for (int d = 0; d < 3; ++d) {
+            double s = xyz[(size_t)conn[e * 8] * 3 + d];
+            for (int k = 1; k < 8; ++k) s += xyz[(size_t)conn[e * 8 + k] * 3 + d];
+            const double cen = s / 8.0;
+            const double f = std::floor((cen - S.lo[d]) / S.H[d]);
+            c[d] = (int)std::min<double>(std::max<double>(f, 0.0), S.b[d] - 1);
+        }
+        ecell[e] = c[0] + bx * (c[1] + by * c[2]);
+    }
+    // trilinear weights of the 8 cell corners at the 8 element vertices
+    auto weights = [&](int64_t e, double W[8][8]) {
+        const int cid = ecell[e];
+        const int ci[3] = {cid % bx, (cid / bx) % by, cid / (bx * by)};
+        for (int k = 0; k < 8; ++k) {
+            const int32_t v = conn[e * 8 + k];
+            double t[3];
+            for (int d = 0; d < 3; ++d) t[d] = (xyz[(size_t)v * 3 + d] - (S.lo[d] + ci[d] * S.H[d])) / S.H[d];
+            for (int m = 0; m < 8; ++m) {
+                double w = 1.0;
+                for (int d = 0; d < 3; ++d) w *= ((m >> d) & 1) ? t[d] : (1.0 - t[d]);
+                W[k][m] = S.dir[v] ? 0.0 : w;
+            }
+        }
+    };
+    auto corner_id = [&](int cid, int m) -> int64_t {
+        const int i = cid % bx + (m & 1), j = (cid / bx) % by + ((m >> 1) & 1),
+                  k = cid / (bx * by) + ((m >> 2) & 1);
+        return i + (int64_t)(bx + 1) * (j + (int64_t)(by + 1) * k);
+    };
+    std::vector<double> colmax(nbv, 0.0);
+    std::vector<uint8_t> occupied(nbv, 0);
+    for (int64_t e = 0; e < ne; ++e) {
+        double W[8][8];
+        weights(e, W);
+        for (int m = 0; m < 8; ++m) {
+            const int64_t g = corner_id(ecell[e], m);
+            occupied[g] = 1;
+            for (int k = 0; k < 8; ++k) colmax[g] = std::max(colmax[g], std::fabs(W[k][m]));
+        }
+    }
+    std::vector<int32_t> col(nbv, -1);
+    S.box_active.clear();
+    for (int64_t g = 0; g < nbv; ++g)
+        if (occupied[g] && colmax[g] > 1e-12) {
+            col[g] = (int32_t)S.box_active.size();
+            S.box_active.push_back(g);
+        }
+    S.nr = (int64_t)S.box_active.size();
+    S.cell_cols.assign(ncell * 8, -1);
+    for (int64_t c = 0; c < ncell; ++c)
+        for (int m = 0; m < 8; ++m) S.cell_cols[c * 8 + m] = col[corner_id((int)c, m)];
+
+    // ---- element order on the device: by cell, then subdomain, then id -----
+    S.elem_order.resize(ne);
+    std::iota(S.elem_order.begin(), S.elem_order.end(), 0);
+    std::stable_sort(S.elem_order.begin(), S.elem_order.end(), [&](int32_t a, int32_t b) {
+        if (ecell[a] != ecell[b]) return ecell[a] < ecell[b];
+        const int32_t pa = elem_part ? elem_part[a] : 0, pb = elem_part ? elem_part[b] : 0;
+        return pa < pb;
+    });
+
+    // ---- A_r = sum over cells of sum_e J_e^T A^e J_e  (Eq. Aij) --------------
+    if (S.nr > 0) {
+        std::vector<int64_t> cell_ptr(ncell + 1, 0);
+        for (int64_t i = 0; i < ne; ++i) cell_ptr[ecell[S.elem_order[i]] + 1]++;
+        for (int64_t c = 0; c < ncell; ++c) cell_ptr[c + 1] += cell_ptr[c];
+        std::vector<double> Kc((size_t)ncell * 64, 0.0);
+#pragma omp parallel for schedule(dynamic, 4)
+        for (int64_t c = 0; c < ncell; ++c) {
+            double* K = &Kc[(size_t)c * 64];
+            for (int64_t i = cell_ptr[c]; i < cell_ptr[c + 1]; ++i) {
+                const int64_t e = S.elem_order[i];
+                double W[8][8];
+                weights(e, W);
+                for (int m = 0; m < 8; ++m)
+                    if (S.cell_cols[c * 8 + m] < 0)
+                        for (int k = 0; k < 8; ++k) W[k][m] = 0.0;
+                const double* A = &Ae[(size_t)e * 64];
+                double AW[8][8];  // A^e J_e
+                for (int k = 0; k < 8; ++k)
+                    for (int m = 0; m < 8; ++m) {
+                        double s = 0.0;
+                        for (int l = 0; l < 8; ++l) s += A[k * 8 + l] * W[l][m];
+                        AW[k][m] = s;
+                    }
+                for (int m = 0; m < 8; ++m)
+                    for (int n = 0; n < 8; ++n) {
+                        double s = 0.0;
+                        for (int k = 0; k < 8; ++k) s += W[k][m] * AW[k][n];
+                        K[m * 8 + n] += s;
+                    }
+            }
+        }
+        const int64_t nr = S.nr;
+        std::vector<double> Ar((size_t)nr * nr, 0.0);
+        for (int64_t c = 0; c < ncell; ++c)
+            for (int m = 0; m < 8; ++m) {
+                const int32_t a = S.cell_cols[c * 8 + m];
+                if (a < 0) continue;
+                for (int n = 0; n < 8; ++n) {
+                    const int32_t b = S.cell_cols[c * 8 + n];
+                    if (b >= 0) Ar[(size_t)a * nr + b] += Kc[(size_t)c * 64 + m * 8 + n];
+                }
+            }
+        S.ar_inv.assign((size_t)nr * nr, 0.0);
+        if (!spd_inverse(Ar.data(), (int)nr, S.ar_inv.data(), nthreads)) {
+            err = "reduced matrix A_r is not SPD";
+            return CGS_ERR_NOT_SPD;
+        }
+    }
+
+    // ---- device-order element data ------------------------------------------
+    S.conn.resize((size_t)ne * 8);
+    S.cell.resize(ne);
+    S.a36.resize((size_t)kUpper * ne);
+    S.a28.resize((size_t)kOff * ne);
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < ne; ++i) {
+        const int64_t e = S.elem_order[i];
+        for (int k = 0; k < 8; ++k) {
+            const int32_t v = conn[e * 8 + k];
+            S.conn[(size_t)i * 8 + k] = S.dir[v] ? ~v : v;
+        }
+        S.cell[i] = ecell[e];
+        const double* A = &Ae[(size_t)e * 64];
+        for (int r = 0; r < 8; ++r)
+            for (int c = r; c < 8; ++c) {
+                S.a36[(size_t)upper_slot(r, c) * ne + i] = A[r * 8 + c];
+                if (c > r) S.a28[(size_t)off_slot(r, c) * ne + i] = (float)A[r * 8 + c];
+            }
+    }
+    S.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    return CGS_OK;
+}
+
+}  // namespace cgs

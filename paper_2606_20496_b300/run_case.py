@@ -1,0 +1,77 @@
+"""Run a few complete coarse solves of one workload through the C ABI.
+
+    python -m paper_2606_20496_b300.run_case --workload cylinder --prec fp32 --solves 2
+
+Used as the target of profiler runs (ncu) and for quick timing; prints one
+JSON line with the setup time, iteration counts, relative residuals and the
+mean event time per solve.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import time
+
+import numpy as np
+
+
+def load_workload(name: str):
+    from . import meshes
+    if name == "cube8":
+        return meshes.workload_cube8()
+    if name == "cube32":
+        return meshes.workload_cube32()
+    if name == "cylinder":
+        return meshes.workload_cylinder()
+    if name.startswith("cylinder/"):
+        return meshes.workload_cylinder(scale=int(name.split("/")[1]))
+    raise ValueError(name)
+
+
+def main():
+    import torch
+
+    from . import build, cgs
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--workload", default="cube32")
+    ap.add_argument("--prec", default="fp32", choices=list(cgs.PREC))
+    ap.add_argument("--form", default="hybrid", choices=list(cgs.FORM))
+    ap.add_argument("--solves", type=int, default=2)
+    ap.add_argument("--rtol", type=float, default=1e-8)
+    ap.add_argument("--profile", action="store_true", help="per-kernel CUDA-event times")
+    args = ap.parse_args()
+    build.build()
+    m, b = load_workload(args.workload)
+    ctx = cgs.cgs_create(0)
+    t0 = time.perf_counter()
+    h = cgs.Mesh(ctx, m.xyz, m.conn, part=m.part, boxes=m.boxes, prec=args.prec, form=args.form)
+    setup_s = time.perf_counter() - t0
+    bd = torch.as_tensor(b, dtype=torch.float64, device="cuda")
+    x = torch.empty_like(bd)
+    if args.profile:
+        cgs.cgs_profile_enable(h.handle, True)
+    its, rels, ms = [], [], []
+    for _ in range(args.solves):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        st, it, rel = cgs.cgs_solve(h.handle, bd, x, rtol=args.rtol)
+        e1.record()
+        torch.cuda.synchronize()
+        its.append(int(it[0]))
+        rels.append(float(rel[0]))
+        ms.append(e0.elapsed_time(e1))
+        if st != cgs.OK:
+            raise SystemExit(f"solve failed: {cgs.status_string(st)}")
+    out = {"workload": args.workload, "prec": args.prec, "form": args.form, "nv": h.info["nv"],
+           "ne": h.info["ne"], "n_sub": h.info["n_sub"], "n_r": h.info["n_r"],
+           "footprint_mb": h.info["footprint_bytes"] / 2 ** 20, "setup_s": setup_s, "iters": its,
+           "relres": rels, "ms_per_solve": float(np.mean(ms[1:] if len(ms) > 1 else ms))}
+    if args.profile:
+        out["profile"] = cgs.cgs_profile_read(h.handle)
+    print(json.dumps(out))
+    h.free()
+    cgs.cgs_destroy(ctx)
+
+
+if __name__ == "__main__":
+    main()
