@@ -157,6 +157,32 @@ cgs_status cgs_interp(cgs_mesh* mesh, const double* ur, double* z, void* stream)
 /* cgs_apply_preconditioner: z = M r in the mesh's form and precision.       */
 cgs_status cgs_apply_preconditioner(cgs_mesh* mesh, const double* r, double* z, void* stream);
 
+/* ---- preconditioner apply without allocation -------------------------------
+ * cgs_apply_preconditioner_noalloc: the same z = M r as
+ * cgs_apply_preconditioner, for callers that must not allocate device memory
+ * at call time: code that runs while a stream is being captured into a CUDA
+ * graph, serving loops that forbid allocations after warm-up, and hosts whose
+ * device memory is owned by another runtime's pool.  The call performs no
+ * cudaMalloc or cudaFree and uses no allocating library routine.  Its working
+ * vectors (z and s in the bulk precision, r_r and u_r) live in one static
+ * device array of CGS_NOALLOC_SCRATCH_BYTES that every GPU loading this
+ * library keeps until the process exits.
+ *   limits  mesh nv <= CGS_NOALLOC_MAX_NV and n_r <= CGS_NOALLOC_MAX_NR, else
+ *           CGS_ERR_INVALID_ARG with a message naming the limit.
+ *   set-up  the first call on a device looks up the array's device address
+ *           (cudaGetSymbolAddress) with that device current; make that first
+ *           call before any stream capture.
+ *   sharing every call on a device uses the same array, which keeps the
+ *           previous call's contents (the call clears what must start at 0).
+ *           Calls that overlap on the GPU (other streams, other threads, or
+ *           another mesh) race on it: serialise them.
+ * r, z device vectors of length nv; stream-ordered.  The paper has no
+ * counterpart; this is a deployment variant of Eqs. asm / asm1-asm2.       */
+#define CGS_NOALLOC_MAX_NV 131072
+#define CGS_NOALLOC_MAX_NR 8192
+#define CGS_NOALLOC_SCRATCH_BYTES ((size_t)16 * CGS_NOALLOC_MAX_NV + (size_t)16 * CGS_NOALLOC_MAX_NR)
+cgs_status cgs_apply_preconditioner_noalloc(cgs_mesh* mesh, const double* r, double* z, void* stream);
+
 /* ---- solve ----------------------------------------------------------------
  * cgs_solve: flexible PCG (Polak-Ribiere beta, x0 = 0) on A x = b for nrhs
  * right-hand sides stored back to back (b[k*nv ...]); stops when the

@@ -15,6 +15,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libcgs.so")
 
+NOALLOC_MAX_NV, NOALLOC_MAX_NR = 131072, 8192
 OK, ERR_INVALID_ARG, ERR_INVALID_MESH, ERR_NOT_SPD, ERR_NO_CONVERGENCE, ERR_BREAKDOWN, ERR_OOM, \
     ERR_ADMISSION, ERR_TIMEOUT, ERR_CUDA = range(10)
 PREC = {"fp64": 0, "fp32": 1, "fp16": 2}
@@ -24,7 +25,8 @@ FORM = {"hybrid": 0, "additive": 1}
 EXPORTS = (
     "cgs_create", "cgs_destroy", "cgs_ctx_bytes_in_use", "cgs_mesh_setup", "cgs_mesh_free", "cgs_mesh_info",
     "cgs_mesh_set_form", "cgs_mesh_export", "cgs_apply_A", "cgs_apply_local", "cgs_restrict",
-    "cgs_coarse_solve", "cgs_interp", "cgs_apply_preconditioner", "cgs_solve", "cgs_solve_host",
+    "cgs_coarse_solve", "cgs_interp", "cgs_apply_preconditioner", "cgs_apply_preconditioner_noalloc",
+    "cgs_solve", "cgs_solve_host",
     "cgs_profile_enable", "cgs_profile_read", "cgs_status_string", "cgs_last_error",
 )
 KERNEL_CLASSES = ("apply_A64", "apply_A32", "local", "restrict", "coarse", "interp", "pcg_xr", "pcg_dots",
@@ -76,6 +78,7 @@ def load(path: str = LIB_PATH):
         "cgs_coarse_solve": ([P, P, P, P], I32),
         "cgs_interp": ([P, P, P, P], I32),
         "cgs_apply_preconditioner": ([P, P, P, P], I32),
+        "cgs_apply_preconditioner_noalloc": ([P, P, P, P], I32),
         "cgs_solve": ([P, P, P, I32, D, I32, P, P, P], I32),
         "cgs_solve_host": ([P, P, P, I32, D, I32, P, P, P], I32),
         "cgs_profile_enable": ([P, I32], I32),
@@ -208,6 +211,12 @@ def cgs_interp(mesh, ur, z, stream=None):
 
 def cgs_apply_preconditioner(mesh, r, z, stream=None):
     _check(load().cgs_apply_preconditioner(mesh, _ptr(r), _ptr(z), _stream(stream)), "cgs_apply_preconditioner")
+
+
+def cgs_apply_preconditioner_noalloc(mesh, r, z, stream=None):
+    """z = M r without allocating device memory (see include/cgs.h)."""
+    _check(load().cgs_apply_preconditioner_noalloc(mesh, _ptr(r), _ptr(z), _stream(stream)),
+           "cgs_apply_preconditioner_noalloc")
 
 
 def cgs_solve(mesh, b, x, nrhs=1, rtol=1e-8, maxit=1000, stream=None, allow=(ERR_NO_CONVERGENCE, ERR_BREAKDOWN)):

@@ -268,6 +268,16 @@ cgs_status solve_one(cgs_mesh* m, const double* b, double* x, double rtol, int m
 
 }  // namespace
 
+namespace cgs {
+// Read-only views of a mesh for entry points defined in other files.
+const DevMesh& mesh_dev(const cgs_mesh* m) { return m->d; }
+cgs_precision mesh_prec(const cgs_mesh* m) { return m->prm.prec; }
+cgs_form mesh_form(const cgs_mesh* m) { return m->form; }
+const uint8_t* mesh_dir(const cgs_mesh* m) { return m->dir; }
+int mesh_device(const cgs_mesh* m) { return m->ctx->device; }
+void set_last_error(const std::string& msg) { g_err = msg; }
+}  // namespace cgs
+
 extern "C" {
 
 const char* cgs_status_string(cgs_status s) {

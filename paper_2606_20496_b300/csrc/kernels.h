@@ -42,4 +42,12 @@ void launch_copy_d(int64_t n, const double* a, double* b, const uint8_t* dir, cu
 void launch_fill_d(int64_t n, double* a, double v, cudaStream_t st);
 void launch_fill_f(int64_t n, float* a, float v, cudaStream_t st);
 
+// Mesh accessors (api.cu).
+const DevMesh& mesh_dev(const cgs_mesh* m);
+cgs_precision mesh_prec(const cgs_mesh* m);
+cgs_form mesh_form(const cgs_mesh* m);
+const uint8_t* mesh_dir(const cgs_mesh* m);
+int mesh_device(const cgs_mesh* m);
+void set_last_error(const std::string& msg);
+
 }  // namespace cgs

@@ -138,6 +138,20 @@ def test_preconditioner(mesh_of, name, form):
     assert rel_inf(host(z), P.apply_M(r, form)) <= 1e-11
 
 
+@pytest.mark.parametrize("prec", ["fp32", "fp16"])
+@pytest.mark.parametrize("form", ["hybrid", "additive"])
+def test_preconditioner_reduced_precision(mesh_of, prec, form):
+    """M r in the FP32-bulk and FP16-local forms against the FP64 oracle:
+    relative max-norm difference <= 1e-5 (float rounding of the local
+    inverses, the inner apply and the interpolation weights)."""
+    m, b, P, h = mesh_of("cube32", prec=prec, form=form)
+    r = np.random.default_rng(4).standard_normal(m.nv)
+    z = torch.empty(m.nv, dtype=torch.float64, device="cuda")
+    cgs.cgs_apply_preconditioner(h.handle, dev(r), z)
+    tol = 1e-5 if prec == "fp32" else 2e-3
+    assert rel_inf(host(z), P.apply_M(r, form)) <= tol
+
+
 @pytest.mark.parametrize("name", NAMES)
 @pytest.mark.parametrize("form", ["hybrid", "additive"])
 def test_solve_fp64(mesh_of, name, form):
