@@ -57,7 +57,12 @@ struct cgs_mesh {
     std::vector<int32_t> sub_idx_h;
     // device scratch
     uint8_t* dir = nullptr;
-    double *r = nullptr, *p = nullptr, *q = nullptr, *y = nullptr;
+    double *r = nullptr, *p = nullptr, *q = nullptr, *y = nullptr, *x = nullptr;
+    float2 *p2 = nullptr, *q2 = nullptr;   // float-pair p and A p of the mixed forms
+    float* ur32 = nullptr;                 // float copy of u_r for the float interpolation
+    // device-side PCG loop: a graph whose while node repeats one iteration
+    cudaGraphExec_t gexec = nullptr;
+    bool graph_failed = false;
     void* z = nullptr;   // bulk precision (double for FP64, float otherwise)
     void* s = nullptr;
     double *rr = nullptr, *ur = nullptr, *partials = nullptr, *out2 = nullptr;
@@ -97,6 +102,8 @@ struct cgs_mesh {
         return e;
     }
     void release() {
+        if (gexec) cudaGraphExecDestroy(gexec);
+        gexec = nullptr;
         for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
         ev_pool.clear();
         for (void* p : allocs) cudaFree(p);
@@ -176,29 +183,31 @@ void precond_prep(cgs_mesh* m, const double* r, cudaStream_t st) {
     if (m->d.nr) K(CGS_K_OTHER, launch_fill_d(m->d.nr, m->rr, 0.0, st));
 }
 
+// z += J~ A_r^{-1} J~^T s (s the bulk copy of the residual or of r - A l).
+void box_correction(cgs_mesh* m, const SolveScalars* S, cudaStream_t st) {
+    const DevMesh& d = m->d;
+    const bool f64 = m->fp64();
+    K(CGS_K_RESTRICT, launch_restrict(d, f64, m->s, f64, m->rr, S, st));
+    K(CGS_K_COARSE, launch_coarse(d, m->rr, m->ur, f64 ? nullptr : m->ur32, S, st));
+    K(CGS_K_INTERP, launch_interp_add(d, f64, m->ur, f64 ? nullptr : m->ur32, m->z, S, st));
+}
+
 // z (bulk) = M r, assuming precond_prep (or the PCG update kernel) ran.
 void precond_body(cgs_mesh* m, const double* r, const SolveScalars* S, cudaStream_t st) {
     const DevMesh& d = m->d;
     const bool f64 = m->fp64();
     if (m->form == CGS_HYBRID) {
-        K(CGS_K_LOCAL, launch_local(d, m->prm.prec, r, m->z, true, S, st));
+        K(CGS_K_LOCAL, launch_local(d, m->prm.prec, m->s, m->z, true, S, st));
         if (f64)
             K(CGS_K_APPLY_A64, launch_apply64(d, static_cast<const double*>(m->z), static_cast<double*>(m->s),
                                               -1.0, nullptr, const_cast<SolveScalars*>(S), false, st));
         else
-            K(CGS_K_APPLY_A32, launch_apply28f(d, static_cast<const float*>(m->z), static_cast<float*>(m->s), -1.0f, S, st));
-        if (d.nr) {
-            K(CGS_K_RESTRICT, launch_restrict(d, f64, m->s, f64, m->rr, S, st));
-            K(CGS_K_COARSE, launch_coarse(d, m->rr, m->ur, S, st));
-            K(CGS_K_INTERP, launch_interp_add(d, f64, m->ur, m->z, S, st));
-        }
+            K(CGS_K_APPLY_A32, launch_apply28f_tiled(d, static_cast<const float*>(m->z), static_cast<float*>(m->s),
+                                                     -1.0f, const_cast<SolveScalars*>(S), st));
+        if (d.nr) box_correction(m, S, st);
     } else {
-        K(CGS_K_LOCAL, launch_local(d, m->prm.prec, r, m->z, false, S, st));
-        if (d.nr) {
-            K(CGS_K_RESTRICT, launch_restrict(d, f64, r, true, m->rr, S, st));
-            K(CGS_K_COARSE, launch_coarse(d, m->rr, m->ur, S, st));
-            K(CGS_K_INTERP, launch_interp_add(d, f64, m->ur, m->z, S, st));
-        }
+        K(CGS_K_LOCAL, launch_local(d, m->prm.prec, m->s, m->z, false, S, st));
+        if (d.nr) box_correction(m, S, st);
     }
 }
 
@@ -209,23 +218,89 @@ void z_to_double(cgs_mesh* m, double* out, cudaStream_t st) {
         K(CGS_K_OTHER, launch_convert_f2d(m->d.nv, static_cast<const float*>(m->z), out, m->dir, st));
 }
 
+// One flexible-PCG iteration on mesh-owned buffers (x is the mesh's own
+// iterate, so the same launches can be captured once into a graph).
 template <typename Tz>
-void pcg_iteration(cgs_mesh* m, double* x, cudaStream_t st) {
+void pcg_iteration(cgs_mesh* m, cudaStream_t st, cudaGraphConditionalHandle cond, bool use_cond) {
     const DevMesh& d = m->d;
-    K(CGS_K_APPLY_A64, launch_apply64(d, m->p, m->q, 1.0, m->partials, m->S, true, st));
-    K(CGS_K_PCG_XR, launch_pcg_update_xr<Tz>(d, x, m->r, m->p, m->q, static_cast<Tz*>(m->z),
-                                             m->form == CGS_HYBRID ? static_cast<Tz*>(m->s) : nullptr, m->rr,
-                                             m->partials, m->S, st));
-    precond_body(m, m->r, m->S, st);
-    K(CGS_K_PCG_DOTS, launch_pcg_dots<Tz>(d, static_cast<const Tz*>(m->z), m->r, m->q, m->partials, m->S, st));
-    K(CGS_K_PCG_P, launch_pcg_update_p<Tz>(d, static_cast<const Tz*>(m->z), m->p, m->q, m->S, st));
+    Tz* z = static_cast<Tz*>(m->z);
+    Tz* s = static_cast<Tz*>(m->s);
+    if (m->fp64()) {
+        K(CGS_K_APPLY_A64, launch_apply64(d, m->p, m->q, 1.0, m->partials, m->S, true, st));
+        K(CGS_K_PCG_XR, (launch_pcg_update_xr<Tz, double>(d, m->x, m->r, m->p, m->q, z, s, m->rr, m->partials,
+                                                           m->S, st)));
+        precond_body(m, m->r, m->S, st);
+        K(CGS_K_PCG_DOTS, (launch_pcg_dots<Tz, double>(d, z, m->r, m->q, m->partials, m->S, st)));
+        K(CGS_K_PCG_P, (launch_pcg_update_p<Tz, double>(d, z, m->p, nullptr, m->q, m->S, cond, use_cond, st)));
+    } else {
+        K(CGS_K_APPLY_A64, launch_apply_pair_tiled(d, m->p2, m->q2, m->partials, m->S, st));
+        K(CGS_K_PCG_XR, (launch_pcg_update_xr<Tz, float2>(d, m->x, m->r, m->p, m->q2, z, s, m->rr, m->partials,
+                                                           m->S, st)));
+        precond_body(m, m->r, m->S, st);
+        K(CGS_K_PCG_DOTS, (launch_pcg_dots<Tz, float2>(d, z, m->r, m->q2, m->partials, m->S, st)));
+        K(CGS_K_PCG_P, (launch_pcg_update_p<Tz, float2>(d, z, m->p, m->p2, m->q2, m->S, cond, use_cond, st)));
+    }
+}
+
+// Build the graph: one while node whose body is one PCG iteration; the body's
+// last kernel sets the loop condition from the device-side stopping test.
+template <typename Tz>
+cgs_status build_loop_graph(cgs_mesh* m) {
+    cudaStream_t cs = nullptr;
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ex = nullptr;
+    auto bail = [&](cudaError_t e, const char* where) {
+        if (cs) {
+            cudaGraph_t dummy = nullptr;
+            cudaStreamEndCapture(cs, &dummy);
+            cudaStreamDestroy(cs);
+        }
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return cuda_fail(e, where);
+    };
+    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return bail(e, "graph stream");
+    if ((e = cudaGraphCreate(&g, 0)) != cudaSuccess) return bail(e, "cudaGraphCreate");
+    cudaGraphConditionalHandle h;
+    if ((e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault)) != cudaSuccess)
+        return bail(e, "cudaGraphConditionalHandleCreate");
+    cudaGraphNodeParams np = {};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    if ((e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np)) != cudaSuccess) return bail(e, "cudaGraphAddNode");
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    if ((e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal)) !=
+        cudaSuccess)
+        return bail(e, "cudaStreamBeginCaptureToGraph");
+    const bool prof = m->prof;
+    const int64_t launches = m->launches;
+    m->prof = false;
+    pcg_iteration<Tz>(m, cs, h, true);
+    m->prof = prof;
+    m->launches = launches;
+    cudaGraph_t captured = nullptr;
+    e = cudaStreamEndCapture(cs, &captured);
+    cudaStreamDestroy(cs);
+    cs = nullptr;
+    if (e != cudaSuccess) return bail(e, "cudaStreamEndCapture");
+    if ((e = cudaGraphInstantiate(&ex, g, 0)) != cudaSuccess) return bail(e, "cudaGraphInstantiate");
+    cudaGraphDestroy(g);
+    m->gexec = ex;
+    return CGS_OK;
 }
 
 template <typename Tz>
 cgs_status solve_one(cgs_mesh* m, const double* b, double* x, double rtol, int maxit, int* iters, double* relres,
                      cudaStream_t st) {
     const DevMesh& d = m->d;
-    K(CGS_K_OTHER, launch_pcg_init(d, b, m->dir, x, m->r, m->q, rtol, maxit, m->partials, m->S, st));
+    if (m->fp64())
+        K(CGS_K_OTHER, launch_pcg_init<double>(d, b, m->dir, m->x, m->r, m->q, rtol, maxit, m->partials, m->S, st));
+    else
+        K(CGS_K_OTHER, launch_pcg_init<float2>(d, b, m->dir, m->x, m->r, m->q2, rtol, maxit, m->partials, m->S, st));
     // z = M r, p = z, rho = r.z  (skipped when b = 0)
     if (m->fp64()) {
         K(CGS_K_OTHER, launch_fill_d(d.nv, static_cast<double*>(m->z), 0.0, st));
@@ -236,30 +311,42 @@ cgs_status solve_one(cgs_mesh* m, const double* b, double* x, double rtol, int m
     }
     if (d.nr) K(CGS_K_OTHER, launch_fill_d(d.nr, m->rr, 0.0, st));
     precond_body(m, m->r, m->S, st);
-    K(CGS_K_OTHER, launch_pcg_first_dir<Tz>(d, static_cast<const Tz*>(m->z), m->r, m->p, m->partials, m->S, st));
-    int enqueued = 0;
-    int chunk = std::max(2, m->last_iters);
-    for (;;) {
-        const int n = std::min(chunk, maxit - enqueued);
-        for (int i = 0; i < n; ++i) pcg_iteration<Tz>(m, x, st);
-        enqueued += n;
-        CGS_CUDA(cudaMemcpyAsync(m->S_host, m->S, sizeof(SolveScalars), cudaMemcpyDeviceToHost, st));
-        CGS_CUDA(cudaStreamSynchronize(st));
-        if (m->S_host->done || enqueued >= maxit) break;
-        chunk = 4;
+    K(CGS_K_OTHER, launch_pcg_first_dir<Tz>(d, static_cast<const Tz*>(m->z), m->r, m->p, m->p2, m->partials, m->S,
+                                            st));
+    const bool use_graph = !m->prof && !m->graph_failed;
+    if (use_graph && !m->gexec) {
+        if (build_loop_graph<Tz>(m) != CGS_OK) m->graph_failed = true;
     }
-    const SolveScalars h = *m->S_host;
-    if (!h.done && h.status == CGS_OK) m->S_host->status = CGS_ERR_NO_CONVERGENCE;
-    const int status = h.done ? h.status : CGS_ERR_NO_CONVERGENCE;
-    *iters = h.iters;
-    if (h.iters > 0) m->last_iters = h.iters;
-    // true residual ||b - A x|| / ||b|| over the free entries
+    if (use_graph && m->gexec) {
+        // the whole iteration loop runs on the device
+        CGS_CUDA(cudaGraphLaunch(m->gexec, st));
+        m->launches += 1;
+        CGS_CUDA(cudaMemcpyAsync(m->S_host, m->S, sizeof(SolveScalars), cudaMemcpyDeviceToHost, st));
+    } else {
+        int enqueued = 0;
+        int chunk = std::max(2, m->last_iters);
+        for (;;) {
+            const int n = std::min(chunk, maxit - enqueued);
+            for (int i = 0; i < n; ++i) pcg_iteration<Tz>(m, st, cudaGraphConditionalHandle(), false);
+            enqueued += n;
+            CGS_CUDA(cudaMemcpyAsync(m->S_host, m->S, sizeof(SolveScalars), cudaMemcpyDeviceToHost, st));
+            CGS_CUDA(cudaStreamSynchronize(st));
+            if (m->S_host->done || enqueued >= maxit) break;
+            chunk = 4;
+        }
+    }
+    // x out, then the true residual ||b - A x|| / ||b|| over the free entries
+    K(CGS_K_OTHER, launch_copy_d(d.nv, m->x, x, nullptr, st));
     K(CGS_K_OTHER, launch_fill_d(d.nv, m->y, 0.0, st));
-    K(CGS_K_APPLY_A64, launch_apply64(d, x, m->y, 1.0, nullptr, nullptr, false, st));
+    K(CGS_K_APPLY_A64, launch_apply64(d, m->x, m->y, 1.0, nullptr, nullptr, false, st));
     K(CGS_K_OTHER, launch_resid_norm(d, b, m->y, m->dir, m->partials, &m->S->ticket[1], m->out2, st));
     CGS_CUDA(cudaMemcpyAsync(m->out2_host, m->out2, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
     cgs_status fs = finish(st, true);
     if (fs != CGS_OK) return fs;
+    const SolveScalars h = *m->S_host;
+    const int status = h.done ? h.status : CGS_ERR_NO_CONVERGENCE;
+    *iters = h.iters;
+    if (h.iters > 0) m->last_iters = h.iters;
     *relres = m->out2_host[1] > 0 ? std::sqrt(m->out2_host[0] / m->out2_host[1]) : 0.0;
     if (status == CGS_ERR_NO_CONVERGENCE) g_err = "maxit reached before the tolerance";
     if (status == CGS_ERR_BREAKDOWN) g_err = "breakdown in the PCG iteration";
@@ -387,8 +474,18 @@ cgs_status cgs_mesh_setup(cgs_ctx* ctx, const double* xyz, int64_t nv, const int
 
     UP(d.conn, hs.conn);
     UP(d.a36, hs.a36);
-    if (!f64) UP(d.a28, hs.a28);
+    if (!f64) {
+        UP(d.at_hi, hs.at_hi);
+        UP(d.at_lo, hs.at_lo);
+    }
     UP(d.cell, hs.cell);
+    if (!f64) {
+        d.ntiles = (int64_t)hs.tile_ptr.size() - 1;
+        UP(d.tile_ptr, hs.tile_ptr);
+        UP(d.tile_vptr, hs.tile_vptr);
+        UP(d.tile_verts, hs.tile_verts);
+        UP(d.eloc, hs.eloc);
+    }
     UP(d.cell_cols, hs.cell_cols);
     {
         std::vector<int32_t> sp(hs.sub_ptr.begin(), hs.sub_ptr.end());
@@ -447,8 +544,14 @@ cgs_status cgs_mesh_setup(cgs_ctx* ctx, const double* xyz, int64_t nv, const int
     }
     AL(m->r, nv);
     AL(m->p, nv);
-    AL(m->q, nv);
     AL(m->y, nv);
+    AL(m->x, nv);
+    if (f64) {
+        AL(m->q, nv);
+    } else {
+        AL(m->q2, nv);
+        AL(m->p2, nv);
+    }
     if (f64) {
         double* z = nullptr;
         double* s = nullptr;
@@ -465,6 +568,7 @@ cgs_status cgs_mesh_setup(cgs_ctx* ctx, const double* xyz, int64_t nv, const int
         m->s = s;
     }
     AL(m->rr, std::max<int64_t>(hs.nr, 1));
+    if (!f64) AL(m->ur32, std::max<int64_t>(hs.nr, 1));
     AL(m->ur, std::max<int64_t>(hs.nr, 1));
     AL(m->partials, 2 * (size_t)partial_slots(d));
     AL(m->out2, 2);
@@ -587,7 +691,12 @@ cgs_status cgs_apply_local(cgs_mesh* m, const double* r, double* l, int weighted
         K(CGS_K_OTHER, launch_fill_d(m->d.nv, static_cast<double*>(m->z), 0.0, st));
     else
         K(CGS_K_OTHER, launch_fill_f(m->d.nv, static_cast<float*>(m->z), 0.0f, st));
-    K(CGS_K_LOCAL, launch_local(m->d, m->prm.prec, r, m->z, weighted != 0, nullptr, st));
+    const void* rin = r;
+    if (!m->fp64()) {   // the float kernels read the residual in the bulk precision
+        K(CGS_K_OTHER, launch_convert_d2f(m->d.nv, r, static_cast<float*>(m->s), nullptr, st));
+        rin = m->s;
+    }
+    K(CGS_K_LOCAL, launch_local(m->d, m->prm.prec, rin, m->z, weighted != 0, nullptr, st));
     z_to_double(m, l, st);
     return finish(st, false);
 }
@@ -604,7 +713,7 @@ cgs_status cgs_restrict(cgs_mesh* m, const double* s, double* rr, void* stream) 
 cgs_status cgs_coarse_solve(cgs_mesh* m, const double* rr, double* ur, void* stream) {
     if (check_mesh(m) != CGS_OK || ((!rr || !ur) && m->d.nr)) return fail(CGS_ERR_INVALID_ARG, "null argument");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    K(CGS_K_COARSE, launch_coarse(m->d, rr, ur, nullptr, st));
+    K(CGS_K_COARSE, launch_coarse(m->d, rr, ur, nullptr, nullptr, st));
     return finish(st, false);
 }
 
@@ -615,7 +724,9 @@ cgs_status cgs_interp(cgs_mesh* m, const double* ur, double* z, void* stream) {
         K(CGS_K_OTHER, launch_fill_d(m->d.nv, static_cast<double*>(m->z), 0.0, st));
     else
         K(CGS_K_OTHER, launch_fill_f(m->d.nv, static_cast<float*>(m->z), 0.0f, st));
-    if (m->d.nr) K(CGS_K_INTERP, launch_interp_add(m->d, m->fp64(), ur, m->z, nullptr, st));
+    if (m->d.nr) {
+        K(CGS_K_INTERP, launch_interp_add(m->d, m->fp64(), ur, nullptr, m->z, nullptr, st));
+    }
     z_to_double(m, z, st);
     return finish(st, false);
 }

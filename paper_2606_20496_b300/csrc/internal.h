@@ -17,6 +17,11 @@ namespace cgs {
 constexpr int kUpper = 36;   // upper triangle including the diagonal, (i <= j)
 constexpr int kOff = 28;     // strict upper triangle (i < j); diagonal = -row sum
 constexpr int kPackAlign = 8;  // packed inverses start on multiples of 8 entries
+// Element tiles for block-local assembly: consecutive device-order elements
+// with at most kTileElems elements and kTileVerts distinct free vertices.
+constexpr int kTileElems = 256;
+constexpr int kTileVerts = 1024;
+constexpr uint32_t kSharedBit = 0x80000000u;  // tile vertex also touched by another tile
 
 // Everything the host setup produces, in the layout the device uses.
 struct HostSetup {
@@ -26,7 +31,8 @@ struct HostSetup {
     std::vector<int32_t> elem_order;   // device slot -> caller element id
     std::vector<int32_t> conn;         // ne*8, vertex id, or ~v for a Dirichlet vertex
     std::vector<double> a36;           // SoA [kUpper][ne] element matrices, float64
-    std::vector<float> a28;            // SoA [kOff][ne] off-diagonals, float32
+    std::vector<float> a28;            // SoA [kOff][ne] off-diagonals rounded to float32
+    std::vector<float> a28lo;          // SoA [kOff][ne] float32 remainders a - (double)a28
     std::vector<uint8_t> dir;          // nv, 1 = Dirichlet
     std::vector<double> invcnt;        // nv, 1 / (elements at the vertex)
     std::vector<double> wov;           // nv, 1 / (subdomains holding the vertex), 0 if none
@@ -39,6 +45,11 @@ struct HostSetup {
     int b[3] = {1, 1, 1};
     double lo[3] = {0, 0, 0}, H[3] = {1, 1, 1};
     std::vector<int32_t> cell;         // ne (device order), lexicographic cell id
+    std::vector<int32_t> tile_ptr;     // ntiles+1, element ranges (device order)
+    std::vector<int32_t> tile_vptr;    // ntiles+1, ranges in tile_verts
+    std::vector<uint32_t> tile_verts;  // distinct free vertices of each tile, | kSharedBit if shared
+    std::vector<uint16_t> eloc;        // ne*8, tile-local vertex index, 0xFFFF = Dirichlet
+    std::vector<float> at_hi, at_lo;   // [ntiles][kOff][kTileElems] tile-major off-diagonals (float, remainder)
     std::vector<int32_t> cell_cols;    // ncell*8, active column of each cell corner or -1
     std::vector<int64_t> box_active;   // nr, lexicographic box-vertex ids
     std::vector<double> ar_inv;        // nr*nr, A_r^{-1}, full symmetric, float64
@@ -58,10 +69,16 @@ struct DevMesh {
     float lof[3] = {0, 0, 0}, Hf[3] = {1, 1, 1};
     const int32_t* conn = nullptr;     // ne*8 (int4 x2 per element)
     const double* a36 = nullptr;       // [36][ne]
-    const float* a28 = nullptr;        // [28][ne]
     const double2* xyzw = nullptr;     // 2*nv: (x, y), (z, 1/count) per vertex, float64
     const float4* xyzwf = nullptr;     // nv: same, float32
     const int32_t* cell = nullptr;     // ne
+    int64_t ntiles = 0;
+    const int32_t* tile_ptr = nullptr;
+    const int32_t* tile_vptr = nullptr;
+    const uint32_t* tile_verts = nullptr;
+    const uint16_t* eloc = nullptr;
+    const float* at_hi = nullptr;      // [ntiles][28][256] off-diagonals rounded to float, tile-major
+    const float* at_lo = nullptr;      // same layout, float remainders (outer operator only)
     const int32_t* cell_cols = nullptr;// ncell*8
     // subdomains grouped by size class for the warp kernels
     const int32_t* sub_ptr = nullptr;  // n_sub+1 (int32 offsets into sub_idx)
@@ -88,9 +105,11 @@ struct SolveScalars {
     double zr, zq;     // z.r and z.q for the next direction
     int iters;
     int maxit;
+    int loops;         // executions of the device-side loop body
     int done;          // 1 = stop (converged, failed or maxit)
     int status;        // cgs_status of the solve
     unsigned int ticket[4];  // block-completion counters of the fused reductions
+    int timeouts;            // bounded device-side waits that expired
 };
 
 }  // namespace cgs

@@ -9,30 +9,35 @@ unsigned int partial_slots(const DevMesh& m);
 
 void launch_apply64(const DevMesh& m, const double* x, double* y, double alpha, double* partials,
                     SolveScalars* S, bool dot, cudaStream_t st);
-void launch_apply28f(const DevMesh& m, const float* x, float* y, float alpha, const SolveScalars* S,
-                     cudaStream_t st);
-void launch_local(const DevMesh& m, cgs_precision prec, const double* r, void* out, bool weighted,
+void launch_local(const DevMesh& m, cgs_precision prec, const void* r, void* out, bool weighted,
                   const SolveScalars* S, cudaStream_t st);
 void launch_restrict(const DevMesh& m, bool fp64, const void* s, bool s_is_double, double* rr,
                      const SolveScalars* S, cudaStream_t st);
-void launch_interp_add(const DevMesh& m, bool fp64, const double* ur, void* z, const SolveScalars* S,
-                       cudaStream_t st);
-void launch_coarse(const DevMesh& m, const double* rr, double* ur, const SolveScalars* S, cudaStream_t st);
+void launch_interp_add(const DevMesh& m, bool fp64, const double* ur, const float* ur32, void* z,
+                       const SolveScalars* S, cudaStream_t st);
+void launch_coarse(const DevMesh& m, const double* rr, double* ur, float* ur32, const SolveScalars* S,
+                   cudaStream_t st);
+void launch_apply_pair_tiled(const DevMesh& m, const float2* p2, float2* q2, double* partials, SolveScalars* S,
+                             cudaStream_t st);
+void launch_apply28f_tiled(const DevMesh& m, const float* x, float* y, float alpha, SolveScalars* S,
+                           cudaStream_t st);
 
-void launch_pcg_init(const DevMesh& m, const double* b, const uint8_t* dir, double* x, double* r, double* q,
+
+template <typename Tq>
+void launch_pcg_init(const DevMesh& m, const double* b, const uint8_t* dir, double* x, double* r, Tq* q,
                      double rtol, int maxit, double* partials, SolveScalars* S, cudaStream_t st);
 template <typename Tz>
-void launch_pcg_first_dir(const DevMesh& m, const Tz* z, const double* r, double* p, double* partials,
+void launch_pcg_first_dir(const DevMesh& m, const Tz* z, const double* r, double* p, float2* p2, double* partials,
                           SolveScalars* S, cudaStream_t st);
-template <typename Tz>
-void launch_pcg_update_xr(const DevMesh& m, double* x, double* r, const double* p, const double* q, Tz* z, Tz* s,
+template <typename Tz, typename Tq>
+void launch_pcg_update_xr(const DevMesh& m, double* x, double* r, const double* p, const Tq* q, Tz* z, Tz* s,
                           double* rr_vec, double* partials, SolveScalars* S, cudaStream_t st);
-template <typename Tz>
-void launch_pcg_dots(const DevMesh& m, const Tz* z, const double* r, const double* q, double* partials,
-                     SolveScalars* S, cudaStream_t st);
-template <typename Tz>
-void launch_pcg_update_p(const DevMesh& m, const Tz* z, double* p, double* q, const SolveScalars* S,
-                         cudaStream_t st);
+template <typename Tz, typename Tq>
+void launch_pcg_dots(const DevMesh& m, const Tz* z, const double* r, const Tq* q, double* partials, SolveScalars* S,
+                     cudaStream_t st);
+template <typename Tz, typename Tq>
+void launch_pcg_update_p(const DevMesh& m, const Tz* z, double* p, float2* p2, Tq* q, SolveScalars* S,
+                         cudaGraphConditionalHandle cond, bool use_cond, cudaStream_t st);
 void launch_resid_norm(const DevMesh& m, const double* b, const double* y, const uint8_t* dir, double* partials,
                        unsigned int* ticket, double* out2, cudaStream_t st);
 

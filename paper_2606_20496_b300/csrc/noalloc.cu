@@ -84,23 +84,23 @@ extern "C" cgs_status cgs_apply_preconditioner_noalloc(cgs_mesh* mesh, const dou
     }
     if (d.nr) launch_fill_d(d.nr, rr, 0.0, st);
     if (mesh_form(mesh) == CGS_HYBRID) {
-        launch_local(d, mesh_prec(mesh), r, zb, true, nullptr, st);
+        launch_local(d, mesh_prec(mesh), sb, zb, true, nullptr, st);
         if (f64)
             launch_apply64(d, static_cast<const double*>(zb), static_cast<double*>(sb), -1.0, nullptr, nullptr,
                            false, st);
         else
-            launch_apply28f(d, static_cast<const float*>(zb), static_cast<float*>(sb), -1.0f, nullptr, st);
+            launch_apply28f_tiled(d, static_cast<const float*>(zb), static_cast<float*>(sb), -1.0f, nullptr, st);
         if (d.nr) {
             launch_restrict(d, f64, sb, f64, rr, nullptr, st);
-            launch_coarse(d, rr, ur, nullptr, st);
-            launch_interp_add(d, f64, ur, zb, nullptr, st);
+            launch_coarse(d, rr, ur, nullptr, nullptr, st);
+            launch_interp_add(d, f64, ur, nullptr, zb, nullptr, st);
         }
     } else {
-        launch_local(d, mesh_prec(mesh), r, zb, false, nullptr, st);
+        launch_local(d, mesh_prec(mesh), sb, zb, false, nullptr, st);
         if (d.nr) {
-            launch_restrict(d, f64, r, true, rr, nullptr, st);
-            launch_coarse(d, rr, ur, nullptr, st);
-            launch_interp_add(d, f64, ur, zb, nullptr, st);
+            launch_restrict(d, f64, sb, f64, rr, nullptr, st);
+            launch_coarse(d, rr, ur, nullptr, nullptr, st);
+            launch_interp_add(d, f64, ur, nullptr, zb, nullptr, st);
         }
     }
     if (f64)

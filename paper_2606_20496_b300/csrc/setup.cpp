@@ -20,6 +20,9 @@
 // The device keeps explicit inverses instead of sparse Cholesky factors (the
 // paper's CHOLMOD and XX^T): a GEMV with a 27..64-dof inverse is one coalesced
 // stream per subdomain, where a triangular solve would be two dependent sweeps.
+// Each symmetric inverse is stored by cyclic diagonals, entry (i, (i+d) mod m)
+// at d*m + i for d = 0..floor(m/2): m(m+1)/2 entries for odd m (m/2 more for
+// even m), and lane i of a warp reads diagonal d at i and at (i-d) mod m.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -338,11 +341,12 @@ cgs_status host_setup(const double* xyz, int64_t nv, const int32_t* conn, int64_
                 not_spd = true;
                 continue;
             }
+            // cyclic diagonals: entry (i, (i+d) mod m) at d*m + i, d = 0..m/2
             std::vector<double>& pk = sub_inv[p];
-            pk.resize((size_t)m * (m + 1) / 2);
-            size_t o = 0;
-            for (int i = 0; i < m; ++i)
-                for (int j = 0; j <= i; ++j) pk[o++] = full[(size_t)i * m + j];
+            const int nd = m / 2 + 1;
+            pk.resize((size_t)nd * m);
+            for (int d = 0; d < nd; ++d)
+                for (int i = 0; i < m; ++i) pk[(size_t)d * m + i] = full[(size_t)i * m + (i + d) % m];
         }
     }
     if (too_big) {
@@ -359,7 +363,7 @@ cgs_status host_setup(const double* xyz, int64_t nv, const int32_t* conn, int64_
     for (int64_t p = 0; p < n_sub; ++p) {
         const int64_t m = (int64_t)sub_sets[p].size();
         S.sub_ptr[p + 1] = S.sub_ptr[p] + m;
-        const int64_t sz = m * (m + 1) / 2;
+        const int64_t sz = (m / 2 + 1) * m;
         S.inv_ptr[p + 1] = S.inv_ptr[p] + (sz + kPackAlign - 1) / kPackAlign * kPackAlign;
         S.max_m = std::max(S.max_m, m);
     }
@@ -523,6 +527,7 @@ cgs_status host_setup(const double* xyz, int64_t nv, const int32_t* conn, int64_
     S.cell.resize(ne);
     S.a36.resize((size_t)kUpper * ne);
     S.a28.resize((size_t)kOff * ne);
+    S.a28lo.resize((size_t)kOff * ne);
 #pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < ne; ++i) {
         const int64_t e = S.elem_order[i];
@@ -535,8 +540,66 @@ cgs_status host_setup(const double* xyz, int64_t nv, const int32_t* conn, int64_
         for (int r = 0; r < 8; ++r)
             for (int c = r; c < 8; ++c) {
                 S.a36[(size_t)upper_slot(r, c) * ne + i] = A[r * 8 + c];
-                if (c > r) S.a28[(size_t)off_slot(r, c) * ne + i] = (float)A[r * 8 + c];
+                if (c > r) {
+                    const float hi = (float)A[r * 8 + c];
+                    S.a28[(size_t)off_slot(r, c) * ne + i] = hi;
+                    S.a28lo[(size_t)off_slot(r, c) * ne + i] = (float)(A[r * 8 + c] - (double)hi);
+                }
             }
+    }
+    // ---- element tiles for block-local assembly --------------------------
+    {
+        std::vector<int32_t> stamp(nv, -1), loc(nv, 0), in_tile(nv, 0);
+        S.tile_ptr.assign(1, 0);
+        S.tile_vptr.assign(1, 0);
+        S.tile_verts.clear();
+        S.eloc.assign((size_t)ne * 8, 0xFFFF);
+        int32_t tile = 0, tile_begin = 0;
+        std::vector<int32_t> verts;
+        auto close_tile = [&](int32_t end) {
+            for (int32_t v : verts) {
+                const int64_t c = v2e_ptr[v + 1] - v2e_ptr[v];
+                S.tile_verts.push_back((uint32_t)v | (in_tile[v] == c ? 0u : kSharedBit));
+                in_tile[v] = 0;
+            }
+            S.tile_ptr.push_back(end);
+            S.tile_vptr.push_back((int32_t)S.tile_verts.size());
+            verts.clear();
+            ++tile;
+            tile_begin = end;
+        };
+        for (int64_t i = 0; i < ne; ++i) {
+            int fresh = 0;
+            for (int k = 0; k < 8; ++k) {
+                const int32_t v = S.conn[(size_t)i * 8 + k];
+                if (v >= 0 && stamp[v] != tile) ++fresh;
+            }
+            if (i - tile_begin >= kTileElems || (int)verts.size() + fresh > kTileVerts) close_tile((int32_t)i);
+            for (int k = 0; k < 8; ++k) {
+                const int32_t v = S.conn[(size_t)i * 8 + k];
+                if (v < 0) continue;
+                if (stamp[v] != tile) {
+                    stamp[v] = tile;
+                    loc[v] = (int32_t)verts.size();
+                    verts.push_back(v);
+                }
+                in_tile[v]++;
+                S.eloc[(size_t)i * 8 + k] = (uint16_t)loc[v];
+            }
+        }
+        close_tile((int32_t)ne);
+        // tile-major copies of the off-diagonals, zero-padded to kTileElems
+        const int64_t nt = (int64_t)S.tile_ptr.size() - 1;
+        S.at_hi.assign((size_t)nt * kOff * kTileElems, 0.0f);
+        S.at_lo.assign((size_t)nt * kOff * kTileElems, 0.0f);
+#pragma omp parallel for schedule(static)
+        for (int64_t t = 0; t < nt; ++t)
+            for (int32_t i = S.tile_ptr[t]; i < S.tile_ptr[t + 1]; ++i)
+                for (int sl = 0; sl < kOff; ++sl) {
+                    const size_t dst = ((size_t)t * kOff + sl) * kTileElems + (i - S.tile_ptr[t]);
+                    S.at_hi[dst] = S.a28[(size_t)sl * ne + i];
+                    S.at_lo[dst] = S.a28lo[(size_t)sl * ne + i];
+                }
     }
     S.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     return CGS_OK;
