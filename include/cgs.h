@@ -86,6 +86,8 @@ typedef struct {
     size_t footprint_bytes;/* device memory held by the mesh                          */
     double setup_seconds;  /* host wall time of cgs_mesh_setup                        */
     int64_t kernel_launches; /* CUDA kernels this mesh has launched so far           */
+    int32_t vert_chunk;    /* schedule: vertices per block of the vector kernels     */
+    int32_t sub_chunk;     /* schedule: subdomains per block of the local solves      */
 } cgs_mesh_info_t;
 
 /* Kernel classes reported by the profiler. */
@@ -207,6 +209,61 @@ cgs_status cgs_solve_host(cgs_mesh* mesh, const double* b_host, double* x_host, 
  * (launches[CGS_K_COUNT]) since the last read, and resets them.            */
 cgs_status cgs_profile_enable(cgs_mesh* mesh, int enable);
 cgs_status cgs_profile_read(cgs_mesh* mesh, double* ms, int64_t* launches);
+
+/* ---- batches: many meshes and right-hand sides in each launch ---------------
+ * cgs_batch_create: a solve plan over `nmesh` meshes (same context, same
+ * precision and form) with `nrhs` right-hand sides each, i.e. nmesh*nrhs
+ * slots numbered slot = mesh_index * nrhs + rhs.  Every kernel of the
+ * iteration covers all slots in one launch; slots stop independently (each
+ * has its own scalars and stopping test) and the device-side loop ends when
+ * the last slot stops.  The batch holds its own vector pools (the meshes'
+ * data is shared, not copied) and must be freed before its meshes.
+ * cgs_batch_solve: b[slot], x[slot] are device vectors of the slot's mesh
+ * (host arrays of nmesh*nrhs device pointers); iters, relres (and status
+ * when not NULL) are host arrays of nmesh*nrhs, always written.  Synchronous.
+ * Returns the first slot's error if any slot failed.
+ * cgs_solve_batched: create + solve + free in one call.                     */
+typedef struct cgs_batch cgs_batch;
+cgs_status cgs_batch_create(cgs_ctx* ctx, cgs_mesh* const* meshes, int nmesh, int nrhs, cgs_batch** out);
+cgs_status cgs_batch_free(cgs_batch* batch);
+cgs_status cgs_batch_solve(cgs_batch* batch, const double* const* b, double* const* x, double rtol, int maxit,
+                           int* iters, double* relres, int* status, void* stream);
+int64_t cgs_batch_launches(const cgs_batch* batch);
+/* Autotuner: time the local solves over subdomain chunks {8,16,32,64} and the
+ * vector kernels over vertex chunks {256,...,2048} on the object's own data,
+ * keep the fastest schedule (rebuilds the work tables and the loop graph).
+ * Synchronous; call between solves.  Setup picks a default schedule that
+ * gives about four blocks per SM.                                          */
+cgs_status cgs_mesh_tune(cgs_mesh* mesh, void* stream);
+cgs_status cgs_batch_tune(cgs_batch* batch, void* stream);
+cgs_status cgs_solve_batched(cgs_mesh* const* meshes, int nmesh, const double* const* b, double* const* x,
+                             int nrhs, double rtol, int maxit, int* iters, double* relres, void* stream);
+
+/* ---- serving: continuous batching --------------------------------------------
+ * A server keeps `max_slots` solve slots, each with vector space for a mesh of
+ * up to max_nv vertices and max_nr reduced unknowns, all in one precision
+ * and form, all solved to rtol within maxit products.  Meshes stay set up
+ * (resident) across requests; the caller keeps them alive while requests on
+ * them are pending.
+ * cgs_submit: queue one solve; b and x are device vectors of the mesh that
+ *   the caller keeps valid until cgs_poll reports done.  ADMISSION if the
+ *   mesh exceeds the slot capacity.  Host-only, returns at once.
+ * cgs_server_step: admits queued requests into free slots (starting their
+ *   iteration), runs `iterations` PCG iterations over every running slot in
+ *   shared launches (slots at different iteration counts), then retires the
+ *   slots that stopped: true residual, solution copied to x.  Synchronous.
+ *   active/queued/finished (each may be NULL) report the slot counts.
+ * cgs_poll: done = 1 once the request has finished (then iters, relres and
+ *   status are its results and the ticket is released).                    */
+typedef struct cgs_server cgs_server;
+cgs_status cgs_server_create(cgs_ctx* ctx, int max_slots, int64_t max_nv, int64_t max_nr, cgs_precision prec,
+                             cgs_form form, double rtol, int maxit, cgs_server** out);
+cgs_status cgs_server_free(cgs_server* server);
+cgs_status cgs_submit(cgs_server* server, cgs_mesh* mesh, const double* b, double* x, uint64_t* ticket);
+cgs_status cgs_server_step(cgs_server* server, int iterations, void* stream, int* active, int* queued,
+                           int* finished);
+cgs_status cgs_poll(cgs_server* server, uint64_t ticket, int* done, int* iters, double* relres, int* status);
+int64_t cgs_server_launches(const cgs_server* server);
 
 const char* cgs_status_string(cgs_status s);
 const char* cgs_last_error(void);

@@ -27,7 +27,10 @@ EXPORTS = (
     "cgs_mesh_set_form", "cgs_mesh_export", "cgs_apply_A", "cgs_apply_local", "cgs_restrict",
     "cgs_coarse_solve", "cgs_interp", "cgs_apply_preconditioner", "cgs_apply_preconditioner_noalloc",
     "cgs_solve", "cgs_solve_host",
-    "cgs_profile_enable", "cgs_profile_read", "cgs_status_string", "cgs_last_error",
+    "cgs_profile_enable", "cgs_profile_read", "cgs_batch_create", "cgs_batch_free", "cgs_batch_solve",
+    "cgs_batch_launches", "cgs_solve_batched", "cgs_mesh_tune", "cgs_batch_tune", "cgs_server_create",
+    "cgs_server_free", "cgs_submit", "cgs_server_step", "cgs_poll", "cgs_server_launches", "cgs_status_string",
+    "cgs_last_error",
 )
 KERNEL_CLASSES = ("apply_A64", "apply_A32", "local", "restrict", "coarse", "interp", "pcg_xr", "pcg_dots",
                   "pcg_p", "other")
@@ -48,7 +51,7 @@ class MeshInfo(C.Structure):
     _fields_ = [("nv", C.c_int64), ("ne", C.c_int64), ("n_free", C.c_int64), ("n_sub", C.c_int64),
                 ("n_r", C.c_int64), ("max_sub_dofs", C.c_int64), ("sum_sub_dofs", C.c_int64),
                 ("footprint_bytes", C.c_size_t), ("setup_seconds", C.c_double),
-                ("kernel_launches", C.c_int64)]
+                ("kernel_launches", C.c_int64), ("vert_chunk", C.c_int32), ("sub_chunk", C.c_int32)]
 
 
 _lib = None
@@ -83,6 +86,19 @@ def load(path: str = LIB_PATH):
         "cgs_solve_host": ([P, P, P, I32, D, I32, P, P, P], I32),
         "cgs_profile_enable": ([P, I32], I32),
         "cgs_profile_read": ([P, P, P], I32),
+        "cgs_batch_create": ([P, P, I32, I32, C.POINTER(P)], I32),
+        "cgs_batch_free": ([P], I32),
+        "cgs_batch_solve": ([P, P, P, D, I32, P, P, P, P], I32),
+        "cgs_batch_launches": ([P], I64),
+        "cgs_solve_batched": ([P, I32, P, P, I32, D, I32, P, P, P], I32),
+        "cgs_mesh_tune": ([P, P], I32),
+        "cgs_server_create": ([P, I32, I64, I64, I32, I32, D, I32, C.POINTER(P)], I32),
+        "cgs_server_free": ([P], I32),
+        "cgs_submit": ([P, P, P, P, C.POINTER(C.c_uint64)], I32),
+        "cgs_server_step": ([P, I32, P, C.POINTER(I32), C.POINTER(I32), C.POINTER(I32)], I32),
+        "cgs_poll": ([P, C.c_uint64, C.POINTER(I32), C.POINTER(I32), C.POINTER(D), C.POINTER(I32)], I32),
+        "cgs_server_launches": ([P], I64),
+        "cgs_batch_tune": ([P, P], I32),
         "cgs_status_string": ([I32], C.c_char_p),
         "cgs_last_error": ([], C.c_char_p),
     }
@@ -250,6 +266,102 @@ def cgs_profile_read(mesh) -> dict:
     n = np.zeros(len(KERNEL_CLASSES), np.int64)
     _check(load().cgs_profile_read(mesh, _ptr(ms), _ptr(n)), "cgs_profile_read")
     return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(KERNEL_CLASSES)}
+
+
+def _ptr_array(items):
+    arr = (C.c_void_p * len(items))(*[_ptr(i) for i in items])
+    return arr
+
+
+def cgs_batch_create(ctx, meshes, nrhs=1):
+    """meshes: list of Mesh or raw handles; slot = mesh_index * nrhs + rhs."""
+    hs = [m.handle if isinstance(m, Mesh) else m for m in meshes]
+    arr = (C.c_void_p * len(hs))(*[h.value if isinstance(h, C.c_void_p) else h for h in hs])
+    out = C.c_void_p()
+    _check(load().cgs_batch_create(ctx, arr, len(hs), int(nrhs), C.byref(out)), "cgs_batch_create")
+    return out
+
+
+def cgs_batch_free(batch):
+    _check(load().cgs_batch_free(batch), "cgs_batch_free")
+
+
+def cgs_batch_solve(batch, bs, xs, rtol=1e-8, maxit=1000, stream=None,
+                    allow=(ERR_NO_CONVERGENCE, ERR_BREAKDOWN)):
+    """bs, xs: lists (one per slot) of device vectors.  Returns (status,
+    iters, relres, per-slot status)."""
+    n = len(bs)
+    iters = np.zeros(n, np.int32)
+    relres = np.zeros(n, np.float64)
+    status = np.zeros(n, np.int32)
+    st = load().cgs_batch_solve(batch, _ptr_array(bs), _ptr_array(xs), float(rtol), int(maxit), _ptr(iters),
+                                _ptr(relres), _ptr(status), _stream(stream))
+    _check(st, "cgs_batch_solve", allow)
+    return st, iters, relres, status
+
+
+def cgs_mesh_tune(mesh, stream=None):
+    _check(load().cgs_mesh_tune(mesh, _stream(stream)), "cgs_mesh_tune")
+
+
+def cgs_batch_tune(batch, stream=None):
+    _check(load().cgs_batch_tune(batch, _stream(stream)), "cgs_batch_tune")
+
+
+def cgs_batch_launches(batch) -> int:
+    return int(load().cgs_batch_launches(batch))
+
+
+def cgs_solve_batched(meshes, bs, xs, nrhs=1, rtol=1e-8, maxit=1000, stream=None,
+                      allow=(ERR_NO_CONVERGENCE, ERR_BREAKDOWN)):
+    hs = [m.handle if isinstance(m, Mesh) else m for m in meshes]
+    arr = (C.c_void_p * len(hs))(*[h.value if isinstance(h, C.c_void_p) else h for h in hs])
+    n = len(bs)
+    iters = np.zeros(n, np.int32)
+    relres = np.zeros(n, np.float64)
+    st = load().cgs_solve_batched(arr, len(hs), _ptr_array(bs), _ptr_array(xs), int(nrhs), float(rtol), int(maxit),
+                                  _ptr(iters), _ptr(relres), _stream(stream))
+    _check(st, "cgs_solve_batched", allow)
+    return st, iters, relres
+
+
+def cgs_server_create(ctx, max_slots, max_nv, max_nr, prec="fp32", form="hybrid", rtol=1e-8, maxit=1000):
+    out = C.c_void_p()
+    _check(load().cgs_server_create(ctx, int(max_slots), int(max_nv), int(max_nr), PREC[prec], FORM[form],
+                                    float(rtol), int(maxit), C.byref(out)), "cgs_server_create")
+    return out
+
+
+def cgs_server_free(server):
+    _check(load().cgs_server_free(server), "cgs_server_free")
+
+
+def cgs_submit(server, mesh, b, x) -> int:
+    t = C.c_uint64()
+    h = mesh.handle if isinstance(mesh, Mesh) else mesh
+    _check(load().cgs_submit(server, h, _ptr(b), _ptr(x), C.byref(t)), "cgs_submit")
+    return int(t.value)
+
+
+def cgs_server_step(server, iterations=4, stream=None):
+    """Returns (active, queued, finished) slot counts."""
+    a, q, f = C.c_int(), C.c_int(), C.c_int()
+    _check(load().cgs_server_step(server, int(iterations), _stream(stream), C.byref(a), C.byref(q), C.byref(f)),
+           "cgs_server_step")
+    return a.value, q.value, f.value
+
+
+def cgs_poll(server, ticket):
+    """Returns None while pending, else (iters, relres, status)."""
+    d, it, st = C.c_int(), C.c_int(), C.c_int()
+    rr = C.c_double()
+    _check(load().cgs_poll(server, C.c_uint64(ticket), C.byref(d), C.byref(it), C.byref(rr), C.byref(st)),
+           "cgs_poll")
+    return (it.value, rr.value, st.value) if d.value else None
+
+
+def cgs_server_launches(server) -> int:
+    return int(load().cgs_server_launches(server))
 
 
 class Mesh:

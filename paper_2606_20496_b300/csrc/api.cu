@@ -1,8 +1,16 @@
 // C ABI of the coarse-grid Schwarz solver (declared in include/cgs.h).
+//
+// A mesh owns its device data, one solve slot (scratch vectors, scalars) and
+// an Engine: the work tables of that slot, the device-side PCG loop graph and
+// launch accounting.  A batch is an Engine over many slots (meshes x
+// right-hand sides) whose kernels cover all slots in each launch.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <deque>
+#include <functional>
+#include <unordered_map>
 #include <mutex>
 #include <new>
 #include <string>
@@ -33,6 +41,104 @@ cgs_status cuda_fail(cudaError_t e, const char* where) {
         if (e_ != cudaSuccess) return cuda_fail(e_, #call);     \
     } while (0)
 
+// Device allocations owned by one object, freed together.
+struct DevAllocs {
+    std::vector<void*> ptrs;
+    size_t bytes = 0;
+    template <typename T>
+    cudaError_t alloc(T** out, size_t count) {
+        void* p = nullptr;
+        const size_t b = std::max<size_t>(count, 1) * sizeof(T);
+        cudaError_t e = cudaMalloc(&p, b);
+        if (e != cudaSuccess) return e;
+        ptrs.push_back(p);
+        bytes += b;
+        *out = static_cast<T*>(p);
+        return cudaSuccess;
+    }
+    template <typename T>
+    cudaError_t upload(const T** out, const std::vector<T>& h) {
+        T* p = nullptr;
+        cudaError_t e = alloc(&p, h.size());
+        if (e != cudaSuccess) return e;
+        if (!h.empty()) e = cudaMemcpy(p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice);
+        *out = p;
+        return e;
+    }
+    void release() {
+        for (void* p : ptrs) cudaFree(p);
+        ptrs.clear();
+        bytes = 0;
+    }
+};
+
+// Shared solve machinery of a mesh (one slot) or a batch (many slots).
+struct Engine {
+    Plan P;
+    Vecs V;                    // pools of the solve slots
+    Schedule sch;              // block sizes of the work tables
+    DevAllocs tables;          // the work tables (rebuilt by the tuner)
+    // host-side builder of the work tables for a schedule
+    std::function<void(const Schedule&, std::vector<Work> (&)[kWorkKinds])> build;
+    bool f64 = true;
+    cgs_precision prec = CGS_FP64;
+    cgs_form form = CGS_HYBRID;
+    int64_t total_v = 0;       // vertex entries over all slots
+    SolveScalars* S_host = nullptr;   // pinned copy of the slot scalars
+    cudaGraphExec_t gexec = nullptr;
+    bool graph_failed = false;
+    int last_iters = 8;
+    // launch accounting and the optional event profiler
+    int64_t launches = 0;
+    bool prof = false;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<std::pair<int, size_t>> ev_used;
+    size_t ev_next = 0;
+    double prof_ms[CGS_K_COUNT] = {0};
+    int64_t prof_n[CGS_K_COUNT] = {0};
+
+    void release() {
+        if (gexec) cudaGraphExecDestroy(gexec);
+        gexec = nullptr;
+        tables.release();
+        for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
+        ev_pool.clear();
+        if (S_host) cudaFreeHost(S_host);
+        S_host = nullptr;
+    }
+    cudaEvent_t next_event() {
+        if (ev_next == ev_pool.size()) {
+            cudaEvent_t e;
+            cudaEventCreate(&e);
+            ev_pool.push_back(e);
+        }
+        return ev_pool[ev_next++];
+    }
+};
+
+// Run one kernel launcher, counting it and, when profiling, bracketing it by
+// events on its stream.
+template <typename F>
+inline void launch(Engine& E, int cls, cudaStream_t st, F&& f) {
+    E.launches++;
+    if (!E.prof) {
+        f();
+        return;
+    }
+    const size_t i0 = E.ev_next;
+    cudaEventRecord(E.next_event(), st);
+    f();
+    cudaEventRecord(E.next_event(), st);
+    E.ev_used.emplace_back(cls, i0);
+}
+#define K(cls, call) launch(E, (cls), st, [&]() { call; })
+
+// Vecs for steps that must not stop early (no scalars).
+Vecs no_stop(Vecs V) {
+    V.S = nullptr;
+    return V;
+}
+
 }  // namespace
 
 struct cgs_ctx {
@@ -46,74 +152,32 @@ struct cgs_ctx {
 struct cgs_mesh {
     cgs_ctx* ctx = nullptr;
     cgs_params prm{};
-    cgs_form form = CGS_HYBRID;
-    DevMesh d;
+    DevMesh d;                 // host copy of the descriptor
+    DevMesh* d_dev = nullptr;  // device copy
+    MeshSizes sizes{};
     cgs_mesh_info_t info{};
-    std::vector<void*> allocs;
-    size_t bytes = 0;
+    DevAllocs mem;
+    Engine E;
     // host copies kept for cgs_mesh_export
     std::vector<uint8_t> dir_h;
     std::vector<int64_t> box_active_h, sub_ptr_h;
     std::vector<int32_t> sub_idx_h;
-    // device scratch
-    uint8_t* dir = nullptr;
-    double *r = nullptr, *p = nullptr, *q = nullptr, *y = nullptr, *x = nullptr;
-    float2 *p2 = nullptr, *q2 = nullptr;   // float-pair p and A p of the mixed forms
-    float* ur32 = nullptr;                 // float copy of u_r for the float interpolation
-    // device-side PCG loop: a graph whose while node repeats one iteration
-    cudaGraphExec_t gexec = nullptr;
-    bool graph_failed = false;
-    void* z = nullptr;   // bulk precision (double for FP64, float otherwise)
-    void* s = nullptr;
-    double *rr = nullptr, *ur = nullptr, *partials = nullptr, *out2 = nullptr;
-    SolveScalars* S = nullptr;
-    SolveScalars* S_host = nullptr;   // pinned
-    double* out2_host = nullptr;      // pinned
     double *hb = nullptr, *hx = nullptr;  // device staging for cgs_solve_host
     size_t h_cap = 0;
-    int last_iters = 8;
-    // launch accounting and the optional event profiler
-    int64_t launches = 0;
-    bool prof = false;
-    std::vector<cudaEvent_t> ev_pool;
-    std::vector<std::pair<int, size_t>> ev_used;   // (kernel class, index of the start event)
-    size_t ev_next = 0;
-    double prof_ms[CGS_K_COUNT] = {0};
-    int64_t prof_n[CGS_K_COUNT] = {0};
-
-    template <typename T>
-    cudaError_t alloc(T** p_out, size_t count) {
-        void* p = nullptr;
-        const size_t bytes_ = std::max<size_t>(count, 1) * sizeof(T);
-        cudaError_t e = cudaMalloc(&p, bytes_);
-        if (e != cudaSuccess) return e;
-        allocs.push_back(p);
-        bytes += bytes_;
-        *p_out = static_cast<T*>(p);
-        return cudaSuccess;
-    }
-    template <typename T>
-    cudaError_t upload(const T** p_out, const std::vector<T>& h) {
-        T* p = nullptr;
-        cudaError_t e = alloc(&p, h.size());
-        if (e != cudaSuccess) return e;
-        if (!h.empty()) e = cudaMemcpy(p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice);
-        *p_out = p;
-        return e;
-    }
-    void release() {
-        if (gexec) cudaGraphExecDestroy(gexec);
-        gexec = nullptr;
-        for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
-        ev_pool.clear();
-        for (void* p : allocs) cudaFree(p);
-        allocs.clear();
-        if (S_host) cudaFreeHost(S_host);
-        if (out2_host) cudaFreeHost(out2_host);
-        S_host = nullptr;
-        out2_host = nullptr;
-    }
     bool fp64() const { return prm.prec == CGS_FP64; }
+};
+
+struct cgs_batch {
+    cgs_ctx* ctx = nullptr;
+    std::vector<cgs_mesh*> meshes;
+    int nrhs = 1;
+    DevAllocs mem;
+    Engine E;
+    const double** bptr_h = nullptr;   // pinned staging of the per-slot pointers
+    double** xptr_h = nullptr;
+    const double** bptr_d = nullptr;
+    double** xptr_d = nullptr;
+    int64_t max_nv = 0;
 };
 
 namespace {
@@ -128,11 +192,6 @@ cgs_params default_params() {
     return p;
 }
 
-cgs_status check_mesh(const cgs_mesh* m) {
-    if (!m) return fail(CGS_ERR_INVALID_ARG, "null mesh");
-    return CGS_OK;
-}
-
 cgs_status finish(cudaStream_t st, bool sync) {
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
@@ -143,109 +202,56 @@ cgs_status finish(cudaStream_t st, bool sync) {
     return CGS_OK;
 }
 
-cudaEvent_t next_event(cgs_mesh* m) {
-    if (m->ev_next == m->ev_pool.size()) {
-        cudaEvent_t e;
-        cudaEventCreate(&e);
-        m->ev_pool.push_back(e);
-    }
-    return m->ev_pool[m->ev_next++];
+// z += J~ A_r^{-1} J~^T s  (s: the bulk copy of the residual or of r - A l)
+void box_correction(Engine& E, const Vecs& V, cudaStream_t st) {
+    const Plan& P = E.P;
+    K(CGS_K_RESTRICT, launch_restrict(P, V, E.f64, V.s, E.f64, V.rr, st));
+    K(CGS_K_COARSE, launch_coarse(P, V, V.rr, V.ur, E.f64 ? nullptr : V.ur32, st));
+    K(CGS_K_INTERP, launch_interp_add(P, V, E.f64, V.ur, E.f64 ? nullptr : V.ur32, V.z, st));
 }
 
-// Run one kernel launcher, counting it and, when profiling, bracketing it by
-// events on its stream.
-template <typename F>
-inline void launch(cgs_mesh* m, int cls, cudaStream_t st, F&& f) {
-    m->launches++;
-    if (!m->prof) {
-        f();
-        return;
-    }
-    const size_t i0 = m->ev_next;
-    cudaEventRecord(next_event(m), st);
-    f();
-    cudaEventRecord(next_event(m), st);
-    m->ev_used.emplace_back(cls, i0);
-}
-
-#define K(cls, call) launch(m, (cls), st, [&]() { call; })
-
-// Fill z = 0, s = r (bulk precision), r_r = 0 before a preconditioner apply.
-void precond_prep(cgs_mesh* m, const double* r, cudaStream_t st) {
-    const int64_t nv = m->d.nv;
-    if (m->fp64()) {
-        K(CGS_K_OTHER, launch_fill_d(nv, static_cast<double*>(m->z), 0.0, st));
-        K(CGS_K_OTHER, launch_copy_d(nv, r, static_cast<double*>(m->s), nullptr, st));
-    } else {
-        K(CGS_K_OTHER, launch_fill_f(nv, static_cast<float*>(m->z), 0.0f, st));
-        K(CGS_K_OTHER, launch_convert_d2f(nv, r, static_cast<float*>(m->s), nullptr, st));
-    }
-    if (m->d.nr) K(CGS_K_OTHER, launch_fill_d(m->d.nr, m->rr, 0.0, st));
-}
-
-// z += J~ A_r^{-1} J~^T s (s the bulk copy of the residual or of r - A l).
-void box_correction(cgs_mesh* m, const SolveScalars* S, cudaStream_t st) {
-    const DevMesh& d = m->d;
-    const bool f64 = m->fp64();
-    K(CGS_K_RESTRICT, launch_restrict(d, f64, m->s, f64, m->rr, S, st));
-    K(CGS_K_COARSE, launch_coarse(d, m->rr, m->ur, f64 ? nullptr : m->ur32, S, st));
-    K(CGS_K_INTERP, launch_interp_add(d, f64, m->ur, f64 ? nullptr : m->ur32, m->z, S, st));
-}
-
-// z (bulk) = M r, assuming precond_prep (or the PCG update kernel) ran.
-void precond_body(cgs_mesh* m, const double* r, const SolveScalars* S, cudaStream_t st) {
-    const DevMesh& d = m->d;
-    const bool f64 = m->fp64();
-    if (m->form == CGS_HYBRID) {
-        K(CGS_K_LOCAL, launch_local(d, m->prm.prec, m->s, m->z, true, S, st));
-        if (f64)
-            K(CGS_K_APPLY_A64, launch_apply64(d, static_cast<const double*>(m->z), static_cast<double*>(m->s),
-                                              -1.0, nullptr, const_cast<SolveScalars*>(S), false, st));
+// z (bulk) = M r, with z = 0, s = r (bulk) and r_r = 0 on entry.
+void precond_body(Engine& E, const Vecs& V, cudaStream_t st) {
+    const Plan& P = E.P;
+    if (E.form == CGS_HYBRID) {
+        K(CGS_K_LOCAL, launch_local(P, V, E.prec, V.s, V.z, true, st));
+        if (E.f64)
+            K(CGS_K_APPLY_A64, launch_apply64(P, V, static_cast<const double*>(V.z), static_cast<double*>(V.s), -1.0,
+                                              false, st));
         else
-            K(CGS_K_APPLY_A32, launch_apply28f_tiled(d, static_cast<const float*>(m->z), static_cast<float*>(m->s),
-                                                     -1.0f, const_cast<SolveScalars*>(S), st));
-        if (d.nr) box_correction(m, S, st);
+            K(CGS_K_APPLY_A32,
+              launch_apply28f_tiled(P, V, static_cast<const float*>(V.z), static_cast<float*>(V.s), -1.0f, st));
+        if (P.any_nr) box_correction(E, V, st);
     } else {
-        K(CGS_K_LOCAL, launch_local(d, m->prm.prec, m->s, m->z, false, S, st));
-        if (d.nr) box_correction(m, S, st);
+        K(CGS_K_LOCAL, launch_local(P, V, E.prec, V.s, V.z, false, st));
+        if (P.any_nr) box_correction(E, V, st);
     }
 }
 
-void z_to_double(cgs_mesh* m, double* out, cudaStream_t st) {
-    if (m->fp64())
-        K(CGS_K_OTHER, launch_copy_d(m->d.nv, static_cast<const double*>(m->z), out, m->dir, st));
-    else
-        K(CGS_K_OTHER, launch_convert_f2d(m->d.nv, static_cast<const float*>(m->z), out, m->dir, st));
-}
-
-// One flexible-PCG iteration on mesh-owned buffers (x is the mesh's own
-// iterate, so the same launches can be captured once into a graph).
+// One flexible-PCG iteration over every slot of the engine.
 template <typename Tz>
-void pcg_iteration(cgs_mesh* m, cudaStream_t st, cudaGraphConditionalHandle cond, bool use_cond) {
-    const DevMesh& d = m->d;
-    Tz* z = static_cast<Tz*>(m->z);
-    Tz* s = static_cast<Tz*>(m->s);
-    if (m->fp64()) {
-        K(CGS_K_APPLY_A64, launch_apply64(d, m->p, m->q, 1.0, m->partials, m->S, true, st));
-        K(CGS_K_PCG_XR, (launch_pcg_update_xr<Tz, double>(d, m->x, m->r, m->p, m->q, z, s, m->rr, m->partials,
-                                                           m->S, st)));
-        precond_body(m, m->r, m->S, st);
-        K(CGS_K_PCG_DOTS, (launch_pcg_dots<Tz, double>(d, z, m->r, m->q, m->partials, m->S, st)));
-        K(CGS_K_PCG_P, (launch_pcg_update_p<Tz, double>(d, z, m->p, nullptr, m->q, m->S, cond, use_cond, st)));
+void pcg_iteration(Engine& E, cudaStream_t st) {
+    const Plan& P = E.P;
+    const Vecs& V = E.V;
+    if (E.f64) {
+        K(CGS_K_APPLY_A64, launch_apply64(P, V, V.p, V.q, 1.0, true, st));
+        K(CGS_K_PCG_XR, (launch_pcg_update_xr<Tz, double>(P, V, V.q, st)));
+        precond_body(E, V, st);
+        K(CGS_K_PCG_DOTS, (launch_pcg_dots<Tz, double>(P, V, V.q, st)));
+        K(CGS_K_PCG_P, (launch_pcg_update_p<Tz, double>(P, V, V.q, st)));
     } else {
-        K(CGS_K_APPLY_A64, launch_apply_pair_tiled(d, m->p2, m->q2, m->partials, m->S, st));
-        K(CGS_K_PCG_XR, (launch_pcg_update_xr<Tz, float2>(d, m->x, m->r, m->p, m->q2, z, s, m->rr, m->partials,
-                                                           m->S, st)));
-        precond_body(m, m->r, m->S, st);
-        K(CGS_K_PCG_DOTS, (launch_pcg_dots<Tz, float2>(d, z, m->r, m->q2, m->partials, m->S, st)));
-        K(CGS_K_PCG_P, (launch_pcg_update_p<Tz, float2>(d, z, m->p, m->p2, m->q2, m->S, cond, use_cond, st)));
+        K(CGS_K_APPLY_A64, launch_apply_pair_tiled(P, V, st));
+        K(CGS_K_PCG_XR, (launch_pcg_update_xr<Tz, float2>(P, V, V.q2, st)));
+        precond_body(E, V, st);
+        K(CGS_K_PCG_DOTS, (launch_pcg_dots<Tz, float2>(P, V, V.q2, st)));
+        K(CGS_K_PCG_P, (launch_pcg_update_p<Tz, float2>(P, V, V.q2, st)));
     }
 }
 
-// Build the graph: one while node whose body is one PCG iteration; the body's
-// last kernel sets the loop condition from the device-side stopping test.
+// Build the graph: one while node whose body is one PCG iteration over all
+// slots plus the condition kernel (continue while some slot runs).
 template <typename Tz>
-cgs_status build_loop_graph(cgs_mesh* m) {
+cgs_status build_loop_graph(Engine& E) {
     cudaStream_t cs = nullptr;
     cudaGraph_t g = nullptr;
     cudaGraphExec_t ex = nullptr;
@@ -276,12 +282,16 @@ cgs_status build_loop_graph(cgs_mesh* m) {
     if ((e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal)) !=
         cudaSuccess)
         return bail(e, "cudaStreamBeginCaptureToGraph");
-    const bool prof = m->prof;
-    const int64_t launches = m->launches;
-    m->prof = false;
-    pcg_iteration<Tz>(m, cs, h, true);
-    m->prof = prof;
-    m->launches = launches;
+    const bool prof = E.prof;
+    const int64_t launches = E.launches;
+    E.prof = false;
+    {
+        cudaStream_t st = cs;
+        pcg_iteration<Tz>(E, st);
+        launch_loop_cond(E.P, E.V, h, st);
+    }
+    E.prof = prof;
+    E.launches = launches;
     cudaGraph_t captured = nullptr;
     e = cudaStreamEndCapture(cs, &captured);
     cudaStreamDestroy(cs);
@@ -289,68 +299,193 @@ cgs_status build_loop_graph(cgs_mesh* m) {
     if (e != cudaSuccess) return bail(e, "cudaStreamEndCapture");
     if ((e = cudaGraphInstantiate(&ex, g, 0)) != cudaSuccess) return bail(e, "cudaGraphInstantiate");
     cudaGraphDestroy(g);
-    m->gexec = ex;
+    E.gexec = ex;
     return CGS_OK;
 }
 
+// Solve every slot of the engine: V.b / V.bptr give the right-hand sides,
+// the iterates stay in V.x (copied out through V.xptr when set).  On return
+// E.S_host holds every slot's scalars (iters, status, res2, b2).
 template <typename Tz>
-cgs_status solve_one(cgs_mesh* m, const double* b, double* x, double rtol, int maxit, int* iters, double* relres,
-                     cudaStream_t st) {
-    const DevMesh& d = m->d;
-    if (m->fp64())
-        K(CGS_K_OTHER, launch_pcg_init<double>(d, b, m->dir, m->x, m->r, m->q, rtol, maxit, m->partials, m->S, st));
+cgs_status engine_solve(Engine& E, double rtol, int maxit, cudaStream_t st) {
+    const Plan& P = E.P;
+    const Vecs& V = E.V;
+    if (E.f64)
+        K(CGS_K_OTHER, launch_pcg_init<double>(P, V, V.q, rtol, maxit, st));
     else
-        K(CGS_K_OTHER, launch_pcg_init<float2>(d, b, m->dir, m->x, m->r, m->q2, rtol, maxit, m->partials, m->S, st));
-    // z = M r, p = z, rho = r.z  (skipped when b = 0)
-    if (m->fp64()) {
-        K(CGS_K_OTHER, launch_fill_d(d.nv, static_cast<double*>(m->z), 0.0, st));
-        K(CGS_K_OTHER, launch_copy_d(d.nv, m->r, static_cast<double*>(m->s), nullptr, st));
-    } else {
-        K(CGS_K_OTHER, launch_fill_f(d.nv, static_cast<float*>(m->z), 0.0f, st));
-        K(CGS_K_OTHER, launch_convert_d2f(d.nv, m->r, static_cast<float*>(m->s), nullptr, st));
+        K(CGS_K_OTHER, launch_pcg_init<float2>(P, V, V.q2, rtol, maxit, st));
+    K(CGS_K_OTHER, launch_precond_prep<Tz>(P, V, V.r, st));
+    precond_body(E, V, st);
+    K(CGS_K_OTHER, launch_pcg_first_dir<Tz>(P, V, st));
+    const bool use_graph = !E.prof && !E.graph_failed;
+    if (use_graph && !E.gexec) {
+        if (build_loop_graph<Tz>(E) != CGS_OK) E.graph_failed = true;
     }
-    if (d.nr) K(CGS_K_OTHER, launch_fill_d(d.nr, m->rr, 0.0, st));
-    precond_body(m, m->r, m->S, st);
-    K(CGS_K_OTHER, launch_pcg_first_dir<Tz>(d, static_cast<const Tz*>(m->z), m->r, m->p, m->p2, m->partials, m->S,
-                                            st));
-    const bool use_graph = !m->prof && !m->graph_failed;
-    if (use_graph && !m->gexec) {
-        if (build_loop_graph<Tz>(m) != CGS_OK) m->graph_failed = true;
-    }
-    if (use_graph && m->gexec) {
+    const size_t sbytes = sizeof(SolveScalars) * (size_t)P.nslots;
+    if (use_graph && E.gexec) {
         // the whole iteration loop runs on the device
-        CGS_CUDA(cudaGraphLaunch(m->gexec, st));
-        m->launches += 1;
-        CGS_CUDA(cudaMemcpyAsync(m->S_host, m->S, sizeof(SolveScalars), cudaMemcpyDeviceToHost, st));
+        CGS_CUDA(cudaGraphLaunch(E.gexec, st));
+        E.launches += 1;
     } else {
         int enqueued = 0;
-        int chunk = std::max(2, m->last_iters);
+        int chunk = std::max(2, E.last_iters);
         for (;;) {
             const int n = std::min(chunk, maxit - enqueued);
-            for (int i = 0; i < n; ++i) pcg_iteration<Tz>(m, st, cudaGraphConditionalHandle(), false);
+            for (int i = 0; i < n; ++i) pcg_iteration<Tz>(E, st);
             enqueued += n;
-            CGS_CUDA(cudaMemcpyAsync(m->S_host, m->S, sizeof(SolveScalars), cudaMemcpyDeviceToHost, st));
+            CGS_CUDA(cudaMemcpyAsync(E.S_host, V.S, sbytes, cudaMemcpyDeviceToHost, st));
             CGS_CUDA(cudaStreamSynchronize(st));
-            if (m->S_host->done || enqueued >= maxit) break;
+            bool all = true;
+            for (int s = 0; s < P.nslots; ++s) all = all && E.S_host[s].done;
+            if (all || enqueued >= maxit) break;
             chunk = 4;
         }
     }
-    // x out, then the true residual ||b - A x|| / ||b|| over the free entries
-    K(CGS_K_OTHER, launch_copy_d(d.nv, m->x, x, nullptr, st));
-    K(CGS_K_OTHER, launch_fill_d(d.nv, m->y, 0.0, st));
-    K(CGS_K_APPLY_A64, launch_apply64(d, m->x, m->y, 1.0, nullptr, nullptr, false, st));
-    K(CGS_K_OTHER, launch_resid_norm(d, b, m->y, m->dir, m->partials, &m->S->ticket[1], m->out2, st));
-    CGS_CUDA(cudaMemcpyAsync(m->out2_host, m->out2, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    // the true residual ||b - A x|| over the free entries (and copy-out)
+    const Vecs Vn = no_stop(V);
+    launch_fill_d(E.total_v, V.y, 0.0, st);
+    K(CGS_K_APPLY_A64, launch_apply64(P, Vn, V.x, V.y, 1.0, false, st));
+    K(CGS_K_OTHER, launch_resid_norm(P, V, st));
+    CGS_CUDA(cudaMemcpyAsync(E.S_host, V.S, sbytes, cudaMemcpyDeviceToHost, st));
     cgs_status fs = finish(st, true);
     if (fs != CGS_OK) return fs;
-    const SolveScalars h = *m->S_host;
+    int most = 0;
+    for (int s = 0; s < P.nslots; ++s) most = std::max(most, E.S_host[s].iters);
+    if (most > 0) E.last_iters = most;
+    return CGS_OK;
+}
+
+cgs_status slot_status(const SolveScalars& h) {
     const int status = h.done ? h.status : CGS_ERR_NO_CONVERGENCE;
-    *iters = h.iters;
-    if (h.iters > 0) m->last_iters = h.iters;
-    *relres = m->out2_host[1] > 0 ? std::sqrt(m->out2_host[0] / m->out2_host[1]) : 0.0;
     if (status == CGS_ERR_NO_CONVERGENCE) g_err = "maxit reached before the tolerance";
     if (status == CGS_ERR_BREAKDOWN) g_err = "breakdown in the PCG iteration";
+    if (status == CGS_ERR_TIMEOUT) g_err = "a bounded device wait expired";
     return (cgs_status)status;
+}
+
+double slot_relres(const SolveScalars& h) { return h.b2 > 0 ? std::sqrt(h.res2 / h.b2) : 0.0; }
+
+// Allocate the pooled vectors of `nslots` slots with `total_v` vertex and
+// `total_r` reduced entries, `total_p` partials.
+cudaError_t alloc_pools(DevAllocs& mem, Engine& E, int64_t total_v, int64_t total_r, int64_t total_p, int nslots) {
+    cudaError_t e;
+    Vecs& V = E.V;
+#define TRY(x)                          \
+    if ((e = (x)) != cudaSuccess) return e;
+    TRY(mem.alloc(&V.x, total_v));
+    TRY(mem.alloc(&V.r, total_v));
+    TRY(mem.alloc(&V.p, total_v));
+    TRY(mem.alloc(&V.y, total_v));
+    if (E.f64) {
+        TRY(mem.alloc(&V.q, total_v));
+        double *z, *s;
+        TRY(mem.alloc(&z, total_v));
+        TRY(mem.alloc(&s, total_v));
+        V.z = z;
+        V.s = s;
+    } else {
+        TRY(mem.alloc(&V.q2, total_v));
+        TRY(mem.alloc(&V.p2, total_v));
+        float *z, *s;
+        TRY(mem.alloc(&z, total_v));
+        TRY(mem.alloc(&s, total_v));
+        V.z = z;
+        V.s = s;
+        TRY(mem.alloc(&V.ur32, std::max<int64_t>(total_r, 1)));
+    }
+    TRY(mem.alloc(&V.rr, std::max<int64_t>(total_r, 1)));
+    TRY(mem.alloc(&V.ur, std::max<int64_t>(total_r, 1)));
+    TRY(mem.alloc(&V.partials, std::max<int64_t>(total_p, 2)));
+    TRY(mem.alloc(&V.S, nslots));
+    TRY(cudaMemset(V.S, 0, sizeof(SolveScalars) * nslots));
+    TRY(cudaMallocHost(&E.S_host, sizeof(SolveScalars) * nslots));
+#undef TRY
+    E.total_v = total_v;
+    return cudaSuccess;
+}
+
+// (Re)build the work tables of an engine for a schedule and upload them.
+cudaError_t set_schedule(Engine& E, const Schedule& sch) {
+    std::vector<Work> tabs[kWorkKinds];
+    E.build(sch, tabs);
+    DevAllocs fresh;
+    Plan P = E.P;
+    for (int k = 0; k < kWorkKinds; ++k) {
+        const Work* p = nullptr;
+        cudaError_t e = fresh.upload(&p, tabs[k]);
+        if (e != cudaSuccess) {
+            fresh.release();
+            return e;
+        }
+        P.work[k] = p;
+        P.nwork[k] = (unsigned int)tabs[k].size();
+    }
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        fresh.release();
+        return e;
+    }
+    E.tables.release();
+    E.tables = fresh;
+    E.P = P;
+    E.sch = sch;
+    if (E.gexec) {   // the captured loop holds the old grid sizes
+        cudaGraphExecDestroy(E.gexec);
+        E.gexec = nullptr;
+    }
+    return cudaSuccess;
+}
+
+// Autotuner: time the local solves for each subdomain chunk and a vertex
+// kernel for each vertex chunk on the engine's own data, keep the fastest.
+cgs_status tune_engine(Engine& E, cudaStream_t st) {
+    const int verts[] = {256, 512, 1024, 2048};
+    const int subs[] = {8, 16, 32, 64};
+    cudaEvent_t a, b;
+    CGS_CUDA(cudaEventCreate(&a));
+    CGS_CUDA(cudaEventCreate(&b));
+    const Vecs V = no_stop(E.V);
+    auto time_it = [&](auto&& body) -> float {
+        body();   // warm-up
+        cudaEventRecord(a, st);
+        for (int r = 0; r < 3; ++r) body();
+        cudaEventRecord(b, st);
+        cudaEventSynchronize(b);
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, a, b);
+        return ms;
+    };
+    Schedule best = E.sch;
+    float best_sub = 1e30f, best_vert = 1e30f;
+    for (int sc : subs) {
+        Schedule t = E.sch;
+        t.sub_chunk = sc;
+        if (set_schedule(E, t) != cudaSuccess) continue;
+        const float ms = time_it([&]() { launch_local(E.P, V, E.prec, V.s, V.z, true, st); });
+        if (ms < best_sub) {
+            best_sub = ms;
+            best.sub_chunk = sc;
+        }
+    }
+    for (int vc : verts) {
+        Schedule t = E.sch;
+        t.vert_chunk = vc;
+        if (set_schedule(E, t) != cudaSuccess) continue;
+        const float ms = time_it([&]() {
+            if (E.f64)
+                launch_precond_prep<double>(E.P, V, V.r, st);
+            else
+                launch_precond_prep<float>(E.P, V, V.r, st);
+        });
+        if (ms < best_vert) {
+            best_vert = ms;
+            best.vert_chunk = vc;
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    CGS_CUDA(set_schedule(E, best));
+    return finish(st, true);
 }
 
 }  // namespace
@@ -358,9 +493,10 @@ cgs_status solve_one(cgs_mesh* m, const double* b, double* x, double rtol, int m
 namespace cgs {
 // Read-only views of a mesh for entry points defined in other files.
 const DevMesh& mesh_dev(const cgs_mesh* m) { return m->d; }
+const Plan& mesh_plan(const cgs_mesh* m) { return m->E.P; }
 cgs_precision mesh_prec(const cgs_mesh* m) { return m->prm.prec; }
-cgs_form mesh_form(const cgs_mesh* m) { return m->form; }
-const uint8_t* mesh_dir(const cgs_mesh* m) { return m->dir; }
+cgs_form mesh_form(const cgs_mesh* m) { return m->E.form; }
+const uint8_t* mesh_dir(const cgs_mesh* m) { return m->d.dir; }
 int mesh_device(const cgs_mesh* m) { return m->ctx->device; }
 void set_last_error(const std::string& msg) { g_err = msg; }
 }  // namespace cgs
@@ -425,11 +561,23 @@ cgs_status cgs_mesh_setup(cgs_ctx* ctx, const double* xyz, int64_t nv, const int
     cgs_status st = host_setup(xyz, nv, conn, ne, dirichlet, elem_part, prm, hs, err);
     if (st != CGS_OK) return fail(st, err);
 
+    const bool f64 = prm.prec == CGS_FP64;
+    // estimated footprint for admission before allocating
+    const size_t bulk = f64 ? 8 : 4;
+    const size_t est = (size_t)ne * (8 * 4 + kUpper * 8 + 4) + (f64 ? 0 : hs.at_hi.size() * 8 + (size_t)ne * 16) +
+                       (size_t)nv * (32 + 16 + 1 + 8 + 4) + hs.sub_idx.size() * 4 +
+                       hs.inv.size() * (f64 ? 8 : prm.prec == CGS_FP32_BULK ? 4 : 2) + hs.ar_inv.size() * 8 +
+                       (size_t)nv * (5 * 8 + 2 * bulk);
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        if (ctx->budget && ctx->in_use + est > ctx->budget)
+            return fail(CGS_ERR_ADMISSION, "mesh footprint exceeds the context's HBM budget");
+    }
+
     cgs_mesh* m = new (std::nothrow) cgs_mesh;
     if (!m) return fail(CGS_ERR_INVALID_ARG, "host allocation failed");
     m->ctx = ctx;
     m->prm = prm;
-    m->form = prm.form;
     DevMesh& d = m->d;
     d.nv = nv;
     d.ne = ne;
@@ -439,45 +587,24 @@ cgs_status cgs_mesh_setup(cgs_ctx* ctx, const double* xyz, int64_t nv, const int
         d.b[k] = hs.b[k];
         d.lo[k] = 0.0;   // coordinates are stored relative to the box origin
         d.H[k] = hs.H[k];
+        d.iH[k] = 1.0 / hs.H[k];
     }
     d.max_m = (int)hs.max_m;
 
-    // estimated footprint for admission before allocating
-    const bool f64 = prm.prec == CGS_FP64;
-    const size_t bulk = f64 ? 8 : 4;
-    size_t est = (size_t)ne * (8 * 4 + kUpper * 8 + kOff * 4 + 4) + (size_t)nv * (32 + 16 + 1 + 8 + 4) +
-                 hs.sub_idx.size() * 4 + hs.inv.size() * (prm.prec == CGS_FP64 ? 8 : prm.prec == CGS_FP32_BULK ? 4 : 2) +
-                 hs.ar_inv.size() * 8 + (size_t)nv * (4 * 8 + 2 * bulk);
-    {
-        std::lock_guard<std::mutex> lk(ctx->mu);
-        if (ctx->budget && ctx->in_use + est > ctx->budget) {
-            delete m;
-            return fail(CGS_ERR_ADMISSION, "mesh footprint exceeds the context's HBM budget");
-        }
-    }
-
     auto cleanup = [&](cgs_status s) {
-        m->release();
+        m->E.release();
+        m->mem.release();
         delete m;
         return s;
     };
-#define UP(ptr, vec)                                                   \
-    do {                                                               \
-        cudaError_t e_ = m->upload(&(ptr), (vec));                     \
-        if (e_ != cudaSuccess) return cleanup(cuda_fail(e_, "upload")); \
-    } while (0)
-#define AL(ptr, n)                                                     \
-    do {                                                               \
-        cudaError_t e_ = m->alloc(&(ptr), (n));                        \
-        if (e_ != cudaSuccess) return cleanup(cuda_fail(e_, "alloc"));  \
+#define UP(ptr, vec)                                                      \
+    do {                                                                  \
+        cudaError_t e_ = m->mem.upload(&(ptr), (vec));                    \
+        if (e_ != cudaSuccess) return cleanup(cuda_fail(e_, "upload"));    \
     } while (0)
 
     UP(d.conn, hs.conn);
     UP(d.a36, hs.a36);
-    if (!f64) {
-        UP(d.at_hi, hs.at_hi);
-        UP(d.at_lo, hs.at_lo);
-    }
     UP(d.cell, hs.cell);
     if (!f64) {
         d.ntiles = (int64_t)hs.tile_ptr.size() - 1;
@@ -485,6 +612,8 @@ cgs_status cgs_mesh_setup(cgs_ctx* ctx, const double* xyz, int64_t nv, const int
         UP(d.tile_vptr, hs.tile_vptr);
         UP(d.tile_verts, hs.tile_verts);
         UP(d.eloc, hs.eloc);
+        UP(d.at_hi, hs.at_hi);
+        UP(d.at_lo, hs.at_lo);
     }
     UP(d.cell_cols, hs.cell_cols);
     {
@@ -537,48 +666,34 @@ cgs_status cgs_mesh_setup(cgs_ctx* ctx, const double* xyz, int64_t nv, const int
         }
     }
     if (hs.nr) UP(d.ar_inv, hs.ar_inv);
+    UP(d.dir, hs.dir);
     {
-        const uint8_t* dp = nullptr;
-        UP(dp, hs.dir);
-        m->dir = const_cast<uint8_t*>(dp);
+        const DevMesh* dd = nullptr;
+        UP(dd, std::vector<DevMesh>{d});
+        m->d_dev = const_cast<DevMesh*>(dd);
     }
-    AL(m->r, nv);
-    AL(m->p, nv);
-    AL(m->y, nv);
-    AL(m->x, nv);
-    if (f64) {
-        AL(m->q, nv);
-    } else {
-        AL(m->q2, nv);
-        AL(m->p2, nv);
-    }
-    if (f64) {
-        double* z = nullptr;
-        double* s = nullptr;
-        AL(z, nv);
-        AL(s, nv);
-        m->z = z;
-        m->s = s;
-    } else {
-        float* z = nullptr;
-        float* s = nullptr;
-        AL(z, nv);
-        AL(s, nv);
-        m->z = z;
-        m->s = s;
-    }
-    AL(m->rr, std::max<int64_t>(hs.nr, 1));
-    if (!f64) AL(m->ur32, std::max<int64_t>(hs.nr, 1));
-    AL(m->ur, std::max<int64_t>(hs.nr, 1));
-    AL(m->partials, 2 * (size_t)partial_slots(d));
-    AL(m->out2, 2);
-    AL(m->S, 1);
-    CGS_CUDA(cudaMemset(m->S, 0, sizeof(SolveScalars)));
+    // one solve slot and its work tables
+    m->sizes = MeshSizes{nv, ne, d.ntiles, hs.n_sub, hs.nr};
+    Engine& E = m->E;
+    E.f64 = f64;
+    E.prec = prm.prec;
+    E.form = prm.form;
+    E.P.meshes = m->d_dev;
+    E.P.nslots = 1;
+    E.P.max_m = d.max_m;
+    E.P.any_nr = hs.nr > 0;
     {
-        cudaError_t e = cudaMallocHost(&m->S_host, sizeof(SolveScalars));
-        if (e != cudaSuccess) return cleanup(cuda_fail(e, "cudaMallocHost"));
-        e = cudaMallocHost(&m->out2_host, 2 * sizeof(double));
-        if (e != cudaSuccess) return cleanup(cuda_fail(e, "cudaMallocHost"));
+        const MeshSizes sz = m->sizes;
+        E.build = [sz](const Schedule& sch, std::vector<Work> (&tabs)[kWorkKinds]) {
+            append_mesh_work(tabs, 0, 0, 0, 0, 0, sz, sch);
+        };
+        Schedule smallest;
+        smallest.vert_chunk = 256;
+        smallest.sub_chunk = 8;
+        cudaError_t e = alloc_pools(m->mem, E, nv, hs.nr, mesh_partial_slots(sz, smallest), 1);
+        if (e != cudaSuccess) return cleanup(cuda_fail(e, "scratch"));
+        e = set_schedule(E, default_schedule(nv, hs.n_sub));
+        if (e != cudaSuccess) return cleanup(cuda_fail(e, "work tables"));
     }
     {
         cudaError_t e = cudaDeviceSynchronize();
@@ -586,12 +701,12 @@ cgs_status cgs_mesh_setup(cgs_ctx* ctx, const double* xyz, int64_t nv, const int
     }
     {
         std::lock_guard<std::mutex> lk(ctx->mu);
-        if (ctx->budget && ctx->in_use + m->bytes > ctx->budget) {
+        if (ctx->budget && ctx->in_use + m->mem.bytes > ctx->budget)
             return cleanup(fail(CGS_ERR_ADMISSION, "mesh footprint exceeds the context's HBM budget"));
-        }
-        ctx->in_use += m->bytes;
+        ctx->in_use += m->mem.bytes;
         ctx->live_meshes++;
     }
+#undef UP
     m->dir_h = std::move(hs.dir);
     m->box_active_h = std::move(hs.box_active);
     m->sub_ptr_h = std::move(hs.sub_ptr);
@@ -603,11 +718,9 @@ cgs_status cgs_mesh_setup(cgs_ctx* ctx, const double* xyz, int64_t nv, const int
     m->info.n_r = hs.nr;
     m->info.max_sub_dofs = hs.max_m;
     m->info.sum_sub_dofs = hs.sum_m;
-    m->info.footprint_bytes = m->bytes;
+    m->info.footprint_bytes = m->mem.bytes;
     m->info.setup_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     *out = m;
-#undef UP
-#undef AL
     return CGS_OK;
 }
 
@@ -617,10 +730,13 @@ cgs_status cgs_mesh_free(cgs_mesh* m) {
     cudaDeviceSynchronize();
     {
         std::lock_guard<std::mutex> lk(m->ctx->mu);
-        m->ctx->in_use -= m->bytes;
+        m->ctx->in_use -= m->info.footprint_bytes;
         m->ctx->live_meshes--;
     }
-    m->release();
+    if (m->hb) cudaFree(m->hb);
+    if (m->hx) cudaFree(m->hx);
+    m->E.release();
+    m->mem.release();
     delete m;
     return CGS_OK;
 }
@@ -628,41 +744,20 @@ cgs_status cgs_mesh_free(cgs_mesh* m) {
 cgs_status cgs_mesh_info(const cgs_mesh* m, cgs_mesh_info_t* info) {
     if (!m || !info) return fail(CGS_ERR_INVALID_ARG, "null argument");
     *info = m->info;
-    info->kernel_launches = m->launches;
-    return CGS_OK;
-}
-
-cgs_status cgs_profile_enable(cgs_mesh* m, int enable) {
-    if (!m) return fail(CGS_ERR_INVALID_ARG, "null mesh");
-    m->prof = enable != 0;
-    return CGS_OK;
-}
-
-cgs_status cgs_profile_read(cgs_mesh* m, double* ms, int64_t* launches) {
-    if (!m) return fail(CGS_ERR_INVALID_ARG, "null mesh");
-    if (!m->ev_used.empty()) {
-        CGS_CUDA(cudaEventSynchronize(m->ev_pool[m->ev_used.back().second + 1]));
-        for (const auto& u : m->ev_used) {
-            float t = 0.0f;
-            CGS_CUDA(cudaEventElapsedTime(&t, m->ev_pool[u.second], m->ev_pool[u.second + 1]));
-            m->prof_ms[u.first] += t;
-            m->prof_n[u.first] += 1;
-        }
-    }
-    m->ev_used.clear();
-    m->ev_next = 0;
-    for (int k = 0; k < CGS_K_COUNT; ++k) {
-        if (ms) ms[k] = m->prof_ms[k];
-        if (launches) launches[k] = m->prof_n[k];
-        m->prof_ms[k] = 0.0;
-        m->prof_n[k] = 0;
-    }
+    info->kernel_launches = m->E.launches;
+    info->vert_chunk = m->E.sch.vert_chunk;
+    info->sub_chunk = m->E.sch.sub_chunk;
     return CGS_OK;
 }
 
 cgs_status cgs_mesh_set_form(cgs_mesh* m, cgs_form form) {
     if (!m || form < CGS_HYBRID || form > CGS_ADDITIVE) return fail(CGS_ERR_INVALID_ARG, "bad mesh or form");
-    m->form = form;
+    if (form != m->E.form && m->E.gexec) {   // the captured loop holds the old form
+        cudaDeviceSynchronize();
+        cudaGraphExecDestroy(m->E.gexec);
+        m->E.gexec = nullptr;
+    }
+    m->E.form = form;
     return CGS_OK;
 }
 
@@ -676,105 +771,162 @@ cgs_status cgs_mesh_export(const cgs_mesh* m, uint8_t* dirichlet, int64_t* box_a
     return CGS_OK;
 }
 
+cgs_status cgs_profile_enable(cgs_mesh* m, int enable) {
+    if (!m) return fail(CGS_ERR_INVALID_ARG, "null mesh");
+    m->E.prof = enable != 0;
+    return CGS_OK;
+}
+
+cgs_status cgs_profile_read(cgs_mesh* m, double* ms, int64_t* launches) {
+    if (!m) return fail(CGS_ERR_INVALID_ARG, "null mesh");
+    Engine& E = m->E;
+    if (!E.ev_used.empty()) {
+        CGS_CUDA(cudaEventSynchronize(E.ev_pool[E.ev_used.back().second + 1]));
+        for (const auto& u : E.ev_used) {
+            float t = 0.0f;
+            CGS_CUDA(cudaEventElapsedTime(&t, E.ev_pool[u.second], E.ev_pool[u.second + 1]));
+            E.prof_ms[u.first] += t;
+            E.prof_n[u.first] += 1;
+        }
+    }
+    E.ev_used.clear();
+    E.ev_next = 0;
+    for (int k = 0; k < CGS_K_COUNT; ++k) {
+        if (ms) ms[k] = E.prof_ms[k];
+        if (launches) launches[k] = E.prof_n[k];
+        E.prof_ms[k] = 0.0;
+        E.prof_n[k] = 0;
+    }
+    return CGS_OK;
+}
+
+// ---- single steps: user buffers take the place of the slot's vectors -------
+
 cgs_status cgs_apply_A(cgs_mesh* m, const double* x, double* y, void* stream) {
-    if (check_mesh(m) != CGS_OK || !x || !y) return fail(CGS_ERR_INVALID_ARG, "null argument");
+    if (!m || !x || !y) return fail(CGS_ERR_INVALID_ARG, "null argument");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    Engine& E = m->E;
+    const Vecs V = no_stop(E.V);
     K(CGS_K_OTHER, launch_fill_d(m->d.nv, y, 0.0, st));
-    K(CGS_K_APPLY_A64, launch_apply64(m->d, x, y, 1.0, nullptr, nullptr, false, st));
+    K(CGS_K_APPLY_A64, launch_apply64(E.P, V, x, y, 1.0, false, st));
     return finish(st, false);
 }
 
 cgs_status cgs_apply_local(cgs_mesh* m, const double* r, double* l, int weighted, void* stream) {
-    if (check_mesh(m) != CGS_OK || !r || !l) return fail(CGS_ERR_INVALID_ARG, "null argument");
+    if (!m || !r || !l) return fail(CGS_ERR_INVALID_ARG, "null argument");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    if (m->fp64())
-        K(CGS_K_OTHER, launch_fill_d(m->d.nv, static_cast<double*>(m->z), 0.0, st));
-    else
-        K(CGS_K_OTHER, launch_fill_f(m->d.nv, static_cast<float*>(m->z), 0.0f, st));
-    const void* rin = r;
-    if (!m->fp64()) {   // the float kernels read the residual in the bulk precision
-        K(CGS_K_OTHER, launch_convert_d2f(m->d.nv, r, static_cast<float*>(m->s), nullptr, st));
-        rin = m->s;
+    Engine& E = m->E;
+    const Vecs V = no_stop(E.V);
+    if (m->fp64()) {
+        K(CGS_K_OTHER, launch_precond_prep<double>(E.P, V, r, st));
+        K(CGS_K_LOCAL, launch_local(E.P, V, E.prec, V.s, V.z, weighted != 0, st));
+        K(CGS_K_OTHER, launch_copy_d(E.P, static_cast<const double*>(V.z), l, true, st));
+    } else {
+        K(CGS_K_OTHER, launch_precond_prep<float>(E.P, V, r, st));
+        K(CGS_K_LOCAL, launch_local(E.P, V, E.prec, V.s, V.z, weighted != 0, st));
+        K(CGS_K_OTHER, launch_convert_f2d(E.P, static_cast<const float*>(V.z), l, true, st));
     }
-    K(CGS_K_LOCAL, launch_local(m->d, m->prm.prec, rin, m->z, weighted != 0, nullptr, st));
-    z_to_double(m, l, st);
     return finish(st, false);
 }
 
 cgs_status cgs_restrict(cgs_mesh* m, const double* s, double* rr, void* stream) {
-    if (check_mesh(m) != CGS_OK || !s || (!rr && m->d.nr)) return fail(CGS_ERR_INVALID_ARG, "null argument");
+    if (!m || !s || (!rr && m->d.nr)) return fail(CGS_ERR_INVALID_ARG, "null argument");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (m->d.nr == 0) return CGS_OK;
+    Engine& E = m->E;
+    const Vecs V = no_stop(E.V);
     K(CGS_K_OTHER, launch_fill_d(m->d.nr, rr, 0.0, st));
-    K(CGS_K_RESTRICT, launch_restrict(m->d, m->fp64(), s, true, rr, nullptr, st));
+    K(CGS_K_RESTRICT, launch_restrict(E.P, V, m->fp64(), s, true, rr, st));
     return finish(st, false);
 }
 
 cgs_status cgs_coarse_solve(cgs_mesh* m, const double* rr, double* ur, void* stream) {
-    if (check_mesh(m) != CGS_OK || ((!rr || !ur) && m->d.nr)) return fail(CGS_ERR_INVALID_ARG, "null argument");
+    if (!m || ((!rr || !ur) && m->d.nr)) return fail(CGS_ERR_INVALID_ARG, "null argument");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    K(CGS_K_COARSE, launch_coarse(m->d, rr, ur, nullptr, nullptr, st));
+    Engine& E = m->E;
+    const Vecs V = no_stop(E.V);
+    K(CGS_K_COARSE, launch_coarse(E.P, V, rr, ur, nullptr, st));
     return finish(st, false);
 }
 
 cgs_status cgs_interp(cgs_mesh* m, const double* ur, double* z, void* stream) {
-    if (check_mesh(m) != CGS_OK || !z || (!ur && m->d.nr)) return fail(CGS_ERR_INVALID_ARG, "null argument");
+    if (!m || !z || (!ur && m->d.nr)) return fail(CGS_ERR_INVALID_ARG, "null argument");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    if (m->fp64())
-        K(CGS_K_OTHER, launch_fill_d(m->d.nv, static_cast<double*>(m->z), 0.0, st));
-    else
-        K(CGS_K_OTHER, launch_fill_f(m->d.nv, static_cast<float*>(m->z), 0.0f, st));
-    if (m->d.nr) {
-        K(CGS_K_INTERP, launch_interp_add(m->d, m->fp64(), ur, nullptr, m->z, nullptr, st));
+    Engine& E = m->E;
+    const Vecs V = no_stop(E.V);
+    if (m->fp64()) {
+        K(CGS_K_OTHER, launch_fill_d(m->d.nv, static_cast<double*>(V.z), 0.0, st));
+        K(CGS_K_INTERP, launch_interp_add(E.P, V, true, ur, nullptr, V.z, st));
+        K(CGS_K_OTHER, launch_copy_d(E.P, static_cast<const double*>(V.z), z, true, st));
+    } else {
+        K(CGS_K_OTHER, launch_fill_f(m->d.nv, static_cast<float*>(V.z), 0.0f, st));
+        K(CGS_K_INTERP, launch_interp_add(E.P, V, false, ur, nullptr, V.z, st));
+        K(CGS_K_OTHER, launch_convert_f2d(E.P, static_cast<const float*>(V.z), z, true, st));
     }
-    z_to_double(m, z, st);
     return finish(st, false);
 }
 
 cgs_status cgs_apply_preconditioner(cgs_mesh* m, const double* r, double* z, void* stream) {
-    if (check_mesh(m) != CGS_OK || !r || !z) return fail(CGS_ERR_INVALID_ARG, "null argument");
+    if (!m || !r || !z) return fail(CGS_ERR_INVALID_ARG, "null argument");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    precond_prep(m, r, st);
-    precond_body(m, r, nullptr, st);
-    z_to_double(m, z, st);
+    Engine& E = m->E;
+    const Vecs V = no_stop(E.V);
+    if (m->fp64()) {
+        K(CGS_K_OTHER, launch_precond_prep<double>(E.P, V, r, st));
+        precond_body(E, V, st);
+        K(CGS_K_OTHER, launch_copy_d(E.P, static_cast<const double*>(V.z), z, true, st));
+    } else {
+        K(CGS_K_OTHER, launch_precond_prep<float>(E.P, V, r, st));
+        precond_body(E, V, st);
+        K(CGS_K_OTHER, launch_convert_f2d(E.P, static_cast<const float*>(V.z), z, true, st));
+    }
     return finish(st, false);
 }
 
+// ---- solves ------------------------------------------------------------------
+
 cgs_status cgs_solve(cgs_mesh* m, const double* b, double* x, int nrhs, double rtol, int maxit, int* iters,
                      double* relres, void* stream) {
-    if (check_mesh(m) != CGS_OK || !b || !x || !iters || !relres || nrhs < 0 || !(rtol >= 0.0))
+    if (!m || !b || !x || !iters || !relres || nrhs < 0 || !(rtol >= 0.0))
         return fail(CGS_ERR_INVALID_ARG, "bad argument");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    Engine& E = m->E;
     cgs_status first_bad = CGS_OK;
     for (int k = 0; k < nrhs; ++k) {
         const double* bk = b + (size_t)k * m->d.nv;
         double* xk = x + (size_t)k * m->d.nv;
         iters[k] = 0;
         relres[k] = 0.0;
-        cgs_status s = m->fp64() ? solve_one<double>(m, bk, xk, rtol, maxit, &iters[k], &relres[k], st)
-                                 : solve_one<float>(m, bk, xk, rtol, maxit, &iters[k], &relres[k], st);
-        if (s == CGS_ERR_CUDA || s == CGS_ERR_OOM) return s;
-        if (s != CGS_OK && first_bad == CGS_OK) first_bad = s;
+        E.V.b = bk;
+        cgs_status s = m->fp64() ? engine_solve<double>(E, rtol, maxit, st) : engine_solve<float>(E, rtol, maxit, st);
+        E.V.b = nullptr;
+        if (s != CGS_OK) return s;
+        K(CGS_K_OTHER, launch_copy_d(E.P, E.V.x, xk, false, st));
+        const SolveScalars& h = E.S_host[0];
+        iters[k] = h.iters;
+        relres[k] = slot_relres(h);
+        const cgs_status ss = slot_status(h);
+        if (ss != CGS_OK && first_bad == CGS_OK) first_bad = ss;
     }
+    cgs_status fs = finish(st, true);
+    if (fs != CGS_OK) return fs;
     return first_bad;
 }
 
 cgs_status cgs_solve_host(cgs_mesh* m, const double* b_host, double* x_host, int nrhs, double rtol, int maxit,
                           int* iters, double* relres, void* stream) {
-    if (check_mesh(m) != CGS_OK || !b_host || !x_host || nrhs < 0) return fail(CGS_ERR_INVALID_ARG, "bad argument");
+    if (!m || !b_host || !x_host || nrhs < 0) return fail(CGS_ERR_INVALID_ARG, "bad argument");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const size_t n = (size_t)nrhs * m->d.nv;
     if (n > m->h_cap) {
         if (m->hb) {
             cudaFree(m->hb);
             cudaFree(m->hx);
-            m->allocs.erase(std::remove(m->allocs.begin(), m->allocs.end(), (void*)m->hb), m->allocs.end());
-            m->allocs.erase(std::remove(m->allocs.begin(), m->allocs.end(), (void*)m->hx), m->allocs.end());
             m->hb = m->hx = nullptr;
             m->h_cap = 0;
         }
-        CGS_CUDA(m->alloc(&m->hb, n));
-        CGS_CUDA(m->alloc(&m->hx, n));
+        CGS_CUDA(cudaMalloc(&m->hb, n * sizeof(double)));
+        CGS_CUDA(cudaMalloc(&m->hx, n * sizeof(double)));
         m->h_cap = n;
     }
     CGS_CUDA(cudaMemcpyAsync(m->hb, b_host, n * sizeof(double), cudaMemcpyHostToDevice, st));
@@ -784,5 +936,517 @@ cgs_status cgs_solve_host(cgs_mesh* m, const double* b_host, double* x_host, int
     CGS_CUDA(cudaStreamSynchronize(st));
     return s;
 }
+
+// ---- batches -------------------------------------------------------------------
+
+cgs_status cgs_batch_create(cgs_ctx* ctx, cgs_mesh* const* meshes, int nmesh, int nrhs, cgs_batch** out) {
+    if (!out) return fail(CGS_ERR_INVALID_ARG, "null out");
+    *out = nullptr;
+    if (!ctx || !meshes || nmesh <= 0 || nrhs <= 0) return fail(CGS_ERR_INVALID_ARG, "bad argument");
+    for (int i = 0; i < nmesh; ++i) {
+        if (!meshes[i] || meshes[i]->ctx != ctx) return fail(CGS_ERR_INVALID_ARG, "mesh of another context");
+        if (meshes[i]->prm.prec != meshes[0]->prm.prec || meshes[i]->E.form != meshes[0]->E.form)
+            return fail(CGS_ERR_INVALID_ARG, "meshes of one batch share precision and form");
+    }
+    CGS_CUDA(cudaSetDevice(ctx->device));
+    cgs_batch* B = new (std::nothrow) cgs_batch;
+    if (!B) return fail(CGS_ERR_INVALID_ARG, "host allocation failed");
+    B->ctx = ctx;
+    B->meshes.assign(meshes, meshes + nmesh);
+    B->nrhs = nrhs;
+    auto cleanup = [&](cgs_status s) {
+        B->E.release();
+        B->mem.release();
+        if (B->bptr_h) cudaFreeHost(B->bptr_h);
+        if (B->xptr_h) cudaFreeHost(B->xptr_h);
+        delete B;
+        return s;
+    };
+    Engine& E = B->E;
+    E.f64 = meshes[0]->fp64();
+    E.prec = meshes[0]->prm.prec;
+    E.form = meshes[0]->E.form;
+    const int nslots = nmesh * nrhs;
+    std::vector<DevMesh> descs(nmesh);
+    std::vector<MeshSizes> sizes(nmesh);
+    int64_t total_v = 0, total_r = 0, total_sub = 0;
+    for (int i = 0; i < nmesh; ++i) {
+        const cgs_mesh* m = meshes[i];
+        descs[i] = m->d;
+        sizes[i] = m->sizes;
+        E.P.max_m = std::max(E.P.max_m, m->d.max_m);
+        E.P.any_nr = E.P.any_nr || m->d.nr > 0;
+        B->max_nv = std::max(B->max_nv, m->d.nv);
+        total_v += (int64_t)nrhs * m->d.nv;
+        total_r += (int64_t)nrhs * m->d.nr;
+        total_sub += (int64_t)nrhs * m->d.n_sub;
+    }
+    // the slots of one mesh are interleaved item by item so that blocks
+    // reading the same tile run together (the repeats hit L2)
+    E.build = [sizes, nrhs](const Schedule& sch, std::vector<Work> (&tabs)[kWorkKinds]) {
+        int64_t voff = 0, roff = 0, poff = 0;
+        for (size_t i = 0; i < sizes.size(); ++i) {
+            std::vector<Work> one[kWorkKinds];
+            append_mesh_work(one, (int)i, 0, 0, 0, 0, sizes[i], sch);
+            Schedule smallest;
+            smallest.vert_chunk = 256;
+            smallest.sub_chunk = 8;
+            const int64_t ps = mesh_partial_slots(sizes[i], smallest);
+            for (int k = 0; k < kWorkKinds; ++k)
+                for (const Work& w0 : one[k])
+                    for (int r = 0; r < nrhs; ++r) {
+                        Work w = w0;
+                        w.slot = (int32_t)i * nrhs + r;
+                        w.voff = voff + (int64_t)r * sizes[i].nv;
+                        w.roff = (int32_t)(roff + (int64_t)r * sizes[i].nr);
+                        w.poff = (int32_t)(poff + (int64_t)r * ps);
+                        tabs[k].push_back(w);
+                    }
+            voff += (int64_t)nrhs * sizes[i].nv;
+            roff += (int64_t)nrhs * sizes[i].nr;
+            poff += (int64_t)nrhs * ps;
+        }
+    };
+    int64_t total_p = 0;
+    {
+        Schedule smallest;
+        smallest.vert_chunk = 256;
+        smallest.sub_chunk = 8;
+        for (int i = 0; i < nmesh; ++i) total_p += (int64_t)nrhs * mesh_partial_slots(sizes[i], smallest);
+    }
+    if (total_p >= INT32_MAX || total_r >= INT32_MAX) return cleanup(fail(CGS_ERR_INVALID_ARG, "batch too large"));
+    {
+        const DevMesh* dm = nullptr;
+        cudaError_t e = B->mem.upload(&dm, descs);
+        if (e != cudaSuccess) return cleanup(cuda_fail(e, "mesh descriptors"));
+        E.P.meshes = dm;
+        E.P.nslots = nslots;
+        if ((e = alloc_pools(B->mem, E, total_v, total_r, total_p, nslots)) != cudaSuccess)
+            return cleanup(cuda_fail(e, "pools"));
+        if ((e = set_schedule(E, default_schedule(total_v, total_sub))) != cudaSuccess)
+            return cleanup(cuda_fail(e, "work tables"));
+        if ((e = B->mem.alloc(&B->bptr_d, nslots)) != cudaSuccess) return cleanup(cuda_fail(e, "pointers"));
+        if ((e = B->mem.alloc(&B->xptr_d, nslots)) != cudaSuccess) return cleanup(cuda_fail(e, "pointers"));
+        if ((e = cudaMallocHost(&B->bptr_h, sizeof(double*) * nslots)) != cudaSuccess)
+            return cleanup(cuda_fail(e, "pinned pointers"));
+        if ((e = cudaMallocHost(&B->xptr_h, sizeof(double*) * nslots)) != cudaSuccess)
+            return cleanup(cuda_fail(e, "pinned pointers"));
+        if ((e = cudaDeviceSynchronize()) != cudaSuccess) return cleanup(cuda_fail(e, "batch setup"));
+    }
+    E.V.bptr = B->bptr_d;
+    E.V.xptr = B->xptr_d;
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        ctx->in_use += B->mem.bytes;
+        ctx->live_meshes++;
+    }
+    *out = B;
+    return CGS_OK;
+}
+
+cgs_status cgs_batch_free(cgs_batch* B) {
+    if (!B) return fail(CGS_ERR_INVALID_ARG, "null batch");
+    cudaSetDevice(B->ctx->device);
+    cudaDeviceSynchronize();
+    {
+        std::lock_guard<std::mutex> lk(B->ctx->mu);
+        B->ctx->in_use -= B->mem.bytes;
+        B->ctx->live_meshes--;
+    }
+    B->E.release();
+    B->mem.release();
+    if (B->bptr_h) cudaFreeHost(B->bptr_h);
+    if (B->xptr_h) cudaFreeHost(B->xptr_h);
+    delete B;
+    return CGS_OK;
+}
+
+cgs_status cgs_batch_solve(cgs_batch* B, const double* const* b, double* const* x, double rtol, int maxit,
+                           int* iters, double* relres, int* status, void* stream) {
+    if (!B || !b || !x || !iters || !relres || !(rtol >= 0.0)) return fail(CGS_ERR_INVALID_ARG, "bad argument");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    Engine& E = B->E;
+    const int nslots = E.P.nslots;
+    // the staging buffers are free: the previous call on this batch synchronised
+    for (int s = 0; s < nslots; ++s) {
+        if (!b[s] || !x[s]) return fail(CGS_ERR_INVALID_ARG, "null right-hand side or solution");
+        B->bptr_h[s] = b[s];
+        B->xptr_h[s] = x[s];
+    }
+    CGS_CUDA(cudaMemcpyAsync(B->bptr_d, B->bptr_h, sizeof(double*) * nslots, cudaMemcpyHostToDevice, st));
+    CGS_CUDA(cudaMemcpyAsync(B->xptr_d, B->xptr_h, sizeof(double*) * nslots, cudaMemcpyHostToDevice, st));
+    cgs_status s = E.f64 ? engine_solve<double>(E, rtol, maxit, st) : engine_solve<float>(E, rtol, maxit, st);
+    if (s != CGS_OK) return s;
+    cgs_status first_bad = CGS_OK;
+    for (int k = 0; k < nslots; ++k) {
+        const SolveScalars& h = E.S_host[k];
+        iters[k] = h.iters;
+        relres[k] = slot_relres(h);
+        const cgs_status ss = slot_status(h);
+        if (status) status[k] = ss;
+        if (ss != CGS_OK && first_bad == CGS_OK) first_bad = ss;
+    }
+    return first_bad;
+}
+
+int64_t cgs_batch_launches(const cgs_batch* B) { return B ? B->E.launches : 0; }
+
+cgs_status cgs_mesh_tune(cgs_mesh* m, void* stream) {
+    if (!m) return fail(CGS_ERR_INVALID_ARG, "null mesh");
+    return tune_engine(m->E, static_cast<cudaStream_t>(stream));
+}
+
+cgs_status cgs_batch_tune(cgs_batch* B, void* stream) {
+    if (!B) return fail(CGS_ERR_INVALID_ARG, "null batch");
+    return tune_engine(B->E, static_cast<cudaStream_t>(stream));
+}
+
+cgs_status cgs_solve_batched(cgs_mesh* const* meshes, int nmesh, const double* const* b, double* const* x,
+                             int nrhs, double rtol, int maxit, int* iters, double* relres, void* stream) {
+    if (!meshes || nmesh <= 0 || !meshes[0]) return fail(CGS_ERR_INVALID_ARG, "bad argument");
+    cgs_batch* B = nullptr;
+    cgs_status s = cgs_batch_create(meshes[0]->ctx, meshes, nmesh, nrhs, &B);
+    if (s != CGS_OK) return s;
+    s = cgs_batch_solve(B, b, x, rtol, maxit, iters, relres, nullptr, stream);
+    const std::string keep = g_err;
+    cgs_batch_free(B);
+    g_err = keep;
+    return s;
+}
+
+}  // extern "C"
+
+// ---- serving: continuous batching over a pool of solve slots -------------------
+
+struct cgs_server {
+    cgs_ctx* ctx = nullptr;
+    int max_slots = 0;
+    int64_t max_nv = 0, max_nr = 0, pcap = 0;
+    double rtol = 1e-8;
+    int maxit = 1000;
+    DevAllocs mem;
+    Engine E;
+    Schedule sch;
+    // registry of mesh descriptors on the device (index -> mesh)
+    DevMesh* reg_d = nullptr;
+    DevMesh* reg_stage = nullptr;   // pinned staging for descriptor uploads
+    int reg_cap = 0;
+    std::vector<cgs_mesh*> reg;
+    std::vector<int> reg_users;
+    struct Req {
+        uint64_t ticket;
+        cgs_mesh* mesh;
+        const double* b;
+        double* x;
+    };
+    std::deque<Req> queue;
+    struct SlotState {
+        bool busy = false;
+        Req req{};
+        int reg = -1;
+    };
+    std::vector<SlotState> slots;
+    struct Res {
+        int done, iters, status;
+        double relres;
+    };
+    std::unordered_map<uint64_t, Res> results;
+    uint64_t next_ticket = 1;
+    // work tables of the current slots, of the slots admitted this step and
+    // of the slots finished this step (capacity-grown device buffers)
+    struct Table {
+        Work* d[kWorkKinds] = {};
+        size_t cap[kWorkKinds] = {};
+        Work* h[kWorkKinds] = {};     // pinned staging
+        size_t hcap[kWorkKinds] = {};
+    } t_main, t_admit, t_fin;
+    Plan P_main, P_admit, P_fin;
+    bool dirty = true;
+    const double** bptr_h = nullptr;
+    double** xptr_h = nullptr;
+    const double** bptr_d = nullptr;
+    double** xptr_d = nullptr;
+};
+
+namespace {
+
+void free_table(cgs_server::Table& t) {
+    for (int k = 0; k < kWorkKinds; ++k) {
+        if (t.d[k]) cudaFree(t.d[k]);
+        if (t.h[k]) cudaFreeHost(t.h[k]);
+        t.d[k] = nullptr;
+        t.h[k] = nullptr;
+        t.cap[k] = t.hcap[k] = 0;
+    }
+}
+
+// Work tables for the listed slots, uploaded into a capacity-grown table.
+cudaError_t server_tables(cgs_server* sv, const std::vector<int>& ids, cgs_server::Table& t, Plan& P,
+                          cudaStream_t st) {
+    std::vector<Work> tabs[kWorkKinds];
+    P = Plan();
+    P.meshes = sv->reg_d;
+    P.nslots = sv->max_slots;
+    P.wait_limit = sv->E.P.wait_limit;
+    for (int k : ids) {
+        const cgs_server::SlotState& ss = sv->slots[k];
+        const cgs_mesh* m = ss.req.mesh;
+        append_mesh_work(tabs, ss.reg, k, (int64_t)k * sv->max_nv, (int64_t)k * sv->max_nr, (int64_t)k * sv->pcap,
+                         m->sizes, sv->sch);
+        P.max_m = std::max(P.max_m, m->d.max_m);
+        P.any_nr = P.any_nr || m->d.nr > 0;
+    }
+    for (int kind = 0; kind < kWorkKinds; ++kind) {
+        const size_t n = tabs[kind].size();
+        if (n > t.cap[kind]) {
+            if (t.d[kind]) cudaFree(t.d[kind]);
+            if (t.h[kind]) cudaFreeHost(t.h[kind]);
+            const size_t c = std::max<size_t>(n, 2 * t.cap[kind]);
+            cudaError_t e = cudaMalloc(&t.d[kind], c * sizeof(Work));
+            if (e != cudaSuccess) return e;
+            if ((e = cudaMallocHost(&t.h[kind], c * sizeof(Work))) != cudaSuccess) return e;
+            t.cap[kind] = t.hcap[kind] = c;
+        }
+        if (n) {
+            std::memcpy(t.h[kind], tabs[kind].data(), n * sizeof(Work));
+            cudaError_t e = cudaMemcpyAsync(t.d[kind], t.h[kind], n * sizeof(Work), cudaMemcpyHostToDevice, st);
+            if (e != cudaSuccess) return e;
+        }
+        P.work[kind] = t.d[kind];
+        P.nwork[kind] = (unsigned int)n;
+    }
+    return cudaSuccess;
+}
+
+int server_register(cgs_server* sv, cgs_mesh* m, cudaStream_t st) {
+    for (int i = 0; i < sv->reg_cap; ++i)
+        if (sv->reg[i] == m) {
+            sv->reg_users[i]++;
+            return i;
+        }
+    for (int i = 0; i < sv->reg_cap; ++i)
+        if (!sv->reg[i] || sv->reg_users[i] == 0) {
+            sv->reg[i] = m;
+            sv->reg_users[i] = 1;
+            sv->reg_stage[i] = m->d;
+            cudaMemcpyAsync(sv->reg_d + i, sv->reg_stage + i, sizeof(DevMesh), cudaMemcpyHostToDevice, st);
+            return i;
+        }
+    return -1;
+}
+
+}  // namespace
+
+extern "C" {
+
+cgs_status cgs_server_create(cgs_ctx* ctx, int max_slots, int64_t max_nv, int64_t max_nr, cgs_precision prec,
+                             cgs_form form, double rtol, int maxit, cgs_server** out) {
+    if (!out) return fail(CGS_ERR_INVALID_ARG, "null out");
+    *out = nullptr;
+    if (!ctx || max_slots <= 0 || max_nv <= 0 || max_nr < 0 || !(rtol >= 0.0))
+        return fail(CGS_ERR_INVALID_ARG, "bad argument");
+    CGS_CUDA(cudaSetDevice(ctx->device));
+    cgs_server* sv = new (std::nothrow) cgs_server;
+    if (!sv) return fail(CGS_ERR_INVALID_ARG, "host allocation failed");
+    sv->ctx = ctx;
+    sv->max_slots = max_slots;
+    sv->max_nv = max_nv;
+    sv->max_nr = max_nr;
+    sv->pcap = 2 * ((max_nv + 127) / 128 + 8);
+    sv->rtol = rtol;
+    sv->maxit = maxit;
+    sv->slots.resize(max_slots);
+    sv->reg_cap = 4 * max_slots + 16;
+    sv->reg.assign(sv->reg_cap, nullptr);
+    sv->reg_users.assign(sv->reg_cap, 0);
+    Engine& E = sv->E;
+    E.f64 = prec == CGS_FP64;
+    E.prec = prec;
+    E.form = form;
+    auto cleanup = [&](cgs_status s) {
+        E.release();
+        sv->mem.release();
+        if (sv->reg_stage) cudaFreeHost(sv->reg_stage);
+        if (sv->bptr_h) cudaFreeHost(sv->bptr_h);
+        if (sv->xptr_h) cudaFreeHost(sv->xptr_h);
+        delete sv;
+        return s;
+    };
+    cudaError_t e;
+    if ((e = sv->mem.alloc(&sv->reg_d, sv->reg_cap)) != cudaSuccess) return cleanup(cuda_fail(e, "registry"));
+    if ((e = cudaMallocHost(&sv->reg_stage, sizeof(DevMesh) * sv->reg_cap)) != cudaSuccess)
+        return cleanup(cuda_fail(e, "registry staging"));
+    if ((e = alloc_pools(sv->mem, E, (int64_t)max_slots * max_nv, (int64_t)max_slots * max_nr,
+                         (int64_t)max_slots * sv->pcap, max_slots)) != cudaSuccess)
+        return cleanup(cuda_fail(e, "slot pools"));
+    if ((e = sv->mem.alloc(&sv->bptr_d, max_slots)) != cudaSuccess) return cleanup(cuda_fail(e, "pointers"));
+    if ((e = sv->mem.alloc(&sv->xptr_d, max_slots)) != cudaSuccess) return cleanup(cuda_fail(e, "pointers"));
+    if ((e = cudaMallocHost(&sv->bptr_h, sizeof(double*) * max_slots)) != cudaSuccess)
+        return cleanup(cuda_fail(e, "pointers"));
+    if ((e = cudaMallocHost(&sv->xptr_h, sizeof(double*) * max_slots)) != cudaSuccess)
+        return cleanup(cuda_fail(e, "pointers"));
+    for (int k = 0; k < max_slots; ++k) {
+        sv->bptr_h[k] = nullptr;
+        sv->xptr_h[k] = nullptr;
+    }
+    // vertex chunks for the typical slot, subdomain chunks for small meshes
+    sv->sch = default_schedule(max_nv, max_nv / 8);
+    E.V.bptr = sv->bptr_d;
+    E.V.xptr = sv->xptr_d;
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        if (ctx->budget && ctx->in_use + sv->mem.bytes > ctx->budget)
+            return cleanup(fail(CGS_ERR_ADMISSION, "slot pools exceed the context's HBM budget"));
+        ctx->in_use += sv->mem.bytes;
+        ctx->live_meshes++;
+    }
+    *out = sv;
+    return CGS_OK;
+}
+
+cgs_status cgs_server_free(cgs_server* sv) {
+    if (!sv) return fail(CGS_ERR_INVALID_ARG, "null server");
+    cudaSetDevice(sv->ctx->device);
+    cudaDeviceSynchronize();
+    {
+        std::lock_guard<std::mutex> lk(sv->ctx->mu);
+        sv->ctx->in_use -= sv->mem.bytes;
+        sv->ctx->live_meshes--;
+    }
+    free_table(sv->t_main);
+    free_table(sv->t_admit);
+    free_table(sv->t_fin);
+    sv->E.release();
+    sv->mem.release();
+    if (sv->reg_stage) cudaFreeHost(sv->reg_stage);
+    if (sv->bptr_h) cudaFreeHost(sv->bptr_h);
+    if (sv->xptr_h) cudaFreeHost(sv->xptr_h);
+    delete sv;
+    return CGS_OK;
+}
+
+cgs_status cgs_submit(cgs_server* sv, cgs_mesh* mesh, const double* b, double* x, uint64_t* ticket) {
+    if (!sv || !mesh || !b || !x || !ticket) return fail(CGS_ERR_INVALID_ARG, "null argument");
+    if (mesh->ctx != sv->ctx) return fail(CGS_ERR_INVALID_ARG, "mesh of another context");
+    if (mesh->prm.prec != sv->E.prec || mesh->E.form != sv->E.form)
+        return fail(CGS_ERR_INVALID_ARG, "mesh precision or form differs from the server's");
+    if (mesh->d.nv > sv->max_nv || mesh->d.nr > sv->max_nr ||
+        mesh_partial_slots(mesh->sizes, sv->sch) > sv->pcap)
+        return fail(CGS_ERR_ADMISSION, "mesh larger than the server's slot capacity");
+    *ticket = sv->next_ticket++;
+    sv->queue.push_back(cgs_server::Req{*ticket, mesh, b, x});
+    sv->results[*ticket] = cgs_server::Res{0, 0, CGS_OK, 0.0};
+    return CGS_OK;
+}
+
+cgs_status cgs_server_step(cgs_server* sv, int iterations, void* stream, int* active, int* queued,
+                           int* finished) {
+    if (!sv || iterations < 0) return fail(CGS_ERR_INVALID_ARG, "bad argument");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    Engine& E = sv->E;
+    // 1. admit queued requests into free slots
+    std::vector<int> fresh;
+    for (int k = 0; k < sv->max_slots && !sv->queue.empty(); ++k) {
+        cgs_server::SlotState& ss = sv->slots[k];
+        if (ss.busy) continue;
+        const int ri = server_register(sv, sv->queue.front().mesh, st);
+        if (ri < 0) break;
+        ss.busy = true;
+        ss.req = sv->queue.front();
+        ss.reg = ri;
+        sv->queue.pop_front();
+        sv->bptr_h[k] = ss.req.b;
+        sv->xptr_h[k] = ss.req.x;
+        fresh.push_back(k);
+    }
+    std::vector<int> busy;
+    for (int k = 0; k < sv->max_slots; ++k)
+        if (sv->slots[k].busy) busy.push_back(k);
+    if (!fresh.empty()) {
+        CGS_CUDA(cudaMemcpyAsync(sv->bptr_d, sv->bptr_h, sizeof(double*) * sv->max_slots, cudaMemcpyHostToDevice, st));
+        CGS_CUDA(cudaMemcpyAsync(sv->xptr_d, sv->xptr_h, sizeof(double*) * sv->max_slots, cudaMemcpyHostToDevice, st));
+        CGS_CUDA(server_tables(sv, fresh, sv->t_admit, sv->P_admit, st));
+        sv->dirty = true;
+    }
+    if (sv->dirty) {
+        CGS_CUDA(server_tables(sv, busy, sv->t_main, sv->P_main, st));
+        sv->dirty = false;
+    }
+    // 2. start the new slots: r = b, z = M r, p = z
+    if (!fresh.empty()) {
+        E.P = sv->P_admit;
+        const Plan& P = E.P;
+        const Vecs& V = E.V;
+        if (E.f64) {
+            K(CGS_K_OTHER, launch_pcg_init<double>(P, V, V.q, sv->rtol, sv->maxit, st));
+            K(CGS_K_OTHER, launch_precond_prep<double>(P, V, V.r, st));
+            precond_body(E, V, st);
+            K(CGS_K_OTHER, launch_pcg_first_dir<double>(P, V, st));
+        } else {
+            K(CGS_K_OTHER, launch_pcg_init<float2>(P, V, V.q2, sv->rtol, sv->maxit, st));
+            K(CGS_K_OTHER, launch_precond_prep<float>(P, V, V.r, st));
+            precond_body(E, V, st);
+            K(CGS_K_OTHER, launch_pcg_first_dir<float>(P, V, st));
+        }
+    }
+    // 3. iterate every running slot (slots that stop skip their blocks)
+    if (!busy.empty()) {
+        E.P = sv->P_main;
+        for (int i = 0; i < iterations; ++i) {
+            if (E.f64)
+                pcg_iteration<double>(E, st);
+            else
+                pcg_iteration<float>(E, st);
+        }
+    }
+    CGS_CUDA(cudaMemcpyAsync(E.S_host, E.V.S, sizeof(SolveScalars) * sv->max_slots, cudaMemcpyDeviceToHost, st));
+    CGS_CUDA(cudaStreamSynchronize(st));
+    // 4. retire finished slots: true residual, solution out
+    std::vector<int> done;
+    for (int k : busy)
+        if (E.S_host[k].done) done.push_back(k);
+    if (!done.empty()) {
+        CGS_CUDA(server_tables(sv, done, sv->t_fin, sv->P_fin, st));
+        E.P = sv->P_fin;
+        const Vecs Vn = no_stop(E.V);
+        for (int k : done)
+            CGS_CUDA(cudaMemsetAsync(E.V.y + (int64_t)k * sv->max_nv, 0,
+                                     sizeof(double) * sv->slots[k].req.mesh->d.nv, st));
+        K(CGS_K_APPLY_A64, launch_apply64(E.P, Vn, E.V.x, E.V.y, 1.0, false, st));
+        K(CGS_K_OTHER, launch_resid_norm(E.P, E.V, st));
+        CGS_CUDA(cudaMemcpyAsync(E.S_host, E.V.S, sizeof(SolveScalars) * sv->max_slots, cudaMemcpyDeviceToHost, st));
+        CGS_CUDA(cudaStreamSynchronize(st));
+        for (int k : done) {
+            cgs_server::SlotState& ss = sv->slots[k];
+            const SolveScalars& h = E.S_host[k];
+            sv->results[ss.req.ticket] = cgs_server::Res{1, h.iters, (int)slot_status(h), slot_relres(h)};
+            sv->reg_users[ss.reg]--;
+            ss.busy = false;
+            ss.reg = -1;
+        }
+        sv->dirty = true;
+    }
+    cgs_status fs = finish(st, false);
+    if (fs != CGS_OK) return fs;
+    if (active) *active = (int)(busy.size() - done.size());
+    if (queued) *queued = (int)sv->queue.size();
+    if (finished) *finished = (int)done.size();
+    return CGS_OK;
+}
+
+cgs_status cgs_poll(cgs_server* sv, uint64_t ticket, int* done, int* iters, double* relres, int* status) {
+    if (!sv || !done) return fail(CGS_ERR_INVALID_ARG, "null argument");
+    auto it = sv->results.find(ticket);
+    if (it == sv->results.end()) return fail(CGS_ERR_INVALID_ARG, "unknown ticket");
+    const cgs_server::Res& r = it->second;
+    *done = r.done;
+    if (iters) *iters = r.iters;
+    if (relres) *relres = r.relres;
+    if (status) *status = r.status;
+    if (r.done) sv->results.erase(it);
+    return CGS_OK;
+}
+
+int64_t cgs_server_launches(const cgs_server* sv) { return sv ? sv->E.launches : 0; }
 
 }  // extern "C"

@@ -65,9 +65,9 @@ cgs_status host_setup(const double* xyz, int64_t nv, const int32_t* conn, int64_
 struct DevMesh {
     int64_t nv = 0, ne = 0, n_sub = 0, nr = 0;
     int b[3] = {1, 1, 1};
-    double lo[3] = {0, 0, 0}, H[3] = {1, 1, 1};
-    float lof[3] = {0, 0, 0}, Hf[3] = {1, 1, 1};
+    double lo[3] = {0, 0, 0}, H[3] = {1, 1, 1}, iH[3] = {1, 1, 1};
     const int32_t* conn = nullptr;     // ne*8 (int4 x2 per element)
+    const uint8_t* dir = nullptr;      // nv, 1 = Dirichlet
     const double* a36 = nullptr;       // [36][ne]
     const double2* xyzw = nullptr;     // 2*nv: (x, y), (z, 1/count) per vertex, float64
     const float4* xyzwf = nullptr;     // nv: same, float32
@@ -94,6 +94,18 @@ struct DevMesh {
     int max_m = 0;
 };
 
+// Mesh descriptors and work tables of one set of solve slots (launchers).
+struct Work;
+struct Plan {
+    const DevMesh* meshes = nullptr;       // device array of mesh descriptors
+    const Work* work[5] = {};              // device work tables, one per WorkKind
+    unsigned int nwork[5] = {};
+    int nslots = 0;
+    int max_m = 0;                         // largest subdomain over the meshes
+    bool any_nr = false;                   // some mesh has a reduced space
+    int wait_limit = 1 << 20;              // iteration limit of bounded device waits
+};
+
 // Device scalars of one PCG solve (kernels.cu).
 struct SolveScalars {
     double bnorm2;     // ||b||^2
@@ -110,6 +122,41 @@ struct SolveScalars {
     int status;        // cgs_status of the solve
     unsigned int ticket[4];  // block-completion counters of the fused reductions
     int timeouts;            // bounded device-side waits that expired
+    double res2, b2;         // ||b - A x||^2 and ||b||^2 over free entries (final check)
+};
+
+// One block's share of work: a range of elements, tiles, vertices,
+// subdomains or reduced rows of one solve slot (one mesh and one right-hand
+// side).  A slot's vectors live in pooled arrays at the given offsets; its
+// blocks of one kind are numbered idx = 0..count-1 for the per-slot
+// reductions.
+struct Work {
+    int32_t mesh;          // index into the mesh descriptor array
+    int32_t slot;          // index into the SolveScalars array
+    int64_t voff;          // offset of the slot's vertex vectors (nv entries)
+    int32_t roff;          // offset of the slot's reduced-space vectors (n_r entries)
+    int32_t poff;          // offset of the slot's partial sums (2 * count entries)
+    int32_t begin, end;    // the range
+    int32_t idx, count;    // this block among the slot's blocks of this kind
+};
+
+enum WorkKind { kWorkElem = 0, kWorkTile, kWorkVert, kWorkSub, kWorkRow, kWorkKinds };
+constexpr int kElemChunk = 256;   // elements per block
+constexpr int kRowChunk = 8;      // reduced rows per block (one warp each)
+
+// Vector pools of a set of slots, passed by value to every kernel.  A slot's
+// vector is pool + work.voff (vertex vectors) or pool + work.roff (reduced).
+struct Vecs {
+    double *x = nullptr, *r = nullptr, *p = nullptr, *y = nullptr, *q = nullptr;
+    float2 *p2 = nullptr, *q2 = nullptr;   // float-pair p and A p (mixed forms)
+    void *z = nullptr, *s = nullptr;       // bulk precision (double or float)
+    double *rr = nullptr, *ur = nullptr;
+    float* ur32 = nullptr;
+    double* partials = nullptr;
+    SolveScalars* S = nullptr;             // nullptr: no early exit (single steps)
+    const double* b = nullptr;             // right-hand sides (pool), or
+    const double* const* bptr = nullptr;   // per-slot right-hand side pointers
+    double* const* xptr = nullptr;         // per-slot solution pointers (copy-out)
 };
 
 }  // namespace cgs

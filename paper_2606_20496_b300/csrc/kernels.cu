@@ -1,22 +1,28 @@
 // CUDA kernels of the coarse-grid solve (sm_103a).
 //
-//   apply64 / apply28f  y += alpha * Q^T A_L Q x              (Sec. 3)
-//   local_warp          out += W_ov sum_p R_p^T A_p^{-1} R_p r (Eq. asm1)
-//   restrict_box        r_r += J_L^T Q W s                    (Sec. 4)
-//   coarse_gemv         u_r = A_r^{-1} r_r                    (float64)
-//   interp_add          z += W Q^T J_L u_r                    (Sec. 4)
-//   pcg_*               vector updates and fused dot products of flexible PCG
+//   apply64               y += alpha Q^T A_L Q x, float64          (Sec. 3)
+//   apply_pair_tiled      q  = A p, float-pair outer operator      (Sec. 3)
+//   apply28f_tiled        s -= A l, float32 inner apply            (Eq. asm2)
+//   local_warp            out += W_ov sum_p R_p^T A_p^{-1} R_p r   (Eq. asm1)
+//   restrict              r_r += J_L^T Q W s                       (Sec. 4)
+//   coarse_gemv           u_r = A_r^{-1} r_r, float64              (Sec. 4)
+//   interp_add            z += W Q^T J_L u_r                       (Sec. 4)
+//   pcg_*                 flexible-PCG vector updates, fused dots
 //
-// Layout: element data is structure-of-arrays in "device order" (elements
-// sorted by centroid cell), so a warp reads 32 consecutive entries of each
-// element-matrix slot and its 32 elements mostly share one box cell.  The
-// connectivity of an element is two int4 loads; a Dirichlet vertex v is
-// stored as ~v (negative): reads give 0, writes are skipped.
+// Every kernel works through a table of Work items, one per block: a range
+// of elements, element tiles, vertices, subdomains or reduced rows of one
+// solve slot (one mesh and one right-hand side).  A single solve is one slot;
+// a batch of meshes and right-hand sides is many slots in the same launch.
+// Mesh data comes from a device array of mesh descriptors, so the slots of
+// one mesh share it (their blocks are adjacent in the tables, so repeated
+// reads of the same tile hit L2).
 //
-// Reductions are deterministic: each block writes one partial, the last
-// block to finish (ticket counter) sums the partials in a fixed order and
-// finalises the PCG scalars on the device, so the host never has to read a
-// scalar inside the iteration.
+// Per-slot reductions are deterministic: each block writes a partial, the
+// last of the slot's blocks (ticket counter) sums them in a fixed order and
+// finalises the slot's PCG scalars on the device.
+//
+// Layout: elements in "device order" (sorted by centroid cell).  A Dirichlet
+// vertex v appears in the connectivity as ~v: reads give 0, writes skip it.
 #include <algorithm>
 
 #include <cuda_fp16.h>
@@ -59,19 +65,20 @@ __device__ __forceinline__ void block_sum(double (&v)[NV]) {
     }
 }
 
-// Grid-wide deterministic sum: every block calls this with its values; the
-// last block to arrive gets true and the totals in tot (all its threads).
+// Deterministic per-slot sum: every block of the slot calls this with its
+// values; the last of the slot's `count` blocks gets true and the totals.
 template <int NV>
-__device__ bool grid_sum(double (&v)[NV], double* partials, unsigned int* ticket, double (&tot)[NV]) {
+__device__ bool slot_sum(double (&v)[NV], double* partials, int idx, int count, unsigned int* ticket,
+                         double (&tot)[NV]) {
     __shared__ bool last;
     __shared__ double res[NV];
     block_sum<NV>(v);
     if (threadIdx.x == 0) {
 #pragma unroll
-        for (int i = 0; i < NV; ++i) partials[(size_t)i * gridDim.x + blockIdx.x] = v[i];
+        for (int i = 0; i < NV; ++i) partials[(size_t)i * count + idx] = v[i];
         __threadfence();
         const unsigned int t = atomicAdd(ticket, 1u);
-        last = (t == gridDim.x - 1);
+        last = (t == (unsigned int)count - 1);
     }
     __syncthreads();
     if (!last) return false;
@@ -80,8 +87,7 @@ __device__ bool grid_sum(double (&v)[NV], double* partials, unsigned int* ticket
 #pragma unroll
     for (int i = 0; i < NV; ++i) {
         s[i] = 0.0;
-        for (unsigned int b = threadIdx.x; b < gridDim.x; b += blockDim.x)
-            s[i] += __ldcg(&partials[(size_t)i * gridDim.x + b]);
+        for (int b = threadIdx.x; b < count; b += blockDim.x) s[i] += __ldcg(&partials[(size_t)i * count + b]);
     }
     block_sum<NV>(s);
     if (threadIdx.x == 0) {
@@ -102,26 +108,35 @@ __device__ __forceinline__ void load_conn(const int32_t* __restrict__ conn, int6
     v[4] = c1.x; v[5] = c1.y; v[6] = c1.z; v[7] = c1.w;
 }
 
-template <typename T>
-__device__ __forceinline__ T to(double x) { return static_cast<T>(x); }
+// Block prologue: this block's work item, its slot's scalars, and early exit
+// once the slot has stopped.
+#define CGS_WORK_PROLOGUE()                              \
+    const Work w = work[blockIdx.x];                     \
+    SolveScalars* S = V.S ? V.S + w.slot : nullptr;      \
+    if (is_done(S)) return;                              \
+    const DevMesh& M = meshes[w.mesh];                   \
+    (void)M;
 
 // ---------------------------------------------------------------------------
-// Operator apply, float64, 36 stored entries (upper triangle with diagonal).
-// kDot: also sum the element energies x_e^T A^e x_e = x^T A x (used as p.q in
-// PCG; Dirichlet entries of x are zero so this equals p^T A p on free dofs),
-// finalise alpha = rho / pq in the last block.
+// Operator apply, float64 (FP64 form and the final true residual), 36 stored
+// entries (upper triangle with diagonal).  kDot: also sum the element
+// energies x_e^T A^e x_e = p.Ap (Dirichlet entries of p are 0) and finalise
+// alpha = rho / pq in the slot's last block.
 // ---------------------------------------------------------------------------
 template <bool kDot>
-__global__ void __launch_bounds__(kBlock) apply64_kernel(int64_t ne, const int32_t* __restrict__ conn,
-                                                         const double* __restrict__ a36,
-                                                         const double* __restrict__ x, double* __restrict__ y,
-                                                         double alpha, double* partials, SolveScalars* S) {
-    if (is_done(S)) return;
-    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(kBlock) apply64_kernel(const DevMesh* __restrict__ meshes,
+                                                         const Work* __restrict__ work, Vecs V,
+                                                         const double* __restrict__ xin, double* __restrict__ yout,
+                                                         double alpha) {
+    CGS_WORK_PROLOGUE();
+    const double* x = xin + w.voff;
+    double* y = yout + w.voff;
+    const int64_t ne = M.ne;
+    const int64_t e = (int64_t)w.begin + threadIdx.x;
     double energy = 0.0;
-    if (e < ne) {
+    if (e < w.end) {
         int v[8];
-        load_conn(conn, e, v);
+        load_conn(M.conn, e, v);
         double xe[8], ye[8];
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
@@ -133,7 +148,7 @@ __global__ void __launch_bounds__(kBlock) apply64_kernel(int64_t ne, const int32
         for (int i = 0; i < 8; ++i) {
 #pragma unroll
             for (int j = i; j < 8; ++j, ++s) {
-                const double a = __ldg(&a36[(size_t)s * ne + e]);
+                const double a = __ldg(&M.a36[(size_t)s * ne + e]);
                 if (i == j) {
                     ye[i] = fma(a, xe[i], ye[i]);
                 } else {
@@ -150,7 +165,7 @@ __global__ void __launch_bounds__(kBlock) apply64_kernel(int64_t ne, const int32
     }
     if (kDot) {
         double val[1] = {energy}, tot[1];
-        if (grid_sum<1>(val, partials, &S->ticket[0], tot) && threadIdx.x == 0) {
+        if (slot_sum<1>(val, V.partials + w.poff, w.idx, w.count, &S->ticket[0], tot) && threadIdx.x == 0) {
             const double pq = tot[0];
             S->pq = pq;
             if (!(pq > 0.0) || !isfinite(pq)) {
@@ -166,8 +181,9 @@ __global__ void __launch_bounds__(kBlock) apply64_kernel(int64_t ne, const int32
 // ---------------------------------------------------------------------------
 // Float-pair ("double-float") arithmetic on the FP32 pipes.  A value is
 // hi + lo with |lo| <= ulp(hi)/2, about 48 significant bits.  B300 runs FP32
-// FMA ~60x faster than FP64, so the outer operator of the mixed forms is
-// evaluated this way: same iterates as FP64 to ~1e-14, no FP64 instruction.
+// FMA ~60x faster than FP64 (and converts between them at the FP64 rate), so
+// the outer operator of the mixed forms is evaluated this way: the same
+// iterates as FP64 to ~1e-14, no FP64 instruction per element.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
     s = __fadd_rn(a, b);
@@ -229,11 +245,11 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     return ok != 0;
 }
 // Wait for phase 0 of the tile barrier with an iteration limit.  On expiry
-// the solve is flagged CGS_ERR_TIMEOUT and stopped, and the block waits once
+// the slot is flagged CGS_ERR_TIMEOUT and stopped, and the block waits once
 // more (bounded) for its copy before it may return.
 constexpr int kWaitLimit = 1 << 20;
-__device__ __forceinline__ bool wait_tile(uint64_t* bar, SolveScalars* S) {
-    for (int i = 0; i < kWaitLimit; ++i)
+__device__ __forceinline__ bool wait_tile(uint64_t* bar, SolveScalars* S, int limit) {
+    for (int i = 0; i < limit; ++i)
         if (mbar_try_wait(bar, 0)) return true;
     if (S) {
         atomicAdd(&S->timeouts, 1);
@@ -258,42 +274,42 @@ __device__ __forceinline__ void load_loc(const uint16_t* __restrict__ eloc, int6
 
 constexpr uint32_t kTileSlotBytes = kOff * kTileElems * sizeof(float);   // 28 KiB
 
-// q += A p in float-pair arithmetic (outer operator of the mixed forms): the
+// q = A p in float-pair arithmetic (outer operator of the mixed forms): the
 // difference form y_i = sum_j a_ij (x_j - x_i) keeps the error relative to
 // |a||x_j - x_i|; q is summed as pairs with compensated atomics (the exact
 // rounding error of each add to q.hi, recovered from the returned old value,
-// goes to q.lo).  Also sums p.Ap and finalises alpha in the last block.
-__global__ void __launch_bounds__(kBlock) apply_pair_tiled_kernel(
-    int64_t ntiles, const int32_t* __restrict__ tile_ptr, const int32_t* __restrict__ tile_vptr,
-    const uint32_t* __restrict__ tile_verts, const uint16_t* __restrict__ eloc, const float* __restrict__ at_hi,
-    const float* __restrict__ at_lo, const float2* __restrict__ p2, float2* __restrict__ q2, double* partials,
-    SolveScalars* S) {
+// goes to q.lo).  Also sums p.Ap and finalises alpha in the slot's last block.
+__global__ void __launch_bounds__(kBlock) apply_pair_tiled_kernel(const DevMesh* __restrict__ meshes,
+                                                                  const Work* __restrict__ work, Vecs V,
+                                                                  int wait_limit) {
     extern __shared__ __align__(128) unsigned char smem[];
     float* sh_hi = reinterpret_cast<float*>(smem);
     float* sh_lo = sh_hi + kOff * kTileElems;
     float2* ps = reinterpret_cast<float2*>(sh_lo + kOff * kTileElems);
     float2* ys = ps + kTileVerts;
     __shared__ uint64_t bar;
-    if (is_done(S)) return;
-    const int t = blockIdx.x;
+    CGS_WORK_PROLOGUE();
+    const float2* p2 = V.p2 + w.voff;
+    float2* q2 = V.q2 + w.voff;
+    const int t = w.begin;
     if (threadIdx.x == 0) {
         mbar_init(&bar, 1);
         mbar_expect_tx(&bar, 2 * kTileSlotBytes);
-        bulk_copy_g2s(sh_hi, at_hi + (size_t)t * kOff * kTileElems, kTileSlotBytes, &bar);
-        bulk_copy_g2s(sh_lo, at_lo + (size_t)t * kOff * kTileElems, kTileSlotBytes, &bar);
+        bulk_copy_g2s(sh_hi, M.at_hi + (size_t)t * kOff * kTileElems, kTileSlotBytes, &bar);
+        bulk_copy_g2s(sh_lo, M.at_lo + (size_t)t * kOff * kTileElems, kTileSlotBytes, &bar);
     }
-    const int e0 = __ldg(&tile_ptr[t]), net = __ldg(&tile_ptr[t + 1]) - e0;
-    const int v0 = __ldg(&tile_vptr[t]), nvt = __ldg(&tile_vptr[t + 1]) - v0;
+    const int e0 = __ldg(&M.tile_ptr[t]), net = __ldg(&M.tile_ptr[t + 1]) - e0;
+    const int v0 = __ldg(&M.tile_vptr[t]), nvt = __ldg(&M.tile_vptr[t + 1]) - v0;
     for (int i = threadIdx.x; i < nvt; i += blockDim.x) {
-        ps[i] = __ldg(&p2[__ldg(&tile_verts[v0 + i]) & ~kSharedBit]);
+        ps[i] = __ldg(&p2[__ldg(&M.tile_verts[v0 + i]) & ~kSharedBit]);
         ys[i] = make_float2(0.0f, 0.0f);
     }
     __syncthreads();
-    const bool ok = wait_tile(&bar, S);
+    const bool ok = wait_tile(&bar, S, wait_limit);
     double energy = 0.0;
     if (ok && (int)threadIdx.x < net) {
         int L[8];
-        load_loc(eloc, e0 + threadIdx.x, L);
+        load_loc(M.eloc, e0 + threadIdx.x, L);
         float xh[8], xl[8], yh[8], yl[8];
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
@@ -340,7 +356,7 @@ __global__ void __launch_bounds__(kBlock) apply_pair_tiled_kernel(
     __syncthreads();
     if (ok) {
         for (int i = threadIdx.x; i < nvt; i += blockDim.x) {
-            const uint32_t raw = __ldg(&tile_verts[v0 + i]);
+            const uint32_t raw = __ldg(&M.tile_verts[v0 + i]);
             const int v = (int)(raw & ~kSharedBit);
             float h, l;
             fast_two_sum(ys[i].x, ys[i].y, h, l);
@@ -356,7 +372,7 @@ __global__ void __launch_bounds__(kBlock) apply_pair_tiled_kernel(
         }
     }
     double val[1] = {energy}, tot[1];
-    if (grid_sum<1>(val, partials, &S->ticket[0], tot) && threadIdx.x == 0) {
+    if (slot_sum<1>(val, V.partials + w.poff, w.idx, w.count, &S->ticket[0], tot) && threadIdx.x == 0) {
         const double pq = tot[0];
         S->pq = pq;
         if (S->status == CGS_ERR_TIMEOUT) {
@@ -371,33 +387,36 @@ __global__ void __launch_bounds__(kBlock) apply_pair_tiled_kernel(
 }
 
 // y += alpha A x in float32 (inner apply s -= A l of the hybrid step).
-__global__ void __launch_bounds__(kBlock) apply28f_tiled_kernel(
-    int64_t ntiles, const int32_t* __restrict__ tile_ptr, const int32_t* __restrict__ tile_vptr,
-    const uint32_t* __restrict__ tile_verts, const uint16_t* __restrict__ eloc, const float* __restrict__ at_hi,
-    const float* __restrict__ x, float* __restrict__ y, float alpha, SolveScalars* S) {
+__global__ void __launch_bounds__(kBlock) apply28f_tiled_kernel(const DevMesh* __restrict__ meshes,
+                                                                const Work* __restrict__ work, Vecs V,
+                                                                const float* __restrict__ xin,
+                                                                float* __restrict__ yout, float alpha,
+                                                                int wait_limit) {
     extern __shared__ __align__(128) unsigned char smem[];
     float* sh_a = reinterpret_cast<float*>(smem);
     float* xs = sh_a + kOff * kTileElems;
     float* ys = xs + kTileVerts;
     __shared__ uint64_t bar;
-    if (is_done(S)) return;
-    const int t = blockIdx.x;
+    CGS_WORK_PROLOGUE();
+    const float* x = xin + w.voff;
+    float* y = yout + w.voff;
+    const int t = w.begin;
     if (threadIdx.x == 0) {
         mbar_init(&bar, 1);
         mbar_expect_tx(&bar, kTileSlotBytes);
-        bulk_copy_g2s(sh_a, at_hi + (size_t)t * kOff * kTileElems, kTileSlotBytes, &bar);
+        bulk_copy_g2s(sh_a, M.at_hi + (size_t)t * kOff * kTileElems, kTileSlotBytes, &bar);
     }
-    const int e0 = __ldg(&tile_ptr[t]), net = __ldg(&tile_ptr[t + 1]) - e0;
-    const int v0 = __ldg(&tile_vptr[t]), nvt = __ldg(&tile_vptr[t + 1]) - v0;
+    const int e0 = __ldg(&M.tile_ptr[t]), net = __ldg(&M.tile_ptr[t + 1]) - e0;
+    const int v0 = __ldg(&M.tile_vptr[t]), nvt = __ldg(&M.tile_vptr[t + 1]) - v0;
     for (int i = threadIdx.x; i < nvt; i += blockDim.x) {
-        xs[i] = __ldg(&x[__ldg(&tile_verts[v0 + i]) & ~kSharedBit]);
+        xs[i] = __ldg(&x[__ldg(&M.tile_verts[v0 + i]) & ~kSharedBit]);
         ys[i] = 0.0f;
     }
     __syncthreads();
-    if (!wait_tile(&bar, S)) return;
+    if (!wait_tile(&bar, S, wait_limit)) return;
     if ((int)threadIdx.x < net) {
         int L[8];
-        load_loc(eloc, e0 + threadIdx.x, L);
+        load_loc(M.eloc, e0 + threadIdx.x, L);
         float xe[8], ye[8];
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
@@ -420,7 +439,7 @@ __global__ void __launch_bounds__(kBlock) apply28f_tiled_kernel(
     }
     __syncthreads();
     for (int i = threadIdx.x; i < nvt; i += blockDim.x) {
-        const uint32_t raw = __ldg(&tile_verts[v0 + i]);
+        const uint32_t raw = __ldg(&M.tile_verts[v0 + i]);
         const int v = (int)(raw & ~kSharedBit);
         if (!(raw & kSharedBit))
             y[v] += alpha * ys[i];
@@ -463,30 +482,46 @@ __device__ __forceinline__ T diag_entry(const Stor* inv, size_t io, int m, int i
     return stage<T, Stor>(inv, io + (size_t)(m - d) * m + j, sc);
 }
 
+template <typename Stor>
+__device__ __forceinline__ const Stor* inverse_store(const DevMesh& M);
+template <>
+__device__ __forceinline__ const double* inverse_store<double>(const DevMesh& M) { return M.inv64; }
+template <>
+__device__ __forceinline__ const float* inverse_store<float>(const DevMesh& M) { return M.inv32; }
+template <>
+__device__ __forceinline__ const __half* inverse_store<__half>(const DevMesh& M) { return M.inv16; }
+
+template <typename T>
+__device__ __forceinline__ const T* overlap_weights(const DevMesh& M);
+template <>
+__device__ __forceinline__ const double* overlap_weights<double>(const DevMesh& M) { return M.wov64; }
+template <>
+__device__ __forceinline__ const float* overlap_weights<float>(const DevMesh& M) { return M.wov32; }
+
 template <typename T, typename Stor>
-__global__ void __launch_bounds__(kBlock) local_warp_kernel(int64_t n_sub, const int32_t* __restrict__ sub_ptr,
-                                                            const int32_t* __restrict__ sub_idx,
-                                                            const int64_t* __restrict__ inv_ptr,
-                                                            const Stor* __restrict__ inv,
-                                                            const float* __restrict__ scale,
-                                                            const T* __restrict__ r,
-                                                            const T* __restrict__ wov, T* __restrict__ out,
-                                                            const SolveScalars* S) {
-    if (is_done(S)) return;
+__global__ void __launch_bounds__(kBlock) local_warp_kernel(const DevMesh* __restrict__ meshes,
+                                                            const Work* __restrict__ work, Vecs V,
+                                                            const T* __restrict__ rin, T* __restrict__ outv,
+                                                            int weighted) {
+    CGS_WORK_PROLOGUE();
+    const T* r = rin + w.voff;
+    T* out = outv + w.voff;
+    const Stor* inv = inverse_store<Stor>(M);
+    const float* scale = M.inv16_scale;
+    const T* wov = weighted ? overlap_weights<T>(M) : nullptr;
     const int lane = threadIdx.x & 31;
-    const int64_t nwt = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; p < n_sub; p += nwt) {
-        const int o = __ldg(&sub_ptr[p]);
-        const int m = __ldg(&sub_ptr[p + 1]) - o;
+    for (int p = w.begin + (int)(threadIdx.x >> 5); p < w.end; p += kBlock / 32) {
+        const int o = __ldg(&M.sub_ptr[p]);
+        const int m = __ldg(&M.sub_ptr[p + 1]) - o;
         if (m == 0 || m > 64) continue;
-        const size_t io = (size_t)__ldg(&inv_ptr[p]);
+        const size_t io = (size_t)__ldg(&M.inv_ptr[p]);
         const float sc = scale ? __ldg(&scale[p]) : 1.0f;
         const int nd = m / 2 + 1;
         if (m <= 32) {
             // every load of this lane is issued before the first FMA: the
             // entries inv(i, i+d) and inv(i-d, i) for d < nd <= 17
             const bool h = lane < m;
-            const int v = h ? __ldg(&sub_idx[o + lane]) : 0;
+            const int v = h ? __ldg(&M.sub_idx[o + lane]) : 0;
             T ap[17], am[17];
 #pragma unroll
             for (int d = 0; d < 17; ++d) {
@@ -513,8 +548,8 @@ __global__ void __launch_bounds__(kBlock) local_warp_kernel(int64_t n_sub, const
         } else {
             // 33..64 dofs: lane holds rows lane and lane + 32
             const bool h1 = lane + 32 < m;
-            const int v0 = __ldg(&sub_idx[o + lane]);
-            const int v1 = h1 ? __ldg(&sub_idx[o + lane + 32]) : 0;
+            const int v0 = __ldg(&M.sub_idx[o + lane]);
+            const int v1 = h1 ? __ldg(&M.sub_idx[o + lane + 32]) : 0;
             const T x0 = __ldg(&r[v0]);
             const T x1 = h1 ? __ldg(&r[v1]) : T(0);
             T y0 = stage<T, Stor>(inv, io + lane, sc) * x0;
@@ -546,27 +581,28 @@ __global__ void __launch_bounds__(kBlock) local_warp_kernel(int64_t n_sub, const
     }
 }
 
-// Subdomains with more than 64 dofs: one block each, rows spread over threads.
+// Subdomains with more than 64 dofs: the whole block on one subdomain, rows
+// spread over threads.
 template <typename T, typename Stor>
-__global__ void __launch_bounds__(kBlock) local_block_kernel(int64_t n_sub, const int32_t* __restrict__ sub_ptr,
-                                                             const int32_t* __restrict__ sub_idx,
-                                                             const int64_t* __restrict__ inv_ptr,
-                                                             const Stor* __restrict__ inv,
-                                                             const float* __restrict__ scale,
-                                                             const T* __restrict__ r,
-                                                             const T* __restrict__ wov, T* __restrict__ out,
-                                                             const SolveScalars* S) {
-    if (is_done(S)) return;
-    for (int64_t p = blockIdx.x; p < n_sub; p += gridDim.x) {
-        const int o = sub_ptr[p];
-        const int m = sub_ptr[p + 1] - o;
+__global__ void __launch_bounds__(kBlock) local_block_kernel(const DevMesh* __restrict__ meshes,
+                                                             const Work* __restrict__ work, Vecs V,
+                                                             const T* __restrict__ rin, T* __restrict__ outv,
+                                                             int weighted) {
+    CGS_WORK_PROLOGUE();
+    const T* r = rin + w.voff;
+    T* out = outv + w.voff;
+    const Stor* inv = inverse_store<Stor>(M);
+    const T* wov = weighted ? overlap_weights<T>(M) : nullptr;
+    for (int p = w.begin; p < w.end; ++p) {
+        const int o = M.sub_ptr[p];
+        const int m = M.sub_ptr[p + 1] - o;
         if (m <= 64) continue;
-        const size_t io = (size_t)inv_ptr[p];
-        const float sc = scale ? scale[p] : 1.0f;
+        const size_t io = (size_t)M.inv_ptr[p];
+        const float sc = M.inv16_scale ? M.inv16_scale[p] : 1.0f;
         for (int i = threadIdx.x; i < m; i += blockDim.x) {
             T y = 0;
-            for (int j = 0; j < m; ++j) y += diag_entry<T, Stor>(inv, io, m, i, j, sc) * __ldg(&r[sub_idx[o + j]]);
-            const int v = sub_idx[o + i];
+            for (int j = 0; j < m; ++j) y += diag_entry<T, Stor>(inv, io, m, i, j, sc) * __ldg(&r[M.sub_idx[o + j]]);
+            const int v = M.sub_idx[o + i];
             atomicAdd(&out[v], wov ? y * wov[v] : y);
         }
     }
@@ -574,10 +610,11 @@ __global__ void __launch_bounds__(kBlock) local_block_kernel(int64_t n_sub, cons
 
 // ---------------------------------------------------------------------------
 // Box coarse space.  Element e (device order) lies in cell c(e) with lower
-// corner lo + (ci,cj,ck) H; its vertex x has local cell coordinates
-// t = (x - corner) / H (outside [0,1] = extrapolation) and corner m = (ma,
-// mb, mc) has weight prod_d (t_d if m_d else 1 - t_d).  Vertex data holds the
-// coordinates and 1/count, so W = diag(1/count) comes with the same load.
+// corner (ci,cj,ck) H (coordinates are stored relative to the box origin);
+// its vertex x has local cell coordinates t = (x - corner) / H (outside
+// [0,1] = extrapolation) and corner m = (ma, mb, mc) has weight
+// prod_d (t_d if m_d else 1 - t_d).  Vertex records hold the coordinates and
+// 1/count, so W = diag(1/count) comes with the same load.
 // ---------------------------------------------------------------------------
 template <typename T>
 struct VertexXYZW;
@@ -597,11 +634,16 @@ struct VertexXYZW<float> {
         x = a.x; y = a.y; z = a.z; w = a.w;
     }
 };
+__device__ __forceinline__ VertexXYZW<double> vertex_data(const DevMesh& M, double) { return {M.xyzw}; }
+__device__ __forceinline__ VertexXYZW<float> vertex_data(const DevMesh& M, float) { return {M.xyzwf}; }
 
 template <typename T>
 struct BoxGrid {
     int bx, by;
-    T lox, loy, loz, hx, hy, hz, ihx, ihy, ihz;
+    T hx, hy, hz, ihx, ihy, ihz;
+    __device__ __forceinline__ explicit BoxGrid(const DevMesh& M)
+        : bx(M.b[0]), by(M.b[1]), hx((T)M.H[0]), hy((T)M.H[1]), hz((T)M.H[2]), ihx((T)M.iH[0]),
+          ihy((T)M.iH[1]), ihz((T)M.iH[2]) {}
 };
 
 template <typename T>
@@ -613,15 +655,15 @@ __device__ __forceinline__ void corner_weights(T tx, T ty, T tz, T (&w)[8]) {
 
 // Warp sum of per-element cell contributions in float64 accuracy.  The FP64
 // form adds doubles; the float form adds float pairs (hi, lo) with exact
-// two-sums, so no FP64 instruction runs per lane (B300 issues FP64 ~60x
-// slower than FP32) and the result still carries ~48 significant bits.
+// two-sums, so no FP64 instruction runs per lane and the result still
+// carries ~48 significant bits.
 struct CellSum64 {
     double v;
     __device__ __forceinline__ double value() const { return v; }
 };
 struct CellSum32 {
     float h, l;
-    __device__ __forceinline__ double value() const { return (double)h + (double)l; }  // leader lane only
+    __device__ __forceinline__ double value() const { return (double)h + (double)l; }
 };
 __device__ __forceinline__ CellSum64 cell_sum(double v) { return {warp_sum(v)}; }
 __device__ __forceinline__ CellSum32 cell_sum(float v) {
@@ -639,38 +681,39 @@ __device__ __forceinline__ CellSum32 cell_sum(float v) {
 }
 
 template <typename T, typename Tin>
-__global__ void __launch_bounds__(kBlock) restrict_kernel(int64_t ne, const int32_t* __restrict__ conn,
-                                                          const int32_t* __restrict__ cell,
-                                                          const int32_t* __restrict__ cell_cols,
-                                                          VertexXYZW<T> vx, BoxGrid<T> g,
-                                                          const Tin* __restrict__ s, double* __restrict__ rr,
-                                                          const SolveScalars* S) {
-    if (is_done(S)) return;
-    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool valid = e < ne;
+__global__ void __launch_bounds__(kBlock) restrict_kernel(const DevMesh* __restrict__ meshes,
+                                                          const Work* __restrict__ work, Vecs V,
+                                                          const Tin* __restrict__ sin, double* __restrict__ rrv) {
+    CGS_WORK_PROLOGUE();
+    const Tin* s = sin + w.voff;
+    double* rr = rrv + w.roff;
+    const BoxGrid<T> g(M);
+    const auto vx = vertex_data(M, T(0));
+    const int64_t e = (int64_t)w.begin + threadIdx.x;
+    const bool valid = e < w.end;
     T acc[8];
 #pragma unroll
     for (int m = 0; m < 8; ++m) acc[m] = T(0);
     int c = -1;
     if (valid) {
-        c = __ldg(&cell[e]);
+        c = __ldg(&M.cell[e]);
         const int ci = c % g.bx, cj = (c / g.bx) % g.by, ck = c / (g.bx * g.by);
-        const T cx = g.lox + ci * g.hx, cy = g.loy + cj * g.hy, cz = g.loz + ck * g.hz;
+        const T cx = ci * g.hx, cy = cj * g.hy, cz = ck * g.hz;
         int v[8];
-        load_conn(conn, e, v);
+        load_conn(M.conn, e, v);
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
             if (v[k] < 0) continue;
             T x, y, z, ic;
             vx.load(v[k], x, y, z, ic);
             const T sv = (T)__ldg(&s[v[k]]) * ic;
-            T w[8];
-            corner_weights<T>((x - cx) * g.ihx, (y - cy) * g.ihy, (z - cz) * g.ihz, w);
+            T wt[8];
+            corner_weights<T>((x - cx) * g.ihx, (y - cy) * g.ihy, (z - cz) * g.ihz, wt);
 #pragma unroll
-            for (int m = 0; m < 8; ++m) acc[m] += w[m] * sv;
+            for (int m = 0; m < 8; ++m) acc[m] += wt[m] * sv;
         }
     }
-    // segmented warp reduction over lanes sharing a cell, float64 sums
+    // segmented warp reduction over lanes sharing a cell
     const int lane = threadIdx.x & 31;
     unsigned int todo = __ballot_sync(0xffffffffu, valid);
     while (todo) {
@@ -678,8 +721,8 @@ __global__ void __launch_bounds__(kBlock) restrict_kernel(int64_t ne, const int3
         const int cc = __shfl_sync(0xffffffffu, c, leader);
         const bool mine = valid && c == cc;
         todo &= ~__ballot_sync(0xffffffffu, mine);
-        // corner m's total ends up in lane m (one FP64 conversion and one
-        // atomic per corner, issued as a single warp instruction)
+        // corner m's total ends up in lane m: one FP64 conversion and one
+        // atomic per corner, issued as a single warp instruction
         auto mine_sum = cell_sum(mine ? acc[0] : T(0));
 #pragma unroll
         for (int m = 1; m < 8; ++m) {
@@ -687,71 +730,73 @@ __global__ void __launch_bounds__(kBlock) restrict_kernel(int64_t ne, const int3
             if (lane == m) mine_sum = sum;
         }
         if (lane < 8) {
-            const int col = __ldg(&cell_cols[(size_t)cc * 8 + lane]);
+            const int col = __ldg(&M.cell_cols[(size_t)cc * 8 + lane]);
             if (col >= 0) atomicAdd(&rr[col], mine_sum.value());
         }
     }
 }
 
 template <typename T, typename Tu>
-__global__ void __launch_bounds__(kBlock) interp_add_kernel(int64_t ne, const int32_t* __restrict__ conn,
-                                                            const int32_t* __restrict__ cell,
-                                                            const int32_t* __restrict__ cell_cols,
-                                                            VertexXYZW<T> vx, BoxGrid<T> g,
-                                                            const Tu* __restrict__ ur, T* __restrict__ z,
-                                                            const SolveScalars* S) {
-    if (is_done(S)) return;
-    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= ne) return;
-    const int c = __ldg(&cell[e]);
+__global__ void __launch_bounds__(kBlock) interp_add_kernel(const DevMesh* __restrict__ meshes,
+                                                            const Work* __restrict__ work, Vecs V,
+                                                            const Tu* __restrict__ urv, T* __restrict__ zv) {
+    CGS_WORK_PROLOGUE();
+    const Tu* ur = urv + w.roff;
+    T* z = zv + w.voff;
+    const int64_t e = (int64_t)w.begin + threadIdx.x;
+    if (e >= w.end) return;
+    const BoxGrid<T> g(M);
+    const auto vx = vertex_data(M, T(0));
+    const int c = __ldg(&M.cell[e]);
     const int ci = c % g.bx, cj = (c / g.bx) % g.by, ck = c / (g.bx * g.by);
-    const T cx = g.lox + ci * g.hx, cy = g.loy + cj * g.hy, cz = g.loz + ck * g.hz;
+    const T cx = ci * g.hx, cy = cj * g.hy, cz = ck * g.hz;
     T u[8];
 #pragma unroll
     for (int m = 0; m < 8; ++m) {
-        const int col = __ldg(&cell_cols[(size_t)c * 8 + m]);
+        const int col = __ldg(&M.cell_cols[(size_t)c * 8 + m]);
         u[m] = col >= 0 ? (T)__ldg(&ur[col]) : T(0);
     }
     int v[8];
-    load_conn(conn, e, v);
+    load_conn(M.conn, e, v);
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
         if (v[k] < 0) continue;
         T x, y, zz, ic;
         vx.load(v[k], x, y, zz, ic);
-        T w[8];
-        corner_weights<T>((x - cx) * g.ihx, (y - cy) * g.ihy, (zz - cz) * g.ihz, w);
+        T wt[8];
+        corner_weights<T>((x - cx) * g.ihx, (y - cy) * g.ihy, (zz - cz) * g.ihz, wt);
         T val = T(0);
 #pragma unroll
-        for (int m = 0; m < 8; ++m) val += w[m] * u[m];
+        for (int m = 0; m < 8; ++m) val += wt[m] * u[m];
         atomicAdd(&z[v[k]], val * ic);
     }
 }
 
-// u_r = A_r^{-1} r_r: one warp per row of the full symmetric inverse.
-__global__ void __launch_bounds__(kBlock) coarse_gemv_kernel(int64_t nr, const double* __restrict__ Ainv,
-                                                             const double* __restrict__ rr,
-                                                             double* __restrict__ ur, float* __restrict__ ur32,
-                                                             const SolveScalars* S) {
-    if (is_done(S)) return;
+// u_r = A_r^{-1} r_r: one warp per row of the full symmetric inverse; also a
+// float copy of u_r for the float interpolation (no conversions per element).
+__global__ void __launch_bounds__(kBlock) coarse_gemv_kernel(const DevMesh* __restrict__ meshes,
+                                                             const Work* __restrict__ work, Vecs V,
+                                                             const double* __restrict__ rrv,
+                                                             double* __restrict__ urv, float* __restrict__ ur32v) {
+    CGS_WORK_PROLOGUE();
+    const int64_t nr = M.nr;
+    const double* rr = rrv + w.roff;
     const int lane = threadIdx.x & 31;
-    const int64_t nwt = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < nr; i += nwt) {
-        const double* row = Ainv + (size_t)i * nr;
-        double s = 0.0;
-        for (int64_t j = lane; j < nr; j += 32) s = fma(__ldg(&row[j]), __ldg(&rr[j]), s);
-        s = warp_sum(s);
-        if (lane == 0) {
-            ur[i] = s;
-            if (ur32) ur32[i] = (float)s;
-        }
+    const int64_t i = (int64_t)w.begin + (threadIdx.x >> 5);
+    if (i >= w.end) return;
+    const double* row = M.ar_inv + (size_t)i * nr;
+    double s = 0.0;
+    for (int64_t j = lane; j < nr; j += 32) s = fma(__ldg(&row[j]), __ldg(&rr[j]), s);
+    s = warp_sum(s);
+    if (lane == 0) {
+        urv[w.roff + i] = s;
+        if (ur32v) ur32v[w.roff + i] = (float)s;
     }
 }
 
 // ---------------------------------------------------------------------------
-// PCG vector kernels (float64 outer iteration)
+// PCG vector kernels (float64 outer iteration), over vertex ranges.
 // ---------------------------------------------------------------------------
-
 // q is double (FP64 form) or a float pair (mixed forms, written by apply_pair).
 __device__ __forceinline__ double qval(const double* q, int64_t i) { return q[i]; }
 __device__ __forceinline__ double qval(const float2* q, int64_t i) {
@@ -766,28 +811,36 @@ __device__ __forceinline__ float2 split_pair(double x) {
     return make_float2(h, __double2float_rn(x - (double)h));
 }
 
+#define CGS_VERT_LOOP(i) for (int64_t i = (int64_t)w.begin + threadIdx.x; i < w.end; i += blockDim.x)
+
 // r = b with Dirichlet entries zeroed, x = 0, q = 0; ||b||^2 -> bnorm2, tol2.
 template <typename Tq>
-__global__ void __launch_bounds__(kBlock) pcg_init_kernel(int64_t nv, const double* __restrict__ b,
-                                                          const uint8_t* __restrict__ dir, double* __restrict__ x,
-                                                          double* __restrict__ r, Tq* __restrict__ q,
-                                                          double rtol, int maxit, double* partials,
-                                                          SolveScalars* S) {
+__global__ void __launch_bounds__(kBlock) pcg_init_kernel(const DevMesh* __restrict__ meshes,
+                                                          const Work* __restrict__ work, Vecs V, Tq* qv,
+                                                          double rtol, int maxit) {
+    const Work w = work[blockIdx.x];
+    SolveScalars* S = V.S + w.slot;
+    const DevMesh& M = meshes[w.mesh];
+    const double* b = V.bptr ? V.bptr[w.slot] : V.b + w.voff;
+    double* x = V.x + w.voff;
+    double* r = V.r + w.voff;
+    Tq* q = qv + w.voff;
     double acc = 0.0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += (int64_t)gridDim.x * blockDim.x) {
-        const double bi = dir[i] ? 0.0 : b[i];
+    CGS_VERT_LOOP(i) {
+        const double bi = M.dir[i] ? 0.0 : b[i];
         r[i] = bi;
         x[i] = 0.0;
         qzero(q, i);
         acc = fma(bi, bi, acc);
     }
     double val[1] = {acc}, tot[1];
-    if (grid_sum<1>(val, partials, &S->ticket[1], tot) && threadIdx.x == 0) {
+    if (slot_sum<1>(val, V.partials + w.poff, w.idx, w.count, &S->ticket[1], tot) && threadIdx.x == 0) {
         S->bnorm2 = tot[0];
         S->tol2 = rtol * rtol * tot[0];
         S->iters = 0;
         S->maxit = maxit;
         S->loops = 0;
+        S->timeouts = 0;
         S->status = CGS_OK;
         S->done = (tot[0] == 0.0 || maxit <= 0) ? 1 : 0;
         if (maxit <= 0 && tot[0] != 0.0) S->status = CGS_ERR_NO_CONVERGENCE;
@@ -795,22 +848,43 @@ __global__ void __launch_bounds__(kBlock) pcg_init_kernel(int64_t nv, const doub
     }
 }
 
+// z = 0, s = r in the bulk precision, r_r = 0 (before a preconditioner apply).
+template <typename Tz>
+__global__ void __launch_bounds__(kBlock) precond_prep_kernel(const DevMesh* __restrict__ meshes,
+                                                              const Work* __restrict__ work, Vecs V,
+                                                              const double* __restrict__ rin) {
+    CGS_WORK_PROLOGUE();
+    const double* r = rin + w.voff;
+    Tz* z = static_cast<Tz*>(V.z) + w.voff;
+    Tz* s = static_cast<Tz*>(V.s) + w.voff;
+    CGS_VERT_LOOP(i) {
+        z[i] = Tz(0);
+        s[i] = (Tz)r[i];
+    }
+    // this block's share of r_r
+    const int64_t chunk = (M.nr + w.count - 1) / w.count;
+    const int64_t r0 = (int64_t)w.idx * chunk, r1 = min((int64_t)M.nr, r0 + chunk);
+    for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) V.rr[w.roff + i] = 0.0;
+}
+
 // p = z (and its float pair p2 when the mixed operator needs it), rho = r.z.
 template <typename Tz>
-__global__ void __launch_bounds__(kBlock) pcg_first_dir_kernel(int64_t nv, const Tz* __restrict__ z,
-                                                               const double* __restrict__ r, double* __restrict__ p,
-                                                               float2* __restrict__ p2, double* partials,
-                                                               SolveScalars* S) {
-    if (is_done(S)) return;
+__global__ void __launch_bounds__(kBlock) pcg_first_dir_kernel(const DevMesh* __restrict__ meshes,
+                                                               const Work* __restrict__ work, Vecs V) {
+    CGS_WORK_PROLOGUE();
+    const Tz* z = static_cast<const Tz*>(V.z) + w.voff;
+    const double* r = V.r + w.voff;
+    double* p = V.p + w.voff;
+    float2* p2 = V.p2 ? V.p2 + w.voff : nullptr;
     double acc = 0.0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += (int64_t)gridDim.x * blockDim.x) {
+    CGS_VERT_LOOP(i) {
         const double zi = (double)z[i];
         p[i] = zi;
         if (p2) p2[i] = split_pair(zi);
         acc = fma(zi, r[i], acc);
     }
     double val[1] = {acc}, tot[1];
-    if (grid_sum<1>(val, partials, &S->ticket[1], tot) && threadIdx.x == 0) {
+    if (slot_sum<1>(val, V.partials + w.poff, w.idx, w.count, &S->ticket[1], tot) && threadIdx.x == 0) {
         S->rho = tot[0];
         if (!(tot[0] > 0.0) || !isfinite(tot[0])) {
             S->status = CGS_ERR_BREAKDOWN;
@@ -820,19 +894,22 @@ __global__ void __launch_bounds__(kBlock) pcg_first_dir_kernel(int64_t nv, const
 }
 
 // x += alpha p, r -= alpha q, ||r||^2; prepare the preconditioner buffers
-// (zero z, s = r in the bulk precision, zero r_r).  Last block: iteration
-// count and the stopping test.
+// (zero z, s = r in the bulk precision, zero r_r).  The slot's last block
+// counts the iteration and applies the stopping test.
 template <typename Tz, typename Tq>
-__global__ void __launch_bounds__(kBlock) pcg_update_xr_kernel(int64_t nv, double* __restrict__ x,
-                                                               double* __restrict__ r, const double* __restrict__ p,
-                                                               const Tq* __restrict__ q, Tz* __restrict__ z,
-                                                               Tz* __restrict__ s, double* __restrict__ rr_vec,
-                                                               int64_t nr, double* partials, SolveScalars* S) {
-    if (is_done(S)) return;
+__global__ void __launch_bounds__(kBlock) pcg_update_xr_kernel(const DevMesh* __restrict__ meshes,
+                                                               const Work* __restrict__ work, Vecs V,
+                                                               const Tq* __restrict__ qv) {
+    CGS_WORK_PROLOGUE();
+    double* x = V.x + w.voff;
+    double* r = V.r + w.voff;
+    const double* p = V.p + w.voff;
+    const Tq* q = qv + w.voff;
+    Tz* z = static_cast<Tz*>(V.z) + w.voff;
+    Tz* s = static_cast<Tz*>(V.s) + w.voff;
     const double alpha = S->alpha;
     double acc = 0.0;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += stride) {
+    CGS_VERT_LOOP(i) {
         x[i] = fma(alpha, p[i], x[i]);
         const double ri = fma(-alpha, qval(q, i), r[i]);
         r[i] = ri;
@@ -840,9 +917,11 @@ __global__ void __launch_bounds__(kBlock) pcg_update_xr_kernel(int64_t nv, doubl
         z[i] = Tz(0);
         s[i] = (Tz)ri;
     }
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nr; i += stride) rr_vec[i] = 0.0;
+    const int64_t chunk = (M.nr + w.count - 1) / w.count;
+    const int64_t r0 = (int64_t)w.idx * chunk, r1 = min((int64_t)M.nr, r0 + chunk);
+    for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) V.rr[w.roff + i] = 0.0;
     double val[1] = {acc}, tot[1];
-    if (grid_sum<1>(val, partials, &S->ticket[2], tot) && threadIdx.x == 0) {
+    if (slot_sum<1>(val, V.partials + w.poff, w.idx, w.count, &S->ticket[2], tot) && threadIdx.x == 0) {
         S->rr = tot[0];
         const int it = S->iters + 1;
         S->iters = it;
@@ -862,18 +941,21 @@ __global__ void __launch_bounds__(kBlock) pcg_update_xr_kernel(int64_t nv, doubl
 // z.r and z.q; beta = -alpha (z.q) / rho (Polak-Ribiere, since
 // r_new - r_old = -alpha q), rho = z.r.
 template <typename Tz, typename Tq>
-__global__ void __launch_bounds__(kBlock) pcg_dots_kernel(int64_t nv, const Tz* __restrict__ z,
-                                                          const double* __restrict__ r, const Tq* __restrict__ q,
-                                                          double* partials, SolveScalars* S) {
-    if (is_done(S)) return;
+__global__ void __launch_bounds__(kBlock) pcg_dots_kernel(const DevMesh* __restrict__ meshes,
+                                                          const Work* __restrict__ work, Vecs V,
+                                                          const Tq* __restrict__ qv) {
+    CGS_WORK_PROLOGUE();
+    const Tz* z = static_cast<const Tz*>(V.z) + w.voff;
+    const double* r = V.r + w.voff;
+    const Tq* q = qv + w.voff;
     double zr = 0.0, zq = 0.0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += (int64_t)gridDim.x * blockDim.x) {
+    CGS_VERT_LOOP(i) {
         const double zi = (double)z[i];
         zr = fma(zi, r[i], zr);
         zq = fma(zi, qval(q, i), zq);
     }
     double val[2] = {zr, zq}, tot[2];
-    if (grid_sum<2>(val, partials, &S->ticket[3], tot) && threadIdx.x == 0) {
+    if (slot_sum<2>(val, V.partials + w.poff, w.idx, w.count, &S->ticket[3], tot) && threadIdx.x == 0) {
         S->zr = tot[0];
         S->zq = tot[1];
         const double beta = -S->alpha * tot[1] / S->rho;
@@ -886,22 +968,17 @@ __global__ void __launch_bounds__(kBlock) pcg_dots_kernel(int64_t nv, const Tz* 
     }
 }
 
-// p = z + beta p (and p2), q = 0 for the next product.  Block 0 also sets
-// the condition of the device-side loop when the iteration runs inside a
-// graph's while node: continue while not done and fewer than maxit loops.
+// p = z + beta p (and p2), q = 0 for the next product.
 template <typename Tz, typename Tq>
-__global__ void __launch_bounds__(kBlock) pcg_update_p_kernel(int64_t nv, const Tz* __restrict__ z,
-                                                              double* __restrict__ p, float2* __restrict__ p2,
-                                                              Tq* __restrict__ q, SolveScalars* S,
-                                                              cudaGraphConditionalHandle cond, int use_cond) {
-    if (use_cond && blockIdx.x == 0 && threadIdx.x == 0) {
-        const int loops = ++S->loops;
-        const bool go = !*(volatile int*)&S->done && loops < S->maxit + 2;
-        cudaGraphSetConditional(cond, go ? 1u : 0u);
-    }
-    if (is_done(S)) return;
+__global__ void __launch_bounds__(kBlock) pcg_update_p_kernel(const DevMesh* __restrict__ meshes,
+                                                              const Work* __restrict__ work, Vecs V, Tq* qv) {
+    CGS_WORK_PROLOGUE();
+    const Tz* z = static_cast<const Tz*>(V.z) + w.voff;
+    double* p = V.p + w.voff;
+    float2* p2 = V.p2 ? V.p2 + w.voff : nullptr;
+    Tq* q = qv + w.voff;
     const double beta = S->beta;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += (int64_t)gridDim.x * blockDim.x) {
+    CGS_VERT_LOOP(i) {
         const double pi = fma(beta, p[i], (double)z[i]);
         p[i] = pi;
         if (p2) p2[i] = split_pair(pi);
@@ -909,30 +986,53 @@ __global__ void __launch_bounds__(kBlock) pcg_update_p_kernel(int64_t nv, const 
     }
 }
 
-// ||b - y||^2 and ||b||^2 over free entries (true residual at the end).
-__global__ void __launch_bounds__(kBlock) resid_norm_kernel(int64_t nv, const double* __restrict__ b,
-                                                            const double* __restrict__ y,
-                                                            const uint8_t* __restrict__ dir, double* partials,
-                                                            unsigned int* ticket, double* out2) {
+// Condition of the device-side loop (graph while node): continue while some
+// slot is still running and fewer than maxit + 2 bodies have run (slot 0
+// counts the bodies; all slots share maxit).
+__global__ void __launch_bounds__(kBlock) loop_cond_kernel(SolveScalars* __restrict__ S, int nslots,
+                                                           cudaGraphConditionalHandle cond) {
+    int running = 0;
+    for (int i = threadIdx.x; i < nslots; i += blockDim.x) running |= !*(volatile const int*)&S[i].done;
+    running = __syncthreads_or(running);
+    if (threadIdx.x == 0) {
+        const int loops = ++S[0].loops;
+        cudaGraphSetConditional(cond, (running && loops < S[0].maxit + 2) ? 1u : 0u);
+    }
+}
+
+// x_out = x (copy-out), then ||b - y||^2 and ||b||^2 over free entries.
+__global__ void __launch_bounds__(kBlock) resid_norm_kernel(const DevMesh* __restrict__ meshes,
+                                                            const Work* __restrict__ work, Vecs V) {
+    const Work w = work[blockIdx.x];
+    SolveScalars* S = V.S + w.slot;
+    const DevMesh& M = meshes[w.mesh];
+    const double* b = V.bptr ? V.bptr[w.slot] : V.b + w.voff;
+    double* xo = V.xptr ? V.xptr[w.slot] : nullptr;
+    const double* x = V.x + w.voff;
+    const double* y = V.y + w.voff;
     double rn = 0.0, bn = 0.0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += (int64_t)gridDim.x * blockDim.x) {
-        if (dir[i]) continue;
+    CGS_VERT_LOOP(i) {
+        if (xo) xo[i] = x[i];
+        if (M.dir[i]) continue;
         const double d = b[i] - y[i];
         rn = fma(d, d, rn);
         bn = fma(b[i], b[i], bn);
     }
     double val[2] = {rn, bn}, tot[2];
-    if (grid_sum<2>(val, partials, ticket, tot) && threadIdx.x == 0) {
-        out2[0] = tot[0];
-        out2[1] = tot[1];
+    if (slot_sum<2>(val, V.partials + w.poff, w.idx, w.count, &S->ticket[1], tot) && threadIdx.x == 0) {
+        S->res2 = tot[0];
+        S->b2 = tot[1];
     }
 }
 
+// dst = src (optionally zero at Dirichlet vertices) over the slot's vertices.
 template <typename Ta, typename Tb>
-__global__ void __launch_bounds__(kBlock) convert_kernel(int64_t n, const Ta* __restrict__ a, Tb* __restrict__ b,
-                                                         const uint8_t* __restrict__ dir) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        b[i] = (dir && dir[i]) ? Tb(0) : (Tb)a[i];
+__global__ void __launch_bounds__(kBlock) convert_kernel(const DevMesh* __restrict__ meshes,
+                                                         const Work* __restrict__ work, const Ta* __restrict__ a,
+                                                         Tb* __restrict__ b, int mask_dirichlet) {
+    const Work w = work[blockIdx.x];
+    const DevMesh& M = meshes[w.mesh];
+    CGS_VERT_LOOP(i) b[w.voff + i] = (mask_dirichlet && M.dir[i]) ? Tb(0) : (Tb)a[w.voff + i];
 }
 
 template <typename T>
@@ -941,200 +1041,215 @@ __global__ void __launch_bounds__(kBlock) fill_kernel(int64_t n, T* __restrict__
         a[i] = v;
 }
 
-inline unsigned int grid_for(int64_t n, unsigned int cap = 148 * 8) {
-    const int64_t b = (n + kBlock - 1) / kBlock;
-    return (unsigned int)std::max<int64_t>(1, std::min<int64_t>(b, cap));
-}
-inline unsigned int grid_exact(int64_t n) { return (unsigned int)std::max<int64_t>(1, (n + kBlock - 1) / kBlock); }
-
-template <typename T>
-BoxGrid<T> box_grid(const DevMesh& m) {
-    BoxGrid<T> g;
-    g.bx = m.b[0];
-    g.by = m.b[1];
-    g.lox = (T)m.lo[0]; g.loy = (T)m.lo[1]; g.loz = (T)m.lo[2];
-    g.hx = (T)m.H[0]; g.hy = (T)m.H[1]; g.hz = (T)m.H[2];
-    g.ihx = (T)(1.0 / m.H[0]); g.ihy = (T)(1.0 / m.H[1]); g.ihz = (T)(1.0 / m.H[2]);
-    return g;
-}
-
 }  // namespace
 
 // ---------------------------------------------------------------------------
-// Launchers
+// Launchers.  A Plan names the mesh descriptors and the work tables of one
+// set of slots (one mesh with one right-hand side, or a batch).
 // ---------------------------------------------------------------------------
 
-unsigned int partial_slots(const DevMesh& m) {
-    const unsigned int a = std::max(grid_exact(m.ne), grid_for(m.nv));
-    return std::max(a, (unsigned int)std::max<int64_t>(m.ntiles, 1));
-}
-
-void launch_apply64(const DevMesh& m, const double* x, double* y, double alpha, double* partials,
-                    SolveScalars* S, bool dot, cudaStream_t st) {
+void launch_apply64(const Plan& P, const Vecs& V, const double* x, double* y, double alpha, bool dot,
+                    cudaStream_t st) {
+    if (!P.nwork[kWorkElem]) return;
     if (dot)
-        apply64_kernel<true><<<grid_exact(m.ne), kBlock, 0, st>>>(m.ne, m.conn, m.a36, x, y, alpha, partials, S);
+        apply64_kernel<true><<<P.nwork[kWorkElem], kBlock, 0, st>>>(P.meshes, P.work[kWorkElem], V, x, y, alpha);
     else
-        apply64_kernel<false><<<grid_exact(m.ne), kBlock, 0, st>>>(m.ne, m.conn, m.a36, x, y, alpha, partials, S);
+        apply64_kernel<false><<<P.nwork[kWorkElem], kBlock, 0, st>>>(P.meshes, P.work[kWorkElem], V, x, y, alpha);
 }
 
-template <typename T, typename Stor>
-static void local_launch(const DevMesh& m, const Stor* inv, const float* scale, const T* r, const T* wov, T* out,
-                         const SolveScalars* S, cudaStream_t st) {
-    if (m.n_sub == 0) return;
-    const unsigned int blocks =
-        (unsigned int)std::max<int64_t>(1, std::min<int64_t>((m.n_sub + 7) / 8, 148 * 16));
-    local_warp_kernel<T, Stor><<<blocks, kBlock, 0, st>>>(m.n_sub, m.sub_ptr, m.sub_idx, m.inv_ptr, inv, scale, r,
-                                                          wov, out, S);
-    if (m.max_m > 64)
-        local_block_kernel<T, Stor><<<(unsigned int)std::min<int64_t>(m.n_sub, 148 * 8), kBlock, 0, st>>>(
-            m.n_sub, m.sub_ptr, m.sub_idx, m.inv_ptr, inv, scale, r, wov, out, S);
-}
-
-void launch_local(const DevMesh& m, cgs_precision prec, const void* r, void* out, bool weighted,
-                  const SolveScalars* S, cudaStream_t st) {
-    // r is float64 in the FP64 form and the float copy of the residual otherwise
-    if (prec == CGS_FP64)
-        local_launch<double, double>(m, m.inv64, nullptr, static_cast<const double*>(r), weighted ? m.wov64 : nullptr,
-                                     static_cast<double*>(out), S, st);
-    else if (prec == CGS_FP32_BULK)
-        local_launch<float, float>(m, m.inv32, nullptr, static_cast<const float*>(r), weighted ? m.wov32 : nullptr,
-                                   static_cast<float*>(out), S, st);
-    else
-        local_launch<float, __half>(m, m.inv16, m.inv16_scale, static_cast<const float*>(r),
-                                    weighted ? m.wov32 : nullptr, static_cast<float*>(out), S, st);
-}
-
-void launch_restrict(const DevMesh& m, bool fp64, const void* s, bool s_is_double, double* rr,
-                     const SolveScalars* S, cudaStream_t st) {
-    if (fp64) {
-        VertexXYZW<double> vx{m.xyzw};
-        restrict_kernel<double, double><<<grid_exact(m.ne), kBlock, 0, st>>>(
-            m.ne, m.conn, m.cell, m.cell_cols, vx, box_grid<double>(m), static_cast<const double*>(s), rr, S);
-    } else {
-        VertexXYZW<float> vx{m.xyzwf};
-        if (s_is_double)
-            restrict_kernel<float, double><<<grid_exact(m.ne), kBlock, 0, st>>>(
-                m.ne, m.conn, m.cell, m.cell_cols, vx, box_grid<float>(m), static_cast<const double*>(s), rr, S);
-        else
-            restrict_kernel<float, float><<<grid_exact(m.ne), kBlock, 0, st>>>(
-                m.ne, m.conn, m.cell, m.cell_cols, vx, box_grid<float>(m), static_cast<const float*>(s), rr, S);
-    }
-}
-
-void launch_interp_add(const DevMesh& m, bool fp64, const double* ur, const float* ur32, void* z,
-                       const SolveScalars* S, cudaStream_t st) {
-    if (fp64) {
-        VertexXYZW<double> vx{m.xyzw};
-        interp_add_kernel<double, double><<<grid_exact(m.ne), kBlock, 0, st>>>(
-            m.ne, m.conn, m.cell, m.cell_cols, vx, box_grid<double>(m), ur, static_cast<double*>(z), S);
-    } else {
-        VertexXYZW<float> vx{m.xyzwf};
-        if (ur32)   // float copy of u_r written by the reduced solve: no conversions per element
-            interp_add_kernel<float, float><<<grid_exact(m.ne), kBlock, 0, st>>>(
-                m.ne, m.conn, m.cell, m.cell_cols, vx, box_grid<float>(m), ur32, static_cast<float*>(z), S);
-        else
-            interp_add_kernel<float, double><<<grid_exact(m.ne), kBlock, 0, st>>>(
-                m.ne, m.conn, m.cell, m.cell_cols, vx, box_grid<float>(m), ur, static_cast<float*>(z), S);
-    }
-}
-
-void launch_coarse(const DevMesh& m, const double* rr, double* ur, float* ur32, const SolveScalars* S,
-                   cudaStream_t st) {
-    if (m.nr == 0) return;
-    const unsigned int blocks = (unsigned int)std::min<int64_t>((m.nr + 7) / 8, 148 * 16);
-    coarse_gemv_kernel<<<blocks, kBlock, 0, st>>>(m.nr, m.ar_inv, rr, ur, ur32, S);
-}
-
-void launch_apply_pair_tiled(const DevMesh& m, const float2* p2, float2* q2, double* partials, SolveScalars* S,
-                             cudaStream_t st) {
+void launch_apply_pair_tiled(const Plan& P, const Vecs& V, cudaStream_t st) {
+    if (!P.nwork[kWorkTile]) return;
     const int smem = (int)(2 * kTileSlotBytes + 2 * kTileVerts * sizeof(float2));
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(apply_pair_tiled_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         attr = true;
     }
-    apply_pair_tiled_kernel<<<(unsigned int)m.ntiles, kBlock, smem, st>>>(
-        m.ntiles, m.tile_ptr, m.tile_vptr, m.tile_verts, m.eloc, m.at_hi, m.at_lo, p2, q2, partials, S);
+    apply_pair_tiled_kernel<<<P.nwork[kWorkTile], kBlock, smem, st>>>(P.meshes, P.work[kWorkTile], V,
+                                                                      P.wait_limit);
 }
-void launch_apply28f_tiled(const DevMesh& m, const float* x, float* y, float alpha, SolveScalars* S,
-                           cudaStream_t st) {
+
+void launch_apply28f_tiled(const Plan& P, const Vecs& V, const float* x, float* y, float alpha, cudaStream_t st) {
+    if (!P.nwork[kWorkTile]) return;
     const int smem = (int)(kTileSlotBytes + 2 * kTileVerts * sizeof(float));
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(apply28f_tiled_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         attr = true;
     }
-    apply28f_tiled_kernel<<<(unsigned int)m.ntiles, kBlock, smem, st>>>(m.ntiles, m.tile_ptr, m.tile_vptr,
-                                                                        m.tile_verts, m.eloc, m.at_hi, x, y, alpha,
-                                                                        S);
+    apply28f_tiled_kernel<<<P.nwork[kWorkTile], kBlock, smem, st>>>(P.meshes, P.work[kWorkTile], V, x, y, alpha,
+                                                                    P.wait_limit);
+}
+
+void launch_local(const Plan& P, const Vecs& V, cgs_precision prec, const void* r, void* out, bool weighted,
+                  cudaStream_t st) {
+    if (!P.nwork[kWorkSub]) return;
+    const unsigned int n = P.nwork[kWorkSub];
+    const Work* W = P.work[kWorkSub];
+    const int wt = weighted ? 1 : 0;
+    // r is float64 in the FP64 form and the float copy of the residual otherwise
+    if (prec == CGS_FP64) {
+        local_warp_kernel<double, double><<<n, kBlock, 0, st>>>(P.meshes, W, V, static_cast<const double*>(r),
+                                                                static_cast<double*>(out), wt);
+        if (P.max_m > 64)
+            local_block_kernel<double, double><<<n, kBlock, 0, st>>>(P.meshes, W, V, static_cast<const double*>(r),
+                                                                     static_cast<double*>(out), wt);
+    } else if (prec == CGS_FP32_BULK) {
+        local_warp_kernel<float, float><<<n, kBlock, 0, st>>>(P.meshes, W, V, static_cast<const float*>(r),
+                                                              static_cast<float*>(out), wt);
+        if (P.max_m > 64)
+            local_block_kernel<float, float><<<n, kBlock, 0, st>>>(P.meshes, W, V, static_cast<const float*>(r),
+                                                                   static_cast<float*>(out), wt);
+    } else {
+        local_warp_kernel<float, __half><<<n, kBlock, 0, st>>>(P.meshes, W, V, static_cast<const float*>(r),
+                                                               static_cast<float*>(out), wt);
+        if (P.max_m > 64)
+            local_block_kernel<float, __half><<<n, kBlock, 0, st>>>(P.meshes, W, V, static_cast<const float*>(r),
+                                                                    static_cast<float*>(out), wt);
+    }
+}
+
+void launch_restrict(const Plan& P, const Vecs& V, bool fp64, const void* s, bool s_is_double, double* rr,
+                     cudaStream_t st) {
+    if (!P.nwork[kWorkElem] || !P.any_nr) return;
+    const unsigned int n = P.nwork[kWorkElem];
+    const Work* W = P.work[kWorkElem];
+    if (fp64)
+        restrict_kernel<double, double><<<n, kBlock, 0, st>>>(P.meshes, W, V, static_cast<const double*>(s), rr);
+    else if (s_is_double)
+        restrict_kernel<float, double><<<n, kBlock, 0, st>>>(P.meshes, W, V, static_cast<const double*>(s), rr);
+    else
+        restrict_kernel<float, float><<<n, kBlock, 0, st>>>(P.meshes, W, V, static_cast<const float*>(s), rr);
+}
+
+void launch_interp_add(const Plan& P, const Vecs& V, bool fp64, const double* ur, const float* ur32, void* z,
+                       cudaStream_t st) {
+    if (!P.nwork[kWorkElem] || !P.any_nr) return;
+    const unsigned int n = P.nwork[kWorkElem];
+    const Work* W = P.work[kWorkElem];
+    if (fp64)
+        interp_add_kernel<double, double><<<n, kBlock, 0, st>>>(P.meshes, W, V, ur, static_cast<double*>(z));
+    else if (ur32)   // float copy of u_r written by the reduced solve: no conversions per element
+        interp_add_kernel<float, float><<<n, kBlock, 0, st>>>(P.meshes, W, V, ur32, static_cast<float*>(z));
+    else
+        interp_add_kernel<float, double><<<n, kBlock, 0, st>>>(P.meshes, W, V, ur, static_cast<float*>(z));
+}
+
+void launch_coarse(const Plan& P, const Vecs& V, const double* rr, double* ur, float* ur32, cudaStream_t st) {
+    if (!P.nwork[kWorkRow]) return;
+    coarse_gemv_kernel<<<P.nwork[kWorkRow], kBlock, 0, st>>>(P.meshes, P.work[kWorkRow], V, rr, ur, ur32);
 }
 
 template <typename Tq>
-void launch_pcg_init(const DevMesh& m, const double* b, const uint8_t* dir, double* x, double* r, Tq* q,
-                     double rtol, int maxit, double* partials, SolveScalars* S, cudaStream_t st) {
-    pcg_init_kernel<Tq><<<grid_for(m.nv), kBlock, 0, st>>>(m.nv, b, dir, x, r, q, rtol, maxit, partials, S);
+void launch_pcg_init(const Plan& P, const Vecs& V, Tq* q, double rtol, int maxit, cudaStream_t st) {
+    pcg_init_kernel<Tq><<<P.nwork[kWorkVert], kBlock, 0, st>>>(P.meshes, P.work[kWorkVert], V, q, rtol, maxit);
 }
 template <typename Tz>
-void launch_pcg_first_dir(const DevMesh& m, const Tz* z, const double* r, double* p, float2* p2, double* partials,
-                          SolveScalars* S, cudaStream_t st) {
-    pcg_first_dir_kernel<Tz><<<grid_for(m.nv), kBlock, 0, st>>>(m.nv, z, r, p, p2, partials, S);
+void launch_precond_prep(const Plan& P, const Vecs& V, const double* r, cudaStream_t st) {
+    precond_prep_kernel<Tz><<<P.nwork[kWorkVert], kBlock, 0, st>>>(P.meshes, P.work[kWorkVert], V, r);
+}
+template <typename Tz>
+void launch_pcg_first_dir(const Plan& P, const Vecs& V, cudaStream_t st) {
+    pcg_first_dir_kernel<Tz><<<P.nwork[kWorkVert], kBlock, 0, st>>>(P.meshes, P.work[kWorkVert], V);
 }
 template <typename Tz, typename Tq>
-void launch_pcg_update_xr(const DevMesh& m, double* x, double* r, const double* p, const Tq* q, Tz* z, Tz* s,
-                          double* rr_vec, double* partials, SolveScalars* S, cudaStream_t st) {
-    pcg_update_xr_kernel<Tz, Tq><<<grid_for(m.nv), kBlock, 0, st>>>(m.nv, x, r, p, q, z, s, rr_vec, m.nr, partials,
-                                                                     S);
+void launch_pcg_update_xr(const Plan& P, const Vecs& V, const Tq* q, cudaStream_t st) {
+    pcg_update_xr_kernel<Tz, Tq><<<P.nwork[kWorkVert], kBlock, 0, st>>>(P.meshes, P.work[kWorkVert], V, q);
 }
 template <typename Tz, typename Tq>
-void launch_pcg_dots(const DevMesh& m, const Tz* z, const double* r, const Tq* q, double* partials, SolveScalars* S,
-                     cudaStream_t st) {
-    pcg_dots_kernel<Tz, Tq><<<grid_for(m.nv), kBlock, 0, st>>>(m.nv, z, r, q, partials, S);
+void launch_pcg_dots(const Plan& P, const Vecs& V, const Tq* q, cudaStream_t st) {
+    pcg_dots_kernel<Tz, Tq><<<P.nwork[kWorkVert], kBlock, 0, st>>>(P.meshes, P.work[kWorkVert], V, q);
 }
 template <typename Tz, typename Tq>
-void launch_pcg_update_p(const DevMesh& m, const Tz* z, double* p, float2* p2, Tq* q, SolveScalars* S,
-                         cudaGraphConditionalHandle cond, bool use_cond, cudaStream_t st) {
-    pcg_update_p_kernel<Tz, Tq><<<grid_for(m.nv), kBlock, 0, st>>>(m.nv, z, p, p2, q, S, cond, use_cond ? 1 : 0);
+void launch_pcg_update_p(const Plan& P, const Vecs& V, Tq* q, cudaStream_t st) {
+    pcg_update_p_kernel<Tz, Tq><<<P.nwork[kWorkVert], kBlock, 0, st>>>(P.meshes, P.work[kWorkVert], V, q);
 }
-#define CGS_INST(TZ, TQ)                                                                                          \
-    template void launch_pcg_update_xr<TZ, TQ>(const DevMesh&, double*, double*, const double*, const TQ*, TZ*,   \
-                                               TZ*, double*, double*, SolveScalars*, cudaStream_t);               \
-    template void launch_pcg_dots<TZ, TQ>(const DevMesh&, const TZ*, const double*, const TQ*, double*,           \
-                                          SolveScalars*, cudaStream_t);                                           \
-    template void launch_pcg_update_p<TZ, TQ>(const DevMesh&, const TZ*, double*, float2*, TQ*, SolveScalars*,    \
-                                              cudaGraphConditionalHandle, bool, cudaStream_t);
+void launch_loop_cond(const Plan& P, const Vecs& V, cudaGraphConditionalHandle cond, cudaStream_t st) {
+    loop_cond_kernel<<<1, kBlock, 0, st>>>(V.S, P.nslots, cond);
+}
+
+void launch_resid_norm(const Plan& P, const Vecs& V, cudaStream_t st) {
+    resid_norm_kernel<<<P.nwork[kWorkVert], kBlock, 0, st>>>(P.meshes, P.work[kWorkVert], V);
+}
+
+Schedule default_schedule(int64_t total_nv, int64_t total_sub) {
+    const int64_t target = 4 * 148;
+    Schedule s;
+    int64_t v = (total_nv + target - 1) / target;
+    s.vert_chunk = (int)std::min<int64_t>(2048, std::max<int64_t>(256, (v + 255) / 256 * 256));
+    int64_t c = (total_sub + target - 1) / target;
+    s.sub_chunk = (int)std::min<int64_t>(64, std::max<int64_t>(8, (c + 7) / 8 * 8));
+    return s;
+}
+
+// Work tables of one mesh as one slot: element ranges, tiles, vertex ranges,
+// subdomain ranges and reduced-row ranges, each numbered within the slot.
+void append_mesh_work(std::vector<Work> (&tabs)[kWorkKinds], int mesh, int slot, int64_t voff, int64_t roff,
+                      int64_t poff, const MeshSizes& z, const Schedule& sch) {
+    auto add = [&](int kind, int64_t n, int64_t chunk) {
+        const int64_t count = (n + chunk - 1) / chunk;
+        for (int64_t i = 0; i < count; ++i) {
+            Work w;
+            w.mesh = mesh;
+            w.slot = slot;
+            w.voff = voff;
+            w.roff = (int32_t)roff;
+            w.poff = (int32_t)poff;
+            w.begin = (int32_t)(i * chunk);
+            w.end = (int32_t)std::min(n, (i + 1) * chunk);
+            w.idx = (int32_t)i;
+            w.count = (int32_t)count;
+            tabs[kind].push_back(w);
+        }
+    };
+    add(kWorkElem, z.ne, kElemChunk);
+    add(kWorkTile, z.ntiles, 1);
+    add(kWorkVert, z.nv, sch.vert_chunk);
+    add(kWorkSub, z.n_sub, sch.sub_chunk);
+    add(kWorkRow, z.nr, kRowChunk);
+}
+
+int64_t mesh_partial_slots(const MeshSizes& z, const Schedule& sch) {
+    int64_t c = (z.ne + kElemChunk - 1) / kElemChunk;
+    c = std::max(c, z.ntiles);
+    c = std::max(c, (z.nv + sch.vert_chunk - 1) / sch.vert_chunk);
+    return 2 * std::max<int64_t>(c, 1);
+}
+
+#define CGS_INST(TZ, TQ)                                                                                       \
+    template void launch_pcg_update_xr<TZ, TQ>(const Plan&, const Vecs&, const TQ*, cudaStream_t);             \
+    template void launch_pcg_dots<TZ, TQ>(const Plan&, const Vecs&, const TQ*, cudaStream_t);                  \
+    template void launch_pcg_update_p<TZ, TQ>(const Plan&, const Vecs&, TQ*, cudaStream_t);
 CGS_INST(double, double)
 CGS_INST(double, float2)
 CGS_INST(float, double)
 CGS_INST(float, float2)
 #undef CGS_INST
-template void launch_pcg_init<double>(const DevMesh&, const double*, const uint8_t*, double*, double*, double*,
-                                      double, int, double*, SolveScalars*, cudaStream_t);
-template void launch_pcg_init<float2>(const DevMesh&, const double*, const uint8_t*, double*, double*, float2*,
-                                      double, int, double*, SolveScalars*, cudaStream_t);
-template void launch_pcg_first_dir<double>(const DevMesh&, const double*, const double*, double*, float2*, double*,
-                                           SolveScalars*, cudaStream_t);
-template void launch_pcg_first_dir<float>(const DevMesh&, const float*, const double*, double*, float2*, double*,
-                                          SolveScalars*, cudaStream_t);
+template void launch_pcg_init<double>(const Plan&, const Vecs&, double*, double, int, cudaStream_t);
+template void launch_pcg_init<float2>(const Plan&, const Vecs&, float2*, double, int, cudaStream_t);
+template void launch_precond_prep<double>(const Plan&, const Vecs&, const double*, cudaStream_t);
+template void launch_precond_prep<float>(const Plan&, const Vecs&, const double*, cudaStream_t);
+template void launch_pcg_first_dir<double>(const Plan&, const Vecs&, cudaStream_t);
+template void launch_pcg_first_dir<float>(const Plan&, const Vecs&, cudaStream_t);
 
-void launch_resid_norm(const DevMesh& m, const double* b, const double* y, const uint8_t* dir, double* partials,
-                       unsigned int* ticket, double* out2, cudaStream_t st) {
-    resid_norm_kernel<<<grid_for(m.nv), kBlock, 0, st>>>(m.nv, b, y, dir, partials, ticket, out2);
+void launch_convert_f2d(const Plan& P, const float* a, double* b, bool mask, cudaStream_t st) {
+    convert_kernel<float, double><<<P.nwork[kWorkVert], kBlock, 0, st>>>(P.meshes, P.work[kWorkVert], a, b, mask);
 }
-
-void launch_convert_f2d(int64_t n, const float* a, double* b, const uint8_t* dir, cudaStream_t st) {
-    convert_kernel<float, double><<<grid_for(n), kBlock, 0, st>>>(n, a, b, dir);
+void launch_convert_d2f(const Plan& P, const double* a, float* b, bool mask, cudaStream_t st) {
+    convert_kernel<double, float><<<P.nwork[kWorkVert], kBlock, 0, st>>>(P.meshes, P.work[kWorkVert], a, b, mask);
 }
-void launch_convert_d2f(int64_t n, const double* a, float* b, const uint8_t* dir, cudaStream_t st) {
-    convert_kernel<double, float><<<grid_for(n), kBlock, 0, st>>>(n, a, b, dir);
-}
-void launch_copy_d(int64_t n, const double* a, double* b, const uint8_t* dir, cudaStream_t st) {
-    convert_kernel<double, double><<<grid_for(n), kBlock, 0, st>>>(n, a, b, dir);
+void launch_copy_d(const Plan& P, const double* a, double* b, bool mask, cudaStream_t st) {
+    convert_kernel<double, double><<<P.nwork[kWorkVert], kBlock, 0, st>>>(P.meshes, P.work[kWorkVert], a, b, mask);
 }
 void launch_fill_d(int64_t n, double* a, double v, cudaStream_t st) {
-    fill_kernel<double><<<grid_for(n), kBlock, 0, st>>>(n, a, v);
+    if (n <= 0) return;
+    const int64_t b = std::min<int64_t>((n + kBlock - 1) / kBlock, 148 * 8);
+    fill_kernel<double><<<(unsigned int)b, kBlock, 0, st>>>(n, a, v);
 }
 void launch_fill_f(int64_t n, float* a, float v, cudaStream_t st) {
-    fill_kernel<float><<<grid_for(n), kBlock, 0, st>>>(n, a, v);
+    if (n <= 0) return;
+    const int64_t b = std::min<int64_t>((n + kBlock - 1) / kBlock, 148 * 8);
+    fill_kernel<float><<<(unsigned int)b, kBlock, 0, st>>>(n, a, v);
 }
 
 }  // namespace cgs

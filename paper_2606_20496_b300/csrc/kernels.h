@@ -1,54 +1,68 @@
-// Launchers of the CUDA kernels (kernels.cu), called by the C ABI (api.cu).
+// Launchers of the CUDA kernels (kernels.cu), called by the C ABI (api.cu,
+// noalloc.cu).  Every launcher runs over the work tables of a Plan; vectors
+// are pools addressed per slot through the work items' offsets.
 #pragma once
+
+#include <string>
 
 #include "internal.h"
 
 namespace cgs {
 
-unsigned int partial_slots(const DevMesh& m);
-
-void launch_apply64(const DevMesh& m, const double* x, double* y, double alpha, double* partials,
-                    SolveScalars* S, bool dot, cudaStream_t st);
-void launch_local(const DevMesh& m, cgs_precision prec, const void* r, void* out, bool weighted,
-                  const SolveScalars* S, cudaStream_t st);
-void launch_restrict(const DevMesh& m, bool fp64, const void* s, bool s_is_double, double* rr,
-                     const SolveScalars* S, cudaStream_t st);
-void launch_interp_add(const DevMesh& m, bool fp64, const double* ur, const float* ur32, void* z,
-                       const SolveScalars* S, cudaStream_t st);
-void launch_coarse(const DevMesh& m, const double* rr, double* ur, float* ur32, const SolveScalars* S,
-                   cudaStream_t st);
-void launch_apply_pair_tiled(const DevMesh& m, const float2* p2, float2* q2, double* partials, SolveScalars* S,
-                             cudaStream_t st);
-void launch_apply28f_tiled(const DevMesh& m, const float* x, float* y, float alpha, SolveScalars* S,
-                           cudaStream_t st);
-
+void launch_apply64(const Plan& P, const Vecs& V, const double* x, double* y, double alpha, bool dot,
+                    cudaStream_t st);
+void launch_apply_pair_tiled(const Plan& P, const Vecs& V, cudaStream_t st);
+void launch_apply28f_tiled(const Plan& P, const Vecs& V, const float* x, float* y, float alpha, cudaStream_t st);
+void launch_local(const Plan& P, const Vecs& V, cgs_precision prec, const void* r, void* out, bool weighted,
+                  cudaStream_t st);
+void launch_restrict(const Plan& P, const Vecs& V, bool fp64, const void* s, bool s_is_double, double* rr,
+                     cudaStream_t st);
+void launch_interp_add(const Plan& P, const Vecs& V, bool fp64, const double* ur, const float* ur32, void* z,
+                       cudaStream_t st);
+void launch_coarse(const Plan& P, const Vecs& V, const double* rr, double* ur, float* ur32, cudaStream_t st);
 
 template <typename Tq>
-void launch_pcg_init(const DevMesh& m, const double* b, const uint8_t* dir, double* x, double* r, Tq* q,
-                     double rtol, int maxit, double* partials, SolveScalars* S, cudaStream_t st);
+void launch_pcg_init(const Plan& P, const Vecs& V, Tq* q, double rtol, int maxit, cudaStream_t st);
 template <typename Tz>
-void launch_pcg_first_dir(const DevMesh& m, const Tz* z, const double* r, double* p, float2* p2, double* partials,
-                          SolveScalars* S, cudaStream_t st);
+void launch_precond_prep(const Plan& P, const Vecs& V, const double* r, cudaStream_t st);
+template <typename Tz>
+void launch_pcg_first_dir(const Plan& P, const Vecs& V, cudaStream_t st);
 template <typename Tz, typename Tq>
-void launch_pcg_update_xr(const DevMesh& m, double* x, double* r, const double* p, const Tq* q, Tz* z, Tz* s,
-                          double* rr_vec, double* partials, SolveScalars* S, cudaStream_t st);
+void launch_pcg_update_xr(const Plan& P, const Vecs& V, const Tq* q, cudaStream_t st);
 template <typename Tz, typename Tq>
-void launch_pcg_dots(const DevMesh& m, const Tz* z, const double* r, const Tq* q, double* partials, SolveScalars* S,
-                     cudaStream_t st);
+void launch_pcg_dots(const Plan& P, const Vecs& V, const Tq* q, cudaStream_t st);
 template <typename Tz, typename Tq>
-void launch_pcg_update_p(const DevMesh& m, const Tz* z, double* p, float2* p2, Tq* q, SolveScalars* S,
-                         cudaGraphConditionalHandle cond, bool use_cond, cudaStream_t st);
-void launch_resid_norm(const DevMesh& m, const double* b, const double* y, const uint8_t* dir, double* partials,
-                       unsigned int* ticket, double* out2, cudaStream_t st);
+void launch_pcg_update_p(const Plan& P, const Vecs& V, Tq* q, cudaStream_t st);
+void launch_loop_cond(const Plan& P, const Vecs& V, cudaGraphConditionalHandle cond, cudaStream_t st);
+void launch_resid_norm(const Plan& P, const Vecs& V, cudaStream_t st);
 
-void launch_convert_f2d(int64_t n, const float* a, double* b, const uint8_t* dir, cudaStream_t st);
-void launch_convert_d2f(int64_t n, const double* a, float* b, const uint8_t* dir, cudaStream_t st);
-void launch_copy_d(int64_t n, const double* a, double* b, const uint8_t* dir, cudaStream_t st);
+void launch_convert_f2d(const Plan& P, const float* a, double* b, bool mask, cudaStream_t st);
+void launch_convert_d2f(const Plan& P, const double* a, float* b, bool mask, cudaStream_t st);
+void launch_copy_d(const Plan& P, const double* a, double* b, bool mask, cudaStream_t st);
 void launch_fill_d(int64_t n, double* a, double v, cudaStream_t st);
 void launch_fill_f(int64_t n, float* a, float v, cudaStream_t st);
 
+// Work tables of one mesh as slot `slot` (host side, appended to tabs).
+struct MeshSizes {
+    int64_t nv, ne, ntiles, n_sub, nr;
+};
+// Block sizes of the range-parallel kernels: vertices per block (vector
+// kernels) and subdomains per block (local solves).  Elements (256) and
+// reduced rows (8) per block are fixed by the thread mapping.
+struct Schedule {
+    int vert_chunk = 1024;
+    int sub_chunk = 64;
+};
+// Default schedule: enough blocks to fill the GPU (about four per SM) for
+// `total` work of each kind, chunks within the kernels' ranges.
+Schedule default_schedule(int64_t total_nv, int64_t total_sub);
+void append_mesh_work(std::vector<Work> (&tabs)[kWorkKinds], int mesh, int slot, int64_t voff, int64_t roff,
+                      int64_t poff, const MeshSizes& z, const Schedule& sch);
+int64_t mesh_partial_slots(const MeshSizes& z, const Schedule& sch);   // partial sums one slot needs
+
 // Mesh accessors (api.cu).
 const DevMesh& mesh_dev(const cgs_mesh* m);
+const Plan& mesh_plan(const cgs_mesh* m);
 cgs_precision mesh_prec(const cgs_mesh* m);
 cgs_form mesh_form(const cgs_mesh* m);
 const uint8_t* mesh_dir(const cgs_mesh* m);

@@ -68,45 +68,38 @@ extern "C" cgs_status cgs_apply_preconditioner_noalloc(cgs_mesh* mesh, const dou
     }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     unsigned char* p = static_cast<unsigned char*>(base);
-    void* zb = p;                                        // nv entries of 8 bytes
-    void* sb = p + (size_t)8 * CGS_NOALLOC_MAX_NV;       // nv entries of 8 bytes
-    double* rr = reinterpret_cast<double*>(p + (size_t)16 * CGS_NOALLOC_MAX_NV);
-    double* ur = rr + CGS_NOALLOC_MAX_NR;
-    const bool f64 = mesh_prec(mesh) == CGS_FP64;
-    const int64_t nv = d.nv;
+    // the mesh's own work tables (one slot at offset 0) with every working
+    // vector in the static array
+    const Plan& P = mesh_plan(mesh);
+    Vecs V;
+    V.z = p;                                           // nv entries of 8 bytes
+    V.s = p + (size_t)8 * CGS_NOALLOC_MAX_NV;          // nv entries of 8 bytes
+    V.rr = reinterpret_cast<double*>(p + (size_t)16 * CGS_NOALLOC_MAX_NV);
+    V.ur = V.rr + CGS_NOALLOC_MAX_NR;
+    const cgs_precision prec = mesh_prec(mesh);
+    const bool f64 = prec == CGS_FP64;
     // z = 0, s = r in the bulk precision, r_r = 0
-    if (f64) {
-        launch_fill_d(nv, static_cast<double*>(zb), 0.0, st);
-        launch_copy_d(nv, r, static_cast<double*>(sb), nullptr, st);
-    } else {
-        launch_fill_f(nv, static_cast<float*>(zb), 0.0f, st);
-        launch_convert_d2f(nv, r, static_cast<float*>(sb), nullptr, st);
-    }
-    if (d.nr) launch_fill_d(d.nr, rr, 0.0, st);
-    if (mesh_form(mesh) == CGS_HYBRID) {
-        launch_local(d, mesh_prec(mesh), sb, zb, true, nullptr, st);
+    if (f64)
+        launch_precond_prep<double>(P, V, r, st);
+    else
+        launch_precond_prep<float>(P, V, r, st);
+    const bool weighted = mesh_form(mesh) == CGS_HYBRID;
+    launch_local(P, V, prec, V.s, V.z, weighted, st);
+    if (weighted) {
         if (f64)
-            launch_apply64(d, static_cast<const double*>(zb), static_cast<double*>(sb), -1.0, nullptr, nullptr,
-                           false, st);
+            launch_apply64(P, V, static_cast<const double*>(V.z), static_cast<double*>(V.s), -1.0, false, st);
         else
-            launch_apply28f_tiled(d, static_cast<const float*>(zb), static_cast<float*>(sb), -1.0f, nullptr, st);
-        if (d.nr) {
-            launch_restrict(d, f64, sb, f64, rr, nullptr, st);
-            launch_coarse(d, rr, ur, nullptr, nullptr, st);
-            launch_interp_add(d, f64, ur, nullptr, zb, nullptr, st);
-        }
-    } else {
-        launch_local(d, mesh_prec(mesh), sb, zb, false, nullptr, st);
-        if (d.nr) {
-            launch_restrict(d, f64, sb, f64, rr, nullptr, st);
-            launch_coarse(d, rr, ur, nullptr, nullptr, st);
-            launch_interp_add(d, f64, ur, nullptr, zb, nullptr, st);
-        }
+            launch_apply28f_tiled(P, V, static_cast<const float*>(V.z), static_cast<float*>(V.s), -1.0f, st);
+    }
+    if (d.nr) {
+        launch_restrict(P, V, f64, V.s, f64, V.rr, st);
+        launch_coarse(P, V, V.rr, V.ur, nullptr, st);
+        launch_interp_add(P, V, f64, V.ur, nullptr, V.z, st);
     }
     if (f64)
-        launch_copy_d(nv, static_cast<const double*>(zb), z, mesh_dir(mesh), st);
+        launch_copy_d(P, static_cast<const double*>(V.z), z, true, st);
     else
-        launch_convert_f2d(nv, static_cast<const float*>(zb), z, mesh_dir(mesh), st);
+        launch_convert_f2d(P, static_cast<const float*>(V.z), z, true, st);
     e = cudaGetLastError();
     if (e != cudaSuccess) {
         set_last_error(std::string("kernel launch: ") + cudaGetErrorString(e));

@@ -39,6 +39,7 @@ def main():
     ap.add_argument("--solves", type=int, default=2)
     ap.add_argument("--rtol", type=float, default=1e-8)
     ap.add_argument("--maxit", type=int, default=1000)
+    ap.add_argument("--tune", action="store_true", help="run the schedule autotuner after setup")
     ap.add_argument("--profile", action="store_true", help="per-kernel CUDA-event times (host-driven loop)")
     args = ap.parse_args()
     build.build()
@@ -47,6 +48,8 @@ def main():
     t0 = time.perf_counter()
     h = cgs.Mesh(ctx, m.xyz, m.conn, part=m.part, boxes=m.boxes, prec=args.prec, form=args.form)
     setup_s = time.perf_counter() - t0
+    if args.tune:
+        cgs.cgs_mesh_tune(h.handle)
     bd = torch.as_tensor(b, dtype=torch.float64, device="cuda")
     x = torch.empty_like(bd)
     if args.profile:
@@ -63,7 +66,9 @@ def main():
         ms.append(e0.elapsed_time(e1))
         if st != cgs.OK and not (st == cgs.ERR_NO_CONVERGENCE and it[0] == args.maxit):
             raise SystemExit(f"solve failed: {cgs.status_string(st)}")
+    info = cgs.cgs_mesh_info(h.handle)
     out = {"workload": args.workload, "prec": args.prec, "form": args.form, "nv": h.info["nv"],
+           "schedule": {k: info[k] for k in ("vert_chunk", "sub_chunk")},
            "ne": h.info["ne"], "n_sub": h.info["n_sub"], "n_r": h.info["n_r"],
            "footprint_mb": h.info["footprint_bytes"] / 2 ** 20, "setup_s": setup_s, "iters": its,
            "relres": rels, "ms_per_solve": float(np.mean(ms[1:] if len(ms) > 1 else ms))}

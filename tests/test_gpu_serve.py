@@ -1,0 +1,89 @@
+"""Serving by continuous batching: requests that arrive while others run join
+free slots and share their launches; each result must equal the solo solve
+of the same mesh and right-hand side within the solve tolerance."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2606_20496_b300 import cgs, meshes  # noqa: E402
+
+
+def dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = cgs.cgs_create(0)
+    yield c
+    cgs.cgs_destroy(c)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_results_same_alone_and_in_the_mix(ctx, prec):
+    mesh_defs = [meshes.cube(10, perturb=0.15, seed=1), meshes.cube(16, deform=True, permute_seed=3),
+                 meshes.cylinder(6, 24, 8, grading=1.1, aspect=5.0, boxes=(3, 3, 3)),
+                 meshes.cube((7, 9, 5), perturb=0.1, seed=4, part_mode="mixed")]
+    hs = [cgs.Mesh(ctx, m.xyz, m.conn, part=m.part, boxes=m.boxes, prec=prec) for m in mesh_defs]
+    rtol = 1e-10
+    server = cgs.cgs_server_create(ctx, max_slots=3, max_nv=max(m.nv for m in mesh_defs),
+                                   max_nr=max(h.info["n_r"] for h in hs), prec=prec, rtol=rtol)
+    try:
+        rng = np.random.default_rng(0)
+        reqs = []   # (mesh index, b, x, ticket)
+        pending = []
+        # arrivals over several steps: 3 slots for 10 requests, so some queue
+        schedule = [2, 0, 3, 1, 0, 4, 0, 0]
+        k = 0
+        for step, n_new in enumerate(schedule + [0] * 60):
+            for _ in range(n_new):
+                mi = k % len(hs)
+                b = dev(rng.standard_normal(mesh_defs[mi].nv))
+                x = torch.zeros_like(b)
+                t = cgs.cgs_submit(server, hs[mi], b, x)
+                reqs.append([mi, b, x, t, None])
+                pending.append(len(reqs) - 1)
+                k += 1
+            active, queued, finished = cgs.cgs_server_step(server, iterations=3)
+            assert active <= 3
+            for i in list(pending):
+                r = cgs.cgs_poll(server, reqs[i][3])
+                if r is not None:
+                    reqs[i][4] = r
+                    pending.remove(i)
+            if not pending and step >= len(schedule):
+                break
+        assert not pending and len(reqs) == 10
+        for mi, b, x, t, (its, rel, st) in reqs:
+            assert st == cgs.OK and rel <= rtol * 1.01
+            x1 = torch.empty_like(x)
+            st1, its1, rel1 = cgs.cgs_solve(hs[mi].handle, b, x1, rtol=rtol)
+            assert abs(int(its1[0]) - its) <= 1
+            xa, xb = x1.cpu().numpy(), x.cpu().numpy()
+            assert np.linalg.norm(xb - xa) / np.linalg.norm(xa) <= 1e-8
+    finally:
+        cgs.cgs_server_free(server)
+        for h in hs:
+            h.free()
+
+
+def test_admission_by_slot_capacity(ctx):
+    small = meshes.cube(6, perturb=0.1, seed=2)
+    big = meshes.cube(12, perturb=0.1, seed=3)
+    hs, hb = (cgs.Mesh(ctx, m.xyz, m.conn, part=m.part, boxes=m.boxes, prec="fp32") for m in (small, big))
+    server = cgs.cgs_server_create(ctx, max_slots=2, max_nv=small.nv, max_nr=hs.info["n_r"], prec="fp32")
+    try:
+        b = dev(np.ones(big.nv))
+        with pytest.raises(cgs.CGSError) as ei:
+            cgs.cgs_submit(server, hb, b, torch.zeros_like(b))
+        assert ei.value.status == cgs.ERR_ADMISSION
+        b = dev(np.zeros(small.nv))
+        t = cgs.cgs_submit(server, hs, b, torch.zeros_like(b))
+        cgs.cgs_server_step(server, iterations=1)
+        assert cgs.cgs_poll(server, t) == (0, 0.0, cgs.OK)
+    finally:
+        cgs.cgs_server_free(server)
+        hs.free()
+        hb.free()
