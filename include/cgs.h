@@ -240,29 +240,45 @@ cgs_status cgs_solve_batched(cgs_mesh* const* meshes, int nmesh, const double* c
                              int nrhs, double rtol, int maxit, int* iters, double* relres, void* stream);
 
 /* ---- serving: continuous batching --------------------------------------------
- * A server keeps `max_slots` solve slots, each with vector space for a mesh of
- * up to max_nv vertices and max_nr reduced unknowns, all in one precision
- * and form, all solved to rtol within maxit products.  Meshes stay set up
+ * A server keeps up to `max_slots` solves in flight, all in one precision and
+ * form, each solved to rtol within maxit products.  Meshes stay set up
  * (resident) across requests; the caller keeps them alive while requests on
  * them are pending.
+ *
+ * Admission is by device-memory footprint.  The working vectors of every
+ * running solve live in one arena of `pool_nv` vertex entries and `pool_nr`
+ * reduced (box) entries, allocated at creation.  A request needs nv vertex
+ * entries (56 bytes each: x, r, p, y, q and the bulk z, s), n_r reduced
+ * entries and a few partial-sum entries; it is admitted, in arrival order,
+ * when a slot is free and the arena has room for all three (first fit).  A
+ * request that waits blocks those behind it (no overtaking), so large
+ * requests are not starved.
+ *
+ * cgs_server_create: pool_nv >= 1, pool_nr >= 0.  ADMISSION if the arena
+ *   exceeds the context's HBM budget.
  * cgs_submit: queue one solve; b and x are device vectors of the mesh that
  *   the caller keeps valid until cgs_poll reports done.  ADMISSION if the
- *   mesh exceeds the slot capacity.  Host-only, returns at once.
- * cgs_server_step: admits queued requests into free slots (starting their
- *   iteration), runs `iterations` PCG iterations over every running slot in
- *   shared launches (slots at different iteration counts), then retires the
- *   slots that stopped: true residual, solution copied to x.  Synchronous.
- *   active/queued/finished (each may be NULL) report the slot counts.
+ *   request could never fit the arena.  Host-only, returns at once.
+ * cgs_server_step: admits queued requests (starting their iteration), runs
+ *   `iterations` PCG iterations over every running slot in shared launches
+ *   (slots at different iteration counts), then retires the slots that
+ *   stopped: true residual, solution copied to x, arena space released.
+ *   Synchronous.  active/queued/finished (each may be NULL) report counts.
  * cgs_poll: done = 1 once the request has finished (then iters, relres and
- *   status are its results and the ticket is released).                    */
+ *   status are its results and the ticket is released).
+ * cgs_server_footprint: arena bytes a request on `mesh` would hold.
+ * cgs_server_stats: arena capacity and bytes held by running solves.       */
 typedef struct cgs_server cgs_server;
-cgs_status cgs_server_create(cgs_ctx* ctx, int max_slots, int64_t max_nv, int64_t max_nr, cgs_precision prec,
+cgs_status cgs_server_create(cgs_ctx* ctx, int max_slots, int64_t pool_nv, int64_t pool_nr, cgs_precision prec,
                              cgs_form form, double rtol, int maxit, cgs_server** out);
 cgs_status cgs_server_free(cgs_server* server);
 cgs_status cgs_submit(cgs_server* server, cgs_mesh* mesh, const double* b, double* x, uint64_t* ticket);
 cgs_status cgs_server_step(cgs_server* server, int iterations, void* stream, int* active, int* queued,
                            int* finished);
 cgs_status cgs_poll(cgs_server* server, uint64_t ticket, int* done, int* iters, double* relres, int* status);
+cgs_status cgs_server_footprint(const cgs_server* server, const cgs_mesh* mesh, size_t* bytes);
+cgs_status cgs_server_stats(const cgs_server* server, size_t* arena_bytes, size_t* bytes_in_use, int* active,
+                            int* queued);
 int64_t cgs_server_launches(const cgs_server* server);
 
 const char* cgs_status_string(cgs_status s);

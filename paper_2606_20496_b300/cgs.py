@@ -29,7 +29,8 @@ EXPORTS = (
     "cgs_solve", "cgs_solve_host",
     "cgs_profile_enable", "cgs_profile_read", "cgs_batch_create", "cgs_batch_free", "cgs_batch_solve",
     "cgs_batch_launches", "cgs_solve_batched", "cgs_mesh_tune", "cgs_batch_tune", "cgs_server_create",
-    "cgs_server_free", "cgs_submit", "cgs_server_step", "cgs_poll", "cgs_server_launches", "cgs_status_string",
+    "cgs_server_free", "cgs_submit", "cgs_server_step", "cgs_poll", "cgs_server_footprint", "cgs_server_stats",
+    "cgs_server_launches", "cgs_status_string",
     "cgs_last_error",
 )
 KERNEL_CLASSES = ("apply_A64", "apply_A32", "local", "restrict", "coarse", "interp", "pcg_xr", "pcg_dots",
@@ -97,6 +98,8 @@ def load(path: str = LIB_PATH):
         "cgs_submit": ([P, P, P, P, C.POINTER(C.c_uint64)], I32),
         "cgs_server_step": ([P, I32, P, C.POINTER(I32), C.POINTER(I32), C.POINTER(I32)], I32),
         "cgs_poll": ([P, C.c_uint64, C.POINTER(I32), C.POINTER(I32), C.POINTER(D), C.POINTER(I32)], I32),
+        "cgs_server_footprint": ([P, P, C.POINTER(C.c_size_t)], I32),
+        "cgs_server_stats": ([P, C.POINTER(C.c_size_t), C.POINTER(C.c_size_t), C.POINTER(I32), C.POINTER(I32)], I32),
         "cgs_server_launches": ([P], I64),
         "cgs_batch_tune": ([P, P], I32),
         "cgs_status_string": ([I32], C.c_char_p),
@@ -325,11 +328,28 @@ def cgs_solve_batched(meshes, bs, xs, nrhs=1, rtol=1e-8, maxit=1000, stream=None
     return st, iters, relres
 
 
-def cgs_server_create(ctx, max_slots, max_nv, max_nr, prec="fp32", form="hybrid", rtol=1e-8, maxit=1000):
+def cgs_server_create(ctx, max_slots, pool_nv, pool_nr, prec="fp32", form="hybrid", rtol=1e-8, maxit=1000):
+    """Server with up to max_slots solves in flight whose vectors share an
+    arena of pool_nv vertex entries and pool_nr reduced entries."""
     out = C.c_void_p()
-    _check(load().cgs_server_create(ctx, int(max_slots), int(max_nv), int(max_nr), PREC[prec], FORM[form],
+    _check(load().cgs_server_create(ctx, int(max_slots), int(pool_nv), int(pool_nr), PREC[prec], FORM[form],
                                     float(rtol), int(maxit), C.byref(out)), "cgs_server_create")
     return out
+
+
+def cgs_server_footprint(server, mesh) -> int:
+    """Arena bytes one request on this mesh holds while it runs."""
+    n = C.c_size_t()
+    h = mesh.handle if isinstance(mesh, Mesh) else mesh
+    _check(load().cgs_server_footprint(server, h, C.byref(n)), "cgs_server_footprint")
+    return int(n.value)
+
+
+def cgs_server_stats(server) -> dict:
+    ab, ub = C.c_size_t(), C.c_size_t()
+    a, q = C.c_int(), C.c_int()
+    _check(load().cgs_server_stats(server, C.byref(ab), C.byref(ub), C.byref(a), C.byref(q)), "cgs_server_stats")
+    return {"arena_bytes": int(ab.value), "bytes_in_use": int(ub.value), "active": a.value, "queued": q.value}
 
 
 def cgs_server_free(server):

@@ -10,6 +10,8 @@
 #include <cstring>
 #include <deque>
 #include <functional>
+#include <iterator>
+#include <map>
 #include <unordered_map>
 #include <mutex>
 #include <new>
@@ -1118,15 +1120,72 @@ cgs_status cgs_solve_batched(cgs_mesh* const* meshes, int nmesh, const double* c
 
 // ---- serving: continuous batching over a pool of solve slots -------------------
 
+namespace {
+
+// First-fit allocator over [0, cap) in units of `align` entries, with
+// coalescing of neighbouring free ranges.  Host-side bookkeeping only; the
+// entries themselves are one device allocation per vector.
+class Arena {
+public:
+    void init(int64_t cap, int64_t align) {
+        align_ = align;
+        cap_ = cap / align * align;
+        free_.clear();
+        if (cap_ > 0) free_[0] = cap_;
+        used_ = 0;
+    }
+    int64_t round(int64_t n) const { return (std::max<int64_t>(n, 1) + align_ - 1) / align_ * align_; }
+    int64_t capacity() const { return cap_; }
+    int64_t used() const { return used_; }
+    // offset of n entries, or -1 when no free range is large enough
+    int64_t alloc(int64_t n) {
+        n = round(n);
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second < n) continue;
+            const int64_t off = it->first, rest = it->second - n;
+            free_.erase(it);
+            if (rest > 0) free_[off + n] = rest;
+            used_ += n;
+            return off;
+        }
+        return -1;
+    }
+    void release(int64_t off, int64_t n) {
+        n = round(n);
+        used_ -= n;
+        auto next = free_.lower_bound(off);
+        if (next != free_.end() && off + n == next->first) {
+            n += next->second;
+            next = free_.erase(next);
+        }
+        if (next != free_.begin()) {
+            auto prev = std::prev(next);
+            if (prev->first + prev->second == off) {
+                prev->second += n;
+                return;
+            }
+        }
+        free_[off] = n;
+    }
+
+private:
+    std::map<int64_t, int64_t> free_;
+    int64_t cap_ = 0, align_ = 1, used_ = 0;
+};
+
+}  // namespace
+
 struct cgs_server {
     cgs_ctx* ctx = nullptr;
     int max_slots = 0;
-    int64_t max_nv = 0, max_nr = 0, pcap = 0;
     double rtol = 1e-8;
     int maxit = 1000;
     DevAllocs mem;
     Engine E;
     Schedule sch;
+    // arenas of vertex entries, reduced entries and partial-sum entries
+    Arena av, ar, ap;
+    size_t bytes_per_v = 0, bytes_per_r = 0, bytes_per_p = sizeof(double);
     // registry of mesh descriptors on the device (index -> mesh)
     DevMesh* reg_d = nullptr;
     DevMesh* reg_stage = nullptr;   // pinned staging for descriptor uploads
@@ -1144,6 +1203,7 @@ struct cgs_server {
         bool busy = false;
         Req req{};
         int reg = -1;
+        int64_t voff = 0, roff = 0, poff = 0, np = 0;
     };
     std::vector<SlotState> slots;
     struct Res {
@@ -1191,8 +1251,7 @@ cudaError_t server_tables(cgs_server* sv, const std::vector<int>& ids, cgs_serve
     for (int k : ids) {
         const cgs_server::SlotState& ss = sv->slots[k];
         const cgs_mesh* m = ss.req.mesh;
-        append_mesh_work(tabs, ss.reg, k, (int64_t)k * sv->max_nv, (int64_t)k * sv->max_nr, (int64_t)k * sv->pcap,
-                         m->sizes, sv->sch);
+        append_mesh_work(tabs, ss.reg, k, ss.voff, ss.roff, ss.poff, m->sizes, sv->sch);
         P.max_m = std::max(P.max_m, m->d.max_m);
         P.any_nr = P.any_nr || m->d.nr > 0;
     }
@@ -1239,20 +1298,24 @@ int server_register(cgs_server* sv, cgs_mesh* m, cudaStream_t st) {
 
 extern "C" {
 
-cgs_status cgs_server_create(cgs_ctx* ctx, int max_slots, int64_t max_nv, int64_t max_nr, cgs_precision prec,
+cgs_status cgs_server_create(cgs_ctx* ctx, int max_slots, int64_t pool_nv, int64_t pool_nr, cgs_precision prec,
                              cgs_form form, double rtol, int maxit, cgs_server** out) {
     if (!out) return fail(CGS_ERR_INVALID_ARG, "null out");
     *out = nullptr;
-    if (!ctx || max_slots <= 0 || max_nv <= 0 || max_nr < 0 || !(rtol >= 0.0))
+    if (!ctx || max_slots <= 0 || pool_nv <= 0 || pool_nr < 0 || !(rtol >= 0.0) || pool_nv > (int64_t(1) << 40) ||
+        pool_nr > (int64_t(1) << 30))
         return fail(CGS_ERR_INVALID_ARG, "bad argument");
     CGS_CUDA(cudaSetDevice(ctx->device));
     cgs_server* sv = new (std::nothrow) cgs_server;
     if (!sv) return fail(CGS_ERR_INVALID_ARG, "host allocation failed");
     sv->ctx = ctx;
     sv->max_slots = max_slots;
-    sv->max_nv = max_nv;
-    sv->max_nr = max_nr;
-    sv->pcap = 2 * ((max_nv + 127) / 128 + 8);
+    // vertex entries in 32-entry units (256-byte aligned double vectors)
+    sv->av.init((pool_nv + 31) / 32 * 32, 32);
+    sv->ar.init((pool_nr + 7) / 8 * 8 + 8 * max_slots, 8);
+    sv->ap.init(2 * ((pool_nv + 127) / 128) + 64 * (int64_t)max_slots, 8);
+    sv->bytes_per_v = 4 * sizeof(double) + (prec == CGS_FP64 ? 3 * sizeof(double) : 2 * sizeof(float2) + 2 * sizeof(float));
+    sv->bytes_per_r = 2 * sizeof(double) + (prec == CGS_FP64 ? 0 : sizeof(float));
     sv->rtol = rtol;
     sv->maxit = maxit;
     sv->slots.resize(max_slots);
@@ -1276,9 +1339,9 @@ cgs_status cgs_server_create(cgs_ctx* ctx, int max_slots, int64_t max_nv, int64_
     if ((e = sv->mem.alloc(&sv->reg_d, sv->reg_cap)) != cudaSuccess) return cleanup(cuda_fail(e, "registry"));
     if ((e = cudaMallocHost(&sv->reg_stage, sizeof(DevMesh) * sv->reg_cap)) != cudaSuccess)
         return cleanup(cuda_fail(e, "registry staging"));
-    if ((e = alloc_pools(sv->mem, E, (int64_t)max_slots * max_nv, (int64_t)max_slots * max_nr,
-                         (int64_t)max_slots * sv->pcap, max_slots)) != cudaSuccess)
-        return cleanup(cuda_fail(e, "slot pools"));
+    if ((e = alloc_pools(sv->mem, E, sv->av.capacity(), sv->ar.capacity(), sv->ap.capacity(), max_slots)) !=
+        cudaSuccess)
+        return cleanup(cuda_fail(e, "vector arena"));
     if ((e = sv->mem.alloc(&sv->bptr_d, max_slots)) != cudaSuccess) return cleanup(cuda_fail(e, "pointers"));
     if ((e = sv->mem.alloc(&sv->xptr_d, max_slots)) != cudaSuccess) return cleanup(cuda_fail(e, "pointers"));
     if ((e = cudaMallocHost(&sv->bptr_h, sizeof(double*) * max_slots)) != cudaSuccess)
@@ -1289,14 +1352,14 @@ cgs_status cgs_server_create(cgs_ctx* ctx, int max_slots, int64_t max_nv, int64_
         sv->bptr_h[k] = nullptr;
         sv->xptr_h[k] = nullptr;
     }
-    // vertex chunks for the typical slot, subdomain chunks for small meshes
-    sv->sch = default_schedule(max_nv, max_nv / 8);
+    // chunks sized for the whole arena as one problem: many slots at once
+    sv->sch = default_schedule(pool_nv, pool_nv / 8);
     E.V.bptr = sv->bptr_d;
     E.V.xptr = sv->xptr_d;
     {
         std::lock_guard<std::mutex> lk(ctx->mu);
         if (ctx->budget && ctx->in_use + sv->mem.bytes > ctx->budget)
-            return cleanup(fail(CGS_ERR_ADMISSION, "slot pools exceed the context's HBM budget"));
+            return cleanup(fail(CGS_ERR_ADMISSION, "vector arena exceeds the context's HBM budget"));
         ctx->in_use += sv->mem.bytes;
         ctx->live_meshes++;
     }
@@ -1330,9 +1393,9 @@ cgs_status cgs_submit(cgs_server* sv, cgs_mesh* mesh, const double* b, double* x
     if (mesh->ctx != sv->ctx) return fail(CGS_ERR_INVALID_ARG, "mesh of another context");
     if (mesh->prm.prec != sv->E.prec || mesh->E.form != sv->E.form)
         return fail(CGS_ERR_INVALID_ARG, "mesh precision or form differs from the server's");
-    if (mesh->d.nv > sv->max_nv || mesh->d.nr > sv->max_nr ||
-        mesh_partial_slots(mesh->sizes, sv->sch) > sv->pcap)
-        return fail(CGS_ERR_ADMISSION, "mesh larger than the server's slot capacity");
+    if (sv->av.round(mesh->d.nv) > sv->av.capacity() || sv->ar.round(mesh->d.nr) > sv->ar.capacity() ||
+        sv->ap.round(mesh_partial_slots(mesh->sizes, sv->sch)) > sv->ap.capacity())
+        return fail(CGS_ERR_ADMISSION, "request larger than the server's vector arena");
     *ticket = sv->next_ticket++;
     sv->queue.push_back(cgs_server::Req{*ticket, mesh, b, x});
     sv->results[*ticket] = cgs_server::Res{0, 0, CGS_OK, 0.0};
@@ -1344,16 +1407,43 @@ cgs_status cgs_server_step(cgs_server* sv, int iterations, void* stream, int* ac
     if (!sv || iterations < 0) return fail(CGS_ERR_INVALID_ARG, "bad argument");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     Engine& E = sv->E;
-    // 1. admit queued requests into free slots
+    // 1. admit queued requests, in arrival order, while a slot is free and
+    //    the arena holds the request's vectors
     std::vector<int> fresh;
-    for (int k = 0; k < sv->max_slots && !sv->queue.empty(); ++k) {
+    int k = 0;
+    while (!sv->queue.empty()) {
+        while (k < sv->max_slots && sv->slots[k].busy) ++k;
+        if (k == sv->max_slots) break;
+        const cgs_server::Req& rq = sv->queue.front();
+        const int64_t np = mesh_partial_slots(rq.mesh->sizes, sv->sch);
+        const int64_t vo = sv->av.alloc(rq.mesh->d.nv);
+        if (vo < 0) break;
+        const int64_t ro = sv->ar.alloc(rq.mesh->d.nr);
+        if (ro < 0) {
+            sv->av.release(vo, rq.mesh->d.nv);
+            break;
+        }
+        const int64_t po = sv->ap.alloc(np);
+        if (po < 0) {
+            sv->av.release(vo, rq.mesh->d.nv);
+            sv->ar.release(ro, rq.mesh->d.nr);
+            break;
+        }
+        const int ri = server_register(sv, rq.mesh, st);
+        if (ri < 0) {
+            sv->av.release(vo, rq.mesh->d.nv);
+            sv->ar.release(ro, rq.mesh->d.nr);
+            sv->ap.release(po, np);
+            break;
+        }
         cgs_server::SlotState& ss = sv->slots[k];
-        if (ss.busy) continue;
-        const int ri = server_register(sv, sv->queue.front().mesh, st);
-        if (ri < 0) break;
         ss.busy = true;
-        ss.req = sv->queue.front();
+        ss.req = rq;
         ss.reg = ri;
+        ss.voff = vo;
+        ss.roff = ro;
+        ss.poff = po;
+        ss.np = np;
         sv->queue.pop_front();
         sv->bptr_h[k] = ss.req.b;
         sv->xptr_h[k] = ss.req.x;
@@ -1410,8 +1500,7 @@ cgs_status cgs_server_step(cgs_server* sv, int iterations, void* stream, int* ac
         E.P = sv->P_fin;
         const Vecs Vn = no_stop(E.V);
         for (int k : done)
-            CGS_CUDA(cudaMemsetAsync(E.V.y + (int64_t)k * sv->max_nv, 0,
-                                     sizeof(double) * sv->slots[k].req.mesh->d.nv, st));
+            CGS_CUDA(cudaMemsetAsync(E.V.y + sv->slots[k].voff, 0, sizeof(double) * sv->slots[k].req.mesh->d.nv, st));
         K(CGS_K_APPLY_A64, launch_apply64(E.P, Vn, E.V.x, E.V.y, 1.0, false, st));
         K(CGS_K_OTHER, launch_resid_norm(E.P, E.V, st));
         CGS_CUDA(cudaMemcpyAsync(E.S_host, E.V.S, sizeof(SolveScalars) * sv->max_slots, cudaMemcpyDeviceToHost, st));
@@ -1421,6 +1510,9 @@ cgs_status cgs_server_step(cgs_server* sv, int iterations, void* stream, int* ac
             const SolveScalars& h = E.S_host[k];
             sv->results[ss.req.ticket] = cgs_server::Res{1, h.iters, (int)slot_status(h), slot_relres(h)};
             sv->reg_users[ss.reg]--;
+            sv->av.release(ss.voff, ss.req.mesh->d.nv);
+            sv->ar.release(ss.roff, ss.req.mesh->d.nr);
+            sv->ap.release(ss.poff, ss.np);
             ss.busy = false;
             ss.reg = -1;
         }
@@ -1444,6 +1536,31 @@ cgs_status cgs_poll(cgs_server* sv, uint64_t ticket, int* done, int* iters, doub
     if (relres) *relres = r.relres;
     if (status) *status = r.status;
     if (r.done) sv->results.erase(it);
+    return CGS_OK;
+}
+
+cgs_status cgs_server_footprint(const cgs_server* sv, const cgs_mesh* mesh, size_t* bytes) {
+    if (!sv || !mesh || !bytes) return fail(CGS_ERR_INVALID_ARG, "null argument");
+    *bytes = (size_t)sv->av.round(mesh->d.nv) * sv->bytes_per_v + (size_t)sv->ar.round(mesh->d.nr) * sv->bytes_per_r +
+             (size_t)sv->ap.round(mesh_partial_slots(mesh->sizes, sv->sch)) * sv->bytes_per_p;
+    return CGS_OK;
+}
+
+cgs_status cgs_server_stats(const cgs_server* sv, size_t* arena_bytes, size_t* bytes_in_use, int* active,
+                            int* queued) {
+    if (!sv) return fail(CGS_ERR_INVALID_ARG, "null server");
+    if (arena_bytes)
+        *arena_bytes = (size_t)sv->av.capacity() * sv->bytes_per_v + (size_t)sv->ar.capacity() * sv->bytes_per_r +
+                       (size_t)sv->ap.capacity() * sv->bytes_per_p;
+    if (bytes_in_use)
+        *bytes_in_use = (size_t)sv->av.used() * sv->bytes_per_v + (size_t)sv->ar.used() * sv->bytes_per_r +
+                        (size_t)sv->ap.used() * sv->bytes_per_p;
+    if (active) {
+        int n = 0;
+        for (const auto& ss : sv->slots) n += ss.busy ? 1 : 0;
+        *active = n;
+    }
+    if (queued) *queued = (int)sv->queue.size();
     return CGS_OK;
 }
 

@@ -28,8 +28,8 @@ def test_results_same_alone_and_in_the_mix(ctx, prec):
                  meshes.cube((7, 9, 5), perturb=0.1, seed=4, part_mode="mixed")]
     hs = [cgs.Mesh(ctx, m.xyz, m.conn, part=m.part, boxes=m.boxes, prec=prec) for m in mesh_defs]
     rtol = 1e-10
-    server = cgs.cgs_server_create(ctx, max_slots=3, max_nv=max(m.nv for m in mesh_defs),
-                                   max_nr=max(h.info["n_r"] for h in hs), prec=prec, rtol=rtol)
+    server = cgs.cgs_server_create(ctx, max_slots=3, pool_nv=3 * max(m.nv for m in mesh_defs),
+                                   pool_nr=3 * max(h.info["n_r"] for h in hs), prec=prec, rtol=rtol)
     try:
         rng = np.random.default_rng(0)
         reqs = []   # (mesh index, b, x, ticket)
@@ -69,11 +69,11 @@ def test_results_same_alone_and_in_the_mix(ctx, prec):
             h.free()
 
 
-def test_admission_by_slot_capacity(ctx):
+def test_request_larger_than_the_arena_is_refused(ctx):
     small = meshes.cube(6, perturb=0.1, seed=2)
     big = meshes.cube(12, perturb=0.1, seed=3)
     hs, hb = (cgs.Mesh(ctx, m.xyz, m.conn, part=m.part, boxes=m.boxes, prec="fp32") for m in (small, big))
-    server = cgs.cgs_server_create(ctx, max_slots=2, max_nv=small.nv, max_nr=hs.info["n_r"], prec="fp32")
+    server = cgs.cgs_server_create(ctx, max_slots=2, pool_nv=small.nv, pool_nr=hs.info["n_r"], prec="fp32")
     try:
         b = dev(np.ones(big.nv))
         with pytest.raises(cgs.CGSError) as ei:
@@ -87,3 +87,54 @@ def test_admission_by_slot_capacity(ctx):
         cgs.cgs_server_free(server)
         hs.free()
         hb.free()
+
+
+def test_admission_by_footprint(ctx):
+    """Four free slots but an arena for two requests: two run, two wait for
+    arena space, in arrival order; every result still equals its solo solve."""
+    m = meshes.cube(12, perturb=0.1, seed=5)
+    small = meshes.cube(5, perturb=0.1, seed=6)
+    h = cgs.Mesh(ctx, m.xyz, m.conn, part=m.part, boxes=m.boxes, prec="fp32")
+    hsm = cgs.Mesh(ctx, small.xyz, small.conn, part=small.part, boxes=small.boxes, prec="fp32")
+    pool_nv = 2 * ((m.nv + 31) // 32 * 32)
+    server = cgs.cgs_server_create(ctx, max_slots=4, pool_nv=pool_nv, pool_nr=2 * h.info["n_r"], prec="fp32",
+                                   rtol=1e-10)
+    try:
+        fp = cgs.cgs_server_footprint(server, h)
+        st0 = cgs.cgs_server_stats(server)
+        assert fp >= 56 * m.nv and st0["bytes_in_use"] == 0 and st0["arena_bytes"] >= 2 * fp
+        rng = np.random.default_rng(7)
+        reqs = []
+        for i in range(4):
+            mm, hh = (m, h) if i < 3 else (small, hsm)
+            b = dev(rng.standard_normal(mm.nv))
+            x = torch.zeros_like(b)
+            reqs.append((hh, b, x, cgs.cgs_submit(server, hh, b, x)))
+        active, queued, finished = cgs.cgs_server_step(server, iterations=1)
+        st1 = cgs.cgs_server_stats(server)
+        # the small request fits beside the two but may not overtake the third
+        assert (active, queued, finished) == (2, 2, 0)
+        assert st1["bytes_in_use"] == 2 * fp and st1["active"] == 2 and st1["queued"] == 2
+        results = {}
+        for _ in range(400):
+            cgs.cgs_server_step(server, iterations=4)
+            for hh, b, x, t in reqs:
+                if t not in results:
+                    r = cgs.cgs_poll(server, t)
+                    if r is not None:
+                        results[t] = r
+            if len(results) == 4:
+                break
+        assert len(results) == 4
+        assert cgs.cgs_server_stats(server)["bytes_in_use"] == 0
+        for hh, b, x, t in reqs:
+            its, rel, st = results[t]
+            assert st == cgs.OK and rel <= 1e-10 * 1.01
+            x1 = torch.empty_like(x)
+            cgs.cgs_solve(hh.handle, b, x1, rtol=1e-10)
+            xa, xb = x1.cpu().numpy(), x.cpu().numpy()
+            assert np.linalg.norm(xb - xa) / np.linalg.norm(xa) <= 1e-8
+    finally:
+        cgs.cgs_server_free(server)
+        h.free()
+        hsm.free()
