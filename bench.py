@@ -112,21 +112,41 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 
 def algorithmic_bytes(info, prec):
-    """Bytes each kernel must move at least once per launch (every mandatory
-    array once; gathers counted once per vertex)."""
+    """Bytes each kernel class must move at least once per launch: every
+    mandatory array once, each gathered vertex value once, padding not
+    counted.  Mixed forms (fp32/fp16): float-pair outer vectors (8 B),
+    float-pair element matrices (28 x 8 B), lane-pack local solves; FP64 form:
+    float64 everything."""
     E, nv, nr = info["ne"], info["nv"], info["n_r"]
     sm = info["sum_sub_dofs"]
+    nb = info["n_box_entries"]
     sb = 8 if prec == "fp64" else 4
     sl = {"fp64": 8, "fp32": 4, "fp16": 2}[prec]
-    n_sub = info["n_sub"]
     packed = info["_packed_entries"]
+    if prec == "fp64":
+        return {
+            "apply_A64": E * (36 * 8 + 32) + nv * (8 + 16),
+            "local": packed * sl + sm * 4 + nv * (8 + 2 * sb + sb),
+            "restrict": nb * 16 + nv * (32 + sb) + nr * 16,
+            "coarse": nr * nr * 8 + nr * 16,
+            "interp": nb * 16 + nv * (4 + 32 + 2 * sb + 16) + nr * 8,
+            "pcg_xr": nv * (8 * 6 + 2 * sb),
+            "pcg_dots": nv * (sb + 16),
+            "pcg_p": nv * (sb + 24),
+        }
     return {
-        "apply_A64": E * (36 * 8 + 32) + nv * (8 + 16),
-        "apply_A32": E * (28 * 4 + 32) + nv * (4 + 2 * 4),
-        "local": packed * sl + sm * 4 + n_sub * 16 + nv * (8 + 2 * sb + sb),
-        "restrict": E * (32 + 4) + nv * ((32 if prec == "fp64" else 16) + sb) + nr * 16,
-        "coarse": nr * nr * 8 + nr * 16,
-        "interp": E * (32 + 4) + nv * ((32 if prec == "fp64" else 16) + 2 * sb) + nr * 8,
+        # q = A p: hi/lo off-diagonals and 16-bit local indices per element;
+        # p gathered and q written once per vertex
+        "apply_A64": E * (28 * 8 + 16) + nv * (8 + 8),
+        # s -= A l: float off-diagonals and indices; l read, s read and written
+        "apply_A32": E * (28 * 4 + 16) + nv * (4 + 2 * 4),
+        # upper triangles, vertex ids, W_ov; r gathered, z read and written
+        "local": packed * sl + sm * 4 + nv * (4 + sb + 2 * sb),
+        # (vertex, cell, weight) entries; coordinates and s per vertex; r_r pairs
+        "restrict": nb * 12 + nv * (16 + sb) + nr * 8,
+        # per-vertex lists, coordinates, z read and written, r and q pairs (dots)
+        "interp": nv * 8 + nb * 8 + nv * (16 + 2 * sb + 16) + nr * 4,
+        "coarse": nr * nr * 8 + nr * 12,
         "pcg_xr": nv * (8 * 6 + 2 * sb),
         "pcg_dots": nv * (sb + 16),
         "pcg_p": nv * (sb + 24),

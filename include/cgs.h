@@ -68,8 +68,8 @@ typedef enum {
 } cgs_form;
 
 typedef struct {
-    int box[3];            /* b_x, b_y, b_z: box cells per axis over the bounding box
-                              (Sec. 4); each >= 1                                       */
+    int box[3];            /* b_x, b_y, b_z in [1, 1023]: box cells per axis over the
+                              bounding box (Sec. 4)                                    */
     double box_margin;     /* bounding box grown by this fraction of its extent, >= 0  */
     int overlap_layers;    /* delta: element layers added to each Omega_p (Sec. 3), >= 0 */
     cgs_precision prec;
@@ -88,18 +88,22 @@ typedef struct {
     int64_t kernel_launches; /* CUDA kernels this mesh has launched so far           */
     int32_t vert_chunk;    /* schedule: vertices per block of the vector kernels     */
     int32_t sub_chunk;     /* schedule: subdomains per block of the local solves      */
+    int32_t tile_tma;      /* schedule: 1 = element tiles staged by TMA, 0 = streamed  */
+    int64_t n_box_entries; /* (vertex, cell) entries of the per-vertex box lists     */
+    int64_t n_lane_packs;  /* lane packs of the mixed-form local solves (32 each)    */
 } cgs_mesh_info_t;
 
 /* Kernel classes reported by the profiler. */
 typedef enum {
-    CGS_K_APPLY_A64 = 0,   /* y += A x, float64 (outer product A p, FP64 inner apply) */
+    CGS_K_APPLY_A64 = 0,   /* outer product q = A p: float64, or float pairs in the
+                              mixed forms (also the FP64 inner apply)              */
     CGS_K_APPLY_A32 = 1,   /* s -= A l, float32 inner apply                           */
     CGS_K_LOCAL = 2,       /* local solves                                            */
     CGS_K_RESTRICT = 3,    /* r_r = J~^T s                                            */
     CGS_K_COARSE = 4,      /* u_r = A_r^{-1} r_r                                      */
     CGS_K_INTERP = 5,      /* z += J~ u_r                                             */
     CGS_K_PCG_XR = 6,      /* x, r update and ||r||                                   */
-    CGS_K_PCG_DOTS = 7,    /* z.r, z.q                                                */
+    CGS_K_PCG_DOTS = 7,    /* z.r, z.q (inside CGS_K_INTERP when there is a box space) */
     CGS_K_PCG_P = 8,       /* p = z + beta p                                          */
     CGS_K_OTHER = 9,       /* fills, copies, init, final residual                     */
     CGS_K_COUNT = 10
@@ -229,12 +233,18 @@ cgs_status cgs_batch_free(cgs_batch* batch);
 cgs_status cgs_batch_solve(cgs_batch* batch, const double* const* b, double* const* x, double rtol, int maxit,
                            int* iters, double* relres, int* status, void* stream);
 int64_t cgs_batch_launches(const cgs_batch* batch);
-/* Autotuner: time the local solves over subdomain chunks {8,16,32,64} and the
- * vector kernels over vertex chunks {256,...,2048} on the object's own data,
- * keep the fastest schedule (rebuilds the work tables and the loop graph).
+/* Autotuner: time the local solves over subdomain chunks {8,16,32,64}, the
+ * vector kernels over vertex chunks {256,...,2048} and, in the mixed forms,
+ * the tiled operator applies with TMA-staged or thread-streamed element
+ * tiles, on the object's own data; keep the fastest schedule (rebuilds the
+ * work tables and the loop graph).
  * Synchronous; call between solves.  Setup picks a default schedule that
  * gives about four blocks per SM.                                          */
 cgs_status cgs_mesh_tune(cgs_mesh* mesh, void* stream);
+/* Set the schedule explicitly: vert_chunk a multiple of 256 in [256, 8192],
+ * sub_chunk a multiple of 8 in [8, 512], tile_tma 0 or 1 (INVALID_ARG
+ * otherwise).  Synchronous; call between solves.                          */
+cgs_status cgs_mesh_set_schedule(cgs_mesh* mesh, int vert_chunk, int sub_chunk, int tile_tma);
 cgs_status cgs_batch_tune(cgs_batch* batch, void* stream);
 cgs_status cgs_solve_batched(cgs_mesh* const* meshes, int nmesh, const double* const* b, double* const* x,
                              int nrhs, double rtol, int maxit, int* iters, double* relres, void* stream);
@@ -248,7 +258,7 @@ cgs_status cgs_solve_batched(cgs_mesh* const* meshes, int nmesh, const double* c
  * Admission is by device-memory footprint.  The working vectors of every
  * running solve live in one arena of `pool_nv` vertex entries and `pool_nr`
  * reduced (box) entries, allocated at creation.  A request needs nv vertex
- * entries (56 bytes each: x, r, p, y, q and the bulk z, s), n_r reduced
+ * entries (56 bytes each in the FP64 form, 48 in the mixed forms), n_r reduced
  * entries and a few partial-sum entries; it is admitted, in arrival order,
  * when a slot is free and the arena has room for all three (first fit).  A
  * request that waits blocks those behind it (no overtaking), so large

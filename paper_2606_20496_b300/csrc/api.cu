@@ -205,15 +205,25 @@ cgs_status finish(cudaStream_t st, bool sync) {
 }
 
 // z += J~ A_r^{-1} J~^T s  (s: the bulk copy of the residual or of r - A l)
-void box_correction(Engine& E, const Vecs& V, cudaStream_t st) {
+// z += J A_r^{-1} J^T s (r_r = 0 on entry).  dots: the interpolation also
+// forms the PCG dots z.r, z.q and beta.
+void box_correction(Engine& E, const Vecs& V, bool dots, cudaStream_t st) {
     const Plan& P = E.P;
-    K(CGS_K_RESTRICT, launch_restrict(P, V, E.f64, V.s, E.f64, V.rr, st));
-    K(CGS_K_COARSE, launch_coarse(P, V, V.rr, V.ur, E.f64 ? nullptr : V.ur32, st));
-    K(CGS_K_INTERP, launch_interp_add(P, V, E.f64, V.ur, E.f64 ? nullptr : V.ur32, V.z, st));
+    if (E.f64) {
+        K(CGS_K_RESTRICT, launch_restrict(P, V, true, V.s, true, V.rr, false, st));
+        K(CGS_K_COARSE, launch_coarse(P, V, V.rr, V.ur, nullptr, st));
+    } else {
+        // r_r and the reduced product in float pairs, u_r rounded to float
+        K(CGS_K_RESTRICT, launch_restrict(P, V, false, V.s, false, V.rr, true, st));
+        K(CGS_K_COARSE, launch_coarse_pair(P, V, reinterpret_cast<const float2*>(V.rr), nullptr, V.ur32, st));
+    }
+    K(CGS_K_INTERP, launch_interp_add(P, V, E.f64, V.ur, E.f64 ? nullptr : V.ur32, V.z, dots, st));
 }
 
-// z (bulk) = M r, with z = 0, s = r (bulk) and r_r = 0 on entry.
-void precond_body(Engine& E, const Vecs& V, cudaStream_t st) {
+// z (bulk) = M r, with z = 0, s = r (bulk) and r_r = 0 on entry.  dots: also
+// the PCG dots (fused into the interpolation when there is a reduced space);
+// returns whether they were formed.
+bool precond_body(Engine& E, const Vecs& V, cudaStream_t st, bool dots = false) {
     const Plan& P = E.P;
     if (E.form == CGS_HYBRID) {
         K(CGS_K_LOCAL, launch_local(P, V, E.prec, V.s, V.z, true, st));
@@ -223,36 +233,51 @@ void precond_body(Engine& E, const Vecs& V, cudaStream_t st) {
         else
             K(CGS_K_APPLY_A32,
               launch_apply28f_tiled(P, V, static_cast<const float*>(V.z), static_cast<float*>(V.s), -1.0f, st));
-        if (P.any_nr) box_correction(E, V, st);
     } else {
         K(CGS_K_LOCAL, launch_local(P, V, E.prec, V.s, V.z, false, st));
-        if (P.any_nr) box_correction(E, V, st);
     }
+    if (!P.any_nr) return false;
+    box_correction(E, V, dots, st);
+    return dots;
 }
 
-// One flexible-PCG iteration over every slot of the engine.
-template <typename Tz>
+// One flexible-PCG iteration over every slot of the engine: float64 vectors
+// in the FP64 form, float-pair vectors in the mixed forms.
 void pcg_iteration(Engine& E, cudaStream_t st) {
     const Plan& P = E.P;
     const Vecs& V = E.V;
     if (E.f64) {
         K(CGS_K_APPLY_A64, launch_apply64(P, V, V.p, V.q, 1.0, true, st));
-        K(CGS_K_PCG_XR, (launch_pcg_update_xr<Tz, double>(P, V, V.q, st)));
-        precond_body(E, V, st);
-        K(CGS_K_PCG_DOTS, (launch_pcg_dots<Tz, double>(P, V, V.q, st)));
-        K(CGS_K_PCG_P, (launch_pcg_update_p<Tz, double>(P, V, V.q, st)));
+        K(CGS_K_PCG_XR, (launch_pcg_update_xr<double, double>(P, V, V.q, st)));
+        if (!precond_body(E, V, st, true)) K(CGS_K_PCG_DOTS, (launch_pcg_dots<double, double>(P, V, V.q, st)));
+        K(CGS_K_PCG_P, (launch_pcg_update_p<double, double>(P, V, V.q, st)));
     } else {
         K(CGS_K_APPLY_A64, launch_apply_pair_tiled(P, V, st));
-        K(CGS_K_PCG_XR, (launch_pcg_update_xr<Tz, float2>(P, V, V.q2, st)));
-        precond_body(E, V, st);
-        K(CGS_K_PCG_DOTS, (launch_pcg_dots<Tz, float2>(P, V, V.q2, st)));
-        K(CGS_K_PCG_P, (launch_pcg_update_p<Tz, float2>(P, V, V.q2, st)));
+        K(CGS_K_PCG_XR, launch_pcg_update_xr_pair(P, V, st));
+        if (!precond_body(E, V, st, true)) K(CGS_K_PCG_DOTS, launch_pcg_dots_pair(P, V, st));
+        K(CGS_K_PCG_P, launch_pcg_update_p_pair(P, V, st));
     }
+}
+
+// Start every slot of the plan: r = b, x = 0, z = M r, p = z, rho = r.z.
+void pcg_start(Engine& E, const Plan& P, double rtol, int maxit, cudaStream_t st) {
+    const Vecs& V = E.V;
+    if (E.f64) {
+        K(CGS_K_OTHER, launch_pcg_init<double>(P, V, V.q, rtol, maxit, st));
+        K(CGS_K_OTHER, launch_precond_prep<double>(P, V, V.r, st));
+    } else {
+        K(CGS_K_OTHER, launch_pcg_init_pair(P, V, rtol, maxit, st));
+        K(CGS_K_OTHER, launch_precond_prep_pair(P, V, st));
+    }
+    precond_body(E, V, st);
+    if (E.f64)
+        K(CGS_K_OTHER, launch_pcg_first_dir<double>(P, V, st));
+    else
+        K(CGS_K_OTHER, launch_pcg_first_dir_pair(P, V, st));
 }
 
 // Build the graph: one while node whose body is one PCG iteration over all
 // slots plus the condition kernel (continue while some slot runs).
-template <typename Tz>
 cgs_status build_loop_graph(Engine& E) {
     cudaStream_t cs = nullptr;
     cudaGraph_t g = nullptr;
@@ -289,7 +314,7 @@ cgs_status build_loop_graph(Engine& E) {
     E.prof = false;
     {
         cudaStream_t st = cs;
-        pcg_iteration<Tz>(E, st);
+        pcg_iteration(E, st);
         launch_loop_cond(E.P, E.V, h, st);
     }
     E.prof = prof;
@@ -308,20 +333,13 @@ cgs_status build_loop_graph(Engine& E) {
 // Solve every slot of the engine: V.b / V.bptr give the right-hand sides,
 // the iterates stay in V.x (copied out through V.xptr when set).  On return
 // E.S_host holds every slot's scalars (iters, status, res2, b2).
-template <typename Tz>
 cgs_status engine_solve(Engine& E, double rtol, int maxit, cudaStream_t st) {
     const Plan& P = E.P;
     const Vecs& V = E.V;
-    if (E.f64)
-        K(CGS_K_OTHER, launch_pcg_init<double>(P, V, V.q, rtol, maxit, st));
-    else
-        K(CGS_K_OTHER, launch_pcg_init<float2>(P, V, V.q2, rtol, maxit, st));
-    K(CGS_K_OTHER, launch_precond_prep<Tz>(P, V, V.r, st));
-    precond_body(E, V, st);
-    K(CGS_K_OTHER, launch_pcg_first_dir<Tz>(P, V, st));
+    pcg_start(E, P, rtol, maxit, st);
     const bool use_graph = !E.prof && !E.graph_failed;
     if (use_graph && !E.gexec) {
-        if (build_loop_graph<Tz>(E) != CGS_OK) E.graph_failed = true;
+        if (build_loop_graph(E) != CGS_OK) E.graph_failed = true;
     }
     const size_t sbytes = sizeof(SolveScalars) * (size_t)P.nslots;
     if (use_graph && E.gexec) {
@@ -333,7 +351,7 @@ cgs_status engine_solve(Engine& E, double rtol, int maxit, cudaStream_t st) {
         int chunk = std::max(2, E.last_iters);
         for (;;) {
             const int n = std::min(chunk, maxit - enqueued);
-            for (int i = 0; i < n; ++i) pcg_iteration<Tz>(E, st);
+            for (int i = 0; i < n; ++i) pcg_iteration(E, st);
             enqueued += n;
             CGS_CUDA(cudaMemcpyAsync(E.S_host, V.S, sbytes, cudaMemcpyDeviceToHost, st));
             CGS_CUDA(cudaStreamSynchronize(st));
@@ -345,8 +363,9 @@ cgs_status engine_solve(Engine& E, double rtol, int maxit, cudaStream_t st) {
     }
     // the true residual ||b - A x|| over the free entries (and copy-out)
     const Vecs Vn = no_stop(V);
+    if (!E.f64) K(CGS_K_OTHER, launch_finalize_x_pair(P, V, st));
     launch_fill_d(E.total_v, V.y, 0.0, st);
-    K(CGS_K_APPLY_A64, launch_apply64(P, Vn, V.x, V.y, 1.0, false, st));
+    K(CGS_K_OTHER, launch_apply64(P, Vn, V.x, V.y, 1.0, false, st));
     K(CGS_K_OTHER, launch_resid_norm(P, V, st));
     CGS_CUDA(cudaMemcpyAsync(E.S_host, V.S, sbytes, cudaMemcpyDeviceToHost, st));
     cgs_status fs = finish(st, true);
@@ -387,7 +406,7 @@ cudaError_t alloc_pools(DevAllocs& mem, Engine& E, int64_t total_v, int64_t tota
         V.s = s;
     } else {
         TRY(mem.alloc(&V.q2, total_v));
-        TRY(mem.alloc(&V.p2, total_v));
+        V.p2 = reinterpret_cast<float2*>(V.p);   // p is a float pair in the mixed forms
         float *z, *s;
         TRY(mem.alloc(&z, total_v));
         TRY(mem.alloc(&s, total_v));
@@ -429,6 +448,7 @@ cudaError_t set_schedule(Engine& E, const Schedule& sch) {
     }
     E.tables.release();
     E.tables = fresh;
+    P.tile_tma = sch.tile_tma != 0;
     E.P = P;
     E.sch = sch;
     if (E.gexec) {   // the captured loop holds the old grid sizes
@@ -477,11 +497,28 @@ cgs_status tune_engine(Engine& E, cudaStream_t st) {
             if (E.f64)
                 launch_precond_prep<double>(E.P, V, V.r, st);
             else
-                launch_precond_prep<float>(E.P, V, V.r, st);
+                launch_precond_prep_pair(E.P, V, st);
         });
         if (ms < best_vert) {
             best_vert = ms;
             best.vert_chunk = vc;
+        }
+    }
+    // mixed forms: element tiles staged by TMA or streamed by the threads
+    if (!E.f64) {
+        float best_tile = 1e30f;
+        for (int tma = 0; tma < 2; ++tma) {
+            Schedule t = best;
+            t.tile_tma = tma;
+            if (set_schedule(E, t) != cudaSuccess) continue;
+            const float ms = time_it([&]() {
+                launch_apply_pair_tiled(E.P, V, st);
+                launch_apply28f_tiled(E.P, V, static_cast<const float*>(V.z), static_cast<float*>(V.s), -1.0f, st);
+            });
+            if (ms < best_tile) {
+                best_tile = ms;
+                best.tile_tma = tma;
+            }
         }
     }
     cudaEventDestroy(a);
@@ -568,7 +605,8 @@ cgs_status cgs_mesh_setup(cgs_ctx* ctx, const double* xyz, int64_t nv, const int
     const size_t bulk = f64 ? 8 : 4;
     const size_t est = (size_t)ne * (8 * 4 + kUpper * 8 + 4) + (f64 ? 0 : hs.at_hi.size() * 8 + (size_t)ne * 16) +
                        (size_t)nv * (32 + 16 + 1 + 8 + 4) + hs.sub_idx.size() * 4 +
-                       hs.inv.size() * (f64 ? 8 : prm.prec == CGS_FP32_BULK ? 4 : 2) + hs.ar_inv.size() * 8 +
+                       (hs.inv.size() + hs.pack_inv.size()) * (f64 ? 8 : prm.prec == CGS_FP32_BULK ? 4 : 2) +
+                       hs.pack_idx.size() * 4 + hs.ar_inv.size() * 8 +
                        (size_t)nv * (5 * 8 + 2 * bulk);
     {
         std::lock_guard<std::mutex> lk(ctx->mu);
@@ -583,15 +621,18 @@ cgs_status cgs_mesh_setup(cgs_ctx* ctx, const double* xyz, int64_t nv, const int
     DevMesh& d = m->d;
     d.nv = nv;
     d.ne = ne;
-    d.n_sub = hs.n_sub;
+    d.n_sub = hs.n_wsub;
+    d.n_pack = (int64_t)hs.pack_m.size();
     d.nr = hs.nr;
     for (int k = 0; k < 3; ++k) {
         d.b[k] = hs.b[k];
         d.lo[k] = 0.0;   // coordinates are stored relative to the box origin
         d.H[k] = hs.H[k];
         d.iH[k] = 1.0 / hs.H[k];
+        d.Hf[k] = (float)d.H[k];
+        d.iHf[k] = (float)d.iH[k];
     }
-    d.max_m = (int)hs.max_m;
+    d.max_m = (int)hs.max_wm;
 
     auto cleanup = [&](cgs_status s) {
         m->E.release();
@@ -618,11 +659,27 @@ cgs_status cgs_mesh_setup(cgs_ctx* ctx, const double* xyz, int64_t nv, const int
         UP(d.at_lo, hs.at_lo);
     }
     UP(d.cell_cols, hs.cell_cols);
+    d.nvb = (int64_t)hs.vb_vert.size();
+    if (d.nvb) {
+        UP(d.vb_vert, hs.vb_vert);
+        UP(d.vb_ptr, hs.vb_ptr);
+        UP(d.vb_cell, hs.vb_cell);
+        d.nre = (int64_t)hs.re_vert.size();
+        UP(d.re_vert, hs.re_vert);
+        UP(d.re_cell, hs.re_cell);
+        if (f64) {
+            UP(d.vb_w64, hs.vb_w);
+            UP(d.re_w64, hs.re_w);
+        } else {
+            UP(d.vb_w32, std::vector<float>(hs.vb_w.begin(), hs.vb_w.end()));
+            UP(d.re_w32, std::vector<float>(hs.re_w.begin(), hs.re_w.end()));
+        }
+    }
     {
-        std::vector<int32_t> sp(hs.sub_ptr.begin(), hs.sub_ptr.end());
+        std::vector<int32_t> sp(hs.wsub_ptr.begin(), hs.wsub_ptr.end());
         UP(d.sub_ptr, sp);
     }
-    UP(d.sub_idx, hs.sub_idx);
+    UP(d.sub_idx, hs.wsub_idx);
     UP(d.inv_ptr, hs.inv_ptr);
     if (prm.prec == CGS_FP64) {
         UP(d.inv64, hs.inv);
@@ -631,8 +688,8 @@ cgs_status cgs_mesh_setup(cgs_ctx* ctx, const double* xyz, int64_t nv, const int
         UP(d.inv32, f);
     } else {
         std::vector<__half> h(hs.inv.size());
-        std::vector<float> sc(hs.n_sub, 1.0f);
-        for (int64_t p = 0; p < hs.n_sub; ++p) {
+        std::vector<float> sc(hs.n_wsub, 1.0f);
+        for (int64_t p = 0; p < hs.n_wsub; ++p) {
             double mx = 0.0;
             for (int64_t i = hs.inv_ptr[p]; i < hs.inv_ptr[p + 1]; ++i) mx = std::max(mx, std::fabs(hs.inv[i]));
             const double s = mx > 0 ? mx : 1.0;
@@ -641,6 +698,41 @@ cgs_status cgs_mesh_setup(cgs_ctx* ctx, const double* xyz, int64_t nv, const int
         }
         UP(d.inv16, h);
         UP(d.inv16_scale, sc);
+    }
+    if (d.n_pack) {
+        // lane packs: host [pack][lane][entry] -> device groups across lanes
+        const int64_t np = d.n_pack;
+        UP(d.pack_m, hs.pack_m);
+        UP(d.pack_idx_off, std::vector<int64_t>(hs.pack_idx_off.begin(), hs.pack_idx_off.end() - 1));
+        UP(d.pack_inv_off, std::vector<int64_t>(hs.pack_inv_off.begin(), hs.pack_inv_off.end() - 1));
+        UP(d.pack_idx, hs.pack_idx);
+        const size_t total = hs.pack_inv.size();
+        if (prm.prec == CGS_FP32_BULK) {
+            std::vector<float> f(total);
+            for (int64_t P = 0; P < np; ++P) {
+                const int64_t ao = hs.pack_inv_off[P], T = lane_entries(hs.pack_m[P]);
+                for (int l = 0; l < 32; ++l)
+                    for (int64_t e = 0; e < T; ++e)
+                        f[ao + (e / 4) * 128 + l * 4 + e % 4] = (float)hs.pack_inv[ao + l * T + e];
+            }
+            UP(d.pack_inv32, f);
+        } else {
+            std::vector<__half> h(total);
+            std::vector<float> sc((size_t)np * 32, 1.0f);
+            for (int64_t P = 0; P < np; ++P) {
+                const int64_t ao = hs.pack_inv_off[P], T = lane_entries(hs.pack_m[P]);
+                for (int l = 0; l < 32; ++l) {
+                    double mx = 0.0;
+                    for (int64_t e = 0; e < T; ++e) mx = std::max(mx, std::fabs(hs.pack_inv[ao + l * T + e]));
+                    const double s = mx > 0 ? mx : 1.0;
+                    sc[(size_t)P * 32 + l] = (float)s;
+                    for (int64_t e = 0; e < T; ++e)
+                        h[ao + (e / 8) * 256 + l * 8 + e % 8] = __float2half_rn((float)(hs.pack_inv[ao + l * T + e] / s));
+                }
+            }
+            UP(d.pack_inv16, h);
+            UP(d.pack_scale, sc);
+        }
     }
     UP(d.wov64, hs.wov);
     if (!f64) {
@@ -667,7 +759,22 @@ cgs_status cgs_mesh_setup(cgs_ctx* ctx, const double* xyz, int64_t nv, const int
             d.xyzwf = reinterpret_cast<const float4*>(p);
         }
     }
-    if (hs.nr) UP(d.ar_inv, hs.ar_inv);
+    if (hs.nr && f64) {
+        UP(d.ar_inv, hs.ar_inv);
+    } else if (hs.nr) {
+        // hi = entry rounded to float, lo = the rounded remainder; rows padded
+        // to an even length (16-byte aligned row starts)
+        const int64_t nr = hs.nr, nr2 = (nr + 1) / 2 * 2;
+        std::vector<float2> a2((size_t)nr * nr2, make_float2(0.0f, 0.0f));
+        for (int64_t i = 0; i < nr; ++i)
+            for (int64_t j = 0; j < nr; ++j) {
+                const double a = hs.ar_inv[(size_t)i * nr + j];
+                const float h = (float)a;
+                a2[(size_t)i * nr2 + j] = make_float2(h, (float)(a - (double)h));
+            }
+        d.nr2 = nr2;
+        UP(d.ar_inv2, a2);
+    }
     UP(d.dir, hs.dir);
     {
         const DevMesh* dd = nullptr;
@@ -675,7 +782,7 @@ cgs_status cgs_mesh_setup(cgs_ctx* ctx, const double* xyz, int64_t nv, const int
         m->d_dev = const_cast<DevMesh*>(dd);
     }
     // one solve slot and its work tables
-    m->sizes = MeshSizes{nv, ne, d.ntiles, hs.n_sub, hs.nr};
+    m->sizes = MeshSizes{nv, ne, d.ntiles, hs.n_wsub, hs.nr, d.n_pack, d.nvb, d.nre};
     Engine& E = m->E;
     E.f64 = f64;
     E.prec = prm.prec;
@@ -694,7 +801,7 @@ cgs_status cgs_mesh_setup(cgs_ctx* ctx, const double* xyz, int64_t nv, const int
         smallest.sub_chunk = 8;
         cudaError_t e = alloc_pools(m->mem, E, nv, hs.nr, mesh_partial_slots(sz, smallest), 1);
         if (e != cudaSuccess) return cleanup(cuda_fail(e, "scratch"));
-        e = set_schedule(E, default_schedule(nv, hs.n_sub));
+        e = set_schedule(E, default_schedule(nv, hs.n_wsub, d.n_pack));
         if (e != cudaSuccess) return cleanup(cuda_fail(e, "work tables"));
     }
     {
@@ -720,6 +827,8 @@ cgs_status cgs_mesh_setup(cgs_ctx* ctx, const double* xyz, int64_t nv, const int
     m->info.n_r = hs.nr;
     m->info.max_sub_dofs = hs.max_m;
     m->info.sum_sub_dofs = hs.sum_m;
+    m->info.n_box_entries = (int64_t)hs.vb_cell.size();
+    m->info.n_lane_packs = (int64_t)hs.pack_m.size();
     m->info.footprint_bytes = m->mem.bytes;
     m->info.setup_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     *out = m;
@@ -749,6 +858,7 @@ cgs_status cgs_mesh_info(const cgs_mesh* m, cgs_mesh_info_t* info) {
     info->kernel_launches = m->E.launches;
     info->vert_chunk = m->E.sch.vert_chunk;
     info->sub_chunk = m->E.sch.sub_chunk;
+    info->tile_tma = m->E.sch.tile_tma;
     return CGS_OK;
 }
 
@@ -838,7 +948,7 @@ cgs_status cgs_restrict(cgs_mesh* m, const double* s, double* rr, void* stream) 
     Engine& E = m->E;
     const Vecs V = no_stop(E.V);
     K(CGS_K_OTHER, launch_fill_d(m->d.nr, rr, 0.0, st));
-    K(CGS_K_RESTRICT, launch_restrict(E.P, V, m->fp64(), s, true, rr, st));
+    K(CGS_K_RESTRICT, launch_restrict(E.P, V, m->fp64(), s, true, rr, false, st));
     return finish(st, false);
 }
 
@@ -847,7 +957,14 @@ cgs_status cgs_coarse_solve(cgs_mesh* m, const double* rr, double* ur, void* str
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     Engine& E = m->E;
     const Vecs V = no_stop(E.V);
-    K(CGS_K_COARSE, launch_coarse(E.P, V, rr, ur, nullptr, st));
+    if (m->fp64()) {
+        K(CGS_K_COARSE, launch_coarse(E.P, V, rr, ur, nullptr, st));
+    } else {
+        // the mixed forms keep A_r^{-1} as float pairs: r_r -> pairs first
+        float2* rr2 = reinterpret_cast<float2*>(V.rr);
+        K(CGS_K_OTHER, launch_split_pair(m->d.nr, rr, rr2, st));
+        K(CGS_K_COARSE, launch_coarse_pair(E.P, V, rr2, ur, nullptr, st));
+    }
     return finish(st, false);
 }
 
@@ -858,11 +975,11 @@ cgs_status cgs_interp(cgs_mesh* m, const double* ur, double* z, void* stream) {
     const Vecs V = no_stop(E.V);
     if (m->fp64()) {
         K(CGS_K_OTHER, launch_fill_d(m->d.nv, static_cast<double*>(V.z), 0.0, st));
-        K(CGS_K_INTERP, launch_interp_add(E.P, V, true, ur, nullptr, V.z, st));
+        K(CGS_K_INTERP, launch_interp_add(E.P, V, true, ur, nullptr, V.z, false, st));
         K(CGS_K_OTHER, launch_copy_d(E.P, static_cast<const double*>(V.z), z, true, st));
     } else {
         K(CGS_K_OTHER, launch_fill_f(m->d.nv, static_cast<float*>(V.z), 0.0f, st));
-        K(CGS_K_INTERP, launch_interp_add(E.P, V, false, ur, nullptr, V.z, st));
+        K(CGS_K_INTERP, launch_interp_add(E.P, V, false, ur, nullptr, V.z, false, st));
         K(CGS_K_OTHER, launch_convert_f2d(E.P, static_cast<const float*>(V.z), z, true, st));
     }
     return finish(st, false);
@@ -900,7 +1017,7 @@ cgs_status cgs_solve(cgs_mesh* m, const double* b, double* x, int nrhs, double r
         iters[k] = 0;
         relres[k] = 0.0;
         E.V.b = bk;
-        cgs_status s = m->fp64() ? engine_solve<double>(E, rtol, maxit, st) : engine_solve<float>(E, rtol, maxit, st);
+        cgs_status s = engine_solve(E, rtol, maxit, st);
         E.V.b = nullptr;
         if (s != CGS_OK) return s;
         K(CGS_K_OTHER, launch_copy_d(E.P, E.V.x, xk, false, st));
@@ -971,7 +1088,7 @@ cgs_status cgs_batch_create(cgs_ctx* ctx, cgs_mesh* const* meshes, int nmesh, in
     const int nslots = nmesh * nrhs;
     std::vector<DevMesh> descs(nmesh);
     std::vector<MeshSizes> sizes(nmesh);
-    int64_t total_v = 0, total_r = 0, total_sub = 0;
+    int64_t total_v = 0, total_r = 0, total_sub = 0, total_pack = 0;
     for (int i = 0; i < nmesh; ++i) {
         const cgs_mesh* m = meshes[i];
         descs[i] = m->d;
@@ -982,6 +1099,7 @@ cgs_status cgs_batch_create(cgs_ctx* ctx, cgs_mesh* const* meshes, int nmesh, in
         total_v += (int64_t)nrhs * m->d.nv;
         total_r += (int64_t)nrhs * m->d.nr;
         total_sub += (int64_t)nrhs * m->d.n_sub;
+        total_pack += (int64_t)nrhs * m->d.n_pack;
     }
     // the slots of one mesh are interleaved item by item so that blocks
     // reading the same tile run together (the repeats hit L2)
@@ -1025,7 +1143,7 @@ cgs_status cgs_batch_create(cgs_ctx* ctx, cgs_mesh* const* meshes, int nmesh, in
         E.P.nslots = nslots;
         if ((e = alloc_pools(B->mem, E, total_v, total_r, total_p, nslots)) != cudaSuccess)
             return cleanup(cuda_fail(e, "pools"));
-        if ((e = set_schedule(E, default_schedule(total_v, total_sub))) != cudaSuccess)
+        if ((e = set_schedule(E, default_schedule(total_v, total_sub, total_pack))) != cudaSuccess)
             return cleanup(cuda_fail(e, "work tables"));
         if ((e = B->mem.alloc(&B->bptr_d, nslots)) != cudaSuccess) return cleanup(cuda_fail(e, "pointers"));
         if ((e = B->mem.alloc(&B->xptr_d, nslots)) != cudaSuccess) return cleanup(cuda_fail(e, "pointers"));
@@ -1077,7 +1195,7 @@ cgs_status cgs_batch_solve(cgs_batch* B, const double* const* b, double* const* 
     }
     CGS_CUDA(cudaMemcpyAsync(B->bptr_d, B->bptr_h, sizeof(double*) * nslots, cudaMemcpyHostToDevice, st));
     CGS_CUDA(cudaMemcpyAsync(B->xptr_d, B->xptr_h, sizeof(double*) * nslots, cudaMemcpyHostToDevice, st));
-    cgs_status s = E.f64 ? engine_solve<double>(E, rtol, maxit, st) : engine_solve<float>(E, rtol, maxit, st);
+    cgs_status s = engine_solve(E, rtol, maxit, st);
     if (s != CGS_OK) return s;
     cgs_status first_bad = CGS_OK;
     for (int k = 0; k < nslots; ++k) {
@@ -1092,6 +1210,20 @@ cgs_status cgs_batch_solve(cgs_batch* B, const double* const* b, double* const* 
 }
 
 int64_t cgs_batch_launches(const cgs_batch* B) { return B ? B->E.launches : 0; }
+
+cgs_status cgs_mesh_set_schedule(cgs_mesh* m, int vert_chunk, int sub_chunk, int tile_tma) {
+    if (!m) return fail(CGS_ERR_INVALID_ARG, "null mesh");
+    if (vert_chunk < 256 || vert_chunk > 8192 || vert_chunk % 256 || sub_chunk < 8 || sub_chunk > 512 ||
+        sub_chunk % 8 || (tile_tma != 0 && tile_tma != 1))
+        return fail(CGS_ERR_INVALID_ARG, "schedule out of range");
+    CGS_CUDA(cudaSetDevice(m->ctx->device));
+    Schedule sch;
+    sch.vert_chunk = vert_chunk;
+    sch.sub_chunk = sub_chunk;
+    sch.tile_tma = tile_tma;
+    CGS_CUDA(set_schedule(m->E, sch));
+    return CGS_OK;
+}
 
 cgs_status cgs_mesh_tune(cgs_mesh* m, void* stream) {
     if (!m) return fail(CGS_ERR_INVALID_ARG, "null mesh");
@@ -1248,6 +1380,7 @@ cudaError_t server_tables(cgs_server* sv, const std::vector<int>& ids, cgs_serve
     P.meshes = sv->reg_d;
     P.nslots = sv->max_slots;
     P.wait_limit = sv->E.P.wait_limit;
+    P.tile_tma = sv->sch.tile_tma != 0;
     for (int k : ids) {
         const cgs_server::SlotState& ss = sv->slots[k];
         const cgs_mesh* m = ss.req.mesh;
@@ -1314,7 +1447,7 @@ cgs_status cgs_server_create(cgs_ctx* ctx, int max_slots, int64_t pool_nv, int64
     sv->av.init((pool_nv + 31) / 32 * 32, 32);
     sv->ar.init((pool_nr + 7) / 8 * 8 + 8 * max_slots, 8);
     sv->ap.init(2 * ((pool_nv + 127) / 128) + 64 * (int64_t)max_slots, 8);
-    sv->bytes_per_v = 4 * sizeof(double) + (prec == CGS_FP64 ? 3 * sizeof(double) : 2 * sizeof(float2) + 2 * sizeof(float));
+    sv->bytes_per_v = 4 * sizeof(double) + (prec == CGS_FP64 ? 3 * sizeof(double) : sizeof(float2) + 2 * sizeof(float));
     sv->bytes_per_r = 2 * sizeof(double) + (prec == CGS_FP64 ? 0 : sizeof(float));
     sv->rtol = rtol;
     sv->maxit = maxit;
@@ -1353,7 +1486,7 @@ cgs_status cgs_server_create(cgs_ctx* ctx, int max_slots, int64_t pool_nv, int64
         sv->xptr_h[k] = nullptr;
     }
     // chunks sized for the whole arena as one problem: many slots at once
-    sv->sch = default_schedule(pool_nv, pool_nv / 8);
+    sv->sch = default_schedule(pool_nv, pool_nv / 8, pool_nv / 256);
     E.V.bptr = sv->bptr_d;
     E.V.xptr = sv->xptr_d;
     {
@@ -1465,29 +1598,12 @@ cgs_status cgs_server_step(cgs_server* sv, int iterations, void* stream, int* ac
     // 2. start the new slots: r = b, z = M r, p = z
     if (!fresh.empty()) {
         E.P = sv->P_admit;
-        const Plan& P = E.P;
-        const Vecs& V = E.V;
-        if (E.f64) {
-            K(CGS_K_OTHER, launch_pcg_init<double>(P, V, V.q, sv->rtol, sv->maxit, st));
-            K(CGS_K_OTHER, launch_precond_prep<double>(P, V, V.r, st));
-            precond_body(E, V, st);
-            K(CGS_K_OTHER, launch_pcg_first_dir<double>(P, V, st));
-        } else {
-            K(CGS_K_OTHER, launch_pcg_init<float2>(P, V, V.q2, sv->rtol, sv->maxit, st));
-            K(CGS_K_OTHER, launch_precond_prep<float>(P, V, V.r, st));
-            precond_body(E, V, st);
-            K(CGS_K_OTHER, launch_pcg_first_dir<float>(P, V, st));
-        }
+        pcg_start(E, E.P, sv->rtol, sv->maxit, st);
     }
     // 3. iterate every running slot (slots that stop skip their blocks)
     if (!busy.empty()) {
         E.P = sv->P_main;
-        for (int i = 0; i < iterations; ++i) {
-            if (E.f64)
-                pcg_iteration<double>(E, st);
-            else
-                pcg_iteration<float>(E, st);
-        }
+        for (int i = 0; i < iterations; ++i) pcg_iteration(E, st);
     }
     CGS_CUDA(cudaMemcpyAsync(E.S_host, E.V.S, sizeof(SolveScalars) * sv->max_slots, cudaMemcpyDeviceToHost, st));
     CGS_CUDA(cudaStreamSynchronize(st));
@@ -1499,9 +1615,10 @@ cgs_status cgs_server_step(cgs_server* sv, int iterations, void* stream, int* ac
         CGS_CUDA(server_tables(sv, done, sv->t_fin, sv->P_fin, st));
         E.P = sv->P_fin;
         const Vecs Vn = no_stop(E.V);
+        if (!E.f64) K(CGS_K_OTHER, launch_finalize_x_pair(E.P, E.V, st));
         for (int k : done)
             CGS_CUDA(cudaMemsetAsync(E.V.y + sv->slots[k].voff, 0, sizeof(double) * sv->slots[k].req.mesh->d.nv, st));
-        K(CGS_K_APPLY_A64, launch_apply64(E.P, Vn, E.V.x, E.V.y, 1.0, false, st));
+        K(CGS_K_OTHER, launch_apply64(E.P, Vn, E.V.x, E.V.y, 1.0, false, st));
         K(CGS_K_OTHER, launch_resid_norm(E.P, E.V, st));
         CGS_CUDA(cudaMemcpyAsync(E.S_host, E.V.S, sizeof(SolveScalars) * sv->max_slots, cudaMemcpyDeviceToHost, st));
         CGS_CUDA(cudaStreamSynchronize(st));

@@ -39,8 +39,19 @@ struct HostSetup {
     // subdomains, in caller order
     std::vector<int64_t> sub_ptr;      // n_sub+1
     std::vector<int32_t> sub_idx;      // sum_m, ascending vertex ids per subdomain
-    std::vector<int64_t> inv_ptr;      // n_sub+1, offsets (entries) of packed inverses
-    std::vector<double> inv;           // packed lower triangle, row-major, float64
+    // subdomains solved by the warp kernels (all of them in the FP64 form,
+    // those with more than kLaneMaxM dofs in the mixed forms), caller order
+    int64_t n_wsub = 0, max_wm = 0;
+    std::vector<int64_t> wsub_ptr;     // n_wsub+1
+    std::vector<int32_t> wsub_idx;
+    std::vector<int64_t> inv_ptr;      // n_wsub+1, offsets (entries) of the inverses
+    std::vector<double> inv;           // cyclic diagonals (i, (i+d) mod m) at d*m + i, float64
+    // lane packs (mixed forms): 32 subdomains of one size class, one per lane
+    std::vector<int32_t> pack_m;       // n_pack, class size
+    std::vector<int64_t> pack_idx_off; // n_pack+1, offsets into pack_idx (32*M per pack)
+    std::vector<int64_t> pack_inv_off; // n_pack+1, offsets into pack_inv (32*lane_entries(M) per pack)
+    std::vector<int32_t> pack_idx;     // [pack][k][lane] vertex id, -1 = padding
+    std::vector<double> pack_inv;      // [pack][lane][lane_entries(M)] upper triangle, row-major, float64
     // box coarse space
     int b[3] = {1, 1, 1};
     double lo[3] = {0, 0, 0}, H[3] = {1, 1, 1};
@@ -49,8 +60,15 @@ struct HostSetup {
     std::vector<int32_t> tile_vptr;    // ntiles+1, ranges in tile_verts
     std::vector<uint32_t> tile_verts;  // distinct free vertices of each tile, | kSharedBit if shared
     std::vector<uint16_t> eloc;        // ne*8, tile-local vertex index, 0xFFFF = Dirichlet
-    std::vector<float> at_hi, at_lo;   // [ntiles][kOff][kTileElems] tile-major off-diagonals (float, remainder)
+    std::vector<float> at_hi, at_lo;   // [ntiles][kOff/4][kTileElems][4] tile-major off-diagonals (float, remainder)
     std::vector<int32_t> cell_cols;    // ncell*8, active column of each cell corner or -1
+    // per-vertex box lists (restriction and interpolation by vertex)
+    std::vector<int32_t> vb_vert;      // free vertices with elements, by first cell
+    std::vector<int32_t> vb_ptr;       // +1, ranges in vb_cell / vb_w
+    std::vector<int32_t> vb_cell;      // cells of the vertex's elements, ascending (packed coordinates)
+    std::vector<double> vb_w;          // elements of the vertex in that cell / elements of the vertex
+    std::vector<int32_t> re_vert, re_cell;   // the same entries sorted by cell (restriction)
+    std::vector<double> re_w;
     std::vector<int64_t> box_active;   // nr, lexicographic box-vertex ids
     std::vector<double> ar_inv;        // nr*nr, A_r^{-1}, full symmetric, float64
     double seconds = 0.0;
@@ -66,6 +84,7 @@ struct DevMesh {
     int64_t nv = 0, ne = 0, n_sub = 0, nr = 0;
     int b[3] = {1, 1, 1};
     double lo[3] = {0, 0, 0}, H[3] = {1, 1, 1}, iH[3] = {1, 1, 1};
+    float Hf[3] = {1, 1, 1}, iHf[3] = {1, 1, 1};   // the same, rounded to float
     const int32_t* conn = nullptr;     // ne*8 (int4 x2 per element)
     const uint8_t* dir = nullptr;      // nv, 1 = Dirichlet
     const double* a36 = nullptr;       // [36][ne]
@@ -77,10 +96,24 @@ struct DevMesh {
     const int32_t* tile_vptr = nullptr;
     const uint32_t* tile_verts = nullptr;
     const uint16_t* eloc = nullptr;
-    const float* at_hi = nullptr;      // [ntiles][28][256] off-diagonals rounded to float, tile-major
+    const float* at_hi = nullptr;      // [ntiles][7][256][4] off-diagonals rounded to float, tile-major
     const float* at_lo = nullptr;      // same layout, float remainders (outer operator only)
     const int32_t* cell_cols = nullptr;// ncell*8
-    // subdomains grouped by size class for the warp kernels
+    // per-vertex box lists: vertex, its (cell, weight) entries
+    int64_t nvb = 0;
+    const int32_t* vb_vert = nullptr;  // nvb
+    const int32_t* vb_ptr = nullptr;   // nvb+1
+    const int32_t* vb_cell = nullptr;  // packed cell coordinates ci | cj << 10 | ck << 20
+    const double* vb_w64 = nullptr;    // FP64 form
+    const float* vb_w32 = nullptr;     // mixed forms
+    // the same (vertex, cell, weight) entries sorted by cell
+    int64_t nre = 0;
+    const int32_t* re_vert = nullptr;
+    const int32_t* re_cell = nullptr;  // packed, as vb_cell
+    const double* re_w64 = nullptr;
+    const float* re_w32 = nullptr;
+    // subdomains of the warp kernels (n_sub of them: all in the FP64 form,
+    // those with more than kLaneMaxM dofs in the mixed forms)
     const int32_t* sub_ptr = nullptr;  // n_sub+1 (int32 offsets into sub_idx)
     const int32_t* sub_idx = nullptr;
     const int64_t* inv_ptr = nullptr;  // n_sub+1
@@ -88,22 +121,52 @@ struct DevMesh {
     const float* inv32 = nullptr;
     const __half* inv16 = nullptr;
     const float* inv16_scale = nullptr;// n_sub
+    // lane packs (mixed forms): 32 subdomains of one size class M per pack,
+    // lane l of the pack solves one; idx [k][32], entries float4 groups
+    // [e/4][32][4] (float) or 8-entry groups [e/8][32][8] (half, per-lane scale)
+    int64_t n_pack = 0;
+    const int32_t* pack_m = nullptr;       // n_pack
+    const int64_t* pack_idx_off = nullptr; // n_pack
+    const int64_t* pack_inv_off = nullptr; // n_pack (entries)
+    const int32_t* pack_idx = nullptr;
+    const float* pack_inv32 = nullptr;
+    const __half* pack_inv16 = nullptr;
+    const float* pack_scale = nullptr;     // n_pack*32 (half entries)
     const double* wov64 = nullptr;     // nv
     const float* wov32 = nullptr;      // nv
-    const double* ar_inv = nullptr;    // nr*nr
+    const double* ar_inv = nullptr;    // nr*nr (FP64 form)
+    const float2* ar_inv2 = nullptr;   // nr rows of nr2 float pairs (mixed forms; nr2 = nr rounded up to even)
+    int64_t nr2 = 0;
     int max_m = 0;
+};
+
+// Work tables: element ranges, element tiles, vertex ranges, warp-kernel
+// subdomain ranges, reduced-row ranges, lane-pack ranges, ranges of the
+// per-vertex box lists (interpolation) and of their cell-sorted entries
+// (restriction).
+enum WorkKind {
+    kWorkElem = 0,
+    kWorkTile,
+    kWorkVert,
+    kWorkSub,
+    kWorkRow,
+    kWorkPack,
+    kWorkBox,
+    kWorkBoxEnt,
+    kWorkKinds
 };
 
 // Mesh descriptors and work tables of one set of solve slots (launchers).
 struct Work;
 struct Plan {
     const DevMesh* meshes = nullptr;       // device array of mesh descriptors
-    const Work* work[5] = {};              // device work tables, one per WorkKind
-    unsigned int nwork[5] = {};
+    const Work* work[kWorkKinds] = {};     // device work tables, one per WorkKind
+    unsigned int nwork[kWorkKinds] = {};
     int nslots = 0;
-    int max_m = 0;                         // largest subdomain over the meshes
+    int max_m = 0;                         // largest warp-kernel subdomain over the meshes
     bool any_nr = false;                   // some mesh has a reduced space
     int wait_limit = 1 << 20;              // iteration limit of bounded device waits
+    bool tile_tma = false;                 // element tiles staged by TMA (else streamed by the threads)
 };
 
 // Device scalars of one PCG solve (kernels.cu).
@@ -113,6 +176,7 @@ struct SolveScalars {
     double rho;        // r.z of the current iterate
     double pq;         // p.A p
     double alpha, beta;
+    float2 alpha2, beta2;  // alpha and beta as float pairs (mixed forms)
     double rr;         // ||r||^2 after the update
     double zr, zq;     // z.r and z.q for the next direction
     int iters;
@@ -140,12 +204,32 @@ struct Work {
     int32_t idx, count;    // this block among the slot's blocks of this kind
 };
 
-enum WorkKind { kWorkElem = 0, kWorkTile, kWorkVert, kWorkSub, kWorkRow, kWorkKinds };
+// Lane packs of the mixed-form local solves: subdomains with at most
+// kLaneMaxM dofs, padded to the next size class, 32 of one class per pack.
+constexpr int kLaneMaxM = 32;
+constexpr int kLaneClasses[] = {8, 12, 16, 18, 20, 24, 27, 32};
+inline int lane_class(int m) {
+    for (int c : kLaneClasses)
+        if (m <= c) return c;
+    return 0;
+}
+// entries stored per lane: the upper triangle, padded to a multiple of 8
+constexpr int lane_entries(int M) { return (M * (M + 1) / 2 + 7) / 8 * 8; }
 constexpr int kElemChunk = 256;   // elements per block
-constexpr int kRowChunk = 8;      // reduced rows per block (one warp each)
+// Box cells per axis, at most kMaxBoxes; the box lists store a cell as its
+// packed coordinates ci | cj << 10 | ck << 20.
+constexpr int kMaxBoxes = 1023;
+inline int32_t pack_cell(int32_t c, int bx, int by) {
+    return (c % bx) | (((c / bx) % by) << 10) | ((c / (bx * by)) << 20);
+}
+constexpr int kRowChunk = 4;      // reduced rows per block (one warp each)
 
 // Vector pools of a set of slots, passed by value to every kernel.  A slot's
 // vector is pool + work.voff (vertex vectors) or pool + work.roff (reduced).
+// In the mixed forms the outer iterates
+// x, r and p are float pairs stored in the 8-byte entries of x, r and p
+// (p2 aliases p); x is turned back into float64 in place before the final
+// residual.
 struct Vecs {
     double *x = nullptr, *r = nullptr, *p = nullptr, *y = nullptr, *q = nullptr;
     float2 *p2 = nullptr, *q2 = nullptr;   // float-pair p and A p (mixed forms)

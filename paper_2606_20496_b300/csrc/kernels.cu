@@ -24,6 +24,7 @@
 // Layout: elements in "device order" (sorted by centroid cell).  A Dirichlet
 // vertex v appears in the connectivity as ~v: reads give 0, writes skip it.
 #include <algorithm>
+#include <type_traits>
 
 #include <cuda_fp16.h>
 
@@ -65,14 +66,14 @@ __device__ __forceinline__ void block_sum(double (&v)[NV]) {
     }
 }
 
-// Deterministic per-slot sum: every block of the slot calls this with its
-// values; the last of the slot's `count` blocks gets true and the totals.
+// Publish a block's values (valid in thread 0) as partial `idx` of the
+// slot's `count` blocks; the last block to arrive sums the partials in a
+// fixed order and gets true and the totals (deterministic per-slot sums).
 template <int NV>
-__device__ bool slot_sum(double (&v)[NV], double* partials, int idx, int count, unsigned int* ticket,
-                         double (&tot)[NV]) {
+__device__ bool slot_publish(const double (&v)[NV], double* partials, int idx, int count, unsigned int* ticket,
+                             double (&tot)[NV]) {
     __shared__ bool last;
     __shared__ double res[NV];
-    block_sum<NV>(v);
     if (threadIdx.x == 0) {
 #pragma unroll
         for (int i = 0; i < NV; ++i) partials[(size_t)i * count + idx] = v[i];
@@ -99,6 +100,14 @@ __device__ bool slot_sum(double (&v)[NV], double* partials, int idx, int count, 
 #pragma unroll
     for (int i = 0; i < NV; ++i) tot[i] = res[i];
     return true;
+}
+
+// Deterministic per-slot sum of float64 values.
+template <int NV>
+__device__ bool slot_sum(double (&v)[NV], double* partials, int idx, int count, unsigned int* ticket,
+                         double (&tot)[NV]) {
+    block_sum<NV>(v);
+    return slot_publish<NV>(v, partials, idx, count, ticket, tot);
 }
 
 __device__ __forceinline__ void load_conn(const int32_t* __restrict__ conn, int64_t e, int (&v)[8]) {
@@ -201,12 +210,89 @@ __device__ __forceinline__ void pair_mul(float ah, float al, float bh, float bl,
     pl = __fmaf_rn(ah, bl, pl);
     pl = __fmaf_rn(al, bh, pl);
 }
+// x -> (hi, lo) float pair, hi = x rounded to float, lo = rounded remainder
+__device__ __forceinline__ float2 split_pair(double x) {
+    const float h = __double2float_rn(x);
+    return make_float2(h, __double2float_rn(x - (double)h));
+}
 // (yh, yl) += (ph, pl) without renormalising (few terms per accumulator)
 __device__ __forceinline__ void pair_acc(float& yh, float& yl, float ph, float pl) {
     float s, e;
     two_sum(yh, ph, s, e);
     yh = s;
     yl = __fadd_rn(yl, __fadd_rn(e, pl));
+}
+
+__device__ __forceinline__ float2* as_pair(double* p) { return reinterpret_cast<float2*>(p); }
+__device__ __forceinline__ const float2* as_pair(const double* p) { return reinterpret_cast<const float2*>(p); }
+
+// a + b, renormalised (the low words are added once, error ~2^-48 |a + b|
+// unless the high words cancel, where it stays ~2^-48 max(|a|, |b|))
+__device__ __forceinline__ float2 pr_add(float2 a, float2 b) {
+    float s, e, h, l;
+    two_sum(a.x, b.x, s, e);
+    e = __fadd_rn(e, __fadd_rn(a.y, b.y));
+    fast_two_sum(s, e, h, l);
+    return make_float2(h, l);
+}
+// a b + c
+__device__ __forceinline__ float2 pr_fma(float2 a, float2 b, float2 c) {
+    float ph, pl;
+    pair_mul(a.x, a.y, b.x, b.y, ph, pl);
+    return pr_add(make_float2(ph, pl), c);
+}
+// acc += a b (unnormalised accumulator, a few terms per thread)
+__device__ __forceinline__ void pr_dot_acc(float& h, float& l, float2 a, float2 b) {
+    float ph, pl;
+    pair_mul(a.x, a.y, b.x, b.y, ph, pl);
+    pair_acc(h, l, ph, pl);
+}
+__device__ __forceinline__ double pr_value(float h, float l) { return (double)h + (double)l; }
+
+// Block-wide sum of NV float pairs on the FP32 pipes (shuffle trees of
+// two-sums); the block totals are converted to float64 once, in thread 0.
+template <int NV>
+__device__ __forceinline__ void block_sum_pair(float (&h)[NV], float (&l)[NV]) {
+    __shared__ float2 sh[NV][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int i = 0; i < NV; ++i)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float oh = __shfl_xor_sync(0xffffffffu, h[i], o), ol = __shfl_xor_sync(0xffffffffu, l[i], o);
+            pair_acc(h[i], l[i], oh, ol);
+        }
+    __syncthreads();
+    if (lane == 0)
+#pragma unroll
+        for (int i = 0; i < NV; ++i) sh[i][w] = make_float2(h[i], l[i]);
+    __syncthreads();
+    if (w == 0) {
+#pragma unroll
+        for (int i = 0; i < NV; ++i) {
+            const float2 t = lane < nw ? sh[i][lane] : make_float2(0.0f, 0.0f);
+            h[i] = t.x;
+            l[i] = t.y;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const float oh = __shfl_xor_sync(0xffffffffu, h[i], o), ol = __shfl_xor_sync(0xffffffffu, l[i], o);
+                pair_acc(h[i], l[i], oh, ol);
+            }
+        }
+    }
+}
+
+// Deterministic per-slot sum of float-pair values (block sums in pairs,
+// partials and the final sum in float64).
+template <int NV>
+__device__ bool slot_sum_pair(float (&h)[NV], float (&l)[NV], double* partials, int idx, int count,
+                              unsigned int* ticket, double (&tot)[NV]) {
+    block_sum_pair<NV>(h, l);
+    double v[NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) v[i] = threadIdx.x == 0 ? pr_value(h[i], l[i]) : 0.0;
+    return slot_publish<NV>(v, partials, idx, count, ticket, tot);
 }
 
 // ---------------------------------------------------------------------------
@@ -261,6 +347,14 @@ __device__ __forceinline__ bool wait_tile(uint64_t* bar, SolveScalars* S, int li
     return false;
 }
 
+// tile-local index k (0..7) of an element from its packed 16-bit indices,
+// -1 for a Dirichlet vertex
+__device__ __forceinline__ int loc_of(const uint4& w, int k) {
+    const uint32_t u = k < 2 ? w.x : k < 4 ? w.y : k < 6 ? w.z : w.w;
+    const int v = (int)((k & 1) ? (u >> 16) : (u & 0xFFFFu));
+    return v == 0xFFFF ? -1 : v;
+}
+
 __device__ __forceinline__ void load_loc(const uint16_t* __restrict__ eloc, int64_t e, int (&L)[8]) {
     const uint4 w = __ldg(reinterpret_cast<const uint4*>(eloc) + e);
     const uint32_t u[4] = {w.x, w.y, w.z, w.w};
@@ -273,70 +367,181 @@ __device__ __forceinline__ void load_loc(const uint16_t* __restrict__ eloc, int6
 }
 
 constexpr uint32_t kTileSlotBytes = kOff * kTileElems * sizeof(float);   // 28 KiB
+constexpr int kGroups = kOff / 4;                                            // float4 groups per element
 
-// q = A p in float-pair arithmetic (outer operator of the mixed forms): the
-// difference form y_i = sum_j a_ij (x_j - x_i) keeps the error relative to
-// |a||x_j - x_i|; q is summed as pairs with compensated atomics (the exact
-// rounding error of each add to q.hi, recovered from the returned old value,
-// goes to q.lo).  Also sums p.Ap and finalises alpha in the slot's last block.
-__global__ void __launch_bounds__(kBlock) apply_pair_tiled_kernel(const DevMesh* __restrict__ meshes,
-                                                                  const Work* __restrict__ work, Vecs V,
-                                                                  int wait_limit) {
+// Where a thread finds its element's off-diagonals, four slots per 16-byte
+// group g: the tile staged in shared memory by TMA, or read straight from
+// global memory (contiguous across the warp, streamed past L1).
+struct SmemSlots {
+    const float4* hi;
+    const float4* lo;
+    int e;
+    __device__ __forceinline__ float4 h(int g) const { return hi[g * kTileElems + e]; }
+    __device__ __forceinline__ float4 l(int g) const { return lo[g * kTileElems + e]; }
+};
+// read-only streaming load (not volatile: the compiler may hoist it)
+__device__ __forceinline__ float4 ld_stream(const float4* p) {
+    float4 v;
+    asm("ld.global.nc.L1::no_allocate.v4.f32 {%0, %1, %2, %3}, [%4];"
+        : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+        : "l"(p));
+    return v;
+}
+struct GlobalSlots {
+    const float4* hi;   // this tile's [7][256] groups
+    const float4* lo;
+    int e;
+    __device__ __forceinline__ float4 h(int g) const { return ld_stream(hi + g * kTileElems + e); }
+    __device__ __forceinline__ float4 l(int g) const { return ld_stream(lo + g * kTileElems + e); }
+};
+__device__ __forceinline__ float comp(const float4& v, int c) {
+    return c == 0 ? v.x : c == 1 ? v.y : c == 2 ? v.z : v.w;
+}
+
+// y_e = A^e x_e in float-pair arithmetic, difference form
+// y_i = sum_j a_ij (x_j - x_i): the error stays relative to |a_ij||x_j - x_i|.
+// The difference is left unnormalised (hi + lo, |lo| small against the
+// product's rounding), the products and sums are error-free transformations.
+template <class Slots>
+__device__ __forceinline__ void element_pair(const Slots& A, float4 H, float4 L, const float (&xh)[8],
+                                             const float (&xl)[8], float (&yh)[8], float (&yl)[8]) {
+    // group g + 1 is requested while group g is used
+    float4 Hn = A.h(1), Ln = A.l(1);
+    int s = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+#pragma unroll
+        for (int j = i + 1; j < 8; ++j, ++s) {
+            if ((s & 3) == 0 && s > 0) {
+                H = Hn;
+                L = Ln;
+                if ((s >> 2) + 1 < kGroups) {
+                    Hn = A.h((s >> 2) + 1);
+                    Ln = A.l((s >> 2) + 1);
+                }
+            }
+            const float ah = comp(H, s & 3), al = comp(L, s & 3);
+            float dh, dl;
+            two_sum(xh[j], -xh[i], dh, dl);
+            dl = __fadd_rn(dl, __fsub_rn(xl[j], xl[i]));
+            float ph, pl;
+            pair_mul(ah, al, dh, dl, ph, pl);
+            pair_acc(yh[i], yl[i], ph, pl);
+            pair_acc(yh[j], yl[j], -ph, -pl);
+        }
+    }
+}
+
+// y_e = A^e x_e in float32, difference form.
+template <class Slots>
+__device__ __forceinline__ void element_f32(const Slots& A, float4 H, const float (&xe)[8], float (&ye)[8]) {
+    float4 Hn = A.h(1);
+    int s = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+#pragma unroll
+        for (int j = i + 1; j < 8; ++j, ++s) {
+            if ((s & 3) == 0 && s > 0) {
+                H = Hn;
+                if ((s >> 2) + 1 < kGroups) Hn = A.h((s >> 2) + 1);
+            }
+            const float d = comp(H, s & 3) * (xe[j] - xe[i]);
+            ye[i] += d;
+            ye[j] -= d;
+        }
+    }
+}
+
+// Up to kTileVerts / kBlock tile vertices per thread: all index loads first,
+// then all value loads (two dependent round trips in total).
+constexpr int kVertsPerThread = kTileVerts / kBlock;
+__device__ __forceinline__ void tile_vertex_ids(const DevMesh& M, int v0, int nvt, uint32_t (&raw)[kVertsPerThread]) {
+#pragma unroll
+    for (int k = 0; k < kVertsPerThread; ++k) {
+        const int i = (int)threadIdx.x + k * kBlock;
+        raw[k] = i < nvt ? __ldg(&M.tile_verts[v0 + i]) : 0u;
+    }
+}
+
+// q = A p in float-pair arithmetic (outer operator of the mixed forms), one
+// block per element tile.  kTma: the tile's matrices (hi and lo, 56 KiB)
+// arrive in shared memory by one bulk asynchronous copy while the block
+// gathers the tile's vertex values; otherwise every thread streams its
+// element's 14 groups from global memory (less shared memory, more blocks
+// per SM).  Element outputs are summed in shared memory with compensated
+// float atomics and every tile vertex is written once: a plain store when no
+// other tile touches it, compensated global atomics otherwise.  Also sums
+// p.Ap and finalises alpha in the slot's last block.
+template <bool kTma>
+__global__ void __launch_bounds__(kBlock, kTma ? 3 : 4) apply_pair_tiled_kernel(const DevMesh* __restrict__ meshes,
+                                                                                 const Work* __restrict__ work,
+                                                                                 Vecs V, int wait_limit) {
     extern __shared__ __align__(128) unsigned char smem[];
-    float* sh_hi = reinterpret_cast<float*>(smem);
-    float* sh_lo = sh_hi + kOff * kTileElems;
-    float2* ps = reinterpret_cast<float2*>(sh_lo + kOff * kTileElems);
+    float2* ps = reinterpret_cast<float2*>(smem);
     float2* ys = ps + kTileVerts;
+    float4* sh_hi = reinterpret_cast<float4*>(ys + kTileVerts);
+    float4* sh_lo = sh_hi + kGroups * kTileElems;
     __shared__ uint64_t bar;
     CGS_WORK_PROLOGUE();
     const float2* p2 = V.p2 + w.voff;
     float2* q2 = V.q2 + w.voff;
     const int t = w.begin;
-    if (threadIdx.x == 0) {
+    const float4* ghi = reinterpret_cast<const float4*>(M.at_hi) + (size_t)t * kGroups * kTileElems;
+    const float4* glo = reinterpret_cast<const float4*>(M.at_lo) + (size_t)t * kGroups * kTileElems;
+    if (kTma && threadIdx.x == 0) {
         mbar_init(&bar, 1);
         mbar_expect_tx(&bar, 2 * kTileSlotBytes);
-        bulk_copy_g2s(sh_hi, M.at_hi + (size_t)t * kOff * kTileElems, kTileSlotBytes, &bar);
-        bulk_copy_g2s(sh_lo, M.at_lo + (size_t)t * kOff * kTileElems, kTileSlotBytes, &bar);
+        bulk_copy_g2s(sh_hi, ghi, kTileSlotBytes, &bar);
+        bulk_copy_g2s(sh_lo, glo, kTileSlotBytes, &bar);
     }
     const int e0 = __ldg(&M.tile_ptr[t]), net = __ldg(&M.tile_ptr[t + 1]) - e0;
     const int v0 = __ldg(&M.tile_vptr[t]), nvt = __ldg(&M.tile_vptr[t + 1]) - v0;
-    for (int i = threadIdx.x; i < nvt; i += blockDim.x) {
-        ps[i] = __ldg(&p2[__ldg(&M.tile_verts[v0 + i]) & ~kSharedBit]);
-        ys[i] = make_float2(0.0f, 0.0f);
+    const bool has_e = (int)threadIdx.x < net;
+    // the first group of this thread's element is requested before the gather
+    float4 H = make_float4(0.f, 0.f, 0.f, 0.f), L = H;
+    if (!kTma && has_e) {
+        H = ld_stream(ghi + threadIdx.x);
+        L = ld_stream(glo + threadIdx.x);
+    }
+    const uint4 lw = has_e ? __ldg(reinterpret_cast<const uint4*>(M.eloc) + e0 + threadIdx.x)
+                           : make_uint4(~0u, ~0u, ~0u, ~0u);
+    {
+        uint32_t raw[kVertsPerThread];
+        tile_vertex_ids(M, v0, nvt, raw);
+#pragma unroll
+        for (int k = 0; k < kVertsPerThread; ++k) {
+            const int i = (int)threadIdx.x + k * kBlock;
+            if (i < nvt) {
+                ps[i] = __ldg(&p2[raw[k] & ~kSharedBit]);
+                ys[i] = make_float2(0.0f, 0.0f);
+            }
+        }
     }
     __syncthreads();
-    const bool ok = wait_tile(&bar, S, wait_limit);
-    double energy = 0.0;
-    if (ok && (int)threadIdx.x < net) {
-        int L[8];
-        load_loc(M.eloc, e0 + threadIdx.x, L);
+    bool ok = true;
+    if (kTma) {
+        ok = __syncthreads_and(wait_tile(&bar, S, wait_limit)) != 0;   // one decision per block
+        if (ok && has_e) {
+            H = sh_hi[threadIdx.x];
+            L = sh_lo[threadIdx.x];
+        }
+    }
+    float eh = 0.0f, el = 0.0f;   // p.Ap share of this thread's element
+    if (ok && has_e) {
         float xh[8], xl[8], yh[8], yl[8];
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
-            const float2 t2 = L[k] >= 0 ? ps[L[k]] : make_float2(0.0f, 0.0f);
+            const int lk = loc_of(lw, k);
+            const float2 t2 = lk >= 0 ? ps[lk] : make_float2(0.0f, 0.0f);
             xh[k] = t2.x;
             xl[k] = t2.y;
             yh[k] = 0.0f;
             yl[k] = 0.0f;
         }
-        int s = 0;
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-#pragma unroll
-            for (int j = i + 1; j < 8; ++j, ++s) {
-                const float ah = sh_hi[s * kTileElems + threadIdx.x];
-                const float al = sh_lo[s * kTileElems + threadIdx.x];
-                float dh, dl, t1, t2;
-                two_sum(xh[j], -xh[i], t1, t2);
-                t2 = __fadd_rn(t2, __fsub_rn(xl[j], xl[i]));
-                fast_two_sum(t1, t2, dh, dl);
-                float ph, pl;
-                pair_mul(ah, al, dh, dl, ph, pl);
-                pair_acc(yh[i], yl[i], ph, pl);
-                pair_acc(yh[j], yl[j], -ph, -pl);
-            }
-        }
-        float eh = 0.0f, el = 0.0f;
+        if (kTma)
+            element_pair(SmemSlots{sh_hi, sh_lo, (int)threadIdx.x}, H, L, xh, xl, yh, yl);
+        else
+            element_pair(GlobalSlots{ghi, glo, (int)threadIdx.x}, H, L, xh, xl, yh, yl);
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
             float h, l;
@@ -344,18 +549,18 @@ __global__ void __launch_bounds__(kBlock) apply_pair_tiled_kernel(const DevMesh*
             float ph, pl;
             pair_mul(xh[k], xl[k], h, l, ph, pl);
             pair_acc(eh, el, ph, pl);
-            if (L[k] >= 0) {
-                const float old = atomicAdd(&ys[L[k]].x, h);
+            const int lk = loc_of(lw, k);
+            if (lk >= 0) {
+                const float old = atomicAdd(&ys[lk].x, h);
                 float sum, err;
                 two_sum(old, h, sum, err);
-                atomicAdd(&ys[L[k]].y, __fadd_rn(err, l));
+                atomicAdd(&ys[lk].y, __fadd_rn(err, l));
             }
         }
-        energy = (double)eh + (double)el;
     }
     __syncthreads();
     if (ok) {
-        for (int i = threadIdx.x; i < nvt; i += blockDim.x) {
+        for (int i = threadIdx.x; i < nvt; i += kBlock) {
             const uint32_t raw = __ldg(&M.tile_verts[v0 + i]);
             const int v = (int)(raw & ~kSharedBit);
             float h, l;
@@ -371,8 +576,10 @@ __global__ void __launch_bounds__(kBlock) apply_pair_tiled_kernel(const DevMesh*
             }
         }
     }
-    double val[1] = {energy}, tot[1];
-    if (slot_sum<1>(val, V.partials + w.poff, w.idx, w.count, &S->ticket[0], tot) && threadIdx.x == 0) {
+    if (!S) return;   // no slot scalars (timing runs): no reduction
+    float vh[1] = {eh}, vl[1] = {el};
+    double tot[1];
+    if (slot_sum_pair<1>(vh, vl, V.partials + w.poff, w.idx, w.count, &S->ticket[0], tot) && threadIdx.x == 0) {
         const double pq = tot[0];
         S->pq = pq;
         if (S->status == CGS_ERR_TIMEOUT) {
@@ -382,63 +589,78 @@ __global__ void __launch_bounds__(kBlock) apply_pair_tiled_kernel(const DevMesh*
             S->done = 1;
         } else {
             S->alpha = S->rho / pq;
+            S->alpha2 = split_pair(S->alpha);
         }
     }
 }
 
-// y += alpha A x in float32 (inner apply s -= A l of the hybrid step).
-__global__ void __launch_bounds__(kBlock) apply28f_tiled_kernel(const DevMesh* __restrict__ meshes,
-                                                                const Work* __restrict__ work, Vecs V,
-                                                                const float* __restrict__ xin,
-                                                                float* __restrict__ yout, float alpha,
-                                                                int wait_limit) {
+// y += alpha A x in float32 (inner apply s -= A l of the hybrid step); the
+// same two variants (TMA-staged tile or streamed groups).
+template <bool kTma>
+__global__ void __launch_bounds__(kBlock, kTma ? 4 : 5) apply28f_tiled_kernel(const DevMesh* __restrict__ meshes,
+                                                                               const Work* __restrict__ work, Vecs V,
+                                                                               const float* __restrict__ xin,
+                                                                               float* __restrict__ yout, float alpha,
+                                                                               int wait_limit) {
     extern __shared__ __align__(128) unsigned char smem[];
-    float* sh_a = reinterpret_cast<float*>(smem);
-    float* xs = sh_a + kOff * kTileElems;
+    float* xs = reinterpret_cast<float*>(smem);
     float* ys = xs + kTileVerts;
+    float4* sh_a = reinterpret_cast<float4*>(ys + kTileVerts);
     __shared__ uint64_t bar;
     CGS_WORK_PROLOGUE();
     const float* x = xin + w.voff;
     float* y = yout + w.voff;
     const int t = w.begin;
-    if (threadIdx.x == 0) {
+    const float4* ga = reinterpret_cast<const float4*>(M.at_hi) + (size_t)t * kGroups * kTileElems;
+    if (kTma && threadIdx.x == 0) {
         mbar_init(&bar, 1);
         mbar_expect_tx(&bar, kTileSlotBytes);
-        bulk_copy_g2s(sh_a, M.at_hi + (size_t)t * kOff * kTileElems, kTileSlotBytes, &bar);
+        bulk_copy_g2s(sh_a, ga, kTileSlotBytes, &bar);
     }
     const int e0 = __ldg(&M.tile_ptr[t]), net = __ldg(&M.tile_ptr[t + 1]) - e0;
     const int v0 = __ldg(&M.tile_vptr[t]), nvt = __ldg(&M.tile_vptr[t + 1]) - v0;
-    for (int i = threadIdx.x; i < nvt; i += blockDim.x) {
-        xs[i] = __ldg(&x[__ldg(&M.tile_verts[v0 + i]) & ~kSharedBit]);
-        ys[i] = 0.0f;
+    const bool has_e = (int)threadIdx.x < net;
+    float4 H = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (!kTma && has_e) H = ld_stream(ga + threadIdx.x);
+    const uint4 lw = has_e ? __ldg(reinterpret_cast<const uint4*>(M.eloc) + e0 + threadIdx.x)
+                           : make_uint4(~0u, ~0u, ~0u, ~0u);
+    {
+        uint32_t raw[kVertsPerThread];
+        tile_vertex_ids(M, v0, nvt, raw);
+#pragma unroll
+        for (int k = 0; k < kVertsPerThread; ++k) {
+            const int i = (int)threadIdx.x + k * kBlock;
+            if (i < nvt) {
+                xs[i] = __ldg(&x[raw[k] & ~kSharedBit]);
+                ys[i] = 0.0f;
+            }
+        }
     }
     __syncthreads();
-    if (!wait_tile(&bar, S, wait_limit)) return;
-    if ((int)threadIdx.x < net) {
-        int L[8];
-        load_loc(M.eloc, e0 + threadIdx.x, L);
+    if (kTma) {
+        if (!__syncthreads_and(wait_tile(&bar, S, wait_limit))) return;   // uniform: the whole block leaves
+        if (has_e) H = sh_a[threadIdx.x];
+    }
+    if (has_e) {
         float xe[8], ye[8];
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
-            xe[k] = L[k] >= 0 ? xs[L[k]] : 0.0f;
+            const int lk = loc_of(lw, k);
+            xe[k] = lk >= 0 ? xs[lk] : 0.0f;
             ye[k] = 0.0f;
         }
-        int s = 0;
+        if (kTma)
+            element_f32(SmemSlots{sh_a, nullptr, (int)threadIdx.x}, H, xe, ye);
+        else
+            element_f32(GlobalSlots{ga, nullptr, (int)threadIdx.x}, H, xe, ye);
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-#pragma unroll
-            for (int j = i + 1; j < 8; ++j, ++s) {
-                const float d = sh_a[s * kTileElems + threadIdx.x] * (xe[j] - xe[i]);
-                ye[i] += d;
-                ye[j] -= d;
-            }
+        for (int k = 0; k < 8; ++k) {
+            const int lk = loc_of(lw, k);
+            if (lk >= 0) atomicAdd(&ys[lk], ye[k]);
         }
-#pragma unroll
-        for (int k = 0; k < 8; ++k)
-            if (L[k] >= 0) atomicAdd(&ys[L[k]], ye[k]);
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < nvt; i += blockDim.x) {
+    for (int i = threadIdx.x; i < nvt; i += kBlock) {
         const uint32_t raw = __ldg(&M.tile_verts[v0 + i]);
         const int v = (int)(raw & ~kSharedBit);
         if (!(raw & kSharedBit))
@@ -609,6 +831,119 @@ __global__ void __launch_bounds__(kBlock) local_block_kernel(const DevMesh* __re
 }
 
 // ---------------------------------------------------------------------------
+// Local solves of the mixed forms, one lane per subdomain.  A warp takes a
+// pack of 32 subdomains of one size class M (<= 32 dofs, zero-padded): lane
+// l keeps its subdomain's x and y (M values each) in registers and walks the
+// upper triangle of its inverse, a_ij feeding y_i += a_ij x_j and
+// y_j += a_ij x_i.  The entries of the 32 lanes are interleaved in 16-byte
+// groups, so each load of the warp reads 512 contiguous bytes; every entry is
+// read once, and the warp issues ~M^2/32 + 2M instructions per subdomain
+// (the warp-per-subdomain form needs ~20x more).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 ld_stream_u4(const uint4* p) {
+    uint4 v;
+    asm("ld.global.nc.L1::no_allocate.v4.u32 {%0, %1, %2, %3}, [%4];"
+        : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+        : "l"(p));
+    return v;
+}
+
+// entries of one lane, group by group: float (4 per group) or half (8)
+struct LaneEntries32 {
+    const float4* a;   // pack base, groups [g][32]
+    int lane;
+    float4 cur;
+    __device__ __forceinline__ float get(int e) {
+        if ((e & 3) == 0) cur = ld_stream(a + (e >> 2) * 32 + lane);
+        return comp(cur, e & 3);
+    }
+};
+struct LaneEntries16 {
+    const uint4* a;    // pack base, groups [g][32] of 8 halves
+    int lane;
+    float scale;
+    uint4 cur;
+    __device__ __forceinline__ float get(int e) {
+        if ((e & 7) == 0) cur = ld_stream_u4(a + (e >> 3) * 32 + lane);
+        const uint32_t w = (e & 7) < 2 ? cur.x : (e & 7) < 4 ? cur.y : (e & 7) < 6 ? cur.z : cur.w;
+        const __half2 h2 = *reinterpret_cast<const __half2*>(&w);
+        return ((e & 1) ? __high2float(h2) : __low2float(h2)) * scale;
+    }
+};
+
+template <int Mc, class Entries>
+__device__ __forceinline__ void lane_solve(Entries A, const int32_t* __restrict__ idx, const float* __restrict__ r,
+                                           float* __restrict__ out, const float* __restrict__ wov, int lane) {
+    float x[Mc], y[Mc];
+#pragma unroll
+    for (int k = 0; k < Mc; ++k) {
+        const int v = __ldg(&idx[k * 32 + lane]);
+        x[k] = v >= 0 ? __ldg(&r[v]) : 0.0f;
+        y[k] = 0.0f;
+    }
+    int e = 0;
+#pragma unroll
+    for (int i = 0; i < Mc; ++i) {
+#pragma unroll
+        for (int j = i; j < Mc; ++j, ++e) {
+            const float a = A.get(e);
+            if (i == j) {
+                y[i] = fmaf(a, x[i], y[i]);
+            } else {
+                y[i] = fmaf(a, x[j], y[i]);
+                y[j] = fmaf(a, x[i], y[j]);
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < Mc; ++k) {
+        const int v = __ldg(&idx[k * 32 + lane]);
+        if (v >= 0) atomicAdd(&out[v], wov ? y[k] * __ldg(&wov[v]) : y[k]);
+    }
+}
+
+template <class Entries>
+__device__ __forceinline__ void lane_dispatch(int Mc, const Entries& A, const int32_t* idx, const float* r,
+                                              float* out, const float* wov, int lane) {
+    switch (Mc) {
+        case 8: lane_solve<8>(A, idx, r, out, wov, lane); break;
+        case 12: lane_solve<12>(A, idx, r, out, wov, lane); break;
+        case 16: lane_solve<16>(A, idx, r, out, wov, lane); break;
+        case 18: lane_solve<18>(A, idx, r, out, wov, lane); break;
+        case 20: lane_solve<20>(A, idx, r, out, wov, lane); break;
+        case 24: lane_solve<24>(A, idx, r, out, wov, lane); break;
+        case 27: lane_solve<27>(A, idx, r, out, wov, lane); break;
+        default: lane_solve<32>(A, idx, r, out, wov, lane); break;
+    }
+}
+
+// out += W_ov sum_p R_p^T A_p^{-1} R_p r over the lane packs (float r, out).
+template <typename Stor>
+__global__ void __launch_bounds__(kBlock, 2) local_lane_kernel(const DevMesh* __restrict__ meshes,
+                                                               const Work* __restrict__ work, Vecs V,
+                                                               const float* __restrict__ rin,
+                                                               float* __restrict__ outv, int weighted) {
+    CGS_WORK_PROLOGUE();
+    const float* r = rin + w.voff;
+    float* out = outv + w.voff;
+    const float* wov = weighted ? M.wov32 : nullptr;
+    const int lane = threadIdx.x & 31;
+    for (int pk = w.begin + (int)(threadIdx.x >> 5); pk < w.end; pk += kBlock / 32) {
+        const int Mc = __ldg(&M.pack_m[pk]);
+        const int32_t* idx = M.pack_idx + __ldg(&M.pack_idx_off[pk]);
+        const int64_t ao = __ldg(&M.pack_inv_off[pk]);
+        if (std::is_same<Stor, float>::value) {
+            LaneEntries32 A{reinterpret_cast<const float4*>(M.pack_inv32 + ao), lane, {}};
+            lane_dispatch(Mc, A, idx, r, out, wov, lane);
+        } else {
+            LaneEntries16 A{reinterpret_cast<const uint4*>(M.pack_inv16 + ao), lane,
+                            __ldg(&M.pack_scale[(size_t)pk * 32 + lane]), {}};
+            lane_dispatch(Mc, A, idx, r, out, wov, lane);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Box coarse space.  Element e (device order) lies in cell c(e) with lower
 // corner (ci,cj,ck) H (coordinates are stored relative to the box origin);
 // its vertex x has local cell coordinates t = (x - corner) / H (outside
@@ -637,13 +972,24 @@ struct VertexXYZW<float> {
 __device__ __forceinline__ VertexXYZW<double> vertex_data(const DevMesh& M, double) { return {M.xyzw}; }
 __device__ __forceinline__ VertexXYZW<float> vertex_data(const DevMesh& M, float) { return {M.xyzwf}; }
 
+// Box sizes H and 1/H in the kernel's precision (the float copies are
+// rounded at setup: no conversion per thread).
 template <typename T>
-struct BoxGrid {
+struct BoxGrid;
+template <>
+struct BoxGrid<double> {
     int bx, by;
-    T hx, hy, hz, ihx, ihy, ihz;
+    double hx, hy, hz, ihx, ihy, ihz;
     __device__ __forceinline__ explicit BoxGrid(const DevMesh& M)
-        : bx(M.b[0]), by(M.b[1]), hx((T)M.H[0]), hy((T)M.H[1]), hz((T)M.H[2]), ihx((T)M.iH[0]),
-          ihy((T)M.iH[1]), ihz((T)M.iH[2]) {}
+        : bx(M.b[0]), by(M.b[1]), hx(M.H[0]), hy(M.H[1]), hz(M.H[2]), ihx(M.iH[0]), ihy(M.iH[1]), ihz(M.iH[2]) {}
+};
+template <>
+struct BoxGrid<float> {
+    int bx, by;
+    float hx, hy, hz, ihx, ihy, ihz;
+    __device__ __forceinline__ explicit BoxGrid(const DevMesh& M)
+        : bx(M.b[0]), by(M.b[1]), hx(M.Hf[0]), hy(M.Hf[1]), hz(M.Hf[2]), ihx(M.iHf[0]), ihy(M.iHf[1]),
+          ihz(M.iHf[2]) {}
 };
 
 template <typename T>
@@ -653,10 +999,9 @@ __device__ __forceinline__ void corner_weights(T tx, T ty, T tz, T (&w)[8]) {
     for (int m = 0; m < 8; ++m) w[m] = fx[m & 1] * fy[(m >> 1) & 1] * fz[(m >> 2) & 1];
 }
 
-// Warp sum of per-element cell contributions in float64 accuracy.  The FP64
-// form adds doubles; the float form adds float pairs (hi, lo) with exact
-// two-sums, so no FP64 instruction runs per lane and the result still
-// carries ~48 significant bits.
+// A cell-corner total on its way into r_r: a float64 value (FP64 form) or a
+// float (mixed forms, whose inputs are float-rounded) that enters r_r as a
+// float pair.
 struct CellSum64 {
     double v;
     __device__ __forceinline__ double value() const { return v; }
@@ -665,55 +1010,69 @@ struct CellSum32 {
     float h, l;
     __device__ __forceinline__ double value() const { return (double)h + (double)l; }
 };
-__device__ __forceinline__ CellSum64 cell_sum(double v) { return {warp_sum(v)}; }
-__device__ __forceinline__ CellSum32 cell_sum(float v) {
-    float h = v, l = 0.0f;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const float oh = __shfl_xor_sync(0xffffffffu, h, o);
-        const float ol = __shfl_xor_sync(0xffffffffu, l, o);
-        float sh, se;
-        two_sum(h, oh, sh, se);
-        h = sh;
-        l = __fadd_rn(l, __fadd_rn(ol, se));
-    }
-    return {h, l};
+__device__ __forceinline__ CellSum64 one_sum(double v) { return {v}; }
+__device__ __forceinline__ CellSum32 one_sum(float v) { return {v, 0.0f}; }
+
+// add a cell total to entry `col` of r_r: float64 atomics, or a float pair
+// with the exact rounding error of the high add (two-sum of the returned
+// old value) folded into the low word
+template <typename C>
+__device__ __forceinline__ void pool_add(double* rr, float2*, int col, const C& c, std::false_type) {
+    atomicAdd(&rr[col], c.value());
+}
+__device__ __forceinline__ void pool_add(double*, float2* rr2, int col, const CellSum32& c, std::true_type) {
+    float* q = reinterpret_cast<float*>(&rr2[col]);
+    const float old = atomicAdd(q, c.h);
+    float sum, err;
+    two_sum(old, c.h, sum, err);
+    atomicAdd(q + 1, __fadd_rn(err, c.l));
 }
 
-template <typename T, typename Tin>
+// trilinear weights of the 8 corners of the cell with packed coordinates pc
+// (ci | cj << 10 | ck << 20) at point (x, y, z); returns the cell id
+template <typename T>
+__device__ __forceinline__ int cell_weights(const BoxGrid<T>& g, int pc, T x, T y, T z, T (&wt)[8]) {
+    const int ci = pc & 1023, cj = (pc >> 10) & 1023, ck = pc >> 20;
+    corner_weights<T>((x - ci * g.hx) * g.ihx, (y - cj * g.hy) * g.ihy, (z - ck * g.hz) * g.ihz, wt);
+    return ci + g.bx * (cj + g.by * ck);
+}
+__device__ __forceinline__ const double* box_w(const DevMesh& M, double) { return M.vb_w64; }
+__device__ __forceinline__ const float* box_w(const DevMesh& M, float) { return M.vb_w32; }
+
+// r_r += J^T W s over the cell-sorted box-list entries: thread i takes entry
+// (v, c, weight) and forms w_m^c(x_v) * weight * s_v for the 8 corners m of
+// cell c; a segmented warp reduction over the lanes of one cell sums them,
+// and lane m of the segment adds corner m's total.  kPairOut: r_r is a float
+// pair per entry (compensated float atomics); otherwise float64.
+__device__ __forceinline__ const double* rent_w(const DevMesh& M, double) { return M.re_w64; }
+__device__ __forceinline__ const float* rent_w(const DevMesh& M, float) { return M.re_w32; }
+
+template <typename T, typename Tin, bool kPairOut>
 __global__ void __launch_bounds__(kBlock) restrict_kernel(const DevMesh* __restrict__ meshes,
                                                           const Work* __restrict__ work, Vecs V,
-                                                          const Tin* __restrict__ sin, double* __restrict__ rrv) {
+                                                          const Tin* __restrict__ sin, void* __restrict__ rrv) {
     CGS_WORK_PROLOGUE();
     const Tin* s = sin + w.voff;
-    double* rr = rrv + w.roff;
-    const BoxGrid<T> g(M);
-    const auto vx = vertex_data(M, T(0));
-    const int64_t e = (int64_t)w.begin + threadIdx.x;
-    const bool valid = e < w.end;
+    double* rr = static_cast<double*>(rrv) + w.roff;
+    float2* rr2 = static_cast<float2*>(rrv) + w.roff;
+    const int64_t i = (int64_t)w.begin + threadIdx.x;
+    const bool valid = i < w.end;
     T acc[8];
 #pragma unroll
     for (int m = 0; m < 8; ++m) acc[m] = T(0);
     int c = -1;
     if (valid) {
-        c = __ldg(&M.cell[e]);
-        const int ci = c % g.bx, cj = (c / g.bx) % g.by, ck = c / (g.bx * g.by);
-        const T cx = ci * g.hx, cy = cj * g.hy, cz = ck * g.hz;
-        int v[8];
-        load_conn(M.conn, e, v);
+        const BoxGrid<T> g(M);
+        const auto vx = vertex_data(M, T(0));
+        const int v = __ldg(&M.re_vert[i]);
+        T x, y, z, ic;
+        vx.load(v, x, y, z, ic);
+        T wt[8];
+        c = cell_weights(g, __ldg(&M.re_cell[i]), x, y, z, wt);
+        const T f = __ldg(&rent_w(M, T(0))[i]) * (T)__ldg(&s[v]);
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            if (v[k] < 0) continue;
-            T x, y, z, ic;
-            vx.load(v[k], x, y, z, ic);
-            const T sv = (T)__ldg(&s[v[k]]) * ic;
-            T wt[8];
-            corner_weights<T>((x - cx) * g.ihx, (y - cy) * g.ihy, (z - cz) * g.ihz, wt);
-#pragma unroll
-            for (int m = 0; m < 8; ++m) acc[m] += wt[m] * sv;
-        }
+        for (int m = 0; m < 8; ++m) acc[m] = wt[m] * f;
     }
-    // segmented warp reduction over lanes sharing a cell
     const int lane = threadIdx.x & 31;
     unsigned int todo = __ballot_sync(0xffffffffu, valid);
     while (todo) {
@@ -721,54 +1080,98 @@ __global__ void __launch_bounds__(kBlock) restrict_kernel(const DevMesh* __restr
         const int cc = __shfl_sync(0xffffffffu, c, leader);
         const bool mine = valid && c == cc;
         todo &= ~__ballot_sync(0xffffffffu, mine);
-        // corner m's total ends up in lane m: one FP64 conversion and one
-        // atomic per corner, issued as a single warp instruction
-        auto mine_sum = cell_sum(mine ? acc[0] : T(0));
+        // reduce-scatter of the segment's 8 corner sums over the warp: lanes
+        // exchange halves (4, 2, 1 values), then sum over lane bits 1 and 0;
+        // lane 4m ends with corner m's total
+        T v4[4], v2[2], v1;
+        const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
 #pragma unroll
-        for (int m = 1; m < 8; ++m) {
-            const auto sum = cell_sum(mine ? acc[m] : T(0));
-            if (lane == m) mine_sum = sum;
+        for (int k = 0; k < 4; ++k) {
+            const T lo = mine ? acc[k] : T(0), hi = mine ? acc[k + 4] : T(0);
+            v4[k] = (b4 ? hi : lo) + __shfl_xor_sync(0xffffffffu, b4 ? lo : hi, 16);
         }
-        if (lane < 8) {
-            const int col = __ldg(&M.cell_cols[(size_t)cc * 8 + lane]);
-            if (col >= 0) atomicAdd(&rr[col], mine_sum.value());
+#pragma unroll
+        for (int k = 0; k < 2; ++k) v2[k] = (b3 ? v4[k + 2] : v4[k]) + __shfl_xor_sync(0xffffffffu, b3 ? v4[k] : v4[k + 2], 8);
+        v1 = (b2 ? v2[1] : v2[0]) + __shfl_xor_sync(0xffffffffu, b2 ? v2[0] : v2[1], 4);
+        v1 += __shfl_xor_sync(0xffffffffu, v1, 2);
+        v1 += __shfl_xor_sync(0xffffffffu, v1, 1);
+        if ((lane & 3) == 0) {
+            const int m = lane >> 2;   // = 4 b4 + 2 b3 + b2
+            const int col = __ldg(&M.cell_cols[(size_t)cc * 8 + m]);
+            if (col >= 0) pool_add(rr, rr2, col, one_sum(v1), std::integral_constant<bool, kPairOut>());
         }
     }
 }
 
-template <typename T, typename Tu>
+// z += W Q^T J_L u_r by vertex: z_v += sum_c weight_c sum_m w_m^c(x_v) u_r[m]
+// (each box-list vertex once: plain read-modify-write).  kDots fuses the
+// PCG dots that follow the preconditioner, z.r and z.q (Dirichlet and
+// element-free vertices have z = 0): 1 = float64 vectors, 2 = float-pair r
+// and q; the slot's last block forms beta = -alpha (z.q) / rho, rho = z.r.
+template <typename T, typename Tu, int kDots>
 __global__ void __launch_bounds__(kBlock) interp_add_kernel(const DevMesh* __restrict__ meshes,
                                                             const Work* __restrict__ work, Vecs V,
                                                             const Tu* __restrict__ urv, T* __restrict__ zv) {
     CGS_WORK_PROLOGUE();
     const Tu* ur = urv + w.roff;
     T* z = zv + w.voff;
-    const int64_t e = (int64_t)w.begin + threadIdx.x;
-    if (e >= w.end) return;
-    const BoxGrid<T> g(M);
-    const auto vx = vertex_data(M, T(0));
-    const int c = __ldg(&M.cell[e]);
-    const int ci = c % g.bx, cj = (c / g.bx) % g.by, ck = c / (g.bx * g.by);
-    const T cx = ci * g.hx, cy = cj * g.hy, cz = ck * g.hz;
-    T u[8];
-#pragma unroll
-    for (int m = 0; m < 8; ++m) {
-        const int col = __ldg(&M.cell_cols[(size_t)c * 8 + m]);
-        u[m] = col >= 0 ? (T)__ldg(&ur[col]) : T(0);
-    }
-    int v[8];
-    load_conn(M.conn, e, v);
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-        if (v[k] < 0) continue;
+    const int64_t i = (int64_t)w.begin + threadIdx.x;
+    double zr = 0.0, zq = 0.0;
+    float rh = 0.0f, rl = 0.0f, qh = 0.0f, ql = 0.0f;
+    if (i < w.end) {
+        const BoxGrid<T> g(M);
+        const auto vx = vertex_data(M, T(0));
+        const T* bw = box_w(M, T(0));
+        const int v = __ldg(&M.vb_vert[i]);
+        const int e0 = __ldg(&M.vb_ptr[i]), e1 = __ldg(&M.vb_ptr[i + 1]);
         T x, y, zz, ic;
-        vx.load(v[k], x, y, zz, ic);
-        T wt[8];
-        corner_weights<T>((x - cx) * g.ihx, (y - cy) * g.ihy, (zz - cz) * g.ihz, wt);
+        vx.load(v, x, y, zz, ic);
         T val = T(0);
+        if (M.nr > 0) {
+            for (int e = e0; e < e1; ++e) {
+                T wt[8];
+                const int c = cell_weights(g, __ldg(&M.vb_cell[e]), x, y, zz, wt);
+                T sum = T(0);
 #pragma unroll
-        for (int m = 0; m < 8; ++m) val += wt[m] * u[m];
-        atomicAdd(&z[v[k]], val * ic);
+                for (int m = 0; m < 8; ++m) {
+                    const int col = __ldg(&M.cell_cols[(size_t)c * 8 + m]);
+                    sum += wt[m] * (col >= 0 ? (T)__ldg(&ur[col]) : T(0));
+                }
+                val += __ldg(&bw[e]) * sum;
+            }
+        }
+        const T zi = z[v] + val;
+        z[v] = zi;
+        if (kDots == 1) {
+            zr = fma((double)zi, V.r[w.voff + v], zr);
+            zq = fma((double)zi, V.q[w.voff + v], zq);
+        } else if (kDots == 2) {
+            const float2 z2 = make_float2((float)zi, 0.0f);
+            pr_dot_acc(rh, rl, z2, reinterpret_cast<const float2*>(V.r)[w.voff + v]);
+            pr_dot_acc(qh, ql, z2, V.q2[w.voff + v]);
+        }
+    }
+    if (kDots == 0 || !S) return;
+    double tot[2];
+    bool last;
+    if (kDots == 2) {
+        float vh[2] = {rh, qh}, vl[2] = {rl, ql};
+        last = slot_sum_pair<2>(vh, vl, V.partials + w.poff, w.idx, w.count, &S->ticket[3], tot);
+    } else {
+        double val2[2] = {zr, zq};
+        last = slot_sum<2>(val2, V.partials + w.poff, w.idx, w.count, &S->ticket[3], tot);
+    }
+    if (last && threadIdx.x == 0) {
+        S->zr = tot[0];
+        S->zq = tot[1];
+        const double beta = -S->alpha * tot[1] / S->rho;
+        S->beta = beta;
+        S->beta2 = split_pair(beta);
+        S->rho = tot[0];
+        if (!(tot[0] > 0.0) || !isfinite(tot[0]) || !isfinite(beta)) {
+            S->status = CGS_ERR_BREAKDOWN;
+            S->done = 1;
+        }
     }
 }
 
@@ -794,6 +1197,58 @@ __global__ void __launch_bounds__(kBlock) coarse_gemv_kernel(const DevMesh* __re
     }
 }
 
+// u_r = A_r^{-1} r_r in float-pair arithmetic (mixed forms): the inverse and
+// r_r are hi/lo float pairs, every lane keeps a pair accumulator, the warp
+// sums pairs by shuffles.  Same ~48-bit accuracy as the float64 product on
+// the FP32 pipes, so the product runs at the bandwidth of the 8-byte entries.
+// Writes u_r as float64 (ur, optional) and rounded to float (ur32, optional).
+__global__ void __launch_bounds__(kBlock) coarse_pair_kernel(const DevMesh* __restrict__ meshes,
+                                                             const Work* __restrict__ work, Vecs V,
+                                                             const float2* __restrict__ rr2v,
+                                                             double* __restrict__ urv, float* __restrict__ ur32v) {
+    CGS_WORK_PROLOGUE();
+    const int64_t nr = M.nr;
+    const float2* rr = rr2v + w.roff;
+    const int lane = threadIdx.x & 31;
+    const int64_t i = (int64_t)w.begin + (threadIdx.x >> 5);
+    if (i >= w.end) return;
+    // the row as 16-byte groups of two entries; four groups per lane in flight
+    const float4* row = reinterpret_cast<const float4*>(M.ar_inv2 + (size_t)i * M.nr2);
+    const int64_t ng = M.nr2 / 2;
+    float h = 0.0f, l = 0.0f, h2 = 0.0f, l2 = 0.0f;
+    for (int64_t g0 = lane; g0 < ng; g0 += 128) {
+        float4 a[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int64_t g = g0 + 32 * k;
+            a[k] = g < ng ? ld_stream(row + g) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int64_t j = 2 * (g0 + 32 * k);
+            if (j >= nr) continue;
+            const float2 r0 = __ldg(&rr[j]);
+            const float2 r1 = j + 1 < nr ? __ldg(&rr[j + 1]) : make_float2(0.0f, 0.0f);
+            float ph, pl;
+            pair_mul(a[k].x, a[k].y, r0.x, r0.y, ph, pl);
+            pair_acc(h, l, ph, pl);
+            pair_mul(a[k].z, a[k].w, r1.x, r1.y, ph, pl);
+            pair_acc(h2, l2, ph, pl);
+        }
+    }
+    pair_acc(h, l, h2, l2);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float oh = __shfl_xor_sync(0xffffffffu, h, o);
+        const float ol = __shfl_xor_sync(0xffffffffu, l, o);
+        pair_acc(h, l, oh, ol);
+    }
+    if (lane == 0) {
+        if (urv) urv[w.roff + i] = (double)h + (double)l;
+        if (ur32v) ur32v[w.roff + i] = __fadd_rn(h, l);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // PCG vector kernels (float64 outer iteration), over vertex ranges.
 // ---------------------------------------------------------------------------
@@ -805,13 +1260,11 @@ __device__ __forceinline__ double qval(const float2* q, int64_t i) {
 }
 __device__ __forceinline__ void qzero(double* q, int64_t i) { q[i] = 0.0; }
 __device__ __forceinline__ void qzero(float2* q, int64_t i) { q[i] = make_float2(0.0f, 0.0f); }
-// x -> (hi, lo) float pair, hi = x rounded to float, lo = rounded remainder
-__device__ __forceinline__ float2 split_pair(double x) {
-    const float h = __double2float_rn(x);
-    return make_float2(h, __double2float_rn(x - (double)h));
-}
 
 #define CGS_VERT_LOOP(i) for (int64_t i = (int64_t)w.begin + threadIdx.x; i < w.end; i += blockDim.x)
+// four vertices per thread and round: i0, i0 + blockDim, ... (loads first)
+#define CGS_VERT_LOOP4(i0) \
+    for (int64_t i0 = (int64_t)w.begin + threadIdx.x; i0 < w.end; i0 += 4 * (int64_t)blockDim.x)
 
 // r = b with Dirichlet entries zeroed, x = 0, q = 0; ||b||^2 -> bnorm2, tol2.
 template <typename Tq>
@@ -986,6 +1439,237 @@ __global__ void __launch_bounds__(kBlock) pcg_update_p_kernel(const DevMesh* __r
     }
 }
 
+// ---------------------------------------------------------------------------
+// Outer iteration of the mixed forms in float-pair arithmetic.  x, r, p and
+// q = A p are hi/lo float pairs (~48 significant bits); the products and sums
+// run on the FP32 pipes, each thread keeps pair accumulators for its dot
+// products and converts them to float64 once, and the per-slot reduction of
+// those partials is float64.  B300 issues FP64 (and float<->double
+// conversions) at 1/60 of its FP32 rate, which made the float64 form of these
+// kernels FP64-bound at a fraction of the memory bandwidth.
+// ---------------------------------------------------------------------------
+
+// r = b with Dirichlet entries zeroed, x = 0, q = 0; ||b||^2 -> bnorm2, tol2.
+__global__ void __launch_bounds__(kBlock) pcg_init_pair_kernel(const DevMesh* __restrict__ meshes,
+                                                               const Work* __restrict__ work, Vecs V, double rtol,
+                                                               int maxit) {
+    const Work w = work[blockIdx.x];
+    SolveScalars* S = V.S + w.slot;
+    const DevMesh& M = meshes[w.mesh];
+    const double* b = V.bptr ? V.bptr[w.slot] : V.b + w.voff;
+    float2* x = as_pair(V.x) + w.voff;
+    float2* r = as_pair(V.r) + w.voff;
+    float2* q = V.q2 + w.voff;
+    double acc = 0.0;
+    CGS_VERT_LOOP(i) {
+        const double bi = M.dir[i] ? 0.0 : b[i];
+        r[i] = split_pair(bi);
+        x[i] = make_float2(0.0f, 0.0f);
+        q[i] = make_float2(0.0f, 0.0f);
+        acc = fma(bi, bi, acc);
+    }
+    double val[1] = {acc}, tot[1];
+    if (slot_sum<1>(val, V.partials + w.poff, w.idx, w.count, &S->ticket[1], tot) && threadIdx.x == 0) {
+        S->bnorm2 = tot[0];
+        S->tol2 = rtol * rtol * tot[0];
+        S->iters = 0;
+        S->maxit = maxit;
+        S->loops = 0;
+        S->timeouts = 0;
+        S->status = CGS_OK;
+        S->done = (tot[0] == 0.0 || maxit <= 0) ? 1 : 0;
+        if (maxit <= 0 && tot[0] != 0.0) S->status = CGS_ERR_NO_CONVERGENCE;
+        S->rho = 0.0;
+    }
+}
+
+// z = 0, s = hi(r) (the float rounding of r), r_r = 0.
+__global__ void __launch_bounds__(kBlock) precond_prep_pair_kernel(const DevMesh* __restrict__ meshes,
+                                                                   const Work* __restrict__ work, Vecs V) {
+    CGS_WORK_PROLOGUE();
+    const float2* r = as_pair(V.r) + w.voff;
+    float* z = static_cast<float*>(V.z) + w.voff;
+    float* s = static_cast<float*>(V.s) + w.voff;
+    CGS_VERT_LOOP(i) {
+        z[i] = 0.0f;
+        s[i] = r[i].x;
+    }
+    const int64_t chunk = (M.nr + w.count - 1) / w.count;
+    const int64_t r0 = (int64_t)w.idx * chunk, r1 = min((int64_t)M.nr, r0 + chunk);
+    for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) V.rr[w.roff + i] = 0.0;
+}
+
+// p = z, rho = r.z.
+__global__ void __launch_bounds__(kBlock) pcg_first_dir_pair_kernel(const DevMesh* __restrict__ meshes,
+                                                                    const Work* __restrict__ work, Vecs V) {
+    CGS_WORK_PROLOGUE();
+    const float* z = static_cast<const float*>(V.z) + w.voff;
+    const float2* r = as_pair(V.r) + w.voff;
+    float2* p = V.p2 + w.voff;
+    float h = 0.0f, l = 0.0f;
+    CGS_VERT_LOOP(i) {
+        const float2 zi = make_float2(z[i], 0.0f);
+        p[i] = zi;
+        pr_dot_acc(h, l, zi, r[i]);
+    }
+    float vh[1] = {h}, vl[1] = {l};
+    double tot[1];
+    if (slot_sum_pair<1>(vh, vl, V.partials + w.poff, w.idx, w.count, &S->ticket[1], tot) && threadIdx.x == 0) {
+        S->rho = tot[0];
+        if (!(tot[0] > 0.0) || !isfinite(tot[0])) {
+            S->status = CGS_ERR_BREAKDOWN;
+            S->done = 1;
+        }
+    }
+}
+
+// x += alpha p, r -= alpha q, ||r||^2; z = 0, s = hi(r), r_r = 0.  The
+// slot's last block counts the iteration and applies the stopping test.
+__global__ void __launch_bounds__(kBlock) pcg_update_xr_pair_kernel(const DevMesh* __restrict__ meshes,
+                                                                    const Work* __restrict__ work, Vecs V) {
+    CGS_WORK_PROLOGUE();
+    float2* __restrict__ x = as_pair(V.x) + w.voff;
+    float2* __restrict__ r = as_pair(V.r) + w.voff;
+    const float2* __restrict__ p = V.p2 + w.voff;
+    const float2* __restrict__ q = V.q2 + w.voff;
+    float* __restrict__ z = static_cast<float*>(V.z) + w.voff;
+    float* __restrict__ s = static_cast<float*>(V.s) + w.voff;
+    const float2 a = S->alpha2, na = make_float2(-a.x, -a.y);
+    float h = 0.0f, l = 0.0f;
+    for (int64_t i0 = (int64_t)w.begin + threadIdx.x; i0 < w.end; i0 += 2 * (int64_t)blockDim.x) {
+        // the loads of two vertices are issued before their arithmetic
+        float2 pi[2], qi[2], xi[2], ri[2];
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const int64_t i = i0 + k * (int64_t)blockDim.x;
+            if (i < w.end) {
+                pi[k] = p[i];
+                qi[k] = q[i];
+                xi[k] = x[i];
+                ri[k] = r[i];
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const int64_t i = i0 + k * (int64_t)blockDim.x;
+            if (i < w.end) {
+                x[i] = pr_fma(a, pi[k], xi[k]);
+                const float2 rn = pr_fma(na, qi[k], ri[k]);
+                r[i] = rn;
+                pr_dot_acc(h, l, rn, rn);
+                z[i] = 0.0f;
+                s[i] = rn.x;
+            }
+        }
+    }
+    const int64_t chunk = (M.nr + w.count - 1) / w.count;
+    const int64_t r0 = (int64_t)w.idx * chunk, r1 = min((int64_t)M.nr, r0 + chunk);
+    for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) V.rr[w.roff + i] = 0.0;
+    float vh[1] = {h}, vl[1] = {l};
+    double tot[1];
+    if (slot_sum_pair<1>(vh, vl, V.partials + w.poff, w.idx, w.count, &S->ticket[2], tot) && threadIdx.x == 0) {
+        S->rr = tot[0];
+        const int it = S->iters + 1;
+        S->iters = it;
+        if (!isfinite(tot[0])) {
+            S->status = CGS_ERR_BREAKDOWN;
+            S->done = 1;
+        } else if (tot[0] <= S->tol2) {
+            S->status = CGS_OK;
+            S->done = 1;
+        } else if (it >= S->maxit) {
+            S->status = CGS_ERR_NO_CONVERGENCE;
+            S->done = 1;
+        }
+    }
+}
+
+// z.r and z.q; beta = -alpha (z.q) / rho, rho = z.r.
+__global__ void __launch_bounds__(kBlock) pcg_dots_pair_kernel(const DevMesh* __restrict__ meshes,
+                                                               const Work* __restrict__ work, Vecs V) {
+    CGS_WORK_PROLOGUE();
+    const float* __restrict__ z = static_cast<const float*>(V.z) + w.voff;
+    const float2* __restrict__ r = as_pair(V.r) + w.voff;
+    const float2* __restrict__ q = V.q2 + w.voff;
+    float rh = 0.0f, rl = 0.0f, qh = 0.0f, ql = 0.0f;
+    CGS_VERT_LOOP4(i0) {
+        float zi[4];
+        float2 ri[4], qi[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int64_t i = i0 + k * (int64_t)blockDim.x;
+            zi[k] = 0.0f;
+            ri[k] = qi[k] = make_float2(0.0f, 0.0f);
+            if (i < w.end) {
+                zi[k] = z[i];
+                ri[k] = r[i];
+                qi[k] = q[i];
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float2 z2 = make_float2(zi[k], 0.0f);
+            pr_dot_acc(rh, rl, z2, ri[k]);
+            pr_dot_acc(qh, ql, z2, qi[k]);
+        }
+    }
+    float vh[2] = {rh, qh}, vl[2] = {rl, ql};
+    double tot[2];
+    if (slot_sum_pair<2>(vh, vl, V.partials + w.poff, w.idx, w.count, &S->ticket[3], tot) && threadIdx.x == 0) {
+        S->zr = tot[0];
+        S->zq = tot[1];
+        const double beta = -S->alpha * tot[1] / S->rho;
+        S->beta = beta;
+        S->beta2 = split_pair(beta);
+        S->rho = tot[0];
+        if (!(tot[0] > 0.0) || !isfinite(tot[0]) || !isfinite(beta)) {
+            S->status = CGS_ERR_BREAKDOWN;
+            S->done = 1;
+        }
+    }
+}
+
+// p = z + beta p, q = 0 for the next product.
+__global__ void __launch_bounds__(kBlock) pcg_update_p_pair_kernel(const DevMesh* __restrict__ meshes,
+                                                                   const Work* __restrict__ work, Vecs V) {
+    CGS_WORK_PROLOGUE();
+    const float* __restrict__ z = static_cast<const float*>(V.z) + w.voff;
+    float2* __restrict__ p = V.p2 + w.voff;
+    float2* __restrict__ q = V.q2 + w.voff;
+    const float2 beta = S->beta2;
+    CGS_VERT_LOOP4(i0) {
+        float zi[4];
+        float2 pi[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int64_t i = i0 + k * (int64_t)blockDim.x;
+            if (i < w.end) {
+                zi[k] = z[i];
+                pi[k] = p[i];
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int64_t i = i0 + k * (int64_t)blockDim.x;
+            if (i < w.end) {
+                p[i] = pr_fma(beta, pi[k], make_float2(zi[k], 0.0f));
+                q[i] = make_float2(0.0f, 0.0f);
+            }
+        }
+    }
+}
+
+// x (float pair) -> float64 in place, before the final residual.
+__global__ void __launch_bounds__(kBlock) finalize_x_pair_kernel(const DevMesh* __restrict__ meshes,
+                                                                 const Work* __restrict__ work, Vecs V) {
+    const Work w = work[blockIdx.x];
+    double* x = V.x + w.voff;
+    CGS_VERT_LOOP(i) {
+        const float2 t = as_pair(x)[i];
+        x[i] = (double)t.x + (double)t.y;
+    }
+}
+
 // Condition of the device-side loop (graph while node): continue while some
 // slot is still running and fewer than maxit + 2 bodies have run (slot 0
 // counts the bodies; all slots share maxit).
@@ -1057,36 +1741,62 @@ void launch_apply64(const Plan& P, const Vecs& V, const double* x, double* y, do
         apply64_kernel<false><<<P.nwork[kWorkElem], kBlock, 0, st>>>(P.meshes, P.work[kWorkElem], V, x, y, alpha);
 }
 
+template <bool kTma>
+void set_smem_attr(const void* fn, int bytes, bool& done) {
+    if (!done) {
+        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        done = true;
+    }
+}
+
 void launch_apply_pair_tiled(const Plan& P, const Vecs& V, cudaStream_t st) {
     if (!P.nwork[kWorkTile]) return;
-    const int smem = (int)(2 * kTileSlotBytes + 2 * kTileVerts * sizeof(float2));
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(apply_pair_tiled_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        attr = true;
+    const int verts = (int)(2 * kTileVerts * sizeof(float2));
+    if (P.tile_tma) {
+        static bool attr = false;
+        const int smem = verts + (int)(2 * kTileSlotBytes);
+        set_smem_attr<true>((const void*)apply_pair_tiled_kernel<true>, smem, attr);
+        apply_pair_tiled_kernel<true><<<P.nwork[kWorkTile], kBlock, smem, st>>>(P.meshes, P.work[kWorkTile], V,
+                                                                                P.wait_limit);
+    } else {
+        apply_pair_tiled_kernel<false><<<P.nwork[kWorkTile], kBlock, verts, st>>>(P.meshes, P.work[kWorkTile], V,
+                                                                                 P.wait_limit);
     }
-    apply_pair_tiled_kernel<<<P.nwork[kWorkTile], kBlock, smem, st>>>(P.meshes, P.work[kWorkTile], V,
-                                                                      P.wait_limit);
 }
 
 void launch_apply28f_tiled(const Plan& P, const Vecs& V, const float* x, float* y, float alpha, cudaStream_t st) {
     if (!P.nwork[kWorkTile]) return;
-    const int smem = (int)(kTileSlotBytes + 2 * kTileVerts * sizeof(float));
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(apply28f_tiled_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        attr = true;
+    const int verts = (int)(2 * kTileVerts * sizeof(float));
+    if (P.tile_tma) {
+        static bool attr = false;
+        const int smem = verts + (int)kTileSlotBytes;
+        set_smem_attr<true>((const void*)apply28f_tiled_kernel<true>, smem, attr);
+        apply28f_tiled_kernel<true><<<P.nwork[kWorkTile], kBlock, smem, st>>>(P.meshes, P.work[kWorkTile], V, x, y,
+                                                                              alpha, P.wait_limit);
+    } else {
+        apply28f_tiled_kernel<false><<<P.nwork[kWorkTile], kBlock, verts, st>>>(P.meshes, P.work[kWorkTile], V, x,
+                                                                               y, alpha, P.wait_limit);
     }
-    apply28f_tiled_kernel<<<P.nwork[kWorkTile], kBlock, smem, st>>>(P.meshes, P.work[kWorkTile], V, x, y, alpha,
-                                                                    P.wait_limit);
 }
 
 void launch_local(const Plan& P, const Vecs& V, cgs_precision prec, const void* r, void* out, bool weighted,
                   cudaStream_t st) {
+    const int wt = weighted ? 1 : 0;
+    // mixed forms: subdomains of at most kLaneMaxM dofs in lane packs
+    if (prec != CGS_FP64 && P.nwork[kWorkPack]) {
+        const float* rf = static_cast<const float*>(r);
+        float* of = static_cast<float*>(out);
+        if (prec == CGS_FP32_BULK)
+            local_lane_kernel<float><<<P.nwork[kWorkPack], kBlock, 0, st>>>(P.meshes, P.work[kWorkPack], V, rf, of, wt);
+        else
+            local_lane_kernel<__half><<<P.nwork[kWorkPack], kBlock, 0, st>>>(P.meshes, P.work[kWorkPack], V, rf, of,
+                                                                             wt);
+    }
+    // the rest (every subdomain in the FP64 form): a warp per subdomain of
+    // up to 64 dofs, a block per larger one
     if (!P.nwork[kWorkSub]) return;
     const unsigned int n = P.nwork[kWorkSub];
     const Work* W = P.work[kWorkSub];
-    const int wt = weighted ? 1 : 0;
     // r is float64 in the FP64 form and the float copy of the residual otherwise
     if (prec == CGS_FP64) {
         local_warp_kernel<double, double><<<n, kBlock, 0, st>>>(P.meshes, W, V, static_cast<const double*>(r),
@@ -1109,35 +1819,82 @@ void launch_local(const Plan& P, const Vecs& V, cgs_precision prec, const void* 
     }
 }
 
-void launch_restrict(const Plan& P, const Vecs& V, bool fp64, const void* s, bool s_is_double, double* rr,
-                     cudaStream_t st) {
-    if (!P.nwork[kWorkElem] || !P.any_nr) return;
-    const unsigned int n = P.nwork[kWorkElem];
-    const Work* W = P.work[kWorkElem];
+void launch_restrict(const Plan& P, const Vecs& V, bool fp64, const void* s, bool s_is_double, void* rr,
+                     bool pair_out, cudaStream_t st) {
+    if (!P.nwork[kWorkBoxEnt] || !P.any_nr) return;
+    const unsigned int n = P.nwork[kWorkBoxEnt];
+    const Work* W = P.work[kWorkBoxEnt];
     if (fp64)
-        restrict_kernel<double, double><<<n, kBlock, 0, st>>>(P.meshes, W, V, static_cast<const double*>(s), rr);
+        restrict_kernel<double, double, false><<<n, kBlock, 0, st>>>(P.meshes, W, V, static_cast<const double*>(s),
+                                                                     rr);
     else if (s_is_double)
-        restrict_kernel<float, double><<<n, kBlock, 0, st>>>(P.meshes, W, V, static_cast<const double*>(s), rr);
+        restrict_kernel<float, double, false><<<n, kBlock, 0, st>>>(P.meshes, W, V, static_cast<const double*>(s), rr);
+    else if (pair_out)
+        restrict_kernel<float, float, true><<<n, kBlock, 0, st>>>(P.meshes, W, V, static_cast<const float*>(s), rr);
     else
-        restrict_kernel<float, float><<<n, kBlock, 0, st>>>(P.meshes, W, V, static_cast<const float*>(s), rr);
+        restrict_kernel<float, float, false><<<n, kBlock, 0, st>>>(P.meshes, W, V, static_cast<const float*>(s), rr);
 }
 
 void launch_interp_add(const Plan& P, const Vecs& V, bool fp64, const double* ur, const float* ur32, void* z,
-                       cudaStream_t st) {
-    if (!P.nwork[kWorkElem] || !P.any_nr) return;
-    const unsigned int n = P.nwork[kWorkElem];
-    const Work* W = P.work[kWorkElem];
-    if (fp64)
-        interp_add_kernel<double, double><<<n, kBlock, 0, st>>>(P.meshes, W, V, ur, static_cast<double*>(z));
-    else if (ur32)   // float copy of u_r written by the reduced solve: no conversions per element
-        interp_add_kernel<float, float><<<n, kBlock, 0, st>>>(P.meshes, W, V, ur32, static_cast<float*>(z));
-    else
-        interp_add_kernel<float, double><<<n, kBlock, 0, st>>>(P.meshes, W, V, ur, static_cast<float*>(z));
+                       bool dots, cudaStream_t st) {
+    if (!P.nwork[kWorkBox] || !P.any_nr) return;
+    const unsigned int n = P.nwork[kWorkBox];
+    const Work* W = P.work[kWorkBox];
+    if (fp64) {
+        if (dots)
+            interp_add_kernel<double, double, 1><<<n, kBlock, 0, st>>>(P.meshes, W, V, ur, static_cast<double*>(z));
+        else
+            interp_add_kernel<double, double, 0><<<n, kBlock, 0, st>>>(P.meshes, W, V, ur, static_cast<double*>(z));
+    } else if (ur32) {   // float copy of u_r written by the reduced solve: no conversions per vertex
+        if (dots)
+            interp_add_kernel<float, float, 2><<<n, kBlock, 0, st>>>(P.meshes, W, V, ur32, static_cast<float*>(z));
+        else
+            interp_add_kernel<float, float, 0><<<n, kBlock, 0, st>>>(P.meshes, W, V, ur32, static_cast<float*>(z));
+    } else {
+        interp_add_kernel<float, double, 0><<<n, kBlock, 0, st>>>(P.meshes, W, V, ur, static_cast<float*>(z));
+    }
 }
 
 void launch_coarse(const Plan& P, const Vecs& V, const double* rr, double* ur, float* ur32, cudaStream_t st) {
     if (!P.nwork[kWorkRow]) return;
-    coarse_gemv_kernel<<<P.nwork[kWorkRow], kBlock, 0, st>>>(P.meshes, P.work[kWorkRow], V, rr, ur, ur32);
+    coarse_gemv_kernel<<<P.nwork[kWorkRow], 32 * kRowChunk, 0, st>>>(P.meshes, P.work[kWorkRow], V, rr, ur, ur32);
+}
+void launch_coarse_pair(const Plan& P, const Vecs& V, const float2* rr2, double* ur, float* ur32, cudaStream_t st) {
+    if (!P.nwork[kWorkRow]) return;
+    coarse_pair_kernel<<<P.nwork[kWorkRow], 32 * kRowChunk, 0, st>>>(P.meshes, P.work[kWorkRow], V, rr2, ur,
+                                                                      ur32);
+}
+
+#define CGS_VLAUNCH(kernel, ...) \
+    kernel<<<P.nwork[kWorkVert], kBlock, 0, st>>>(P.meshes, P.work[kWorkVert], V, ##__VA_ARGS__)
+void launch_pcg_init_pair(const Plan& P, const Vecs& V, double rtol, int maxit, cudaStream_t st) {
+    CGS_VLAUNCH(pcg_init_pair_kernel, rtol, maxit);
+}
+void launch_precond_prep_pair(const Plan& P, const Vecs& V, cudaStream_t st) {
+    CGS_VLAUNCH(precond_prep_pair_kernel);
+}
+void launch_pcg_first_dir_pair(const Plan& P, const Vecs& V, cudaStream_t st) {
+    CGS_VLAUNCH(pcg_first_dir_pair_kernel);
+}
+void launch_pcg_update_xr_pair(const Plan& P, const Vecs& V, cudaStream_t st) {
+    CGS_VLAUNCH(pcg_update_xr_pair_kernel);
+}
+void launch_pcg_dots_pair(const Plan& P, const Vecs& V, cudaStream_t st) { CGS_VLAUNCH(pcg_dots_pair_kernel); }
+void launch_pcg_update_p_pair(const Plan& P, const Vecs& V, cudaStream_t st) {
+    CGS_VLAUNCH(pcg_update_p_pair_kernel);
+}
+void launch_finalize_x_pair(const Plan& P, const Vecs& V, cudaStream_t st) { CGS_VLAUNCH(finalize_x_pair_kernel); }
+#undef CGS_VLAUNCH
+
+// float64 -> float pair over n entries (r_r of the single-step reduced solve)
+__global__ void split_pair_kernel(int64_t n, const double* __restrict__ a, float2* __restrict__ b) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        b[i] = split_pair(a[i]);
+}
+void launch_split_pair(int64_t n, const double* a, float2* b, cudaStream_t st) {
+    if (n <= 0) return;
+    const int blocks = (int)std::min<int64_t>((n + kBlock - 1) / kBlock, 1024);
+    split_pair_kernel<<<blocks, kBlock, 0, st>>>(n, a, b);
 }
 
 template <typename Tq>
@@ -1172,13 +1929,15 @@ void launch_resid_norm(const Plan& P, const Vecs& V, cudaStream_t st) {
     resid_norm_kernel<<<P.nwork[kWorkVert], kBlock, 0, st>>>(P.meshes, P.work[kWorkVert], V);
 }
 
-Schedule default_schedule(int64_t total_nv, int64_t total_sub) {
+Schedule default_schedule(int64_t total_nv, int64_t total_sub, int64_t total_pack) {
     const int64_t target = 4 * 148;
     Schedule s;
     int64_t v = (total_nv + target - 1) / target;
     s.vert_chunk = (int)std::min<int64_t>(2048, std::max<int64_t>(256, (v + 255) / 256 * 256));
     int64_t c = (total_sub + target - 1) / target;
     s.sub_chunk = (int)std::min<int64_t>(64, std::max<int64_t>(8, (c + 7) / 8 * 8));
+    int64_t k = (total_pack + target - 1) / target;
+    s.pack_chunk = (int)std::min<int64_t>(32, std::max<int64_t>(8, (k + 7) / 8 * 8));
     return s;
 }
 
@@ -1207,30 +1966,26 @@ void append_mesh_work(std::vector<Work> (&tabs)[kWorkKinds], int mesh, int slot,
     add(kWorkVert, z.nv, sch.vert_chunk);
     add(kWorkSub, z.n_sub, sch.sub_chunk);
     add(kWorkRow, z.nr, kRowChunk);
+    add(kWorkPack, z.n_pack, sch.pack_chunk);
+    add(kWorkBox, z.nvb, kElemChunk);
+    if (z.nr > 0) add(kWorkBoxEnt, z.nre, kElemChunk);
 }
 
 int64_t mesh_partial_slots(const MeshSizes& z, const Schedule& sch) {
     int64_t c = (z.ne + kElemChunk - 1) / kElemChunk;
     c = std::max(c, z.ntiles);
     c = std::max(c, (z.nv + sch.vert_chunk - 1) / sch.vert_chunk);
+    c = std::max(c, (z.nvb + kElemChunk - 1) / kElemChunk);
     return 2 * std::max<int64_t>(c, 1);
 }
 
-#define CGS_INST(TZ, TQ)                                                                                       \
-    template void launch_pcg_update_xr<TZ, TQ>(const Plan&, const Vecs&, const TQ*, cudaStream_t);             \
-    template void launch_pcg_dots<TZ, TQ>(const Plan&, const Vecs&, const TQ*, cudaStream_t);                  \
-    template void launch_pcg_update_p<TZ, TQ>(const Plan&, const Vecs&, TQ*, cudaStream_t);
-CGS_INST(double, double)
-CGS_INST(double, float2)
-CGS_INST(float, double)
-CGS_INST(float, float2)
-#undef CGS_INST
+template void launch_pcg_update_xr<double, double>(const Plan&, const Vecs&, const double*, cudaStream_t);
+template void launch_pcg_dots<double, double>(const Plan&, const Vecs&, const double*, cudaStream_t);
+template void launch_pcg_update_p<double, double>(const Plan&, const Vecs&, double*, cudaStream_t);
 template void launch_pcg_init<double>(const Plan&, const Vecs&, double*, double, int, cudaStream_t);
-template void launch_pcg_init<float2>(const Plan&, const Vecs&, float2*, double, int, cudaStream_t);
 template void launch_precond_prep<double>(const Plan&, const Vecs&, const double*, cudaStream_t);
 template void launch_precond_prep<float>(const Plan&, const Vecs&, const double*, cudaStream_t);
 template void launch_pcg_first_dir<double>(const Plan&, const Vecs&, cudaStream_t);
-template void launch_pcg_first_dir<float>(const Plan&, const Vecs&, cudaStream_t);
 
 void launch_convert_f2d(const Plan& P, const float* a, double* b, bool mask, cudaStream_t st) {
     convert_kernel<float, double><<<P.nwork[kWorkVert], kBlock, 0, st>>>(P.meshes, P.work[kWorkVert], a, b, mask);

@@ -15,11 +15,25 @@ void launch_apply_pair_tiled(const Plan& P, const Vecs& V, cudaStream_t st);
 void launch_apply28f_tiled(const Plan& P, const Vecs& V, const float* x, float* y, float alpha, cudaStream_t st);
 void launch_local(const Plan& P, const Vecs& V, cgs_precision prec, const void* r, void* out, bool weighted,
                   cudaStream_t st);
-void launch_restrict(const Plan& P, const Vecs& V, bool fp64, const void* s, bool s_is_double, double* rr,
-                     cudaStream_t st);
+// r_r += J^T W s.  pair_out: rr holds float pairs (mixed forms, float s)
+void launch_restrict(const Plan& P, const Vecs& V, bool fp64, const void* s, bool s_is_double, void* rr,
+                     bool pair_out, cudaStream_t st);
+// z += W Q^T J_L u_r.  dots: also z.r and z.q with beta and rho (fused PCG
+// dots; r and q of the engine's slots)
 void launch_interp_add(const Plan& P, const Vecs& V, bool fp64, const double* ur, const float* ur32, void* z,
-                       cudaStream_t st);
+                       bool dots, cudaStream_t st);
 void launch_coarse(const Plan& P, const Vecs& V, const double* rr, double* ur, float* ur32, cudaStream_t st);
+void launch_coarse_pair(const Plan& P, const Vecs& V, const float2* rr2, double* ur, float* ur32, cudaStream_t st);
+void launch_split_pair(int64_t n, const double* a, float2* b, cudaStream_t st);
+
+// Outer iteration of the mixed forms (float-pair x, r, p, q).
+void launch_pcg_init_pair(const Plan& P, const Vecs& V, double rtol, int maxit, cudaStream_t st);
+void launch_precond_prep_pair(const Plan& P, const Vecs& V, cudaStream_t st);
+void launch_pcg_first_dir_pair(const Plan& P, const Vecs& V, cudaStream_t st);
+void launch_pcg_update_xr_pair(const Plan& P, const Vecs& V, cudaStream_t st);
+void launch_pcg_dots_pair(const Plan& P, const Vecs& V, cudaStream_t st);
+void launch_pcg_update_p_pair(const Plan& P, const Vecs& V, cudaStream_t st);
+void launch_finalize_x_pair(const Plan& P, const Vecs& V, cudaStream_t st);
 
 template <typename Tq>
 void launch_pcg_init(const Plan& P, const Vecs& V, Tq* q, double rtol, int maxit, cudaStream_t st);
@@ -44,18 +58,21 @@ void launch_fill_f(int64_t n, float* a, float v, cudaStream_t st);
 
 // Work tables of one mesh as slot `slot` (host side, appended to tabs).
 struct MeshSizes {
-    int64_t nv, ne, ntiles, n_sub, nr;
+    int64_t nv, ne, ntiles, n_sub, nr, n_pack, nvb, nre;   // n_sub: warp-kernel subdomains
 };
 // Block sizes of the range-parallel kernels: vertices per block (vector
-// kernels) and subdomains per block (local solves).  Elements (256) and
-// reduced rows (8) per block are fixed by the thread mapping.
+// kernels) and subdomains per block (local solves), and how the tiled
+// applies load their element matrices.  Elements (256) and reduced rows (8)
+// per block are fixed by the thread mapping.
 struct Schedule {
     int vert_chunk = 1024;
     int sub_chunk = 64;
+    int pack_chunk = 8;  // lane packs per block (a multiple of the 8 warps)
+    int tile_tma = 0;    // 1: element tiles of the mixed-form applies staged by TMA
 };
 // Default schedule: enough blocks to fill the GPU (about four per SM) for
 // `total` work of each kind, chunks within the kernels' ranges.
-Schedule default_schedule(int64_t total_nv, int64_t total_sub);
+Schedule default_schedule(int64_t total_nv, int64_t total_sub, int64_t total_pack);
 void append_mesh_work(std::vector<Work> (&tabs)[kWorkKinds], int mesh, int slot, int64_t voff, int64_t roff,
                       int64_t poff, const MeshSizes& z, const Schedule& sch);
 int64_t mesh_partial_slots(const MeshSizes& z, const Schedule& sch);   // partial sums one slot needs

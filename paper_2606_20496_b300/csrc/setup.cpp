@@ -164,8 +164,8 @@ cgs_status host_setup(const double* xyz, int64_t nv, const int32_t* conn, int64_
         return CGS_ERR_INVALID_ARG;
     }
     for (int d = 0; d < 3; ++d)
-        if (prm.box[d] < 1 || prm.box[d] > 4096) {
-            err = "box counts must lie in [1, 4096]";
+        if (prm.box[d] < 1 || prm.box[d] > kMaxBoxes) {
+            err = "box counts must lie in [1, 1023]";
             return CGS_ERR_INVALID_ARG;
         }
     if (prm.overlap_layers < 0 || !(prm.box_margin >= 0.0)) {
@@ -274,6 +274,8 @@ cgs_status host_setup(const double* xyz, int64_t nv, const int32_t* conn, int64_
     }
     std::vector<std::vector<int32_t>> sub_sets(n_sub);
     std::vector<std::vector<double>> sub_inv(n_sub);
+    // the mixed forms solve subdomains of at most kLaneMaxM dofs one per lane
+    const bool lane_packs = prm.prec != CGS_FP64;
     bool not_spd = false, too_big = false;
 #pragma omp parallel
     {
@@ -341,12 +343,20 @@ cgs_status host_setup(const double* xyz, int64_t nv, const int32_t* conn, int64_
                 not_spd = true;
                 continue;
             }
-            // cyclic diagonals: entry (i, (i+d) mod m) at d*m + i, d = 0..m/2
             std::vector<double>& pk = sub_inv[p];
-            const int nd = m / 2 + 1;
-            pk.resize((size_t)nd * m);
-            for (int d = 0; d < nd; ++d)
-                for (int i = 0; i < m; ++i) pk[(size_t)d * m + i] = full[(size_t)i * m + (i + d) % m];
+            if (lane_packs && m <= kLaneMaxM) {
+                // upper triangle, row-major (lane packs)
+                pk.resize((size_t)m * (m + 1) / 2);
+                size_t e = 0;
+                for (int i = 0; i < m; ++i)
+                    for (int j = i; j < m; ++j) pk[e++] = full[(size_t)i * m + j];
+            } else {
+                // cyclic diagonals: entry (i, (i+d) mod m) at d*m + i, d = 0..m/2
+                const int nd = m / 2 + 1;
+                pk.resize((size_t)nd * m);
+                for (int d = 0; d < nd; ++d)
+                    for (int i = 0; i < m; ++i) pk[(size_t)d * m + i] = full[(size_t)i * m + (i + d) % m];
+            }
         }
     }
     if (too_big) {
@@ -358,13 +368,10 @@ cgs_status host_setup(const double* xyz, int64_t nv, const int32_t* conn, int64_
         return CGS_ERR_NOT_SPD;
     }
     S.sub_ptr.assign(n_sub + 1, 0);
-    S.inv_ptr.assign(n_sub + 1, 0);
     S.max_m = 0;
     for (int64_t p = 0; p < n_sub; ++p) {
         const int64_t m = (int64_t)sub_sets[p].size();
         S.sub_ptr[p + 1] = S.sub_ptr[p] + m;
-        const int64_t sz = (m / 2 + 1) * m;
-        S.inv_ptr[p + 1] = S.inv_ptr[p] + (sz + kPackAlign - 1) / kPackAlign * kPackAlign;
         S.max_m = std::max(S.max_m, m);
     }
     S.sum_m = S.sub_ptr[n_sub];
@@ -373,15 +380,69 @@ cgs_status host_setup(const double* xyz, int64_t nv, const int32_t* conn, int64_
         return CGS_ERR_INVALID_ARG;
     }
     S.sub_idx.resize(S.sum_m);
-    S.inv.assign(S.inv_ptr[n_sub], 0.0);
     S.wov.assign(nv, 0.0);
     std::vector<int32_t> mult(nv, 0);
     for (int64_t p = 0; p < n_sub; ++p) {
         std::copy(sub_sets[p].begin(), sub_sets[p].end(), S.sub_idx.begin() + S.sub_ptr[p]);
-        std::copy(sub_inv[p].begin(), sub_inv[p].end(), S.inv.begin() + S.inv_ptr[p]);
         for (int32_t v : sub_sets[p]) mult[v]++;
     }
     for (int64_t v = 0; v < nv; ++v) S.wov[v] = mult[v] ? 1.0 / mult[v] : 0.0;
+    auto in_lane = [&](int64_t p) {
+        const size_t m = sub_sets[p].size();
+        return lane_packs && m > 0 && m <= (size_t)kLaneMaxM;
+    };
+    // warp-kernel subdomains, caller order
+    S.wsub_ptr.assign(1, 0);
+    S.inv_ptr.assign(1, 0);
+    S.max_wm = 0;
+    for (int64_t p = 0; p < n_sub; ++p) {
+        if (in_lane(p)) continue;
+        const int64_t m = (int64_t)sub_sets[p].size();
+        S.wsub_ptr.push_back(S.wsub_ptr.back() + m);
+        const int64_t sz = (m / 2 + 1) * m;
+        S.inv_ptr.push_back(S.inv_ptr.back() + (sz + kPackAlign - 1) / kPackAlign * kPackAlign);
+        S.max_wm = std::max(S.max_wm, m);
+    }
+    S.n_wsub = (int64_t)S.wsub_ptr.size() - 1;
+    S.wsub_idx.resize(S.wsub_ptr.back());
+    S.inv.assign(S.inv_ptr.back(), 0.0);
+    for (int64_t p = 0, w = 0; p < n_sub; ++p) {
+        if (in_lane(p)) continue;
+        std::copy(sub_sets[p].begin(), sub_sets[p].end(), S.wsub_idx.begin() + S.wsub_ptr[w]);
+        std::copy(sub_inv[p].begin(), sub_inv[p].end(), S.inv.begin() + S.inv_ptr[w]);
+        ++w;
+    }
+    // lane packs: per size class (ascending), 32 subdomains in caller order
+    S.pack_m.clear();
+    S.pack_idx_off.assign(1, 0);
+    S.pack_inv_off.assign(1, 0);
+    for (int c : kLaneClasses) {
+        std::vector<int64_t> members;
+        for (int64_t p = 0; p < n_sub; ++p)
+            if (in_lane(p) && lane_class((int)sub_sets[p].size()) == c) members.push_back(p);
+        for (size_t b = 0; b < members.size(); b += 32) {
+            S.pack_m.push_back(c);
+            S.pack_idx_off.push_back(S.pack_idx_off.back() + (int64_t)32 * c);
+            S.pack_inv_off.push_back(S.pack_inv_off.back() + (int64_t)32 * lane_entries(c));
+            const int64_t io = S.pack_idx_off[S.pack_idx_off.size() - 2];
+            const int64_t ao = S.pack_inv_off[S.pack_inv_off.size() - 2];
+            S.pack_idx.resize(S.pack_idx_off.back(), -1);
+            S.pack_inv.resize(S.pack_inv_off.back(), 0.0);
+            for (int l = 0; l < 32 && b + l < members.size(); ++l) {
+                const int64_t p = members[b + l];
+                const std::vector<int32_t>& R = sub_sets[p];
+                const int m = (int)R.size();
+                for (int k = 0; k < m; ++k) S.pack_idx[io + (int64_t)k * 32 + l] = R[k];
+                // the m x m triangle inside the c x c one (zero padding)
+                const std::vector<double>& tri = sub_inv[p];
+                size_t src = 0;
+                int64_t e = 0;
+                for (int i = 0; i < c; ++i)
+                    for (int j = i; j < c; ++j, ++e)
+                        if (i < m && j < m) S.pack_inv[ao + (int64_t)l * lane_entries(c) + e] = tri[src++];
+            }
+        }
+    }
     sub_sets.clear();
     sub_inv.clear();
 
@@ -462,6 +523,56 @@ cgs_status host_setup(const double* xyz, int64_t nv, const int32_t* conn, int64_
     S.cell_cols.assign(ncell * 8, -1);
     for (int64_t c = 0; c < ncell; ++c)
         for (int m = 0; m < 8; ++m) S.cell_cols[c * 8 + m] = col[corner_id((int)c, m)];
+
+    // ---- per-vertex box lists ----------------------------------------------
+    // W Q^T J_L regrouped by vertex: vertex v with cnt_v elements, n_c of
+    // them in cell c, takes weight n_c / cnt_v on that cell's trilinear
+    // interpolant.  Free vertices with elements, ordered by their smallest
+    // cell (then id) so that neighbouring threads share a cell.
+    {
+        std::vector<int32_t> first(nv, INT32_MAX);
+        for (int64_t v = 0; v < nv; ++v)
+            for (int64_t t = v2e_ptr[v]; t < v2e_ptr[v + 1]; ++t) first[v] = std::min(first[v], ecell[v2e[t]]);
+        S.vb_vert.clear();
+        for (int64_t v = 0; v < nv; ++v)
+            if (!S.dir[v] && v2e_ptr[v + 1] > v2e_ptr[v]) S.vb_vert.push_back((int32_t)v);
+        std::stable_sort(S.vb_vert.begin(), S.vb_vert.end(),
+                         [&](int32_t a, int32_t b) { return first[a] < first[b]; });
+        S.vb_ptr.assign(1, 0);
+        S.vb_cell.clear();
+        S.vb_w.clear();
+        std::vector<int32_t> cells;
+        for (int32_t v : S.vb_vert) {
+            cells.clear();
+            for (int64_t t = v2e_ptr[v]; t < v2e_ptr[v + 1]; ++t) cells.push_back(ecell[v2e[t]]);
+            std::sort(cells.begin(), cells.end());
+            const double cnt = (double)cells.size();
+            for (size_t a = 0; a < cells.size();) {
+                size_t b = a;
+                while (b < cells.size() && cells[b] == cells[a]) ++b;
+                S.vb_cell.push_back(pack_cell(cells[a], bx, by));
+                S.vb_w.push_back((double)(b - a) / cnt);
+                a = b;
+            }
+            S.vb_ptr.push_back((int32_t)S.vb_cell.size());
+        }
+        // the same entries as one list sorted by cell (then vertex order)
+        const size_t nnz = S.vb_cell.size();
+        std::vector<int64_t> ord(nnz);
+        std::vector<int32_t> owner(nnz);
+        for (size_t i = 0; i < S.vb_vert.size(); ++i)
+            for (int32_t e = S.vb_ptr[i]; e < S.vb_ptr[i + 1]; ++e) owner[e] = S.vb_vert[i];
+        std::iota(ord.begin(), ord.end(), 0);
+        std::stable_sort(ord.begin(), ord.end(), [&](int64_t a, int64_t b) { return S.vb_cell[a] < S.vb_cell[b]; });
+        S.re_vert.resize(nnz);
+        S.re_cell.resize(nnz);
+        S.re_w.resize(nnz);
+        for (size_t i = 0; i < nnz; ++i) {
+            S.re_vert[i] = owner[ord[i]];
+            S.re_cell[i] = S.vb_cell[ord[i]];
+            S.re_w[i] = S.vb_w[ord[i]];
+        }
+    }
 
     // ---- element order on the device: by cell, then subdomain, then id -----
     S.elem_order.resize(ne);
@@ -588,7 +699,9 @@ cgs_status host_setup(const double* xyz, int64_t nv, const int32_t* conn, int64_
             }
         }
         close_tile((int32_t)ne);
-        // tile-major copies of the off-diagonals, zero-padded to kTileElems
+        // tile-major copies of the off-diagonals, zero-padded to kTileElems:
+        // [tile][slot / 4][element][slot % 4], so one 16-byte load gives an
+        // element four consecutive slots and a warp's load is contiguous
         const int64_t nt = (int64_t)S.tile_ptr.size() - 1;
         S.at_hi.assign((size_t)nt * kOff * kTileElems, 0.0f);
         S.at_lo.assign((size_t)nt * kOff * kTileElems, 0.0f);
@@ -596,7 +709,8 @@ cgs_status host_setup(const double* xyz, int64_t nv, const int32_t* conn, int64_
         for (int64_t t = 0; t < nt; ++t)
             for (int32_t i = S.tile_ptr[t]; i < S.tile_ptr[t + 1]; ++i)
                 for (int sl = 0; sl < kOff; ++sl) {
-                    const size_t dst = ((size_t)t * kOff + sl) * kTileElems + (i - S.tile_ptr[t]);
+                    const size_t dst =
+                        (((size_t)t * (kOff / 4) + sl / 4) * kTileElems + (i - S.tile_ptr[t])) * 4 + sl % 4;
                     S.at_hi[dst] = S.a28[(size_t)sl * ne + i];
                     S.at_lo[dst] = S.a28lo[(size_t)sl * ne + i];
                 }

@@ -102,7 +102,7 @@ def test_admission_by_footprint(ctx):
     try:
         fp = cgs.cgs_server_footprint(server, h)
         st0 = cgs.cgs_server_stats(server)
-        assert fp >= 56 * m.nv and st0["bytes_in_use"] == 0 and st0["arena_bytes"] >= 2 * fp
+        assert fp >= 48 * m.nv and st0["bytes_in_use"] == 0 and st0["arena_bytes"] >= 2 * fp
         rng = np.random.default_rng(7)
         reqs = []
         for i in range(4):
