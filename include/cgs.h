@@ -91,6 +91,7 @@ typedef struct {
     int32_t tile_tma;      /* schedule: 1 = element tiles staged by TMA, 0 = streamed  */
     int64_t n_box_entries; /* (vertex, cell) entries of the per-vertex box lists     */
     int64_t n_lane_packs;  /* lane packs of the mixed-form local solves (32 each)    */
+    int32_t persistent;    /* 1 = solves run the persistent loop (mixed forms)       */
 } cgs_mesh_info_t;
 
 /* Kernel classes reported by the profiler. */
@@ -106,7 +107,8 @@ typedef enum {
     CGS_K_PCG_DOTS = 7,    /* z.r, z.q (inside CGS_K_INTERP when there is a box space) */
     CGS_K_PCG_P = 8,       /* p = z + beta p                                          */
     CGS_K_OTHER = 9,       /* fills, copies, init, final residual                     */
-    CGS_K_COUNT = 10
+    CGS_K_LOOP = 10,       /* the persistent loop: whole iterations in one launch     */
+    CGS_K_COUNT = 11
 } cgs_kernel_class;
 
 /* ---- context --------------------------------------------------------------
@@ -234,17 +236,21 @@ cgs_status cgs_batch_solve(cgs_batch* batch, const double* const* b, double* con
                            int* iters, double* relres, int* status, void* stream);
 int64_t cgs_batch_launches(const cgs_batch* batch);
 /* Autotuner: time the local solves over subdomain chunks {8,16,32,64}, the
- * vector kernels over vertex chunks {256,...,2048} and, in the mixed forms,
- * the tiled operator applies with TMA-staged or thread-streamed element
- * tiles, on the object's own data; keep the fastest schedule (rebuilds the
- * work tables and the loop graph).
+ * vector kernels over vertex chunks {256,...,2048}, the interpolation over
+ * box-list chunks {256, 512, 1024} and, in the mixed forms, the tiled
+ * operator applies with TMA-staged or thread-streamed element tiles, on the
+ * object's own data; keep the fastest schedule (rebuilds the work tables and
+ * the loop graph).
  * Synchronous; call between solves.  Setup picks a default schedule that
  * gives about four blocks per SM.                                          */
 cgs_status cgs_mesh_tune(cgs_mesh* mesh, void* stream);
 /* Set the schedule explicitly: vert_chunk a multiple of 256 in [256, 8192],
- * sub_chunk a multiple of 8 in [8, 512], tile_tma 0 or 1 (INVALID_ARG
- * otherwise).  Synchronous; call between solves.                          */
-cgs_status cgs_mesh_set_schedule(cgs_mesh* mesh, int vert_chunk, int sub_chunk, int tile_tma);
+ * sub_chunk a multiple of 8 in [8, 512], tile_tma 0 or 1, persistent 1 (run
+ * the mixed-form iterations in one persistent cooperative launch with grid
+ * barriers between the phases) or 0 / -1 (one launch per phase inside the
+ * device-side graph loop, the default); INVALID_ARG otherwise.
+ * Synchronous; call between solves.                                        */
+cgs_status cgs_mesh_set_schedule(cgs_mesh* mesh, int vert_chunk, int sub_chunk, int tile_tma, int persistent);
 cgs_status cgs_batch_tune(cgs_batch* batch, void* stream);
 cgs_status cgs_solve_batched(cgs_mesh* const* meshes, int nmesh, const double* const* b, double* const* x,
                              int nrhs, double rtol, int maxit, int* iters, double* relres, void* stream);
@@ -276,6 +282,10 @@ cgs_status cgs_solve_batched(cgs_mesh* const* meshes, int nmesh, const double* c
  *   Synchronous.  active/queued/finished (each may be NULL) report counts.
  * cgs_poll: done = 1 once the request has finished (then iters, relres and
  *   status are its results and the ticket is released).
+ * cgs_server_drain: copies up to `cap` requests finished since the last
+ *   drain (ticket and, where the arrays are not NULL, iters, relres, status)
+ *   and releases their tickets; returns how many, or -1 on a bad argument.
+ *   A ticket already released by cgs_poll is skipped.
  * cgs_server_footprint: arena bytes a request on `mesh` would hold.
  * cgs_server_stats: arena capacity and bytes held by running solves.       */
 typedef struct cgs_server cgs_server;
@@ -286,6 +296,7 @@ cgs_status cgs_submit(cgs_server* server, cgs_mesh* mesh, const double* b, doubl
 cgs_status cgs_server_step(cgs_server* server, int iterations, void* stream, int* active, int* queued,
                            int* finished);
 cgs_status cgs_poll(cgs_server* server, uint64_t ticket, int* done, int* iters, double* relres, int* status);
+int cgs_server_drain(cgs_server* server, uint64_t* tickets, int* iters, double* relres, int* status, int cap);
 cgs_status cgs_server_footprint(const cgs_server* server, const cgs_mesh* mesh, size_t* bytes);
 cgs_status cgs_server_stats(const cgs_server* server, size_t* arena_bytes, size_t* bytes_in_use, int* active,
                             int* queued);

@@ -30,12 +30,13 @@ EXPORTS = (
     "cgs_profile_enable", "cgs_profile_read", "cgs_batch_create", "cgs_batch_free", "cgs_batch_solve",
     "cgs_batch_launches", "cgs_solve_batched", "cgs_mesh_tune", "cgs_mesh_set_schedule", "cgs_batch_tune",
     "cgs_server_create",
-    "cgs_server_free", "cgs_submit", "cgs_server_step", "cgs_poll", "cgs_server_footprint", "cgs_server_stats",
+    "cgs_server_free", "cgs_submit", "cgs_server_step", "cgs_poll", "cgs_server_drain", "cgs_server_footprint",
+    "cgs_server_stats",
     "cgs_server_launches", "cgs_status_string",
     "cgs_last_error",
 )
 KERNEL_CLASSES = ("apply_A64", "apply_A32", "local", "restrict", "coarse", "interp", "pcg_xr", "pcg_dots",
-                  "pcg_p", "other")
+                  "pcg_p", "other", "loop")
 
 
 class CGSError(RuntimeError):
@@ -54,7 +55,8 @@ class MeshInfo(C.Structure):
                 ("n_r", C.c_int64), ("max_sub_dofs", C.c_int64), ("sum_sub_dofs", C.c_int64),
                 ("footprint_bytes", C.c_size_t), ("setup_seconds", C.c_double),
                 ("kernel_launches", C.c_int64), ("vert_chunk", C.c_int32), ("sub_chunk", C.c_int32),
-                ("tile_tma", C.c_int32), ("n_box_entries", C.c_int64), ("n_lane_packs", C.c_int64)]
+                ("tile_tma", C.c_int32), ("n_box_entries", C.c_int64), ("n_lane_packs", C.c_int64),
+                ("persistent", C.c_int32)]
 
 
 _lib = None
@@ -100,11 +102,12 @@ def load(path: str = LIB_PATH):
         "cgs_submit": ([P, P, P, P, C.POINTER(C.c_uint64)], I32),
         "cgs_server_step": ([P, I32, P, C.POINTER(I32), C.POINTER(I32), C.POINTER(I32)], I32),
         "cgs_poll": ([P, C.c_uint64, C.POINTER(I32), C.POINTER(I32), C.POINTER(D), C.POINTER(I32)], I32),
+        "cgs_server_drain": ([P, C.POINTER(C.c_uint64), C.POINTER(I32), C.POINTER(D), C.POINTER(I32), I32], I32),
         "cgs_server_footprint": ([P, P, C.POINTER(C.c_size_t)], I32),
         "cgs_server_stats": ([P, C.POINTER(C.c_size_t), C.POINTER(C.c_size_t), C.POINTER(I32), C.POINTER(I32)], I32),
         "cgs_server_launches": ([P], I64),
         "cgs_batch_tune": ([P, P], I32),
-        "cgs_mesh_set_schedule": ([P, I32, I32, I32], I32),
+        "cgs_mesh_set_schedule": ([P, I32, I32, I32, I32], I32),
         "cgs_status_string": ([I32], C.c_char_p),
         "cgs_last_error": ([], C.c_char_p),
     }
@@ -310,8 +313,8 @@ def cgs_mesh_tune(mesh, stream=None):
     _check(load().cgs_mesh_tune(mesh, _stream(stream)), "cgs_mesh_tune")
 
 
-def cgs_mesh_set_schedule(mesh, vert_chunk, sub_chunk, tile_tma):
-    _check(load().cgs_mesh_set_schedule(mesh, int(vert_chunk), int(sub_chunk), int(tile_tma)),
+def cgs_mesh_set_schedule(mesh, vert_chunk, sub_chunk, tile_tma, persistent=-1):
+    _check(load().cgs_mesh_set_schedule(mesh, int(vert_chunk), int(sub_chunk), int(tile_tma), int(persistent)),
            "cgs_mesh_set_schedule")
 
 
@@ -343,6 +346,18 @@ def cgs_server_create(ctx, max_slots, pool_nv, pool_nr, prec="fp32", form="hybri
     _check(load().cgs_server_create(ctx, int(max_slots), int(pool_nv), int(pool_nr), PREC[prec], FORM[form],
                                     float(rtol), int(maxit), C.byref(out)), "cgs_server_create")
     return out
+
+
+def cgs_server_drain(server, cap=4096):
+    """Requests finished since the last drain: list of (ticket, iters, relres, status)."""
+    t = (C.c_uint64 * cap)()
+    it = (C.c_int * cap)()
+    rr = (C.c_double * cap)()
+    st = (C.c_int * cap)()
+    n = load().cgs_server_drain(server, t, it, rr, st, int(cap))
+    if n < 0:
+        _check(ERR_INVALID_ARG, "cgs_server_drain")
+    return [(int(t[i]), int(it[i]), float(rr[i]), int(st[i])) for i in range(n)]
 
 
 def cgs_server_footprint(server, mesh) -> int:

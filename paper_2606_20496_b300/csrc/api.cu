@@ -90,6 +90,10 @@ struct Engine {
     cudaGraphExec_t gexec = nullptr;
     bool graph_failed = false;
     int last_iters = 8;
+    // persistent loop (mixed forms, schedule.persistent): its grid barrier
+    // and the resident block count
+    GridBar* bar = nullptr;
+    int pblocks = 0;
     // launch accounting and the optional event profiler
     int64_t launches = 0;
     bool prof = false;
@@ -102,6 +106,8 @@ struct Engine {
     void release() {
         if (gexec) cudaGraphExecDestroy(gexec);
         gexec = nullptr;
+        if (bar) cudaFree(bar);
+        bar = nullptr;
         tables.release();
         for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
         ev_pool.clear();
@@ -330,6 +336,29 @@ cgs_status build_loop_graph(Engine& E) {
     return CGS_OK;
 }
 
+// Whether the engine runs its iterations in the persistent loop (mixed forms
+// only): by the schedule, or (auto) when the element tiles of a launch fit
+// about two per resident block.
+bool use_persistent(Engine& E, const Schedule& sch) {
+    if (E.f64 || sch.persistent == 0) return false;
+    if (!E.pblocks) E.pblocks = persistent_blocks(E.prec);
+    if (E.pblocks <= 0) return false;
+    return sch.persistent == 1;
+}
+
+// Launch the persistent loop for up to max_iters iterations of every slot.
+cudaError_t persistent_launch(Engine& E, int max_iters, cudaStream_t st) {
+    if (!E.bar) {
+        cudaError_t e = cudaMalloc(&E.bar, sizeof(GridBar));
+        if (e != cudaSuccess) return e;
+    }
+    if (!E.pblocks) E.pblocks = persistent_blocks(E.prec);
+    cudaError_t e = cudaMemsetAsync(E.bar, 0, sizeof(GridBar), st);
+    if (e != cudaSuccess) return e;
+    K(CGS_K_LOOP, e = launch_pcg_persistent(E.P, E.V, E.prec, E.form == CGS_HYBRID, E.bar, max_iters, E.pblocks, st));
+    return e;
+}
+
 // Solve every slot of the engine: V.b / V.bptr give the right-hand sides,
 // the iterates stay in V.x (copied out through V.xptr when set).  On return
 // E.S_host holds every slot's scalars (iters, status, res2, b2).
@@ -337,12 +366,16 @@ cgs_status engine_solve(Engine& E, double rtol, int maxit, cudaStream_t st) {
     const Plan& P = E.P;
     const Vecs& V = E.V;
     pcg_start(E, P, rtol, maxit, st);
-    const bool use_graph = !E.prof && !E.graph_failed;
+    const bool persistent = use_persistent(E, E.sch);
+    const bool use_graph = !E.prof && !E.graph_failed && !persistent;
     if (use_graph && !E.gexec) {
         if (build_loop_graph(E) != CGS_OK) E.graph_failed = true;
     }
     const size_t sbytes = sizeof(SolveScalars) * (size_t)P.nslots;
-    if (use_graph && E.gexec) {
+    if (persistent) {
+        // every iteration in one cooperative launch
+        CGS_CUDA(persistent_launch(E, maxit + 2, st));
+    } else if (use_graph && E.gexec) {
         // the whole iteration loop runs on the device
         CGS_CUDA(cudaGraphLaunch(E.gexec, st));
         E.launches += 1;
@@ -458,6 +491,8 @@ cudaError_t set_schedule(Engine& E, const Schedule& sch) {
     return cudaSuccess;
 }
 
+bool P_any_nr(const Engine& E) { return E.P.any_nr; }
+
 // Autotuner: time the local solves for each subdomain chunk and a vertex
 // kernel for each vertex chunk on the engine's own data, keep the fastest.
 cgs_status tune_engine(Engine& E, cudaStream_t st) {
@@ -502,6 +537,22 @@ cgs_status tune_engine(Engine& E, cudaStream_t st) {
         if (ms < best_vert) {
             best_vert = ms;
             best.vert_chunk = vc;
+        }
+    }
+    // box-list vertices per interpolation block
+    if (P_any_nr(E)) {
+        float best_box = 1e30f;
+        for (int bc : {256, 512, 1024}) {
+            Schedule t = best;
+            t.box_chunk = bc;
+            if (set_schedule(E, t) != cudaSuccess) continue;
+            const float ms = time_it([&]() {
+                launch_interp_add(E.P, V, E.f64, V.ur, E.f64 ? nullptr : V.ur32, V.z, false, st);
+            });
+            if (ms < best_box) {
+                best_box = ms;
+                best.box_chunk = bc;
+            }
         }
     }
     // mixed forms: element tiles staged by TMA or streamed by the threads
@@ -667,6 +718,12 @@ cgs_status cgs_mesh_setup(cgs_ctx* ctx, const double* xyz, int64_t nv, const int
         d.nre = (int64_t)hs.re_vert.size();
         UP(d.re_vert, hs.re_vert);
         UP(d.re_cell, hs.re_cell);
+        d.nrng = (int64_t)hs.re_rng.size() / 2;
+        {
+            const int32_t* rp = nullptr;
+            UP(rp, hs.re_rng);
+            d.re_rng = reinterpret_cast<const int2*>(rp);
+        }
         if (f64) {
             UP(d.vb_w64, hs.vb_w);
             UP(d.re_w64, hs.re_w);
@@ -727,7 +784,8 @@ cgs_status cgs_mesh_setup(cgs_ctx* ctx, const double* xyz, int64_t nv, const int
                     const double s = mx > 0 ? mx : 1.0;
                     sc[(size_t)P * 32 + l] = (float)s;
                     for (int64_t e = 0; e < T; ++e)
-                        h[ao + (e / 8) * 256 + l * 8 + e % 8] = __float2half_rn((float)(hs.pack_inv[ao + l * T + e] / s));
+                        h[ao + (e / 8) * 256 + l * 8 + e % 8] =
+                            __float2half_rn((float)(hs.pack_inv[ao + l * T + e] / s));
                 }
             }
             UP(d.pack_inv16, h);
@@ -782,7 +840,7 @@ cgs_status cgs_mesh_setup(cgs_ctx* ctx, const double* xyz, int64_t nv, const int
         m->d_dev = const_cast<DevMesh*>(dd);
     }
     // one solve slot and its work tables
-    m->sizes = MeshSizes{nv, ne, d.ntiles, hs.n_wsub, hs.nr, d.n_pack, d.nvb, d.nre};
+    m->sizes = MeshSizes{nv, ne, d.ntiles, hs.n_wsub, hs.nr, d.n_pack, d.nvb, d.nrng};
     Engine& E = m->E;
     E.f64 = f64;
     E.prec = prm.prec;
@@ -799,6 +857,7 @@ cgs_status cgs_mesh_setup(cgs_ctx* ctx, const double* xyz, int64_t nv, const int
         Schedule smallest;
         smallest.vert_chunk = 256;
         smallest.sub_chunk = 8;
+        smallest.box_chunk = 256;
         cudaError_t e = alloc_pools(m->mem, E, nv, hs.nr, mesh_partial_slots(sz, smallest), 1);
         if (e != cudaSuccess) return cleanup(cuda_fail(e, "scratch"));
         e = set_schedule(E, default_schedule(nv, hs.n_wsub, d.n_pack));
@@ -859,6 +918,7 @@ cgs_status cgs_mesh_info(const cgs_mesh* m, cgs_mesh_info_t* info) {
     info->vert_chunk = m->E.sch.vert_chunk;
     info->sub_chunk = m->E.sch.sub_chunk;
     info->tile_tma = m->E.sch.tile_tma;
+    info->persistent = use_persistent(const_cast<Engine&>(m->E), m->E.sch) ? 1 : 0;
     return CGS_OK;
 }
 
@@ -1111,6 +1171,7 @@ cgs_status cgs_batch_create(cgs_ctx* ctx, cgs_mesh* const* meshes, int nmesh, in
             Schedule smallest;
             smallest.vert_chunk = 256;
             smallest.sub_chunk = 8;
+            smallest.box_chunk = 256;
             const int64_t ps = mesh_partial_slots(sizes[i], smallest);
             for (int k = 0; k < kWorkKinds; ++k)
                 for (const Work& w0 : one[k])
@@ -1132,6 +1193,7 @@ cgs_status cgs_batch_create(cgs_ctx* ctx, cgs_mesh* const* meshes, int nmesh, in
         Schedule smallest;
         smallest.vert_chunk = 256;
         smallest.sub_chunk = 8;
+        smallest.box_chunk = 256;
         for (int i = 0; i < nmesh; ++i) total_p += (int64_t)nrhs * mesh_partial_slots(sizes[i], smallest);
     }
     if (total_p >= INT32_MAX || total_r >= INT32_MAX) return cleanup(fail(CGS_ERR_INVALID_ARG, "batch too large"));
@@ -1211,16 +1273,17 @@ cgs_status cgs_batch_solve(cgs_batch* B, const double* const* b, double* const* 
 
 int64_t cgs_batch_launches(const cgs_batch* B) { return B ? B->E.launches : 0; }
 
-cgs_status cgs_mesh_set_schedule(cgs_mesh* m, int vert_chunk, int sub_chunk, int tile_tma) {
+cgs_status cgs_mesh_set_schedule(cgs_mesh* m, int vert_chunk, int sub_chunk, int tile_tma, int persistent) {
     if (!m) return fail(CGS_ERR_INVALID_ARG, "null mesh");
     if (vert_chunk < 256 || vert_chunk > 8192 || vert_chunk % 256 || sub_chunk < 8 || sub_chunk > 512 ||
-        sub_chunk % 8 || (tile_tma != 0 && tile_tma != 1))
+        sub_chunk % 8 || (tile_tma != 0 && tile_tma != 1) || persistent < -1 || persistent > 1)
         return fail(CGS_ERR_INVALID_ARG, "schedule out of range");
     CGS_CUDA(cudaSetDevice(m->ctx->device));
-    Schedule sch;
+    Schedule sch = m->E.sch;
     sch.vert_chunk = vert_chunk;
     sch.sub_chunk = sub_chunk;
     sch.tile_tma = tile_tma;
+    sch.persistent = persistent;
     CGS_CUDA(set_schedule(m->E, sch));
     return CGS_OK;
 }
@@ -1343,6 +1406,7 @@ struct cgs_server {
         double relres;
     };
     std::unordered_map<uint64_t, Res> results;
+    std::deque<uint64_t> completed;   // finished tickets not yet drained
     uint64_t next_ticket = 1;
     // work tables of the current slots, of the slots admitted this step and
     // of the slots finished this step (capacity-grown device buffers)
@@ -1603,7 +1667,10 @@ cgs_status cgs_server_step(cgs_server* sv, int iterations, void* stream, int* ac
     // 3. iterate every running slot (slots that stop skip their blocks)
     if (!busy.empty()) {
         E.P = sv->P_main;
-        for (int i = 0; i < iterations; ++i) pcg_iteration(E, st);
+        if (use_persistent(E, sv->sch))
+            CGS_CUDA(persistent_launch(E, iterations, st));
+        else
+            for (int i = 0; i < iterations; ++i) pcg_iteration(E, st);
     }
     CGS_CUDA(cudaMemcpyAsync(E.S_host, E.V.S, sizeof(SolveScalars) * sv->max_slots, cudaMemcpyDeviceToHost, st));
     CGS_CUDA(cudaStreamSynchronize(st));
@@ -1626,6 +1693,7 @@ cgs_status cgs_server_step(cgs_server* sv, int iterations, void* stream, int* ac
             cgs_server::SlotState& ss = sv->slots[k];
             const SolveScalars& h = E.S_host[k];
             sv->results[ss.req.ticket] = cgs_server::Res{1, h.iters, (int)slot_status(h), slot_relres(h)};
+            sv->completed.push_back(ss.req.ticket);
             sv->reg_users[ss.reg]--;
             sv->av.release(ss.voff, ss.req.mesh->d.nv);
             sv->ar.release(ss.roff, ss.req.mesh->d.nr);
@@ -1654,6 +1722,27 @@ cgs_status cgs_poll(cgs_server* sv, uint64_t ticket, int* done, int* iters, doub
     if (status) *status = r.status;
     if (r.done) sv->results.erase(it);
     return CGS_OK;
+}
+
+int cgs_server_drain(cgs_server* sv, uint64_t* tickets, int* iters, double* relres, int* status, int cap) {
+    if (!sv || cap < 0 || (cap > 0 && !tickets)) {
+        fail(CGS_ERR_INVALID_ARG, "bad argument");
+        return -1;
+    }
+    int n = 0;
+    while (n < cap && !sv->completed.empty()) {
+        const uint64_t t = sv->completed.front();
+        sv->completed.pop_front();
+        auto it = sv->results.find(t);
+        if (it == sv->results.end()) continue;   // already taken by cgs_poll
+        tickets[n] = t;
+        if (iters) iters[n] = it->second.iters;
+        if (relres) relres[n] = it->second.relres;
+        if (status) status[n] = it->second.status;
+        sv->results.erase(it);
+        ++n;
+    }
+    return n;
 }
 
 cgs_status cgs_server_footprint(const cgs_server* sv, const cgs_mesh* mesh, size_t* bytes) {

@@ -69,6 +69,7 @@ struct HostSetup {
     std::vector<double> vb_w;          // elements of the vertex in that cell / elements of the vertex
     std::vector<int32_t> re_vert, re_cell;   // the same entries sorted by cell (restriction)
     std::vector<double> re_w;
+    std::vector<int32_t> re_rng;       // (begin, end) entry ranges within one cell, <= kBoxRange each
     std::vector<int64_t> box_active;   // nr, lexicographic box-vertex ids
     std::vector<double> ar_inv;        // nr*nr, A_r^{-1}, full symmetric, float64
     double seconds = 0.0;
@@ -112,6 +113,8 @@ struct DevMesh {
     const int32_t* re_cell = nullptr;  // packed, as vb_cell
     const double* re_w64 = nullptr;
     const float* re_w32 = nullptr;
+    int64_t nrng = 0;
+    const int2* re_rng = nullptr;      // nrng (begin, end) ranges of one cell's entries
     // subdomains of the warp kernels (n_sub of them: all in the FP64 form,
     // those with more than kLaneMaxM dofs in the mixed forms)
     const int32_t* sub_ptr = nullptr;  // n_sub+1 (int32 offsets into sub_idx)
@@ -169,6 +172,15 @@ struct Plan {
     bool tile_tma = false;                 // element tiles staged by TMA (else streamed by the threads)
 };
 
+// Grid-wide barrier of the persistent PCG kernel (device memory, zeroed
+// before each launch): arrival count, generation, error flag.
+struct GridBar {
+    unsigned int count;
+    unsigned int gen;
+    int error;
+    int pad;
+};
+
 // Device scalars of one PCG solve (kernels.cu).
 struct SolveScalars {
     double bnorm2;     // ||b||^2
@@ -223,6 +235,7 @@ inline int32_t pack_cell(int32_t c, int bx, int by) {
     return (c % bx) | (((c / bx) % by) << 10) | ((c / (bx * by)) << 20);
 }
 constexpr int kRowChunk = 4;      // reduced rows per block (one warp each)
+constexpr int kBoxRange = 256;    // restriction entries (of one cell) per warp
 
 // Vector pools of a set of slots, passed by value to every kernel.  A slot's
 // vector is pool + work.voff (vertex vectors) or pool + work.roff (reduced).

@@ -84,11 +84,21 @@ __device__ bool slot_publish(const double (&v)[NV], double* partials, int idx, i
     __syncthreads();
     if (!last) return false;
     __threadfence();
+    // four independent loads and sums per thread and round (the order is
+    // fixed by count and the block size: deterministic)
     double s[NV];
 #pragma unroll
     for (int i = 0; i < NV; ++i) {
-        s[i] = 0.0;
-        for (int b = threadIdx.x; b < count; b += blockDim.x) s[i] += __ldcg(&partials[(size_t)i * count + b]);
+        double a[4] = {0.0, 0.0, 0.0, 0.0};
+        const double* pi = partials + (size_t)i * count;
+        for (int b = threadIdx.x; b < count; b += 4 * blockDim.x) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int bk = b + k * (int)blockDim.x;
+                if (bk < count) a[k] += __ldcg(&pi[bk]);
+            }
+        }
+        s[i] = (a[0] + a[1]) + (a[2] + a[3]);
     }
     block_sum<NV>(s);
     if (threadIdx.x == 0) {
@@ -125,6 +135,13 @@ __device__ __forceinline__ void load_conn(const int32_t* __restrict__ conn, int6
     if (is_done(S)) return;                              \
     const DevMesh& M = meshes[w.mesh];                   \
     (void)M;
+// The same for a per-item device function that gets its work item `w`
+// (kernels launched one block per item, or the persistent loop).
+#define CGS_ITEM_PROLOGUE()                              \
+    SolveScalars* S = V.S ? V.S + w.slot : nullptr;      \
+    if (is_done(S)) return;                              \
+    const DevMesh& M = meshes[w.mesh];                   \
+    (void)M;
 
 // ---------------------------------------------------------------------------
 // Operator apply, float64 (FP64 form and the final true residual), 36 stored
@@ -133,11 +150,9 @@ __device__ __forceinline__ void load_conn(const int32_t* __restrict__ conn, int6
 // alpha = rho / pq in the slot's last block.
 // ---------------------------------------------------------------------------
 template <bool kDot>
-__global__ void __launch_bounds__(kBlock) apply64_kernel(const DevMesh* __restrict__ meshes,
-                                                         const Work* __restrict__ work, Vecs V,
-                                                         const double* __restrict__ xin, double* __restrict__ yout,
-                                                         double alpha) {
-    CGS_WORK_PROLOGUE();
+__device__ __forceinline__ void apply64_item(const DevMesh* __restrict__ meshes, const Work& w, Vecs V,
+                                             const double* __restrict__ xin, double* __restrict__ yout, double alpha) {
+    CGS_ITEM_PROLOGUE();
     const double* x = xin + w.voff;
     double* y = yout + w.voff;
     const int64_t ne = M.ne;
@@ -185,6 +200,13 @@ __global__ void __launch_bounds__(kBlock) apply64_kernel(const DevMesh* __restri
             }
         }
     }
+}
+template <bool kDot>
+__global__ void __launch_bounds__(kBlock) apply64_kernel(const DevMesh* __restrict__ meshes,
+                                                         const Work* __restrict__ work, Vecs V,
+                                                         const double* __restrict__ xin, double* __restrict__ yout,
+                                                         double alpha) {
+    apply64_item<kDot>(meshes, work[blockIdx.x], V, xin, yout, alpha);
 }
 
 // ---------------------------------------------------------------------------
@@ -473,16 +495,15 @@ __device__ __forceinline__ void tile_vertex_ids(const DevMesh& M, int v0, int nv
 // other tile touches it, compensated global atomics otherwise.  Also sums
 // p.Ap and finalises alpha in the slot's last block.
 template <bool kTma>
-__global__ void __launch_bounds__(kBlock, kTma ? 3 : 4) apply_pair_tiled_kernel(const DevMesh* __restrict__ meshes,
-                                                                                 const Work* __restrict__ work,
-                                                                                 Vecs V, int wait_limit) {
+__device__ __forceinline__ void apply_pair_tiled_item(const DevMesh* __restrict__ meshes, const Work& w, Vecs V,
+                                                      int wait_limit) {
     extern __shared__ __align__(128) unsigned char smem[];
     float2* ps = reinterpret_cast<float2*>(smem);
     float2* ys = ps + kTileVerts;
     float4* sh_hi = reinterpret_cast<float4*>(ys + kTileVerts);
     float4* sh_lo = sh_hi + kGroups * kTileElems;
     __shared__ uint64_t bar;
-    CGS_WORK_PROLOGUE();
+    CGS_ITEM_PROLOGUE();
     const float2* p2 = V.p2 + w.voff;
     float2* q2 = V.q2 + w.voff;
     const int t = w.begin;
@@ -526,7 +547,7 @@ __global__ void __launch_bounds__(kBlock, kTma ? 3 : 4) apply_pair_tiled_kernel(
             L = sh_lo[threadIdx.x];
         }
     }
-    float eh = 0.0f, el = 0.0f;   // p.Ap share of this thread's element
+    float eh = 0.0f, el = 0.0f;   // this thread's share of p.Ap
     if (ok && has_e) {
         float xh[8], xl[8], yh[8], yl[8];
 #pragma unroll
@@ -546,9 +567,6 @@ __global__ void __launch_bounds__(kBlock, kTma ? 3 : 4) apply_pair_tiled_kernel(
         for (int k = 0; k < 8; ++k) {
             float h, l;
             fast_two_sum(yh[k], yl[k], h, l);
-            float ph, pl;
-            pair_mul(xh[k], xl[k], h, l, ph, pl);
-            pair_acc(eh, el, ph, pl);
             const int lk = loc_of(lw, k);
             if (lk >= 0) {
                 const float old = atomicAdd(&ys[lk].x, h);
@@ -565,6 +583,8 @@ __global__ void __launch_bounds__(kBlock, kTma ? 3 : 4) apply_pair_tiled_kernel(
             const int v = (int)(raw & ~kSharedBit);
             float h, l;
             fast_two_sum(ys[i].x, ys[i].y, h, l);
+            // p.Ap summed as p_v times this tile's share of (A p)_v
+            pr_dot_acc(eh, el, ps[i], make_float2(h, l));
             if (!(raw & kSharedBit)) {
                 q2[v] = make_float2(h, l);
             } else {
@@ -593,21 +613,25 @@ __global__ void __launch_bounds__(kBlock, kTma ? 3 : 4) apply_pair_tiled_kernel(
         }
     }
 }
+template <bool kTma>
+__global__ void __launch_bounds__(kBlock, kTma ? 3 : 4) apply_pair_tiled_kernel(const DevMesh* __restrict__ meshes,
+                                                                                 const Work* __restrict__ work,
+                                                                                 Vecs V, int wait_limit) {
+    apply_pair_tiled_item<kTma>(meshes, work[blockIdx.x], V, wait_limit);
+}
 
 // y += alpha A x in float32 (inner apply s -= A l of the hybrid step); the
 // same two variants (TMA-staged tile or streamed groups).
 template <bool kTma>
-__global__ void __launch_bounds__(kBlock, kTma ? 4 : 5) apply28f_tiled_kernel(const DevMesh* __restrict__ meshes,
-                                                                               const Work* __restrict__ work, Vecs V,
-                                                                               const float* __restrict__ xin,
-                                                                               float* __restrict__ yout, float alpha,
-                                                                               int wait_limit) {
+__device__ __forceinline__ void apply28f_tiled_item(const DevMesh* __restrict__ meshes, const Work& w, Vecs V,
+                                                    const float* __restrict__ xin, float* __restrict__ yout,
+                                                    float alpha, int wait_limit) {
     extern __shared__ __align__(128) unsigned char smem[];
     float* xs = reinterpret_cast<float*>(smem);
     float* ys = xs + kTileVerts;
     float4* sh_a = reinterpret_cast<float4*>(ys + kTileVerts);
     __shared__ uint64_t bar;
-    CGS_WORK_PROLOGUE();
+    CGS_ITEM_PROLOGUE();
     const float* x = xin + w.voff;
     float* y = yout + w.voff;
     const int t = w.begin;
@@ -669,6 +693,14 @@ __global__ void __launch_bounds__(kBlock, kTma ? 4 : 5) apply28f_tiled_kernel(co
             atomicAdd(&y[v], alpha * ys[i]);
     }
 }
+template <bool kTma>
+__global__ void __launch_bounds__(kBlock, kTma ? 4 : 5) apply28f_tiled_kernel(const DevMesh* __restrict__ meshes,
+                                                                               const Work* __restrict__ work, Vecs V,
+                                                                               const float* __restrict__ xin,
+                                                                               float* __restrict__ yout, float alpha,
+                                                                               int wait_limit) {
+    apply28f_tiled_item<kTma>(meshes, work[blockIdx.x], V, xin, yout, alpha, wait_limit);
+}
 
 // ---------------------------------------------------------------------------
 // Local solves, one warp per subdomain with m_p <= 64 dofs.  The explicit
@@ -721,11 +753,9 @@ template <>
 __device__ __forceinline__ const float* overlap_weights<float>(const DevMesh& M) { return M.wov32; }
 
 template <typename T, typename Stor>
-__global__ void __launch_bounds__(kBlock) local_warp_kernel(const DevMesh* __restrict__ meshes,
-                                                            const Work* __restrict__ work, Vecs V,
-                                                            const T* __restrict__ rin, T* __restrict__ outv,
-                                                            int weighted) {
-    CGS_WORK_PROLOGUE();
+__device__ __forceinline__ void local_warp_item(const DevMesh* __restrict__ meshes, const Work& w, Vecs V,
+                                                const T* __restrict__ rin, T* __restrict__ outv, int weighted) {
+    CGS_ITEM_PROLOGUE();
     const T* r = rin + w.voff;
     T* out = outv + w.voff;
     const Stor* inv = inverse_store<Stor>(M);
@@ -802,15 +832,20 @@ __global__ void __launch_bounds__(kBlock) local_warp_kernel(const DevMesh* __res
         }
     }
 }
+template <typename T, typename Stor>
+__global__ void __launch_bounds__(kBlock) local_warp_kernel(const DevMesh* __restrict__ meshes,
+                                                            const Work* __restrict__ work, Vecs V,
+                                                            const T* __restrict__ rin, T* __restrict__ outv,
+                                                            int weighted) {
+    local_warp_item<T, Stor>(meshes, work[blockIdx.x], V, rin, outv, weighted);
+}
 
 // Subdomains with more than 64 dofs: the whole block on one subdomain, rows
 // spread over threads.
 template <typename T, typename Stor>
-__global__ void __launch_bounds__(kBlock) local_block_kernel(const DevMesh* __restrict__ meshes,
-                                                             const Work* __restrict__ work, Vecs V,
-                                                             const T* __restrict__ rin, T* __restrict__ outv,
-                                                             int weighted) {
-    CGS_WORK_PROLOGUE();
+__device__ __forceinline__ void local_block_item(const DevMesh* __restrict__ meshes, const Work& w, Vecs V,
+                                                 const T* __restrict__ rin, T* __restrict__ outv, int weighted) {
+    CGS_ITEM_PROLOGUE();
     const T* r = rin + w.voff;
     T* out = outv + w.voff;
     const Stor* inv = inverse_store<Stor>(M);
@@ -828,6 +863,13 @@ __global__ void __launch_bounds__(kBlock) local_block_kernel(const DevMesh* __re
             atomicAdd(&out[v], wov ? y * wov[v] : y);
         }
     }
+}
+template <typename T, typename Stor>
+__global__ void __launch_bounds__(kBlock) local_block_kernel(const DevMesh* __restrict__ meshes,
+                                                             const Work* __restrict__ work, Vecs V,
+                                                             const T* __restrict__ rin, T* __restrict__ outv,
+                                                             int weighted) {
+    local_block_item<T, Stor>(meshes, work[blockIdx.x], V, rin, outv, weighted);
 }
 
 // ---------------------------------------------------------------------------
@@ -919,11 +961,9 @@ __device__ __forceinline__ void lane_dispatch(int Mc, const Entries& A, const in
 
 // out += W_ov sum_p R_p^T A_p^{-1} R_p r over the lane packs (float r, out).
 template <typename Stor>
-__global__ void __launch_bounds__(kBlock, 2) local_lane_kernel(const DevMesh* __restrict__ meshes,
-                                                               const Work* __restrict__ work, Vecs V,
-                                                               const float* __restrict__ rin,
-                                                               float* __restrict__ outv, int weighted) {
-    CGS_WORK_PROLOGUE();
+__device__ __forceinline__ void local_lane_item(const DevMesh* __restrict__ meshes, const Work& w, Vecs V,
+                                                const float* __restrict__ rin, float* __restrict__ outv, int weighted) {
+    CGS_ITEM_PROLOGUE();
     const float* r = rin + w.voff;
     float* out = outv + w.voff;
     const float* wov = weighted ? M.wov32 : nullptr;
@@ -941,6 +981,13 @@ __global__ void __launch_bounds__(kBlock, 2) local_lane_kernel(const DevMesh* __
             lane_dispatch(Mc, A, idx, r, out, wov, lane);
         }
     }
+}
+template <typename Stor>
+__global__ void __launch_bounds__(kBlock, 2) local_lane_kernel(const DevMesh* __restrict__ meshes,
+                                                               const Work* __restrict__ work, Vecs V,
+                                                               const float* __restrict__ rin,
+                                                               float* __restrict__ outv, int weighted) {
+    local_lane_item<Stor>(meshes, work[blockIdx.x], V, rin, outv, weighted);
 }
 
 // ---------------------------------------------------------------------------
@@ -1039,68 +1086,85 @@ __device__ __forceinline__ int cell_weights(const BoxGrid<T>& g, int pc, T x, T 
 __device__ __forceinline__ const double* box_w(const DevMesh& M, double) { return M.vb_w64; }
 __device__ __forceinline__ const float* box_w(const DevMesh& M, float) { return M.vb_w32; }
 
-// r_r += J^T W s over the cell-sorted box-list entries: thread i takes entry
-// (v, c, weight) and forms w_m^c(x_v) * weight * s_v for the 8 corners m of
-// cell c; a segmented warp reduction over the lanes of one cell sums them,
-// and lane m of the segment adds corner m's total.  kPairOut: r_r is a float
-// pair per entry (compensated float atomics); otherwise float64.
+// r_r += J^T W s over the cell-sorted box-list entries: each warp takes a
+// range of one cell's entries (v, weight) (<= kBoxRange, a work item holds 8
+// ranges), forms w_m(x_v) * weight * s_v for the cell's 8 corners, sums them
+// over the warp (reduce-scatter) and adds each corner's total to r_r once.
+// kPairOut: r_r is a float pair per entry (compensated float atomics);
+// otherwise float64.
 __device__ __forceinline__ const double* rent_w(const DevMesh& M, double) { return M.re_w64; }
 __device__ __forceinline__ const float* rent_w(const DevMesh& M, float) { return M.re_w32; }
 
+// Reduce-scatter of 8 values over a warp: lane 4m ends with the warp's total
+// of value m (lanes exchange halves of their values, then sum over bits 1, 0).
+template <typename T>
+__device__ __forceinline__ T warp_scatter8(const T (&a)[8], int lane) {
+    T v4[4], v2[2];
+    const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        v4[k] = (b4 ? a[k + 4] : a[k]) + __shfl_xor_sync(0xffffffffu, b4 ? a[k] : a[k + 4], 16);
+#pragma unroll
+    for (int k = 0; k < 2; ++k)
+        v2[k] = (b3 ? v4[k + 2] : v4[k]) + __shfl_xor_sync(0xffffffffu, b3 ? v4[k] : v4[k + 2], 8);
+    T v1 = (b2 ? v2[1] : v2[0]) + __shfl_xor_sync(0xffffffffu, b2 ? v2[0] : v2[1], 4);
+    v1 += __shfl_xor_sync(0xffffffffu, v1, 2);
+    v1 += __shfl_xor_sync(0xffffffffu, v1, 1);
+    return v1;
+}
+
+template <typename T, typename Tin, bool kPairOut>
+__device__ __forceinline__ void restrict_item(const DevMesh* __restrict__ meshes, const Work& w, Vecs V,
+                                              const Tin* __restrict__ sin, void* __restrict__ rrv) {
+    CGS_ITEM_PROLOGUE();
+    const int r = w.begin + (int)(threadIdx.x >> 5);
+    if (r >= w.end) return;
+    const Tin* s = sin + w.voff;
+    const BoxGrid<T> g(M);
+    const auto vx = vertex_data(M, T(0));
+    const T* rw = rent_w(M, T(0));
+    const int lane = threadIdx.x & 31;
+    const int2 rg = __ldg(&M.re_rng[r]);
+    const int pc = __ldg(&M.re_cell[rg.x]);   // one cell per range
+    T acc[8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) acc[m] = T(0);
+    for (int i0 = rg.x + lane; i0 < rg.y; i0 += 64) {
+        // two entries per lane and round, their loads first
+        int v[2];
+        T f[2];
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const int i = i0 + 32 * k;
+            v[k] = i < rg.y ? __ldg(&M.re_vert[i]) : -1;
+            f[k] = i < rg.y ? __ldg(&rw[i]) : T(0);
+        }
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            if (v[k] < 0) continue;
+            T x, y, z, ic;
+            vx.load(v[k], x, y, z, ic);
+            T wt[8];
+            cell_weights(g, pc, x, y, z, wt);
+            const T fv = f[k] * (T)__ldg(&s[v[k]]);
+#pragma unroll
+            for (int m = 0; m < 8; ++m) acc[m] += wt[m] * fv;
+        }
+    }
+    const T tot = warp_scatter8(acc, lane);
+    if ((lane & 3) == 0) {
+        const int c = (pc & 1023) + g.bx * (((pc >> 10) & 1023) + g.by * (pc >> 20));
+        const int col = __ldg(&M.cell_cols[(size_t)c * 8 + (lane >> 2)]);
+        if (col >= 0)
+            pool_add(static_cast<double*>(rrv) + w.roff, static_cast<float2*>(rrv) + w.roff, col, one_sum(tot),
+                     std::integral_constant<bool, kPairOut>());
+    }
+}
 template <typename T, typename Tin, bool kPairOut>
 __global__ void __launch_bounds__(kBlock) restrict_kernel(const DevMesh* __restrict__ meshes,
                                                           const Work* __restrict__ work, Vecs V,
                                                           const Tin* __restrict__ sin, void* __restrict__ rrv) {
-    CGS_WORK_PROLOGUE();
-    const Tin* s = sin + w.voff;
-    double* rr = static_cast<double*>(rrv) + w.roff;
-    float2* rr2 = static_cast<float2*>(rrv) + w.roff;
-    const int64_t i = (int64_t)w.begin + threadIdx.x;
-    const bool valid = i < w.end;
-    T acc[8];
-#pragma unroll
-    for (int m = 0; m < 8; ++m) acc[m] = T(0);
-    int c = -1;
-    if (valid) {
-        const BoxGrid<T> g(M);
-        const auto vx = vertex_data(M, T(0));
-        const int v = __ldg(&M.re_vert[i]);
-        T x, y, z, ic;
-        vx.load(v, x, y, z, ic);
-        T wt[8];
-        c = cell_weights(g, __ldg(&M.re_cell[i]), x, y, z, wt);
-        const T f = __ldg(&rent_w(M, T(0))[i]) * (T)__ldg(&s[v]);
-#pragma unroll
-        for (int m = 0; m < 8; ++m) acc[m] = wt[m] * f;
-    }
-    const int lane = threadIdx.x & 31;
-    unsigned int todo = __ballot_sync(0xffffffffu, valid);
-    while (todo) {
-        const int leader = __ffs(todo) - 1;
-        const int cc = __shfl_sync(0xffffffffu, c, leader);
-        const bool mine = valid && c == cc;
-        todo &= ~__ballot_sync(0xffffffffu, mine);
-        // reduce-scatter of the segment's 8 corner sums over the warp: lanes
-        // exchange halves (4, 2, 1 values), then sum over lane bits 1 and 0;
-        // lane 4m ends with corner m's total
-        T v4[4], v2[2], v1;
-        const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const T lo = mine ? acc[k] : T(0), hi = mine ? acc[k + 4] : T(0);
-            v4[k] = (b4 ? hi : lo) + __shfl_xor_sync(0xffffffffu, b4 ? lo : hi, 16);
-        }
-#pragma unroll
-        for (int k = 0; k < 2; ++k) v2[k] = (b3 ? v4[k + 2] : v4[k]) + __shfl_xor_sync(0xffffffffu, b3 ? v4[k] : v4[k + 2], 8);
-        v1 = (b2 ? v2[1] : v2[0]) + __shfl_xor_sync(0xffffffffu, b2 ? v2[0] : v2[1], 4);
-        v1 += __shfl_xor_sync(0xffffffffu, v1, 2);
-        v1 += __shfl_xor_sync(0xffffffffu, v1, 1);
-        if ((lane & 3) == 0) {
-            const int m = lane >> 2;   // = 4 b4 + 2 b3 + b2
-            const int col = __ldg(&M.cell_cols[(size_t)cc * 8 + m]);
-            if (col >= 0) pool_add(rr, rr2, col, one_sum(v1), std::integral_constant<bool, kPairOut>());
-        }
-    }
+    restrict_item<T, Tin, kPairOut>(meshes, work[blockIdx.x], V, sin, rrv);
 }
 
 // z += W Q^T J_L u_r by vertex: z_v += sum_c weight_c sum_m w_m^c(x_v) u_r[m]
@@ -1109,46 +1173,59 @@ __global__ void __launch_bounds__(kBlock) restrict_kernel(const DevMesh* __restr
 // element-free vertices have z = 0): 1 = float64 vectors, 2 = float-pair r
 // and q; the slot's last block forms beta = -alpha (z.q) / rho, rho = z.r.
 template <typename T, typename Tu, int kDots>
-__global__ void __launch_bounds__(kBlock) interp_add_kernel(const DevMesh* __restrict__ meshes,
-                                                            const Work* __restrict__ work, Vecs V,
-                                                            const Tu* __restrict__ urv, T* __restrict__ zv) {
-    CGS_WORK_PROLOGUE();
+__device__ __forceinline__ void interp_add_item(const DevMesh* __restrict__ meshes, const Work& w, Vecs V,
+                                                const Tu* __restrict__ urv, T* __restrict__ zv) {
+    CGS_ITEM_PROLOGUE();
     const Tu* ur = urv + w.roff;
     T* z = zv + w.voff;
-    const int64_t i = (int64_t)w.begin + threadIdx.x;
     double zr = 0.0, zq = 0.0;
     float rh = 0.0f, rl = 0.0f, qh = 0.0f, ql = 0.0f;
-    if (i < w.end) {
-        const BoxGrid<T> g(M);
-        const auto vx = vertex_data(M, T(0));
-        const T* bw = box_w(M, T(0));
-        const int v = __ldg(&M.vb_vert[i]);
-        const int e0 = __ldg(&M.vb_ptr[i]), e1 = __ldg(&M.vb_ptr[i + 1]);
-        T x, y, zz, ic;
-        vx.load(v, x, y, zz, ic);
-        T val = T(0);
-        if (M.nr > 0) {
-            for (int e = e0; e < e1; ++e) {
-                T wt[8];
-                const int c = cell_weights(g, __ldg(&M.vb_cell[e]), x, y, zz, wt);
-                T sum = T(0);
+    const BoxGrid<T> g(M);
+    const auto vx = vertex_data(M, T(0));
+    const T* bw = box_w(M, T(0));
+    // four vertices per thread and round, their list heads loaded first
+    for (int64_t i0 = (int64_t)w.begin + threadIdx.x; i0 < w.end; i0 += 4 * (int64_t)blockDim.x) {
+        int v[4], e0[4], e1[4];
 #pragma unroll
-                for (int m = 0; m < 8; ++m) {
-                    const int col = __ldg(&M.cell_cols[(size_t)c * 8 + m]);
-                    sum += wt[m] * (col >= 0 ? (T)__ldg(&ur[col]) : T(0));
-                }
-                val += __ldg(&bw[e]) * sum;
+        for (int k = 0; k < 4; ++k) {
+            const int64_t i = i0 + k * (int64_t)blockDim.x;
+            v[k] = -1;
+            e0[k] = e1[k] = 0;
+            if (i < w.end) {
+                v[k] = __ldg(&M.vb_vert[i]);
+                e0[k] = __ldg(&M.vb_ptr[i]);
+                e1[k] = __ldg(&M.vb_ptr[i + 1]);
             }
         }
-        const T zi = z[v] + val;
-        z[v] = zi;
-        if (kDots == 1) {
-            zr = fma((double)zi, V.r[w.voff + v], zr);
-            zq = fma((double)zi, V.q[w.voff + v], zq);
-        } else if (kDots == 2) {
-            const float2 z2 = make_float2((float)zi, 0.0f);
-            pr_dot_acc(rh, rl, z2, reinterpret_cast<const float2*>(V.r)[w.voff + v]);
-            pr_dot_acc(qh, ql, z2, V.q2[w.voff + v]);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (v[k] < 0) continue;
+            T x, y, zz, ic;
+            vx.load(v[k], x, y, zz, ic);
+            T val = T(0);
+            if (M.nr > 0) {
+                for (int e = e0[k]; e < e1[k]; ++e) {
+                    T wt[8];
+                    const int c = cell_weights(g, __ldg(&M.vb_cell[e]), x, y, zz, wt);
+                    T sum = T(0);
+#pragma unroll
+                    for (int m = 0; m < 8; ++m) {
+                        const int col = __ldg(&M.cell_cols[(size_t)c * 8 + m]);
+                        sum += wt[m] * (col >= 0 ? (T)__ldg(&ur[col]) : T(0));
+                    }
+                    val += __ldg(&bw[e]) * sum;
+                }
+            }
+            const T zi = z[v[k]] + val;
+            z[v[k]] = zi;
+            if (kDots == 1) {
+                zr = fma((double)zi, V.r[w.voff + v[k]], zr);
+                zq = fma((double)zi, V.q[w.voff + v[k]], zq);
+            } else if (kDots == 2) {
+                const float2 z2 = make_float2((float)zi, 0.0f);
+                pr_dot_acc(rh, rl, z2, reinterpret_cast<const float2*>(V.r)[w.voff + v[k]]);
+                pr_dot_acc(qh, ql, z2, V.q2[w.voff + v[k]]);
+            }
         }
     }
     if (kDots == 0 || !S) return;
@@ -1174,14 +1251,19 @@ __global__ void __launch_bounds__(kBlock) interp_add_kernel(const DevMesh* __res
         }
     }
 }
+template <typename T, typename Tu, int kDots>
+__global__ void __launch_bounds__(kBlock) interp_add_kernel(const DevMesh* __restrict__ meshes,
+                                                            const Work* __restrict__ work, Vecs V,
+                                                            const Tu* __restrict__ urv, T* __restrict__ zv) {
+    interp_add_item<T, Tu, kDots>(meshes, work[blockIdx.x], V, urv, zv);
+}
 
 // u_r = A_r^{-1} r_r: one warp per row of the full symmetric inverse; also a
 // float copy of u_r for the float interpolation (no conversions per element).
-__global__ void __launch_bounds__(kBlock) coarse_gemv_kernel(const DevMesh* __restrict__ meshes,
-                                                             const Work* __restrict__ work, Vecs V,
-                                                             const double* __restrict__ rrv,
-                                                             double* __restrict__ urv, float* __restrict__ ur32v) {
-    CGS_WORK_PROLOGUE();
+__device__ __forceinline__ void coarse_gemv_item(const DevMesh* __restrict__ meshes, const Work& w, Vecs V,
+                                                 const double* __restrict__ rrv, double* __restrict__ urv,
+                                                 float* __restrict__ ur32v) {
+    CGS_ITEM_PROLOGUE();
     const int64_t nr = M.nr;
     const double* rr = rrv + w.roff;
     const int lane = threadIdx.x & 31;
@@ -1196,17 +1278,22 @@ __global__ void __launch_bounds__(kBlock) coarse_gemv_kernel(const DevMesh* __re
         if (ur32v) ur32v[w.roff + i] = (float)s;
     }
 }
+__global__ void __launch_bounds__(kBlock) coarse_gemv_kernel(const DevMesh* __restrict__ meshes,
+                                                             const Work* __restrict__ work, Vecs V,
+                                                             const double* __restrict__ rrv,
+                                                             double* __restrict__ urv, float* __restrict__ ur32v) {
+    coarse_gemv_item(meshes, work[blockIdx.x], V, rrv, urv, ur32v);
+}
 
 // u_r = A_r^{-1} r_r in float-pair arithmetic (mixed forms): the inverse and
 // r_r are hi/lo float pairs, every lane keeps a pair accumulator, the warp
 // sums pairs by shuffles.  Same ~48-bit accuracy as the float64 product on
 // the FP32 pipes, so the product runs at the bandwidth of the 8-byte entries.
 // Writes u_r as float64 (ur, optional) and rounded to float (ur32, optional).
-__global__ void __launch_bounds__(kBlock) coarse_pair_kernel(const DevMesh* __restrict__ meshes,
-                                                             const Work* __restrict__ work, Vecs V,
-                                                             const float2* __restrict__ rr2v,
-                                                             double* __restrict__ urv, float* __restrict__ ur32v) {
-    CGS_WORK_PROLOGUE();
+__device__ __forceinline__ void coarse_pair_item(const DevMesh* __restrict__ meshes, const Work& w, Vecs V,
+                                                 const float2* __restrict__ rr2v, double* __restrict__ urv,
+                                                 float* __restrict__ ur32v) {
+    CGS_ITEM_PROLOGUE();
     const int64_t nr = M.nr;
     const float2* rr = rr2v + w.roff;
     const int lane = threadIdx.x & 31;
@@ -1247,6 +1334,12 @@ __global__ void __launch_bounds__(kBlock) coarse_pair_kernel(const DevMesh* __re
         if (urv) urv[w.roff + i] = (double)h + (double)l;
         if (ur32v) ur32v[w.roff + i] = __fadd_rn(h, l);
     }
+}
+__global__ void __launch_bounds__(kBlock) coarse_pair_kernel(const DevMesh* __restrict__ meshes,
+                                                             const Work* __restrict__ work, Vecs V,
+                                                             const float2* __restrict__ rr2v,
+                                                             double* __restrict__ urv, float* __restrict__ ur32v) {
+    coarse_pair_item(meshes, work[blockIdx.x], V, rr2v, urv, ur32v);
 }
 
 // ---------------------------------------------------------------------------
@@ -1350,10 +1443,9 @@ __global__ void __launch_bounds__(kBlock) pcg_first_dir_kernel(const DevMesh* __
 // (zero z, s = r in the bulk precision, zero r_r).  The slot's last block
 // counts the iteration and applies the stopping test.
 template <typename Tz, typename Tq>
-__global__ void __launch_bounds__(kBlock) pcg_update_xr_kernel(const DevMesh* __restrict__ meshes,
-                                                               const Work* __restrict__ work, Vecs V,
-                                                               const Tq* __restrict__ qv) {
-    CGS_WORK_PROLOGUE();
+__device__ __forceinline__ void pcg_update_xr_item(const DevMesh* __restrict__ meshes, const Work& w, Vecs V,
+                                                   const Tq* __restrict__ qv) {
+    CGS_ITEM_PROLOGUE();
     double* x = V.x + w.voff;
     double* r = V.r + w.voff;
     const double* p = V.p + w.voff;
@@ -1390,14 +1482,19 @@ __global__ void __launch_bounds__(kBlock) pcg_update_xr_kernel(const DevMesh* __
         }
     }
 }
+template <typename Tz, typename Tq>
+__global__ void __launch_bounds__(kBlock) pcg_update_xr_kernel(const DevMesh* __restrict__ meshes,
+                                                               const Work* __restrict__ work, Vecs V,
+                                                               const Tq* __restrict__ qv) {
+    pcg_update_xr_item<Tz, Tq>(meshes, work[blockIdx.x], V, qv);
+}
 
 // z.r and z.q; beta = -alpha (z.q) / rho (Polak-Ribiere, since
 // r_new - r_old = -alpha q), rho = z.r.
 template <typename Tz, typename Tq>
-__global__ void __launch_bounds__(kBlock) pcg_dots_kernel(const DevMesh* __restrict__ meshes,
-                                                          const Work* __restrict__ work, Vecs V,
-                                                          const Tq* __restrict__ qv) {
-    CGS_WORK_PROLOGUE();
+__device__ __forceinline__ void pcg_dots_item(const DevMesh* __restrict__ meshes, const Work& w, Vecs V,
+                                              const Tq* __restrict__ qv) {
+    CGS_ITEM_PROLOGUE();
     const Tz* z = static_cast<const Tz*>(V.z) + w.voff;
     const double* r = V.r + w.voff;
     const Tq* q = qv + w.voff;
@@ -1420,12 +1517,17 @@ __global__ void __launch_bounds__(kBlock) pcg_dots_kernel(const DevMesh* __restr
         }
     }
 }
+template <typename Tz, typename Tq>
+__global__ void __launch_bounds__(kBlock) pcg_dots_kernel(const DevMesh* __restrict__ meshes,
+                                                          const Work* __restrict__ work, Vecs V,
+                                                          const Tq* __restrict__ qv) {
+    pcg_dots_item<Tz, Tq>(meshes, work[blockIdx.x], V, qv);
+}
 
 // p = z + beta p (and p2), q = 0 for the next product.
 template <typename Tz, typename Tq>
-__global__ void __launch_bounds__(kBlock) pcg_update_p_kernel(const DevMesh* __restrict__ meshes,
-                                                              const Work* __restrict__ work, Vecs V, Tq* qv) {
-    CGS_WORK_PROLOGUE();
+__device__ __forceinline__ void pcg_update_p_item(const DevMesh* __restrict__ meshes, const Work& w, Vecs V, Tq* qv) {
+    CGS_ITEM_PROLOGUE();
     const Tz* z = static_cast<const Tz*>(V.z) + w.voff;
     double* p = V.p + w.voff;
     float2* p2 = V.p2 ? V.p2 + w.voff : nullptr;
@@ -1437,6 +1539,11 @@ __global__ void __launch_bounds__(kBlock) pcg_update_p_kernel(const DevMesh* __r
         if (p2) p2[i] = split_pair(pi);
         qzero(q, i);
     }
+}
+template <typename Tz, typename Tq>
+__global__ void __launch_bounds__(kBlock) pcg_update_p_kernel(const DevMesh* __restrict__ meshes,
+                                                              const Work* __restrict__ work, Vecs V, Tq* qv) {
+    pcg_update_p_item<Tz, Tq>(meshes, work[blockIdx.x], V, qv);
 }
 
 // ---------------------------------------------------------------------------
@@ -1525,9 +1632,8 @@ __global__ void __launch_bounds__(kBlock) pcg_first_dir_pair_kernel(const DevMes
 
 // x += alpha p, r -= alpha q, ||r||^2; z = 0, s = hi(r), r_r = 0.  The
 // slot's last block counts the iteration and applies the stopping test.
-__global__ void __launch_bounds__(kBlock) pcg_update_xr_pair_kernel(const DevMesh* __restrict__ meshes,
-                                                                    const Work* __restrict__ work, Vecs V) {
-    CGS_WORK_PROLOGUE();
+__device__ __forceinline__ void pcg_update_xr_pair_item(const DevMesh* __restrict__ meshes, const Work& w, Vecs V) {
+    CGS_ITEM_PROLOGUE();
     float2* __restrict__ x = as_pair(V.x) + w.voff;
     float2* __restrict__ r = as_pair(V.r) + w.voff;
     const float2* __restrict__ p = V.p2 + w.voff;
@@ -1583,11 +1689,14 @@ __global__ void __launch_bounds__(kBlock) pcg_update_xr_pair_kernel(const DevMes
         }
     }
 }
+__global__ void __launch_bounds__(kBlock) pcg_update_xr_pair_kernel(const DevMesh* __restrict__ meshes,
+                                                                    const Work* __restrict__ work, Vecs V) {
+    pcg_update_xr_pair_item(meshes, work[blockIdx.x], V);
+}
 
 // z.r and z.q; beta = -alpha (z.q) / rho, rho = z.r.
-__global__ void __launch_bounds__(kBlock) pcg_dots_pair_kernel(const DevMesh* __restrict__ meshes,
-                                                               const Work* __restrict__ work, Vecs V) {
-    CGS_WORK_PROLOGUE();
+__device__ __forceinline__ void pcg_dots_pair_item(const DevMesh* __restrict__ meshes, const Work& w, Vecs V) {
+    CGS_ITEM_PROLOGUE();
     const float* __restrict__ z = static_cast<const float*>(V.z) + w.voff;
     const float2* __restrict__ r = as_pair(V.r) + w.voff;
     const float2* __restrict__ q = V.q2 + w.voff;
@@ -1628,11 +1737,14 @@ __global__ void __launch_bounds__(kBlock) pcg_dots_pair_kernel(const DevMesh* __
         }
     }
 }
+__global__ void __launch_bounds__(kBlock) pcg_dots_pair_kernel(const DevMesh* __restrict__ meshes,
+                                                               const Work* __restrict__ work, Vecs V) {
+    pcg_dots_pair_item(meshes, work[blockIdx.x], V);
+}
 
 // p = z + beta p, q = 0 for the next product.
-__global__ void __launch_bounds__(kBlock) pcg_update_p_pair_kernel(const DevMesh* __restrict__ meshes,
-                                                                   const Work* __restrict__ work, Vecs V) {
-    CGS_WORK_PROLOGUE();
+__device__ __forceinline__ void pcg_update_p_pair_item(const DevMesh* __restrict__ meshes, const Work& w, Vecs V) {
+    CGS_ITEM_PROLOGUE();
     const float* __restrict__ z = static_cast<const float*>(V.z) + w.voff;
     float2* __restrict__ p = V.p2 + w.voff;
     float2* __restrict__ q = V.q2 + w.voff;
@@ -1657,6 +1769,10 @@ __global__ void __launch_bounds__(kBlock) pcg_update_p_pair_kernel(const DevMesh
             }
         }
     }
+}
+__global__ void __launch_bounds__(kBlock) pcg_update_p_pair_kernel(const DevMesh* __restrict__ meshes,
+                                                                   const Work* __restrict__ work, Vecs V) {
+    pcg_update_p_pair_item(meshes, work[blockIdx.x], V);
 }
 
 // x (float pair) -> float64 in place, before the final residual.
@@ -1683,6 +1799,111 @@ __global__ void __launch_bounds__(kBlock) loop_cond_kernel(SolveScalars* __restr
         cudaGraphSetConditional(cond, (running && loops < S[0].maxit + 2) ? 1u : 0u);
     }
 }
+
+// ---------------------------------------------------------------------------
+// Persistent PCG loop of the mixed forms: one cooperative launch runs whole
+// iterations, every block walking each phase's work items (the same
+// per-item functions as the one-kernel-per-phase path) with a grid barrier
+// between phases.  For problems too small to fill the GPU per kernel, this
+// trades ~8 kernel launches and their ramp-up and drain per iteration for 8
+// barriers.  The barrier waits are bounded: a block that gives up records
+// the failure and every block leaves at its next barrier.
+// ---------------------------------------------------------------------------
+__device__ bool grid_sync(GridBar* b, int limit) {
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned int g = *(volatile unsigned int*)&b->gen;
+        __threadfence();
+        if (atomicAdd(&b->count, 1u) == gridDim.x - 1) {
+            b->count = 0u;
+            __threadfence();
+            atomicAdd(&b->gen, 1u);
+            ok = 1;
+        } else {
+            int i = 0;
+            while (*(volatile unsigned int*)&b->gen == g && i < limit) {
+                __nanosleep(64);
+                ++i;
+            }
+            ok = i < limit;
+            if (!ok) atomicExch(&b->error, 1);
+        }
+        __threadfence();
+        if (*(volatile int*)&b->error) ok = 0;
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+// Work tables of the persistent loop, by value.
+struct LoopTables {
+    const Work* w[kWorkKinds];
+    unsigned int n[kWorkKinds];
+};
+#define CGS_FOR_ITEMS(kind, k) for (unsigned int k = blockIdx.x; k < T.n[kind]; k += gridDim.x)
+
+// A barrier wait gave up: stop every slot with CGS_ERR_TIMEOUT (idempotent,
+// any block may do it) and leave.
+__device__ void abort_slots(SolveScalars* S, int nslots) {
+    for (int i = threadIdx.x; i < nslots; i += blockDim.x) {
+        S[i].status = CGS_ERR_TIMEOUT;
+        S[i].done = 1;
+    }
+}
+#define CGS_SYNC_OR_LEAVE()                \
+    if (!grid_sync(bar, bar_limit)) {      \
+        abort_slots(V.S, nslots);          \
+        return;                            \
+    }
+
+template <typename Stor>
+__global__ void __launch_bounds__(kBlock, 2) pcg_persistent_kernel(const DevMesh* __restrict__ meshes, LoopTables T,
+                                                                   Vecs V, GridBar* bar, int nslots, int hybrid,
+                                                                   int any_nr, int big_subs, int max_iters,
+                                                                   int wait_limit, int bar_limit) {
+    float* s = static_cast<float*>(V.s);
+    float* z = static_cast<float*>(V.z);
+    for (int it = 0; it < max_iters; ++it) {
+        // q = A p, p.q and alpha
+        CGS_FOR_ITEMS(kWorkTile, k) apply_pair_tiled_item<false>(meshes, T.w[kWorkTile][k], V, wait_limit);
+        CGS_SYNC_OR_LEAVE();
+        // x, r, ||r||, stopping test; z = 0, s = hi(r), r_r = 0
+        CGS_FOR_ITEMS(kWorkVert, k) pcg_update_xr_pair_item(meshes, T.w[kWorkVert][k], V);
+        CGS_SYNC_OR_LEAVE();
+        int running = 0;
+        for (int i = threadIdx.x; i < nslots; i += blockDim.x) running |= !*(volatile const int*)&V.S[i].done;
+        if (!__syncthreads_or(running)) return;
+        // z = M r
+        CGS_FOR_ITEMS(kWorkPack, k) local_lane_item<Stor>(meshes, T.w[kWorkPack][k], V, s, z, hybrid);
+        CGS_FOR_ITEMS(kWorkSub, k) local_warp_item<float, Stor>(meshes, T.w[kWorkSub][k], V, s, z, hybrid);
+        if (big_subs)
+            CGS_FOR_ITEMS(kWorkSub, k) local_block_item<float, Stor>(meshes, T.w[kWorkSub][k], V, s, z, hybrid);
+        CGS_SYNC_OR_LEAVE();
+        if (hybrid) {
+            CGS_FOR_ITEMS(kWorkTile, k)
+                apply28f_tiled_item<false>(meshes, T.w[kWorkTile][k], V, z, s, -1.0f, wait_limit);
+            CGS_SYNC_OR_LEAVE();
+        }
+        if (any_nr) {
+            CGS_FOR_ITEMS(kWorkBoxEnt, k) restrict_item<float, float, true>(meshes, T.w[kWorkBoxEnt][k], V, s, V.rr);
+            CGS_SYNC_OR_LEAVE();
+            CGS_FOR_ITEMS(kWorkRow, k)
+                coarse_pair_item(meshes, T.w[kWorkRow][k], V, reinterpret_cast<const float2*>(V.rr), nullptr, V.ur32);
+            CGS_SYNC_OR_LEAVE();
+            // z += J u_r with the dots z.r, z.q and beta
+            CGS_FOR_ITEMS(kWorkBox, k) interp_add_item<float, float, 2>(meshes, T.w[kWorkBox][k], V, V.ur32, z);
+        } else {
+            CGS_FOR_ITEMS(kWorkVert, k) pcg_dots_pair_item(meshes, T.w[kWorkVert][k], V);
+        }
+        CGS_SYNC_OR_LEAVE();
+        // p = z + beta p, q = 0
+        CGS_FOR_ITEMS(kWorkVert, k) pcg_update_p_pair_item(meshes, T.w[kWorkVert][k], V);
+        CGS_SYNC_OR_LEAVE();
+    }
+}
+#undef CGS_FOR_ITEMS
+#undef CGS_SYNC_OR_LEAVE
 
 // x_out = x (copy-out), then ||b - y||^2 and ||b||^2 over free entries.
 __global__ void __launch_bounds__(kBlock) resid_norm_kernel(const DevMesh* __restrict__ meshes,
@@ -1925,6 +2146,38 @@ void launch_loop_cond(const Plan& P, const Vecs& V, cudaGraphConditionalHandle c
     loop_cond_kernel<<<1, kBlock, 0, st>>>(V.S, P.nslots, cond);
 }
 
+// Blocks of the persistent loop that fit on the device at once (the
+// cooperative launch requires all of them resident).
+int persistent_blocks(cgs_precision prec) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int smem = (int)(2 * kTileVerts * sizeof(float2));
+    if (prec == CGS_FP16_LOCAL)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pcg_persistent_kernel<__half>, kBlock, smem);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pcg_persistent_kernel<float>, kBlock, smem);
+    return per_sm * sms;
+}
+
+cudaError_t launch_pcg_persistent(const Plan& P, const Vecs& V, cgs_precision prec, bool hybrid, GridBar* bar,
+                                  int max_iters, int blocks, cudaStream_t st) {
+    LoopTables T;
+    for (int k = 0; k < kWorkKinds; ++k) {
+        T.w[k] = P.work[k];
+        T.n[k] = P.nwork[k];
+    }
+    int nslots = P.nslots, hyb = hybrid ? 1 : 0, any_nr = P.any_nr ? 1 : 0, big = P.max_m > 64 ? 1 : 0;
+    int wait_limit = P.wait_limit, bar_limit = 1 << 22;
+    Vecs Vv = V;
+    const DevMesh* meshes = P.meshes;
+    void* args[] = {(void*)&meshes, &T, &Vv, &bar, &nslots, &hyb, &any_nr, &big, &max_iters, &wait_limit, &bar_limit};
+    const int smem = (int)(2 * kTileVerts * sizeof(float2));
+    const void* fn = prec == CGS_FP16_LOCAL ? (const void*)pcg_persistent_kernel<__half>
+                                            : (const void*)pcg_persistent_kernel<float>;
+    return cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(kBlock), args, smem, st);
+}
+
 void launch_resid_norm(const Plan& P, const Vecs& V, cudaStream_t st) {
     resid_norm_kernel<<<P.nwork[kWorkVert], kBlock, 0, st>>>(P.meshes, P.work[kWorkVert], V);
 }
@@ -1938,6 +2191,7 @@ Schedule default_schedule(int64_t total_nv, int64_t total_sub, int64_t total_pac
     s.sub_chunk = (int)std::min<int64_t>(64, std::max<int64_t>(8, (c + 7) / 8 * 8));
     int64_t k = (total_pack + target - 1) / target;
     s.pack_chunk = (int)std::min<int64_t>(32, std::max<int64_t>(8, (k + 7) / 8 * 8));
+    s.box_chunk = (int)std::min<int64_t>(1024, std::max<int64_t>(256, (v + 255) / 256 * 256));
     return s;
 }
 
@@ -1967,15 +2221,15 @@ void append_mesh_work(std::vector<Work> (&tabs)[kWorkKinds], int mesh, int slot,
     add(kWorkSub, z.n_sub, sch.sub_chunk);
     add(kWorkRow, z.nr, kRowChunk);
     add(kWorkPack, z.n_pack, sch.pack_chunk);
-    add(kWorkBox, z.nvb, kElemChunk);
-    if (z.nr > 0) add(kWorkBoxEnt, z.nre, kElemChunk);
+    add(kWorkBox, z.nvb, sch.box_chunk);
+    if (z.nr > 0) add(kWorkBoxEnt, z.nrng, kBlock / 32);
 }
 
 int64_t mesh_partial_slots(const MeshSizes& z, const Schedule& sch) {
     int64_t c = (z.ne + kElemChunk - 1) / kElemChunk;
     c = std::max(c, z.ntiles);
     c = std::max(c, (z.nv + sch.vert_chunk - 1) / sch.vert_chunk);
-    c = std::max(c, (z.nvb + kElemChunk - 1) / kElemChunk);
+    c = std::max(c, (z.nvb + sch.box_chunk - 1) / sch.box_chunk);
     return 2 * std::max<int64_t>(c, 1);
 }
 

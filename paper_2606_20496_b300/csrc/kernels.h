@@ -4,6 +4,7 @@
 #pragma once
 
 #include <string>
+#include <vector>
 
 #include "internal.h"
 
@@ -48,6 +49,12 @@ void launch_pcg_dots(const Plan& P, const Vecs& V, const Tq* q, cudaStream_t st)
 template <typename Tz, typename Tq>
 void launch_pcg_update_p(const Plan& P, const Vecs& V, Tq* q, cudaStream_t st);
 void launch_loop_cond(const Plan& P, const Vecs& V, cudaGraphConditionalHandle cond, cudaStream_t st);
+// Persistent PCG loop of the mixed forms: up to max_iters iterations over
+// every slot of the plan in one cooperative launch of `blocks` blocks (at
+// most persistent_blocks(prec)); bar must be zero on entry.
+int persistent_blocks(cgs_precision prec);
+cudaError_t launch_pcg_persistent(const Plan& P, const Vecs& V, cgs_precision prec, bool hybrid, GridBar* bar,
+                                  int max_iters, int blocks, cudaStream_t st);
 void launch_resid_norm(const Plan& P, const Vecs& V, cudaStream_t st);
 
 void launch_convert_f2d(const Plan& P, const float* a, double* b, bool mask, cudaStream_t st);
@@ -58,7 +65,7 @@ void launch_fill_f(int64_t n, float* a, float v, cudaStream_t st);
 
 // Work tables of one mesh as slot `slot` (host side, appended to tabs).
 struct MeshSizes {
-    int64_t nv, ne, ntiles, n_sub, nr, n_pack, nvb, nre;   // n_sub: warp-kernel subdomains
+    int64_t nv, ne, ntiles, n_sub, nr, n_pack, nvb, nrng;   // n_sub: warp-kernel subdomains
 };
 // Block sizes of the range-parallel kernels: vertices per block (vector
 // kernels) and subdomains per block (local solves), and how the tiled
@@ -68,7 +75,10 @@ struct Schedule {
     int vert_chunk = 1024;
     int sub_chunk = 64;
     int pack_chunk = 8;  // lane packs per block (a multiple of the 8 warps)
+    int box_chunk = 1024;// box-list vertices per block of the interpolation (multiple of 256)
     int tile_tma = 0;    // 1: element tiles of the mixed-form applies staged by TMA
+    int persistent = -1; // mixed-form iterations in one persistent cooperative launch:
+                         // 1 yes; 0 or -1 (default) no
 };
 // Default schedule: enough blocks to fill the GPU (about four per SM) for
 // `total` work of each kind, chunks within the kernels' ranges.

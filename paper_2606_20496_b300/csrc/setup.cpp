@@ -572,6 +572,17 @@ cgs_status host_setup(const double* xyz, int64_t nv, const int32_t* conn, int64_
             S.re_cell[i] = S.vb_cell[ord[i]];
             S.re_w[i] = S.vb_w[ord[i]];
         }
+        // restriction work: each cell's entries, in ranges of at most kBoxRange
+        S.re_rng.clear();
+        for (size_t a = 0; a < nnz;) {
+            size_t b = a;
+            while (b < nnz && S.re_cell[b] == S.re_cell[a]) ++b;
+            for (size_t c = a; c < b; c += kBoxRange) {
+                S.re_rng.push_back((int32_t)c);
+                S.re_rng.push_back((int32_t)std::min(b, c + kBoxRange));
+            }
+            a = b;
+        }
     }
 
     // ---- element order on the device: by cell, then subdomain, then id -----

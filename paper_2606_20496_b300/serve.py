@@ -87,14 +87,12 @@ def run_server(ctx, hs, pool, t_arr, which, slots, iters_per_step, rtol, prec, a
             active_sum += active
             peak_use = max(peak_use, cgs.cgs_server_stats(server)["bytes_in_use"])
             tnow = time.perf_counter() - t0
-            for tk in list(pending):
-                r = cgs.cgs_poll(server, tk)
-                if r is not None:
-                    i, _, _ = pending.pop(tk)
-                    lat[i] = tnow - t_arr[i]
-                    its[i] = r[0]
-                    assert r[2] == cgs.OK and r[1] <= rtol * 1.5, r
-                    done += 1
+            for tk, it, rel, st in cgs.cgs_server_drain(server):
+                i, _, _ = pending.pop(tk)
+                lat[i] = tnow - t_arr[i]
+                its[i] = it
+                assert st == cgs.OK and rel <= rtol * 1.5, (st, rel)
+                done += 1
         elif nxt < n:
             time.sleep(max(0.0, min(1e-3, t_arr[nxt] - (time.perf_counter() - t0))))
     wall = time.perf_counter() - t0

@@ -138,3 +138,31 @@ def test_admission_by_footprint(ctx):
         cgs.cgs_server_free(server)
         h.free()
         hsm.free()
+
+
+def test_drain_returns_each_finished_request_once(ctx):
+    m = meshes.cube(9, perturb=0.1, seed=8)
+    h = cgs.Mesh(ctx, m.xyz, m.conn, part=m.part, boxes=m.boxes, prec="fp32")
+    server = cgs.cgs_server_create(ctx, max_slots=2, pool_nv=4 * m.nv, pool_nr=4 * h.info["n_r"], prec="fp32",
+                                   rtol=1e-9)
+    try:
+        rng = np.random.default_rng(9)
+        bs = [dev(rng.standard_normal(m.nv)) for _ in range(5)]
+        xs = [torch.zeros_like(b) for b in bs]
+        tickets = [cgs.cgs_submit(server, h, b, x) for b, x in zip(bs, xs)]
+        got = {}
+        for _ in range(300):
+            cgs.cgs_server_step(server, iterations=2)
+            for t, its, rel, st in cgs.cgs_server_drain(server):
+                assert t not in got
+                got[t] = (its, rel, st)
+            if len(got) == len(tickets):
+                break
+        assert sorted(got) == sorted(tickets)
+        assert all(st == cgs.OK and rel <= 1e-9 * 1.01 and its > 0 for its, rel, st in got.values())
+        assert cgs.cgs_server_drain(server) == []
+        with pytest.raises(cgs.CGSError):
+            cgs.cgs_poll(server, tickets[0])   # released by the drain
+    finally:
+        cgs.cgs_server_free(server)
+        h.free()
