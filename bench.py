@@ -243,6 +243,32 @@ def run_reference(args):
 # our arm
 # ---------------------------------------------------------------------------
 
+def serve_probe(ctx, args):
+    """Continuous-batching server on a Poisson stream (this rank's replica):
+    pool meshes drawn like the serving workload (cubes and cylinders with
+    k^3 elements, k log-uniform in [8, 64], seed 3), FP32 bulk to 1e-8,
+    latency from arrival to completion on the wall clock."""
+    from paper_2606_20496_b300 import cgs, serve
+    import torch
+    pool = serve.make_pool(args.serve_pool)
+    hs = [cgs.Mesh(ctx, mm.xyz, mm.conn, part=mm.part, boxes=mm.boxes, prec="fp32") for mm in pool]
+    try:
+        # warm-up: every pool mesh once
+        serve.run_server(ctx, hs, pool, np.zeros(len(pool)), np.arange(len(pool)), min(256, len(pool)), 8,
+                         RTOL, "fp32", 2048.0)
+        torch.cuda.synchronize()
+        t_arr, which = serve.arrivals(args.serve_rate, args.serve_seconds, len(pool))
+        r = serve.run_server(ctx, hs, pool, t_arr, which, 256, 8, RTOL, "fp32", 2048.0)
+    finally:
+        for h in hs:
+            h.free()
+    return {"p50": r["p50_ms"], "p99": r["p99_ms"], "solves_per_s": r["solves_per_s"],
+            "offered_req_per_s": args.serve_rate, "requests": int(t_arr.size), "seconds": args.serve_seconds,
+            "workload": f"Poisson stream over {len(pool)} cube/cylinder meshes, k^3 elements, k log-uniform in "
+                        "[8, 64] (seed 3), one N(0,1) RHS per request, rtol 1e-8, FP32 bulk",
+            "server": {"slots": 256, "iters_per_step": 8, "arena_mb": 2048, "mean_active": r["mean_active_after_step"]}}
+
+
 def run_ours(args):
     import torch
 
@@ -265,7 +291,8 @@ def run_ours(args):
     # the library's autotuner picks the block sizes on this mesh (untimed setup)
     cgs.cgs_mesh_tune(h32.handle)
     cgs.cgs_mesh_tune(h64.handle)
-    sched = {k: cgs.cgs_mesh_info(h32.handle)[k] for k in ("vert_chunk", "sub_chunk", "tile_tma", "persistent")}
+    sched = cgs.cgs_mesh_get_schedule(h32.handle)
+    sched64 = cgs.cgs_mesh_get_schedule(h64.handle)
     bd = torch.as_tensor(b, dtype=torch.float64, device="cuda")
     x = torch.empty_like(bd)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
@@ -341,10 +368,10 @@ def run_ours(args):
     shares = {k: {"share": round(t / total_ms, 4), "launches": n, "avg_us": round(1e3 * t / n, 2)}
               for k, (t, n) in prof.items() if n}
     # the same solves one launch per phase (per-phase attribution)
-    i0 = cgs.cgs_mesh_info(h32.handle)
-    cgs.cgs_mesh_set_schedule(h32.handle, i0["vert_chunk"], i0["sub_chunk"], i0["tile_tma"], 0)
+    p0 = cgs.cgs_mesh_get_schedule(h32.handle)["persistent"]
+    cgs.cgs_mesh_set_schedule(h32.handle, persistent=0)
     prof_s = profile(h32, nprof)
-    cgs.cgs_mesh_set_schedule(h32.handle, i0["vert_chunk"], i0["sub_chunk"], i0["tile_tma"], -1)
+    cgs.cgs_mesh_set_schedule(h32.handle, persistent=p0)
     total_s = sum(t for t, n in prof_s.values())
     shares_stepwise = {k: {"share": round(t / total_s, 4), "launches": n, "avg_us": round(1e3 * t / n, 2),
                            "achieved_gbs": round(algo[k] / (t / n * 1e-3) / 1e9, 1) if k in algo else None}
@@ -370,6 +397,8 @@ def run_ours(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_ms = float(t.item())
 
+    serving = serve_probe(ctx, args) if args.serve_seconds > 0 else None
+
     line = None
     if rank == 0:
         ms_per_step = ms32 / args.steps
@@ -383,8 +412,8 @@ def run_ours(args):
                 "iters": {"fp32_bulk": int(np.median(its32)), "fp64_plain": int(np.median(its64)),
                           "delta": int(np.median(its32)) - int(np.median(its64))},
                 "fp64_plain": {"value": world * args.steps / (ms64 * 1e-3), "unit": UNIT,
-                               "ms_per_step": ms64 / args.steps},
-                "serve_latency_ms": {"p50": None, "p99": None, "note": "serving loop not measured by this line"},
+                               "ms_per_step": ms64 / args.steps, "schedule": sched64},
+                "serve_latency_ms": serving,
                 "roofline": roofline, "kernel_shares": shares, "kernel_shares_stepwise": shares_stepwise,
                 "cpu_baseline": cpu,
                 "e2e": {"value": world * args.steps / (e2e_ms * 1e-3), "unit": UNIT,
@@ -407,6 +436,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--serve-seconds", type=float, default=3.0, help="serving probe length (0: skip)")
+    ap.add_argument("--serve-rate", type=float, default=2000.0)
+    ap.add_argument("--serve-pool", type=int, default=32)
     ap.add_argument("--oracle-sample", nargs=2, type=float, default=None, help=argparse.SUPPRESS)
     args = ap.parse_args()
     if args.oracle_sample:

@@ -86,13 +86,28 @@ typedef struct {
     size_t footprint_bytes;/* device memory held by the mesh                          */
     double setup_seconds;  /* host wall time of cgs_mesh_setup                        */
     int64_t kernel_launches; /* CUDA kernels this mesh has launched so far           */
-    int32_t vert_chunk;    /* schedule: vertices per block of the vector kernels     */
-    int32_t sub_chunk;     /* schedule: subdomains per block of the local solves      */
-    int32_t tile_tma;      /* schedule: 1 = element tiles staged by TMA, 0 = streamed  */
     int64_t n_box_entries; /* (vertex, cell) entries of the per-vertex box lists     */
     int64_t n_lane_packs;  /* lane packs of the mixed-form local solves (32 each)    */
-    int32_t persistent;    /* 1 = solves run the persistent loop (mixed forms)       */
+    int32_t loop;          /* how solves iterate: 0 host-driven loop, 1 device-side
+                              graph loop, 2 persistent cooperative kernel          */
 } cgs_mesh_info_t;
+
+/* Launch schedule of a mesh's kernels (cgs_mesh_get_schedule / _set_schedule):
+ *   vert_chunk  vertices per block of the vector kernels, multiple of 256 in [256, 8192]
+ *   sub_chunk   subdomains per block of the warp-kernel local solves, multiple of 8 in [8, 512]
+ *   pack_chunk  lane packs per block of the lane local solves, multiple of 8 in [8, 256]
+ *   box_chunk   box-list vertices per interpolation block, multiple of 256 in [256, 4096]
+ *   tile_tma    1: element tiles of the mixed-form applies staged by TMA; 0: streamed
+ *   persistent  1: mixed-form iterations in one persistent cooperative launch with grid
+ *               barriers between the phases; 0 or -1: one launch per phase in the
+ *               device-side graph loop (default)
+ *   pdl         1: kernels launched with programmatic stream serialization (each may
+ *               start while its predecessor drains); 0: ordinary launches
+ *   row_packs   1: meshes small enough to have row packs solve each small subdomain
+ *               with 4 lanes (full rows; more parallelism); 0: one lane each   */
+typedef struct {
+    int32_t vert_chunk, sub_chunk, pack_chunk, box_chunk, tile_tma, persistent, pdl, row_packs;
+} cgs_schedule;
 
 /* Kernel classes reported by the profiler. */
 typedef enum {
@@ -244,13 +259,10 @@ int64_t cgs_batch_launches(const cgs_batch* batch);
  * Synchronous; call between solves.  Setup picks a default schedule that
  * gives about four blocks per SM.                                          */
 cgs_status cgs_mesh_tune(cgs_mesh* mesh, void* stream);
-/* Set the schedule explicitly: vert_chunk a multiple of 256 in [256, 8192],
- * sub_chunk a multiple of 8 in [8, 512], tile_tma 0 or 1, persistent 1 (run
- * the mixed-form iterations in one persistent cooperative launch with grid
- * barriers between the phases) or 0 / -1 (one launch per phase inside the
- * device-side graph loop, the default); INVALID_ARG otherwise.
- * Synchronous; call between solves.                                        */
-cgs_status cgs_mesh_set_schedule(cgs_mesh* mesh, int vert_chunk, int sub_chunk, int tile_tma, int persistent);
+/* The schedule in use, and an explicit one (INVALID_ARG if a field is out of
+ * range; synchronous, call between solves).                                */
+cgs_status cgs_mesh_get_schedule(const cgs_mesh* mesh, cgs_schedule* out);
+cgs_status cgs_mesh_set_schedule(cgs_mesh* mesh, const cgs_schedule* schedule);
 cgs_status cgs_batch_tune(cgs_batch* batch, void* stream);
 cgs_status cgs_solve_batched(cgs_mesh* const* meshes, int nmesh, const double* const* b, double* const* x,
                              int nrhs, double rtol, int maxit, int* iters, double* relres, void* stream);

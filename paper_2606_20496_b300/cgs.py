@@ -28,7 +28,8 @@ EXPORTS = (
     "cgs_coarse_solve", "cgs_interp", "cgs_apply_preconditioner", "cgs_apply_preconditioner_noalloc",
     "cgs_solve", "cgs_solve_host",
     "cgs_profile_enable", "cgs_profile_read", "cgs_batch_create", "cgs_batch_free", "cgs_batch_solve",
-    "cgs_batch_launches", "cgs_solve_batched", "cgs_mesh_tune", "cgs_mesh_set_schedule", "cgs_batch_tune",
+    "cgs_batch_launches", "cgs_solve_batched", "cgs_mesh_tune", "cgs_mesh_get_schedule", "cgs_mesh_set_schedule",
+    "cgs_batch_tune",
     "cgs_server_create",
     "cgs_server_free", "cgs_submit", "cgs_server_step", "cgs_poll", "cgs_server_drain", "cgs_server_footprint",
     "cgs_server_stats",
@@ -54,9 +55,13 @@ class MeshInfo(C.Structure):
     _fields_ = [("nv", C.c_int64), ("ne", C.c_int64), ("n_free", C.c_int64), ("n_sub", C.c_int64),
                 ("n_r", C.c_int64), ("max_sub_dofs", C.c_int64), ("sum_sub_dofs", C.c_int64),
                 ("footprint_bytes", C.c_size_t), ("setup_seconds", C.c_double),
-                ("kernel_launches", C.c_int64), ("vert_chunk", C.c_int32), ("sub_chunk", C.c_int32),
-                ("tile_tma", C.c_int32), ("n_box_entries", C.c_int64), ("n_lane_packs", C.c_int64),
-                ("persistent", C.c_int32)]
+                ("kernel_launches", C.c_int64), ("n_box_entries", C.c_int64), ("n_lane_packs", C.c_int64),
+                ("loop", C.c_int32)]
+
+
+class Schedule(C.Structure):
+    _fields_ = [(k, C.c_int32) for k in ("vert_chunk", "sub_chunk", "pack_chunk", "box_chunk", "tile_tma",
+                                         "persistent", "pdl", "row_packs")]
 
 
 _lib = None
@@ -107,7 +112,8 @@ def load(path: str = LIB_PATH):
         "cgs_server_stats": ([P, C.POINTER(C.c_size_t), C.POINTER(C.c_size_t), C.POINTER(I32), C.POINTER(I32)], I32),
         "cgs_server_launches": ([P], I64),
         "cgs_batch_tune": ([P, P], I32),
-        "cgs_mesh_set_schedule": ([P, I32, I32, I32, I32], I32),
+        "cgs_mesh_get_schedule": ([P, C.POINTER(Schedule)], I32),
+        "cgs_mesh_set_schedule": ([P, C.POINTER(Schedule)], I32),
         "cgs_status_string": ([I32], C.c_char_p),
         "cgs_last_error": ([], C.c_char_p),
     }
@@ -313,9 +319,21 @@ def cgs_mesh_tune(mesh, stream=None):
     _check(load().cgs_mesh_tune(mesh, _stream(stream)), "cgs_mesh_tune")
 
 
-def cgs_mesh_set_schedule(mesh, vert_chunk, sub_chunk, tile_tma, persistent=-1):
-    _check(load().cgs_mesh_set_schedule(mesh, int(vert_chunk), int(sub_chunk), int(tile_tma), int(persistent)),
-           "cgs_mesh_set_schedule")
+def cgs_mesh_get_schedule(mesh) -> dict:
+    sch = Schedule()
+    _check(load().cgs_mesh_get_schedule(mesh, C.byref(sch)), "cgs_mesh_get_schedule")
+    return {f: getattr(sch, f) for f, _ in Schedule._fields_}
+
+
+def cgs_mesh_set_schedule(mesh, **fields):
+    """Change fields of the mesh's schedule (the others keep their values)."""
+    cur = cgs_mesh_get_schedule(mesh)
+    unknown = set(fields) - set(cur)
+    if unknown:
+        raise ValueError(f"unknown schedule fields {sorted(unknown)}")
+    cur.update({k: int(v) for k, v in fields.items()})
+    sch = Schedule(**cur)
+    _check(load().cgs_mesh_set_schedule(mesh, C.byref(sch)), "cgs_mesh_set_schedule")
 
 
 def cgs_batch_tune(batch, stream=None):

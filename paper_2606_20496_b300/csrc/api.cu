@@ -249,19 +249,19 @@ bool precond_body(Engine& E, const Vecs& V, cudaStream_t st, bool dots = false) 
 
 // One flexible-PCG iteration over every slot of the engine: float64 vectors
 // in the FP64 form, float-pair vectors in the mixed forms.
-void pcg_iteration(Engine& E, cudaStream_t st) {
+void pcg_iteration(Engine& E, cudaStream_t st, const cudaGraphConditionalHandle* cond = nullptr) {
     const Plan& P = E.P;
     const Vecs& V = E.V;
     if (E.f64) {
         K(CGS_K_APPLY_A64, launch_apply64(P, V, V.p, V.q, 1.0, true, st));
         K(CGS_K_PCG_XR, (launch_pcg_update_xr<double, double>(P, V, V.q, st)));
         if (!precond_body(E, V, st, true)) K(CGS_K_PCG_DOTS, (launch_pcg_dots<double, double>(P, V, V.q, st)));
-        K(CGS_K_PCG_P, (launch_pcg_update_p<double, double>(P, V, V.q, st)));
+        K(CGS_K_PCG_P, (launch_pcg_update_p<double, double>(P, V, V.q, cond, st)));
     } else {
         K(CGS_K_APPLY_A64, launch_apply_pair_tiled(P, V, st));
         K(CGS_K_PCG_XR, launch_pcg_update_xr_pair(P, V, st));
         if (!precond_body(E, V, st, true)) K(CGS_K_PCG_DOTS, launch_pcg_dots_pair(P, V, st));
-        K(CGS_K_PCG_P, launch_pcg_update_p_pair(P, V, st));
+        K(CGS_K_PCG_P, launch_pcg_update_p_pair(P, V, cond, st));
     }
 }
 
@@ -320,8 +320,7 @@ cgs_status build_loop_graph(Engine& E) {
     E.prof = false;
     {
         cudaStream_t st = cs;
-        pcg_iteration(E, st);
-        launch_loop_cond(E.P, E.V, h, st);
+        pcg_iteration(E, st, &h);   // its last kernel sets the loop condition
     }
     E.prof = prof;
     E.launches = launches;
@@ -482,6 +481,7 @@ cudaError_t set_schedule(Engine& E, const Schedule& sch) {
     E.tables.release();
     E.tables = fresh;
     P.tile_tma = sch.tile_tma != 0;
+    P.pdl = sch.pdl != 0;
     E.P = P;
     E.sch = sch;
     if (E.gexec) {   // the captured loop holds the old grid sizes
@@ -656,8 +656,9 @@ cgs_status cgs_mesh_setup(cgs_ctx* ctx, const double* xyz, int64_t nv, const int
     const size_t bulk = f64 ? 8 : 4;
     const size_t est = (size_t)ne * (8 * 4 + kUpper * 8 + 4) + (f64 ? 0 : hs.at_hi.size() * 8 + (size_t)ne * 16) +
                        (size_t)nv * (32 + 16 + 1 + 8 + 4) + hs.sub_idx.size() * 4 +
-                       (hs.inv.size() + hs.pack_inv.size()) * (f64 ? 8 : prm.prec == CGS_FP32_BULK ? 4 : 2) +
-                       hs.pack_idx.size() * 4 + hs.ar_inv.size() * 8 +
+                       (hs.inv.size() + hs.pack_inv.size() + hs.rpack_inv.size()) *
+                           (f64 ? 8 : prm.prec == CGS_FP32_BULK ? 4 : 2) +
+                       (hs.pack_idx.size() + hs.rpack_idx.size()) * 4 + hs.ar_inv.size() * 8 +
                        (size_t)nv * (5 * 8 + 2 * bulk);
     {
         std::lock_guard<std::mutex> lk(ctx->mu);
@@ -792,6 +793,42 @@ cgs_status cgs_mesh_setup(cgs_ctx* ctx, const double* xyz, int64_t nv, const int
             UP(d.pack_scale, sc);
         }
     }
+    if (!hs.rpack_m.empty()) {
+        // row packs: host [pack][lane][entry] -> device groups across lanes
+        d.n_rpack = (int64_t)hs.rpack_m.size();
+        UP(d.rpack_m, hs.rpack_m);
+        UP(d.rpack_idx_off, std::vector<int64_t>(hs.rpack_idx_off.begin(), hs.rpack_idx_off.end() - 1));
+        UP(d.rpack_inv_off, std::vector<int64_t>(hs.rpack_inv_off.begin(), hs.rpack_inv_off.end() - 1));
+        UP(d.rpack_idx, hs.rpack_idx);
+        const size_t total = hs.rpack_inv.size();
+        if (prm.prec == CGS_FP32_BULK) {
+            std::vector<float> f(total);
+            for (int64_t P = 0; P < d.n_rpack; ++P) {
+                const int64_t ao = hs.rpack_inv_off[P], T = row_entries(hs.rpack_m[P]);
+                for (int l = 0; l < 32; ++l)
+                    for (int64_t e = 0; e < T; ++e)
+                        f[ao + (e / 4) * 128 + l * 4 + e % 4] = (float)hs.rpack_inv[ao + l * T + e];
+            }
+            UP(d.rpack_inv32, f);
+        } else {
+            std::vector<__half> h(total);
+            std::vector<float> sc((size_t)d.n_rpack * 32, 1.0f);
+            for (int64_t P = 0; P < d.n_rpack; ++P) {
+                const int64_t ao = hs.rpack_inv_off[P], T = row_entries(hs.rpack_m[P]);
+                for (int l = 0; l < 32; ++l) {
+                    double mx = 0.0;
+                    for (int64_t e = 0; e < T; ++e) mx = std::max(mx, std::fabs(hs.rpack_inv[ao + l * T + e]));
+                    const double sv = mx > 0 ? mx : 1.0;
+                    sc[(size_t)P * 32 + l] = (float)sv;
+                    for (int64_t e = 0; e < T; ++e)
+                        h[ao + (e / 8) * 256 + l * 8 + e % 8] =
+                            __float2half_rn((float)(hs.rpack_inv[ao + l * T + e] / sv));
+                }
+            }
+            UP(d.rpack_inv16, h);
+            UP(d.rpack_scale, sc);
+        }
+    }
     UP(d.wov64, hs.wov);
     if (!f64) {
         std::vector<float> w(hs.wov.begin(), hs.wov.end());
@@ -840,7 +877,7 @@ cgs_status cgs_mesh_setup(cgs_ctx* ctx, const double* xyz, int64_t nv, const int
         m->d_dev = const_cast<DevMesh*>(dd);
     }
     // one solve slot and its work tables
-    m->sizes = MeshSizes{nv, ne, d.ntiles, hs.n_wsub, hs.nr, d.n_pack, d.nvb, d.nrng};
+    m->sizes = MeshSizes{nv, ne, d.ntiles, hs.n_wsub, hs.nr, d.n_pack, d.nvb, d.nrng, d.n_rpack};
     Engine& E = m->E;
     E.f64 = f64;
     E.prec = prm.prec;
@@ -860,7 +897,7 @@ cgs_status cgs_mesh_setup(cgs_ctx* ctx, const double* xyz, int64_t nv, const int
         smallest.box_chunk = 256;
         cudaError_t e = alloc_pools(m->mem, E, nv, hs.nr, mesh_partial_slots(sz, smallest), 1);
         if (e != cudaSuccess) return cleanup(cuda_fail(e, "scratch"));
-        e = set_schedule(E, default_schedule(nv, hs.n_wsub, d.n_pack));
+        e = set_schedule(E, default_schedule(nv, hs.n_wsub, d.n_pack, d.n_pack * 32));
         if (e != cudaSuccess) return cleanup(cuda_fail(e, "work tables"));
     }
     {
@@ -915,10 +952,10 @@ cgs_status cgs_mesh_info(const cgs_mesh* m, cgs_mesh_info_t* info) {
     if (!m || !info) return fail(CGS_ERR_INVALID_ARG, "null argument");
     *info = m->info;
     info->kernel_launches = m->E.launches;
-    info->vert_chunk = m->E.sch.vert_chunk;
-    info->sub_chunk = m->E.sch.sub_chunk;
-    info->tile_tma = m->E.sch.tile_tma;
-    info->persistent = use_persistent(const_cast<Engine&>(m->E), m->E.sch) ? 1 : 0;
+    {
+        Engine& E = const_cast<Engine&>(m->E);
+        info->loop = use_persistent(E, E.sch) ? 2 : (E.graph_failed ? 0 : 1);
+    }
     return CGS_OK;
 }
 
@@ -1205,7 +1242,7 @@ cgs_status cgs_batch_create(cgs_ctx* ctx, cgs_mesh* const* meshes, int nmesh, in
         E.P.nslots = nslots;
         if ((e = alloc_pools(B->mem, E, total_v, total_r, total_p, nslots)) != cudaSuccess)
             return cleanup(cuda_fail(e, "pools"));
-        if ((e = set_schedule(E, default_schedule(total_v, total_sub, total_pack))) != cudaSuccess)
+        if ((e = set_schedule(E, default_schedule(total_v, total_sub, total_pack, total_pack * 32))) != cudaSuccess)
             return cleanup(cuda_fail(e, "work tables"));
         if ((e = B->mem.alloc(&B->bptr_d, nslots)) != cudaSuccess) return cleanup(cuda_fail(e, "pointers"));
         if ((e = B->mem.alloc(&B->xptr_d, nslots)) != cudaSuccess) return cleanup(cuda_fail(e, "pointers"));
@@ -1273,17 +1310,31 @@ cgs_status cgs_batch_solve(cgs_batch* B, const double* const* b, double* const* 
 
 int64_t cgs_batch_launches(const cgs_batch* B) { return B ? B->E.launches : 0; }
 
-cgs_status cgs_mesh_set_schedule(cgs_mesh* m, int vert_chunk, int sub_chunk, int tile_tma, int persistent) {
-    if (!m) return fail(CGS_ERR_INVALID_ARG, "null mesh");
-    if (vert_chunk < 256 || vert_chunk > 8192 || vert_chunk % 256 || sub_chunk < 8 || sub_chunk > 512 ||
-        sub_chunk % 8 || (tile_tma != 0 && tile_tma != 1) || persistent < -1 || persistent > 1)
+cgs_status cgs_mesh_get_schedule(const cgs_mesh* m, cgs_schedule* out) {
+    if (!m || !out) return fail(CGS_ERR_INVALID_ARG, "null argument");
+    const Schedule& s = m->E.sch;
+    *out = cgs_schedule{s.vert_chunk, s.sub_chunk, s.pack_chunk, s.box_chunk, s.tile_tma, s.persistent,
+                        m->E.P.pdl ? 1 : 0, s.row_packs};
+    return CGS_OK;
+}
+
+cgs_status cgs_mesh_set_schedule(cgs_mesh* m, const cgs_schedule* c) {
+    if (!m || !c) return fail(CGS_ERR_INVALID_ARG, "null argument");
+    auto in = [](int v, int lo, int hi, int step) { return v >= lo && v <= hi && v % step == 0; };
+    if (!in(c->vert_chunk, 256, 8192, 256) || !in(c->sub_chunk, 8, 512, 8) || !in(c->pack_chunk, 8, 256, 8) ||
+        !in(c->box_chunk, 256, 4096, 256) || (c->tile_tma != 0 && c->tile_tma != 1) || c->persistent < -1 ||
+        c->persistent > 1 || (c->pdl != 0 && c->pdl != 1) || (c->row_packs != 0 && c->row_packs != 1))
         return fail(CGS_ERR_INVALID_ARG, "schedule out of range");
     CGS_CUDA(cudaSetDevice(m->ctx->device));
     Schedule sch = m->E.sch;
-    sch.vert_chunk = vert_chunk;
-    sch.sub_chunk = sub_chunk;
-    sch.tile_tma = tile_tma;
-    sch.persistent = persistent;
+    sch.vert_chunk = c->vert_chunk;
+    sch.sub_chunk = c->sub_chunk;
+    sch.pack_chunk = c->pack_chunk;
+    sch.box_chunk = c->box_chunk;
+    sch.tile_tma = c->tile_tma;
+    sch.persistent = c->persistent;
+    sch.pdl = c->pdl;
+    sch.row_packs = c->row_packs;
     CGS_CUDA(set_schedule(m->E, sch));
     return CGS_OK;
 }
@@ -1445,6 +1496,7 @@ cudaError_t server_tables(cgs_server* sv, const std::vector<int>& ids, cgs_serve
     P.nslots = sv->max_slots;
     P.wait_limit = sv->E.P.wait_limit;
     P.tile_tma = sv->sch.tile_tma != 0;
+    P.pdl = sv->sch.pdl != 0;
     for (int k : ids) {
         const cgs_server::SlotState& ss = sv->slots[k];
         const cgs_mesh* m = ss.req.mesh;
@@ -1550,7 +1602,7 @@ cgs_status cgs_server_create(cgs_ctx* ctx, int max_slots, int64_t pool_nv, int64
         sv->xptr_h[k] = nullptr;
     }
     // chunks sized for the whole arena as one problem: many slots at once
-    sv->sch = default_schedule(pool_nv, pool_nv / 8, pool_nv / 256);
+    sv->sch = default_schedule(pool_nv, pool_nv / 8, pool_nv / 256, pool_nv / 8);
     E.V.bptr = sv->bptr_d;
     E.V.xptr = sv->xptr_d;
     {

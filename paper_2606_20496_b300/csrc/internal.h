@@ -52,6 +52,11 @@ struct HostSetup {
     std::vector<int64_t> pack_inv_off; // n_pack+1, offsets into pack_inv (32*lane_entries(M) per pack)
     std::vector<int32_t> pack_idx;     // [pack][k][lane] vertex id, -1 = padding
     std::vector<double> pack_inv;      // [pack][lane][lane_entries(M)] upper triangle, row-major, float64
+    // row packs (small meshes): the same subdomains, 8 per pack, full rows
+    std::vector<int32_t> rpack_m;
+    std::vector<int64_t> rpack_idx_off, rpack_inv_off;
+    std::vector<int32_t> rpack_idx;    // [pack][k][lane] vertex id of row k of lane's subdomain, -1 = padding
+    std::vector<double> rpack_inv;     // [pack][lane][row_entries(M)] rows g, g+4, ... of the inverse
     // box coarse space
     int b[3] = {1, 1, 1};
     double lo[3] = {0, 0, 0}, H[3] = {1, 1, 1};
@@ -135,6 +140,16 @@ struct DevMesh {
     const float* pack_inv32 = nullptr;
     const __half* pack_inv16 = nullptr;
     const float* pack_scale = nullptr;     // n_pack*32 (half entries)
+    // row packs (small meshes): 8 subdomains per pack, 4 lanes each holding
+    // rows g, g + 4, ... in full; same group layouts and per-lane scales
+    int64_t n_rpack = 0;
+    const int32_t* rpack_m = nullptr;
+    const int64_t* rpack_idx_off = nullptr;
+    const int64_t* rpack_inv_off = nullptr;
+    const int32_t* rpack_idx = nullptr;
+    const float* rpack_inv32 = nullptr;
+    const __half* rpack_inv16 = nullptr;
+    const float* rpack_scale = nullptr;
     const double* wov64 = nullptr;     // nv
     const float* wov32 = nullptr;      // nv
     const double* ar_inv = nullptr;    // nr*nr (FP64 form)
@@ -146,7 +161,7 @@ struct DevMesh {
 // Work tables: element ranges, element tiles, vertex ranges, warp-kernel
 // subdomain ranges, reduced-row ranges, lane-pack ranges, ranges of the
 // per-vertex box lists (interpolation) and of their cell-sorted entries
-// (restriction).
+// (restriction), row-pack ranges.
 enum WorkKind {
     kWorkElem = 0,
     kWorkTile,
@@ -156,6 +171,7 @@ enum WorkKind {
     kWorkPack,
     kWorkBox,
     kWorkBoxEnt,
+    kWorkRowPack,
     kWorkKinds
 };
 
@@ -170,6 +186,7 @@ struct Plan {
     bool any_nr = false;                   // some mesh has a reduced space
     int wait_limit = 1 << 20;              // iteration limit of bounded device waits
     bool tile_tma = false;                 // element tiles staged by TMA (else streamed by the threads)
+    bool pdl = true;                       // launch with programmatic stream serialization
 };
 
 // Grid-wide barrier of the persistent PCG kernel (device memory, zeroed
@@ -227,6 +244,13 @@ inline int lane_class(int m) {
 }
 // entries stored per lane: the upper triangle, padded to a multiple of 8
 constexpr int lane_entries(int M) { return (M * (M + 1) / 2 + 7) / 8 * 8; }
+// Row packs (small meshes): 8 subdomains per warp, 4 lanes each; lane g of
+// a subdomain holds the full rows g, g + 4, ... (ceil(M / 4) rows of M).
+constexpr int kRowLanes = 4;
+constexpr int row_pack_rows(int M) { return (M + kRowLanes - 1) / kRowLanes; }
+constexpr int row_entries(int M) { return (row_pack_rows(M) * M + 7) / 8 * 8; }
+// meshes with fewer lane subdomains than this also get row packs
+constexpr int64_t kRowPackMaxSubs = 9472;
 constexpr int kElemChunk = 256;   // elements per block
 // Box cells per axis, at most kMaxBoxes; the box lists store a cell as its
 // packed coordinates ci | cj << 10 | ck << 20.

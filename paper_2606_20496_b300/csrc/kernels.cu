@@ -47,6 +47,17 @@ __device__ __forceinline__ bool is_done(const SolveScalars* S) {
     return S != nullptr && *(volatile const int*)&S->done;
 }
 
+// Programmatic dependent launch: a kernel launched with the programmatic
+// stream-serialization attribute may start while its predecessor runs.
+// pdl_wait returns once the predecessor grids have completed and their
+// writes are visible, so every kernel calls it before touching data produced
+// upstream.  pdl_trigger lets this grid's successor be scheduled; kernels
+// call it late, just before their per-slot reduction tail (or implicitly at
+// exit), so that waiting successors do not take SM resources from the
+// predecessor's main work.  Both are no-ops for an ordinary launch.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // Block-wide sum of NV values; result valid in thread 0.
 template <int NV>
 __device__ __forceinline__ void block_sum(double (&v)[NV]) {
@@ -131,6 +142,7 @@ __device__ __forceinline__ void load_conn(const int32_t* __restrict__ conn, int6
 // once the slot has stopped.
 #define CGS_WORK_PROLOGUE()                              \
     const Work w = work[blockIdx.x];                     \
+    pdl_wait();                                          \
     SolveScalars* S = V.S ? V.S + w.slot : nullptr;      \
     if (is_done(S)) return;                              \
     const DevMesh& M = meshes[w.mesh];                   \
@@ -189,6 +201,7 @@ __device__ __forceinline__ void apply64_item(const DevMesh* __restrict__ meshes,
     }
     if (kDot) {
         double val[1] = {energy}, tot[1];
+        pdl_trigger();   // the successor may launch during the reduction tail
         if (slot_sum<1>(val, V.partials + w.poff, w.idx, w.count, &S->ticket[0], tot) && threadIdx.x == 0) {
             const double pq = tot[0];
             S->pq = pq;
@@ -201,12 +214,15 @@ __device__ __forceinline__ void apply64_item(const DevMesh* __restrict__ meshes,
         }
     }
 }
+
 template <bool kDot>
 __global__ void __launch_bounds__(kBlock) apply64_kernel(const DevMesh* __restrict__ meshes,
                                                          const Work* __restrict__ work, Vecs V,
                                                          const double* __restrict__ xin, double* __restrict__ yout,
                                                          double alpha) {
-    apply64_item<kDot>(meshes, work[blockIdx.x], V, xin, yout, alpha);
+    const Work w_ = work[blockIdx.x];
+    pdl_wait();
+    apply64_item<kDot>(meshes, w_, V, xin, yout, alpha);
 }
 
 // ---------------------------------------------------------------------------
@@ -225,6 +241,7 @@ __device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& 
     s = __fadd_rn(a, b);
     e = __fsub_rn(b, __fsub_rn(s, a));
 }
+
 // (ah + al)(bh + bl) ~= ph + pl (the al*bl term, ~2^-48 relative, is dropped)
 __device__ __forceinline__ void pair_mul(float ah, float al, float bh, float bl, float& ph, float& pl) {
     ph = __fmul_rn(ah, bh);
@@ -232,11 +249,13 @@ __device__ __forceinline__ void pair_mul(float ah, float al, float bh, float bl,
     pl = __fmaf_rn(ah, bl, pl);
     pl = __fmaf_rn(al, bh, pl);
 }
+
 // x -> (hi, lo) float pair, hi = x rounded to float, lo = rounded remainder
 __device__ __forceinline__ float2 split_pair(double x) {
     const float h = __double2float_rn(x);
     return make_float2(h, __double2float_rn(x - (double)h));
 }
+
 // (yh, yl) += (ph, pl) without renormalising (few terms per accumulator)
 __device__ __forceinline__ void pair_acc(float& yh, float& yl, float ph, float pl) {
     float s, e;
@@ -257,12 +276,14 @@ __device__ __forceinline__ float2 pr_add(float2 a, float2 b) {
     fast_two_sum(s, e, h, l);
     return make_float2(h, l);
 }
+
 // a b + c
 __device__ __forceinline__ float2 pr_fma(float2 a, float2 b, float2 c) {
     float ph, pl;
     pair_mul(a.x, a.y, b.x, b.y, ph, pl);
     return pr_add(make_float2(ph, pl), c);
 }
+
 // acc += a b (unnormalised accumulator, a few terms per thread)
 __device__ __forceinline__ void pr_dot_acc(float& h, float& l, float2 a, float2 b) {
     float ph, pl;
@@ -336,6 +357,7 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
                  : "memory");
 }
+
 // bytes must be a multiple of 16, src and dst 16-byte aligned
 __device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
@@ -352,6 +374,7 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
+
 // Wait for phase 0 of the tile barrier with an iteration limit.  On expiry
 // the slot is flagged CGS_ERR_TIMEOUT and stopped, and the block waits once
 // more (bounded) for its copy before it may return.
@@ -599,6 +622,7 @@ __device__ __forceinline__ void apply_pair_tiled_item(const DevMesh* __restrict_
     if (!S) return;   // no slot scalars (timing runs): no reduction
     float vh[1] = {eh}, vl[1] = {el};
     double tot[1];
+    pdl_trigger();   // the successor may launch during the reduction tail
     if (slot_sum_pair<1>(vh, vl, V.partials + w.poff, w.idx, w.count, &S->ticket[0], tot) && threadIdx.x == 0) {
         const double pq = tot[0];
         S->pq = pq;
@@ -613,11 +637,14 @@ __device__ __forceinline__ void apply_pair_tiled_item(const DevMesh* __restrict_
         }
     }
 }
+
 template <bool kTma>
 __global__ void __launch_bounds__(kBlock, kTma ? 3 : 4) apply_pair_tiled_kernel(const DevMesh* __restrict__ meshes,
                                                                                  const Work* __restrict__ work,
                                                                                  Vecs V, int wait_limit) {
-    apply_pair_tiled_item<kTma>(meshes, work[blockIdx.x], V, wait_limit);
+    const Work w_ = work[blockIdx.x];
+    pdl_wait();
+    apply_pair_tiled_item<kTma>(meshes, w_, V, wait_limit);
 }
 
 // y += alpha A x in float32 (inner apply s -= A l of the hybrid step); the
@@ -693,13 +720,16 @@ __device__ __forceinline__ void apply28f_tiled_item(const DevMesh* __restrict__ 
             atomicAdd(&y[v], alpha * ys[i]);
     }
 }
+
 template <bool kTma>
 __global__ void __launch_bounds__(kBlock, kTma ? 4 : 5) apply28f_tiled_kernel(const DevMesh* __restrict__ meshes,
                                                                                const Work* __restrict__ work, Vecs V,
                                                                                const float* __restrict__ xin,
                                                                                float* __restrict__ yout, float alpha,
                                                                                int wait_limit) {
-    apply28f_tiled_item<kTma>(meshes, work[blockIdx.x], V, xin, yout, alpha, wait_limit);
+    const Work w_ = work[blockIdx.x];
+    pdl_wait();
+    apply28f_tiled_item<kTma>(meshes, w_, V, xin, yout, alpha, wait_limit);
 }
 
 // ---------------------------------------------------------------------------
@@ -724,6 +754,7 @@ template <typename T, typename Stor>
 __device__ __forceinline__ T stage(const Stor* p, size_t i, float scale) {
     return (T)load_entry<Stor>(p, i, scale);
 }
+
 template <>
 __device__ __forceinline__ double stage<double, double>(const double* p, size_t i, float) { return __ldg(p + i); }
 
@@ -832,12 +863,15 @@ __device__ __forceinline__ void local_warp_item(const DevMesh* __restrict__ mesh
         }
     }
 }
+
 template <typename T, typename Stor>
 __global__ void __launch_bounds__(kBlock) local_warp_kernel(const DevMesh* __restrict__ meshes,
                                                             const Work* __restrict__ work, Vecs V,
                                                             const T* __restrict__ rin, T* __restrict__ outv,
                                                             int weighted) {
-    local_warp_item<T, Stor>(meshes, work[blockIdx.x], V, rin, outv, weighted);
+    const Work w_ = work[blockIdx.x];
+    pdl_wait();
+    local_warp_item<T, Stor>(meshes, w_, V, rin, outv, weighted);
 }
 
 // Subdomains with more than 64 dofs: the whole block on one subdomain, rows
@@ -864,12 +898,15 @@ __device__ __forceinline__ void local_block_item(const DevMesh* __restrict__ mes
         }
     }
 }
+
 template <typename T, typename Stor>
 __global__ void __launch_bounds__(kBlock) local_block_kernel(const DevMesh* __restrict__ meshes,
                                                              const Work* __restrict__ work, Vecs V,
                                                              const T* __restrict__ rin, T* __restrict__ outv,
                                                              int weighted) {
-    local_block_item<T, Stor>(meshes, work[blockIdx.x], V, rin, outv, weighted);
+    const Work w_ = work[blockIdx.x];
+    pdl_wait();
+    local_block_item<T, Stor>(meshes, w_, V, rin, outv, weighted);
 }
 
 // ---------------------------------------------------------------------------
@@ -982,12 +1019,100 @@ __device__ __forceinline__ void local_lane_item(const DevMesh* __restrict__ mesh
         }
     }
 }
+
 template <typename Stor>
 __global__ void __launch_bounds__(kBlock, 2) local_lane_kernel(const DevMesh* __restrict__ meshes,
                                                                const Work* __restrict__ work, Vecs V,
                                                                const float* __restrict__ rin,
                                                                float* __restrict__ outv, int weighted) {
-    local_lane_item<Stor>(meshes, work[blockIdx.x], V, rin, outv, weighted);
+    const Work w_ = work[blockIdx.x];
+    pdl_wait();
+    local_lane_item<Stor>(meshes, w_, V, rin, outv, weighted);
+}
+
+// ---------------------------------------------------------------------------
+// Local solves of small meshes, four lanes per subdomain (row packs): a warp
+// takes 8 subdomains of one size class; lane 4 s + g keeps subdomain s's x
+// (M values) and forms y_i = sum_j inv(i, j) x_j for its rows i = g, g + 4,
+// ... from full stored rows.  Twice the entries of the triangle, a quarter
+// of the sequential work per lane: for meshes too small to fill the GPU one
+// lane per subdomain.
+// ---------------------------------------------------------------------------
+template <int Mc, class Entries>
+__device__ __forceinline__ void row_solve(Entries A, const int32_t* __restrict__ idx, const float* __restrict__ r,
+                                          float* __restrict__ out, const float* __restrict__ wov, int lane) {
+    constexpr int R = row_pack_rows(Mc);
+    const int g = lane % kRowLanes;
+    float x[Mc], y[R];
+#pragma unroll
+    for (int k = 0; k < Mc; ++k) {
+        const int v = __ldg(&idx[k * 32 + lane]);
+        x[k] = v >= 0 ? __ldg(&r[v]) : 0.0f;
+    }
+    int e = 0;
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+        float acc = 0.0f;
+#pragma unroll
+        for (int j = 0; j < Mc; ++j, ++e) acc = fmaf(A.get(e), x[j], acc);
+        y[q] = acc;
+    }
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+        const int i = q * kRowLanes + g;
+        if (i >= Mc) continue;
+        const int v = __ldg(&idx[i * 32 + lane]);
+        if (v >= 0) atomicAdd(&out[v], wov ? y[q] * __ldg(&wov[v]) : y[q]);
+    }
+}
+
+template <class Entries>
+__device__ __forceinline__ void row_dispatch(int Mc, const Entries& A, const int32_t* idx, const float* r,
+                                             float* out, const float* wov, int lane) {
+    switch (Mc) {
+        case 8: row_solve<8>(A, idx, r, out, wov, lane); break;
+        case 12: row_solve<12>(A, idx, r, out, wov, lane); break;
+        case 16: row_solve<16>(A, idx, r, out, wov, lane); break;
+        case 18: row_solve<18>(A, idx, r, out, wov, lane); break;
+        case 20: row_solve<20>(A, idx, r, out, wov, lane); break;
+        case 24: row_solve<24>(A, idx, r, out, wov, lane); break;
+        case 27: row_solve<27>(A, idx, r, out, wov, lane); break;
+        default: row_solve<32>(A, idx, r, out, wov, lane); break;
+    }
+}
+
+// out += W_ov sum_p R_p^T A_p^{-1} R_p r over the row packs (float r, out).
+template <typename Stor>
+__device__ __forceinline__ void local_rowpack_item(const DevMesh* __restrict__ meshes, const Work& w, Vecs V,
+                                                   const float* __restrict__ rin, float* __restrict__ outv,
+                                                   int weighted) {
+    CGS_ITEM_PROLOGUE();
+    const float* r = rin + w.voff;
+    float* out = outv + w.voff;
+    const float* wov = weighted ? M.wov32 : nullptr;
+    const int lane = threadIdx.x & 31;
+    for (int pk = w.begin + (int)(threadIdx.x >> 5); pk < w.end; pk += kBlock / 32) {
+        const int Mc = __ldg(&M.rpack_m[pk]);
+        const int32_t* idx = M.rpack_idx + __ldg(&M.rpack_idx_off[pk]);
+        const int64_t ao = __ldg(&M.rpack_inv_off[pk]);
+        if (std::is_same<Stor, float>::value) {
+            LaneEntries32 A{reinterpret_cast<const float4*>(M.rpack_inv32 + ao), lane, {}};
+            row_dispatch(Mc, A, idx, r, out, wov, lane);
+        } else {
+            LaneEntries16 A{reinterpret_cast<const uint4*>(M.rpack_inv16 + ao), lane,
+                            __ldg(&M.rpack_scale[(size_t)pk * 32 + lane]), {}};
+            row_dispatch(Mc, A, idx, r, out, wov, lane);
+        }
+    }
+}
+template <typename Stor>
+__global__ void __launch_bounds__(kBlock) local_rowpack_kernel(const DevMesh* __restrict__ meshes,
+                                                               const Work* __restrict__ work, Vecs V,
+                                                               const float* __restrict__ rin,
+                                                               float* __restrict__ outv, int weighted) {
+    const Work w_ = work[blockIdx.x];
+    pdl_wait();
+    local_rowpack_item<Stor>(meshes, w_, V, rin, outv, weighted);
 }
 
 // ---------------------------------------------------------------------------
@@ -1160,11 +1285,14 @@ __device__ __forceinline__ void restrict_item(const DevMesh* __restrict__ meshes
                      std::integral_constant<bool, kPairOut>());
     }
 }
+
 template <typename T, typename Tin, bool kPairOut>
 __global__ void __launch_bounds__(kBlock) restrict_kernel(const DevMesh* __restrict__ meshes,
                                                           const Work* __restrict__ work, Vecs V,
                                                           const Tin* __restrict__ sin, void* __restrict__ rrv) {
-    restrict_item<T, Tin, kPairOut>(meshes, work[blockIdx.x], V, sin, rrv);
+    const Work w_ = work[blockIdx.x];
+    pdl_wait();
+    restrict_item<T, Tin, kPairOut>(meshes, w_, V, sin, rrv);
 }
 
 // z += W Q^T J_L u_r by vertex: z_v += sum_c weight_c sum_m w_m^c(x_v) u_r[m]
@@ -1233,9 +1361,11 @@ __device__ __forceinline__ void interp_add_item(const DevMesh* __restrict__ mesh
     bool last;
     if (kDots == 2) {
         float vh[2] = {rh, qh}, vl[2] = {rl, ql};
+        pdl_trigger();   // the successor may launch during the reduction tail
         last = slot_sum_pair<2>(vh, vl, V.partials + w.poff, w.idx, w.count, &S->ticket[3], tot);
     } else {
         double val2[2] = {zr, zq};
+        pdl_trigger();   // the successor may launch during the reduction tail
         last = slot_sum<2>(val2, V.partials + w.poff, w.idx, w.count, &S->ticket[3], tot);
     }
     if (last && threadIdx.x == 0) {
@@ -1251,11 +1381,14 @@ __device__ __forceinline__ void interp_add_item(const DevMesh* __restrict__ mesh
         }
     }
 }
+
 template <typename T, typename Tu, int kDots>
 __global__ void __launch_bounds__(kBlock) interp_add_kernel(const DevMesh* __restrict__ meshes,
                                                             const Work* __restrict__ work, Vecs V,
                                                             const Tu* __restrict__ urv, T* __restrict__ zv) {
-    interp_add_item<T, Tu, kDots>(meshes, work[blockIdx.x], V, urv, zv);
+    const Work w_ = work[blockIdx.x];
+    pdl_wait();
+    interp_add_item<T, Tu, kDots>(meshes, w_, V, urv, zv);
 }
 
 // u_r = A_r^{-1} r_r: one warp per row of the full symmetric inverse; also a
@@ -1282,7 +1415,9 @@ __global__ void __launch_bounds__(kBlock) coarse_gemv_kernel(const DevMesh* __re
                                                              const Work* __restrict__ work, Vecs V,
                                                              const double* __restrict__ rrv,
                                                              double* __restrict__ urv, float* __restrict__ ur32v) {
-    coarse_gemv_item(meshes, work[blockIdx.x], V, rrv, urv, ur32v);
+    const Work w_ = work[blockIdx.x];
+    pdl_wait();
+    coarse_gemv_item(meshes, w_, V, rrv, urv, ur32v);
 }
 
 // u_r = A_r^{-1} r_r in float-pair arithmetic (mixed forms): the inverse and
@@ -1339,7 +1474,9 @@ __global__ void __launch_bounds__(kBlock) coarse_pair_kernel(const DevMesh* __re
                                                              const Work* __restrict__ work, Vecs V,
                                                              const float2* __restrict__ rr2v,
                                                              double* __restrict__ urv, float* __restrict__ ur32v) {
-    coarse_pair_item(meshes, work[blockIdx.x], V, rr2v, urv, ur32v);
+    const Work w_ = work[blockIdx.x];
+    pdl_wait();
+    coarse_pair_item(meshes, w_, V, rr2v, urv, ur32v);
 }
 
 // ---------------------------------------------------------------------------
@@ -1365,6 +1502,7 @@ __global__ void __launch_bounds__(kBlock) pcg_init_kernel(const DevMesh* __restr
                                                           const Work* __restrict__ work, Vecs V, Tq* qv,
                                                           double rtol, int maxit) {
     const Work w = work[blockIdx.x];
+    pdl_wait();
     SolveScalars* S = V.S + w.slot;
     const DevMesh& M = meshes[w.mesh];
     const double* b = V.bptr ? V.bptr[w.slot] : V.b + w.voff;
@@ -1380,6 +1518,7 @@ __global__ void __launch_bounds__(kBlock) pcg_init_kernel(const DevMesh* __restr
         acc = fma(bi, bi, acc);
     }
     double val[1] = {acc}, tot[1];
+    pdl_trigger();   // the successor may launch during the reduction tail
     if (slot_sum<1>(val, V.partials + w.poff, w.idx, w.count, &S->ticket[1], tot) && threadIdx.x == 0) {
         S->bnorm2 = tot[0];
         S->tol2 = rtol * rtol * tot[0];
@@ -1430,6 +1569,7 @@ __global__ void __launch_bounds__(kBlock) pcg_first_dir_kernel(const DevMesh* __
         acc = fma(zi, r[i], acc);
     }
     double val[1] = {acc}, tot[1];
+    pdl_trigger();   // the successor may launch during the reduction tail
     if (slot_sum<1>(val, V.partials + w.poff, w.idx, w.count, &S->ticket[1], tot) && threadIdx.x == 0) {
         S->rho = tot[0];
         if (!(tot[0] > 0.0) || !isfinite(tot[0])) {
@@ -1466,6 +1606,7 @@ __device__ __forceinline__ void pcg_update_xr_item(const DevMesh* __restrict__ m
     const int64_t r0 = (int64_t)w.idx * chunk, r1 = min((int64_t)M.nr, r0 + chunk);
     for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) V.rr[w.roff + i] = 0.0;
     double val[1] = {acc}, tot[1];
+    pdl_trigger();   // the successor may launch during the reduction tail
     if (slot_sum<1>(val, V.partials + w.poff, w.idx, w.count, &S->ticket[2], tot) && threadIdx.x == 0) {
         S->rr = tot[0];
         const int it = S->iters + 1;
@@ -1482,11 +1623,14 @@ __device__ __forceinline__ void pcg_update_xr_item(const DevMesh* __restrict__ m
         }
     }
 }
+
 template <typename Tz, typename Tq>
 __global__ void __launch_bounds__(kBlock) pcg_update_xr_kernel(const DevMesh* __restrict__ meshes,
                                                                const Work* __restrict__ work, Vecs V,
                                                                const Tq* __restrict__ qv) {
-    pcg_update_xr_item<Tz, Tq>(meshes, work[blockIdx.x], V, qv);
+    const Work w_ = work[blockIdx.x];
+    pdl_wait();
+    pcg_update_xr_item<Tz, Tq>(meshes, w_, V, qv);
 }
 
 // z.r and z.q; beta = -alpha (z.q) / rho (Polak-Ribiere, since
@@ -1505,6 +1649,7 @@ __device__ __forceinline__ void pcg_dots_item(const DevMesh* __restrict__ meshes
         zq = fma(zi, qval(q, i), zq);
     }
     double val[2] = {zr, zq}, tot[2];
+    pdl_trigger();   // the successor may launch during the reduction tail
     if (slot_sum<2>(val, V.partials + w.poff, w.idx, w.count, &S->ticket[3], tot) && threadIdx.x == 0) {
         S->zr = tot[0];
         S->zq = tot[1];
@@ -1517,11 +1662,14 @@ __device__ __forceinline__ void pcg_dots_item(const DevMesh* __restrict__ meshes
         }
     }
 }
+
 template <typename Tz, typename Tq>
 __global__ void __launch_bounds__(kBlock) pcg_dots_kernel(const DevMesh* __restrict__ meshes,
                                                           const Work* __restrict__ work, Vecs V,
                                                           const Tq* __restrict__ qv) {
-    pcg_dots_item<Tz, Tq>(meshes, work[blockIdx.x], V, qv);
+    const Work w_ = work[blockIdx.x];
+    pdl_wait();
+    pcg_dots_item<Tz, Tq>(meshes, w_, V, qv);
 }
 
 // p = z + beta p (and p2), q = 0 for the next product.
@@ -1540,10 +1688,31 @@ __device__ __forceinline__ void pcg_update_p_item(const DevMesh* __restrict__ me
         qzero(q, i);
     }
 }
+
+// Condition of the device-side loop (graph while node): continue while some
+// slot is still running and fewer than maxit + 2 bodies have run (slot 0
+// counts the bodies; all slots share maxit).  Evaluated by block 0 of the
+// iteration's last kernel, once every slot's stopping flag is final.
+__device__ __forceinline__ void loop_condition(SolveScalars* __restrict__ S, int nslots,
+                                               cudaGraphConditionalHandle cond) {
+    int running = 0;
+    for (int i = threadIdx.x; i < nslots; i += blockDim.x) running |= !*(volatile const int*)&S[i].done;
+    running = __syncthreads_or(running);
+    if (threadIdx.x == 0) {
+        const int loops = ++S[0].loops;
+        cudaGraphSetConditional(cond, (running && loops < S[0].maxit + 2) ? 1u : 0u);
+    }
+}
+
 template <typename Tz, typename Tq>
 __global__ void __launch_bounds__(kBlock) pcg_update_p_kernel(const DevMesh* __restrict__ meshes,
-                                                              const Work* __restrict__ work, Vecs V, Tq* qv) {
-    pcg_update_p_item<Tz, Tq>(meshes, work[blockIdx.x], V, qv);
+                                                              const Work* __restrict__ work, Vecs V, Tq* qv,
+                                                              int nslots, cudaGraphConditionalHandle cond,
+                                                              int set_cond) {
+    if (set_cond && blockIdx.x == 0) loop_condition(V.S, nslots, cond);
+    const Work w_ = work[blockIdx.x];
+    pdl_wait();
+    pcg_update_p_item<Tz, Tq>(meshes, w_, V, qv);
 }
 
 // ---------------------------------------------------------------------------
@@ -1561,6 +1730,7 @@ __global__ void __launch_bounds__(kBlock) pcg_init_pair_kernel(const DevMesh* __
                                                                const Work* __restrict__ work, Vecs V, double rtol,
                                                                int maxit) {
     const Work w = work[blockIdx.x];
+    pdl_wait();
     SolveScalars* S = V.S + w.slot;
     const DevMesh& M = meshes[w.mesh];
     const double* b = V.bptr ? V.bptr[w.slot] : V.b + w.voff;
@@ -1576,6 +1746,7 @@ __global__ void __launch_bounds__(kBlock) pcg_init_pair_kernel(const DevMesh* __
         acc = fma(bi, bi, acc);
     }
     double val[1] = {acc}, tot[1];
+    pdl_trigger();   // the successor may launch during the reduction tail
     if (slot_sum<1>(val, V.partials + w.poff, w.idx, w.count, &S->ticket[1], tot) && threadIdx.x == 0) {
         S->bnorm2 = tot[0];
         S->tol2 = rtol * rtol * tot[0];
@@ -1621,6 +1792,7 @@ __global__ void __launch_bounds__(kBlock) pcg_first_dir_pair_kernel(const DevMes
     }
     float vh[1] = {h}, vl[1] = {l};
     double tot[1];
+    pdl_trigger();   // the successor may launch during the reduction tail
     if (slot_sum_pair<1>(vh, vl, V.partials + w.poff, w.idx, w.count, &S->ticket[1], tot) && threadIdx.x == 0) {
         S->rho = tot[0];
         if (!(tot[0] > 0.0) || !isfinite(tot[0])) {
@@ -1673,6 +1845,7 @@ __device__ __forceinline__ void pcg_update_xr_pair_item(const DevMesh* __restric
     for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) V.rr[w.roff + i] = 0.0;
     float vh[1] = {h}, vl[1] = {l};
     double tot[1];
+    pdl_trigger();   // the successor may launch during the reduction tail
     if (slot_sum_pair<1>(vh, vl, V.partials + w.poff, w.idx, w.count, &S->ticket[2], tot) && threadIdx.x == 0) {
         S->rr = tot[0];
         const int it = S->iters + 1;
@@ -1691,7 +1864,9 @@ __device__ __forceinline__ void pcg_update_xr_pair_item(const DevMesh* __restric
 }
 __global__ void __launch_bounds__(kBlock) pcg_update_xr_pair_kernel(const DevMesh* __restrict__ meshes,
                                                                     const Work* __restrict__ work, Vecs V) {
-    pcg_update_xr_pair_item(meshes, work[blockIdx.x], V);
+    const Work w_ = work[blockIdx.x];
+    pdl_wait();
+    pcg_update_xr_pair_item(meshes, w_, V);
 }
 
 // z.r and z.q; beta = -alpha (z.q) / rho, rho = z.r.
@@ -1724,6 +1899,7 @@ __device__ __forceinline__ void pcg_dots_pair_item(const DevMesh* __restrict__ m
     }
     float vh[2] = {rh, qh}, vl[2] = {rl, ql};
     double tot[2];
+    pdl_trigger();   // the successor may launch during the reduction tail
     if (slot_sum_pair<2>(vh, vl, V.partials + w.poff, w.idx, w.count, &S->ticket[3], tot) && threadIdx.x == 0) {
         S->zr = tot[0];
         S->zq = tot[1];
@@ -1739,7 +1915,9 @@ __device__ __forceinline__ void pcg_dots_pair_item(const DevMesh* __restrict__ m
 }
 __global__ void __launch_bounds__(kBlock) pcg_dots_pair_kernel(const DevMesh* __restrict__ meshes,
                                                                const Work* __restrict__ work, Vecs V) {
-    pcg_dots_pair_item(meshes, work[blockIdx.x], V);
+    const Work w_ = work[blockIdx.x];
+    pdl_wait();
+    pcg_dots_pair_item(meshes, w_, V);
 }
 
 // p = z + beta p, q = 0 for the next product.
@@ -1771,14 +1949,19 @@ __device__ __forceinline__ void pcg_update_p_pair_item(const DevMesh* __restrict
     }
 }
 __global__ void __launch_bounds__(kBlock) pcg_update_p_pair_kernel(const DevMesh* __restrict__ meshes,
-                                                                   const Work* __restrict__ work, Vecs V) {
-    pcg_update_p_pair_item(meshes, work[blockIdx.x], V);
+                                                                   const Work* __restrict__ work, Vecs V, int nslots,
+                                                                   cudaGraphConditionalHandle cond, int set_cond) {
+    if (set_cond && blockIdx.x == 0) loop_condition(V.S, nslots, cond);
+    const Work w_ = work[blockIdx.x];
+    pdl_wait();
+    pcg_update_p_pair_item(meshes, w_, V);
 }
 
 // x (float pair) -> float64 in place, before the final residual.
 __global__ void __launch_bounds__(kBlock) finalize_x_pair_kernel(const DevMesh* __restrict__ meshes,
                                                                  const Work* __restrict__ work, Vecs V) {
     const Work w = work[blockIdx.x];
+    pdl_wait();
     double* x = V.x + w.voff;
     CGS_VERT_LOOP(i) {
         const float2 t = as_pair(x)[i];
@@ -1786,19 +1969,6 @@ __global__ void __launch_bounds__(kBlock) finalize_x_pair_kernel(const DevMesh* 
     }
 }
 
-// Condition of the device-side loop (graph while node): continue while some
-// slot is still running and fewer than maxit + 2 bodies have run (slot 0
-// counts the bodies; all slots share maxit).
-__global__ void __launch_bounds__(kBlock) loop_cond_kernel(SolveScalars* __restrict__ S, int nslots,
-                                                           cudaGraphConditionalHandle cond) {
-    int running = 0;
-    for (int i = threadIdx.x; i < nslots; i += blockDim.x) running |= !*(volatile const int*)&S[i].done;
-    running = __syncthreads_or(running);
-    if (threadIdx.x == 0) {
-        const int loops = ++S[0].loops;
-        cudaGraphSetConditional(cond, (running && loops < S[0].maxit + 2) ? 1u : 0u);
-    }
-}
 
 // ---------------------------------------------------------------------------
 // Persistent PCG loop of the mixed forms: one cooperative launch runs whole
@@ -1876,6 +2046,7 @@ __global__ void __launch_bounds__(kBlock, 2) pcg_persistent_kernel(const DevMesh
         if (!__syncthreads_or(running)) return;
         // z = M r
         CGS_FOR_ITEMS(kWorkPack, k) local_lane_item<Stor>(meshes, T.w[kWorkPack][k], V, s, z, hybrid);
+        CGS_FOR_ITEMS(kWorkRowPack, k) local_rowpack_item<Stor>(meshes, T.w[kWorkRowPack][k], V, s, z, hybrid);
         CGS_FOR_ITEMS(kWorkSub, k) local_warp_item<float, Stor>(meshes, T.w[kWorkSub][k], V, s, z, hybrid);
         if (big_subs)
             CGS_FOR_ITEMS(kWorkSub, k) local_block_item<float, Stor>(meshes, T.w[kWorkSub][k], V, s, z, hybrid);
@@ -1909,6 +2080,7 @@ __global__ void __launch_bounds__(kBlock, 2) pcg_persistent_kernel(const DevMesh
 __global__ void __launch_bounds__(kBlock) resid_norm_kernel(const DevMesh* __restrict__ meshes,
                                                             const Work* __restrict__ work, Vecs V) {
     const Work w = work[blockIdx.x];
+    pdl_wait();
     SolveScalars* S = V.S + w.slot;
     const DevMesh& M = meshes[w.mesh];
     const double* b = V.bptr ? V.bptr[w.slot] : V.b + w.voff;
@@ -1924,6 +2096,7 @@ __global__ void __launch_bounds__(kBlock) resid_norm_kernel(const DevMesh* __res
         bn = fma(b[i], b[i], bn);
     }
     double val[2] = {rn, bn}, tot[2];
+    pdl_trigger();   // the successor may launch during the reduction tail
     if (slot_sum<2>(val, V.partials + w.poff, w.idx, w.count, &S->ticket[1], tot) && threadIdx.x == 0) {
         S->res2 = tot[0];
         S->b2 = tot[1];
@@ -1936,17 +2109,39 @@ __global__ void __launch_bounds__(kBlock) convert_kernel(const DevMesh* __restri
                                                          const Work* __restrict__ work, const Ta* __restrict__ a,
                                                          Tb* __restrict__ b, int mask_dirichlet) {
     const Work w = work[blockIdx.x];
+    pdl_wait();
     const DevMesh& M = meshes[w.mesh];
     CGS_VERT_LOOP(i) b[w.voff + i] = (mask_dirichlet && M.dir[i]) ? Tb(0) : (Tb)a[w.voff + i];
 }
 
 template <typename T>
 __global__ void __launch_bounds__(kBlock) fill_kernel(int64_t n, T* __restrict__ a, T v) {
+    pdl_wait();
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         a[i] = v;
 }
 
 }  // namespace
+
+// Launch `kern` with programmatic stream serialization when `pdl` is set
+// (the kernel may start while its predecessor in the stream runs; it waits in
+// pdl_wait before reading upstream data).  Empty grids launch nothing.
+template <typename... KArgs, typename... Args>
+void launch_pdl(bool pdl, void (*kern)(KArgs...), unsigned int grid, unsigned int block, size_t smem,
+                cudaStream_t st, Args... args) {
+    if (grid == 0) return;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = pdl ? 1 : 0;
+    cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
 
 // ---------------------------------------------------------------------------
 // Launchers.  A Plan names the mesh descriptors and the work tables of one
@@ -1957,9 +2152,11 @@ void launch_apply64(const Plan& P, const Vecs& V, const double* x, double* y, do
                     cudaStream_t st) {
     if (!P.nwork[kWorkElem]) return;
     if (dot)
-        apply64_kernel<true><<<P.nwork[kWorkElem], kBlock, 0, st>>>(P.meshes, P.work[kWorkElem], V, x, y, alpha);
+        launch_pdl(P.pdl, apply64_kernel<true>, P.nwork[kWorkElem], kBlock, 0, st, P.meshes, P.work[kWorkElem], V, x, y,
+                   alpha);
     else
-        apply64_kernel<false><<<P.nwork[kWorkElem], kBlock, 0, st>>>(P.meshes, P.work[kWorkElem], V, x, y, alpha);
+        launch_pdl(P.pdl, apply64_kernel<false>, P.nwork[kWorkElem], kBlock, 0, st, P.meshes, P.work[kWorkElem], V, x,
+                   y, alpha);
 }
 
 template <bool kTma>
@@ -1977,11 +2174,11 @@ void launch_apply_pair_tiled(const Plan& P, const Vecs& V, cudaStream_t st) {
         static bool attr = false;
         const int smem = verts + (int)(2 * kTileSlotBytes);
         set_smem_attr<true>((const void*)apply_pair_tiled_kernel<true>, smem, attr);
-        apply_pair_tiled_kernel<true><<<P.nwork[kWorkTile], kBlock, smem, st>>>(P.meshes, P.work[kWorkTile], V,
-                                                                                P.wait_limit);
+        launch_pdl(P.pdl, apply_pair_tiled_kernel<true>, P.nwork[kWorkTile], kBlock, smem, st, P.meshes,
+                   P.work[kWorkTile], V, P.wait_limit);
     } else {
-        apply_pair_tiled_kernel<false><<<P.nwork[kWorkTile], kBlock, verts, st>>>(P.meshes, P.work[kWorkTile], V,
-                                                                                 P.wait_limit);
+        launch_pdl(P.pdl, apply_pair_tiled_kernel<false>, P.nwork[kWorkTile], kBlock, verts, st, P.meshes,
+                   P.work[kWorkTile], V, P.wait_limit);
     }
 }
 
@@ -1992,26 +2189,38 @@ void launch_apply28f_tiled(const Plan& P, const Vecs& V, const float* x, float* 
         static bool attr = false;
         const int smem = verts + (int)kTileSlotBytes;
         set_smem_attr<true>((const void*)apply28f_tiled_kernel<true>, smem, attr);
-        apply28f_tiled_kernel<true><<<P.nwork[kWorkTile], kBlock, smem, st>>>(P.meshes, P.work[kWorkTile], V, x, y,
-                                                                              alpha, P.wait_limit);
+        launch_pdl(P.pdl, apply28f_tiled_kernel<true>, P.nwork[kWorkTile], kBlock, smem, st, P.meshes,
+                   P.work[kWorkTile], V, x, y, alpha, P.wait_limit);
     } else {
-        apply28f_tiled_kernel<false><<<P.nwork[kWorkTile], kBlock, verts, st>>>(P.meshes, P.work[kWorkTile], V, x,
-                                                                               y, alpha, P.wait_limit);
+        launch_pdl(P.pdl, apply28f_tiled_kernel<false>, P.nwork[kWorkTile], kBlock, verts, st, P.meshes,
+                   P.work[kWorkTile], V, x, y, alpha, P.wait_limit);
     }
 }
 
 void launch_local(const Plan& P, const Vecs& V, cgs_precision prec, const void* r, void* out, bool weighted,
                   cudaStream_t st) {
     const int wt = weighted ? 1 : 0;
-    // mixed forms: subdomains of at most kLaneMaxM dofs in lane packs
+    // mixed forms: subdomains of at most kLaneMaxM dofs in lane packs, or in
+    // row packs (small meshes)
+    if (prec != CGS_FP64 && P.nwork[kWorkRowPack]) {
+        const float* rf = static_cast<const float*>(r);
+        float* of = static_cast<float*>(out);
+        if (prec == CGS_FP32_BULK)
+            launch_pdl(P.pdl, local_rowpack_kernel<float>, P.nwork[kWorkRowPack], kBlock, 0, st, P.meshes,
+                       P.work[kWorkRowPack], V, rf, of, wt);
+        else
+            launch_pdl(P.pdl, local_rowpack_kernel<__half>, P.nwork[kWorkRowPack], kBlock, 0, st, P.meshes,
+                       P.work[kWorkRowPack], V, rf, of, wt);
+    }
     if (prec != CGS_FP64 && P.nwork[kWorkPack]) {
         const float* rf = static_cast<const float*>(r);
         float* of = static_cast<float*>(out);
         if (prec == CGS_FP32_BULK)
-            local_lane_kernel<float><<<P.nwork[kWorkPack], kBlock, 0, st>>>(P.meshes, P.work[kWorkPack], V, rf, of, wt);
+            launch_pdl(P.pdl, local_lane_kernel<float>, P.nwork[kWorkPack], kBlock, 0, st, P.meshes, P.work[kWorkPack],
+                       V, rf, of, wt);
         else
-            local_lane_kernel<__half><<<P.nwork[kWorkPack], kBlock, 0, st>>>(P.meshes, P.work[kWorkPack], V, rf, of,
-                                                                             wt);
+            launch_pdl(P.pdl, local_lane_kernel<__half>, P.nwork[kWorkPack], kBlock, 0, st, P.meshes, P.work[kWorkPack],
+                       V, rf, of, wt);
     }
     // the rest (every subdomain in the FP64 form): a warp per subdomain of
     // up to 64 dofs, a block per larger one
@@ -2020,23 +2229,23 @@ void launch_local(const Plan& P, const Vecs& V, cgs_precision prec, const void* 
     const Work* W = P.work[kWorkSub];
     // r is float64 in the FP64 form and the float copy of the residual otherwise
     if (prec == CGS_FP64) {
-        local_warp_kernel<double, double><<<n, kBlock, 0, st>>>(P.meshes, W, V, static_cast<const double*>(r),
-                                                                static_cast<double*>(out), wt);
+        launch_pdl(P.pdl, local_warp_kernel<double, double>, n, kBlock, 0, st, P.meshes, W, V,
+                   static_cast<const double*>(r), static_cast<double*>(out), wt);
         if (P.max_m > 64)
-            local_block_kernel<double, double><<<n, kBlock, 0, st>>>(P.meshes, W, V, static_cast<const double*>(r),
-                                                                     static_cast<double*>(out), wt);
+            launch_pdl(P.pdl, local_block_kernel<double, double>, n, kBlock, 0, st, P.meshes, W, V,
+                       static_cast<const double*>(r), static_cast<double*>(out), wt);
     } else if (prec == CGS_FP32_BULK) {
-        local_warp_kernel<float, float><<<n, kBlock, 0, st>>>(P.meshes, W, V, static_cast<const float*>(r),
-                                                              static_cast<float*>(out), wt);
+        launch_pdl(P.pdl, local_warp_kernel<float, float>, n, kBlock, 0, st, P.meshes, W, V,
+                   static_cast<const float*>(r), static_cast<float*>(out), wt);
         if (P.max_m > 64)
-            local_block_kernel<float, float><<<n, kBlock, 0, st>>>(P.meshes, W, V, static_cast<const float*>(r),
-                                                                   static_cast<float*>(out), wt);
+            launch_pdl(P.pdl, local_block_kernel<float, float>, n, kBlock, 0, st, P.meshes, W, V,
+                       static_cast<const float*>(r), static_cast<float*>(out), wt);
     } else {
-        local_warp_kernel<float, __half><<<n, kBlock, 0, st>>>(P.meshes, W, V, static_cast<const float*>(r),
-                                                               static_cast<float*>(out), wt);
+        launch_pdl(P.pdl, local_warp_kernel<float, __half>, n, kBlock, 0, st, P.meshes, W, V,
+                   static_cast<const float*>(r), static_cast<float*>(out), wt);
         if (P.max_m > 64)
-            local_block_kernel<float, __half><<<n, kBlock, 0, st>>>(P.meshes, W, V, static_cast<const float*>(r),
-                                                                    static_cast<float*>(out), wt);
+            launch_pdl(P.pdl, local_block_kernel<float, __half>, n, kBlock, 0, st, P.meshes, W, V,
+                       static_cast<const float*>(r), static_cast<float*>(out), wt);
     }
 }
 
@@ -2046,14 +2255,17 @@ void launch_restrict(const Plan& P, const Vecs& V, bool fp64, const void* s, boo
     const unsigned int n = P.nwork[kWorkBoxEnt];
     const Work* W = P.work[kWorkBoxEnt];
     if (fp64)
-        restrict_kernel<double, double, false><<<n, kBlock, 0, st>>>(P.meshes, W, V, static_cast<const double*>(s),
-                                                                     rr);
+        launch_pdl(P.pdl, restrict_kernel<double, double, false>, n, kBlock, 0, st, P.meshes, W, V,
+                   static_cast<const double*>(s), rr);
     else if (s_is_double)
-        restrict_kernel<float, double, false><<<n, kBlock, 0, st>>>(P.meshes, W, V, static_cast<const double*>(s), rr);
+        launch_pdl(P.pdl, restrict_kernel<float, double, false>, n, kBlock, 0, st, P.meshes, W, V,
+                   static_cast<const double*>(s), rr);
     else if (pair_out)
-        restrict_kernel<float, float, true><<<n, kBlock, 0, st>>>(P.meshes, W, V, static_cast<const float*>(s), rr);
+        launch_pdl(P.pdl, restrict_kernel<float, float, true>, n, kBlock, 0, st, P.meshes, W, V,
+                   static_cast<const float*>(s), rr);
     else
-        restrict_kernel<float, float, false><<<n, kBlock, 0, st>>>(P.meshes, W, V, static_cast<const float*>(s), rr);
+        launch_pdl(P.pdl, restrict_kernel<float, float, false>, n, kBlock, 0, st, P.meshes, W, V,
+                   static_cast<const float*>(s), rr);
 }
 
 void launch_interp_add(const Plan& P, const Vecs& V, bool fp64, const double* ur, const float* ur32, void* z,
@@ -2063,87 +2275,108 @@ void launch_interp_add(const Plan& P, const Vecs& V, bool fp64, const double* ur
     const Work* W = P.work[kWorkBox];
     if (fp64) {
         if (dots)
-            interp_add_kernel<double, double, 1><<<n, kBlock, 0, st>>>(P.meshes, W, V, ur, static_cast<double*>(z));
+            launch_pdl(P.pdl, interp_add_kernel<double, double, 1>, n, kBlock, 0, st, P.meshes, W, V, ur,
+                       static_cast<double*>(z));
         else
-            interp_add_kernel<double, double, 0><<<n, kBlock, 0, st>>>(P.meshes, W, V, ur, static_cast<double*>(z));
+            launch_pdl(P.pdl, interp_add_kernel<double, double, 0>, n, kBlock, 0, st, P.meshes, W, V, ur,
+                       static_cast<double*>(z));
     } else if (ur32) {   // float copy of u_r written by the reduced solve: no conversions per vertex
         if (dots)
-            interp_add_kernel<float, float, 2><<<n, kBlock, 0, st>>>(P.meshes, W, V, ur32, static_cast<float*>(z));
+            launch_pdl(P.pdl, interp_add_kernel<float, float, 2>, n, kBlock, 0, st, P.meshes, W, V, ur32,
+                       static_cast<float*>(z));
         else
-            interp_add_kernel<float, float, 0><<<n, kBlock, 0, st>>>(P.meshes, W, V, ur32, static_cast<float*>(z));
+            launch_pdl(P.pdl, interp_add_kernel<float, float, 0>, n, kBlock, 0, st, P.meshes, W, V, ur32,
+                       static_cast<float*>(z));
     } else {
-        interp_add_kernel<float, double, 0><<<n, kBlock, 0, st>>>(P.meshes, W, V, ur, static_cast<float*>(z));
+        launch_pdl(P.pdl, interp_add_kernel<float, double, 0>, n, kBlock, 0, st, P.meshes, W, V, ur,
+                   static_cast<float*>(z));
     }
 }
 
 void launch_coarse(const Plan& P, const Vecs& V, const double* rr, double* ur, float* ur32, cudaStream_t st) {
     if (!P.nwork[kWorkRow]) return;
-    coarse_gemv_kernel<<<P.nwork[kWorkRow], 32 * kRowChunk, 0, st>>>(P.meshes, P.work[kWorkRow], V, rr, ur, ur32);
+    launch_pdl(P.pdl, coarse_gemv_kernel, P.nwork[kWorkRow], 32 * kRowChunk, 0, st, P.meshes, P.work[kWorkRow], V, rr,
+               ur, ur32);
 }
+
 void launch_coarse_pair(const Plan& P, const Vecs& V, const float2* rr2, double* ur, float* ur32, cudaStream_t st) {
     if (!P.nwork[kWorkRow]) return;
-    coarse_pair_kernel<<<P.nwork[kWorkRow], 32 * kRowChunk, 0, st>>>(P.meshes, P.work[kWorkRow], V, rr2, ur,
-                                                                      ur32);
+    launch_pdl(P.pdl, coarse_pair_kernel, P.nwork[kWorkRow], 32 * kRowChunk, 0, st, P.meshes, P.work[kWorkRow], V, rr2,
+               ur, ur32);
 }
 
 #define CGS_VLAUNCH(kernel, ...) \
-    kernel<<<P.nwork[kWorkVert], kBlock, 0, st>>>(P.meshes, P.work[kWorkVert], V, ##__VA_ARGS__)
+    launch_pdl(P.pdl, kernel, P.nwork[kWorkVert], kBlock, 0, st, P.meshes, P.work[kWorkVert], V, ##__VA_ARGS__)
 void launch_pcg_init_pair(const Plan& P, const Vecs& V, double rtol, int maxit, cudaStream_t st) {
     CGS_VLAUNCH(pcg_init_pair_kernel, rtol, maxit);
 }
+
 void launch_precond_prep_pair(const Plan& P, const Vecs& V, cudaStream_t st) {
     CGS_VLAUNCH(precond_prep_pair_kernel);
 }
+
 void launch_pcg_first_dir_pair(const Plan& P, const Vecs& V, cudaStream_t st) {
     CGS_VLAUNCH(pcg_first_dir_pair_kernel);
 }
+
 void launch_pcg_update_xr_pair(const Plan& P, const Vecs& V, cudaStream_t st) {
     CGS_VLAUNCH(pcg_update_xr_pair_kernel);
 }
+
 void launch_pcg_dots_pair(const Plan& P, const Vecs& V, cudaStream_t st) { CGS_VLAUNCH(pcg_dots_pair_kernel); }
-void launch_pcg_update_p_pair(const Plan& P, const Vecs& V, cudaStream_t st) {
-    CGS_VLAUNCH(pcg_update_p_pair_kernel);
+void launch_pcg_update_p_pair(const Plan& P, const Vecs& V, const cudaGraphConditionalHandle* cond,
+                              cudaStream_t st) {
+    CGS_VLAUNCH(pcg_update_p_pair_kernel, P.nslots, cond ? *cond : 0, cond ? 1 : 0);
 }
+
 void launch_finalize_x_pair(const Plan& P, const Vecs& V, cudaStream_t st) { CGS_VLAUNCH(finalize_x_pair_kernel); }
 #undef CGS_VLAUNCH
 
 // float64 -> float pair over n entries (r_r of the single-step reduced solve)
 __global__ void split_pair_kernel(int64_t n, const double* __restrict__ a, float2* __restrict__ b) {
+    pdl_wait();
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         b[i] = split_pair(a[i]);
 }
+
 void launch_split_pair(int64_t n, const double* a, float2* b, cudaStream_t st) {
     if (n <= 0) return;
     const int blocks = (int)std::min<int64_t>((n + kBlock - 1) / kBlock, 1024);
-    split_pair_kernel<<<blocks, kBlock, 0, st>>>(n, a, b);
+    launch_pdl(true, split_pair_kernel, blocks, kBlock, 0, st, n, a, b);
 }
 
 template <typename Tq>
 void launch_pcg_init(const Plan& P, const Vecs& V, Tq* q, double rtol, int maxit, cudaStream_t st) {
-    pcg_init_kernel<Tq><<<P.nwork[kWorkVert], kBlock, 0, st>>>(P.meshes, P.work[kWorkVert], V, q, rtol, maxit);
+    launch_pdl(P.pdl, pcg_init_kernel<Tq>, P.nwork[kWorkVert], kBlock, 0, st, P.meshes, P.work[kWorkVert], V, q, rtol,
+               maxit);
 }
+
 template <typename Tz>
 void launch_precond_prep(const Plan& P, const Vecs& V, const double* r, cudaStream_t st) {
-    precond_prep_kernel<Tz><<<P.nwork[kWorkVert], kBlock, 0, st>>>(P.meshes, P.work[kWorkVert], V, r);
+    launch_pdl(P.pdl, precond_prep_kernel<Tz>, P.nwork[kWorkVert], kBlock, 0, st, P.meshes, P.work[kWorkVert], V, r);
 }
+
 template <typename Tz>
 void launch_pcg_first_dir(const Plan& P, const Vecs& V, cudaStream_t st) {
-    pcg_first_dir_kernel<Tz><<<P.nwork[kWorkVert], kBlock, 0, st>>>(P.meshes, P.work[kWorkVert], V);
+    launch_pdl(P.pdl, pcg_first_dir_kernel<Tz>, P.nwork[kWorkVert], kBlock, 0, st, P.meshes, P.work[kWorkVert], V);
 }
+
 template <typename Tz, typename Tq>
 void launch_pcg_update_xr(const Plan& P, const Vecs& V, const Tq* q, cudaStream_t st) {
-    pcg_update_xr_kernel<Tz, Tq><<<P.nwork[kWorkVert], kBlock, 0, st>>>(P.meshes, P.work[kWorkVert], V, q);
+    launch_pdl(P.pdl, pcg_update_xr_kernel<Tz, Tq>, P.nwork[kWorkVert], kBlock, 0, st, P.meshes, P.work[kWorkVert], V,
+               q);
 }
+
 template <typename Tz, typename Tq>
 void launch_pcg_dots(const Plan& P, const Vecs& V, const Tq* q, cudaStream_t st) {
-    pcg_dots_kernel<Tz, Tq><<<P.nwork[kWorkVert], kBlock, 0, st>>>(P.meshes, P.work[kWorkVert], V, q);
+    launch_pdl(P.pdl, pcg_dots_kernel<Tz, Tq>, P.nwork[kWorkVert], kBlock, 0, st, P.meshes, P.work[kWorkVert], V, q);
 }
+
 template <typename Tz, typename Tq>
-void launch_pcg_update_p(const Plan& P, const Vecs& V, Tq* q, cudaStream_t st) {
-    pcg_update_p_kernel<Tz, Tq><<<P.nwork[kWorkVert], kBlock, 0, st>>>(P.meshes, P.work[kWorkVert], V, q);
-}
-void launch_loop_cond(const Plan& P, const Vecs& V, cudaGraphConditionalHandle cond, cudaStream_t st) {
-    loop_cond_kernel<<<1, kBlock, 0, st>>>(V.S, P.nslots, cond);
+void launch_pcg_update_p(const Plan& P, const Vecs& V, Tq* q, const cudaGraphConditionalHandle* cond,
+                         cudaStream_t st) {
+    launch_pdl(P.pdl, pcg_update_p_kernel<Tz, Tq>, P.nwork[kWorkVert], kBlock, 0, st, P.meshes, P.work[kWorkVert], V, q,
+               P.nslots, cond ? *cond : 0, cond ? 1 : 0);
 }
 
 // Blocks of the persistent loop that fit on the device at once (the
@@ -2179,10 +2412,10 @@ cudaError_t launch_pcg_persistent(const Plan& P, const Vecs& V, cgs_precision pr
 }
 
 void launch_resid_norm(const Plan& P, const Vecs& V, cudaStream_t st) {
-    resid_norm_kernel<<<P.nwork[kWorkVert], kBlock, 0, st>>>(P.meshes, P.work[kWorkVert], V);
+    launch_pdl(P.pdl, resid_norm_kernel, P.nwork[kWorkVert], kBlock, 0, st, P.meshes, P.work[kWorkVert], V);
 }
 
-Schedule default_schedule(int64_t total_nv, int64_t total_sub, int64_t total_pack) {
+Schedule default_schedule(int64_t total_nv, int64_t total_sub, int64_t total_pack, int64_t total_lane_subs) {
     const int64_t target = 4 * 148;
     Schedule s;
     int64_t v = (total_nv + target - 1) / target;
@@ -2192,6 +2425,8 @@ Schedule default_schedule(int64_t total_nv, int64_t total_sub, int64_t total_pac
     int64_t k = (total_pack + target - 1) / target;
     s.pack_chunk = (int)std::min<int64_t>(32, std::max<int64_t>(8, (k + 7) / 8 * 8));
     s.box_chunk = (int)std::min<int64_t>(1024, std::max<int64_t>(256, (v + 255) / 256 * 256));
+    // four lanes per small subdomain only while one lane each leaves the GPU idle
+    s.row_packs = total_lane_subs < kRowPackMaxSubs ? 1 : 0;
     return s;
 }
 
@@ -2220,7 +2455,10 @@ void append_mesh_work(std::vector<Work> (&tabs)[kWorkKinds], int mesh, int slot,
     add(kWorkVert, z.nv, sch.vert_chunk);
     add(kWorkSub, z.n_sub, sch.sub_chunk);
     add(kWorkRow, z.nr, kRowChunk);
-    add(kWorkPack, z.n_pack, sch.pack_chunk);
+    if (sch.row_packs && z.n_rpack > 0)
+        add(kWorkRowPack, z.n_rpack, sch.pack_chunk);
+    else
+        add(kWorkPack, z.n_pack, sch.pack_chunk);
     add(kWorkBox, z.nvb, sch.box_chunk);
     if (z.nr > 0) add(kWorkBoxEnt, z.nrng, kBlock / 32);
 }
@@ -2235,30 +2473,38 @@ int64_t mesh_partial_slots(const MeshSizes& z, const Schedule& sch) {
 
 template void launch_pcg_update_xr<double, double>(const Plan&, const Vecs&, const double*, cudaStream_t);
 template void launch_pcg_dots<double, double>(const Plan&, const Vecs&, const double*, cudaStream_t);
-template void launch_pcg_update_p<double, double>(const Plan&, const Vecs&, double*, cudaStream_t);
+template void launch_pcg_update_p<double, double>(const Plan&, const Vecs&, double*,
+                                                  const cudaGraphConditionalHandle*, cudaStream_t);
 template void launch_pcg_init<double>(const Plan&, const Vecs&, double*, double, int, cudaStream_t);
 template void launch_precond_prep<double>(const Plan&, const Vecs&, const double*, cudaStream_t);
 template void launch_precond_prep<float>(const Plan&, const Vecs&, const double*, cudaStream_t);
 template void launch_pcg_first_dir<double>(const Plan&, const Vecs&, cudaStream_t);
 
 void launch_convert_f2d(const Plan& P, const float* a, double* b, bool mask, cudaStream_t st) {
-    convert_kernel<float, double><<<P.nwork[kWorkVert], kBlock, 0, st>>>(P.meshes, P.work[kWorkVert], a, b, mask);
+    launch_pdl(P.pdl, convert_kernel<float, double>, P.nwork[kWorkVert], kBlock, 0, st, P.meshes, P.work[kWorkVert], a,
+               b, mask);
 }
+
 void launch_convert_d2f(const Plan& P, const double* a, float* b, bool mask, cudaStream_t st) {
-    convert_kernel<double, float><<<P.nwork[kWorkVert], kBlock, 0, st>>>(P.meshes, P.work[kWorkVert], a, b, mask);
+    launch_pdl(P.pdl, convert_kernel<double, float>, P.nwork[kWorkVert], kBlock, 0, st, P.meshes, P.work[kWorkVert], a,
+               b, mask);
 }
+
 void launch_copy_d(const Plan& P, const double* a, double* b, bool mask, cudaStream_t st) {
-    convert_kernel<double, double><<<P.nwork[kWorkVert], kBlock, 0, st>>>(P.meshes, P.work[kWorkVert], a, b, mask);
+    launch_pdl(P.pdl, convert_kernel<double, double>, P.nwork[kWorkVert], kBlock, 0, st, P.meshes, P.work[kWorkVert], a,
+               b, mask);
 }
+
 void launch_fill_d(int64_t n, double* a, double v, cudaStream_t st) {
     if (n <= 0) return;
     const int64_t b = std::min<int64_t>((n + kBlock - 1) / kBlock, 148 * 8);
-    fill_kernel<double><<<(unsigned int)b, kBlock, 0, st>>>(n, a, v);
+    launch_pdl(true, fill_kernel<double>, (unsigned int)b, kBlock, 0, st, n, a, v);
 }
+
 void launch_fill_f(int64_t n, float* a, float v, cudaStream_t st) {
     if (n <= 0) return;
     const int64_t b = std::min<int64_t>((n + kBlock - 1) / kBlock, 148 * 8);
-    fill_kernel<float><<<(unsigned int)b, kBlock, 0, st>>>(n, a, v);
+    launch_pdl(true, fill_kernel<float>, (unsigned int)b, kBlock, 0, st, n, a, v);
 }
 
 }  // namespace cgs

@@ -33,7 +33,8 @@ void launch_precond_prep_pair(const Plan& P, const Vecs& V, cudaStream_t st);
 void launch_pcg_first_dir_pair(const Plan& P, const Vecs& V, cudaStream_t st);
 void launch_pcg_update_xr_pair(const Plan& P, const Vecs& V, cudaStream_t st);
 void launch_pcg_dots_pair(const Plan& P, const Vecs& V, cudaStream_t st);
-void launch_pcg_update_p_pair(const Plan& P, const Vecs& V, cudaStream_t st);
+void launch_pcg_update_p_pair(const Plan& P, const Vecs& V, const cudaGraphConditionalHandle* cond,
+                              cudaStream_t st);
 void launch_finalize_x_pair(const Plan& P, const Vecs& V, cudaStream_t st);
 
 template <typename Tq>
@@ -46,9 +47,11 @@ template <typename Tz, typename Tq>
 void launch_pcg_update_xr(const Plan& P, const Vecs& V, const Tq* q, cudaStream_t st);
 template <typename Tz, typename Tq>
 void launch_pcg_dots(const Plan& P, const Vecs& V, const Tq* q, cudaStream_t st);
+// p = z + beta p, q = 0; with cond, block 0 also sets the device-side loop
+// condition (the iteration's last kernel)
 template <typename Tz, typename Tq>
-void launch_pcg_update_p(const Plan& P, const Vecs& V, Tq* q, cudaStream_t st);
-void launch_loop_cond(const Plan& P, const Vecs& V, cudaGraphConditionalHandle cond, cudaStream_t st);
+void launch_pcg_update_p(const Plan& P, const Vecs& V, Tq* q, const cudaGraphConditionalHandle* cond,
+                         cudaStream_t st);
 // Persistent PCG loop of the mixed forms: up to max_iters iterations over
 // every slot of the plan in one cooperative launch of `blocks` blocks (at
 // most persistent_blocks(prec)); bar must be zero on entry.
@@ -65,7 +68,7 @@ void launch_fill_f(int64_t n, float* a, float v, cudaStream_t st);
 
 // Work tables of one mesh as slot `slot` (host side, appended to tabs).
 struct MeshSizes {
-    int64_t nv, ne, ntiles, n_sub, nr, n_pack, nvb, nrng;   // n_sub: warp-kernel subdomains
+    int64_t nv, ne, ntiles, n_sub, nr, n_pack, nvb, nrng, n_rpack;   // n_sub: warp-kernel subdomains
 };
 // Block sizes of the range-parallel kernels: vertices per block (vector
 // kernels) and subdomains per block (local solves), and how the tiled
@@ -79,10 +82,12 @@ struct Schedule {
     int tile_tma = 0;    // 1: element tiles of the mixed-form applies staged by TMA
     int persistent = -1; // mixed-form iterations in one persistent cooperative launch:
                          // 1 yes; 0 or -1 (default) no
+    int pdl = 1;         // programmatic stream serialization of the launches
+    int row_packs = 1;   // lane subdomains of meshes that have row packs solved 4 lanes each
 };
 // Default schedule: enough blocks to fill the GPU (about four per SM) for
 // `total` work of each kind, chunks within the kernels' ranges.
-Schedule default_schedule(int64_t total_nv, int64_t total_sub, int64_t total_pack);
+Schedule default_schedule(int64_t total_nv, int64_t total_sub, int64_t total_pack, int64_t total_lane_subs);
 void append_mesh_work(std::vector<Work> (&tabs)[kWorkKinds], int mesh, int slot, int64_t voff, int64_t roff,
                       int64_t poff, const MeshSizes& z, const Schedule& sch);
 int64_t mesh_partial_slots(const MeshSizes& z, const Schedule& sch);   // partial sums one slot needs

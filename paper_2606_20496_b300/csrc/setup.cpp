@@ -443,6 +443,52 @@ cgs_status host_setup(const double* xyz, int64_t nv, const int32_t* conn, int64_
             }
         }
     }
+    // row packs for small meshes: per size class, 8 subdomains per pack,
+    // lane 4 s + g holds rows g, g + 4, ... of subdomain s in full
+    S.rpack_m.clear();
+    S.rpack_idx_off.assign(1, 0);
+    S.rpack_inv_off.assign(1, 0);
+    S.rpack_idx.clear();
+    S.rpack_inv.clear();
+    int64_t n_lane_subs = 0;
+    for (int64_t p = 0; p < n_sub; ++p) n_lane_subs += in_lane(p) ? 1 : 0;
+    if (lane_packs && n_lane_subs > 0 && n_lane_subs < kRowPackMaxSubs) {
+        for (int c : kLaneClasses) {
+            std::vector<int64_t> members;
+            for (int64_t p = 0; p < n_sub; ++p)
+                if (in_lane(p) && lane_class((int)sub_sets[p].size()) == c) members.push_back(p);
+            const int per = 32 / kRowLanes, R = row_pack_rows(c), T = row_entries(c);
+            for (size_t b = 0; b < members.size(); b += per) {
+                S.rpack_m.push_back(c);
+                S.rpack_idx_off.push_back(S.rpack_idx_off.back() + (int64_t)32 * c);
+                S.rpack_inv_off.push_back(S.rpack_inv_off.back() + (int64_t)32 * T);
+                const int64_t io = S.rpack_idx_off[S.rpack_idx_off.size() - 2];
+                const int64_t ao = S.rpack_inv_off[S.rpack_inv_off.size() - 2];
+                S.rpack_idx.resize(S.rpack_idx_off.back(), -1);
+                S.rpack_inv.resize(S.rpack_inv_off.back(), 0.0);
+                for (int sidx = 0; sidx < per && b + sidx < members.size(); ++sidx) {
+                    const int64_t p = members[b + sidx];
+                    const std::vector<int32_t>& Rp = sub_sets[p];
+                    const std::vector<double>& tri = sub_inv[p];   // upper triangle, row-major
+                    const int m = (int)Rp.size();
+                    auto ainv = [&](int i, int j) {
+                        const int a = std::min(i, j), bb = std::max(i, j);
+                        return tri[(size_t)a * m - (size_t)a * (a - 1) / 2 + (bb - a)];
+                    };
+                    for (int g = 0; g < kRowLanes; ++g) {
+                        const int l = sidx * kRowLanes + g;
+                        for (int k = 0; k < m; ++k) S.rpack_idx[io + (int64_t)k * 32 + l] = Rp[k];
+                        int64_t e = 0;
+                        for (int r = 0; r < R; ++r)
+                            for (int j = 0; j < c; ++j, ++e) {
+                                const int i = r * kRowLanes + g;
+                                if (i < m && j < m) S.rpack_inv[ao + (int64_t)l * T + e] = ainv(i, j);
+                            }
+                    }
+                }
+            }
+        }
+    }
     sub_sets.clear();
     sub_inv.clear();
 

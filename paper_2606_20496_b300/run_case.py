@@ -44,7 +44,11 @@ def main():
     ap.add_argument("--tile-tma", type=int, choices=(0, 1), default=None,
                     help="force the element-tile loading of the mixed-form applies (default: setup's choice)")
     ap.add_argument("--persistent", type=int, choices=(-1, 0, 1), default=None,
-                    help="persistent loop: 1 on, 0 off, -1 auto (default: setup's choice)")
+                    help="persistent loop: 1 on, 0 or -1 off (default: setup's choice)")
+    ap.add_argument("--pdl", type=int, choices=(0, 1), default=None,
+                    help="programmatic dependent launch: 1 on, 0 off (default: setup's choice)")
+    ap.add_argument("--row-packs", type=int, choices=(0, 1), default=None,
+                    help="four lanes per small subdomain where the mesh has row packs: 1 on, 0 off")
     args = ap.parse_args()
     build.build()
     m, b = load_workload(args.workload)
@@ -54,11 +58,10 @@ def main():
     setup_s = time.perf_counter() - t0
     if args.tune:
         cgs.cgs_mesh_tune(h.handle)
-    if args.tile_tma is not None or args.persistent is not None:
-        i0 = cgs.cgs_mesh_info(h.handle)
-        cgs.cgs_mesh_set_schedule(h.handle, i0["vert_chunk"], i0["sub_chunk"],
-                                  i0["tile_tma"] if args.tile_tma is None else args.tile_tma,
-                                  -1 if args.persistent is None else args.persistent)
+    forced = {k: v for k, v in (("tile_tma", args.tile_tma), ("persistent", args.persistent), ("pdl", args.pdl),
+                                ("row_packs", args.row_packs)) if v is not None}
+    if forced:
+        cgs.cgs_mesh_set_schedule(h.handle, **forced)
     bd = torch.as_tensor(b, dtype=torch.float64, device="cuda")
     x = torch.empty_like(bd)
     if args.profile:
@@ -77,7 +80,7 @@ def main():
             raise SystemExit(f"solve failed: {cgs.status_string(st)}")
     info = cgs.cgs_mesh_info(h.handle)
     out = {"workload": args.workload, "prec": args.prec, "form": args.form, "nv": h.info["nv"],
-           "schedule": {k: info[k] for k in ("vert_chunk", "sub_chunk", "tile_tma", "persistent")},
+           "schedule": cgs.cgs_mesh_get_schedule(h.handle), "loop": info["loop"],
            "ne": h.info["ne"], "n_sub": h.info["n_sub"], "n_r": h.info["n_r"],
            "footprint_mb": h.info["footprint_bytes"] / 2 ** 20, "setup_s": setup_s, "iters": its,
            "relres": rels, "ms_per_solve": float(np.mean(ms[1:] if len(ms) > 1 else ms))}

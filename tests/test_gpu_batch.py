@@ -114,8 +114,9 @@ def test_autotuner_keeps_results(ctx, prec):
         x0 = torch.empty(m.nv, dtype=torch.float64, device="cuda")
         st, its0, _ = cgs.cgs_solve(h.handle, dev(b), x0, rtol=1e-10)
         cgs.cgs_mesh_tune(h.handle)
-        info = cgs.cgs_mesh_info(h.handle)
-        assert info["vert_chunk"] in (256, 512, 1024, 2048) and info["sub_chunk"] in (8, 16, 32, 64)
+        sch = cgs.cgs_mesh_get_schedule(h.handle)
+        assert sch["vert_chunk"] in (256, 512, 1024, 2048) and sch["sub_chunk"] in (8, 16, 32, 64)
+        assert sch["box_chunk"] in (256, 512, 1024) and sch["tile_tma"] in (0, 1)
         x1 = torch.empty_like(x0)
         st, its1, rel = cgs.cgs_solve(h.handle, dev(b), x1, rtol=1e-10)
         assert st == cgs.OK and abs(int(its1[0]) - int(its0[0])) <= 1

@@ -32,9 +32,8 @@ CASES = {
 
 
 def set_persistent(h, on):
-    i = cgs.cgs_mesh_info(h.handle)
-    cgs.cgs_mesh_set_schedule(h.handle, i["vert_chunk"], i["sub_chunk"], i["tile_tma"], 1 if on else 0)
-    assert cgs.cgs_mesh_info(h.handle)["persistent"] == (1 if on else 0)
+    cgs.cgs_mesh_set_schedule(h.handle, persistent=1 if on else 0)
+    assert cgs.cgs_mesh_info(h.handle)["loop"] == (2 if on else 1)
 
 
 @pytest.mark.parametrize("name", list(CASES))
@@ -97,3 +96,27 @@ def test_persistent_batch_and_server(ctx):
     finally:
         for h in hs:
             h.free()
+
+
+def test_schedule_round_trip_and_pdl_off(ctx):
+    """Every schedule field is settable, invalid values are refused, and
+    ordinary launches (pdl = 0) give the same solve as programmatic ones."""
+    m, b = meshes.workload_cube8()
+    with cgs.Mesh(ctx, m.xyz, m.conn, part=m.part, boxes=m.boxes, prec="fp32") as h:
+        x0 = torch.empty(m.nv, dtype=torch.float64, device="cuda")
+        x1 = torch.empty_like(x0)
+        st0, it0, _ = cgs.cgs_solve(h.handle, dev(b), x0, rtol=1e-10)
+        cgs.cgs_mesh_set_schedule(h.handle, vert_chunk=512, sub_chunk=16, pack_chunk=16, box_chunk=512, pdl=0)
+        sch = cgs.cgs_mesh_get_schedule(h.handle)
+        assert (sch["vert_chunk"], sch["sub_chunk"], sch["pack_chunk"], sch["box_chunk"], sch["pdl"]) == \
+            (512, 16, 16, 512, 0)
+        st1, it1, _ = cgs.cgs_solve(h.handle, dev(b), x1, rtol=1e-10)
+        assert st0 == st1 == cgs.OK and int(it0[0]) == int(it1[0])
+        assert np.array_equal(x0.cpu().numpy(), x1.cpu().numpy()) or \
+            np.linalg.norm(x0.cpu().numpy() - x1.cpu().numpy()) <= 1e-8 * np.linalg.norm(x0.cpu().numpy())
+        for bad in ({"vert_chunk": 300}, {"sub_chunk": 4}, {"pack_chunk": 7}, {"box_chunk": 100},
+                    {"tile_tma": 2}, {"persistent": 5}, {"pdl": -1}, {"row_packs": 3}):
+            with pytest.raises(cgs.CGSError) as ei:
+                cgs.cgs_mesh_set_schedule(h.handle, **bad)
+            assert ei.value.status == cgs.ERR_INVALID_ARG
+        assert cgs.cgs_mesh_get_schedule(h.handle)["pdl"] == 0
