@@ -83,6 +83,7 @@ typedef struct {
     int64_t n_r;           /* active box vertices (reduced-space unknowns, Sec. 4)    */
     int64_t max_sub_dofs;  /* largest m_p = |R_p|                                     */
     int64_t sum_sub_dofs;  /* sum_p m_p                                               */
+    int64_t sum_sub_tri;   /* sum_p m_p (m_p + 1) / 2: entries of the local inverses  */
     size_t footprint_bytes;/* device memory held by the mesh                          */
     double setup_seconds;  /* host wall time of cgs_mesh_setup                        */
     int64_t kernel_launches; /* CUDA kernels this mesh has launched so far           */

@@ -53,7 +53,7 @@ class Params(C.Structure):
 
 class MeshInfo(C.Structure):
     _fields_ = [("nv", C.c_int64), ("ne", C.c_int64), ("n_free", C.c_int64), ("n_sub", C.c_int64),
-                ("n_r", C.c_int64), ("max_sub_dofs", C.c_int64), ("sum_sub_dofs", C.c_int64),
+                ("n_r", C.c_int64), ("max_sub_dofs", C.c_int64), ("sum_sub_dofs", C.c_int64), ("sum_sub_tri", C.c_int64),
                 ("footprint_bytes", C.c_size_t), ("setup_seconds", C.c_double),
                 ("kernel_launches", C.c_int64), ("n_box_entries", C.c_int64), ("n_lane_packs", C.c_int64),
                 ("loop", C.c_int32)]

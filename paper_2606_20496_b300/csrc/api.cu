@@ -211,16 +211,17 @@ cgs_status finish(cudaStream_t st, bool sync) {
 }
 
 // z += J~ A_r^{-1} J~^T s  (s: the bulk copy of the residual or of r - A l)
-// z += J A_r^{-1} J^T s (r_r = 0 on entry).  dots: the interpolation also
-// forms the PCG dots z.r, z.q and beta.
-void box_correction(Engine& E, const Vecs& V, bool dots, cudaStream_t st) {
+// z += J A_r^{-1} J^T s (r_r = 0 on entry; restricted already when
+// `restricted`).  dots: the interpolation also forms the PCG dots z.r, z.q
+// and beta.
+void box_correction(Engine& E, const Vecs& V, bool dots, cudaStream_t st, bool restricted = false) {
     const Plan& P = E.P;
     if (E.f64) {
         K(CGS_K_RESTRICT, launch_restrict(P, V, true, V.s, true, V.rr, false, st));
         K(CGS_K_COARSE, launch_coarse(P, V, V.rr, V.ur, nullptr, st));
     } else {
         // r_r and the reduced product in float pairs, u_r rounded to float
-        K(CGS_K_RESTRICT, launch_restrict(P, V, false, V.s, false, V.rr, true, st));
+        if (!restricted) K(CGS_K_RESTRICT, launch_restrict(P, V, false, V.s, false, V.rr, true, st));
         K(CGS_K_COARSE, launch_coarse_pair(P, V, reinterpret_cast<const float2*>(V.rr), nullptr, V.ur32, st));
     }
     K(CGS_K_INTERP, launch_interp_add(P, V, E.f64, V.ur, E.f64 ? nullptr : V.ur32, V.z, dots, st));
@@ -240,6 +241,14 @@ bool precond_body(Engine& E, const Vecs& V, cudaStream_t st, bool dots = false) 
             K(CGS_K_APPLY_A32,
               launch_apply28f_tiled(P, V, static_cast<const float*>(V.z), static_cast<float*>(V.s), -1.0f, st));
     } else {
+        // the restriction of s fused with the local solves when every
+        // subdomain is in packs
+        if (!E.f64 && !P.nwork[kWorkSub] && P.any_nr && P.nwork[kWorkBoxEnt]) {
+            K(CGS_K_LOCAL, launch_local_restrict(P, V, E.prec, static_cast<const float*>(V.s),
+                                                 static_cast<float*>(V.z), V.rr, st));
+            box_correction(E, V, dots, st, true);
+            return dots;
+        }
         K(CGS_K_LOCAL, launch_local(P, V, E.prec, V.s, V.z, false, st));
     }
     if (!P.any_nr) return false;
@@ -923,6 +932,11 @@ cgs_status cgs_mesh_setup(cgs_ctx* ctx, const double* xyz, int64_t nv, const int
     m->info.n_r = hs.nr;
     m->info.max_sub_dofs = hs.max_m;
     m->info.sum_sub_dofs = hs.sum_m;
+    m->info.sum_sub_tri = 0;
+    for (size_t p = 0; p + 1 < m->sub_ptr_h.size(); ++p) {   // hs.sub_ptr was moved to the export copy
+        const int64_t mp = m->sub_ptr_h[p + 1] - m->sub_ptr_h[p];
+        m->info.sum_sub_tri += mp * (mp + 1) / 2;
+    }
     m->info.n_box_entries = (int64_t)hs.vb_cell.size();
     m->info.n_lane_packs = (int64_t)hs.pack_m.size();
     m->info.footprint_bytes = m->mem.bytes;

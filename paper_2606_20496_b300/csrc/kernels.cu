@@ -1391,6 +1391,27 @@ __global__ void __launch_bounds__(kBlock) interp_add_kernel(const DevMesh* __res
     interp_add_item<T, Tu, kDots>(meshes, w_, V, urv, zv);
 }
 
+// Additive form, mixed precision: the local solves and the restriction
+// r_r = J^T W s read the same s and are independent, so one launch does both
+// (the restriction fused with the local solve): blocks [0, nl) take
+// local-solve items (lane or row packs), the others restriction ranges.
+template <typename Stor>
+__global__ void __launch_bounds__(kBlock, 2) local_restrict_kernel(const DevMesh* __restrict__ meshes,
+                                                                   const Work* __restrict__ wl, unsigned int nl,
+                                                                   int row_packs, const Work* __restrict__ wr,
+                                                                   Vecs V, const float* __restrict__ s,
+                                                                   float* __restrict__ z, void* __restrict__ rr) {
+    const bool local = blockIdx.x < nl;
+    const Work w_ = local ? wl[blockIdx.x] : wr[blockIdx.x - nl];
+    pdl_wait();
+    if (!local)
+        restrict_item<float, float, true>(meshes, w_, V, s, rr);
+    else if (row_packs)
+        local_rowpack_item<Stor>(meshes, w_, V, s, z, 0);
+    else
+        local_lane_item<Stor>(meshes, w_, V, s, z, 0);
+}
+
 // u_r = A_r^{-1} r_r: one warp per row of the full symmetric inverse; also a
 // float copy of u_r for the float interpolation (no conversions per element).
 __device__ __forceinline__ void coarse_gemv_item(const DevMesh* __restrict__ meshes, const Work& w, Vecs V,
@@ -2247,6 +2268,23 @@ void launch_local(const Plan& P, const Vecs& V, cgs_precision prec, const void* 
             launch_pdl(P.pdl, local_block_kernel<float, __half>, n, kBlock, 0, st, P.meshes, W, V,
                        static_cast<const float*>(r), static_cast<float*>(out), wt);
     }
+}
+
+bool launch_local_restrict(const Plan& P, const Vecs& V, cgs_precision prec, const float* s, float* z, void* rr,
+                           cudaStream_t st) {
+    // only when every subdomain is in packs (no warp-list launch needed)
+    if (prec == CGS_FP64 || P.nwork[kWorkSub] || !P.any_nr || !P.nwork[kWorkBoxEnt]) return false;
+    const bool rowp = P.nwork[kWorkRowPack] > 0;
+    const unsigned int nl = rowp ? P.nwork[kWorkRowPack] : P.nwork[kWorkPack];
+    const Work* wl = rowp ? P.work[kWorkRowPack] : P.work[kWorkPack];
+    const unsigned int grid = nl + P.nwork[kWorkBoxEnt];
+    if (prec == CGS_FP32_BULK)
+        launch_pdl(P.pdl, local_restrict_kernel<float>, grid, kBlock, 0, st, P.meshes, wl, nl, rowp ? 1 : 0,
+                   P.work[kWorkBoxEnt], V, s, z, rr);
+    else
+        launch_pdl(P.pdl, local_restrict_kernel<__half>, grid, kBlock, 0, st, P.meshes, wl, nl, rowp ? 1 : 0,
+                   P.work[kWorkBoxEnt], V, s, z, rr);
+    return true;
 }
 
 void launch_restrict(const Plan& P, const Vecs& V, bool fp64, const void* s, bool s_is_double, void* rr,

@@ -16,6 +16,11 @@ void launch_apply_pair_tiled(const Plan& P, const Vecs& V, cudaStream_t st);
 void launch_apply28f_tiled(const Plan& P, const Vecs& V, const float* x, float* y, float alpha, cudaStream_t st);
 void launch_local(const Plan& P, const Vecs& V, cgs_precision prec, const void* r, void* out, bool weighted,
                   cudaStream_t st);
+// Additive form, mixed precision: z += local solves of s and r_r += J^T W s
+// (float pairs) in one launch; false (nothing launched) unless every
+// subdomain is in packs and there is a reduced space.
+bool launch_local_restrict(const Plan& P, const Vecs& V, cgs_precision prec, const float* s, float* z, void* rr,
+                           cudaStream_t st);
 // r_r += J^T W s.  pair_out: rr holds float pairs (mixed forms, float s)
 void launch_restrict(const Plan& P, const Vecs& V, bool fp64, const void* s, bool s_is_double, void* rr,
                      bool pair_out, cudaStream_t st);

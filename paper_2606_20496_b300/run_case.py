@@ -40,6 +40,8 @@ def main():
     ap.add_argument("--rtol", type=float, default=1e-8)
     ap.add_argument("--maxit", type=int, default=1000)
     ap.add_argument("--tune", action="store_true", help="run the schedule autotuner after setup")
+    ap.add_argument("--compare-fp64", action="store_true",
+                    help="also solve in the FP64 form and report the relative solution difference")
     ap.add_argument("--profile", action="store_true", help="per-kernel CUDA-event times (host-driven loop)")
     ap.add_argument("--tile-tma", type=int, choices=(0, 1), default=None,
                     help="force the element-tile loading of the mixed-form applies (default: setup's choice)")
@@ -82,10 +84,19 @@ def main():
     out = {"workload": args.workload, "prec": args.prec, "form": args.form, "nv": h.info["nv"],
            "schedule": cgs.cgs_mesh_get_schedule(h.handle), "loop": info["loop"],
            "ne": h.info["ne"], "n_sub": h.info["n_sub"], "n_r": h.info["n_r"],
+           "sum_sub_dofs": info["sum_sub_dofs"], "sum_sub_tri": info["sum_sub_tri"],
+           "n_box_entries": info["n_box_entries"],
            "footprint_mb": h.info["footprint_bytes"] / 2 ** 20, "setup_s": setup_s, "iters": its,
            "relres": rels, "ms_per_solve": float(np.mean(ms[1:] if len(ms) > 1 else ms))}
     if args.profile:
         out["profile"] = cgs.cgs_profile_read(h.handle)
+    if args.compare_fp64 and args.prec != "fp64":
+        with cgs.Mesh(ctx, m.xyz, m.conn, part=m.part, boxes=m.boxes, prec="fp64", form=args.form) as h64:
+            x64 = torch.empty_like(bd)
+            st, it, rel = cgs.cgs_solve(h64.handle, bd, x64, rtol=args.rtol, maxit=args.maxit)
+            torch.cuda.synchronize()
+            out["fp64"] = {"iters": int(it[0]), "relres": float(rel[0]),
+                           "rel_diff_x": float(torch.linalg.norm(x - x64) / torch.linalg.norm(x64))}
     print(json.dumps(out))
     h.free()
     cgs.cgs_destroy(ctx)
