@@ -136,18 +136,20 @@ def algorithmic_bytes(info, prec):
         }
     return {
         # q = A p: hi/lo off-diagonals and 16-bit local indices per element;
-        # p gathered and q written once per vertex
-        "apply_A64": E * (28 * 8 + 16) + nv * (8 + 8),
+        # p and z gathered (p = z + beta p on the fly), q written, once per vertex
+        "apply_A64": E * (28 * 8 + 16) + nv * (8 + sb + 8),
         # s -= A l: float off-diagonals and indices; l read, s read and written
         "apply_A32": E * (28 * 4 + 16) + nv * (4 + 2 * 4),
         # upper triangles, vertex ids, W_ov; r gathered, z read and written
         "local": packed * sl + sm * 4 + nv * (4 + sb + 2 * sb),
         # (vertex, cell, weight) entries; coordinates and s per vertex; r_r pairs
         "restrict": nb * 12 + nv * (16 + sb) + nr * 8,
-        # per-vertex lists, coordinates, z read and written, r and q pairs (dots)
-        "interp": nv * 8 + nb * 8 + nv * (16 + 2 * sb + 16) + nr * 4,
+        # per-vertex lists, coordinates, z read and written, r and q pairs
+        # read (dots), q cleared
+        "interp": nv * 8 + nb * 8 + nv * (16 + 2 * sb + 16 + 8) + nr * 4,
         "coarse": nr * nr * 8 + nr * 12,
-        "pcg_xr": nv * (8 * 6 + 2 * sb),
+        # p, q, x, r read; p, x, r written; z read and cleared; s written
+        "pcg_xr": nv * (8 * 7 + 3 * sb),
         "pcg_dots": nv * (sb + 16),
         "pcg_p": nv * (sb + 24),
     }
@@ -341,7 +343,7 @@ def run_ours(args):
     algo = algorithmic_bytes(info, "fp32")
     iters32 = int(np.median(its32))
     # the persistent loop runs every phase of every iteration in one launch
-    per_iter = ["apply_A64", "pcg_xr", "local", "apply_A32", "restrict", "coarse", "interp", "pcg_p"]
+    per_iter = ["apply_A64", "pcg_xr", "local", "apply_A32", "restrict", "coarse", "interp"]
     algo["loop"] = iters32 * sum(algo[k] for k in per_iter)
     total_ms = sum(t for t, n in prof.values())
     dom = max((k for k in prof if k in algo and prof[k][1]), key=lambda k: prof[k][0])
@@ -355,8 +357,8 @@ def run_ours(args):
                 "avg_launch_us": dom_ms * 1e3}
     if dom == "loop":
         roofline["note"] = (f"persistent loop: {iters32} iterations per launch, algorithmic bytes = iterations x "
-                            "(q = A p, x/r update, local solves, s -= A l, restriction, reduced solve, "
-                            "interpolation with the dots, p update)")
+                            "(q = A p, x/r/p update, local solves, s -= A l, restriction, reduced solve, "
+                            "interpolation with the dots)")
     shares = {k: {"share": round(t / total_ms, 4), "launches": n, "avg_us": round(1e3 * t / n, 2)}
               for k, (t, n) in prof.items() if n}
     # the same solves one launch per phase (per-phase attribution)

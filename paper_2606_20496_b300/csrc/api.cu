@@ -214,7 +214,8 @@ cgs_status finish(cudaStream_t st, bool sync) {
 // z += J A_r^{-1} J^T s (r_r = 0 on entry; restricted already when
 // `restricted`).  dots: the interpolation also forms the PCG dots z.r, z.q
 // and beta.
-void box_correction(Engine& E, const Vecs& V, bool dots, cudaStream_t st, bool restricted = false) {
+void box_correction(Engine& E, const Vecs& V, bool dots, cudaStream_t st, bool restricted = false,
+                    const cudaGraphConditionalHandle* cond = nullptr) {
     const Plan& P = E.P;
     if (E.f64) {
         K(CGS_K_RESTRICT, launch_restrict(P, V, true, V.s, true, V.rr, false, st));
@@ -224,13 +225,14 @@ void box_correction(Engine& E, const Vecs& V, bool dots, cudaStream_t st, bool r
         if (!restricted) K(CGS_K_RESTRICT, launch_restrict(P, V, false, V.s, false, V.rr, true, st));
         K(CGS_K_COARSE, launch_coarse_pair(P, V, reinterpret_cast<const float2*>(V.rr), nullptr, V.ur32, st));
     }
-    K(CGS_K_INTERP, launch_interp_add(P, V, E.f64, V.ur, E.f64 ? nullptr : V.ur32, V.z, dots, st));
+    K(CGS_K_INTERP, launch_interp_add(P, V, E.f64, V.ur, E.f64 ? nullptr : V.ur32, V.z, dots, cond, st));
 }
 
 // z (bulk) = M r, with z = 0, s = r (bulk) and r_r = 0 on entry.  dots: also
 // the PCG dots (fused into the interpolation when there is a reduced space);
 // returns whether they were formed.
-bool precond_body(Engine& E, const Vecs& V, cudaStream_t st, bool dots = false) {
+bool precond_body(Engine& E, const Vecs& V, cudaStream_t st, bool dots = false,
+                  const cudaGraphConditionalHandle* cond = nullptr) {
     const Plan& P = E.P;
     if (E.form == CGS_HYBRID) {
         K(CGS_K_LOCAL, launch_local(P, V, E.prec, V.s, V.z, true, st));
@@ -246,13 +248,13 @@ bool precond_body(Engine& E, const Vecs& V, cudaStream_t st, bool dots = false) 
         if (!E.f64 && !P.nwork[kWorkSub] && P.any_nr && P.nwork[kWorkBoxEnt]) {
             K(CGS_K_LOCAL, launch_local_restrict(P, V, E.prec, static_cast<const float*>(V.s),
                                                  static_cast<float*>(V.z), V.rr, st));
-            box_correction(E, V, dots, st, true);
+            box_correction(E, V, dots, st, true, cond);
             return dots;
         }
         K(CGS_K_LOCAL, launch_local(P, V, E.prec, V.s, V.z, false, st));
     }
     if (!P.any_nr) return false;
-    box_correction(E, V, dots, st);
+    box_correction(E, V, dots, st, false, cond);
     return dots;
 }
 
@@ -267,10 +269,12 @@ void pcg_iteration(Engine& E, cudaStream_t st, const cudaGraphConditionalHandle*
         if (!precond_body(E, V, st, true)) K(CGS_K_PCG_DOTS, (launch_pcg_dots<double, double>(P, V, V.q, st)));
         K(CGS_K_PCG_P, (launch_pcg_update_p<double, double>(P, V, V.q, cond, st)));
     } else {
+        // p = z + beta p is formed by the apply and stored by the x, r update;
+        // the interpolation (or the dots) closes the iteration and sets the
+        // loop condition
         K(CGS_K_APPLY_A64, launch_apply_pair_tiled(P, V, st));
         K(CGS_K_PCG_XR, launch_pcg_update_xr_pair(P, V, st));
-        if (!precond_body(E, V, st, true)) K(CGS_K_PCG_DOTS, launch_pcg_dots_pair(P, V, st));
-        K(CGS_K_PCG_P, launch_pcg_update_p_pair(P, V, cond, st));
+        if (!precond_body(E, V, st, true, cond)) K(CGS_K_PCG_DOTS, launch_pcg_dots_pair(P, V, cond, st));
     }
 }
 
@@ -556,7 +560,7 @@ cgs_status tune_engine(Engine& E, cudaStream_t st) {
             t.box_chunk = bc;
             if (set_schedule(E, t) != cudaSuccess) continue;
             const float ms = time_it([&]() {
-                launch_interp_add(E.P, V, E.f64, V.ur, E.f64 ? nullptr : V.ur32, V.z, false, st);
+                launch_interp_add(E.P, V, E.f64, V.ur, E.f64 ? nullptr : V.ur32, V.z, false, nullptr, st);
             });
             if (ms < best_box) {
                 best_box = ms;
@@ -1086,11 +1090,11 @@ cgs_status cgs_interp(cgs_mesh* m, const double* ur, double* z, void* stream) {
     const Vecs V = no_stop(E.V);
     if (m->fp64()) {
         K(CGS_K_OTHER, launch_fill_d(m->d.nv, static_cast<double*>(V.z), 0.0, st));
-        K(CGS_K_INTERP, launch_interp_add(E.P, V, true, ur, nullptr, V.z, false, st));
+        K(CGS_K_INTERP, launch_interp_add(E.P, V, true, ur, nullptr, V.z, false, nullptr, st));
         K(CGS_K_OTHER, launch_copy_d(E.P, static_cast<const double*>(V.z), z, true, st));
     } else {
         K(CGS_K_OTHER, launch_fill_f(m->d.nv, static_cast<float*>(V.z), 0.0f, st));
-        K(CGS_K_INTERP, launch_interp_add(E.P, V, false, ur, nullptr, V.z, false, st));
+        K(CGS_K_INTERP, launch_interp_add(E.P, V, false, ur, nullptr, V.z, false, nullptr, st));
         K(CGS_K_OTHER, launch_convert_f2d(E.P, static_cast<const float*>(V.z), z, true, st));
     }
     return finish(st, false);

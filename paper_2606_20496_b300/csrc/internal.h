@@ -68,7 +68,7 @@ struct HostSetup {
     std::vector<float> at_hi, at_lo;   // [ntiles][kOff/4][kTileElems][4] tile-major off-diagonals (float, remainder)
     std::vector<int32_t> cell_cols;    // ncell*8, active column of each cell corner or -1
     // per-vertex box lists (restriction and interpolation by vertex)
-    std::vector<int32_t> vb_vert;      // free vertices with elements, by first cell
+    std::vector<int32_t> vb_vert;      // free vertices with elements, in vertex order
     std::vector<int32_t> vb_ptr;       // +1, ranges in vb_cell / vb_w
     std::vector<int32_t> vb_cell;      // cells of the vertex's elements, ascending (packed coordinates)
     std::vector<double> vb_w;          // elements of the vertex in that cell / elements of the vertex

@@ -123,6 +123,22 @@ __device__ bool slot_publish(const double (&v)[NV], double* partials, int idx, i
     return true;
 }
 
+// Condition of the device-side loop (graph while node): continue while some
+// slot is still running and fewer than maxit + 2 bodies have run (slot 0
+// counts the bodies; all slots share maxit).  Evaluated by block 0 of the
+// iteration's last kernel (a slot that breaks down inside that kernel runs
+// one more, skipped, body).
+__device__ __forceinline__ void loop_condition(SolveScalars* __restrict__ S, int nslots,
+                                               cudaGraphConditionalHandle cond) {
+    int running = 0;
+    for (int i = threadIdx.x; i < nslots; i += blockDim.x) running |= !*(volatile const int*)&S[i].done;
+    running = __syncthreads_or(running);
+    if (threadIdx.x == 0) {
+        const int loops = ++S[0].loops;
+        cudaGraphSetConditional(cond, (running && loops < S[0].maxit + 2) ? 1u : 0u);
+    }
+}
+
 // Deterministic per-slot sum of float64 values.
 template <int NV>
 __device__ bool slot_sum(double (&v)[NV], double* partials, int idx, int count, unsigned int* ticket,
@@ -528,6 +544,8 @@ __device__ __forceinline__ void apply_pair_tiled_item(const DevMesh* __restrict_
     __shared__ uint64_t bar;
     CGS_ITEM_PROLOGUE();
     const float2* p2 = V.p2 + w.voff;
+    const float* zf = static_cast<const float*>(V.z) + w.voff;
+    const float2 beta2 = S ? S->beta2 : make_float2(0.0f, 0.0f);
     float2* q2 = V.q2 + w.voff;
     const int t = w.begin;
     const float4* ghi = reinterpret_cast<const float4*>(M.at_hi) + (size_t)t * kGroups * kTileElems;
@@ -552,11 +570,24 @@ __device__ __forceinline__ void apply_pair_tiled_item(const DevMesh* __restrict_
     {
         uint32_t raw[kVertsPerThread];
         tile_vertex_ids(M, v0, nvt, raw);
+        // every gather load is issued before the arithmetic and the shared
+        // stores, so that the loads of one thread overlap
+        float2 pg[kVertsPerThread];
+        float zg[kVertsPerThread];
+#pragma unroll
+        for (int k = 0; k < kVertsPerThread; ++k) {
+            const int i = (int)threadIdx.x + k * kBlock;
+            const int v = (int)(raw[k] & ~kSharedBit);
+            pg[k] = i < nvt ? __ldg(&p2[v]) : make_float2(0.0f, 0.0f);
+            zg[k] = (S && i < nvt) ? __ldg(&zf[v]) : 0.0f;
+        }
 #pragma unroll
         for (int k = 0; k < kVertsPerThread; ++k) {
             const int i = (int)threadIdx.x + k * kBlock;
             if (i < nvt) {
-                ps[i] = __ldg(&p2[raw[k] & ~kSharedBit]);
+                // this iteration's direction p = z + beta p, formed on the fly
+                // (the x, r update stores it)
+                ps[i] = S ? pr_fma(beta2, pg[k], make_float2(zg[k], 0.0f)) : pg[k];
                 ys[i] = make_float2(0.0f, 0.0f);
             }
         }
@@ -722,7 +753,7 @@ __device__ __forceinline__ void apply28f_tiled_item(const DevMesh* __restrict__ 
 }
 
 template <bool kTma>
-__global__ void __launch_bounds__(kBlock, kTma ? 4 : 5) apply28f_tiled_kernel(const DevMesh* __restrict__ meshes,
+__global__ void __launch_bounds__(kBlock, 4) apply28f_tiled_kernel(const DevMesh* __restrict__ meshes,
                                                                                const Work* __restrict__ work, Vecs V,
                                                                                const float* __restrict__ xin,
                                                                                float* __restrict__ yout, float alpha,
@@ -1254,18 +1285,18 @@ __device__ __forceinline__ void restrict_item(const DevMesh* __restrict__ meshes
     T acc[8];
 #pragma unroll
     for (int m = 0; m < 8; ++m) acc[m] = T(0);
-    for (int i0 = rg.x + lane; i0 < rg.y; i0 += 64) {
-        // two entries per lane and round, their loads first
-        int v[2];
-        T f[2];
+    for (int i0 = rg.x + lane; i0 < rg.y; i0 += 128) {
+        // four entries per lane and round, their loads first
+        int v[4];
+        T f[4];
 #pragma unroll
-        for (int k = 0; k < 2; ++k) {
+        for (int k = 0; k < 4; ++k) {
             const int i = i0 + 32 * k;
             v[k] = i < rg.y ? __ldg(&M.re_vert[i]) : -1;
             f[k] = i < rg.y ? __ldg(&rw[i]) : T(0);
         }
 #pragma unroll
-        for (int k = 0; k < 2; ++k) {
+        for (int k = 0; k < 4; ++k) {
             if (v[k] < 0) continue;
             T x, y, z, ic;
             vx.load(v[k], x, y, z, ic);
@@ -1311,7 +1342,13 @@ __device__ __forceinline__ void interp_add_item(const DevMesh* __restrict__ mesh
     const BoxGrid<T> g(M);
     const auto vx = vertex_data(M, T(0));
     const T* bw = box_w(M, T(0));
-    // four vertices per thread and round, their list heads loaded first
+    const float2* __restrict__ r2 = reinterpret_cast<const float2*>(V.r) + w.voff;
+    float2* __restrict__ q2 = V.q2 + w.voff;
+    const double* __restrict__ r64 = V.r + w.voff;
+    const double* __restrict__ q64 = V.q + w.voff;
+    // four vertices per thread and round: the list heads and every vertex
+    // operand are loaded first, the four sums formed next and all stores
+    // issued last, so that no store sits between a round's loads
     for (int64_t i0 = (int64_t)w.begin + threadIdx.x; i0 < w.end; i0 += 4 * (int64_t)blockDim.x) {
         int v[4], e0[4], e1[4];
 #pragma unroll
@@ -1325,34 +1362,54 @@ __device__ __forceinline__ void interp_add_item(const DevMesh* __restrict__ mesh
                 e1[k] = __ldg(&M.vb_ptr[i + 1]);
             }
         }
+        T zo[4];
+        float2 rk[4], qk[4];
+        double rd[4], qd[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const bool ok = v[k] >= 0;
+            zo[k] = ok ? z[v[k]] : T(0);
+            if (kDots == 2) {
+                rk[k] = ok ? r2[v[k]] : make_float2(0.0f, 0.0f);
+                qk[k] = ok ? q2[v[k]] : make_float2(0.0f, 0.0f);
+            } else if (kDots == 1) {
+                rd[k] = ok ? r64[v[k]] : 0.0;
+                qd[k] = ok ? q64[v[k]] : 0.0;
+            }
+        }
+        T val[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            val[k] = T(0);
+            if (v[k] < 0 || M.nr <= 0) continue;
+            T x, y, zz, ic;
+            vx.load(v[k], x, y, zz, ic);
+            for (int e = e0[k]; e < e1[k]; ++e) {
+                T wt[8];
+                const int c = cell_weights(g, __ldg(&M.vb_cell[e]), x, y, zz, wt);
+                // the cell's 8 active columns in two 16-byte loads
+                const int4 ca = __ldg(reinterpret_cast<const int4*>(M.cell_cols) + 2 * (size_t)c);
+                const int4 cb = __ldg(reinterpret_cast<const int4*>(M.cell_cols) + 2 * (size_t)c + 1);
+                const int col[8] = {ca.x, ca.y, ca.z, ca.w, cb.x, cb.y, cb.z, cb.w};
+                T sum = T(0);
+#pragma unroll
+                for (int m = 0; m < 8; ++m) sum += wt[m] * (col[m] >= 0 ? (T)__ldg(&ur[col[m]]) : T(0));
+                val[k] += __ldg(&bw[e]) * sum;
+            }
+        }
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             if (v[k] < 0) continue;
-            T x, y, zz, ic;
-            vx.load(v[k], x, y, zz, ic);
-            T val = T(0);
-            if (M.nr > 0) {
-                for (int e = e0[k]; e < e1[k]; ++e) {
-                    T wt[8];
-                    const int c = cell_weights(g, __ldg(&M.vb_cell[e]), x, y, zz, wt);
-                    T sum = T(0);
-#pragma unroll
-                    for (int m = 0; m < 8; ++m) {
-                        const int col = __ldg(&M.cell_cols[(size_t)c * 8 + m]);
-                        sum += wt[m] * (col >= 0 ? (T)__ldg(&ur[col]) : T(0));
-                    }
-                    val += __ldg(&bw[e]) * sum;
-                }
-            }
-            const T zi = z[v[k]] + val;
+            const T zi = zo[k] + val[k];
             z[v[k]] = zi;
             if (kDots == 1) {
-                zr = fma((double)zi, V.r[w.voff + v[k]], zr);
-                zq = fma((double)zi, V.q[w.voff + v[k]], zq);
+                zr = fma((double)zi, rd[k], zr);
+                zq = fma((double)zi, qd[k], zq);
             } else if (kDots == 2) {
                 const float2 z2 = make_float2((float)zi, 0.0f);
-                pr_dot_acc(rh, rl, z2, reinterpret_cast<const float2*>(V.r)[w.voff + v[k]]);
-                pr_dot_acc(qh, ql, z2, V.q2[w.voff + v[k]]);
+                pr_dot_acc(rh, rl, z2, rk[k]);
+                pr_dot_acc(qh, ql, z2, qk[k]);
+                q2[v[k]] = make_float2(0.0f, 0.0f);   // q = 0 for the next product
             }
         }
     }
@@ -1382,12 +1439,16 @@ __device__ __forceinline__ void interp_add_item(const DevMesh* __restrict__ mesh
     }
 }
 
+// three blocks per SM for the float forms, two for float64 (no spills)
 template <typename T, typename Tu, int kDots>
-__global__ void __launch_bounds__(kBlock) interp_add_kernel(const DevMesh* __restrict__ meshes,
+__global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 3 : 2) interp_add_kernel(const DevMesh* __restrict__ meshes,
                                                             const Work* __restrict__ work, Vecs V,
-                                                            const Tu* __restrict__ urv, T* __restrict__ zv) {
+                                                            const Tu* __restrict__ urv, T* __restrict__ zv,
+                                                            int nslots, cudaGraphConditionalHandle cond,
+                                                            int set_cond) {
     const Work w_ = work[blockIdx.x];
     pdl_wait();
+    if (set_cond && blockIdx.x == 0) loop_condition(V.S, nslots, cond);
     interp_add_item<T, Tu, kDots>(meshes, w_, V, urv, zv);
 }
 
@@ -1710,20 +1771,6 @@ __device__ __forceinline__ void pcg_update_p_item(const DevMesh* __restrict__ me
     }
 }
 
-// Condition of the device-side loop (graph while node): continue while some
-// slot is still running and fewer than maxit + 2 bodies have run (slot 0
-// counts the bodies; all slots share maxit).  Evaluated by block 0 of the
-// iteration's last kernel, once every slot's stopping flag is final.
-__device__ __forceinline__ void loop_condition(SolveScalars* __restrict__ S, int nslots,
-                                               cudaGraphConditionalHandle cond) {
-    int running = 0;
-    for (int i = threadIdx.x; i < nslots; i += blockDim.x) running |= !*(volatile const int*)&S[i].done;
-    running = __syncthreads_or(running);
-    if (threadIdx.x == 0) {
-        const int loops = ++S[0].loops;
-        cudaGraphSetConditional(cond, (running && loops < S[0].maxit + 2) ? 1u : 0u);
-    }
-}
 
 template <typename Tz, typename Tq>
 __global__ void __launch_bounds__(kBlock) pcg_update_p_kernel(const DevMesh* __restrict__ meshes,
@@ -1816,6 +1863,8 @@ __global__ void __launch_bounds__(kBlock) pcg_first_dir_pair_kernel(const DevMes
     pdl_trigger();   // the successor may launch during the reduction tail
     if (slot_sum_pair<1>(vh, vl, V.partials + w.poff, w.idx, w.count, &S->ticket[1], tot) && threadIdx.x == 0) {
         S->rho = tot[0];
+        S->beta = 0.0;   // the first iteration's direction z + beta p is z
+        S->beta2 = make_float2(0.0f, 0.0f);
         if (!(tot[0] > 0.0) || !isfinite(tot[0])) {
             S->status = CGS_ERR_BREAKDOWN;
             S->done = 1;
@@ -1829,20 +1878,22 @@ __device__ __forceinline__ void pcg_update_xr_pair_item(const DevMesh* __restric
     CGS_ITEM_PROLOGUE();
     float2* __restrict__ x = as_pair(V.x) + w.voff;
     float2* __restrict__ r = as_pair(V.r) + w.voff;
-    const float2* __restrict__ p = V.p2 + w.voff;
+    float2* __restrict__ p = V.p2 + w.voff;
     const float2* __restrict__ q = V.q2 + w.voff;
     float* __restrict__ z = static_cast<float*>(V.z) + w.voff;
     float* __restrict__ s = static_cast<float*>(V.s) + w.voff;
-    const float2 a = S->alpha2, na = make_float2(-a.x, -a.y);
+    const float2 a = S->alpha2, na = make_float2(-a.x, -a.y), beta = S->beta2;
     float h = 0.0f, l = 0.0f;
     for (int64_t i0 = (int64_t)w.begin + threadIdx.x; i0 < w.end; i0 += 2 * (int64_t)blockDim.x) {
         // the loads of two vertices are issued before their arithmetic
         float2 pi[2], qi[2], xi[2], ri[2];
+        float zi[2];
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
             const int64_t i = i0 + k * (int64_t)blockDim.x;
             if (i < w.end) {
                 pi[k] = p[i];
+                zi[k] = z[i];
                 qi[k] = q[i];
                 xi[k] = x[i];
                 ri[k] = r[i];
@@ -1852,7 +1903,10 @@ __device__ __forceinline__ void pcg_update_xr_pair_item(const DevMesh* __restric
         for (int k = 0; k < 2; ++k) {
             const int64_t i = i0 + k * (int64_t)blockDim.x;
             if (i < w.end) {
-                x[i] = pr_fma(a, pi[k], xi[k]);
+                // p = z + beta p: the same arithmetic as the operator apply's
+                const float2 pn = pr_fma(beta, pi[k], make_float2(zi[k], 0.0f));
+                p[i] = pn;
+                x[i] = pr_fma(a, pn, xi[k]);
                 const float2 rn = pr_fma(na, qi[k], ri[k]);
                 r[i] = rn;
                 pr_dot_acc(h, l, rn, rn);
@@ -1883,7 +1937,7 @@ __device__ __forceinline__ void pcg_update_xr_pair_item(const DevMesh* __restric
         }
     }
 }
-__global__ void __launch_bounds__(kBlock) pcg_update_xr_pair_kernel(const DevMesh* __restrict__ meshes,
+__global__ void __launch_bounds__(kBlock, 4) pcg_update_xr_pair_kernel(const DevMesh* __restrict__ meshes,
                                                                     const Work* __restrict__ work, Vecs V) {
     const Work w_ = work[blockIdx.x];
     pdl_wait();
@@ -1895,7 +1949,7 @@ __device__ __forceinline__ void pcg_dots_pair_item(const DevMesh* __restrict__ m
     CGS_ITEM_PROLOGUE();
     const float* __restrict__ z = static_cast<const float*>(V.z) + w.voff;
     const float2* __restrict__ r = as_pair(V.r) + w.voff;
-    const float2* __restrict__ q = V.q2 + w.voff;
+    float2* __restrict__ q = V.q2 + w.voff;
     float rh = 0.0f, rl = 0.0f, qh = 0.0f, ql = 0.0f;
     CGS_VERT_LOOP4(i0) {
         float zi[4];
@@ -1909,6 +1963,7 @@ __device__ __forceinline__ void pcg_dots_pair_item(const DevMesh* __restrict__ m
                 zi[k] = z[i];
                 ri[k] = r[i];
                 qi[k] = q[i];
+                q[i] = make_float2(0.0f, 0.0f);   // q = 0 for the next product
             }
         }
 #pragma unroll
@@ -1935,48 +1990,14 @@ __device__ __forceinline__ void pcg_dots_pair_item(const DevMesh* __restrict__ m
     }
 }
 __global__ void __launch_bounds__(kBlock) pcg_dots_pair_kernel(const DevMesh* __restrict__ meshes,
-                                                               const Work* __restrict__ work, Vecs V) {
+                                                               const Work* __restrict__ work, Vecs V, int nslots,
+                                                               cudaGraphConditionalHandle cond, int set_cond) {
     const Work w_ = work[blockIdx.x];
     pdl_wait();
+    if (set_cond && blockIdx.x == 0) loop_condition(V.S, nslots, cond);
     pcg_dots_pair_item(meshes, w_, V);
 }
 
-// p = z + beta p, q = 0 for the next product.
-__device__ __forceinline__ void pcg_update_p_pair_item(const DevMesh* __restrict__ meshes, const Work& w, Vecs V) {
-    CGS_ITEM_PROLOGUE();
-    const float* __restrict__ z = static_cast<const float*>(V.z) + w.voff;
-    float2* __restrict__ p = V.p2 + w.voff;
-    float2* __restrict__ q = V.q2 + w.voff;
-    const float2 beta = S->beta2;
-    CGS_VERT_LOOP4(i0) {
-        float zi[4];
-        float2 pi[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const int64_t i = i0 + k * (int64_t)blockDim.x;
-            if (i < w.end) {
-                zi[k] = z[i];
-                pi[k] = p[i];
-            }
-        }
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const int64_t i = i0 + k * (int64_t)blockDim.x;
-            if (i < w.end) {
-                p[i] = pr_fma(beta, pi[k], make_float2(zi[k], 0.0f));
-                q[i] = make_float2(0.0f, 0.0f);
-            }
-        }
-    }
-}
-__global__ void __launch_bounds__(kBlock) pcg_update_p_pair_kernel(const DevMesh* __restrict__ meshes,
-                                                                   const Work* __restrict__ work, Vecs V, int nslots,
-                                                                   cudaGraphConditionalHandle cond, int set_cond) {
-    if (set_cond && blockIdx.x == 0) loop_condition(V.S, nslots, cond);
-    const Work w_ = work[blockIdx.x];
-    pdl_wait();
-    pcg_update_p_pair_item(meshes, w_, V);
-}
 
 // x (float pair) -> float64 in place, before the final residual.
 __global__ void __launch_bounds__(kBlock) finalize_x_pair_kernel(const DevMesh* __restrict__ meshes,
@@ -2089,9 +2110,8 @@ __global__ void __launch_bounds__(kBlock, 2) pcg_persistent_kernel(const DevMesh
             CGS_FOR_ITEMS(kWorkVert, k) pcg_dots_pair_item(meshes, T.w[kWorkVert][k], V);
         }
         CGS_SYNC_OR_LEAVE();
-        // p = z + beta p, q = 0
-        CGS_FOR_ITEMS(kWorkVert, k) pcg_update_p_pair_item(meshes, T.w[kWorkVert][k], V);
-        CGS_SYNC_OR_LEAVE();
+        // (p = z + beta p is formed by the next operator apply and stored by
+        // the next x, r update)
     }
 }
 #undef CGS_FOR_ITEMS
@@ -2307,27 +2327,29 @@ void launch_restrict(const Plan& P, const Vecs& V, bool fp64, const void* s, boo
 }
 
 void launch_interp_add(const Plan& P, const Vecs& V, bool fp64, const double* ur, const float* ur32, void* z,
-                       bool dots, cudaStream_t st) {
+                       bool dots, const cudaGraphConditionalHandle* cond, cudaStream_t st) {
     if (!P.nwork[kWorkBox] || !P.any_nr) return;
     const unsigned int n = P.nwork[kWorkBox];
     const Work* W = P.work[kWorkBox];
+    const cudaGraphConditionalHandle h = cond ? *cond : 0;
+    const int sc = cond ? 1 : 0;
     if (fp64) {
         if (dots)
             launch_pdl(P.pdl, interp_add_kernel<double, double, 1>, n, kBlock, 0, st, P.meshes, W, V, ur,
-                       static_cast<double*>(z));
+                       static_cast<double*>(z), P.nslots, h, sc);
         else
             launch_pdl(P.pdl, interp_add_kernel<double, double, 0>, n, kBlock, 0, st, P.meshes, W, V, ur,
-                       static_cast<double*>(z));
+                       static_cast<double*>(z), P.nslots, h, sc);
     } else if (ur32) {   // float copy of u_r written by the reduced solve: no conversions per vertex
         if (dots)
             launch_pdl(P.pdl, interp_add_kernel<float, float, 2>, n, kBlock, 0, st, P.meshes, W, V, ur32,
-                       static_cast<float*>(z));
+                       static_cast<float*>(z), P.nslots, h, sc);
         else
             launch_pdl(P.pdl, interp_add_kernel<float, float, 0>, n, kBlock, 0, st, P.meshes, W, V, ur32,
-                       static_cast<float*>(z));
+                       static_cast<float*>(z), P.nslots, h, sc);
     } else {
         launch_pdl(P.pdl, interp_add_kernel<float, double, 0>, n, kBlock, 0, st, P.meshes, W, V, ur,
-                   static_cast<float*>(z));
+                   static_cast<float*>(z), P.nslots, h, sc);
     }
 }
 
@@ -2361,10 +2383,8 @@ void launch_pcg_update_xr_pair(const Plan& P, const Vecs& V, cudaStream_t st) {
     CGS_VLAUNCH(pcg_update_xr_pair_kernel);
 }
 
-void launch_pcg_dots_pair(const Plan& P, const Vecs& V, cudaStream_t st) { CGS_VLAUNCH(pcg_dots_pair_kernel); }
-void launch_pcg_update_p_pair(const Plan& P, const Vecs& V, const cudaGraphConditionalHandle* cond,
-                              cudaStream_t st) {
-    CGS_VLAUNCH(pcg_update_p_pair_kernel, P.nslots, cond ? *cond : 0, cond ? 1 : 0);
+void launch_pcg_dots_pair(const Plan& P, const Vecs& V, const cudaGraphConditionalHandle* cond, cudaStream_t st) {
+    CGS_VLAUNCH(pcg_dots_pair_kernel, P.nslots, cond ? *cond : 0, cond ? 1 : 0);
 }
 
 void launch_finalize_x_pair(const Plan& P, const Vecs& V, cudaStream_t st) { CGS_VLAUNCH(finalize_x_pair_kernel); }

@@ -25,9 +25,10 @@ bool launch_local_restrict(const Plan& P, const Vecs& V, cgs_precision prec, con
 void launch_restrict(const Plan& P, const Vecs& V, bool fp64, const void* s, bool s_is_double, void* rr,
                      bool pair_out, cudaStream_t st);
 // z += W Q^T J_L u_r.  dots: also z.r and z.q with beta and rho (fused PCG
-// dots; r and q of the engine's slots)
+// dots; r and q of the engine's slots; mixed forms then zero q).  cond:
+// block 0 also sets the device-side loop condition.
 void launch_interp_add(const Plan& P, const Vecs& V, bool fp64, const double* ur, const float* ur32, void* z,
-                       bool dots, cudaStream_t st);
+                       bool dots, const cudaGraphConditionalHandle* cond, cudaStream_t st);
 void launch_coarse(const Plan& P, const Vecs& V, const double* rr, double* ur, float* ur32, cudaStream_t st);
 void launch_coarse_pair(const Plan& P, const Vecs& V, const float2* rr2, double* ur, float* ur32, cudaStream_t st);
 void launch_split_pair(int64_t n, const double* a, float2* b, cudaStream_t st);
@@ -37,9 +38,7 @@ void launch_pcg_init_pair(const Plan& P, const Vecs& V, double rtol, int maxit, 
 void launch_precond_prep_pair(const Plan& P, const Vecs& V, cudaStream_t st);
 void launch_pcg_first_dir_pair(const Plan& P, const Vecs& V, cudaStream_t st);
 void launch_pcg_update_xr_pair(const Plan& P, const Vecs& V, cudaStream_t st);
-void launch_pcg_dots_pair(const Plan& P, const Vecs& V, cudaStream_t st);
-void launch_pcg_update_p_pair(const Plan& P, const Vecs& V, const cudaGraphConditionalHandle* cond,
-                              cudaStream_t st);
+void launch_pcg_dots_pair(const Plan& P, const Vecs& V, const cudaGraphConditionalHandle* cond, cudaStream_t st);
 void launch_finalize_x_pair(const Plan& P, const Vecs& V, cudaStream_t st);
 
 template <typename Tq>

@@ -94,13 +94,13 @@ extern "C" cgs_status cgs_apply_preconditioner_noalloc(cgs_mesh* mesh, const dou
     if (d.nr && f64) {
         launch_restrict(P, V, true, V.s, true, V.rr, false, st);
         launch_coarse(P, V, V.rr, V.ur, nullptr, st);
-        launch_interp_add(P, V, true, V.ur, nullptr, V.z, false, st);
+        launch_interp_add(P, V, true, V.ur, nullptr, V.z, false, nullptr, st);
     } else if (d.nr) {
         // r_r as float pairs, the pair product writes u_r rounded to float
         float* ur32 = reinterpret_cast<float*>(V.ur);
         launch_restrict(P, V, false, V.s, false, V.rr, true, st);
         launch_coarse_pair(P, V, reinterpret_cast<const float2*>(V.rr), nullptr, ur32, st);
-        launch_interp_add(P, V, false, nullptr, ur32, V.z, false, st);
+        launch_interp_add(P, V, false, nullptr, ur32, V.z, false, nullptr, st);
     }
     if (f64)
         launch_copy_d(P, static_cast<const double*>(V.z), z, true, st);

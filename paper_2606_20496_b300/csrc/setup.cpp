@@ -573,17 +573,12 @@ cgs_status host_setup(const double* xyz, int64_t nv, const int32_t* conn, int64_
     // ---- per-vertex box lists ----------------------------------------------
     // W Q^T J_L regrouped by vertex: vertex v with cnt_v elements, n_c of
     // them in cell c, takes weight n_c / cnt_v on that cell's trilinear
-    // interpolant.  Free vertices with elements, ordered by their smallest
-    // cell (then id) so that neighbouring threads share a cell.
+    // interpolant.  Free vertices with elements, in vertex order (the
+    // interpolation reads and writes vertex vectors through this list).
     {
-        std::vector<int32_t> first(nv, INT32_MAX);
-        for (int64_t v = 0; v < nv; ++v)
-            for (int64_t t = v2e_ptr[v]; t < v2e_ptr[v + 1]; ++t) first[v] = std::min(first[v], ecell[v2e[t]]);
         S.vb_vert.clear();
         for (int64_t v = 0; v < nv; ++v)
             if (!S.dir[v] && v2e_ptr[v + 1] > v2e_ptr[v]) S.vb_vert.push_back((int32_t)v);
-        std::stable_sort(S.vb_vert.begin(), S.vb_vert.end(),
-                         [&](int32_t a, int32_t b) { return first[a] < first[b]; });
         S.vb_ptr.assign(1, 0);
         S.vb_cell.clear();
         S.vb_w.clear();
