@@ -105,9 +105,14 @@ typedef struct {
  *   pdl         1: kernels launched with programmatic stream serialization (each may
  *               start while its predecessor drains); 0: ordinary launches
  *   row_packs   1: meshes small enough to have row packs solve each small subdomain
- *               with 4 lanes (full rows; more parallelism); 0: one lane each   */
+ *               with 4 lanes (full rows; more parallelism); 0: one lane each
+ *   interp_cells 1: the interpolation runs over the cell-sorted (vertex, cell)
+ *               entries, one warp per cell range, adding into z atomically, and
+ *               the PCG dots z.r, z.q follow in their own kernel; 0: by vertex,
+ *               the dots fused (fewer launches; the persistent loop always
+ *               interpolates by vertex)                                        */
 typedef struct {
-    int32_t vert_chunk, sub_chunk, pack_chunk, box_chunk, tile_tma, persistent, pdl, row_packs;
+    int32_t vert_chunk, sub_chunk, pack_chunk, box_chunk, tile_tma, persistent, pdl, row_packs, interp_cells;
 } cgs_schedule;
 
 /* Kernel classes reported by the profiler. */

@@ -61,7 +61,7 @@ class MeshInfo(C.Structure):
 
 class Schedule(C.Structure):
     _fields_ = [(k, C.c_int32) for k in ("vert_chunk", "sub_chunk", "pack_chunk", "box_chunk", "tile_tma",
-                                         "persistent", "pdl", "row_packs")]
+                                         "persistent", "pdl", "row_packs", "interp_cells")]
 
 
 _lib = None

@@ -210,11 +210,12 @@ cgs_status finish(cudaStream_t st, bool sync) {
     return CGS_OK;
 }
 
-// z += J~ A_r^{-1} J~^T s  (s: the bulk copy of the residual or of r - A l)
-// z += J A_r^{-1} J^T s (r_r = 0 on entry; restricted already when
-// `restricted`).  dots: the interpolation also forms the PCG dots z.r, z.q
-// and beta.
-void box_correction(Engine& E, const Vecs& V, bool dots, cudaStream_t st, bool restricted = false,
+// z += J A_r^{-1} J^T s (s: the bulk copy of the residual or of r - A l;
+// r_r = 0 on entry; restricted already when `restricted`).  dots: the
+// per-vertex interpolation also forms the PCG dots z.r, z.q and beta;
+// returns whether it did (the interpolation by cells leaves them to the
+// dots kernel).
+bool box_correction(Engine& E, const Vecs& V, bool dots, cudaStream_t st, bool restricted = false,
                     const cudaGraphConditionalHandle* cond = nullptr) {
     const Plan& P = E.P;
     if (E.f64) {
@@ -225,12 +226,14 @@ void box_correction(Engine& E, const Vecs& V, bool dots, cudaStream_t st, bool r
         if (!restricted) K(CGS_K_RESTRICT, launch_restrict(P, V, false, V.s, false, V.rr, true, st));
         K(CGS_K_COARSE, launch_coarse_pair(P, V, reinterpret_cast<const float2*>(V.rr), nullptr, V.ur32, st));
     }
-    K(CGS_K_INTERP, launch_interp_add(P, V, E.f64, V.ur, E.f64 ? nullptr : V.ur32, V.z, dots, cond, st));
+    bool fused = false;
+    K(CGS_K_INTERP, fused = launch_interp_add(P, V, E.f64, V.ur, E.f64 ? nullptr : V.ur32, V.z, dots, cond, st));
+    return fused;
 }
 
 // z (bulk) = M r, with z = 0, s = r (bulk) and r_r = 0 on entry.  dots: also
-// the PCG dots (fused into the interpolation when there is a reduced space);
-// returns whether they were formed.
+// the PCG dots (fused into the per-vertex interpolation when there is a
+// reduced space); returns whether they were formed.
 bool precond_body(Engine& E, const Vecs& V, cudaStream_t st, bool dots = false,
                   const cudaGraphConditionalHandle* cond = nullptr) {
     const Plan& P = E.P;
@@ -248,14 +251,12 @@ bool precond_body(Engine& E, const Vecs& V, cudaStream_t st, bool dots = false,
         if (!E.f64 && !P.nwork[kWorkSub] && P.any_nr && P.nwork[kWorkBoxEnt]) {
             K(CGS_K_LOCAL, launch_local_restrict(P, V, E.prec, static_cast<const float*>(V.s),
                                                  static_cast<float*>(V.z), V.rr, st));
-            box_correction(E, V, dots, st, true, cond);
-            return dots;
+            return box_correction(E, V, dots, st, true, cond);
         }
         K(CGS_K_LOCAL, launch_local(P, V, E.prec, V.s, V.z, false, st));
     }
     if (!P.any_nr) return false;
-    box_correction(E, V, dots, st, false, cond);
-    return dots;
+    return box_correction(E, V, dots, st, false, cond);
 }
 
 // One flexible-PCG iteration over every slot of the engine: float64 vectors
@@ -495,6 +496,7 @@ cudaError_t set_schedule(Engine& E, const Schedule& sch) {
     E.tables = fresh;
     P.tile_tma = sch.tile_tma != 0;
     P.pdl = sch.pdl != 0;
+    P.interp_cells = sch.interp_cells != 0;
     E.P = P;
     E.sch = sch;
     if (E.gexec) {   // the captured loop holds the old grid sizes
@@ -555,7 +557,7 @@ cgs_status tune_engine(Engine& E, cudaStream_t st) {
     // box-list vertices per interpolation block
     if (P_any_nr(E)) {
         float best_box = 1e30f;
-        for (int bc : {256, 512, 1024}) {
+        for (int bc : {256, 512, 768, 1024, 2048}) {
             Schedule t = best;
             t.box_chunk = bc;
             if (set_schedule(E, t) != cudaSuccess) continue;
@@ -565,6 +567,28 @@ cgs_status tune_engine(Engine& E, cudaStream_t st) {
             if (ms < best_box) {
                 best_box = ms;
                 best.box_chunk = bc;
+            }
+        }
+    }
+    // interpolation by vertex with the dots fused, or by cells followed by
+    // the dots kernel
+    if (P_any_nr(E)) {
+        float best_ip = 1e30f;
+        for (int ic = 0; ic < 2; ++ic) {
+            Schedule t = best;
+            t.interp_cells = ic;
+            if (set_schedule(E, t) != cudaSuccess) continue;
+            const float ms = time_it([&]() {
+                if (!launch_interp_add(E.P, V, E.f64, V.ur, E.f64 ? nullptr : V.ur32, V.z, true, nullptr, st)) {
+                    if (E.f64)
+                        launch_pcg_dots<double, double>(E.P, V, V.q, st);
+                    else
+                        launch_pcg_dots_pair(E.P, V, nullptr, st);
+                }
+            });
+            if (ms < best_ip) {
+                best_ip = ms;
+                best.interp_cells = ic;
             }
         }
     }
@@ -1332,7 +1356,7 @@ cgs_status cgs_mesh_get_schedule(const cgs_mesh* m, cgs_schedule* out) {
     if (!m || !out) return fail(CGS_ERR_INVALID_ARG, "null argument");
     const Schedule& s = m->E.sch;
     *out = cgs_schedule{s.vert_chunk, s.sub_chunk, s.pack_chunk, s.box_chunk, s.tile_tma, s.persistent,
-                        m->E.P.pdl ? 1 : 0, s.row_packs};
+                        m->E.P.pdl ? 1 : 0, s.row_packs, s.interp_cells};
     return CGS_OK;
 }
 
@@ -1341,7 +1365,8 @@ cgs_status cgs_mesh_set_schedule(cgs_mesh* m, const cgs_schedule* c) {
     auto in = [](int v, int lo, int hi, int step) { return v >= lo && v <= hi && v % step == 0; };
     if (!in(c->vert_chunk, 256, 8192, 256) || !in(c->sub_chunk, 8, 512, 8) || !in(c->pack_chunk, 8, 256, 8) ||
         !in(c->box_chunk, 256, 4096, 256) || (c->tile_tma != 0 && c->tile_tma != 1) || c->persistent < -1 ||
-        c->persistent > 1 || (c->pdl != 0 && c->pdl != 1) || (c->row_packs != 0 && c->row_packs != 1))
+        c->persistent > 1 || (c->pdl != 0 && c->pdl != 1) || (c->row_packs != 0 && c->row_packs != 1) ||
+        (c->interp_cells != 0 && c->interp_cells != 1))
         return fail(CGS_ERR_INVALID_ARG, "schedule out of range");
     CGS_CUDA(cudaSetDevice(m->ctx->device));
     Schedule sch = m->E.sch;
@@ -1353,6 +1378,7 @@ cgs_status cgs_mesh_set_schedule(cgs_mesh* m, const cgs_schedule* c) {
     sch.persistent = c->persistent;
     sch.pdl = c->pdl;
     sch.row_packs = c->row_packs;
+    sch.interp_cells = c->interp_cells;
     CGS_CUDA(set_schedule(m->E, sch));
     return CGS_OK;
 }
@@ -1515,6 +1541,7 @@ cudaError_t server_tables(cgs_server* sv, const std::vector<int>& ids, cgs_serve
     P.wait_limit = sv->E.P.wait_limit;
     P.tile_tma = sv->sch.tile_tma != 0;
     P.pdl = sv->sch.pdl != 0;
+    P.interp_cells = sv->sch.interp_cells != 0;
     for (int k : ids) {
         const cgs_server::SlotState& ss = sv->slots[k];
         const cgs_mesh* m = ss.req.mesh;

@@ -187,6 +187,7 @@ struct Plan {
     int wait_limit = 1 << 20;              // iteration limit of bounded device waits
     bool tile_tma = false;                 // element tiles staged by TMA (else streamed by the threads)
     bool pdl = true;                       // launch with programmatic stream serialization
+    bool interp_cells = false;             // interpolation by cell-sorted entries (dots left to the caller)
 };
 
 // Grid-wide barrier of the persistent PCG kernel (device memory, zeroed

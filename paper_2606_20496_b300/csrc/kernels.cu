@@ -248,6 +248,15 @@ __global__ void __launch_bounds__(kBlock) apply64_kernel(const DevMesh* __restri
 // the outer operator of the mixed forms is evaluated this way: the same
 // iterates as FP64 to ~1e-14, no FP64 instruction per element.
 // ---------------------------------------------------------------------------
+// Zero for clearing a value that this thread has just loaded from the same
+// address: 0 * x, which the compiler may not fold, so the store waits for the
+// load's data.  A constant store issued while the load of its own address is
+// still in flight took a slow path on B300 (about 3x the kernel time when the
+// line came from DRAM).  The result is +0 or -0, an exact additive identity
+// for what accumulates there next; x is finite on every path that runs on.
+__device__ __forceinline__ float zero_after(float x) { return __fmul_rn(x, 0.0f); }
+__device__ __forceinline__ float2 zero_after(float2 x) { return make_float2(zero_after(x.x), zero_after(x.y)); }
+
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
     s = __fadd_rn(a, b);
     const float bb = __fsub_rn(s, a);
@@ -1326,6 +1335,69 @@ __global__ void __launch_bounds__(kBlock) restrict_kernel(const DevMesh* __restr
     restrict_item<T, Tin, kPairOut>(meshes, w_, V, sin, rrv);
 }
 
+// z += W Q^T J_L u_r over the cell-sorted box-list entries (the transpose of
+// the restriction, the same (vertex, cell, weight) entries): each warp takes
+// a range of one cell's entries, holds the cell's 8 values of u_r in
+// registers and adds weight * sum_m w_m(x_v) u_r[m] to z_v by an atomic add
+// (a vertex in several cells receives one add per cell, in any order).
+template <typename T, typename Tu>
+__device__ __forceinline__ void interp_cell_item(const DevMesh* __restrict__ meshes, const Work& w, Vecs V,
+                                                 const Tu* __restrict__ urv, T* __restrict__ zv) {
+    CGS_ITEM_PROLOGUE();
+    const int r = w.begin + (int)(threadIdx.x >> 5);
+    if (r >= w.end) return;   // whole warps leave
+    const Tu* ur = urv + w.roff;
+    T* z = zv + w.voff;
+    const BoxGrid<T> g(M);
+    const auto vx = vertex_data(M, T(0));
+    const T* rw = rent_w(M, T(0));
+    const int lane = threadIdx.x & 31;
+    const int2 rg = __ldg(&M.re_rng[r]);
+    const int pc = __ldg(&M.re_cell[rg.x]);   // one cell per range
+    const int c = (pc & 1023) + g.bx * (((pc >> 10) & 1023) + g.by * (pc >> 20));
+    // corner m's value (0 for an inactive corner), loaded by lane m
+    T um = T(0);
+    if (lane < 8) {
+        const int col = __ldg(&M.cell_cols[(size_t)c * 8 + lane]);
+        um = col >= 0 ? (T)__ldg(&ur[col]) : T(0);
+    }
+    T u[8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) u[m] = __shfl_sync(0xffffffffu, um, m);
+    for (int i0 = rg.x + lane; i0 < rg.y; i0 += 128) {
+        // four entries per lane and round, their loads first
+        int v[4];
+        T f[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int i = i0 + 32 * k;
+            v[k] = i < rg.y ? __ldg(&M.re_vert[i]) : -1;
+            f[k] = i < rg.y ? __ldg(&rw[i]) : T(0);
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (v[k] < 0) continue;
+            T x, y, zz, ic;
+            vx.load(v[k], x, y, zz, ic);
+            T wt[8];
+            cell_weights(g, pc, x, y, zz, wt);
+            T sum = T(0);
+#pragma unroll
+            for (int m = 0; m < 8; ++m) sum += wt[m] * u[m];
+            atomicAdd(&z[v[k]], f[k] * sum);
+        }
+    }
+}
+
+template <typename T, typename Tu>
+__global__ void __launch_bounds__(kBlock) interp_cell_kernel(const DevMesh* __restrict__ meshes,
+                                                             const Work* __restrict__ work, Vecs V,
+                                                             const Tu* __restrict__ urv, T* __restrict__ zv) {
+    const Work w_ = work[blockIdx.x];
+    pdl_wait();
+    interp_cell_item<T, Tu>(meshes, w_, V, urv, zv);
+}
+
 // z += W Q^T J_L u_r by vertex: z_v += sum_c weight_c sum_m w_m^c(x_v) u_r[m]
 // (each box-list vertex once: plain read-modify-write).  kDots fuses the
 // PCG dots that follow the preconditioner, z.r and z.q (Dirichlet and
@@ -1409,7 +1481,7 @@ __device__ __forceinline__ void interp_add_item(const DevMesh* __restrict__ mesh
                 const float2 z2 = make_float2((float)zi, 0.0f);
                 pr_dot_acc(rh, rl, z2, rk[k]);
                 pr_dot_acc(qh, ql, z2, qk[k]);
-                q2[v[k]] = make_float2(0.0f, 0.0f);   // q = 0 for the next product
+                q2[v[k]] = zero_after(qk[k]);   // q = 0 for the next product
             }
         }
     }
@@ -1730,6 +1802,7 @@ __device__ __forceinline__ void pcg_dots_item(const DevMesh* __restrict__ meshes
         zr = fma(zi, r[i], zr);
         zq = fma(zi, qval(q, i), zq);
     }
+    if (!S) return;   // no slot scalars (timing runs): no reduction
     double val[2] = {zr, zq}, tot[2];
     pdl_trigger();   // the successor may launch during the reduction tail
     if (slot_sum<2>(val, V.partials + w.poff, w.idx, w.count, &S->ticket[3], tot) && threadIdx.x == 0) {
@@ -1910,7 +1983,7 @@ __device__ __forceinline__ void pcg_update_xr_pair_item(const DevMesh* __restric
                 const float2 rn = pr_fma(na, qi[k], ri[k]);
                 r[i] = rn;
                 pr_dot_acc(h, l, rn, rn);
-                z[i] = 0.0f;
+                z[i] = zero_after(zi[k]);
                 s[i] = rn.x;
             }
         }
@@ -1952,6 +2025,7 @@ __device__ __forceinline__ void pcg_dots_pair_item(const DevMesh* __restrict__ m
     float2* __restrict__ q = V.q2 + w.voff;
     float rh = 0.0f, rl = 0.0f, qh = 0.0f, ql = 0.0f;
     CGS_VERT_LOOP4(i0) {
+        // a round's loads, then its arithmetic, then its stores
         float zi[4];
         float2 ri[4], qi[4];
 #pragma unroll
@@ -1963,7 +2037,6 @@ __device__ __forceinline__ void pcg_dots_pair_item(const DevMesh* __restrict__ m
                 zi[k] = z[i];
                 ri[k] = r[i];
                 qi[k] = q[i];
-                q[i] = make_float2(0.0f, 0.0f);   // q = 0 for the next product
             }
         }
 #pragma unroll
@@ -1972,7 +2045,13 @@ __device__ __forceinline__ void pcg_dots_pair_item(const DevMesh* __restrict__ m
             pr_dot_acc(rh, rl, z2, ri[k]);
             pr_dot_acc(qh, ql, z2, qi[k]);
         }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int64_t i = i0 + k * (int64_t)blockDim.x;
+            if (i < w.end) q[i] = zero_after(qi[k]);   // q = 0 for the next product
+        }
     }
+    if (!S) return;   // no slot scalars (timing runs): no reduction
     float vh[2] = {rh, qh}, vl[2] = {rl, ql};
     double tot[2];
     pdl_trigger();   // the successor may launch during the reduction tail
@@ -2326,9 +2405,24 @@ void launch_restrict(const Plan& P, const Vecs& V, bool fp64, const void* s, boo
                    static_cast<const float*>(s), rr);
 }
 
-void launch_interp_add(const Plan& P, const Vecs& V, bool fp64, const double* ur, const float* ur32, void* z,
+bool launch_interp_add(const Plan& P, const Vecs& V, bool fp64, const double* ur, const float* ur32, void* z,
                        bool dots, const cudaGraphConditionalHandle* cond, cudaStream_t st) {
-    if (!P.nwork[kWorkBox] || !P.any_nr) return;
+    if (P.interp_cells) {   // by cell-sorted entries; the dots are left to the caller
+        if (!P.nwork[kWorkBoxEnt] || !P.any_nr) return false;
+        const unsigned int n = P.nwork[kWorkBoxEnt];
+        const Work* W = P.work[kWorkBoxEnt];
+        if (fp64)
+            launch_pdl(P.pdl, interp_cell_kernel<double, double>, n, kBlock, 0, st, P.meshes, W, V, ur,
+                       static_cast<double*>(z));
+        else if (ur32)
+            launch_pdl(P.pdl, interp_cell_kernel<float, float>, n, kBlock, 0, st, P.meshes, W, V, ur32,
+                       static_cast<float*>(z));
+        else
+            launch_pdl(P.pdl, interp_cell_kernel<float, double>, n, kBlock, 0, st, P.meshes, W, V, ur,
+                       static_cast<float*>(z));
+        return false;
+    }
+    if (!P.nwork[kWorkBox] || !P.any_nr) return false;
     const unsigned int n = P.nwork[kWorkBox];
     const Work* W = P.work[kWorkBox];
     const cudaGraphConditionalHandle h = cond ? *cond : 0;
@@ -2350,7 +2444,9 @@ void launch_interp_add(const Plan& P, const Vecs& V, bool fp64, const double* ur
     } else {
         launch_pdl(P.pdl, interp_add_kernel<float, double, 0>, n, kBlock, 0, st, P.meshes, W, V, ur,
                    static_cast<float*>(z), P.nslots, h, sc);
+        return false;
     }
+    return dots;
 }
 
 void launch_coarse(const Plan& P, const Vecs& V, const double* rr, double* ur, float* ur32, cudaStream_t st) {

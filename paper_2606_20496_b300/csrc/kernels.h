@@ -26,8 +26,10 @@ void launch_restrict(const Plan& P, const Vecs& V, bool fp64, const void* s, boo
                      bool pair_out, cudaStream_t st);
 // z += W Q^T J_L u_r.  dots: also z.r and z.q with beta and rho (fused PCG
 // dots; r and q of the engine's slots; mixed forms then zero q).  cond:
-// block 0 also sets the device-side loop condition.
-void launch_interp_add(const Plan& P, const Vecs& V, bool fp64, const double* ur, const float* ur32, void* z,
+// block 0 also sets the device-side loop condition.  With P.interp_cells the
+// interpolation runs over the cell-sorted entries and fuses nothing.
+// Returns whether the dots (and the loop condition) were fused.
+bool launch_interp_add(const Plan& P, const Vecs& V, bool fp64, const double* ur, const float* ur32, void* z,
                        bool dots, const cudaGraphConditionalHandle* cond, cudaStream_t st);
 void launch_coarse(const Plan& P, const Vecs& V, const double* rr, double* ur, float* ur32, cudaStream_t st);
 void launch_coarse_pair(const Plan& P, const Vecs& V, const float2* rr2, double* ur, float* ur32, cudaStream_t st);
@@ -88,6 +90,8 @@ struct Schedule {
                          // 1 yes; 0 or -1 (default) no
     int pdl = 1;         // programmatic stream serialization of the launches
     int row_packs = 1;   // lane subdomains of meshes that have row packs solved 4 lanes each
+    int interp_cells = 0;// 1: interpolation by cell-sorted entries with atomic adds (the PCG
+                         // dots in their own kernel); 0: by vertex with the dots fused
 };
 // Default schedule: enough blocks to fill the GPU (about four per SM) for
 // `total` work of each kind, chunks within the kernels' ranges.

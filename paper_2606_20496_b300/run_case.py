@@ -51,6 +51,10 @@ def main():
                     help="programmatic dependent launch: 1 on, 0 off (default: setup's choice)")
     ap.add_argument("--row-packs", type=int, choices=(0, 1), default=None,
                     help="four lanes per small subdomain where the mesh has row packs: 1 on, 0 off")
+    ap.add_argument("--interp-cells", type=int, choices=(0, 1), default=None,
+                    help="interpolation by cell-sorted entries (1) or by vertex with the dots fused (0)")
+    for name in ("vert-chunk", "sub-chunk", "pack-chunk", "box-chunk"):
+        ap.add_argument(f"--{name}", type=int, default=None, help=f"force the schedule's {name.replace('-', '_')}")
     args = ap.parse_args()
     build.build()
     m, b = load_workload(args.workload)
@@ -61,7 +65,9 @@ def main():
     if args.tune:
         cgs.cgs_mesh_tune(h.handle)
     forced = {k: v for k, v in (("tile_tma", args.tile_tma), ("persistent", args.persistent), ("pdl", args.pdl),
-                                ("row_packs", args.row_packs)) if v is not None}
+                                ("row_packs", args.row_packs), ("interp_cells", args.interp_cells),
+                                ("vert_chunk", args.vert_chunk), ("sub_chunk", args.sub_chunk),
+                                ("pack_chunk", args.pack_chunk), ("box_chunk", args.box_chunk)) if v is not None}
     if forced:
         cgs.cgs_mesh_set_schedule(h.handle, **forced)
     bd = torch.as_tensor(b, dtype=torch.float64, device="cuda")

@@ -29,6 +29,17 @@ def test_header_declarations_match_binding():
     assert set(_declared()) == set(cgs.EXPORTS)
 
 
+def test_schedule_struct_matches_header():
+    """The binding's cgs_schedule mirrors the header's fields, in order, all int32."""
+    text = open(os.path.join(ROOT, "include", "cgs.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    body = re.search(r"typedef struct \{([^}]*)\}\s*cgs_schedule;", text).group(1)
+    fields = [f.strip() for f in re.sub(r"\bint32_t\b", "", body).replace(";", ",").split(",") if f.strip()]
+    assert body.count("int32_t") == 1
+    assert [f[0] for f in cgs.Schedule._fields_] == fields
+    assert all(f[1] is cgs.C.c_int32 for f in cgs.Schedule._fields_)
+
+
 def test_library_exports_every_declared_symbol(lib):
     for name in _declared():
         assert hasattr(lib, name), name

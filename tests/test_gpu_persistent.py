@@ -115,7 +115,7 @@ def test_schedule_round_trip_and_pdl_off(ctx):
         assert np.array_equal(x0.cpu().numpy(), x1.cpu().numpy()) or \
             np.linalg.norm(x0.cpu().numpy() - x1.cpu().numpy()) <= 1e-8 * np.linalg.norm(x0.cpu().numpy())
         for bad in ({"vert_chunk": 300}, {"sub_chunk": 4}, {"pack_chunk": 7}, {"box_chunk": 100},
-                    {"tile_tma": 2}, {"persistent": 5}, {"pdl": -1}, {"row_packs": 3}):
+                    {"tile_tma": 2}, {"persistent": 5}, {"pdl": -1}, {"row_packs": 3}, {"interp_cells": 2}):
             with pytest.raises(cgs.CGSError) as ei:
                 cgs.cgs_mesh_set_schedule(h.handle, **bad)
             assert ei.value.status == cgs.ERR_INVALID_ARG
