@@ -2569,6 +2569,7 @@ void launch_resid_norm(const Plan& P, const Vecs& V, cudaStream_t st) {
     launch_pdl(P.pdl, resid_norm_kernel, P.nwork[kWorkVert], kBlock, 0, st, P.meshes, P.work[kWorkVert], V);
 }
 
+constexpr int64_t kInterpCellsMinVerts = 65536;
 Schedule default_schedule(int64_t total_nv, int64_t total_sub, int64_t total_pack, int64_t total_lane_subs) {
     const int64_t target = 4 * 148;
     Schedule s;
@@ -2581,6 +2582,9 @@ Schedule default_schedule(int64_t total_nv, int64_t total_sub, int64_t total_pac
     s.box_chunk = (int)std::min<int64_t>(1024, std::max<int64_t>(256, (v + 255) / 256 * 256));
     // four lanes per small subdomain only while one lane each leaves the GPU idle
     s.row_packs = total_lane_subs < kRowPackMaxSubs ? 1 : 0;
+    // the interpolation by cells (and a separate dots kernel) once the vertex
+    // count fills the GPU; below that, one launch fewer per iteration counts more
+    s.interp_cells = total_nv >= kInterpCellsMinVerts ? 1 : 0;
     return s;
 }
 
