@@ -111,12 +111,14 @@ class ClockSampler:
 # algorithmic bytes per launch of each kernel class (HBM roofline)
 # ---------------------------------------------------------------------------
 
-def algorithmic_bytes(info, prec):
+def algorithmic_bytes(info, prec, interp_cells=False):
     """Bytes each kernel class must move at least once per launch: every
     mandatory array once, each gathered vertex value once, padding not
     counted.  Mixed forms (fp32/fp16): float-pair outer vectors (8 B),
     float-pair element matrices (28 x 8 B), lane-pack local solves; FP64 form:
-    float64 everything."""
+    float64 everything.  interp_cells: the interpolation runs over the
+    cell-sorted entries (z added to once per entry) and the dots kernel
+    reads z, r, q (and clears q in the mixed forms)."""
     E, nv, nr = info["ne"], info["nv"], info["n_r"]
     sm = info["sum_sub_dofs"]
     nb = info["n_box_entries"]
@@ -129,7 +131,8 @@ def algorithmic_bytes(info, prec):
             "local": packed * sl + sm * 4 + nv * (8 + 2 * sb + sb),
             "restrict": nb * 16 + nv * (32 + sb) + nr * 16,
             "coarse": nr * nr * 8 + nr * 16,
-            "interp": nb * 16 + nv * (4 + 32 + 2 * sb + 16) + nr * 8,
+            "interp": (nb * 16 + nv * (32 + 2 * sb) + nr * 8) if interp_cells
+            else nb * 16 + nv * (4 + 32 + 2 * sb + 16) + nr * 8,
             "pcg_xr": nv * (8 * 6 + 2 * sb),
             "pcg_dots": nv * (sb + 16),
             "pcg_p": nv * (sb + 24),
@@ -146,11 +149,13 @@ def algorithmic_bytes(info, prec):
         "restrict": nb * 12 + nv * (16 + sb) + nr * 8,
         # per-vertex lists, coordinates, z read and written, r and q pairs
         # read (dots), q cleared
-        "interp": nv * 8 + nb * 8 + nv * (16 + 2 * sb + 16 + 8) + nr * 4,
+        "interp": (nb * 12 + nv * (16 + 2 * sb) + nr * 4) if interp_cells
+        else nv * 8 + nb * 8 + nv * (16 + 2 * sb + 16 + 8) + nr * 4,
         "coarse": nr * nr * 8 + nr * 12,
         # p, q, x, r read; p, x, r written; z read and cleared; s written
         "pcg_xr": nv * (8 * 7 + 3 * sb),
-        "pcg_dots": nv * (sb + 16),
+        # z, r and q read, q cleared
+        "pcg_dots": nv * (sb + 16 + 8),
         "pcg_p": nv * (sb + 24),
     }
 
@@ -340,11 +345,13 @@ def run_ours(args):
     info = dict(h32.info)
     info.update(cgs.cgs_mesh_info(h32.handle))
     info["_packed_entries"] = info["sum_sub_tri"]
-    algo = algorithmic_bytes(info, "fp32")
+    algo = algorithmic_bytes(info, "fp32", interp_cells=bool(sched.get("interp_cells")))
     iters32 = int(np.median(its32))
     # the persistent loop runs every phase of every iteration in one launch
+    # (interpolating by vertex)
     per_iter = ["apply_A64", "pcg_xr", "local", "apply_A32", "restrict", "coarse", "interp"]
-    algo["loop"] = iters32 * sum(algo[k] for k in per_iter)
+    by_vertex = algorithmic_bytes(info, "fp32")
+    algo["loop"] = iters32 * sum(by_vertex[k] for k in per_iter)
     total_ms = sum(t for t, n in prof.values())
     dom = max((k for k in prof if k in algo and prof[k][1]), key=lambda k: prof[k][0])
     dom_ms = prof[dom][0] / prof[dom][1]
