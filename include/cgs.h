@@ -67,6 +67,16 @@ typedef enum {
     CGS_ADDITIVE = 1     /* Eq. asm with R~_p = R_p (symmetric)                         */
 } cgs_form;
 
+/* Reduced solver u_r = A_r^{-1} r_r (Sec. 2, the XX^T paragraph; Sec. 4). */
+typedef enum {
+    CGS_COARSE_AUTO = 0,   /* XX^T when n_r > CGS_COARSE_AUTO_XXT_NR, else dense     */
+    CGS_COARSE_DENSE = 1,  /* explicit A_r^{-1}, one GEMV (n_r^2 entries)             */
+    CGS_COARSE_XXT = 2     /* A_r^{-1} = X X^T with X sparse and A_r-conjugate under a
+                              nested-dissection order of the box lattice: two sparse
+                              passes t = X^T r_r, u_r = X t; needs n_r <= 65535      */
+} cgs_coarse_solver;
+#define CGS_COARSE_AUTO_XXT_NR 1500
+
 typedef struct {
     int box[3];            /* b_x, b_y, b_z in [1, 1023]: box cells per axis over the
                               bounding box (Sec. 4)                                    */
@@ -74,6 +84,7 @@ typedef struct {
     int overlap_layers;    /* delta: element layers added to each Omega_p (Sec. 3), >= 0 */
     cgs_precision prec;
     cgs_form form;
+    cgs_coarse_solver coarse_solver;  /* 0 (zero-initialised params) = auto        */
 } cgs_params;
 
 typedef struct {
@@ -91,6 +102,8 @@ typedef struct {
     int64_t n_lane_packs;  /* lane packs of the mixed-form local solves (32 each)    */
     int32_t loop;          /* how solves iterate: 0 host-driven loop, 1 device-side
                               graph loop, 2 persistent cooperative kernel          */
+    int32_t coarse_solver; /* the reduced solver in use: CGS_COARSE_DENSE or _XXT   */
+    int64_t xxt_nnz;       /* nonzeros of X (XX^T solver), else 0                    */
 } cgs_mesh_info_t;
 
 /* Launch schedule of a mesh's kernels (cgs_mesh_get_schedule / _set_schedule):
@@ -193,7 +206,8 @@ cgs_status cgs_apply_preconditioner(cgs_mesh* mesh, const double* r, double* z, 
  * graph, serving loops that forbid allocations after warm-up, and hosts whose
  * device memory is owned by another runtime's pool.  The call performs no
  * cudaMalloc or cudaFree and uses no allocating library routine.  Its working
- * vectors (z and s in the bulk precision, r_r and u_r) live in one static
+ * vectors (z and s in the bulk precision, r_r, u_r and the XX^T pass's t)
+ * live in one static
  * device array of CGS_NOALLOC_SCRATCH_BYTES that every GPU loading this
  * library keeps until the process exits.
  *   limits  mesh nv <= CGS_NOALLOC_MAX_NV and n_r <= CGS_NOALLOC_MAX_NR, else
@@ -209,7 +223,7 @@ cgs_status cgs_apply_preconditioner(cgs_mesh* mesh, const double* r, double* z, 
  * counterpart; this is a deployment variant of Eqs. asm / asm1-asm2.       */
 #define CGS_NOALLOC_MAX_NV 131072
 #define CGS_NOALLOC_MAX_NR 8192
-#define CGS_NOALLOC_SCRATCH_BYTES ((size_t)16 * CGS_NOALLOC_MAX_NV + (size_t)16 * CGS_NOALLOC_MAX_NR)
+#define CGS_NOALLOC_SCRATCH_BYTES ((size_t)16 * CGS_NOALLOC_MAX_NV + (size_t)24 * CGS_NOALLOC_MAX_NR)
 cgs_status cgs_apply_preconditioner_noalloc(cgs_mesh* mesh, const double* r, double* z, void* stream);
 
 /* ---- solve ----------------------------------------------------------------

@@ -19,6 +19,9 @@ A u = b, Sec. 3):
   each element assigned to the cell holding its centroid, element-local
   trilinear interpolant J_L, averaging W Q^T (Sec. 4, the centroid-assignment
   paragraph), active-vertex compression, and A_r assembled cell-wise (Eq. Aij);
+* the reduced solve exactly (Cholesky) and by XX^T (Sec. 2): A_r-conjugate
+  basis vectors formed by Gram-Schmidt in the A_r inner product, in a
+  nested-dissection order of the box lattice;
 * the preconditioners ASM (Eq. asm) and the hybrid ASM_1 + ASM_2 (Eqs. asm1,
   asm2);
 * flexible preconditioned CG around them.
@@ -28,7 +31,8 @@ notes): 2x2x2 Gauss; Dirichlet = vertices of boundary faces; delta = 1 layer
 of vertex-sharing elements; R_p = free vertices whose elements all lie in the
 grown subdomain; W_ov = 1/multiplicity for the hybrid local step, no weight in
 the additive form; J^T (not J) in the coarse term; A_r by broken (cell-wise)
-assembly with Dirichlet rows of J_e zeroed; Polak-Ribiere beta.
+assembly with Dirichlet rows of J_e zeroed; Polak-Ribiere beta; nested
+dissection by median coordinate planes of the longest extent.
 
 Every function here is pinned by tests under ``tests/`` against closed forms,
 invariants or brute force; none is "parity unpinned".
@@ -292,6 +296,27 @@ class Problem:
         """u_r = A_r^{-1} r_r (exact; the paper uses XX^T, Sec. 2)."""
         return sla.cho_solve(self.Ar_chol, rr)
 
+    def box_lattice_coords(self):
+        """Integer lattice coordinates (i, j, k) of the active box vertices,
+        from their lexicographic ids i + (b_x+1)(j + (b_y+1)k)."""
+        nb = self.box_b + 1
+        g = self.box_active
+        return np.stack([g % nb[0], (g // nb[0]) % nb[1], g // (nb[0] * nb[1])], axis=1)
+
+    def xxt_factor(self):
+        """X of the XX^T reduced solve (Sec. 2), built once: A_r-conjugate
+        columns in the nested-dissection order of the box lattice."""
+        if getattr(self, "_xxt", None) is None:
+            order = nested_dissection(self.box_lattice_coords())
+            self._xxt = xxt_basis(self.Ar, order)
+        return self._xxt
+
+    def coarse_solve_xxt(self, rr):
+        """u_r = X X^T r_r (Sec. 2: the projection onto the full conjugate
+        basis is the exact solution)."""
+        X = self.xxt_factor()
+        return X @ (X.T @ np.asarray(rr, dtype=np.float64))
+
     def box_correction(self, r):
         """B_C r = J~ A_r^{-1} J~^T r."""
         return self.interp(self.coarse_solve(self.restrict(r)))
@@ -320,6 +345,57 @@ class Problem:
         iters counts the products A p; see fcg for the return tuple."""
         return fcg(self.apply_A, lambda r: self.apply_M(r, form),
                    np.where(self.dir, 0.0, np.asarray(b, dtype=np.float64)), rtol, maxit)
+
+
+# ----------------------------------------------------------------------------
+# XX^T reduced solver (Sec. 2, the paragraph on the sparse factorisation
+# A_c^{-1} = X X^T)
+# ----------------------------------------------------------------------------
+
+def nested_dissection(coords, leaf: int = 8):
+    """Nested-dissection order of lattice points (rows of `coords`).
+
+    Reading (the paper names nested dissection without details): a set of
+    more than `leaf` points is cut by the coordinate plane through the median
+    of its distinct coordinates along its longest extent; the points below
+    the plane come first, then those above, each ordered the same way, then
+    the points on the plane (the separator).  Smaller sets keep their order.
+    Returns a permutation of range(len(coords))."""
+    coords = np.asarray(coords)
+
+    def rec(ids):
+        if len(ids) <= leaf:
+            return list(ids)
+        p = coords[ids]
+        ext = p.max(axis=0) - p.min(axis=0)
+        ax = int(np.argmax(ext))            # first axis of the longest extent
+        planes = np.unique(p[:, ax])
+        mid = planes[len(planes) // 2]
+        below = [i for i in ids if coords[i, ax] < mid]
+        above = [i for i in ids if coords[i, ax] > mid]
+        sep = [i for i in ids if coords[i, ax] == mid]
+        return rec(below) + rec(above) + sep
+
+    return np.array(rec(list(range(len(coords)))), dtype=np.int64)
+
+
+def xxt_basis(A, order):
+    """Columns x_1..x_n with x_i^T A x_j = delta_ij (Sec. 2), formed in the
+    given order: the k-th is the unit vector of order[k] minus its A-projection
+    on the earlier ones, scaled to unit A-norm (Gram-Schmidt in the A inner
+    product).  Under a nested-dissection order the columns stay sparse; with
+    all n of them, X X^T = A^{-1}."""
+    A = np.asarray(A, dtype=np.float64)
+    n = A.shape[0]
+    X = np.zeros((n, n))
+    for k, j in enumerate(order):
+        x = np.zeros(n)
+        x[j] = 1.0
+        c = X[:, :k].T @ A[:, j]            # x_i^T A e_j, i < k
+        x -= X[:, :k] @ c
+        x /= np.sqrt(x @ A @ x)
+        X[:, k] = x
+    return X
 
 
 def fcg(apply_A, apply_M, b, rtol, maxit):

@@ -220,10 +220,12 @@ bool box_correction(Engine& E, const Vecs& V, bool dots, cudaStream_t st, bool r
     const Plan& P = E.P;
     if (E.f64) {
         K(CGS_K_RESTRICT, launch_restrict(P, V, true, V.s, true, V.rr, false, st));
+        if (P.any_xxt) K(CGS_K_COARSE, launch_xxt_pass1(P, V, false, V.rr, st));
         K(CGS_K_COARSE, launch_coarse(P, V, V.rr, V.ur, nullptr, st));
     } else {
         // r_r and the reduced product in float pairs, u_r rounded to float
         if (!restricted) K(CGS_K_RESTRICT, launch_restrict(P, V, false, V.s, false, V.rr, true, st));
+        if (P.any_xxt) K(CGS_K_COARSE, launch_xxt_pass1(P, V, true, V.rr, st));
         K(CGS_K_COARSE, launch_coarse_pair(P, V, reinterpret_cast<const float2*>(V.rr), nullptr, V.ur32, st));
     }
     bool fused = false;
@@ -353,7 +355,8 @@ cgs_status build_loop_graph(Engine& E) {
 // only): by the schedule, or (auto) when the element tiles of a launch fit
 // about two per resident block.
 bool use_persistent(Engine& E, const Schedule& sch) {
-    if (E.f64 || sch.persistent == 0) return false;
+    // the persistent loop runs the dense reduced product only
+    if (E.f64 || sch.persistent == 0 || E.P.any_xxt) return false;
     if (!E.pblocks) E.pblocks = persistent_blocks(E.prec);
     if (E.pblocks <= 0) return false;
     return sch.persistent == 1;
@@ -462,6 +465,7 @@ cudaError_t alloc_pools(DevAllocs& mem, Engine& E, int64_t total_v, int64_t tota
     }
     TRY(mem.alloc(&V.rr, std::max<int64_t>(total_r, 1)));
     TRY(mem.alloc(&V.ur, std::max<int64_t>(total_r, 1)));
+    TRY(mem.alloc(&V.rt, std::max<int64_t>(total_r, 1)));
     TRY(mem.alloc(&V.partials, std::max<int64_t>(total_p, 2)));
     TRY(mem.alloc(&V.S, nslots));
     TRY(cudaMemset(V.S, 0, sizeof(SolveScalars) * nslots));
@@ -497,6 +501,7 @@ cudaError_t set_schedule(Engine& E, const Schedule& sch) {
     P.tile_tma = sch.tile_tma != 0;
     P.pdl = sch.pdl != 0;
     P.interp_cells = sch.interp_cells != 0;
+    P.any_xxt = P.nwork[kWorkXSeg] > 0;
     E.P = P;
     E.sch = sch;
     if (E.gexec) {   // the captured loop holds the old grid sizes
@@ -696,6 +701,7 @@ cgs_status cgs_mesh_setup(cgs_ctx* ctx, const double* xyz, int64_t nv, const int
                        (hs.inv.size() + hs.pack_inv.size() + hs.rpack_inv.size()) *
                            (f64 ? 8 : prm.prec == CGS_FP32_BULK ? 4 : 2) +
                        (hs.pack_idx.size() + hs.rpack_idx.size()) * 4 + hs.ar_inv.size() * 8 +
+                       hs.xc_idx.size() * 20 + hs.xs_seg.size() * 4 + hs.xr_ptr.size() * 4 +
                        (size_t)nv * (5 * 8 + 2 * bulk);
     {
         std::lock_guard<std::mutex> lk(ctx->mu);
@@ -891,7 +897,38 @@ cgs_status cgs_mesh_setup(cgs_ctx* ctx, const double* xyz, int64_t nv, const int
             d.xyzwf = reinterpret_cast<const float4*>(p);
         }
     }
-    if (hs.nr && f64) {
+    if (hs.nr && hs.coarse == CGS_COARSE_XXT) {
+        // X by columns (segmented) and by rows; values float64 (FP64 form) or
+        // hi/lo float pairs (mixed forms), 8 bytes either way
+        d.xxt = 1;
+        d.nxseg = (int64_t)hs.xs_seg.size() / 4;
+        const int32_t* seg = nullptr;
+        UP(seg, hs.xs_seg);
+        d.xs_seg = reinterpret_cast<const int4*>(seg);
+        UP(d.xc_idx, hs.xc_idx);
+        UP(d.xr_idx, hs.xr_idx);
+        UP(d.xr_ptr, hs.xr_ptr);
+        auto vals = [&](const std::vector<double>& v, const void** out) -> cudaError_t {
+            if (f64) {
+                const double* p = nullptr;
+                cudaError_t e = m->mem.upload(&p, v);
+                *out = p;
+                return e;
+            }
+            std::vector<float2> v2(v.size());
+            for (size_t i = 0; i < v.size(); ++i) {
+                const float h = (float)v[i];
+                v2[i] = make_float2(h, (float)(v[i] - (double)h));
+            }
+            const float2* p = nullptr;
+            cudaError_t e = m->mem.upload(&p, v2);
+            *out = p;
+            return e;
+        };
+        cudaError_t e1 = vals(hs.xc_val, &d.xc_val);
+        if (e1 == cudaSuccess) e1 = vals(hs.xr_val, &d.xr_val);
+        if (e1 != cudaSuccess) return cleanup(cuda_fail(e1, "upload"));
+    } else if (hs.nr && f64) {
         UP(d.ar_inv, hs.ar_inv);
     } else if (hs.nr) {
         // hi = entry rounded to float, lo = the rounded remainder; rows padded
@@ -914,7 +951,7 @@ cgs_status cgs_mesh_setup(cgs_ctx* ctx, const double* xyz, int64_t nv, const int
         m->d_dev = const_cast<DevMesh*>(dd);
     }
     // one solve slot and its work tables
-    m->sizes = MeshSizes{nv, ne, d.ntiles, hs.n_wsub, hs.nr, d.n_pack, d.nvb, d.nrng, d.n_rpack};
+    m->sizes = MeshSizes{nv, ne, d.ntiles, hs.n_wsub, hs.nr, d.n_pack, d.nvb, d.nrng, d.n_rpack, d.nxseg};
     Engine& E = m->E;
     E.f64 = f64;
     E.prec = prm.prec;
@@ -967,6 +1004,8 @@ cgs_status cgs_mesh_setup(cgs_ctx* ctx, const double* xyz, int64_t nv, const int
     }
     m->info.n_box_entries = (int64_t)hs.vb_cell.size();
     m->info.n_lane_packs = (int64_t)hs.pack_m.size();
+    m->info.coarse_solver = hs.coarse;
+    m->info.xxt_nnz = (int64_t)hs.xc_idx.size();
     m->info.footprint_bytes = m->mem.bytes;
     m->info.setup_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     *out = m;
@@ -1096,12 +1135,15 @@ cgs_status cgs_coarse_solve(cgs_mesh* m, const double* rr, double* ur, void* str
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     Engine& E = m->E;
     const Vecs V = no_stop(E.V);
+    if (E.P.any_xxt) K(CGS_K_OTHER, launch_fill_d(m->d.nr, V.rt, 0.0, st));   // t = X^T r_r accumulates
     if (m->fp64()) {
+        if (E.P.any_xxt) K(CGS_K_COARSE, launch_xxt_pass1(E.P, V, false, rr, st));
         K(CGS_K_COARSE, launch_coarse(E.P, V, rr, ur, nullptr, st));
     } else {
-        // the mixed forms keep A_r^{-1} as float pairs: r_r -> pairs first
+        // the mixed forms keep A_r^{-1} (or X) as float pairs: r_r -> pairs first
         float2* rr2 = reinterpret_cast<float2*>(V.rr);
         K(CGS_K_OTHER, launch_split_pair(m->d.nr, rr, rr2, st));
+        if (E.P.any_xxt) K(CGS_K_COARSE, launch_xxt_pass1(E.P, V, true, V.rr, st));
         K(CGS_K_COARSE, launch_coarse_pair(E.P, V, rr2, ur, nullptr, st));
     }
     return finish(st, false);
@@ -1568,6 +1610,7 @@ cudaError_t server_tables(cgs_server* sv, const std::vector<int>& ids, cgs_serve
         P.work[kind] = t.d[kind];
         P.nwork[kind] = (unsigned int)n;
     }
+    P.any_xxt = P.nwork[kWorkXSeg] > 0;
     return cudaSuccess;
 }
 
@@ -1609,7 +1652,7 @@ cgs_status cgs_server_create(cgs_ctx* ctx, int max_slots, int64_t pool_nv, int64
     sv->ar.init((pool_nr + 7) / 8 * 8 + 8 * max_slots, 8);
     sv->ap.init(2 * ((pool_nv + 127) / 128) + 64 * (int64_t)max_slots, 8);
     sv->bytes_per_v = 4 * sizeof(double) + (prec == CGS_FP64 ? 3 * sizeof(double) : sizeof(float2) + 2 * sizeof(float));
-    sv->bytes_per_r = 2 * sizeof(double) + (prec == CGS_FP64 ? 0 : sizeof(float));
+    sv->bytes_per_r = 3 * sizeof(double) + (prec == CGS_FP64 ? 0 : sizeof(float));
     sv->rtol = rtol;
     sv->maxit = maxit;
     sv->slots.resize(max_slots);

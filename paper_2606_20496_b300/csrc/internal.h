@@ -76,7 +76,18 @@ struct HostSetup {
     std::vector<double> re_w;
     std::vector<int32_t> re_rng;       // (begin, end) entry ranges within one cell, <= kBoxRange each
     std::vector<int64_t> box_active;   // nr, lexicographic box-vertex ids
-    std::vector<double> ar_inv;        // nr*nr, A_r^{-1}, full symmetric, float64
+    int coarse = 1;                    // reduced solver: 1 dense A_r^{-1}, 2 XX^T
+    std::vector<double> ar_inv;        // nr*nr, A_r^{-1}, full symmetric, float64 (dense)
+    // XX^T (Sec. 2): A_r^{-1} = X X^T, column k of X the k-th A_r-conjugate
+    // vector in nested-dissection order; rows are reduced indices
+    std::vector<int32_t> nd_perm;      // nr, nested-dissection position -> reduced index
+    std::vector<int32_t> xc_ptr;       // nr + 1, column starts (pass t = X^T r_r)
+    std::vector<uint16_t> xc_idx;      // rows of each column, ascending
+    std::vector<double> xc_val;
+    std::vector<int32_t> xr_ptr;       // nr + 1, row starts (pass u_r = X t)
+    std::vector<uint16_t> xr_idx;      // columns of each row, ascending
+    std::vector<double> xr_val;
+    std::vector<int32_t> xs_seg;       // 4 per segment: column, begin, end, 0 (<= kXxtSeg entries)
     double seconds = 0.0;
 };
 
@@ -152,6 +163,14 @@ struct DevMesh {
     const float* rpack_scale = nullptr;
     const double* wov64 = nullptr;     // nv
     const float* wov32 = nullptr;      // nv
+    int32_t xxt = 0;                   // 1: reduced solve by XX^T (the fields below), else dense
+    int64_t nxseg = 0;                 // pass-1 segments
+    const int4* xs_seg = nullptr;      // (column, begin, end, 0) of each segment of X's columns
+    const uint16_t* xc_idx = nullptr;  // column-major rows of X
+    const void* xc_val = nullptr;      // column-major values: double (FP64 form) or float pair
+    const int32_t* xr_ptr = nullptr;   // nr + 1 row starts of X
+    const uint16_t* xr_idx = nullptr;  // row-major columns of X
+    const void* xr_val = nullptr;      // row-major values: double or float pair
     const double* ar_inv = nullptr;    // nr*nr (FP64 form)
     const float2* ar_inv2 = nullptr;   // nr rows of nr2 float pairs (mixed forms; nr2 = nr rounded up to even)
     int64_t nr2 = 0;
@@ -172,6 +191,7 @@ enum WorkKind {
     kWorkBox,
     kWorkBoxEnt,
     kWorkRowPack,
+    kWorkXSeg,
     kWorkKinds
 };
 
@@ -188,6 +208,7 @@ struct Plan {
     bool tile_tma = false;                 // element tiles staged by TMA (else streamed by the threads)
     bool pdl = true;                       // launch with programmatic stream serialization
     bool interp_cells = false;             // interpolation by cell-sorted entries (dots left to the caller)
+    bool any_xxt = false;                  // some mesh solves its reduced system by XX^T
 };
 
 // Grid-wide barrier of the persistent PCG kernel (device memory, zeroed
@@ -260,6 +281,7 @@ inline int32_t pack_cell(int32_t c, int bx, int by) {
     return (c % bx) | (((c / bx) % by) << 10) | ((c / (bx * by)) << 20);
 }
 constexpr int kRowChunk = 4;      // reduced rows per block (one warp each)
+constexpr int kXxtSeg = 256;      // entries of one column of X per pass-1 warp
 constexpr int kBoxRange = 256;    // restriction entries (of one cell) per warp
 
 // Vector pools of a set of slots, passed by value to every kernel.  A slot's
@@ -273,6 +295,7 @@ struct Vecs {
     float2 *p2 = nullptr, *q2 = nullptr;   // float-pair p and A p (mixed forms)
     void *z = nullptr, *s = nullptr;       // bulk precision (double or float)
     double *rr = nullptr, *ur = nullptr;
+    double* rt = nullptr;                  // t = X^T r_r of the XX^T solve (float pair or double), n_r per slot
     float* ur32 = nullptr;
     double* partials = nullptr;
     SolveScalars* S = nullptr;             // nullptr: no early exit (single steps)

@@ -1556,6 +1556,19 @@ __device__ __forceinline__ void coarse_gemv_item(const DevMesh* __restrict__ mes
     const int lane = threadIdx.x & 31;
     const int64_t i = (int64_t)w.begin + (threadIdx.x >> 5);
     if (i >= w.end) return;
+    if (M.xxt) {   // second XX^T pass: u_i = sum_k X_ik t_k
+        const double* t = V.rt + w.roff;
+        const double* xv = static_cast<const double*>(M.xr_val);
+        double s = 0.0;
+        for (int e = __ldg(&M.xr_ptr[i]) + lane, e1 = __ldg(&M.xr_ptr[i + 1]); e < e1; e += 32)
+            s = fma(__ldg(&xv[e]), __ldg(&t[__ldg(&M.xr_idx[e])]), s);
+        s = warp_sum(s);
+        if (lane == 0) {
+            urv[w.roff + i] = s;
+            if (ur32v) ur32v[w.roff + i] = (float)s;
+        }
+        return;
+    }
     const double* row = M.ar_inv + (size_t)i * nr;
     double s = 0.0;
     for (int64_t j = lane; j < nr; j += 32) s = fma(__ldg(&row[j]), __ldg(&rr[j]), s);
@@ -1588,6 +1601,39 @@ __device__ __forceinline__ void coarse_pair_item(const DevMesh* __restrict__ mes
     const int lane = threadIdx.x & 31;
     const int64_t i = (int64_t)w.begin + (threadIdx.x >> 5);
     if (i >= w.end) return;
+    if (M.xxt) {   // second XX^T pass: u_i = sum_k X_ik t_k, in float pairs
+        const float2* t = reinterpret_cast<const float2*>(V.rt) + w.roff;
+        const float2* xv = static_cast<const float2*>(M.xr_val);
+        float h = 0.0f, l = 0.0f;
+        const int e1 = __ldg(&M.xr_ptr[i + 1]);
+        for (int e0 = __ldg(&M.xr_ptr[i]) + lane; e0 < e1; e0 += 128) {
+            // four entries per lane in flight
+            float2 a[4], b[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int e = e0 + 32 * k;
+                a[k] = e < e1 ? __ldg(&xv[e]) : make_float2(0.0f, 0.0f);
+                b[k] = e < e1 ? __ldg(&t[__ldg(&M.xr_idx[e])]) : make_float2(0.0f, 0.0f);
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                float ph, pl;
+                pair_mul(a[k].x, a[k].y, b[k].x, b[k].y, ph, pl);
+                pair_acc(h, l, ph, pl);
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float oh = __shfl_xor_sync(0xffffffffu, h, o);
+            const float ol = __shfl_xor_sync(0xffffffffu, l, o);
+            pair_acc(h, l, oh, ol);
+        }
+        if (lane == 0) {
+            if (urv) urv[w.roff + i] = (double)h + (double)l;
+            if (ur32v) ur32v[w.roff + i] = __fadd_rn(h, l);
+        }
+        return;
+    }
     // the row as 16-byte groups of two entries; four groups per lane in flight
     const float4* row = reinterpret_cast<const float4*>(M.ar_inv2 + (size_t)i * M.nr2);
     const int64_t ng = M.nr2 / 2;
@@ -1631,6 +1677,69 @@ __global__ void __launch_bounds__(kBlock) coarse_pair_kernel(const DevMesh* __re
     const Work w_ = work[blockIdx.x];
     pdl_wait();
     coarse_pair_item(meshes, w_, V, rr2v, urv, ur32v);
+}
+
+// First XX^T pass (Sec. 2): t = X^T r_r.  One warp per segment of at most
+// kXxtSeg entries of one column x_k of X (long columns are split); the
+// segment's partial dot product x_k . r_r is added to t_k, which is zero on
+// entry: a float64 atomic (FP64 form), or, in the mixed forms, float pairs
+// whose high add's exact rounding error goes into the low word.
+template <bool kPair>
+__device__ __forceinline__ void xxt_seg_item(const DevMesh* __restrict__ meshes, const Work& w, Vecs V,
+                                             const double* __restrict__ rrv) {
+    CGS_ITEM_PROLOGUE();
+    const int64_t sidx = (int64_t)w.begin + (threadIdx.x >> 5);
+    if (sidx >= w.end) return;   // whole warps leave
+    const int lane = threadIdx.x & 31;
+    const int4 sg = __ldg(&M.xs_seg[sidx]);   // column, begin, end
+    if (kPair) {
+        const float2* r = reinterpret_cast<const float2*>(rrv) + w.roff;
+        const float2* xv = static_cast<const float2*>(M.xc_val);
+        float h = 0.0f, l = 0.0f;
+        for (int e0 = sg.y + lane; e0 < sg.z; e0 += 128) {
+            float2 a[4], b[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int e = e0 + 32 * k;
+                a[k] = e < sg.z ? __ldg(&xv[e]) : make_float2(0.0f, 0.0f);
+                b[k] = e < sg.z ? __ldg(&r[__ldg(&M.xc_idx[e])]) : make_float2(0.0f, 0.0f);
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                float ph, pl;
+                pair_mul(a[k].x, a[k].y, b[k].x, b[k].y, ph, pl);
+                pair_acc(h, l, ph, pl);
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float oh = __shfl_xor_sync(0xffffffffu, h, o);
+            const float ol = __shfl_xor_sync(0xffffffffu, l, o);
+            pair_acc(h, l, oh, ol);
+        }
+        if (lane == 0) {
+            float* t = reinterpret_cast<float*>(reinterpret_cast<float2*>(V.rt) + w.roff + sg.x);
+            const float old = atomicAdd(t, h);
+            float sum, err;
+            two_sum(old, h, sum, err);
+            atomicAdd(t + 1, __fadd_rn(err, l));
+        }
+    } else {
+        const double* r = rrv + w.roff;
+        const double* xv = static_cast<const double*>(M.xc_val);
+        double acc = 0.0;
+        for (int e = sg.y + lane; e < sg.z; e += 32) acc = fma(__ldg(&xv[e]), __ldg(&r[__ldg(&M.xc_idx[e])]), acc);
+        acc = warp_sum(acc);
+        if (lane == 0) atomicAdd(&V.rt[w.roff + sg.x], acc);
+    }
+}
+template <bool kPair>
+__global__ void __launch_bounds__(32 * kRowChunk) xxt_seg_kernel(const DevMesh* __restrict__ meshes,
+                                                                 const Work* __restrict__ work, Vecs V,
+                                                                 const double* __restrict__ rrv) {
+    const Work w_ = work[blockIdx.x];
+    pdl_wait();
+    xxt_seg_item<kPair>(meshes, w_, V, rrv);
 }
 
 // ---------------------------------------------------------------------------
@@ -1703,7 +1812,10 @@ __global__ void __launch_bounds__(kBlock) precond_prep_kernel(const DevMesh* __r
     // this block's share of r_r
     const int64_t chunk = (M.nr + w.count - 1) / w.count;
     const int64_t r0 = (int64_t)w.idx * chunk, r1 = min((int64_t)M.nr, r0 + chunk);
-    for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) V.rr[w.roff + i] = 0.0;
+    for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+        V.rr[w.roff + i] = 0.0;
+        if (M.xxt) V.rt[w.roff + i] = 0.0;   // t = X^T r_r accumulates by segments
+    }
 }
 
 // p = z (and its float pair p2 when the mixed operator needs it), rho = r.z.
@@ -1758,7 +1870,10 @@ __device__ __forceinline__ void pcg_update_xr_item(const DevMesh* __restrict__ m
     }
     const int64_t chunk = (M.nr + w.count - 1) / w.count;
     const int64_t r0 = (int64_t)w.idx * chunk, r1 = min((int64_t)M.nr, r0 + chunk);
-    for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) V.rr[w.roff + i] = 0.0;
+    for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+        V.rr[w.roff + i] = 0.0;
+        if (M.xxt) V.rt[w.roff + i] = 0.0;   // t = X^T r_r accumulates by segments
+    }
     double val[1] = {acc}, tot[1];
     pdl_trigger();   // the successor may launch during the reduction tail
     if (slot_sum<1>(val, V.partials + w.poff, w.idx, w.count, &S->ticket[2], tot) && threadIdx.x == 0) {
@@ -1915,7 +2030,10 @@ __global__ void __launch_bounds__(kBlock) precond_prep_pair_kernel(const DevMesh
     }
     const int64_t chunk = (M.nr + w.count - 1) / w.count;
     const int64_t r0 = (int64_t)w.idx * chunk, r1 = min((int64_t)M.nr, r0 + chunk);
-    for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) V.rr[w.roff + i] = 0.0;
+    for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+        V.rr[w.roff + i] = 0.0;
+        if (M.xxt) V.rt[w.roff + i] = 0.0;   // t = X^T r_r accumulates by segments
+    }
 }
 
 // p = z, rho = r.z.
@@ -1990,7 +2108,10 @@ __device__ __forceinline__ void pcg_update_xr_pair_item(const DevMesh* __restric
     }
     const int64_t chunk = (M.nr + w.count - 1) / w.count;
     const int64_t r0 = (int64_t)w.idx * chunk, r1 = min((int64_t)M.nr, r0 + chunk);
-    for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) V.rr[w.roff + i] = 0.0;
+    for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+        V.rr[w.roff + i] = 0.0;
+        if (M.xxt) V.rt[w.roff + i] = 0.0;   // t = X^T r_r accumulates by segments
+    }
     float vh[1] = {h}, vl[1] = {l};
     double tot[1];
     pdl_trigger();   // the successor may launch during the reduction tail
@@ -2455,6 +2576,17 @@ void launch_coarse(const Plan& P, const Vecs& V, const double* rr, double* ur, f
                ur, ur32);
 }
 
+bool launch_xxt_pass1(const Plan& P, const Vecs& V, bool pair, const double* rr, cudaStream_t st) {
+    if (!P.nwork[kWorkXSeg]) return false;
+    if (pair)
+        launch_pdl(P.pdl, xxt_seg_kernel<true>, P.nwork[kWorkXSeg], 32 * kRowChunk, 0, st, P.meshes,
+                   P.work[kWorkXSeg], V, rr);
+    else
+        launch_pdl(P.pdl, xxt_seg_kernel<false>, P.nwork[kWorkXSeg], 32 * kRowChunk, 0, st, P.meshes,
+                   P.work[kWorkXSeg], V, rr);
+    return true;
+}
+
 void launch_coarse_pair(const Plan& P, const Vecs& V, const float2* rr2, double* ur, float* ur32, cudaStream_t st) {
     if (!P.nwork[kWorkRow]) return;
     launch_pdl(P.pdl, coarse_pair_kernel, P.nwork[kWorkRow], 32 * kRowChunk, 0, st, P.meshes, P.work[kWorkRow], V, rr2,
@@ -2619,6 +2751,7 @@ void append_mesh_work(std::vector<Work> (&tabs)[kWorkKinds], int mesh, int slot,
         add(kWorkPack, z.n_pack, sch.pack_chunk);
     add(kWorkBox, z.nvb, sch.box_chunk);
     if (z.nr > 0) add(kWorkBoxEnt, z.nrng, kBlock / 32);
+    if (z.nxseg > 0) add(kWorkXSeg, z.nxseg, kRowChunk);
 }
 
 int64_t mesh_partial_slots(const MeshSizes& z, const Schedule& sch) {

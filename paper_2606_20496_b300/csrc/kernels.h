@@ -32,6 +32,11 @@ void launch_restrict(const Plan& P, const Vecs& V, bool fp64, const void* s, boo
 bool launch_interp_add(const Plan& P, const Vecs& V, bool fp64, const double* ur, const float* ur32, void* z,
                        bool dots, const cudaGraphConditionalHandle* cond, cudaStream_t st);
 void launch_coarse(const Plan& P, const Vecs& V, const double* rr, double* ur, float* ur32, cudaStream_t st);
+// First pass of the XX^T reduced solve for the plan's XX^T meshes: V.rt =
+// X^T r_r (zero on entry; float pairs when `pair`).  Returns whether it
+// launched (no XX^T mesh: nothing to do).  launch_coarse / launch_coarse_pair
+// then finish every mesh: the dense product, or u_r = X V.rt.
+bool launch_xxt_pass1(const Plan& P, const Vecs& V, bool pair, const double* rr, cudaStream_t st);
 void launch_coarse_pair(const Plan& P, const Vecs& V, const float2* rr2, double* ur, float* ur32, cudaStream_t st);
 void launch_split_pair(int64_t n, const double* a, float2* b, cudaStream_t st);
 
@@ -75,6 +80,7 @@ void launch_fill_f(int64_t n, float* a, float v, cudaStream_t st);
 // Work tables of one mesh as slot `slot` (host side, appended to tabs).
 struct MeshSizes {
     int64_t nv, ne, ntiles, n_sub, nr, n_pack, nvb, nrng, n_rpack;   // n_sub: warp-kernel subdomains
+    int64_t nxseg;                                                   // XX^T pass-1 segments (0: dense)
 };
 // Block sizes of the range-parallel kernels: vertices per block (vector
 // kernels) and subdomains per block (local solves), and how the tiled

@@ -76,6 +76,7 @@ extern "C" cgs_status cgs_apply_preconditioner_noalloc(cgs_mesh* mesh, const dou
     V.s = p + (size_t)8 * CGS_NOALLOC_MAX_NV;          // nv entries of 8 bytes
     V.rr = reinterpret_cast<double*>(p + (size_t)16 * CGS_NOALLOC_MAX_NV);
     V.ur = V.rr + CGS_NOALLOC_MAX_NR;
+    V.rt = V.ur + CGS_NOALLOC_MAX_NR;                  // zeroed with r_r by the prep kernel
     const cgs_precision prec = mesh_prec(mesh);
     const bool f64 = prec == CGS_FP64;
     // z = 0, s = r in the bulk precision, r_r = 0
@@ -93,12 +94,14 @@ extern "C" cgs_status cgs_apply_preconditioner_noalloc(cgs_mesh* mesh, const dou
     }
     if (d.nr && f64) {
         launch_restrict(P, V, true, V.s, true, V.rr, false, st);
+        launch_xxt_pass1(P, V, false, V.rr, st);   // XX^T meshes only
         launch_coarse(P, V, V.rr, V.ur, nullptr, st);
         launch_interp_add(P, V, true, V.ur, nullptr, V.z, false, nullptr, st);
     } else if (d.nr) {
         // r_r as float pairs, the pair product writes u_r rounded to float
         float* ur32 = reinterpret_cast<float*>(V.ur);
         launch_restrict(P, V, false, V.s, false, V.rr, true, st);
+        launch_xxt_pass1(P, V, true, V.rr, st);    // XX^T meshes only
         launch_coarse_pair(P, V, reinterpret_cast<const float2*>(V.rr), nullptr, ur32, st);
         launch_interp_add(P, V, false, nullptr, ur32, V.z, false, nullptr, st);
     }

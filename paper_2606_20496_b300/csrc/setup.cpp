@@ -24,6 +24,7 @@
 // at d*m + i for d = 0..floor(m/2): m(m+1)/2 entries for odd m (m/2 more for
 // even m), and lane i of a warp reads diagonal d at i and at (i-d) mod m.
 #include <algorithm>
+#include <array>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -99,11 +100,10 @@ inline double dot(const double* a, const double* b, int n) {
     return s;
 }
 
-// Explicit inverse of an SPD n x n row-major matrix `a` (destroyed) through
-// its Cholesky factor: a = L L^T, Y = L^{-1}, inv = Y^T Y.  Returns false if
-// a pivot is not positive.  `threads` > 1 parallelises the three O(n^3/6)
-// sweeps.
-bool spd_inverse(double* a, int n, double* inv, int threads) {
+// Cholesky factor of an SPD n x n row-major matrix in place: a = L L^T, L in
+// the lower triangle.  Returns false if a pivot is not positive.  `threads`
+// > 1 parallelises the row updates.
+bool cholesky_lower(double* a, int n, int threads) {
     for (int j = 0; j < n; ++j) {
         double* Lj = a + (size_t)j * n;
         const double d = Lj[j] - dot(Lj, Lj, j);
@@ -116,7 +116,13 @@ bool spd_inverse(double* a, int n, double* inv, int threads) {
             Li[j] = (Li[j] - dot(Li, Lj, j)) / ljj;
         }
     }
-    // columns of Y = L^{-1}, column c stored contiguously in Y[c*n + i], i >= c
+    return true;
+}
+
+// Y = L^{-1} of the factor in the lower triangle of `a`, column c stored
+// contiguously in Y[c*n + i] for i >= c (zero above).  Entries that are
+// structurally zero come out as exact zeros (sums of products with zeros).
+std::vector<double> lower_inverse(const double* a, int n, int threads) {
     std::vector<double> Y((size_t)n * n, 0.0);
 #pragma omp parallel for schedule(dynamic, 8) num_threads(threads) if (threads > 1)
     for (int c = 0; c < n; ++c) {
@@ -129,6 +135,15 @@ bool spd_inverse(double* a, int n, double* inv, int threads) {
             y[i] = -s / Li[i];
         }
     }
+    return Y;
+}
+
+// Explicit inverse of an SPD n x n row-major matrix `a` (destroyed) through
+// its Cholesky factor: a = L L^T, Y = L^{-1}, inv = Y^T Y.  Returns false if
+// a pivot is not positive.
+bool spd_inverse(double* a, int n, double* inv, int threads) {
+    if (!cholesky_lower(a, n, threads)) return false;
+    const std::vector<double> Y = lower_inverse(a, n, threads);
     // inv[i][j] = sum_{k >= max(i,j)} Y[k][i] Y[k][j]
 #pragma omp parallel for schedule(dynamic, 8) num_threads(threads) if (threads > 1)
     for (int i = 0; i < n; ++i) {
@@ -140,6 +155,99 @@ bool spd_inverse(double* a, int n, double* inv, int threads) {
             inv[(size_t)j * n + i] = v;
         }
     }
+    return true;
+}
+
+// Nested-dissection order of lattice points (the active box vertices): a set
+// of more than kNdLeaf points is split at the median coordinate plane of its
+// longest extent; the points below the plane are ordered first, then those
+// above (recursively), then the plane itself, which separates the two
+// halves of a box-lattice stencil.  Appends to `out`.
+constexpr size_t kNdLeaf = 8;
+void nd_order(const std::vector<std::array<int, 3>>& c, std::vector<int32_t> ids, std::vector<int32_t>& out) {
+    if (ids.size() <= kNdLeaf) {
+        out.insert(out.end(), ids.begin(), ids.end());
+        return;
+    }
+    int lo[3] = {INT32_MAX, INT32_MAX, INT32_MAX}, hi[3] = {INT32_MIN, INT32_MIN, INT32_MIN};
+    for (int32_t i : ids)
+        for (int d = 0; d < 3; ++d) {
+            lo[d] = std::min(lo[d], c[i][d]);
+            hi[d] = std::max(hi[d], c[i][d]);
+        }
+    int ax = 0;
+    for (int d = 1; d < 3; ++d)
+        if (hi[d] - lo[d] > hi[ax] - lo[ax]) ax = d;
+    if (hi[ax] == lo[ax]) {   // a single point repeated cannot occur; keep the order
+        out.insert(out.end(), ids.begin(), ids.end());
+        return;
+    }
+    // the median of the distinct plane coordinates
+    std::vector<int> planes;
+    for (int32_t i : ids) planes.push_back(c[i][ax]);
+    std::sort(planes.begin(), planes.end());
+    planes.erase(std::unique(planes.begin(), planes.end()), planes.end());
+    const int mid = planes[planes.size() / 2];
+    std::vector<int32_t> below, above, sep;
+    for (int32_t i : ids) (c[i][ax] < mid ? below : c[i][ax] > mid ? above : sep).push_back(i);
+    nd_order(c, std::move(below), out);
+    nd_order(c, std::move(above), out);
+    out.insert(out.end(), sep.begin(), sep.end());
+}
+
+// XX^T factors of the SPD reduced matrix `Ar` (row-major nr x nr, destroyed):
+// in the nested-dissection order P, P A_r P^T = L L^T and X~ = L^{-T} has
+// A-conjugate columns (x~_i^T (P A_r P^T) x~_j = delta_ij); X = P^T X~ gives
+// A_r^{-1} = X X^T.  Column k of X (nested-dissection position k) is
+// supported on k and the positions before it in its dissection subtree.
+bool xxt_factor(const double* Ar, int64_t nr, const std::vector<int32_t>& perm, int threads, HostSetup& S) {
+    const int n = (int)nr;
+    std::vector<double> a((size_t)n * n);
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) a[(size_t)i * n + j] = Ar[(size_t)perm[i] * n + perm[j]];
+    if (!cholesky_lower(a.data(), n, threads)) return false;
+    const std::vector<double> Y = lower_inverse(a.data(), n, threads);
+    // X~[c][k] = Y[k][c] = Y[c*n + k] (k >= c); row of X = perm[c]
+    S.xc_ptr.assign(n + 1, 0);
+    S.xr_ptr.assign(n + 1, 0);
+    for (int c = 0; c < n; ++c)
+        for (int k = c; k < n; ++k)
+            if (Y[(size_t)c * n + k] != 0.0) {
+                S.xc_ptr[k + 1]++;
+                S.xr_ptr[perm[c] + 1]++;
+            }
+    for (int k = 0; k < n; ++k) {
+        S.xc_ptr[k + 1] += S.xc_ptr[k];
+        S.xr_ptr[k + 1] += S.xr_ptr[k];
+    }
+    const size_t nnz = (size_t)S.xc_ptr[n];
+    S.xc_idx.assign(nnz, 0);
+    S.xc_val.assign(nnz, 0.0);
+    S.xr_idx.assign(nnz, 0);
+    S.xr_val.assign(nnz, 0.0);
+    // columns in ascending row order: walk the reduced rows in order
+    std::vector<int32_t> inv(n);
+    for (int c = 0; c < n; ++c) inv[perm[c]] = c;
+    std::vector<int32_t> fc(S.xc_ptr.begin(), S.xc_ptr.end() - 1), fr(S.xr_ptr.begin(), S.xr_ptr.end() - 1);
+    for (int row = 0; row < n; ++row) {
+        const int c = inv[row];
+        for (int k = c; k < n; ++k) {
+            const double v = Y[(size_t)c * n + k];
+            if (v == 0.0) continue;
+            S.xc_idx[fc[k]] = (uint16_t)row;
+            S.xc_val[fc[k]++] = v;
+            S.xr_idx[fr[row]] = (uint16_t)k;   // ascending k within the row
+            S.xr_val[fr[row]++] = v;
+        }
+    }
+    S.xs_seg.clear();
+    for (int k = 0; k < n; ++k)
+        for (int32_t b = S.xc_ptr[k]; b < S.xc_ptr[k + 1]; b += kXxtSeg) {
+            S.xs_seg.push_back(k);
+            S.xs_seg.push_back(b);
+            S.xs_seg.push_back(std::min(S.xc_ptr[k + 1], b + kXxtSeg));
+            S.xs_seg.push_back(0);
+        }
     return true;
 }
 
@@ -170,6 +278,10 @@ cgs_status host_setup(const double* xyz, int64_t nv, const int32_t* conn, int64_
         }
     if (prm.overlap_layers < 0 || !(prm.box_margin >= 0.0)) {
         err = "negative overlap or margin";
+        return CGS_ERR_INVALID_ARG;
+    }
+    if (prm.coarse_solver < CGS_COARSE_AUTO || prm.coarse_solver > CGS_COARSE_XXT) {
+        err = "coarse_solver must be CGS_COARSE_AUTO, _DENSE or _XXT";
         return CGS_ERR_INVALID_ARG;
     }
     for (int64_t i = 0; i < ne * 8; ++i)
@@ -678,10 +790,37 @@ cgs_status host_setup(const double* xyz, int64_t nv, const int32_t* conn, int64_
                     if (b >= 0) Ar[(size_t)a * nr + b] += Kc[(size_t)c * 64 + m * 8 + n];
                 }
             }
-        S.ar_inv.assign((size_t)nr * nr, 0.0);
-        if (!spd_inverse(Ar.data(), (int)nr, S.ar_inv.data(), nthreads)) {
-            err = "reduced matrix A_r is not SPD";
-            return CGS_ERR_NOT_SPD;
+        const int want = prm.coarse_solver == CGS_COARSE_AUTO
+                             ? (nr > CGS_COARSE_AUTO_XXT_NR ? CGS_COARSE_XXT : CGS_COARSE_DENSE)
+                             : (int)prm.coarse_solver;
+        if (want == CGS_COARSE_XXT) {
+            if (nr > 65535) {
+                err = "XX^T reduced solver needs n_r <= 65535 (16-bit indices)";
+                return CGS_ERR_INVALID_ARG;
+            }
+            // lattice coordinates of the active box vertices
+            const int64_t nbx = bx + 1, nby = by + 1;
+            std::vector<std::array<int, 3>> lc(nr);
+            for (int64_t a = 0; a < nr; ++a) {
+                const int64_t g = S.box_active[a];
+                lc[a] = {(int)(g % nbx), (int)((g / nbx) % nby), (int)(g / (nbx * nby))};
+            }
+            std::vector<int32_t> all(nr);
+            std::iota(all.begin(), all.end(), 0);
+            S.nd_perm.clear();
+            nd_order(lc, std::move(all), S.nd_perm);
+            if (!xxt_factor(Ar.data(), nr, S.nd_perm, nthreads, S)) {
+                err = "reduced matrix A_r is not SPD";
+                return CGS_ERR_NOT_SPD;
+            }
+            S.coarse = CGS_COARSE_XXT;
+        } else {
+            S.ar_inv.assign((size_t)nr * nr, 0.0);
+            if (!spd_inverse(Ar.data(), (int)nr, S.ar_inv.data(), nthreads)) {
+                err = "reduced matrix A_r is not SPD";
+                return CGS_ERR_NOT_SPD;
+            }
+            S.coarse = CGS_COARSE_DENSE;
         }
     }
 

@@ -36,6 +36,8 @@ def main():
     ap.add_argument("--workload", default="cube32")
     ap.add_argument("--prec", default="fp32", choices=list(cgs.PREC))
     ap.add_argument("--form", default="hybrid", choices=list(cgs.FORM))
+    ap.add_argument("--coarse", default="auto", choices=list(cgs.COARSE),
+                    help="reduced solver: auto (XX^T above 1500 unknowns), dense or xxt")
     ap.add_argument("--solves", type=int, default=2)
     ap.add_argument("--rtol", type=float, default=1e-8)
     ap.add_argument("--maxit", type=int, default=1000)
@@ -60,7 +62,7 @@ def main():
     m, b = load_workload(args.workload)
     ctx = cgs.cgs_create(0)
     t0 = time.perf_counter()
-    h = cgs.Mesh(ctx, m.xyz, m.conn, part=m.part, boxes=m.boxes, prec=args.prec, form=args.form)
+    h = cgs.Mesh(ctx, m.xyz, m.conn, part=m.part, boxes=m.boxes, prec=args.prec, form=args.form, coarse=args.coarse)
     setup_s = time.perf_counter() - t0
     if args.tune:
         cgs.cgs_mesh_tune(h.handle)
@@ -92,12 +94,14 @@ def main():
            "ne": h.info["ne"], "n_sub": h.info["n_sub"], "n_r": h.info["n_r"],
            "sum_sub_dofs": info["sum_sub_dofs"], "sum_sub_tri": info["sum_sub_tri"],
            "n_box_entries": info["n_box_entries"],
+           "coarse_solver": {v: k for k, v in cgs.COARSE.items()}[info["coarse_solver"]], "xxt_nnz": info["xxt_nnz"],
            "footprint_mb": h.info["footprint_bytes"] / 2 ** 20, "setup_s": setup_s, "iters": its,
            "relres": rels, "ms_per_solve": float(np.mean(ms[1:] if len(ms) > 1 else ms))}
     if args.profile:
         out["profile"] = cgs.cgs_profile_read(h.handle)
     if args.compare_fp64 and args.prec != "fp64":
-        with cgs.Mesh(ctx, m.xyz, m.conn, part=m.part, boxes=m.boxes, prec="fp64", form=args.form) as h64:
+        with cgs.Mesh(ctx, m.xyz, m.conn, part=m.part, boxes=m.boxes, prec="fp64", form=args.form,
+                      coarse=args.coarse) as h64:
             x64 = torch.empty_like(bd)
             st, it, rel = cgs.cgs_solve(h64.handle, bd, x64, rtol=args.rtol, maxit=args.maxit)
             torch.cuda.synchronize()

@@ -426,3 +426,79 @@ def test_flexible_cg_equals_textbook_pcg_for_symmetric_preconditioner():
             p = z + (rz_new / rz) * p
             rz = rz_new
         np.testing.assert_allclose(x_f, x, rtol=1e-9, atol=1e-9 * np.abs(x).max())
+
+
+# --------------------------------------------------------------------------
+# XX^T reduced solver (Sec. 2: A_c-conjugate sparse basis, A_c^{-1} = X X^T)
+# --------------------------------------------------------------------------
+
+def _lattice_27(n):
+    """Interior points of an (n+1)^3 unit box lattice and the assembled Q1
+    27-point stencil on them (centre 8/3, face 0, edge -1/6, corner -1/12,
+    the closed form of the unit-cube element assembled)."""
+    pts = np.array([(i, j, k) for k in range(1, n) for j in range(1, n) for i in range(1, n)])
+    index = {tuple(p): a for a, p in enumerate(pts)}
+    w = {0: 8.0 / 3.0, 1: 0.0, 2: -1.0 / 6.0, 3: -1.0 / 12.0}
+    A = np.zeros((len(pts), len(pts)))
+    for a, p in enumerate(pts):
+        for d in np.ndindex(3, 3, 3):
+            q = tuple(p + np.array(d) - 1)
+            if q in index:
+                A[a, index[q]] = w[int(np.abs(np.array(d) - 1).sum())]
+    return pts, A
+
+
+@pytest.mark.parametrize("wl", ["cube8", "ragged"])
+def test_xxt_basis_is_conjugate_and_solves(wl):
+    if wl == "cube8":
+        m, _ = meshes.workload_cube8()
+    else:
+        m = meshes.cube((5, 3, 7), perturb=0.15, seed=3, boxes=(3, 2, 3), name="ragged")
+    P = O.Problem(m.xyz, m.conn, m.part, m.boxes)
+    X = P.xxt_factor()
+    assert np.abs(X.T @ P.Ar @ X - np.eye(P.nr)).max() <= 1e-12
+    b = np.random.default_rng(9).standard_normal(P.nr)
+    ref = np.linalg.solve(P.Ar, b)                   # dense LU, not the oracle's Cholesky
+    assert np.abs(P.coarse_solve_xxt(b) - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+def test_xxt_natural_order_on_a_chain_is_inverse_cholesky_transpose():
+    """Gram-Schmidt of the unit vectors in the A inner product, in natural
+    order, is the textbook L^{-T} of A = L L^T (a tridiagonal chain)."""
+    n = 40
+    A = 2.0 * np.eye(n) - np.eye(n, k=1) - np.eye(n, k=-1) + 0.01 * np.eye(n)
+    X = O.xxt_basis(A, np.arange(n))
+    L = np.linalg.cholesky(A)
+    assert np.allclose(X, np.linalg.inv(L).T, rtol=0, atol=1e-12)
+
+
+def test_nested_dissection_separator_decouples_the_halves():
+    """The first cut is a plane; vectors of the points below it vanish exactly
+    on the points above it and on the plane, and vice versa below."""
+    pts, A = _lattice_27(8)
+    order = O.nested_dissection(pts)
+    assert sorted(order.tolist()) == list(range(len(pts)))
+    X = O.xxt_basis(A, order)
+    # the top separator: the trailing points that share one coordinate plane
+    ax = int(np.argmax(pts.max(0) - pts.min(0)))
+    mid = np.unique(pts[:, ax])[len(np.unique(pts[:, ax])) // 2]
+    below = np.flatnonzero(pts[:, ax] < mid)
+    above = np.flatnonzero(pts[:, ax] > mid)
+    sep = np.flatnonzero(pts[:, ax] == mid)
+    nb, na = len(below), len(above)
+    assert set(order[:nb]) == set(below) and set(order[nb:nb + na]) == set(above)
+    assert set(order[nb + na:]) == set(sep)
+    assert np.all(X[np.concatenate([above, sep])][:, :nb] == 0.0)
+    assert np.all(X[np.concatenate([below, sep])][:, nb:nb + na] == 0.0)
+
+
+def test_nested_dissection_keeps_x_sparse():
+    """On a 9^3-point lattice the conjugate basis in nested-dissection order
+    has under a quarter of the entries of a dense matrix; in lexicographic
+    order it fills the whole upper triangle (L^{-T} of a banded matrix)."""
+    pts, A = _lattice_27(10)
+    n = len(pts)
+    nd = np.count_nonzero(O.xxt_basis(A, O.nested_dissection(pts)))
+    lex = np.count_nonzero(O.xxt_basis(A, np.arange(n)))
+    assert nd < 0.25 * n * n
+    assert lex > 0.45 * n * n

@@ -36,12 +36,13 @@ def ctx():
 TOL = {"fp64": 1e-11, "fp32": 1e-5, "fp16": 1e-5}
 
 
-@pytest.mark.parametrize("prec,form", [("fp64", "hybrid"), ("fp64", "additive"), ("fp32", "hybrid"),
-                                       ("fp16", "hybrid")])
-def test_noalloc_matches_regular_preconditioner_twice(ctx, prec, form):
+@pytest.mark.parametrize("prec,form,coarse", [("fp64", "hybrid", "auto"), ("fp64", "additive", "auto"),
+                                              ("fp32", "hybrid", "auto"), ("fp16", "hybrid", "auto"),
+                                              ("fp64", "hybrid", "xxt"), ("fp32", "additive", "xxt")])
+def test_noalloc_matches_regular_preconditioner_twice(ctx, prec, form, coarse):
     m, _ = meshes.workload_cube32()
     rng = np.random.default_rng(21)
-    with cgs.Mesh(ctx, m.xyz, m.conn, part=m.part, boxes=m.boxes, prec=prec, form=form) as h:
+    with cgs.Mesh(ctx, m.xyz, m.conn, part=m.part, boxes=m.boxes, prec=prec, form=form, coarse=coarse) as h:
         for call in range(2):       # two calls in a row: the shared array keeps old contents
             r = torch.as_tensor(rng.standard_normal(m.nv), dtype=torch.float64, device="cuda")
             z_ref = torch.empty_like(r)
