@@ -1545,6 +1545,58 @@ __global__ void __launch_bounds__(kBlock, 2) local_restrict_kernel(const DevMesh
         local_lane_item<Stor>(meshes, w_, V, s, z, 0);
 }
 
+// sum over entries [e, e1) of val[e] * x[idx[e]] by one warp: each lane
+// takes every 32nd entry, eight at a time with all index loads issued first,
+// then the values and the gathers (two dependent round trips per eight).
+// Float pairs: error-free products, pair accumulation, pair warp sum.
+__device__ __forceinline__ void gather_dot_pair(const float2* __restrict__ val, const uint16_t* __restrict__ idx,
+                                                const float2* __restrict__ x, int e, int e1, int lane, float& h,
+                                                float& l) {
+    h = 0.0f;
+    l = 0.0f;
+    for (int e0 = e + lane; e0 < e1; e0 += 256) {
+        int j[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) j[k] = e0 + 32 * k < e1 ? (int)__ldg(&idx[e0 + 32 * k]) : -1;
+        float2 a[8], b[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            a[k] = j[k] >= 0 ? __ldg(&val[e0 + 32 * k]) : make_float2(0.0f, 0.0f);
+            b[k] = j[k] >= 0 ? __ldg(&x[j[k]]) : make_float2(0.0f, 0.0f);
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            float ph, pl;
+            pair_mul(a[k].x, a[k].y, b[k].x, b[k].y, ph, pl);
+            pair_acc(h, l, ph, pl);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float oh = __shfl_xor_sync(0xffffffffu, h, o);
+        const float ol = __shfl_xor_sync(0xffffffffu, l, o);
+        pair_acc(h, l, oh, ol);
+    }
+}
+__device__ __forceinline__ double gather_dot64(const double* __restrict__ val, const uint16_t* __restrict__ idx,
+                                               const double* __restrict__ x, int e, int e1, int lane) {
+    double s = 0.0;
+    for (int e0 = e + lane; e0 < e1; e0 += 256) {
+        int j[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) j[k] = e0 + 32 * k < e1 ? (int)__ldg(&idx[e0 + 32 * k]) : -1;
+        double a[8], b[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            a[k] = j[k] >= 0 ? __ldg(&val[e0 + 32 * k]) : 0.0;
+            b[k] = j[k] >= 0 ? __ldg(&x[j[k]]) : 0.0;
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) s = fma(a[k], b[k], s);
+    }
+    return warp_sum(s);
+}
+
 // u_r = A_r^{-1} r_r: one warp per row of the full symmetric inverse; also a
 // float copy of u_r for the float interpolation (no conversions per element).
 __device__ __forceinline__ void coarse_gemv_item(const DevMesh* __restrict__ meshes, const Work& w, Vecs V,
@@ -1557,12 +1609,8 @@ __device__ __forceinline__ void coarse_gemv_item(const DevMesh* __restrict__ mes
     const int64_t i = (int64_t)w.begin + (threadIdx.x >> 5);
     if (i >= w.end) return;
     if (M.xxt) {   // second XX^T pass: u_i = sum_k X_ik t_k
-        const double* t = V.rt + w.roff;
-        const double* xv = static_cast<const double*>(M.xr_val);
-        double s = 0.0;
-        for (int e = __ldg(&M.xr_ptr[i]) + lane, e1 = __ldg(&M.xr_ptr[i + 1]); e < e1; e += 32)
-            s = fma(__ldg(&xv[e]), __ldg(&t[__ldg(&M.xr_idx[e])]), s);
-        s = warp_sum(s);
+        const double s = gather_dot64(static_cast<const double*>(M.xr_val), M.xr_idx, V.rt + w.roff,
+                                      __ldg(&M.xr_ptr[i]), __ldg(&M.xr_ptr[i + 1]), lane);
         if (lane == 0) {
             urv[w.roff + i] = s;
             if (ur32v) ur32v[w.roff + i] = (float)s;
@@ -1602,32 +1650,9 @@ __device__ __forceinline__ void coarse_pair_item(const DevMesh* __restrict__ mes
     const int64_t i = (int64_t)w.begin + (threadIdx.x >> 5);
     if (i >= w.end) return;
     if (M.xxt) {   // second XX^T pass: u_i = sum_k X_ik t_k, in float pairs
-        const float2* t = reinterpret_cast<const float2*>(V.rt) + w.roff;
-        const float2* xv = static_cast<const float2*>(M.xr_val);
-        float h = 0.0f, l = 0.0f;
-        const int e1 = __ldg(&M.xr_ptr[i + 1]);
-        for (int e0 = __ldg(&M.xr_ptr[i]) + lane; e0 < e1; e0 += 128) {
-            // four entries per lane in flight
-            float2 a[4], b[4];
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const int e = e0 + 32 * k;
-                a[k] = e < e1 ? __ldg(&xv[e]) : make_float2(0.0f, 0.0f);
-                b[k] = e < e1 ? __ldg(&t[__ldg(&M.xr_idx[e])]) : make_float2(0.0f, 0.0f);
-            }
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                float ph, pl;
-                pair_mul(a[k].x, a[k].y, b[k].x, b[k].y, ph, pl);
-                pair_acc(h, l, ph, pl);
-            }
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const float oh = __shfl_xor_sync(0xffffffffu, h, o);
-            const float ol = __shfl_xor_sync(0xffffffffu, l, o);
-            pair_acc(h, l, oh, ol);
-        }
+        float h, l;
+        gather_dot_pair(static_cast<const float2*>(M.xr_val), M.xr_idx, reinterpret_cast<const float2*>(V.rt) + w.roff,
+                        __ldg(&M.xr_ptr[i]), __ldg(&M.xr_ptr[i + 1]), lane, h, l);
         if (lane == 0) {
             if (urv) urv[w.roff + i] = (double)h + (double)l;
             if (ur32v) ur32v[w.roff + i] = __fadd_rn(h, l);
@@ -1693,30 +1718,9 @@ __device__ __forceinline__ void xxt_seg_item(const DevMesh* __restrict__ meshes,
     const int lane = threadIdx.x & 31;
     const int4 sg = __ldg(&M.xs_seg[sidx]);   // column, begin, end
     if (kPair) {
-        const float2* r = reinterpret_cast<const float2*>(rrv) + w.roff;
-        const float2* xv = static_cast<const float2*>(M.xc_val);
-        float h = 0.0f, l = 0.0f;
-        for (int e0 = sg.y + lane; e0 < sg.z; e0 += 128) {
-            float2 a[4], b[4];
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const int e = e0 + 32 * k;
-                a[k] = e < sg.z ? __ldg(&xv[e]) : make_float2(0.0f, 0.0f);
-                b[k] = e < sg.z ? __ldg(&r[__ldg(&M.xc_idx[e])]) : make_float2(0.0f, 0.0f);
-            }
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                float ph, pl;
-                pair_mul(a[k].x, a[k].y, b[k].x, b[k].y, ph, pl);
-                pair_acc(h, l, ph, pl);
-            }
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const float oh = __shfl_xor_sync(0xffffffffu, h, o);
-            const float ol = __shfl_xor_sync(0xffffffffu, l, o);
-            pair_acc(h, l, oh, ol);
-        }
+        float h, l;
+        gather_dot_pair(static_cast<const float2*>(M.xc_val), M.xc_idx,
+                        reinterpret_cast<const float2*>(rrv) + w.roff, sg.y, sg.z, lane, h, l);
         if (lane == 0) {
             float* t = reinterpret_cast<float*>(reinterpret_cast<float2*>(V.rt) + w.roff + sg.x);
             const float old = atomicAdd(t, h);
@@ -1725,11 +1729,7 @@ __device__ __forceinline__ void xxt_seg_item(const DevMesh* __restrict__ meshes,
             atomicAdd(t + 1, __fadd_rn(err, l));
         }
     } else {
-        const double* r = rrv + w.roff;
-        const double* xv = static_cast<const double*>(M.xc_val);
-        double acc = 0.0;
-        for (int e = sg.y + lane; e < sg.z; e += 32) acc = fma(__ldg(&xv[e]), __ldg(&r[__ldg(&M.xc_idx[e])]), acc);
-        acc = warp_sum(acc);
+        const double acc = gather_dot64(static_cast<const double*>(M.xc_val), M.xc_idx, rrv + w.roff, sg.y, sg.z, lane);
         if (lane == 0) atomicAdd(&V.rt[w.roff + sg.x], acc);
     }
 }
