@@ -125,12 +125,16 @@ def algorithmic_bytes(info, prec, interp_cells=False):
     sb = 8 if prec == "fp64" else 4
     sl = {"fp64": 8, "fp32": 4, "fp16": 2}[prec]
     packed = info["_packed_entries"]
+    # reduced solve per launch: the dense inverse once, or one XX^T pass (X's
+    # 8-byte values and 2-byte indices once, r_r or t gathered, t or u_r out)
+    xnnz = info.get("xxt_nnz", 0)
+    coarse = xnnz * 10 + nr * 12 if info.get("coarse_solver") == 2 else nr * nr * 8 + nr * 12
     if prec == "fp64":
         return {
             "apply_A64": E * (36 * 8 + 32) + nv * (8 + 16),
             "local": packed * sl + sm * 4 + nv * (8 + 2 * sb + sb),
             "restrict": nb * 16 + nv * (32 + sb) + nr * 16,
-            "coarse": nr * nr * 8 + nr * 16,
+            "coarse": coarse + (nr * 4 if info.get("coarse_solver") != 2 else 0),
             "interp": (nb * 16 + nv * (32 + 2 * sb) + nr * 8) if interp_cells
             else nb * 16 + nv * (4 + 32 + 2 * sb + 16) + nr * 8,
             "pcg_xr": nv * (8 * 6 + 2 * sb),
@@ -151,7 +155,7 @@ def algorithmic_bytes(info, prec, interp_cells=False):
         # read (dots), q cleared
         "interp": (nb * 12 + nv * (16 + 2 * sb) + nr * 4) if interp_cells
         else nv * 8 + nb * 8 + nv * (16 + 2 * sb + 16 + 8) + nr * 4,
-        "coarse": nr * nr * 8 + nr * 12,
+        "coarse": coarse,
         # p, q, x, r read; p, x, r written; z read and cleared; s written
         "pcg_xr": nv * (8 * 7 + 3 * sb),
         # z, r and q read, q cleared
