@@ -24,6 +24,9 @@ A u = b, Sec. 3):
   nested-dissection order of the box lattice;
 * the preconditioners ASM (Eq. asm) and the hybrid ASM_1 + ASM_2 (Eqs. asm1,
   asm2);
+* repeated right-hand sides (Sec. 5, the projection onto prior solutions):
+  the start is the A-orthogonal best fit onto up to l earlier solutions and
+  the iteration solves for the change;
 * flexible preconditioned CG around them.
 
 Readings taken where the paper is silent or ambiguous (listed with the design
@@ -32,7 +35,8 @@ of vertex-sharing elements; R_p = free vertices whose elements all lie in the
 grown subdomain; W_ov = 1/multiplicity for the hybrid local step, no weight in
 the additive form; J^T (not J) in the coarse term; A_r by broken (cell-wise)
 assembly with Dirichlet rows of J_e zeroed; Polak-Ribiere beta; nested
-dissection by median coordinate planes of the longest extent.
+dissection by median coordinate planes of the longest extent; the projection
+basis restarts from the newest solution once it holds l vectors.
 
 Every function here is pinned by tests under ``tests/`` against closed forms,
 invariants or brute force; none is "parity unpinned".
@@ -396,6 +400,70 @@ def xxt_basis(A, order):
         x /= np.sqrt(x @ A @ x)
         X[:, k] = x
     return X
+
+
+class Projection:
+    """A-orthogonal projection onto prior solutions (Sec. 5: solve for the
+    change u - u_bar, u_bar = sum_j beta_j u^{m-j} the A-orthogonal best fit
+    onto l prior solutions).
+
+    Keeps an A-orthonormal basis x~_1..x~_k (k <= l) of the span of earlier
+    solutions, so the best fit of the new solution is u_bar = sum_j
+    (x~_j . b) x~_j (x~_j^T A u = x~_j . b).  After a solve, the new solution
+    is made A-orthogonal to the basis, scaled to unit A-norm and appended;
+    a full basis first restarts empty (reading: the paper does not say how
+    the l solutions are chosen; this keeps the newest one)."""
+
+    def __init__(self, apply_A, l: int):
+        self.apply_A, self.l = apply_A, int(l)
+        self.X = []          # x~_j
+        self.AX = []         # A x~_j
+
+    def start(self, b):
+        """(u_bar, b - A u_bar)."""
+        ubar = np.zeros_like(b)
+        bp = np.array(b, dtype=np.float64)
+        for x, ax in zip(self.X, self.AX):
+            c = float(x @ b)
+            ubar += c * x
+            bp -= c * ax
+        return ubar, bp
+
+    def add(self, u):
+        if len(self.X) >= self.l:
+            self.X, self.AX = [], []
+        Au = self.apply_A(u)
+        w, Aw = np.array(u, dtype=np.float64), Au.copy()
+        for x, ax in zip(self.X, self.AX):
+            e = float(x @ Au)                     # x~_j^T A u
+            w -= e * x
+            Aw -= e * ax
+        nrm2 = float(w @ Aw)
+        if nrm2 > 1e-28 * max(float(u @ Au), 1e-300):
+            self.X.append(w / np.sqrt(nrm2))
+            self.AX.append(Aw / np.sqrt(nrm2))
+
+
+def solve_projected(P, bs, l: int, rtol: float = 1e-8, maxit: int = 500, form: str = "hybrid"):
+    """Solve A u = b for each b of the sequence with the projection onto up
+    to l prior solutions.  The correction solve stops when its residual
+    (which is b - A u) is below rtol ||b||.  Returns a list of (x, iters,
+    true relres, u_bar)."""
+    proj = Projection(P.apply_A, l)
+    out = []
+    for b in bs:
+        b = np.where(P.dir, 0.0, np.asarray(b, dtype=np.float64))
+        ubar, bp = proj.start(b)
+        nb, nbp = float(np.linalg.norm(b)), float(np.linalg.norm(bp))
+        if nbp > 0.0:
+            d, it, _, _ = fcg(P.apply_A, lambda r: P.apply_M(r, form), bp, rtol * nb / nbp, maxit)
+        else:
+            d, it = np.zeros_like(b), 0
+        x = ubar + d
+        rel = float(np.linalg.norm(b - P.apply_A(x)) / nb) if nb > 0 else 0.0
+        out.append((x, it, rel, ubar))
+        proj.add(x)
+    return out
 
 
 def fcg(apply_A, apply_M, b, rtol, maxit):

@@ -502,3 +502,82 @@ def test_nested_dissection_keeps_x_sparse():
     lex = np.count_nonzero(O.xxt_basis(A, np.arange(n)))
     assert nd < 0.25 * n * n
     assert lex > 0.45 * n * n
+
+
+# --------------------------------------------------------------------------
+# projection onto prior solutions (Sec. 5: solve for the change from the
+# A-orthogonal best fit onto l prior solutions)
+# --------------------------------------------------------------------------
+
+def _direct(P, b):
+    """Exact solution by a dense direct solve of the free block."""
+    x = np.zeros(P.nv)
+    x[P.free] = np.linalg.solve(P.A.toarray(), np.asarray(b)[P.free])
+    return x
+
+
+@pytest.fixture(scope="module")
+def cube8_problem():
+    m, _ = meshes.workload_cube8()
+    return O.Problem(m.xyz, m.conn, m.part, m.boxes)
+
+
+def test_projection_start_is_the_a_orthogonal_best_fit(cube8_problem):
+    """u_bar equals U c with (U^T A U) c = U^T b, U the raw prior solutions
+    (the normal equations of min ||u* - U c||_A, solved densely)."""
+    P = cube8_problem
+    rng = np.random.default_rng(12)
+    proj = O.Projection(P.apply_A, 5)
+    U = []
+    for _ in range(4):
+        u = _direct(P, np.where(P.dir, 0.0, rng.standard_normal(P.nv)))
+        proj.add(u)
+        U.append(u[P.free])
+    U = np.array(U).T
+    b = np.where(P.dir, 0.0, rng.standard_normal(P.nv))
+    ubar, bp = proj.start(b)
+    A = P.A.toarray()
+    c = np.linalg.solve(U.T @ A @ U, U.T @ b[P.free])
+    assert np.abs(ubar[P.free] - U @ c).max() <= 1e-10 * np.abs(U @ c).max()
+    assert np.abs(bp - (b - P.apply_A(ubar))).max() <= 1e-10 * np.abs(b).max()
+
+
+def test_projection_is_exact_for_a_combination_of_prior_right_hand_sides(cube8_problem):
+    P = cube8_problem
+    rng = np.random.default_rng(13)
+    b1, b2 = (np.where(P.dir, 0.0, rng.standard_normal(P.nv)) for _ in range(2))
+    proj = O.Projection(P.apply_A, 4)
+    proj.add(_direct(P, b1))
+    proj.add(_direct(P, b2))
+    b = 0.3 * b1 - 1.7 * b2
+    ubar, bp = proj.start(b)
+    ref = _direct(P, b)
+    assert np.abs(ubar - ref).max() <= 1e-11 * np.abs(ref).max()
+    assert np.linalg.norm(bp) <= 1e-10 * np.linalg.norm(b)
+
+
+def test_projection_basis_is_a_orthonormal_and_restarts(cube8_problem):
+    P = cube8_problem
+    rng = np.random.default_rng(14)
+    proj = O.Projection(P.apply_A, 3)
+    for k in range(3):
+        proj.add(_direct(P, np.where(P.dir, 0.0, rng.standard_normal(P.nv))))
+        X = np.array(proj.X)
+        G = X @ np.array([P.apply_A(x) for x in proj.X]).T
+        assert len(proj.X) == k + 1 and np.abs(G - np.eye(k + 1)).max() <= 1e-12
+    proj.add(_direct(P, np.where(P.dir, 0.0, rng.standard_normal(P.nv))))
+    assert len(proj.X) == 1                     # full basis restarts with the newest solution
+
+
+def test_projected_sequence_converges_with_fewer_iterations(cube8_problem):
+    P = cube8_problem
+    rng = np.random.default_rng(3)
+    b0, b1 = rng.standard_normal(P.nv), rng.standard_normal(P.nv)
+    bs = [b0 + 0.05 * k * b1 for k in range(6)]
+    res = O.solve_projected(P, bs, 3, rtol=1e-10)
+    plain = [P.solve(b, rtol=1e-10)[1] for b in bs]
+    assert res[0][1] == plain[0]                # empty basis: the plain solve
+    assert all(r[1] <= p for r, p in zip(res, plain)) and sum(r[1] for r in res) < sum(plain)
+    for (x, it, rel, _), b in zip(res, bs):
+        ref = _direct(P, np.where(P.dir, 0.0, b))
+        assert rel <= 5e-10 and np.abs(x - ref).max() <= 1e-8 * np.abs(ref).max()
