@@ -410,9 +410,13 @@ class Projection:
     Keeps an A-orthonormal basis x~_1..x~_k (k <= l) of the span of earlier
     solutions, so the best fit of the new solution is u_bar = sum_j
     (x~_j . b) x~_j (x~_j^T A u = x~_j . b).  After a solve, the new solution
-    is made A-orthogonal to the basis, scaled to unit A-norm and appended;
-    a full basis first restarts empty (reading: the paper does not say how
-    the l solutions are chosen; this keeps the newest one)."""
+    is made A-orthogonal to the basis (coefficients (A x~_j) . u, by the
+    symmetry of A), its A x~ formed by one product with A, scaled to unit
+    A-norm and appended; a full basis first restarts empty (reading: the
+    paper does not say how the l solutions are chosen; this keeps the newest
+    one).  A solution that adds no direction (A-norm of the orthogonal part
+    below 1e-6 of its own, far above the solve tolerances used) is not
+    appended: its orthogonal part would be solver error and rounding."""
 
     def __init__(self, apply_A, l: int):
         self.apply_A, self.l = apply_A, int(l)
@@ -432,14 +436,13 @@ class Projection:
     def add(self, u):
         if len(self.X) >= self.l:
             self.X, self.AX = [], []
-        Au = self.apply_A(u)
-        w, Aw = np.array(u, dtype=np.float64), Au.copy()
-        for x, ax in zip(self.X, self.AX):
-            e = float(x @ Au)                     # x~_j^T A u
-            w -= e * x
-            Aw -= e * ax
+        w = np.array(u, dtype=np.float64)
+        e = [float(ax @ w) for ax in self.AX]     # x~_j^T A u
+        for c, x in zip(e, self.X):
+            w -= c * x
+        Aw = self.apply_A(w)
         nrm2 = float(w @ Aw)
-        if nrm2 > 1e-28 * max(float(u @ Au), 1e-300):
+        if nrm2 > 1e-12 * (sum(c * c for c in e) + nrm2):
             self.X.append(w / np.sqrt(nrm2))
             self.AX.append(Aw / np.sqrt(nrm2))
 
@@ -448,7 +451,7 @@ def solve_projected(P, bs, l: int, rtol: float = 1e-8, maxit: int = 500, form: s
     """Solve A u = b for each b of the sequence with the projection onto up
     to l prior solutions.  The correction solve stops when its residual
     (which is b - A u) is below rtol ||b||.  Returns a list of (x, iters,
-    true relres, u_bar)."""
+    true relres, u_bar, basis size after the solve)."""
     proj = Projection(P.apply_A, l)
     out = []
     for b in bs:
@@ -461,8 +464,8 @@ def solve_projected(P, bs, l: int, rtol: float = 1e-8, maxit: int = 500, form: s
             d, it = np.zeros_like(b), 0
         x = ubar + d
         rel = float(np.linalg.norm(b - P.apply_A(x)) / nb) if nb > 0 else 0.0
-        out.append((x, it, rel, ubar))
         proj.add(x)
+        out.append((x, it, rel, ubar, len(proj.X)))
     return out
 
 

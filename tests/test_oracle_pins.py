@@ -567,6 +567,8 @@ def test_projection_basis_is_a_orthonormal_and_restarts(cube8_problem):
         assert len(proj.X) == k + 1 and np.abs(G - np.eye(k + 1)).max() <= 1e-12
     proj.add(_direct(P, np.where(P.dir, 0.0, rng.standard_normal(P.nv))))
     assert len(proj.X) == 1                     # full basis restarts with the newest solution
+    proj.add(2.0 * proj.X[0])                   # no new direction: not appended
+    assert len(proj.X) == 1
 
 
 def test_projected_sequence_converges_with_fewer_iterations(cube8_problem):
@@ -578,6 +580,6 @@ def test_projected_sequence_converges_with_fewer_iterations(cube8_problem):
     plain = [P.solve(b, rtol=1e-10)[1] for b in bs]
     assert res[0][1] == plain[0]                # empty basis: the plain solve
     assert all(r[1] <= p for r, p in zip(res, plain)) and sum(r[1] for r in res) < sum(plain)
-    for (x, it, rel, _), b in zip(res, bs):
+    for (x, it, rel, _, _), b in zip(res, bs):
         ref = _direct(P, np.where(P.dir, 0.0, b))
         assert rel <= 5e-10 and np.abs(x - ref).max() <= 1e-8 * np.abs(ref).max()
