@@ -199,6 +199,28 @@ cgs_status cgs_interp(cgs_mesh* mesh, const double* ur, double* z, void* stream)
 /* cgs_apply_preconditioner: z = M r in the mesh's form and precision.       */
 cgs_status cgs_apply_preconditioner(cgs_mesh* mesh, const double* r, double* z, void* stream);
 
+/* ---- repeated right-hand sides: projection onto prior solutions -----------
+ * For a sequence of solves with the same mesh (a pressure solve per time step),
+ * Sec. 5 solves only for the change from the A-orthogonal best fit onto l
+ * prior solutions.
+ * cgs_mesh_set_projection: keep up to `l` prior solutions of cgs_solve /
+ *   cgs_solve_host on this mesh (0 <= l <= CGS_PROJECTION_MAX; 0 = off, the
+ *   default).  The kept vectors form an A-orthonormal basis x~_j in float64
+ *   (with A x~_j): each solve starts from u_bar = sum_j (x~_j . b) x~_j, runs
+ *   the PCG on b - A u_bar with the stopping test still relative to ||b||,
+ *   returns u_bar + the correction, then makes the solution A-orthogonal to
+ *   the basis and appends it (one extra float64 operator apply; a solution
+ *   that adds no direction, below 1e-6 of its A-norm, is not appended); a
+ *   full basis restarts from the newest solution.  iters counts the correction's
+ *   products A p (0 when the start already meets rtol); relres is
+ *   ||b - A x|| / ||b||.  Allocates 2 l nv + 2 nv doubles (freed with the
+ *   mesh or by l = 0); resets the basis.  Batches, servers and
+ *   cgs_solve_batched do not use it.  INVALID_ARG for l out of range.
+ * cgs_mesh_projection_size: the number of kept vectors now.              */
+#define CGS_PROJECTION_MAX 64
+cgs_status cgs_mesh_set_projection(cgs_mesh* mesh, int l);
+cgs_status cgs_mesh_projection_size(const cgs_mesh* mesh, int* k);
+
 /* ---- preconditioner apply without allocation -------------------------------
  * cgs_apply_preconditioner_noalloc: the same z = M r as
  * cgs_apply_preconditioner, for callers that must not allocate device memory

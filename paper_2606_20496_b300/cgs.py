@@ -16,6 +16,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libcgs.so")
 
 NOALLOC_MAX_NV, NOALLOC_MAX_NR = 131072, 8192
+PROJECTION_MAX = 64
 OK, ERR_INVALID_ARG, ERR_INVALID_MESH, ERR_NOT_SPD, ERR_NO_CONVERGENCE, ERR_BREAKDOWN, ERR_OOM, \
     ERR_ADMISSION, ERR_TIMEOUT, ERR_CUDA = range(10)
 PREC = {"fp64": 0, "fp32": 1, "fp16": 2}
@@ -27,7 +28,7 @@ EXPORTS = (
     "cgs_create", "cgs_destroy", "cgs_ctx_bytes_in_use", "cgs_mesh_setup", "cgs_mesh_free", "cgs_mesh_info",
     "cgs_mesh_set_form", "cgs_mesh_export", "cgs_apply_A", "cgs_apply_local", "cgs_restrict",
     "cgs_coarse_solve", "cgs_interp", "cgs_apply_preconditioner", "cgs_apply_preconditioner_noalloc",
-    "cgs_solve", "cgs_solve_host",
+    "cgs_solve", "cgs_solve_host", "cgs_mesh_set_projection", "cgs_mesh_projection_size",
     "cgs_profile_enable", "cgs_profile_read", "cgs_batch_create", "cgs_batch_free", "cgs_batch_solve",
     "cgs_batch_launches", "cgs_solve_batched", "cgs_mesh_tune", "cgs_mesh_get_schedule", "cgs_mesh_set_schedule",
     "cgs_batch_tune",
@@ -95,6 +96,8 @@ def load(path: str = LIB_PATH):
         "cgs_apply_preconditioner_noalloc": ([P, P, P, P], I32),
         "cgs_solve": ([P, P, P, I32, D, I32, P, P, P], I32),
         "cgs_solve_host": ([P, P, P, I32, D, I32, P, P, P], I32),
+        "cgs_mesh_set_projection": ([P, I32], I32),
+        "cgs_mesh_projection_size": ([P, C.POINTER(I32)], I32),
         "cgs_profile_enable": ([P, I32], I32),
         "cgs_profile_read": ([P, P, P], I32),
         "cgs_batch_create": ([P, P, I32, I32, C.POINTER(P)], I32),
@@ -271,6 +274,17 @@ def cgs_solve_host(mesh, b, x, nrhs=1, rtol=1e-8, maxit=1000, stream=None,
                                _ptr(relres), _stream(stream))
     _check(st, "cgs_solve_host", allow)
     return st, iters, relres
+
+
+def cgs_mesh_set_projection(mesh, l: int):
+    """Keep up to l prior solutions for the projected start of cgs_solve (0 = off)."""
+    _check(load().cgs_mesh_set_projection(mesh, int(l)), "cgs_mesh_set_projection")
+
+
+def cgs_mesh_projection_size(mesh) -> int:
+    k = C.c_int(0)
+    _check(load().cgs_mesh_projection_size(mesh, C.byref(k)), "cgs_mesh_projection_size")
+    return k.value
 
 
 def cgs_profile_enable(mesh, enable=True):

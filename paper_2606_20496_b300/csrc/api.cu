@@ -172,6 +172,19 @@ struct cgs_mesh {
     std::vector<int32_t> sub_idx_h;
     double *hb = nullptr, *hx = nullptr;  // device staging for cgs_solve_host
     size_t h_cap = 0;
+    // projection onto prior solutions (cgs_mesh_set_projection): l x nv rows
+    // of the A-orthonormal basis X and of A X, work vectors, dot results
+    struct Projection {
+        int l = 0, k = 0;
+        double *X = nullptr, *AX = nullptr, *ubar = nullptr, *bp = nullptr;
+        double *coef = nullptr, *partial = nullptr;
+        double* host = nullptr;   // pinned copy of coef
+        void release() {
+            for (double* p : {X, AX, ubar, bp, coef, partial}) if (p) cudaFree(p);
+            if (host) cudaFreeHost(host);
+            *this = Projection();
+        }
+    } proj;
     bool fp64() const { return prm.prec == CGS_FP64; }
 };
 
@@ -1023,6 +1036,7 @@ cgs_status cgs_mesh_free(cgs_mesh* m) {
     }
     if (m->hb) cudaFree(m->hb);
     if (m->hx) cudaFree(m->hx);
+    m->proj.release();
     m->E.release();
     m->mem.release();
     delete m;
@@ -1185,6 +1199,115 @@ cgs_status cgs_apply_preconditioner(cgs_mesh* m, const double* r, double* z, voi
 
 // ---- solves ------------------------------------------------------------------
 
+cgs_status cgs_mesh_set_projection(cgs_mesh* m, int l) {
+    if (!m || l < 0 || l > CGS_PROJECTION_MAX) return fail(CGS_ERR_INVALID_ARG, "bad mesh or projection size");
+    CGS_CUDA(cudaSetDevice(m->ctx->device));
+    CGS_CUDA(cudaDeviceSynchronize());
+    m->proj.release();
+    if (l == 0) return CGS_OK;
+    auto& pj = m->proj;
+    const size_t nv = (size_t)m->d.nv;
+    cudaError_t e = cudaSuccess;
+    auto get = [&](double** p, size_t n) {
+        if (e == cudaSuccess) e = cudaMalloc(p, n * sizeof(double));
+    };
+    get(&pj.X, (size_t)l * nv);
+    get(&pj.AX, (size_t)l * nv);
+    get(&pj.ubar, nv);
+    get(&pj.bp, nv);
+    get(&pj.coef, (size_t)l + 1);
+    get(&pj.partial, (size_t)proj_partial_entries(l));
+    if (e == cudaSuccess) e = cudaMallocHost(&pj.host, sizeof(double) * (l + 1));
+    if (e != cudaSuccess) {
+        pj.release();
+        return e == cudaErrorMemoryAllocation ? fail(CGS_ERR_OOM, "projection vectors") : cuda_fail(e, "projection");
+    }
+    pj.l = l;
+    return CGS_OK;
+}
+
+cgs_status cgs_mesh_projection_size(const cgs_mesh* m, int* k) {
+    if (!m || !k) return fail(CGS_ERR_INVALID_ARG, "null argument");
+    *k = m->proj.k;
+    return CGS_OK;
+}
+
+namespace {
+// coef[0..k] of the last launch_proj_dots, read on the host (synchronises)
+cgs_status read_coef(cgs_mesh* m, int k1, cudaStream_t st) {
+    CGS_CUDA(cudaMemcpyAsync(m->proj.host, m->proj.coef, sizeof(double) * k1, cudaMemcpyDeviceToHost, st));
+    CGS_CUDA(cudaStreamSynchronize(st));
+    return CGS_OK;
+}
+
+// One solve with the projected start (Sec. 5), then the basis update.
+cgs_status projected_solve(cgs_mesh* m, const double* b, double* x, double rtol, int maxit, int& iters,
+                           double& relres, cudaStream_t st) {
+    Engine& E = m->E;
+    auto& pj = m->proj;
+    const int64_t nv = m->d.nv;
+    const uint8_t* dir = m->d.dir;
+    // c_j = x~_j . b and ||b||^2 (free entries); u_bar = sum c_j x~_j;
+    // b' = b - sum c_j A x~_j
+    K(CGS_K_OTHER, launch_proj_dots(pj.X, pj.k, nv, b, dir, pj.partial, pj.coef, st));
+    E.launches++;   // two kernels
+    if (cgs_status s = read_coef(m, pj.k + 1, st)) return s;
+    const double nb2 = pj.host[pj.k];
+    K(CGS_K_OTHER, launch_proj_combine(nv, nullptr, dir, 1.0, pj.coef, pj.k, pj.X, pj.ubar, st));
+    K(CGS_K_OTHER, launch_proj_combine(nv, b, dir, -1.0, pj.coef, pj.k, pj.AX, pj.bp, st));
+    K(CGS_K_OTHER, launch_proj_dots(nullptr, 0, nv, pj.bp, dir, pj.partial, pj.coef, st));
+    E.launches++;
+    if (cgs_status s = read_coef(m, 1, st)) return s;
+    const double nbp2 = pj.host[0];
+    iters = 0;
+    relres = 0.0;
+    cgs_status slot = CGS_OK;
+    if (nb2 > 0.0 && nbp2 > rtol * rtol * nb2) {
+        // the correction solve, its stopping test relative to ||b||
+        E.V.b = pj.bp;
+        cgs_status s = engine_solve(E, rtol * std::sqrt(nb2 / nbp2), maxit, st);
+        E.V.b = nullptr;
+        if (s != CGS_OK) return s;
+        const SolveScalars& h = E.S_host[0];
+        iters = h.iters;
+        relres = slot_relres(h) * std::sqrt(nbp2 / nb2);   // ||b - A x|| / ||b||
+        slot = slot_status(h);
+        K(CGS_K_OTHER, launch_vec_add(nv, pj.ubar, E.V.x, x, st));
+    } else {
+        // the start meets the tolerance: x = u_bar, relres from b'
+        K(CGS_K_OTHER, launch_copy_d(E.P, pj.ubar, x, false, st));
+        relres = nb2 > 0.0 ? std::sqrt(nbp2 / nb2) : 0.0;
+    }
+    // append x, A-orthonormalised against the basis (a full basis restarts):
+    // e_j = (A x~_j) . x (A symmetric), w = x - sum e_j x~_j, A w by one
+    // product (so the kept A x~ matches x~ even when w is small), then
+    // w / ||w||_A unless x adds no direction (||w||_A^2 below 1e-12 of
+    // x's, sum e_j^2 + ||w||_A^2: its orthogonal part is solver error)
+    if (pj.k >= pj.l) pj.k = 0;
+    double* w = pj.X + (size_t)pj.k * nv;
+    double* Aw = pj.AX + (size_t)pj.k * nv;
+    K(CGS_K_OTHER, launch_proj_dots(pj.AX, pj.k, nv, x, dir, pj.partial, pj.coef, st));
+    E.launches++;
+    if (cgs_status s = read_coef(m, pj.k + 1, st)) return s;
+    double esum = 0.0;
+    for (int j = 0; j < pj.k; ++j) esum += pj.host[j] * pj.host[j];
+    K(CGS_K_OTHER, launch_proj_combine(nv, x, dir, -1.0, pj.coef, pj.k, pj.X, w, st));
+    K(CGS_K_OTHER, launch_fill_d(nv, Aw, 0.0, st));
+    K(CGS_K_OTHER, launch_apply64(E.P, no_stop(E.V), w, Aw, 1.0, false, st));
+    K(CGS_K_OTHER, launch_proj_dots(w, 1, nv, Aw, dir, pj.partial, pj.coef, st));
+    E.launches++;
+    if (cgs_status s = read_coef(m, 1, st)) return s;
+    const double nrm2 = pj.host[0];          // w^T A w
+    if (nrm2 > 1e-12 * (esum + nrm2) && std::isfinite(nrm2)) {
+        const double s = 1.0 / std::sqrt(nrm2);
+        K(CGS_K_OTHER, launch_vec_scale(nv, w, s, st));
+        K(CGS_K_OTHER, launch_vec_scale(nv, Aw, s, st));
+        pj.k++;
+    }
+    return slot;
+}
+}  // namespace
+
 cgs_status cgs_solve(cgs_mesh* m, const double* b, double* x, int nrhs, double rtol, int maxit, int* iters,
                      double* relres, void* stream) {
     if (!m || !b || !x || !iters || !relres || nrhs < 0 || !(rtol >= 0.0))
@@ -1197,6 +1320,12 @@ cgs_status cgs_solve(cgs_mesh* m, const double* b, double* x, int nrhs, double r
         double* xk = x + (size_t)k * m->d.nv;
         iters[k] = 0;
         relres[k] = 0.0;
+        if (m->proj.l > 0) {
+            const cgs_status ss = projected_solve(m, bk, xk, rtol, maxit, iters[k], relres[k], st);
+            if (ss == CGS_ERR_CUDA || ss == CGS_ERR_OOM) return ss;
+            if (ss != CGS_OK && first_bad == CGS_OK) first_bad = ss;
+            continue;
+        }
         E.V.b = bk;
         cgs_status s = engine_solve(E, rtol, maxit, st);
         E.V.b = nullptr;

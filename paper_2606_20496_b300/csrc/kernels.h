@@ -10,6 +10,19 @@
 
 namespace cgs {
 
+// Projection onto prior solutions (projection.cu), float64 vectors of length
+// n; X and Y hold k rows of n.  launch_proj_dots: out[j] = X_j . v (j < k),
+// out[k] = v . v, Dirichlet entries of v (dir != 0) taken as zero; `partial`
+// holds proj_partial_entries(k) doubles.  Two kernels.
+int proj_partial_entries(int max_k);
+void launch_proj_dots(const double* X, int k, int64_t n, const double* v, const uint8_t* dir, double* partial,
+                      double* out, cudaStream_t st);
+// out = base (Dirichlet entries zeroed; nullptr = 0) + s sum_{j<k} coef[j] Y_j
+void launch_proj_combine(int64_t n, const double* base, const uint8_t* dir, double s, const double* coef, int k,
+                         const double* Y, double* out, cudaStream_t st);
+void launch_vec_scale(int64_t n, double* a, double alpha, cudaStream_t st);
+void launch_vec_add(int64_t n, const double* a, const double* b, double* out, cudaStream_t st);
+
 void launch_apply64(const Plan& P, const Vecs& V, const double* x, double* y, double alpha, bool dot,
                     cudaStream_t st);
 void launch_apply_pair_tiled(const Plan& P, const Vecs& V, cudaStream_t st);

@@ -55,6 +55,10 @@ def main():
                     help="four lanes per small subdomain where the mesh has row packs: 1 on, 0 off")
     ap.add_argument("--interp-cells", type=int, choices=(0, 1), default=None,
                     help="interpolation by cell-sorted entries (1) or by vertex with the dots fused (0)")
+    ap.add_argument("--sequence", type=int, default=0,
+                    help="also solve a slowly varying series of this many right-hand sides, plain and with "
+                         "the projection onto prior solutions")
+    ap.add_argument("--projection", type=int, default=8, help="prior solutions kept for --sequence")
     for name in ("vert-chunk", "sub-chunk", "pack-chunk", "box-chunk"):
         ap.add_argument(f"--{name}", type=int, default=None, help=f"force the schedule's {name.replace('-', '_')}")
     args = ap.parse_args()
@@ -97,6 +101,28 @@ def main():
            "coarse_solver": {v: k for k, v in cgs.COARSE.items()}[info["coarse_solver"]], "xxt_nnz": info["xxt_nnz"],
            "footprint_mb": h.info["footprint_bytes"] / 2 ** 20, "setup_s": setup_s, "iters": its,
            "relres": rels, "ms_per_solve": float(np.mean(ms[1:] if len(ms) > 1 else ms))}
+    if args.sequence > 0:
+        # b_k = b + 0.05 sin(0.3 k) b1 + 0.02 k b2: a time series of right-hand sides
+        rng = np.random.default_rng(17)
+        b1, b2 = rng.standard_normal(m.nv), rng.standard_normal(m.nv)
+        seq = [bd + torch.as_tensor(0.05 * np.sin(0.3 * k) * b1 + 0.02 * k * b2, device="cuda")
+               for k in range(args.sequence)]
+        res = {}
+        for mode, l in (("plain", 0), ("projected", args.projection)):
+            cgs.cgs_mesh_set_projection(h.handle, l)
+            its_s, ms_s, rels = [], [], []
+            for bk in seq:
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                st, it, rel = cgs.cgs_solve(h.handle, bk, x, rtol=args.rtol, maxit=args.maxit)
+                e1.record()
+                torch.cuda.synchronize()
+                its_s.append(int(it[0]))
+                ms_s.append(e0.elapsed_time(e1))
+                rels.append(float(rel[0]))
+            res[mode] = {"iters": its_s, "ms_per_solve": float(np.mean(ms_s)), "max_relres": max(rels)}
+        cgs.cgs_mesh_set_projection(h.handle, 0)
+        out["sequence"] = {"n": args.sequence, "kept": args.projection, **res}
     if args.profile:
         out["profile"] = cgs.cgs_profile_read(h.handle)
     if args.compare_fp64 and args.prec != "fp64":

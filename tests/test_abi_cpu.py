@@ -88,3 +88,11 @@ def test_segments_rule():
     assert meshes.segments(7, "two") == [2, 2, 2, 1]
     for n in range(1, 30):
         assert sum(meshes.segments(n, "mixed")) == n
+
+
+def test_binding_constants_match_header():
+    text = open(os.path.join(ROOT, "include", "cgs.h")).read()
+    defs = dict(re.findall(r"#define (CGS_\w+) (\d+)\b", text))
+    assert int(defs["CGS_NOALLOC_MAX_NV"]) == cgs.NOALLOC_MAX_NV
+    assert int(defs["CGS_NOALLOC_MAX_NR"]) == cgs.NOALLOC_MAX_NR
+    assert int(defs["CGS_PROJECTION_MAX"]) == cgs.PROJECTION_MAX
