@@ -19,6 +19,9 @@ A u = b, Sec. 3):
   each element assigned to the cell holding its centroid, element-local
   trilinear interpolant J_L, averaging W Q^T (Sec. 4, the centroid-assignment
   paragraph), active-vertex compression, and A_r assembled cell-wise (Eq. Aij);
+* three coarse operators (Sec. 4): the cell-wise A_r of Eq. Aij (default),
+  the Galerkin J~^T A J~ of the averaged interpolant, and the vertex-based J
+  (each node in the box cell holding it) with A_r = J^T A J;
 * the reduced solve exactly (Cholesky) and by XX^T (Sec. 2): A_r-conjugate
   basis vectors formed by Gram-Schmidt in the A_r inner product, in a
   nested-dissection order of the box lattice;
@@ -119,7 +122,7 @@ class Problem:
     """Setup of the two-level Schwarz preconditioner for one mesh."""
 
     def __init__(self, xyz, conn, part, boxes, overlap: int = 1, margin: float = 0.0,
-                 dirichlet=None):
+                 dirichlet=None, coarse_operator: str = "broken"):
         self.xyz = np.asarray(xyz, dtype=np.float64)
         self.conn = np.asarray(conn, dtype=np.int64)
         self.part = np.asarray(part, dtype=np.int64)
@@ -134,6 +137,9 @@ class Problem:
         self.A = self.A_full[self.free][:, self.free]          # free block, SPD
         self.cnt = vertex_element_counts(self.conn, self.nv)
         self._setup_subdomains(overlap)
+        if coarse_operator not in ("broken", "galerkin", "vertex"):
+            raise ValueError(coarse_operator)
+        self.coarse_operator = coarse_operator
         self._setup_boxes(tuple(int(b) for b in boxes), margin)
 
     # -- vectors of length nv (Dirichlet entries zero) ------------------------
@@ -252,6 +258,9 @@ class Problem:
         for m in range(8):
             c = cell + np.array([m & 1, (m >> 1) & 1, (m >> 2) & 1])
             corner[:, m] = c[:, 0] + nb[0] * (c[:, 1] + nb[1] * c[:, 2])
+        if self.coarse_operator == "vertex":
+            self._setup_vertex_J(nb)
+            return self._factor_Ar()
         # active vertices: corners of occupied cells with a nontrivial column
         colmax = np.zeros(int(np.prod(nb)))
         np.maximum.at(colmax, corner.ravel(), np.abs(Je).max(axis=1).ravel())
@@ -264,6 +273,17 @@ class Problem:
         self.corner_col = col[corner]                              # (E, 8); -1 = dropped
         self.Je = Je
         self.nr = int(self.box_active.size)
+        if self.coarse_operator == "galerkin":
+            # A_r = J~^T A J~ with J~ = W Q^T J_L (Sec. 4: the Galerkin reading
+            # of A_r; full support of the averaged interpolant, 5^3 stencil)
+            keep = self.corner_col >= 0
+            e_idx, k_idx, m_idx = np.nonzero(np.broadcast_to(keep[:, None, :], (self.ne, 8, 8)))
+            rows = self.conn[e_idx, k_idx]
+            vals = Je[e_idx, k_idx, m_idx] / self.cnt[rows]
+            Jt = sp.coo_array((vals, (rows, self.corner_col[e_idx, m_idx])), shape=(self.nv, self.nr)).tocsr()
+            Jf = Jt[self.free]
+            self.Ar = (Jf.T @ self.A @ Jf).toarray()
+            return self._factor_Ar()
         # A_r = sum_e J_e^T A^e J_e (Eq. Aij, cell-wise assembly)
         Jk = np.where((self.corner_col >= 0)[:, None, :], Je, 0.0)
         Ke = np.einsum("ekm,ekl,eln->emn", Jk, self.Ae, Jk)
@@ -271,6 +291,40 @@ class Problem:
         rows = np.repeat(cc, 8, axis=1).ravel()
         cols = np.tile(cc, (1, 8)).ravel()
         self.Ar = sp.coo_array((Ke.ravel(), (rows, cols)), shape=(self.nr, self.nr)).toarray()
+        return self._factor_Ar()
+
+    def _setup_vertex_J(self, nb):
+        """Vertex-based J (Sec. 4, the nodal construction): each node x_i takes
+        the trilinear interpolants of the 8 corners of the box cell holding it
+        (clamped to the grid); J_ij = Phi_j(x_i), Dirichlet rows zero; box
+        vertices with no entry above 1e-12 are compressed out; A_r = J^T A J
+        (full support, 5^3 stencil)."""
+        t = (self.xyz - self.box_lo) / self.box_H
+        vcell = np.clip(np.floor(t).astype(np.int64), 0, self.box_b - 1)
+        f = t - vcell
+        W = np.ones((self.nv, 8))
+        corner = np.empty((self.nv, 8), dtype=np.int64)
+        for m in range(8):
+            bit = np.array([m & 1, (m >> 1) & 1, (m >> 2) & 1])
+            for d in range(3):
+                W[:, m] *= f[:, d] if bit[d] else (1.0 - f[:, d])
+            c = vcell + bit
+            corner[:, m] = c[:, 0] + nb[0] * (c[:, 1] + nb[1] * c[:, 2])
+        W[self.dir] = 0.0
+        colmax = np.zeros(int(np.prod(nb)))
+        np.maximum.at(colmax, corner.ravel(), np.abs(W).ravel())
+        self.box_active = np.flatnonzero(colmax > 1e-12)
+        col = -np.ones(int(np.prod(nb)), dtype=np.int64)
+        col[self.box_active] = np.arange(self.box_active.size)
+        self.nr = int(self.box_active.size)
+        c = col[corner]
+        keep = c >= 0
+        r = np.repeat(np.arange(self.nv), 8).reshape(self.nv, 8)
+        self.Jv = sp.coo_array((W[keep], (r[keep], c[keep])), shape=(self.nv, self.nr)).tocsr()
+        Jf = self.Jv[self.free]
+        self.Ar = (Jf.T @ self.A @ Jf).toarray()
+
+    def _factor_Ar(self):
         try:
             self.Ar_chol = sla.cho_factor(self.Ar, lower=True)
         except np.linalg.LinAlgError as exc:
@@ -278,7 +332,12 @@ class Problem:
 
     def interp(self, ur):
         """z = W Q^T J_L u_r: element-local trilinear values, averaged at the
-        vertices by the inverse element counts (Sec. 4)."""
+        vertices by the inverse element counts (Sec. 4); z = J u_r with the
+        vertex-based J."""
+        if self.coarse_operator == "vertex":
+            z = self.Jv @ np.asarray(ur, dtype=np.float64)
+            z[self.dir] = 0.0
+            return z
         urx = np.append(np.asarray(ur, dtype=np.float64), 0.0)     # dropped columns read 0
         zl = np.einsum("ekm,em->ek", self.Je, urx[self.corner_col])     # J_L u_r, (E, 8)
         z = np.zeros(self.nv)
@@ -289,6 +348,8 @@ class Problem:
 
     def restrict(self, s):
         """r_r = J_L^T Q W s (the transpose of interp)."""
+        if self.coarse_operator == "vertex":
+            return self.Jv.T @ np.where(self.dir, 0.0, np.asarray(s, dtype=np.float64))
         w = np.asarray(s, dtype=np.float64) / self.cnt
         w = np.where(self.dir, 0.0, w)
         contrib = np.einsum("ekm,ek->em", self.Je, w[self.conn])   # (E, 8)

@@ -583,3 +583,55 @@ def test_projected_sequence_converges_with_fewer_iterations(cube8_problem):
     for (x, it, rel, _, _), b in zip(res, bs):
         ref = _direct(P, np.where(P.dir, 0.0, b))
         assert rel <= 5e-10 and np.abs(x - ref).max() <= 1e-8 * np.abs(ref).max()
+
+
+# --------------------------------------------------------------------------
+# coarse-operator variants (Sec. 4): Galerkin J~^T A J~ and the vertex-based J
+# --------------------------------------------------------------------------
+
+def test_coarse_operators_coincide_on_box_aligned_mesh():
+    """With element planes on box planes J_L is continuous: the cell-wise
+    A_r (Eq. Aij), the Galerkin J~^T A J~ and the vertex-based J^T A J agree."""
+    m = meshes.cube(8, boxes=(4, 2, 4))
+    Ps = {op: O.Problem(m.xyz, m.conn, m.part, m.boxes, coarse_operator=op)
+          for op in ("broken", "galerkin", "vertex")}
+    ref = Ps["broken"]
+    for op in ("galerkin", "vertex"):
+        assert np.array_equal(Ps[op].box_active, ref.box_active)
+        np.testing.assert_allclose(Ps[op].Ar, ref.Ar, atol=1e-13 * np.abs(ref.Ar).max())
+
+
+def test_vertex_based_J_reproduces_trilinear_fields():
+    """J u_r with u_r = f at the box vertices gives f at every free node for a
+    trilinear f (Sec. 4: J interpolates box-vertex values to each node)."""
+    m = meshes.cube(9, perturb=0.2, seed=5, boxes=(3, 4, 2))
+    P = O.Problem(m.xyz, m.conn, m.part, m.boxes, coarse_operator="vertex")
+    c = np.random.default_rng(2).standard_normal(8)
+    f = lambda X: (c[0] + c[1] * X[:, 0] + c[2] * X[:, 1] + c[3] * X[:, 2] + c[4] * X[:, 0] * X[:, 1]
+                   + c[5] * X[:, 1] * X[:, 2] + c[6] * X[:, 0] * X[:, 2] + c[7] * X[:, 0] * X[:, 1] * X[:, 2])
+    nb = P.box_b + 1
+    g = P.box_active
+    Xb = P.box_lo + np.stack([g % nb[0], (g // nb[0]) % nb[1], g // (nb[0] * nb[1])], axis=1) * P.box_H
+    z = P.interp(f(Xb))
+    ref = f(P.xyz)
+    assert np.abs(z[P.free] - ref[P.free]).max() <= 1e-12 * np.abs(ref).max()
+    assert np.all(z[P.dir] == 0.0)
+
+
+@pytest.mark.parametrize("op", ["galerkin", "vertex"])
+def test_full_support_variants_have_the_wider_stencil(op):
+    """On a perturbed mesh the cell-wise assembly keeps 3^3 = 27 nonzeros per
+    row; the full-support operators reach up to 5^3 = 125 (Sec. 4)."""
+    m, _ = meshes.workload_cube8()
+    Pb = O.Problem(m.xyz, m.conn, m.part, m.boxes)
+    Pv = O.Problem(m.xyz, m.conn, m.part, m.boxes, coarse_operator=op)
+    nz = lambda A: (np.abs(A) > 1e-14 * np.abs(A).max()).sum(axis=1)
+    assert nz(Pb.Ar).max() <= 27
+    assert 27 < nz(Pv.Ar).max() <= 125
+    np.testing.assert_allclose(Pv.Ar, Pv.Ar.T, atol=1e-14 * np.abs(Pv.Ar).max())
+    assert np.linalg.eigvalsh(Pv.Ar).min() > 0.0
+    # the reduced solve and restriction are each other's transposes
+    rng = np.random.default_rng(6)
+    s, u = rng.standard_normal(m.nv), rng.standard_normal(Pv.nr)
+    s[Pv.dir] = 0.0
+    assert abs(Pv.restrict(s) @ u - s @ Pv.interp(u)) <= 1e-12 * np.abs(s).sum() * np.abs(u).max()
