@@ -77,6 +77,15 @@ typedef enum {
 } cgs_coarse_solver;
 #define CGS_COARSE_AUTO_XXT_NR 1500
 
+/* The reduced operator A_r and its interpolation (Sec. 4). */
+typedef enum {
+    CGS_COARSE_OP_CELLWISE = 0, /* cell-wise assembly of Eq. Aij (3^3 stencil) with the
+                                   averaged interpolant W Q^T J_L (default)            */
+    CGS_COARSE_OP_GALERKIN = 1, /* the same interpolant, A_r = J~^T A J~ (5^3 stencil) */
+    CGS_COARSE_OP_VERTEX = 2    /* vertex-based J: each node interpolated in the box
+                                   cell holding it, A_r = J^T A J (5^3 stencil)         */
+} cgs_coarse_operator;
+
 typedef struct {
     int box[3];            /* b_x, b_y, b_z in [1, 1023]: box cells per axis over the
                               bounding box (Sec. 4)                                    */
@@ -85,6 +94,7 @@ typedef struct {
     cgs_precision prec;
     cgs_form form;
     cgs_coarse_solver coarse_solver;  /* 0 (zero-initialised params) = auto        */
+    cgs_coarse_operator coarse_operator; /* 0 = cell-wise (Eq. Aij)                  */
 } cgs_params;
 
 typedef struct {
@@ -104,6 +114,8 @@ typedef struct {
                               graph loop, 2 persistent cooperative kernel          */
     int32_t coarse_solver; /* the reduced solver in use: CGS_COARSE_DENSE or _XXT   */
     int64_t xxt_nnz;       /* nonzeros of X (XX^T solver), else 0                    */
+    int64_t ar_nnz;        /* nonzeros of A_r                                         */
+    int32_t coarse_operator; /* the cgs_coarse_operator of the set-up                */
 } cgs_mesh_info_t;
 
 /* Launch schedule of a mesh's kernels (cgs_mesh_get_schedule / _set_schedule):

@@ -22,6 +22,7 @@ OK, ERR_INVALID_ARG, ERR_INVALID_MESH, ERR_NOT_SPD, ERR_NO_CONVERGENCE, ERR_BREA
 PREC = {"fp64": 0, "fp32": 1, "fp16": 2}
 FORM = {"hybrid": 0, "additive": 1}
 COARSE = {"auto": 0, "dense": 1, "xxt": 2}
+COARSE_OP = {"cellwise": 0, "galerkin": 1, "vertex": 2}
 
 # every symbol include/cgs.h declares
 EXPORTS = (
@@ -50,7 +51,7 @@ class CGSError(RuntimeError):
 
 class Params(C.Structure):
     _fields_ = [("box", C.c_int * 3), ("box_margin", C.c_double), ("overlap_layers", C.c_int),
-                ("prec", C.c_int), ("form", C.c_int), ("coarse_solver", C.c_int)]
+                ("prec", C.c_int), ("form", C.c_int), ("coarse_solver", C.c_int), ("coarse_operator", C.c_int)]
 
 
 class MeshInfo(C.Structure):
@@ -58,7 +59,8 @@ class MeshInfo(C.Structure):
                 ("n_r", C.c_int64), ("max_sub_dofs", C.c_int64), ("sum_sub_dofs", C.c_int64), ("sum_sub_tri", C.c_int64),
                 ("footprint_bytes", C.c_size_t), ("setup_seconds", C.c_double),
                 ("kernel_launches", C.c_int64), ("n_box_entries", C.c_int64), ("n_lane_packs", C.c_int64),
-                ("loop", C.c_int32), ("coarse_solver", C.c_int32), ("xxt_nnz", C.c_int64)]
+                ("loop", C.c_int32), ("coarse_solver", C.c_int32), ("xxt_nnz", C.c_int64), ("ar_nnz", C.c_int64),
+                ("coarse_operator", C.c_int32)]
 
 
 class Schedule(C.Structure):
@@ -188,13 +190,14 @@ def cgs_ctx_bytes_in_use(ctx) -> int:
 
 
 def cgs_mesh_setup(ctx, xyz, conn, dirichlet=None, elem_part=None, boxes=(4, 4, 4), margin=0.0, overlap=1,
-                   prec="fp64", form="hybrid", coarse="auto"):
+                   prec="fp64", form="hybrid", coarse="auto", coarse_operator="cellwise"):
     xyz = np.ascontiguousarray(xyz, dtype=np.float64)
     conn = np.ascontiguousarray(conn, dtype=np.int32)
     d = None if dirichlet is None else np.ascontiguousarray(dirichlet, dtype=np.uint8)
     part = None if elem_part is None else np.ascontiguousarray(elem_part, dtype=np.int32)
     prm = Params((C.c_int * 3)(*[int(b) for b in boxes]), float(margin), int(overlap), PREC[prec], FORM[form],
-                 COARSE[coarse] if isinstance(coarse, str) else int(coarse))
+                 COARSE[coarse] if isinstance(coarse, str) else int(coarse),
+                 COARSE_OP[coarse_operator] if isinstance(coarse_operator, str) else int(coarse_operator))
     mesh = C.c_void_p()
     st = load().cgs_mesh_setup(ctx, _ptr(xyz), xyz.shape[0], _ptr(conn), conn.shape[0], _ptr(d), _ptr(part),
                                C.byref(prm), C.byref(mesh))
@@ -445,8 +448,9 @@ class Mesh:
     """Owning handle around cgs_mesh_setup / cgs_mesh_free."""
 
     def __init__(self, ctx, xyz, conn, part=None, boxes=(4, 4, 4), dirichlet=None, margin=0.0, overlap=1,
-                 prec="fp64", form="hybrid", coarse="auto"):
-        self.handle = cgs_mesh_setup(ctx, xyz, conn, dirichlet, part, boxes, margin, overlap, prec, form, coarse)
+                 prec="fp64", form="hybrid", coarse="auto", coarse_operator="cellwise"):
+        self.handle = cgs_mesh_setup(ctx, xyz, conn, dirichlet, part, boxes, margin, overlap, prec, form, coarse,
+                                     coarse_operator)
         self.info = cgs_mesh_info(self.handle)
         self.prec = prec
 

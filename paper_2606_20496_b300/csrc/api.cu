@@ -204,7 +204,7 @@ struct cgs_batch {
 namespace {
 
 cgs_params default_params() {
-    cgs_params p;
+    cgs_params p{};
     p.box[0] = p.box[1] = p.box[2] = 4;
     p.box_margin = 0.0;
     p.overlap_layers = 1;
@@ -1018,6 +1018,8 @@ cgs_status cgs_mesh_setup(cgs_ctx* ctx, const double* xyz, int64_t nv, const int
     m->info.n_box_entries = (int64_t)hs.vb_cell.size();
     m->info.n_lane_packs = (int64_t)hs.pack_m.size();
     m->info.coarse_solver = hs.coarse;
+    m->info.ar_nnz = hs.ar_nnz;
+    m->info.coarse_operator = prm.coarse_operator;
     m->info.xxt_nnz = (int64_t)hs.xc_idx.size();
     m->info.footprint_bytes = m->mem.bytes;
     m->info.setup_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();

@@ -77,6 +77,7 @@ struct HostSetup {
     std::vector<int32_t> re_rng;       // (begin, end) entry ranges within one cell, <= kBoxRange each
     std::vector<int64_t> box_active;   // nr, lexicographic box-vertex ids
     int coarse = 1;                    // reduced solver: 1 dense A_r^{-1}, 2 XX^T
+    int64_t ar_nnz = 0;                // nonzeros of A_r
     std::vector<double> ar_inv;        // nr*nr, A_r^{-1}, full symmetric, float64 (dense)
     // XX^T (Sec. 2): A_r^{-1} = X X^T, column k of X the k-th A_r-conjugate
     // vector in nested-dissection order; rows are reduced indices

@@ -284,6 +284,10 @@ cgs_status host_setup(const double* xyz, int64_t nv, const int32_t* conn, int64_
         err = "coarse_solver must be CGS_COARSE_AUTO, _DENSE or _XXT";
         return CGS_ERR_INVALID_ARG;
     }
+    if (prm.coarse_operator < CGS_COARSE_OP_CELLWISE || prm.coarse_operator > CGS_COARSE_OP_VERTEX) {
+        err = "coarse_operator must be CGS_COARSE_OP_CELLWISE, _GALERKIN or _VERTEX";
+        return CGS_ERR_INVALID_ARG;
+    }
     for (int64_t i = 0; i < ne * 8; ++i)
         if (conn[i] < 0 || conn[i] >= nv) {
             err = "connectivity index out of range at entry " + std::to_string(i);
@@ -659,15 +663,53 @@ cgs_status host_setup(const double* xyz, int64_t nv, const int32_t* conn, int64_
                   k = cid / (bx * by) + ((m >> 2) & 1);
         return i + (int64_t)(bx + 1) * (j + (int64_t)(by + 1) * k);
     };
+    // trilinear weight of corner m of cell (ci, cj, ck) at point p
+    auto corner_weight = [&](const double* pnt, int ci, int cj, int ck, int m) {
+        const int c[3] = {ci, cj, ck};
+        double w = 1.0;
+        for (int d = 0; d < 3; ++d) {
+            const double t = (pnt[d] - (S.lo[d] + c[d] * S.H[d])) / S.H[d];
+            w *= ((m >> d) & 1) ? t : (1.0 - t);
+        }
+        return w;
+    };
+    // the vertex-based J (Sec. 4): every node in the box cell holding it
+    const bool vertex_J = prm.coarse_operator == CGS_COARSE_OP_VERTEX;
+    std::vector<int32_t> vcell;
+    if (vertex_J) {
+        vcell.resize(nv);
+        for (int64_t v = 0; v < nv; ++v) {
+            int c[3];
+            for (int d = 0; d < 3; ++d) {
+                const double f = std::floor((xyz[(size_t)v * 3 + d] - S.lo[d]) / S.H[d]);
+                c[d] = (int)std::min<double>(std::max<double>(f, 0.0), S.b[d] - 1);
+            }
+            vcell[v] = c[0] + bx * (c[1] + by * c[2]);
+        }
+    }
     std::vector<double> colmax(nbv, 0.0);
     std::vector<uint8_t> occupied(nbv, 0);
-    for (int64_t e = 0; e < ne; ++e) {
-        double W[8][8];
-        weights(e, W);
-        for (int m = 0; m < 8; ++m) {
-            const int64_t g = corner_id(ecell[e], m);
-            occupied[g] = 1;
-            for (int k = 0; k < 8; ++k) colmax[g] = std::max(colmax[g], std::fabs(W[k][m]));
+    if (vertex_J) {
+        // columns with an entry above 1e-12 at some free node
+        for (int64_t v = 0; v < nv; ++v) {
+            if (S.dir[v] || v2e_ptr[v + 1] == v2e_ptr[v]) continue;
+            const int cid = vcell[v];
+            for (int m = 0; m < 8; ++m) {
+                const int64_t g = corner_id(cid, m);
+                occupied[g] = 1;
+                const double w = corner_weight(&xyz[(size_t)v * 3], cid % bx, (cid / bx) % by, cid / (bx * by), m);
+                colmax[g] = std::max(colmax[g], std::fabs(w));
+            }
+        }
+    } else {
+        for (int64_t e = 0; e < ne; ++e) {
+            double W[8][8];
+            weights(e, W);
+            for (int m = 0; m < 8; ++m) {
+                const int64_t g = corner_id(ecell[e], m);
+                occupied[g] = 1;
+                for (int k = 0; k < 8; ++k) colmax[g] = std::max(colmax[g], std::fabs(W[k][m]));
+            }
         }
     }
     std::vector<int32_t> col(nbv, -1);
@@ -696,6 +738,12 @@ cgs_status host_setup(const double* xyz, int64_t nv, const int32_t* conn, int64_
         S.vb_w.clear();
         std::vector<int32_t> cells;
         for (int32_t v : S.vb_vert) {
+            if (vertex_J) {   // one cell per node, weight 1
+                S.vb_cell.push_back(pack_cell(vcell[v], bx, by));
+                S.vb_w.push_back(1.0);
+                S.vb_ptr.push_back((int32_t)S.vb_cell.size());
+                continue;
+            }
             cells.clear();
             for (int64_t t = v2e_ptr[v]; t < v2e_ptr[v + 1]; ++t) cells.push_back(ecell[v2e[t]]);
             std::sort(cells.begin(), cells.end());
@@ -748,10 +796,92 @@ cgs_status host_setup(const double* xyz, int64_t nv, const int32_t* conn, int64_
     });
 
     // ---- A_r = sum over cells of sum_e J_e^T A^e J_e  (Eq. Aij) --------------
+    // or, for the full-support operators, A_r = J^T A J assembled element by
+    // element from the rows of J at the element's nodes
     if (S.nr > 0) {
         std::vector<int64_t> cell_ptr(ncell + 1, 0);
         for (int64_t i = 0; i < ne; ++i) cell_ptr[ecell[S.elem_order[i]] + 1]++;
         for (int64_t c = 0; c < ncell; ++c) cell_ptr[c + 1] += cell_ptr[c];
+        const int64_t nr = S.nr;
+        std::vector<double> Ar((size_t)nr * nr, 0.0);
+        if (prm.coarse_operator != CGS_COARSE_OP_CELLWISE) {
+            // rows of J (J~ = W Q^T J_L, or the vertex-based J) by node: from the
+            // box lists, each (cell, weight) times the cell's 8 trilinear weights
+            std::vector<int64_t> jr_ptr(nv + 1, 0);
+            std::vector<int32_t> jr_col;
+            std::vector<double> jr_val;
+            {
+                std::vector<int64_t> cnt(nv, 0);
+                for (size_t i = 0; i < S.vb_vert.size(); ++i) cnt[S.vb_vert[i]] = 8 * (S.vb_ptr[i + 1] - S.vb_ptr[i]);
+                for (int64_t v = 0; v < nv; ++v) jr_ptr[v + 1] = jr_ptr[v] + cnt[v];
+                jr_col.assign(jr_ptr[nv], -1);
+                jr_val.assign(jr_ptr[nv], 0.0);
+                for (size_t i = 0; i < S.vb_vert.size(); ++i) {
+                    const int32_t v = S.vb_vert[i];
+                    int64_t o = jr_ptr[v];
+                    for (int32_t e = S.vb_ptr[i]; e < S.vb_ptr[i + 1]; ++e) {
+                        const int32_t pc = S.vb_cell[e];
+                        const int ci = pc & 1023, cj = (pc >> 10) & 1023, ck = pc >> 20;
+                        const int64_t cid = ci + (int64_t)bx * (cj + (int64_t)by * ck);
+                        for (int m = 0; m < 8; ++m, ++o) {
+                            jr_col[o] = S.cell_cols[cid * 8 + m];
+                            jr_val[o] = S.vb_w[e] * corner_weight(&xyz[(size_t)v * 3], ci, cj, ck, m);
+                        }
+                    }
+                }
+            }
+#pragma omp parallel
+            {
+                std::vector<int32_t> U;
+                std::vector<double> KL;
+                std::vector<std::pair<int32_t, double>> rows[8];
+#pragma omp for schedule(dynamic, 4)
+                for (int64_t c = 0; c < ncell; ++c) {
+                    // the cell's columns, then its elements' J^T A^e J on them
+                    U.clear();
+                    for (int64_t i = cell_ptr[c]; i < cell_ptr[c + 1]; ++i) {
+                        const int64_t e = S.elem_order[i];
+                        for (int k = 0; k < 8; ++k) {
+                            const int32_t v = conn[e * 8 + k];
+                            for (int64_t o = jr_ptr[v]; o < jr_ptr[v + 1]; ++o)
+                                if (jr_col[o] >= 0) U.push_back(jr_col[o]);
+                        }
+                    }
+                    std::sort(U.begin(), U.end());
+                    U.erase(std::unique(U.begin(), U.end()), U.end());
+                    const size_t L = U.size();
+                    if (!L) continue;
+                    KL.assign(L * L, 0.0);
+                    for (int64_t i = cell_ptr[c]; i < cell_ptr[c + 1]; ++i) {
+                        const int64_t e = S.elem_order[i];
+                        for (int k = 0; k < 8; ++k) {
+                            rows[k].clear();
+                            const int32_t v = conn[e * 8 + k];
+                            for (int64_t o = jr_ptr[v]; o < jr_ptr[v + 1]; ++o)
+                                if (jr_col[o] >= 0 && jr_val[o] != 0.0)
+                                    rows[k].emplace_back(
+                                        (int32_t)(std::lower_bound(U.begin(), U.end(), jr_col[o]) - U.begin()),
+                                        jr_val[o]);
+                        }
+                        const double* A = &Ae[(size_t)e * 64];
+                        for (int k = 0; k < 8; ++k)
+                            for (int l = 0; l < 8; ++l) {
+                                const double a = A[k * 8 + l];
+                                if (a == 0.0) continue;
+                                for (const auto& ri : rows[k])
+                                    for (const auto& rj : rows[l]) KL[(size_t)ri.first * L + rj.first] += a * ri.second * rj.second;
+                            }
+                    }
+                    for (size_t i = 0; i < L; ++i)
+                        for (size_t j = 0; j < L; ++j) {
+                            const double val = KL[i * L + j];
+                            if (val == 0.0) continue;
+#pragma omp atomic
+                            Ar[(size_t)U[i] * nr + U[j]] += val;
+                        }
+                }
+            }
+        } else {
         std::vector<double> Kc((size_t)ncell * 64, 0.0);
 #pragma omp parallel for schedule(dynamic, 4)
         for (int64_t c = 0; c < ncell; ++c) {
@@ -779,8 +909,6 @@ cgs_status host_setup(const double* xyz, int64_t nv, const int32_t* conn, int64_
                     }
             }
         }
-        const int64_t nr = S.nr;
-        std::vector<double> Ar((size_t)nr * nr, 0.0);
         for (int64_t c = 0; c < ncell; ++c)
             for (int m = 0; m < 8; ++m) {
                 const int32_t a = S.cell_cols[c * 8 + m];
@@ -790,6 +918,9 @@ cgs_status host_setup(const double* xyz, int64_t nv, const int32_t* conn, int64_
                     if (b >= 0) Ar[(size_t)a * nr + b] += Kc[(size_t)c * 64 + m * 8 + n];
                 }
             }
+        }
+        S.ar_nnz = 0;
+        for (size_t i = 0; i < Ar.size(); ++i) S.ar_nnz += Ar[i] != 0.0;
         const int want = prm.coarse_solver == CGS_COARSE_AUTO
                              ? (nr > CGS_COARSE_AUTO_XXT_NR ? CGS_COARSE_XXT : CGS_COARSE_DENSE)
                              : (int)prm.coarse_solver;

@@ -36,6 +36,8 @@ def main():
     ap.add_argument("--workload", default="cube32")
     ap.add_argument("--prec", default="fp32", choices=list(cgs.PREC))
     ap.add_argument("--form", default="hybrid", choices=list(cgs.FORM))
+    ap.add_argument("--coarse-operator", default="cellwise", choices=list(cgs.COARSE_OP),
+                    help="A_r: cell-wise (Eq. Aij), galerkin (J~^T A J~) or vertex (vertex-based J^T A J)")
     ap.add_argument("--coarse", default="auto", choices=list(cgs.COARSE),
                     help="reduced solver: auto (XX^T above 1500 unknowns), dense or xxt")
     ap.add_argument("--solves", type=int, default=2)
@@ -66,7 +68,8 @@ def main():
     m, b = load_workload(args.workload)
     ctx = cgs.cgs_create(0)
     t0 = time.perf_counter()
-    h = cgs.Mesh(ctx, m.xyz, m.conn, part=m.part, boxes=m.boxes, prec=args.prec, form=args.form, coarse=args.coarse)
+    h = cgs.Mesh(ctx, m.xyz, m.conn, part=m.part, boxes=m.boxes, prec=args.prec, form=args.form, coarse=args.coarse,
+                 coarse_operator=args.coarse_operator)
     setup_s = time.perf_counter() - t0
     if args.tune:
         cgs.cgs_mesh_tune(h.handle)
@@ -99,6 +102,7 @@ def main():
            "sum_sub_dofs": info["sum_sub_dofs"], "sum_sub_tri": info["sum_sub_tri"],
            "n_box_entries": info["n_box_entries"],
            "coarse_solver": {v: k for k, v in cgs.COARSE.items()}[info["coarse_solver"]], "xxt_nnz": info["xxt_nnz"],
+           "coarse_operator": args.coarse_operator, "ar_nnz": info["ar_nnz"],
            "footprint_mb": h.info["footprint_bytes"] / 2 ** 20, "setup_s": setup_s, "iters": its,
            "relres": rels, "ms_per_solve": float(np.mean(ms[1:] if len(ms) > 1 else ms))}
     if args.sequence > 0:

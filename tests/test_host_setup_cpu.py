@@ -41,3 +41,45 @@ def test_xxt_factors_equal_dense_inverse(driver, n, boxes, nr):
     assert int(m.group(1)) == nr and int(m.group(3)) == 0
     assert 0 < int(m.group(2)) < nr * nr * 0.25          # sparse under nested dissection
     assert float(m.group(4)) <= 1e-13
+
+
+def test_coarse_operators_match_oracle(tmp_path):
+    """The library's host set-up of A_r (cell-wise Eq. Aij, Galerkin J~^T A J~,
+    vertex-based J^T A J) against the oracle's on a perturbed cube: the same
+    active box vertices, the same nonzero count, A_r^{-1} to 1e-13."""
+    import numpy as np
+
+    from oracle import cgs_oracle as O
+    gxx = shutil.which("g++")
+    if gxx is None:
+        pytest.skip("no host C++ compiler")
+    exe = str(tmp_path / "ar_check")
+    res = subprocess.run([gxx, "-std=c++17", "-O2", "-fopenmp", "-I", CSRC, "-I", os.path.join(ROOT, "include"),
+                          "-I", "/usr/local/cuda/include", "-o", exe,
+                          os.path.join(ROOT, "tests", "host", "ar_check.cpp"), os.path.join(CSRC, "setup.cpp")],
+                         capture_output=True, text=True)
+    assert res.returncode == 0, res.stderr[-3000:]
+    dump = str(tmp_path / "ar.txt")
+    assert subprocess.run([exe, dump], timeout=300).returncode == 0
+    lines = open(dump).read().split("\n")
+    nv = int(lines[0])
+    xyz = np.array([[float(t) for t in line.split()] for line in lines[1:1 + nv]])
+    n = 8
+    conn = np.array([[(i + (m & 1)) + (n + 1) * ((j + ((m >> 1) & 1)) + (n + 1) * (k + ((m >> 2) & 1)))
+                      for m in range(8)] for k in range(n) for j in range(n) for i in range(n)])
+    part = np.array([(i // 2) + (n // 2) * ((j // 2) + (n // 2) * (k // 2))
+                     for k in range(n) for j in range(n) for i in range(n)])
+    pos = 1 + nv
+    nnzs = {}
+    for op in ("broken", "galerkin", "vertex"):
+        nr, nnz = map(int, lines[pos].split())
+        active = np.array([int(t) for t in lines[pos + 1].split()])
+        inv = np.array([float(t) for t in lines[pos + 2:pos + 2 + nr * nr]]).reshape(nr, nr)
+        pos += 2 + nr * nr
+        P = O.Problem(xyz, conn, part, (4, 4, 4), coarse_operator=op)
+        ref = np.linalg.inv(P.Ar)
+        assert nr == P.nr and np.array_equal(active, P.box_active)
+        assert nnz == int(np.count_nonzero(P.Ar))
+        assert np.abs(inv - ref).max() <= 1e-13 * np.abs(ref).max()
+        nnzs[op] = nnz
+    assert nnzs["galerkin"] > 2 * nnzs["broken"] and nnzs["vertex"] > 2 * nnzs["broken"]
