@@ -227,6 +227,22 @@ def oracle_sample(budget_s, max_solves):
                                 f"one thread, setup excluded), {sum(times):.1f} s; iters {iters[0]}"}))
 
 
+def max_over_ranks(dist, value: float, device: str) -> float:
+    """The maximum of `value` over all ranks (the slowest rank's time); the
+    value itself without a process group."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world: int, units_per_rank: int, ms_max: float) -> float:
+    """Units processed by all ranks per second of the slowest rank."""
+    return world * units_per_rank / (ms_max * 1e-3)
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -321,11 +337,8 @@ def run_ours(args):
         torch.cuda.synchronize()
         wall = time.perf_counter() - wall0
         launches = cgs.cgs_mesh_info(h.handle)["kernel_launches"] - n0
-        ms = sum(a.elapsed_time(c) for a, c in ev)
+        ms = max_over_ranks(dist, sum(a.elapsed_time(c) for a, c in ev), "cuda")
         if dist:
-            t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
             dist.barrier()
         return ms, its, launches, wall
 
@@ -397,17 +410,14 @@ def run_ours(args):
         st, it, rel = cgs.cgs_solve_host(h32.handle, bh, xh, rtol=RTOL)
         e2e_ms += (time.perf_counter() - t0) * 1e3
         assert st == cgs.OK
-    if dist:
-        t = torch.tensor([e2e_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks(dist, e2e_ms, "cuda")
 
     serving = serve_probe(ctx, args) if args.serve_seconds > 0 else None
 
     line = None
     if rank == 0:
         ms_per_step = ms32 / args.steps
-        value = world * args.steps / (ms32 * 1e-3)
+        value = whole_job_rate(world, args.steps, ms32)
         cpu = time_oracle(budget_s=args.cpu_seconds) if world == 1 else None
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -416,12 +426,12 @@ def run_ours(args):
                                         "schedule": sched}),
                 "iters": {"fp32_bulk": int(np.median(its32)), "fp64_plain": int(np.median(its64)),
                           "delta": int(np.median(its32)) - int(np.median(its64))},
-                "fp64_plain": {"value": world * args.steps / (ms64 * 1e-3), "unit": UNIT,
+                "fp64_plain": {"value": whole_job_rate(world, args.steps, ms64), "unit": UNIT,
                                "ms_per_step": ms64 / args.steps, "schedule": sched64},
                 "serve_latency_ms": serving,
                 "roofline": roofline, "kernel_shares": shares, "kernel_shares_stepwise": shares_stepwise,
                 "cpu_baseline": cpu,
-                "e2e": {"value": world * args.steps / (e2e_ms * 1e-3), "unit": UNIT,
+                "e2e": {"value": whole_job_rate(world, args.steps, e2e_ms), "unit": UNIT,
                         "h2d_bytes_per_step": m.nv * 8, "d2h_bytes_per_step": m.nv * 8 + 16},
                 "gpu_launches": int(launches32), "clocks": clocks,
                 "impl": "ours"}
