@@ -830,55 +830,64 @@ cgs_status host_setup(const double* xyz, int64_t nv, const int32_t* conn, int64_
                     }
                 }
             }
+            // cells in chunks: each chunk's cells assembled in parallel into
+            // their own blocks, then added into A_r in cell order (the sums do
+            // not depend on the thread count)
+            constexpr int64_t kChunk = 64;
+            std::vector<std::vector<int32_t>> Uc(kChunk);
+            std::vector<std::vector<double>> Kc(kChunk);
+            for (int64_t c0 = 0; c0 < ncell; c0 += kChunk) {
+                const int64_t c1 = std::min(ncell, c0 + kChunk);
 #pragma omp parallel
-            {
-                std::vector<int32_t> U;
-                std::vector<double> KL;
-                std::vector<std::pair<int32_t, double>> rows[8];
-#pragma omp for schedule(dynamic, 4)
-                for (int64_t c = 0; c < ncell; ++c) {
-                    // the cell's columns, then its elements' J^T A^e J on them
-                    U.clear();
-                    for (int64_t i = cell_ptr[c]; i < cell_ptr[c + 1]; ++i) {
-                        const int64_t e = S.elem_order[i];
-                        for (int k = 0; k < 8; ++k) {
-                            const int32_t v = conn[e * 8 + k];
-                            for (int64_t o = jr_ptr[v]; o < jr_ptr[v + 1]; ++o)
-                                if (jr_col[o] >= 0) U.push_back(jr_col[o]);
-                        }
-                    }
-                    std::sort(U.begin(), U.end());
-                    U.erase(std::unique(U.begin(), U.end()), U.end());
-                    const size_t L = U.size();
-                    if (!L) continue;
-                    KL.assign(L * L, 0.0);
-                    for (int64_t i = cell_ptr[c]; i < cell_ptr[c + 1]; ++i) {
-                        const int64_t e = S.elem_order[i];
-                        for (int k = 0; k < 8; ++k) {
-                            rows[k].clear();
-                            const int32_t v = conn[e * 8 + k];
-                            for (int64_t o = jr_ptr[v]; o < jr_ptr[v + 1]; ++o)
-                                if (jr_col[o] >= 0 && jr_val[o] != 0.0)
-                                    rows[k].emplace_back(
-                                        (int32_t)(std::lower_bound(U.begin(), U.end(), jr_col[o]) - U.begin()),
-                                        jr_val[o]);
-                        }
-                        const double* A = &Ae[(size_t)e * 64];
-                        for (int k = 0; k < 8; ++k)
-                            for (int l = 0; l < 8; ++l) {
-                                const double a = A[k * 8 + l];
-                                if (a == 0.0) continue;
-                                for (const auto& ri : rows[k])
-                                    for (const auto& rj : rows[l]) KL[(size_t)ri.first * L + rj.first] += a * ri.second * rj.second;
+                {
+                    std::vector<std::pair<int32_t, double>> rows[8];
+#pragma omp for schedule(dynamic, 1)
+                    for (int64_t c = c0; c < c1; ++c) {
+                        // the cell's columns, then its elements' J^T A^e J on them
+                        std::vector<int32_t>& U = Uc[c - c0];
+                        std::vector<double>& KL = Kc[c - c0];
+                        U.clear();
+                        for (int64_t i = cell_ptr[c]; i < cell_ptr[c + 1]; ++i) {
+                            const int64_t e = S.elem_order[i];
+                            for (int k = 0; k < 8; ++k) {
+                                const int32_t v = conn[e * 8 + k];
+                                for (int64_t o = jr_ptr[v]; o < jr_ptr[v + 1]; ++o)
+                                    if (jr_col[o] >= 0) U.push_back(jr_col[o]);
                             }
-                    }
-                    for (size_t i = 0; i < L; ++i)
-                        for (size_t j = 0; j < L; ++j) {
-                            const double val = KL[i * L + j];
-                            if (val == 0.0) continue;
-#pragma omp atomic
-                            Ar[(size_t)U[i] * nr + U[j]] += val;
                         }
+                        std::sort(U.begin(), U.end());
+                        U.erase(std::unique(U.begin(), U.end()), U.end());
+                        const size_t L = U.size();
+                        KL.assign(L * L, 0.0);
+                        for (int64_t i = cell_ptr[c]; i < cell_ptr[c + 1]; ++i) {
+                            const int64_t e = S.elem_order[i];
+                            for (int k = 0; k < 8; ++k) {
+                                rows[k].clear();
+                                const int32_t v = conn[e * 8 + k];
+                                for (int64_t o = jr_ptr[v]; o < jr_ptr[v + 1]; ++o)
+                                    if (jr_col[o] >= 0 && jr_val[o] != 0.0)
+                                        rows[k].emplace_back(
+                                            (int32_t)(std::lower_bound(U.begin(), U.end(), jr_col[o]) - U.begin()),
+                                            jr_val[o]);
+                            }
+                            const double* A = &Ae[(size_t)e * 64];
+                            for (int k = 0; k < 8; ++k)
+                                for (int l = 0; l < 8; ++l) {
+                                    const double a = A[k * 8 + l];
+                                    if (a == 0.0) continue;
+                                    for (const auto& ri : rows[k])
+                                        for (const auto& rj : rows[l])
+                                            KL[(size_t)ri.first * L + rj.first] += a * ri.second * rj.second;
+                                }
+                        }
+                    }
+                }
+                for (int64_t c = c0; c < c1; ++c) {
+                    const std::vector<int32_t>& U = Uc[c - c0];
+                    const std::vector<double>& KL = Kc[c - c0];
+                    const size_t L = U.size();
+                    for (size_t i = 0; i < L; ++i)
+                        for (size_t j = 0; j < L; ++j) Ar[(size_t)U[i] * nr + U[j]] += KL[i * L + j];
                 }
             }
         } else {

@@ -61,6 +61,11 @@ def test_coarse_operators_match_oracle(tmp_path):
     assert res.returncode == 0, res.stderr[-3000:]
     dump = str(tmp_path / "ar.txt")
     assert subprocess.run([exe, dump], timeout=300).returncode == 0
+    # the assembly does not depend on the number of threads
+    one = str(tmp_path / "ar1.txt")
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    assert subprocess.run([exe, one], timeout=300, env=env).returncode == 0
+    assert open(one).read() == open(dump).read()
     lines = open(dump).read().split("\n")
     nv = int(lines[0])
     xyz = np.array([[float(t) for t in line.split()] for line in lines[1:1 + nv]])
