@@ -96,3 +96,25 @@ def test_binding_constants_match_header():
     assert int(defs["CGS_NOALLOC_MAX_NV"]) == cgs.NOALLOC_MAX_NV
     assert int(defs["CGS_NOALLOC_MAX_NR"]) == cgs.NOALLOC_MAX_NR
     assert int(defs["CGS_PROJECTION_MAX"]) == cgs.PROJECTION_MAX
+
+
+def _struct_fields(name):
+    text = open(os.path.join(ROOT, "include", "cgs.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    body = re.search(r"typedef struct \{([^}]*)\}\s*" + name + ";", text).group(1)
+    names = []
+    for decl in body.split(";"):
+        decl = decl.strip()
+        if not decl:
+            continue
+        for part in decl.split(","):
+            m = re.search(r"(\w+)\s*(\[\d+\])?\s*$", part.strip())
+            names.append(m.group(1))
+    return names
+
+
+@pytest.mark.parametrize("cname,py", [("cgs_params", "Params"), ("cgs_mesh_info_t", "MeshInfo"),
+                                      ("cgs_schedule", "Schedule")])
+def test_binding_structs_follow_the_header(cname, py):
+    """Every ABI struct of the binding has the header's fields in its order."""
+    assert [f[0] for f in getattr(cgs, py)._fields_] == _struct_fields(cname)
