@@ -27,6 +27,10 @@ A u = b, Sec. 3):
   nested-dissection order of the box lattice;
 * the preconditioners ASM (Eq. asm) and the hybrid ASM_1 + ASM_2 (Eqs. asm1,
   asm2);
+* variants and wrappers for the next steps: restricted additive Schwarz
+  (Sec. 3, R~_p without the grown part), inexact local solves by a fixed
+  number of CG steps (Sec. 6), Schwarz-Richardson and flexible GMRES
+  wrappers, and any Dirichlet set (Neumann except an outflow cap, Sec. 5);
 * repeated right-hand sides (Sec. 5, the projection onto prior solutions):
   the start is the A-orthogonal best fit onto up to l earlier solutions and
   the iteration solves for the change;
@@ -166,6 +170,11 @@ class Problem:
         E2V.sum_duplicates()
         E2V.data[:] = 1.0
         S = sp.csr_array((np.ones(ne), (self.part, np.arange(ne))), shape=(nparts, ne))
+        # vertices of the original (not grown) subdomains, for RAS
+        own = (S @ E2V).tocsr()
+        own.data[:] = 1.0
+        self.own_mult = np.asarray(own.sum(axis=0)).ravel()         # original subdomains holding v
+        self._own = own
         for _ in range(overlap):   # add every element sharing a vertex with Omega_p
             touched_v = (S @ E2V)
             touched_v.data[:] = 1.0
@@ -205,18 +214,32 @@ class Problem:
             except np.linalg.LinAlgError as exc:
                 raise ValueError("local matrix not SPD") from exc
             self.groups[int(m)] = (ps, I, Ap, L)
+        # RAS prolongation weights (Sec. 3: R~_p^T is R_p^T with the columns of
+        # the grown part Omega~_p minus Omega_p null; the surface nodes that
+        # several original subdomains store are averaged for continuity)
+        self.ras_w = {}
+        for m, (ps, I, Ap, L) in self.groups.items():
+            inown = np.stack([np.asarray(self._own[[p]].toarray()).ravel()[I[g]] for g, p in enumerate(ps)])
+            self.ras_w[m] = np.where(inown > 0, 1.0 / np.maximum(self.own_mult[I], 1.0), 0.0)
 
-    def local_solves(self, r, weighted: bool):
-        """sum_p R_p^T A_p^{-1} R_p r, optionally scaled by W_ov = 1/multiplicity
-        (Eq. asm1 with R~_p = R_p)."""
+    def local_solves(self, r, weighted, inner: int = 0):
+        """sum_p R~_p^T A_p^{-1} R_p r (Eq. asm, asm1).  weighted: True scales
+        by W_ov = 1/multiplicity (R~_p = R_p); False adds plainly; "ras" uses
+        the restricted prolongation.  inner > 0 replaces A_p^{-1} by that many
+        CG steps on A_p from zero (an inexact local solve, Sec. 6)."""
         r = np.asarray(r, dtype=np.float64)
         out = np.zeros(self.nv)
         for m, (ps, I, Ap, L) in self.groups.items():
-            rp = r[I][..., None]                                    # R_p r
-            y = sla.solve_triangular(L, rp, lower=True)
-            y = sla.solve_triangular(np.swapaxes(L, 1, 2), y, lower=False)[..., 0]
-            np.add.at(out, I.ravel(), y.ravel())                    # R_p^T, summed
-        if weighted:
+            rp = r[I]                                               # R_p r
+            if inner > 0:
+                y = _batched_cg(Ap, rp, inner)
+            else:
+                y = sla.solve_triangular(L, rp[..., None], lower=True)
+                y = sla.solve_triangular(np.swapaxes(L, 1, 2), y, lower=False)[..., 0]
+            if weighted == "ras":
+                y = y * self.ras_w[m]
+            np.add.at(out, I.ravel(), y.ravel())                    # R~_p^T, summed
+        if weighted is True:
             nz = self.mult > 0
             out[nz] /= self.mult[nz]
         return out
@@ -395,6 +418,8 @@ class Problem:
             return l + self.box_correction(s)
         if form == "additive":                  # Eq. asm
             return self.local_solves(r, weighted=False) + self.box_correction(r)
+        if form == "ras":                       # Eq. asm with the restricted R~_p (RAS)
+            return self.local_solves(r, weighted="ras") + self.box_correction(r)
         if form == "local":                     # ASM_1 alone
             return self.local_solves(r, weighted=True)
         if form == "box":                       # J A_r^{-1} J^T alone
@@ -461,6 +486,77 @@ def xxt_basis(A, order):
         x /= np.sqrt(x @ A @ x)
         X[:, k] = x
     return X
+
+
+def _batched_cg(Ap, rp, steps: int):
+    """`steps` CG iterations on each A_p y = r_p of a group, from y = 0."""
+    y = np.zeros_like(rp)
+    res = rp.copy()
+    d = res.copy()
+    rr = np.einsum("gi,gi->g", res, res)
+    for _ in range(steps):
+        Ad = np.einsum("gij,gj->gi", Ap, d)
+        dAd = np.einsum("gi,gi->g", d, Ad)
+        a = np.where(dAd > 0, rr / np.where(dAd > 0, dAd, 1.0), 0.0)
+        y += a[:, None] * d
+        res -= a[:, None] * Ad
+        rr_new = np.einsum("gi,gi->g", res, res)
+        d = res + np.where(rr > 0, rr_new / np.where(rr > 0, rr, 1.0), 0.0)[:, None] * d
+        rr = rr_new
+    return y
+
+
+def richardson(apply_A, apply_M, b, rtol, maxit, theta: float = 1.0):
+    """Schwarz-Richardson (the paper's alternative wrapper): x += theta M (b -
+    A x) from x = 0 until ||b - A x|| <= rtol ||b||.  Returns (x, iters,
+    relres, converged)."""
+    x = np.zeros_like(b)
+    nb = float(np.linalg.norm(b))
+    r = b.copy()
+    for k in range(maxit + 1):
+        rel = float(np.linalg.norm(r)) / nb if nb > 0 else 0.0
+        if rel <= rtol:
+            return x, k, rel, True
+        if k == maxit:
+            return x, k, rel, False
+        x = x + theta * apply_M(r)
+        r = b - apply_A(x)
+
+
+def fgmres(apply_A, apply_M, b, rtol, maxit, restart: int = 30):
+    """Right-preconditioned flexible GMRES(restart) from x = 0 (the paper's
+    GMRES wrapping; flexible, so M may change between steps): the Arnoldi
+    basis V of the preconditioned directions Z = M V, x = Z y with y the
+    least-squares minimiser of ||beta e_1 - H y||.  Returns (x, products A z,
+    relres of b - A x, converged)."""
+    x = np.zeros_like(b)
+    nb = float(np.linalg.norm(b))
+    if nb == 0.0:
+        return x, 0, 0.0, True
+    its = 0
+    while True:
+        r = b - apply_A(x)
+        beta = float(np.linalg.norm(r))
+        if beta <= rtol * nb or its >= maxit:
+            return x, its, beta / nb, beta <= rtol * nb
+        V, Z = [r / beta], []
+        H = np.zeros((restart + 1, restart))
+        for j in range(restart):
+            Z.append(apply_M(V[j]))
+            w = apply_A(Z[j])
+            its += 1
+            for i in range(j + 1):                 # modified Gram-Schmidt
+                H[i, j] = float(V[i] @ w)
+                w = w - H[i, j] * V[i]
+            H[j + 1, j] = float(np.linalg.norm(w))
+            e1 = np.zeros(j + 2)
+            e1[0] = beta
+            y, *_ = np.linalg.lstsq(H[:j + 2, :j + 1], e1, rcond=None)
+            res = float(np.linalg.norm(e1 - H[:j + 2, :j + 1] @ y))
+            if res <= rtol * nb or its >= maxit or H[j + 1, j] == 0.0:
+                break
+            V.append(w / H[j + 1, j])
+        x = x + np.array(Z).T @ y
 
 
 class Projection:

@@ -181,6 +181,14 @@ def cylinder(nr: int = 64, nt: int = 128, nz: int = 128, r_in: float = 1.0, r_ou
                 name=name, meta={"dims": dims, "h0": h0, "length": length})
 
 
+def outflow_dirichlet(mesh, axis: int = 2) -> np.ndarray:
+    """Dirichlet mask for Neumann boundaries everywhere except an outflow cap:
+    the vertices at the largest coordinate along `axis` (the end of the
+    cylinder or the top of a cube), as uint8 (1 = Dirichlet)."""
+    c = mesh.xyz[:, axis]
+    return (c >= c.max() - 1e-12 * max(abs(c.max()), 1.0)).astype(np.uint8)
+
+
 def rhs(nv: int, seed, count: int | None = None) -> np.ndarray:
     """i.i.d. N(0,1) right-hand side(s) of length nv from ``default_rng(seed)``."""
     rng = np.random.default_rng(seed)

@@ -635,3 +635,116 @@ def test_full_support_variants_have_the_wider_stencil(op):
     s, u = rng.standard_normal(m.nv), rng.standard_normal(Pv.nr)
     s[Pv.dir] = 0.0
     assert abs(Pv.restrict(s) @ u - s @ Pv.interp(u)) <= 1e-12 * np.abs(s).sum() * np.abs(u).max()
+
+
+# --------------------------------------------------------------------------
+# wrappers and local variants (Sec. 3 RAS, Sec. 5 boundary conditions,
+# Sec. 6 inexact local solves; the Schwarz-Richardson and GMRES wrappers)
+# --------------------------------------------------------------------------
+
+def test_ras_without_overlap_equals_the_additive_local_sum():
+    m, _ = meshes.workload_cube8()
+    P = O.Problem(m.xyz, m.conn, m.part, m.boxes, overlap=0)
+    r = np.random.default_rng(21).standard_normal(m.nv)
+    np.testing.assert_allclose(P.local_solves(r, "ras"), P.local_solves(r, False), rtol=0, atol=1e-14)
+
+
+def test_ras_prolongation_is_a_partition_of_unity():
+    """With overlap the restricted prolongations sum to one at every free
+    node, and a single subdomain gives A^{-1} r."""
+    m, _ = meshes.workload_cube8()
+    P = O.Problem(m.xyz, m.conn, m.part, m.boxes)
+    tot = np.zeros(m.nv)
+    for mm, (ps, I, Ap, L) in P.groups.items():
+        np.add.at(tot, I.ravel(), P.ras_w[mm].ravel())
+    assert np.allclose(tot[P.free], 1.0, rtol=0, atol=1e-15)
+    one = O.Problem(m.xyz, m.conn, np.zeros(m.ne, int), m.boxes)
+    r = np.random.default_rng(22).standard_normal(m.nv)
+    x = np.zeros(m.nv)
+    x[one.free] = np.linalg.solve(one.A.toarray(), r[one.free])
+    np.testing.assert_allclose(one.local_solves(r, "ras"), x, rtol=0, atol=1e-12 * np.abs(x).max())
+
+
+def test_inexact_local_solves():
+    """m_p CG steps solve each local system (to rounding); two steps do not."""
+    m, _ = meshes.workload_cube8()
+    P = O.Problem(m.xyz, m.conn, m.part, m.boxes)
+    r = np.random.default_rng(23).standard_normal(m.nv)
+    exact = P.local_solves(r, True)
+    full = P.local_solves(r, True, inner=max(P.groups))
+    assert np.abs(full - exact).max() <= 1e-9 * np.abs(exact).max()
+    assert np.abs(P.local_solves(r, True, inner=2) - exact).max() > 1e-3 * np.abs(exact).max()
+
+
+def test_schwarz_richardson_converges_at_the_spectral_radius():
+    """x += M (b - A x) with the hybrid M: the fixed point is A^{-1} b, and the
+    residual shrinks at the spectral radius of I - M A (dense eigenvalues)."""
+    m, b = meshes.workload_cube8()
+    P = O.Problem(m.xyz, m.conn, m.part, m.boxes)
+    bb = np.where(P.dir, 0.0, b)
+    x, it, rel, ok = O.richardson(P.apply_A, P.apply_M, bb, 1e-10, 200)
+    ref = _direct(P, bb)
+    assert ok and np.abs(x - ref).max() <= 1e-8 * np.abs(ref).max()
+    n = P.free.size
+    E = np.zeros((n, n))
+    for j in range(n):
+        e = np.zeros(P.nv)
+        e[P.free[j]] = 1.0
+        E[:, j] = e[P.free] - P.apply_M(P.apply_A(e))[P.free]
+    rho = np.abs(np.linalg.eigvals(E)).max()
+    assert rho < 1.0
+    # iterations needed for 1e-10 agree with the rate within a few steps
+    assert abs(it - np.log(1e-10) / np.log(rho)) <= 0.25 * it + 3
+
+
+def test_fgmres_minimises_the_residual_over_the_krylov_space():
+    """Without a preconditioner, k steps give the least-squares minimum of
+    ||b - A x|| over span{b, A b, ..., A^{k-1} b} (formed densely)."""
+    m, b = meshes.workload_cube8()
+    P = O.Problem(m.xyz, m.conn, m.part, m.boxes)
+    bb = np.where(P.dir, 0.0, b)
+    k = 6
+    x, it, rel, ok = O.fgmres(P.apply_A, lambda v: v.copy(), bb, 1e-30, k, restart=k)
+    A = P.A.toarray()
+    K = [bb[P.free]]
+    for _ in range(k - 1):
+        K.append(A @ K[-1])
+    Q, _ = np.linalg.qr(np.array(K).T)
+    c, *_ = np.linalg.lstsq(A @ Q, bb[P.free], rcond=None)
+    best = np.linalg.norm(bb[P.free] - A @ (Q @ c)) / np.linalg.norm(bb)
+    assert it == k and abs(rel - best) <= 1e-9 * best
+
+
+def test_fgmres_with_schwarz_matches_direct_and_pcg():
+    m, b = meshes.workload_cube8()
+    P = O.Problem(m.xyz, m.conn, m.part, m.boxes)
+    bb = np.where(P.dir, 0.0, b)
+    ref = _direct(P, bb)
+    for form in ("hybrid", "ras"):
+        x, it, rel, ok = O.fgmres(P.apply_A, lambda r: P.apply_M(r, form), bb, 1e-10, 200)
+        assert ok and np.abs(x - ref).max() <= 1e-8 * np.abs(ref).max()
+    # inexact local solves need the flexible outer iteration
+    x, it, rel, ok = O.fgmres(P.apply_A, lambda r: P.local_solves(r, True, inner=3) + P.box_correction(r),
+                              bb, 1e-10, 300)
+    assert ok and np.abs(x - ref).max() <= 1e-8 * np.abs(ref).max()
+
+
+def test_outflow_dirichlet_problem():
+    """Neumann everywhere except the outflow cap (Sec. 5): A stays SPD, the
+    box functions inherit the condition through J (zero rows at the cap),
+    and the hybrid PCG solve matches the dense solve."""
+    m, b = meshes.workload_cylinder(scale=8)
+    d = meshes.outflow_dirichlet(m).astype(bool)
+    P = O.Problem(m.xyz, m.conn, m.part, m.boxes, dirichlet=d)
+    assert d.sum() > 0 and P.free.size == m.nv - d.sum()
+    assert np.linalg.eigvalsh(P.A.toarray()).min() > 0.0
+    u = np.random.default_rng(7).standard_normal(P.nr)
+    assert np.all(P.interp(u)[d] == 0.0)
+    bb = np.where(d, 0.0, b)
+    ref = _direct(P, bb)
+    x, it, rel, ok = P.solve(bb, rtol=1e-10, maxit=1000, form="additive")
+    assert ok and rel <= 2e-10 and np.abs(x - ref).max() <= 1e-7 * np.abs(ref).max()
+    # the weighted hybrid form converges too, far more slowly on this 2^3-box
+    # space (about 1,500 products against about 250)
+    x, it2, rel, ok = P.solve(bb, rtol=1e-10, maxit=3000)
+    assert ok and it2 > it and np.abs(x - ref).max() <= 1e-7 * np.abs(ref).max()
