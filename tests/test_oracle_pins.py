@@ -349,6 +349,111 @@ def _dense_M(P, form):
     return np.array(cols).T
 
 
+def _cell_by_search(P, point):
+    """Box cell holding `point`, by searching the cell intervals along each
+    axis (the top face belongs to the last cell)."""
+    c = []
+    for d in range(3):
+        edges = P.box_lo[d] + P.box_H[d] * np.arange(P.box_b[d] + 1)
+        k = 0
+        while k < P.box_b[d] - 1 and not (edges[k] <= point[d] < edges[k + 1]):
+            k += 1
+        c.append(k)
+    return np.array(c)
+
+
+def _brute_force_coarse(P, m):
+    """Cell of each element's centroid, the averaged interpolant J~ = W Q^T J_L
+    (dense, free rows, active columns) and A_r = sum_e J_e^T A^e J_e (Eq. Aij),
+    element by element with Python loops (Sec. 4: each element belongs to the
+    box cell holding its centroid, and interpolates trilinearly from that
+    cell's eight corners, extrapolating where its vertices lie outside)."""
+    nb = P.box_b + 1
+    col = {g: j for j, g in enumerate(P.box_active)}
+    nf = P.free.size
+    Jt = np.zeros((nf, P.nr))
+    Ar = np.zeros((P.nr, P.nr))
+    cells = np.zeros((m.ne, 3), dtype=np.int64)
+    cnt = np.bincount(m.conn.ravel(), minlength=m.nv)
+    for e in range(m.ne):
+        X = m.xyz[m.conn[e]]
+        c = _cell_by_search(P, X.mean(axis=0))
+        cells[e] = c
+        Je = np.zeros((8, 8))
+        cols = []
+        for q in range(8):          # cell corner q = a + 2b + 4c
+            bits = np.array([q & 1, (q >> 1) & 1, (q >> 2) & 1])
+            cols.append(col.get(int((c[0] + bits[0]) + nb[0] * ((c[1] + bits[1]) + nb[1] * (c[2] + bits[2]))), -1))
+            for k in range(8):
+                t = (X[k] - (P.box_lo + c * P.box_H)) / P.box_H
+                w = 1.0
+                for d in range(3):
+                    w *= t[d] if bits[d] else 1.0 - t[d]
+                Je[k, q] = 0.0 if P.dir[m.conn[e, k]] else w
+        Ke = Je.T @ P.Ae[e] @ Je
+        for q in range(8):
+            if cols[q] < 0:
+                continue
+            for k in range(8):
+                v = m.conn[e, k]
+                if not P.dir[v]:
+                    Jt[P.free_pos[v], cols[q]] += Je[k, q] / cnt[v]
+            for q2 in range(8):
+                if cols[q2] >= 0:
+                    Ar[cols[q], cols[q2]] += Ke[q, q2]
+    return cells, Jt, Ar
+
+
+@pytest.fixture(scope="module")
+def perturbed4():
+    m = meshes.cube(4, perturb=0.15, seed=0, boxes=(2, 2, 2))
+    return m, O.Problem(m.xyz, m.conn, m.part, m.boxes)
+
+
+def test_element_cells_follow_the_centroid(perturbed4):
+    """Sec. 4 assigns each element to the box cell holding its centroid.  On
+    this perturbed mesh the cell of an element's first vertex differs from
+    its centroid's for some elements, so a rule that took any vertex's cell
+    fails here; the reduced operator assembled from the searched cells equals
+    the oracle's A_r."""
+    m, P = perturbed4
+    cells, Jt, Ar = _brute_force_coarse(P, m)
+    np.testing.assert_array_equal(P.cell, cells)
+    first = np.array([_cell_by_search(P, m.xyz[m.conn[e, 0]]) for e in range(m.ne)])
+    assert (first != cells).any(axis=1).sum() >= 4
+    np.testing.assert_allclose(P.Ar, Ar, rtol=0, atol=1e-13 * np.abs(Ar).max())
+
+
+@pytest.mark.parametrize("form", ["hybrid", "additive"])
+def test_preconditioner_matches_its_dense_formula(perturbed4, form):
+    """M applied to every unit vector equals the matrix composed from dense
+    factors (Sec. 3, Eqs. asm, asm1, asm2; Sec. 4, J~ = W Q^T J_L):
+      additive  sum_p R_p^T A_p^{-1} R_p + J~ A_r^{-1} J~^T
+      hybrid    M_1 + J~ A_r^{-1} J~^T (I - A M_1),  M_1 = W_ov sum_p R_p^T A_p^{-1} R_p
+    with R_p the selection matrices of the subdomain index sets, W_ov their
+    inverse multiplicities, and J~ and A_r from the element-by-element
+    construction."""
+    m, P = perturbed4
+    _, Jt, Ar = _brute_force_coarse(P, m)
+    A = P.A.toarray()
+    nf = P.free.size
+    S = np.zeros((nf, nf))
+    mult = np.zeros(nf)
+    for idx in P.sub_idx:
+        R = np.zeros((idx.size, nf))
+        R[np.arange(idx.size), P.free_pos[idx]] = 1.0
+        S += R.T @ np.linalg.inv(R @ A @ R.T) @ R
+        mult += R.sum(axis=0)
+    B = Jt @ np.linalg.inv(Ar) @ Jt.T
+    if form == "additive":
+        ref = S + B
+    else:
+        M1 = np.diag(1.0 / mult) @ S
+        ref = M1 + B @ (np.eye(nf) - A @ M1)
+    M = _dense_M(P, form)
+    assert np.abs(M - ref).max() <= 1e-13 * np.abs(ref).max()
+
+
 def test_additive_preconditioner_symmetric_positive_definite():
     m = meshes.cube(4, perturb=0.15, seed=0, boxes=(2, 2, 2))
     P = O.Problem(m.xyz, m.conn, m.part, m.boxes)
