@@ -176,8 +176,13 @@ size_t cgs_ctx_bytes_in_use(const cgs_ctx* ctx);
  *   params    host; NULL = 4x4x4 boxes, margin 0, delta 1, FP64, hybrid
  * Host work: element matrices (2x2x2 Gauss), Dirichlet set, grown subdomains
  * and the explicit inverses of A_p = R_p A R_p^T (Cholesky, float64), box
- * grid, centroid cells, active box vertices, A_r by cell assembly (Eq. Aij)
- * and its inverse (float64).  Then one upload to the device.  Synchronous.
+ * grid, centroid cells, active box vertices, the reduced operator A_r chosen
+ * by params->coarse_operator (cell-wise assembly of Eq. Aij, Galerkin
+ * J~^T A J~, or vertex-based J^T A J; Sec. 4), and its reduced solver chosen
+ * by params->coarse_solver (explicit dense inverse, or the XX^T factor X of
+ * Sec. 2 in a nested-dissection order), all in float64; the mixed forms also
+ * keep hi/lo float-pair copies of A_r^{-1} or X.  Then one upload to the
+ * device.  Synchronous.
  * Errors: INVALID_ARG, INVALID_MESH (index out of range, Jacobian <= 0 at a
  * quadrature point, empty mesh), NOT_SPD, ADMISSION, OOM, CUDA.  On error
  * *out is NULL and nothing stays allocated.                                 */
@@ -197,14 +202,50 @@ cgs_status cgs_mesh_export(const cgs_mesh* mesh, uint8_t* dirichlet, int64_t* bo
                            int64_t* sub_ptr, int32_t* sub_idx);
 
 /* ---- hot-path steps, device vectors, stream-ordered -------------------------
+ * These single-step calls use the mesh's scratch vectors (so they must not
+ * overlap each other or a solve on the same mesh).  A bounded device-side wait
+ * that expires inside one of them (only the TMA-staged element tiles of the
+ * mixed-form applies wait) skips the rest of that call's work and is recorded
+ * in the mesh's step status word; cgs_mesh_step_status reports it.
+ *
  * cgs_apply_A: y = A x, A = Q^T A_L Q (Sec. 3), float64.  x, y device, nv.  */
 cgs_status cgs_apply_A(cgs_mesh* mesh, const double* x, double* y, void* stream);
+/* cgs_apply_A_prec: y = A x (Sec. 3) evaluated by one of the mesh's operator
+ * kernels, for checking each precision form against its error bound:
+ *   CGS_OP_FP64   the float64 operator (as cgs_apply_A);
+ *   CGS_OP_INNER  the inner apply of the hybrid step (Eq. asm2, s = r - A l):
+ *                 x rounded to float32, 28 float32 off-diagonals per element,
+ *                 float32 sums, then widened to float64;
+ *   CGS_OP_OUTER  the outer operator of the PCG (q = A p): hi/lo float pairs
+ *                 (about 48 bits) in the mixed forms.
+ * In the FP64 form every op is the float64 operator.  x, y device, nv; Dirichlet
+ * entries of x are ignored and y is 0 there.  INVALID_ARG for an unknown op.  */
+enum { CGS_OP_FP64 = 0, CGS_OP_INNER = 1, CGS_OP_OUTER = 2 };
+cgs_status cgs_apply_A_prec(cgs_mesh* mesh, const double* x, double* y, int op, void* stream);
+/* cgs_mesh_step_status: waits for `stream`, then returns CGS_ERR_TIMEOUT if a
+ * bounded device wait expired in a single-step call on this mesh (any call of
+ * this section and cgs_apply_preconditioner_noalloc) since the last query,
+ * else CGS_OK; the status word is reset either way.                          */
+cgs_status cgs_mesh_step_status(cgs_mesh* mesh, void* stream);
+/* cgs_mesh_set_wait_limits: iteration limits of the bounded device-side waits
+ * of this mesh's kernels: tile_wait for the element-tile TMA copies (default
+ * 1 << 20 polls) and barrier_wait for the grid barriers of the persistent loop
+ * (default 1 << 22 polls).  A testing aid: 0 makes every such wait give up at
+ * once, so the timeout path (CGS_ERR_TIMEOUT, the call's work skipped, the
+ * context still usable) runs without any fault.  A block that gives up still
+ * waits, with its own limit, for the copy it started before it returns.
+ * Synchronous.  INVALID_ARG for a negative limit.                            */
+cgs_status cgs_mesh_set_wait_limits(cgs_mesh* mesh, int tile_wait, int barrier_wait);
 /* cgs_apply_local: l = sum_p R_p^T A_p^{-1} R_p r (Eq. asm1), weighted by
  * W_ov = 1/multiplicity when `weighted` != 0.  Mesh precision.              */
 cgs_status cgs_apply_local(cgs_mesh* mesh, const double* r, double* l, int weighted, void* stream);
 /* cgs_restrict: r_r = J_L^T Q W s (Sec. 4); s device nv, r_r device n_r.     */
 cgs_status cgs_restrict(cgs_mesh* mesh, const double* s, double* rr, void* stream);
-/* cgs_coarse_solve: u_r = A_r^{-1} r_r, float64; device n_r vectors.        */
+/* cgs_coarse_solve: u_r = A_r^{-1} r_r (Sec. 4) by the mesh's reduced solver
+ * (dense explicit inverse, or XX^T, Sec. 2); device n_r vectors, float64 in and
+ * out.  The FP64 form computes in float64; the mixed forms keep A_r^{-1} (or
+ * X) and r_r as hi/lo float pairs (about 48 bits) and multiply on the FP32
+ * pipes.                                                                     */
 cgs_status cgs_coarse_solve(cgs_mesh* mesh, const double* rr, double* ur, void* stream);
 /* cgs_interp: z = W Q^T J_L u_r (Sec. 4); u_r device n_r, z device nv.       */
 cgs_status cgs_interp(cgs_mesh* mesh, const double* ur, double* z, void* stream);
@@ -236,9 +277,9 @@ cgs_status cgs_mesh_projection_size(const cgs_mesh* mesh, int* k);
 /* ---- preconditioner apply without allocation -------------------------------
  * cgs_apply_preconditioner_noalloc: the same z = M r as
  * cgs_apply_preconditioner, for callers that must not allocate device memory
- * at call time: code that runs while a stream is being captured into a CUDA
- * graph, serving loops that forbid allocations after warm-up, and hosts whose
- * device memory is owned by another runtime's pool.  The call performs no
+ * at call time: serving loops that forbid allocations after warm-up, and hosts
+ * whose device memory is owned by another runtime's pool (an allocation there
+ * would bypass that pool's accounting or fail outright).  The call performs no
  * cudaMalloc or cudaFree and uses no allocating library routine.  Its working
  * vectors (z and s in the bulk precision, r_r, u_r and the XX^T pass's t)
  * live in one static
@@ -253,8 +294,10 @@ cgs_status cgs_mesh_projection_size(const cgs_mesh* mesh, int* k);
  *           previous call's contents (the call clears what must start at 0).
  *           Calls that overlap on the GPU (other streams, other threads, or
  *           another mesh) race on it: serialise them.
+ *   status  an expired element-tile wait is recorded in the mesh's step
+ *           status word (cgs_mesh_step_status), which setup allocated.
  * r, z device vectors of length nv; stream-ordered.  The paper has no
- * counterpart; this is a deployment variant of Eqs. asm / asm1-asm2.       */
+ * counterpart.                                                              */
 #define CGS_NOALLOC_MAX_NV 131072
 #define CGS_NOALLOC_MAX_NR 8192
 #define CGS_NOALLOC_SCRATCH_BYTES ((size_t)16 * CGS_NOALLOC_MAX_NV + (size_t)24 * CGS_NOALLOC_MAX_NR)

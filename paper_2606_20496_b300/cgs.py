@@ -23,11 +23,13 @@ PREC = {"fp64": 0, "fp32": 1, "fp16": 2}
 FORM = {"hybrid": 0, "additive": 1}
 COARSE = {"auto": 0, "dense": 1, "xxt": 2}
 COARSE_OP = {"cellwise": 0, "galerkin": 1, "vertex": 2}
+OP = {"fp64": 0, "inner": 1, "outer": 2}
 
 # every symbol include/cgs.h declares
 EXPORTS = (
     "cgs_create", "cgs_destroy", "cgs_ctx_bytes_in_use", "cgs_mesh_setup", "cgs_mesh_free", "cgs_mesh_info",
-    "cgs_mesh_set_form", "cgs_mesh_export", "cgs_apply_A", "cgs_apply_local", "cgs_restrict",
+    "cgs_mesh_set_form", "cgs_mesh_export", "cgs_apply_A", "cgs_apply_A_prec", "cgs_mesh_step_status",
+    "cgs_mesh_set_wait_limits", "cgs_apply_local", "cgs_restrict",
     "cgs_coarse_solve", "cgs_interp", "cgs_apply_preconditioner", "cgs_apply_preconditioner_noalloc",
     "cgs_solve", "cgs_solve_host", "cgs_mesh_set_projection", "cgs_mesh_projection_size",
     "cgs_profile_enable", "cgs_profile_read", "cgs_batch_create", "cgs_batch_free", "cgs_batch_solve",
@@ -90,6 +92,9 @@ def load(path: str = LIB_PATH):
         "cgs_mesh_set_form": ([P, I32], I32),
         "cgs_mesh_export": ([P, P, P, P, P], I32),
         "cgs_apply_A": ([P, P, P, P], I32),
+        "cgs_apply_A_prec": ([P, P, P, I32, P], I32),
+        "cgs_mesh_step_status": ([P, P], I32),
+        "cgs_mesh_set_wait_limits": ([P, I32, I32], I32),
         "cgs_apply_local": ([P, P, P, I32, P], I32),
         "cgs_restrict": ([P, P, P, P], I32),
         "cgs_coarse_solve": ([P, P, P, P], I32),
@@ -230,6 +235,23 @@ def cgs_mesh_export(mesh) -> dict:
 
 def cgs_apply_A(mesh, x, y, stream=None):
     _check(load().cgs_apply_A(mesh, _ptr(x), _ptr(y), _stream(stream)), "cgs_apply_A")
+
+
+def cgs_apply_A_prec(mesh, x, y, op="inner", stream=None):
+    """y = A x by the operator kernel `op` ("fp64", "inner" or "outer")."""
+    _check(load().cgs_apply_A_prec(mesh, _ptr(x), _ptr(y), OP[op], _stream(stream)), "cgs_apply_A_prec")
+
+
+def cgs_mesh_step_status(mesh, stream=None) -> int:
+    """Status of the single-step calls since the last query (OK or ERR_TIMEOUT); resets it."""
+    st = load().cgs_mesh_step_status(mesh, _stream(stream))
+    _check(st, "cgs_mesh_step_status", allow=(ERR_TIMEOUT,))
+    return st
+
+
+def cgs_mesh_set_wait_limits(mesh, tile_wait=1 << 20, barrier_wait=1 << 22):
+    """Iteration limits of the bounded device waits (a testing aid; 0 = give up at once)."""
+    _check(load().cgs_mesh_set_wait_limits(mesh, int(tile_wait), int(barrier_wait)), "cgs_mesh_set_wait_limits")
 
 
 def cgs_apply_local(mesh, r, l, weighted=True, stream=None):

@@ -171,6 +171,10 @@ struct cgs_mesh {
     std::vector<int64_t> box_active_h, sub_ptr_h;
     std::vector<int32_t> sub_idx_h;
     double *hb = nullptr, *hx = nullptr;  // device staging for cgs_solve_host
+    // status of the single-step calls (cgs_apply_*, cgs_restrict, ..., and
+    // cgs_apply_preconditioner_noalloc): a bounded device wait that expired
+    // leaves CGS_ERR_TIMEOUT here until cgs_mesh_step_status reads it
+    SolveScalars* step_S = nullptr;
     size_t h_cap = 0;
     // projection onto prior solutions (cgs_mesh_set_projection): l x nv rows
     // of the A-orthonormal basis X and of A X, work vectors, dot results
@@ -643,6 +647,10 @@ cgs_precision mesh_prec(const cgs_mesh* m) { return m->prm.prec; }
 cgs_form mesh_form(const cgs_mesh* m) { return m->E.form; }
 const uint8_t* mesh_dir(const cgs_mesh* m) { return m->d.dir; }
 int mesh_device(const cgs_mesh* m) { return m->ctx->device; }
+SolveScalars* mesh_step_status_word(cgs_mesh* m, cudaStream_t st) {
+    cudaMemsetAsync(&m->step_S->done, 0, sizeof(int), st);
+    return m->step_S;
+}
 void set_last_error(const std::string& msg) { g_err = msg; }
 }  // namespace cgs
 
@@ -959,6 +967,11 @@ cgs_status cgs_mesh_setup(cgs_ctx* ctx, const double* xyz, int64_t nv, const int
     }
     UP(d.dir, hs.dir);
     {
+        cudaError_t e_ = m->mem.alloc(&m->step_S, 1);
+        if (e_ == cudaSuccess) e_ = cudaMemset(m->step_S, 0, sizeof(SolveScalars));
+        if (e_ != cudaSuccess) return cleanup(cuda_fail(e_, "step status"));
+    }
+    {
         const DevMesh* dd = nullptr;
         UP(dd, std::vector<DevMesh>{d});
         m->d_dev = const_cast<DevMesh*>(dd);
@@ -1108,21 +1121,91 @@ cgs_status cgs_profile_read(cgs_mesh* m, double* ms, int64_t* launches) {
 
 // ---- single steps: user buffers take the place of the slot's vectors -------
 
+namespace {
+// Vecs of a single-step call: the slot scalars are the mesh's step status
+// word, which only bounded waits write.  Its stop flag is cleared first, so
+// a wait that expired in an earlier call does not skip this call's work; the
+// recorded timeout stays until cgs_mesh_step_status reads it.
+Vecs step_vecs(cgs_mesh* m, cudaStream_t st) {
+    Vecs V = m->E.V;
+    V.S = m->step_S;
+    V.step = 1;
+    cudaMemsetAsync(&m->step_S->done, 0, sizeof(int), st);
+    return V;
+}
+}  // namespace
+
 cgs_status cgs_apply_A(cgs_mesh* m, const double* x, double* y, void* stream) {
     if (!m || !x || !y) return fail(CGS_ERR_INVALID_ARG, "null argument");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     Engine& E = m->E;
-    const Vecs V = no_stop(E.V);
+    const Vecs V = step_vecs(m, st);
     K(CGS_K_OTHER, launch_fill_d(m->d.nv, y, 0.0, st));
     K(CGS_K_APPLY_A64, launch_apply64(E.P, V, x, y, 1.0, false, st));
     return finish(st, false);
+}
+
+cgs_status cgs_apply_A_prec(cgs_mesh* m, const double* x, double* y, int op, void* stream) {
+    if (!m || !x || !y) return fail(CGS_ERR_INVALID_ARG, "null argument");
+    if (op < CGS_OP_FP64 || op > CGS_OP_OUTER) return fail(CGS_ERR_INVALID_ARG, "unknown operator");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    Engine& E = m->E;
+    const Vecs V = step_vecs(m, st);
+    const int64_t nv = m->d.nv;
+    if (m->fp64() || op == CGS_OP_FP64) {
+        K(CGS_K_OTHER, launch_fill_d(nv, y, 0.0, st));
+        K(CGS_K_APPLY_A64, launch_apply64(E.P, V, x, y, 1.0, false, st));
+    } else if (op == CGS_OP_INNER) {
+        // x rounded to float, y = A x accumulated in float, then widened
+        float* xf = static_cast<float*>(V.z);
+        float* yf = static_cast<float*>(V.s);
+        K(CGS_K_OTHER, launch_convert_d2f(E.P, x, xf, true, st));
+        K(CGS_K_OTHER, launch_fill_f(nv, yf, 0.0f, st));
+        K(CGS_K_APPLY_A32, launch_apply28f_tiled(E.P, V, xf, yf, 1.0f, st));
+        K(CGS_K_OTHER, launch_convert_f2d(E.P, yf, y, true, st));
+    } else {
+        // x split into float pairs, y = A x in float-pair arithmetic
+        K(CGS_K_OTHER, launch_split_pair(nv, x, V.p2, st));
+        K(CGS_K_OTHER, launch_fill_d(nv, reinterpret_cast<double*>(V.q2), 0.0, st));
+        K(CGS_K_APPLY_A64, launch_apply_pair_tiled(E.P, V, st));
+        K(CGS_K_OTHER, launch_pair_to_double(nv, V.q2, y, st));
+    }
+    return finish(st, false);
+}
+
+cgs_status cgs_mesh_step_status(cgs_mesh* m, void* stream) {
+    if (!m) return fail(CGS_ERR_INVALID_ARG, "null mesh");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    CGS_CUDA(cudaSetDevice(m->ctx->device));
+    SolveScalars h{};
+    CGS_CUDA(cudaMemcpyAsync(&h, m->step_S, sizeof(SolveScalars), cudaMemcpyDeviceToHost, st));
+    CGS_CUDA(cudaStreamSynchronize(st));
+    CGS_CUDA(cudaMemsetAsync(m->step_S, 0, sizeof(SolveScalars), st));
+    CGS_CUDA(cudaStreamSynchronize(st));
+    if (h.timeouts > 0 || h.status == CGS_ERR_TIMEOUT)
+        return fail(CGS_ERR_TIMEOUT, "a bounded device wait of a single-step call expired (" +
+                                         std::to_string(h.timeouts) + " waits)");
+    return CGS_OK;
+}
+
+cgs_status cgs_mesh_set_wait_limits(cgs_mesh* m, int tile_wait, int barrier_wait) {
+    if (!m || tile_wait < 0 || barrier_wait < 0) return fail(CGS_ERR_INVALID_ARG, "bad mesh or limit");
+    CGS_CUDA(cudaSetDevice(m->ctx->device));
+    CGS_CUDA(cudaDeviceSynchronize());
+    m->E.P.wait_limit = tile_wait;
+    m->E.P.bar_limit = barrier_wait;
+    if (m->E.gexec) {   // the captured loop holds the old limits
+        cudaGraphExecDestroy(m->E.gexec);
+        m->E.gexec = nullptr;
+    }
+    return CGS_OK;
 }
 
 cgs_status cgs_apply_local(cgs_mesh* m, const double* r, double* l, int weighted, void* stream) {
     if (!m || !r || !l) return fail(CGS_ERR_INVALID_ARG, "null argument");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     Engine& E = m->E;
-    const Vecs V = no_stop(E.V);
+    const Vecs V = step_vecs(m, st);
     if (m->fp64()) {
         K(CGS_K_OTHER, launch_precond_prep<double>(E.P, V, r, st));
         K(CGS_K_LOCAL, launch_local(E.P, V, E.prec, V.s, V.z, weighted != 0, st));
@@ -1140,7 +1223,7 @@ cgs_status cgs_restrict(cgs_mesh* m, const double* s, double* rr, void* stream) 
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (m->d.nr == 0) return CGS_OK;
     Engine& E = m->E;
-    const Vecs V = no_stop(E.V);
+    const Vecs V = step_vecs(m, st);
     K(CGS_K_OTHER, launch_fill_d(m->d.nr, rr, 0.0, st));
     K(CGS_K_RESTRICT, launch_restrict(E.P, V, m->fp64(), s, true, rr, false, st));
     return finish(st, false);
@@ -1150,7 +1233,7 @@ cgs_status cgs_coarse_solve(cgs_mesh* m, const double* rr, double* ur, void* str
     if (!m || ((!rr || !ur) && m->d.nr)) return fail(CGS_ERR_INVALID_ARG, "null argument");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     Engine& E = m->E;
-    const Vecs V = no_stop(E.V);
+    const Vecs V = step_vecs(m, st);
     if (E.P.any_xxt) K(CGS_K_OTHER, launch_fill_d(m->d.nr, V.rt, 0.0, st));   // t = X^T r_r accumulates
     if (m->fp64()) {
         if (E.P.any_xxt) K(CGS_K_COARSE, launch_xxt_pass1(E.P, V, false, rr, st));
@@ -1169,7 +1252,7 @@ cgs_status cgs_interp(cgs_mesh* m, const double* ur, double* z, void* stream) {
     if (!m || !z || (!ur && m->d.nr)) return fail(CGS_ERR_INVALID_ARG, "null argument");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     Engine& E = m->E;
-    const Vecs V = no_stop(E.V);
+    const Vecs V = step_vecs(m, st);
     if (m->fp64()) {
         K(CGS_K_OTHER, launch_fill_d(m->d.nv, static_cast<double*>(V.z), 0.0, st));
         K(CGS_K_INTERP, launch_interp_add(E.P, V, true, ur, nullptr, V.z, false, nullptr, st));
@@ -1186,7 +1269,7 @@ cgs_status cgs_apply_preconditioner(cgs_mesh* m, const double* r, double* z, voi
     if (!m || !r || !z) return fail(CGS_ERR_INVALID_ARG, "null argument");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     Engine& E = m->E;
-    const Vecs V = no_stop(E.V);
+    const Vecs V = step_vecs(m, st);
     if (m->fp64()) {
         K(CGS_K_OTHER, launch_precond_prep<double>(E.P, V, r, st));
         precond_body(E, V, st);

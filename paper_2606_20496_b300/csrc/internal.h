@@ -205,7 +205,8 @@ struct Plan {
     int nslots = 0;
     int max_m = 0;                         // largest warp-kernel subdomain over the meshes
     bool any_nr = false;                   // some mesh has a reduced space
-    int wait_limit = 1 << 20;              // iteration limit of bounded device waits
+    int wait_limit = 1 << 20;              // iteration limit of the element-tile (TMA) waits
+    int bar_limit = 1 << 22;               // iteration limit of the persistent loop's grid-barrier waits
     bool tile_tma = false;                 // element tiles staged by TMA (else streamed by the threads)
     bool pdl = true;                       // launch with programmatic stream serialization
     bool interp_cells = false;             // interpolation by cell-sorted entries (dots left to the caller)
@@ -299,7 +300,9 @@ struct Vecs {
     double* rt = nullptr;                  // t = X^T r_r of the XX^T solve (float pair or double), n_r per slot
     float* ur32 = nullptr;
     double* partials = nullptr;
-    SolveScalars* S = nullptr;             // nullptr: no early exit (single steps)
+    SolveScalars* S = nullptr;             // nullptr: no early exit and no wait status (timing runs)
+    int step = 0;                          // 1: a single-step call; S then only carries the status of
+                                           // bounded waits (no PCG scalar is read or written)
     const double* b = nullptr;             // right-hand sides (pool), or
     const double* const* bptr = nullptr;   // per-slot right-hand side pointers
     double* const* xptr = nullptr;         // per-slot solution pointers (copy-out)

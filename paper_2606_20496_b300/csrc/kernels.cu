@@ -554,7 +554,10 @@ __device__ __forceinline__ void apply_pair_tiled_item(const DevMesh* __restrict_
     CGS_ITEM_PROLOGUE();
     const float2* p2 = V.p2 + w.voff;
     const float* zf = static_cast<const float*>(V.z) + w.voff;
-    const float2 beta2 = S ? S->beta2 : make_float2(0.0f, 0.0f);
+    // inside the PCG: this iteration's p is formed from z and beta on the fly
+    // and p.Ap is reduced; a single step (or a timing run) applies A to p2
+    const bool pcg = S && !V.step;
+    const float2 beta2 = pcg ? S->beta2 : make_float2(0.0f, 0.0f);
     float2* q2 = V.q2 + w.voff;
     const int t = w.begin;
     const float4* ghi = reinterpret_cast<const float4*>(M.at_hi) + (size_t)t * kGroups * kTileElems;
@@ -588,7 +591,7 @@ __device__ __forceinline__ void apply_pair_tiled_item(const DevMesh* __restrict_
             const int i = (int)threadIdx.x + k * kBlock;
             const int v = (int)(raw[k] & ~kSharedBit);
             pg[k] = i < nvt ? __ldg(&p2[v]) : make_float2(0.0f, 0.0f);
-            zg[k] = (S && i < nvt) ? __ldg(&zf[v]) : 0.0f;
+            zg[k] = (pcg && i < nvt) ? __ldg(&zf[v]) : 0.0f;
         }
 #pragma unroll
         for (int k = 0; k < kVertsPerThread; ++k) {
@@ -596,7 +599,7 @@ __device__ __forceinline__ void apply_pair_tiled_item(const DevMesh* __restrict_
             if (i < nvt) {
                 // this iteration's direction p = z + beta p, formed on the fly
                 // (the x, r update stores it)
-                ps[i] = S ? pr_fma(beta2, pg[k], make_float2(zg[k], 0.0f)) : pg[k];
+                ps[i] = pcg ? pr_fma(beta2, pg[k], make_float2(zg[k], 0.0f)) : pg[k];
                 ys[i] = make_float2(0.0f, 0.0f);
             }
         }
@@ -659,7 +662,7 @@ __device__ __forceinline__ void apply_pair_tiled_item(const DevMesh* __restrict_
             }
         }
     }
-    if (!S) return;   // no slot scalars (timing runs): no reduction
+    if (!pcg) return;   // no PCG scalars (single steps, timing runs): no reduction
     float vh[1] = {eh}, vl[1] = {el};
     double tot[1];
     pdl_trigger();   // the successor may launch during the reduction tail
@@ -2631,6 +2634,21 @@ void launch_split_pair(int64_t n, const double* a, float2* b, cudaStream_t st) {
     launch_pdl(true, split_pair_kernel, blocks, kBlock, 0, st, n, a, b);
 }
 
+// float pair -> float64 (hi + lo) over n entries (single-step outer operator)
+__global__ void pair_to_double_kernel(int64_t n, const float2* __restrict__ a, double* __restrict__ b) {
+    pdl_wait();
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float2 t = a[i];
+        b[i] = (double)t.x + (double)t.y;
+    }
+}
+
+void launch_pair_to_double(int64_t n, const float2* a, double* b, cudaStream_t st) {
+    if (n <= 0) return;
+    const int blocks = (int)std::min<int64_t>((n + kBlock - 1) / kBlock, 1024);
+    launch_pdl(true, pair_to_double_kernel, blocks, kBlock, 0, st, n, a, b);
+}
+
 template <typename Tq>
 void launch_pcg_init(const Plan& P, const Vecs& V, Tq* q, double rtol, int maxit, cudaStream_t st) {
     launch_pdl(P.pdl, pcg_init_kernel<Tq>, P.nwork[kWorkVert], kBlock, 0, st, P.meshes, P.work[kWorkVert], V, q, rtol,
@@ -2687,7 +2705,7 @@ cudaError_t launch_pcg_persistent(const Plan& P, const Vecs& V, cgs_precision pr
         T.n[k] = P.nwork[k];
     }
     int nslots = P.nslots, hyb = hybrid ? 1 : 0, any_nr = P.any_nr ? 1 : 0, big = P.max_m > 64 ? 1 : 0;
-    int wait_limit = P.wait_limit, bar_limit = 1 << 22;
+    int wait_limit = P.wait_limit, bar_limit = P.bar_limit;
     Vecs Vv = V;
     const DevMesh* meshes = P.meshes;
     void* args[] = {(void*)&meshes, &T, &Vv, &bar, &nslots, &hyb, &any_nr, &big, &max_iters, &wait_limit, &bar_limit};

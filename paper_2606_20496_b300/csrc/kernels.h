@@ -52,6 +52,7 @@ void launch_coarse(const Plan& P, const Vecs& V, const double* rr, double* ur, f
 bool launch_xxt_pass1(const Plan& P, const Vecs& V, bool pair, const double* rr, cudaStream_t st);
 void launch_coarse_pair(const Plan& P, const Vecs& V, const float2* rr2, double* ur, float* ur32, cudaStream_t st);
 void launch_split_pair(int64_t n, const double* a, float2* b, cudaStream_t st);
+void launch_pair_to_double(int64_t n, const float2* a, double* b, cudaStream_t st);
 
 // Outer iteration of the mixed forms (float-pair x, r, p, q).
 void launch_pcg_init_pair(const Plan& P, const Vecs& V, double rtol, int maxit, cudaStream_t st);
@@ -125,6 +126,8 @@ const Plan& mesh_plan(const cgs_mesh* m);
 cgs_precision mesh_prec(const cgs_mesh* m);
 cgs_form mesh_form(const cgs_mesh* m);
 const uint8_t* mesh_dir(const cgs_mesh* m);
+// the mesh's single-step status word (device), its stop flag cleared on `st`
+SolveScalars* mesh_step_status_word(cgs_mesh* m, cudaStream_t st);
 int mesh_device(const cgs_mesh* m);
 void set_last_error(const std::string& msg);
 

@@ -1,9 +1,10 @@
 // cgs_apply_preconditioner_noalloc: z = M r with every working vector in a
 // static device array, so the call never allocates device memory.
 //
-// Who needs it: callers that cannot allocate at call time, such as work being
-// captured into a CUDA graph, serving loops that forbid allocation after
-// warm-up, or hosts whose device memory belongs to another runtime's pool.
+// Who needs it: callers that cannot allocate at call time, such as serving
+// loops that forbid allocation after warm-up, or hosts whose device memory
+// belongs to another runtime's pool (an allocation of ours would bypass that
+// pool's accounting or fail).
 //
 // The array below is a host-side stand-in when named in host code: only its
 // device address, looked up once per device by cudaGetSymbolAddress with that
@@ -72,6 +73,10 @@ extern "C" cgs_status cgs_apply_preconditioner_noalloc(cgs_mesh* mesh, const dou
     // vector in the static array
     const Plan& P = mesh_plan(mesh);
     Vecs V;
+    // an expired element-tile wait is recorded in the mesh's step status
+    // word (set up with the mesh, so nothing is allocated here)
+    V.S = mesh_step_status_word(mesh, st);
+    V.step = 1;
     V.z = p;                                           // nv entries of 8 bytes
     V.s = p + (size_t)8 * CGS_NOALLOC_MAX_NV;          // nv entries of 8 bytes
     V.rr = reinterpret_cast<double*>(p + (size_t)16 * CGS_NOALLOC_MAX_NV);
@@ -85,7 +90,12 @@ extern "C" cgs_status cgs_apply_preconditioner_noalloc(cgs_mesh* mesh, const dou
     else
         launch_precond_prep<float>(P, V, r, st);
     const bool weighted = mesh_form(mesh) == CGS_HYBRID;
-    launch_local(P, V, prec, V.s, V.z, weighted, st);
+    // additive mixed form: the local solves and the restriction of s share
+    // one launch when every subdomain is in packs (as in the regular call)
+    const bool restricted = !weighted && !f64 && d.nr &&
+                            launch_local_restrict(P, V, prec, static_cast<const float*>(V.s),
+                                                  static_cast<float*>(V.z), V.rr, st);
+    if (!restricted) launch_local(P, V, prec, V.s, V.z, weighted, st);
     if (weighted) {
         if (f64)
             launch_apply64(P, V, static_cast<const double*>(V.z), static_cast<double*>(V.s), -1.0, false, st);
@@ -100,7 +110,7 @@ extern "C" cgs_status cgs_apply_preconditioner_noalloc(cgs_mesh* mesh, const dou
     } else if (d.nr) {
         // r_r as float pairs, the pair product writes u_r rounded to float
         float* ur32 = reinterpret_cast<float*>(V.ur);
-        launch_restrict(P, V, false, V.s, false, V.rr, true, st);
+        if (!restricted) launch_restrict(P, V, false, V.s, false, V.rr, true, st);
         launch_xxt_pass1(P, V, true, V.rr, st);    // XX^T meshes only
         launch_coarse_pair(P, V, reinterpret_cast<const float2*>(V.rr), nullptr, ur32, st);
         launch_interp_add(P, V, false, nullptr, ur32, V.z, false, nullptr, st);

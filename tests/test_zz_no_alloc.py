@@ -1,11 +1,11 @@
 """The no-allocation preconditioner entry point against the regular one.
 
 cgs_apply_preconditioner_noalloc serves callers that cannot allocate device
-memory when they call (work being captured into a CUDA graph, serving loops
-that forbid allocation after warm-up, hosts whose device memory belongs to
-another runtime's pool).  It keeps its working vectors in a static device
-array, so these tests check that it returns what cgs_apply_preconditioner
-returns, call after call, and that it refuses meshes beyond its size limit.
+memory when they call (serving loops that forbid allocation after warm-up,
+hosts whose device memory belongs to another runtime's pool).  It keeps its
+working vectors in a static device array, so these tests check that it
+returns what cgs_apply_preconditioner returns, call after call, and that it
+refuses meshes beyond either of its size limits (vertices, reduced unknowns).
 This file is collected last so a stop-at-first-failure run has already run
 every other test; it also passes on its own in a fresh process.
 """
@@ -65,3 +65,18 @@ def test_noalloc_rejects_meshes_beyond_its_limit(ctx):
             cgs.cgs_apply_preconditioner_noalloc(h.handle, r, z)
         assert ei.value.status == cgs.ERR_INVALID_ARG
         assert "limit" in cgs.load().cgs_last_error().decode()
+
+
+def test_noalloc_rejects_reduced_spaces_beyond_its_limit(ctx):
+    # 40 x 40 x 4 box cells over a 48 x 48 x 6 slab: every cell holds element
+    # centroids, so all 41 * 41 * 5 = 8,405 box vertices are active (> 8,192)
+    # while the mesh itself (16,807 vertices) is within the vertex limit
+    m = meshes.cube((48, 48, 6), perturb=0.1, seed=5, boxes=(40, 40, 4))
+    with cgs.Mesh(ctx, m.xyz, m.conn, part=m.part, boxes=m.boxes, prec="fp32") as h:
+        assert h.info["n_r"] > cgs.NOALLOC_MAX_NR and m.nv <= cgs.NOALLOC_MAX_NV
+        r = torch.zeros(m.nv, dtype=torch.float64, device="cuda")
+        z = torch.empty_like(r)
+        with pytest.raises(cgs.CGSError) as ei:
+            cgs.cgs_apply_preconditioner_noalloc(h.handle, r, z)
+        assert ei.value.status == cgs.ERR_INVALID_ARG
+        assert "n_r" in cgs.load().cgs_last_error().decode()
