@@ -1,12 +1,15 @@
 """Serving by continuous batching: requests that arrive while others run join
 free slots and share their launches; each result must equal the solo solve
-of the same mesh and right-hand side within the solve tolerance."""
+of the same mesh and right-hand side within the solve tolerance, and the FP64
+oracle's solve (iterations within one, relative solution difference <= 1e-8
+at rtol 1e-10)."""
 import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
+from oracle import cgs_oracle as O  # noqa: E402
 from paper_2606_20496_b300 import cgs, meshes  # noqa: E402
 
 
@@ -27,6 +30,7 @@ def test_results_same_alone_and_in_the_mix(ctx, prec):
                  meshes.cylinder(6, 24, 8, grading=1.1, aspect=5.0, boxes=(3, 3, 3)),
                  meshes.cube((7, 9, 5), perturb=0.1, seed=4, part_mode="mixed")]
     hs = [cgs.Mesh(ctx, m.xyz, m.conn, part=m.part, boxes=m.boxes, prec=prec) for m in mesh_defs]
+    oracles = [O.Problem(m.xyz, m.conn, m.part, m.boxes) for m in mesh_defs]
     rtol = 1e-10
     server = cgs.cgs_server_create(ctx, max_slots=3, pool_nv=3 * max(m.nv for m in mesh_defs),
                                    pool_nr=3 * max(h.info["n_r"] for h in hs), prec=prec, rtol=rtol)
@@ -63,6 +67,10 @@ def test_results_same_alone_and_in_the_mix(ctx, prec):
             assert abs(int(its1[0]) - its) <= 1
             xa, xb = x1.cpu().numpy(), x.cpu().numpy()
             assert np.linalg.norm(xb - xa) / np.linalg.norm(xa) <= 1e-8
+            # against the oracle's solve of the same request
+            xo, its_o, _, ok = oracles[mi].solve(b.cpu().numpy(), rtol=rtol)
+            assert ok and abs(its_o - its) <= 1
+            assert np.linalg.norm(xb - xo) / np.linalg.norm(xo) <= 1e-8
     finally:
         cgs.cgs_server_free(server)
         for h in hs:
@@ -134,6 +142,10 @@ def test_admission_by_footprint(ctx):
             cgs.cgs_solve(hh.handle, b, x1, rtol=1e-10)
             xa, xb = x1.cpu().numpy(), x.cpu().numpy()
             assert np.linalg.norm(xb - xa) / np.linalg.norm(xa) <= 1e-8
+            # against the oracle's solve of the same request
+            xo, its_o, _, ok = oracles[mi].solve(b.cpu().numpy(), rtol=rtol)
+            assert ok and abs(its_o - its) <= 1
+            assert np.linalg.norm(xb - xo) / np.linalg.norm(xo) <= 1e-8
     finally:
         cgs.cgs_server_free(server)
         h.free()
