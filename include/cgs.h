@@ -64,7 +64,12 @@ typedef enum {
 
 typedef enum {
     CGS_HYBRID = 0,      /* ASM_1 then ASM_2 (Eqs. asm1, asm2), W_ov-weighted local sum */
-    CGS_ADDITIVE = 1     /* Eq. asm with R~_p = R_p (symmetric)                         */
+    CGS_ADDITIVE = 1,    /* Eq. asm with R~_p = R_p (symmetric)                         */
+    CGS_RAS = 2          /* Eq. asm with the restricted prolongation R~_p (Sec. 3, RAS):
+                            a local solution keeps only the nodes of the original,
+                            not grown, Omega_p, averaged where several original
+                            subdomains store a node; not symmetric, so solve it
+                            with a flexible method (the PCG here is flexible)     */
 } cgs_form;
 
 /* Reduced solver u_r = A_r^{-1} r_r (Sec. 2, the XX^T paragraph; Sec. 4). */
@@ -95,6 +100,12 @@ typedef struct {
     cgs_form form;
     cgs_coarse_solver coarse_solver;  /* 0 (zero-initialised params) = auto        */
     cgs_coarse_operator coarse_operator; /* 0 = cell-wise (Eq. Aij)                  */
+    int local_cg_steps;    /* 0: exact local solves (explicit A_p^{-1}); k > 0: inexact
+                              local solves, k CG steps on each A_p from zero (Sec. 6),
+                              one warp per subdomain; needs m_p <= 64 and the FP64 or
+                              FP32-bulk form (INVALID_ARG otherwise).  The
+                              preconditioner then varies with r, which the flexible
+                              PCG and cgs_solve_wrapped's flexible GMRES allow    */
 } cgs_params;
 
 typedef struct {

@@ -20,7 +20,7 @@ PROJECTION_MAX = 64
 OK, ERR_INVALID_ARG, ERR_INVALID_MESH, ERR_NOT_SPD, ERR_NO_CONVERGENCE, ERR_BREAKDOWN, ERR_OOM, \
     ERR_ADMISSION, ERR_TIMEOUT, ERR_CUDA = range(10)
 PREC = {"fp64": 0, "fp32": 1, "fp16": 2}
-FORM = {"hybrid": 0, "additive": 1}
+FORM = {"hybrid": 0, "additive": 1, "ras": 2}
 COARSE = {"auto": 0, "dense": 1, "xxt": 2}
 COARSE_OP = {"cellwise": 0, "galerkin": 1, "vertex": 2}
 OP = {"fp64": 0, "inner": 1, "outer": 2}
@@ -53,7 +53,8 @@ class CGSError(RuntimeError):
 
 class Params(C.Structure):
     _fields_ = [("box", C.c_int * 3), ("box_margin", C.c_double), ("overlap_layers", C.c_int),
-                ("prec", C.c_int), ("form", C.c_int), ("coarse_solver", C.c_int), ("coarse_operator", C.c_int)]
+                ("prec", C.c_int), ("form", C.c_int), ("coarse_solver", C.c_int), ("coarse_operator", C.c_int),
+                ("local_cg_steps", C.c_int)]
 
 
 class MeshInfo(C.Structure):
@@ -195,14 +196,15 @@ def cgs_ctx_bytes_in_use(ctx) -> int:
 
 
 def cgs_mesh_setup(ctx, xyz, conn, dirichlet=None, elem_part=None, boxes=(4, 4, 4), margin=0.0, overlap=1,
-                   prec="fp64", form="hybrid", coarse="auto", coarse_operator="cellwise"):
+                   prec="fp64", form="hybrid", coarse="auto", coarse_operator="cellwise", local_cg_steps=0):
     xyz = np.ascontiguousarray(xyz, dtype=np.float64)
     conn = np.ascontiguousarray(conn, dtype=np.int32)
     d = None if dirichlet is None else np.ascontiguousarray(dirichlet, dtype=np.uint8)
     part = None if elem_part is None else np.ascontiguousarray(elem_part, dtype=np.int32)
     prm = Params((C.c_int * 3)(*[int(b) for b in boxes]), float(margin), int(overlap), PREC[prec], FORM[form],
                  COARSE[coarse] if isinstance(coarse, str) else int(coarse),
-                 COARSE_OP[coarse_operator] if isinstance(coarse_operator, str) else int(coarse_operator))
+                 COARSE_OP[coarse_operator] if isinstance(coarse_operator, str) else int(coarse_operator),
+                 int(local_cg_steps))
     mesh = C.c_void_p()
     st = load().cgs_mesh_setup(ctx, _ptr(xyz), xyz.shape[0], _ptr(conn), conn.shape[0], _ptr(d), _ptr(part),
                                C.byref(prm), C.byref(mesh))
@@ -470,9 +472,9 @@ class Mesh:
     """Owning handle around cgs_mesh_setup / cgs_mesh_free."""
 
     def __init__(self, ctx, xyz, conn, part=None, boxes=(4, 4, 4), dirichlet=None, margin=0.0, overlap=1,
-                 prec="fp64", form="hybrid", coarse="auto", coarse_operator="cellwise"):
+                 prec="fp64", form="hybrid", coarse="auto", coarse_operator="cellwise", local_cg_steps=0):
         self.handle = cgs_mesh_setup(ctx, xyz, conn, dirichlet, part, boxes, margin, overlap, prec, form, coarse,
-                                     coarse_operator)
+                                     coarse_operator, local_cg_steps)
         self.info = cgs_mesh_info(self.handle)
         self.prec = prec
 

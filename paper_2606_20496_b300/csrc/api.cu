@@ -236,7 +236,7 @@ bool box_correction(Engine& E, const Vecs& V, bool dots, cudaStream_t st, bool r
                     const cudaGraphConditionalHandle* cond = nullptr) {
     const Plan& P = E.P;
     if (E.f64) {
-        K(CGS_K_RESTRICT, launch_restrict(P, V, true, V.s, true, V.rr, false, st));
+        if (!restricted) K(CGS_K_RESTRICT, launch_restrict(P, V, true, V.s, true, V.rr, false, st));
         if (P.any_xxt) K(CGS_K_COARSE, launch_xxt_pass1(P, V, false, V.rr, st));
         K(CGS_K_COARSE, launch_coarse(P, V, V.rr, V.ur, nullptr, st));
     } else {
@@ -257,13 +257,21 @@ bool precond_body(Engine& E, const Vecs& V, cudaStream_t st, bool dots = false,
                   const cudaGraphConditionalHandle* cond = nullptr) {
     const Plan& P = E.P;
     if (E.form == CGS_HYBRID) {
-        K(CGS_K_LOCAL, launch_local(P, V, E.prec, V.s, V.z, true, st));
+        K(CGS_K_LOCAL, launch_local(P, V, E.prec, V.s, V.z, 1, st));
+        if (P.hyb_restrict) {
+            // r_r = J~^T r - (A J~)^T l: s = r - A l is never formed
+            K(CGS_K_RESTRICT, launch_restrict_hybrid(P, V, E.f64, V.s, V.z, V.rr, st));
+            return box_correction(E, V, dots, st, true, cond);
+        }
         if (E.f64)
             K(CGS_K_APPLY_A64, launch_apply64(P, V, static_cast<const double*>(V.z), static_cast<double*>(V.s), -1.0,
                                               false, st));
         else
             K(CGS_K_APPLY_A32,
               launch_apply28f_tiled(P, V, static_cast<const float*>(V.z), static_cast<float*>(V.s), -1.0f, st));
+    } else if (E.form == CGS_RAS) {
+        // restricted prolongation: a weight per subdomain entry
+        K(CGS_K_LOCAL, launch_local(P, V, E.prec, V.s, V.z, 2, st));
     } else {
         // the restriction of s fused with the local solves when every
         // subdomain is in packs
@@ -272,7 +280,7 @@ bool precond_body(Engine& E, const Vecs& V, cudaStream_t st, bool dots = false,
                                                  static_cast<float*>(V.z), V.rr, st));
             return box_correction(E, V, dots, st, true, cond);
         }
-        K(CGS_K_LOCAL, launch_local(P, V, E.prec, V.s, V.z, false, st));
+        K(CGS_K_LOCAL, launch_local(P, V, E.prec, V.s, V.z, 0, st));
     }
     if (!P.any_nr) return false;
     return box_correction(E, V, dots, st, false, cond);
@@ -492,6 +500,24 @@ cudaError_t alloc_pools(DevAllocs& mem, Engine& E, int64_t total_v, int64_t tota
     return cudaSuccess;
 }
 
+// Whether every slot with a reduced space has hybrid-restriction ranges
+// (then the hybrid step restricts r and l directly, without s = r - A l).
+bool hyb_restrict_ok(const Plan& P, const std::vector<Work> (&tabs)[kWorkKinds]) {
+    if (!P.any_nr || tabs[kWorkHybR].empty()) return false;
+    std::vector<char> with_box, with_hr;
+    for (const Work& w : tabs[kWorkBoxEnt]) {
+        if ((size_t)w.slot >= with_box.size()) with_box.resize(w.slot + 1, 0);
+        with_box[w.slot] = 1;
+    }
+    for (const Work& w : tabs[kWorkHybR]) {
+        if ((size_t)w.slot >= with_hr.size()) with_hr.resize(w.slot + 1, 0);
+        with_hr[w.slot] = 1;
+    }
+    for (size_t k = 0; k < with_box.size(); ++k)
+        if (with_box[k] && (k >= with_hr.size() || !with_hr[k])) return false;
+    return true;
+}
+
 // (Re)build the work tables of an engine for a schedule and upload them.
 cudaError_t set_schedule(Engine& E, const Schedule& sch) {
     std::vector<Work> tabs[kWorkKinds];
@@ -519,6 +545,7 @@ cudaError_t set_schedule(Engine& E, const Schedule& sch) {
     P.pdl = sch.pdl != 0;
     P.interp_cells = sch.interp_cells != 0;
     P.any_xxt = P.nwork[kWorkXSeg] > 0;
+    P.hyb_restrict = hyb_restrict_ok(P, tabs);
     E.P = P;
     E.sch = sch;
     if (E.gexec) {   // the captured loop holds the old grid sizes
@@ -706,8 +733,11 @@ cgs_status cgs_mesh_setup(cgs_ctx* ctx, const double* xyz, int64_t nv, const int
     if (!ctx) return fail(CGS_ERR_INVALID_ARG, "null ctx");
     const auto t0 = std::chrono::steady_clock::now();
     const cgs_params prm = params ? *params : default_params();
-    if (prm.prec < CGS_FP64 || prm.prec > CGS_FP16_LOCAL || prm.form < CGS_HYBRID || prm.form > CGS_ADDITIVE)
+    if (prm.prec < CGS_FP64 || prm.prec > CGS_FP16_LOCAL || prm.form < CGS_HYBRID || prm.form > CGS_RAS)
         return fail(CGS_ERR_INVALID_ARG, "unknown precision or form");
+    if (prm.local_cg_steps < 0 || prm.local_cg_steps > 1024 ||
+        (prm.local_cg_steps > 0 && prm.prec == CGS_FP16_LOCAL))
+        return fail(CGS_ERR_INVALID_ARG, "local_cg_steps must be in [0, 1024], and 0 in the FP16-local form");
     CGS_CUDA(cudaSetDevice(ctx->device));
     HostSetup hs;
     std::string err;
@@ -792,9 +822,30 @@ cgs_status cgs_mesh_setup(cgs_ctx* ctx, const double* xyz, int64_t nv, const int
         if (f64) {
             UP(d.vb_w64, hs.vb_w);
             UP(d.re_w64, hs.re_w);
+            // explicit rows of J~ for the float64 interpolation
+            UP(d.jt_ptr, hs.jt_ptr);
+            UP(d.jt_col, hs.jt_col);
+            UP(d.jt_val, hs.jt_val);
         } else {
             UP(d.vb_w32, std::vector<float>(hs.vb_w.begin(), hs.vb_w.end()));
             UP(d.re_w32, std::vector<float>(hs.re_w.begin(), hs.re_w.end()));
+        }
+    }
+    d.nhr = (int64_t)hs.hr_rng.size() / 4;
+    if (d.nhr) {
+        const int32_t* rp = nullptr;
+        UP(rp, hs.hr_rng);
+        d.hr_rng = reinterpret_cast<const int4*>(rp);
+        UP(d.hr_vert, hs.hr_vert);
+        const size_t nh = hs.hr_vert.size();
+        if (f64) {
+            std::vector<double2> jg(nh);
+            for (size_t i = 0; i < nh; ++i) jg[i] = make_double2(hs.hr_j[i], hs.hr_g[i]);
+            UP(d.hr_jg64, jg);
+        } else {
+            std::vector<float2> jg(nh);
+            for (size_t i = 0; i < nh; ++i) jg[i] = make_float2((float)hs.hr_j[i], (float)hs.hr_g[i]);
+            UP(d.hr_jg32, jg);
         }
     }
     {
@@ -803,12 +854,18 @@ cgs_status cgs_mesh_setup(cgs_ctx* ctx, const double* xyz, int64_t nv, const int
     }
     UP(d.sub_idx, hs.wsub_idx);
     UP(d.inv_ptr, hs.inv_ptr);
+    d.cg_steps = prm.local_cg_steps;
     if (prm.prec == CGS_FP64) {
         UP(d.inv64, hs.inv);
+        UP(d.went64, hs.wsub_ras);
+        if (d.cg_steps) UP(d.ap64, hs.ap);
     } else if (prm.prec == CGS_FP32_BULK) {
         std::vector<float> f(hs.inv.begin(), hs.inv.end());
         UP(d.inv32, f);
+        UP(d.went32, std::vector<float>(hs.wsub_ras.begin(), hs.wsub_ras.end()));
+        if (d.cg_steps) UP(d.ap32, std::vector<float>(hs.ap.begin(), hs.ap.end()));
     } else {
+        UP(d.went32, std::vector<float>(hs.wsub_ras.begin(), hs.wsub_ras.end()));
         std::vector<__half> h(hs.inv.size());
         std::vector<float> sc(hs.n_wsub, 1.0f);
         for (int64_t p = 0; p < hs.n_wsub; ++p) {
@@ -828,8 +885,22 @@ cgs_status cgs_mesh_setup(cgs_ctx* ctx, const double* xyz, int64_t nv, const int
         UP(d.pack_idx_off, std::vector<int64_t>(hs.pack_idx_off.begin(), hs.pack_idx_off.end() - 1));
         UP(d.pack_inv_off, std::vector<int64_t>(hs.pack_inv_off.begin(), hs.pack_inv_off.end() - 1));
         UP(d.pack_idx, hs.pack_idx);
+        if (f64)
+            UP(d.pack_went64, hs.pack_ras);
+        else
+            UP(d.pack_went32, std::vector<float>(hs.pack_ras.begin(), hs.pack_ras.end()));
         const size_t total = hs.pack_inv.size();
-        if (prm.prec == CGS_FP32_BULK) {
+        if (prm.prec == CGS_FP64) {
+            // 16-byte groups of two entries across the 32 lanes
+            std::vector<double> f(total);
+            for (int64_t P = 0; P < np; ++P) {
+                const int64_t ao = hs.pack_inv_off[P], T = lane_entries(hs.pack_m[P]);
+                for (int l = 0; l < 32; ++l)
+                    for (int64_t e = 0; e < T; ++e)
+                        f[ao + (e / 2) * 64 + l * 2 + e % 2] = hs.pack_inv[ao + l * T + e];
+            }
+            UP(d.pack_inv64, f);
+        } else if (prm.prec == CGS_FP32_BULK) {
             std::vector<float> f(total);
             for (int64_t P = 0; P < np; ++P) {
                 const int64_t ao = hs.pack_inv_off[P], T = lane_entries(hs.pack_m[P]);
@@ -864,6 +935,7 @@ cgs_status cgs_mesh_setup(cgs_ctx* ctx, const double* xyz, int64_t nv, const int
         UP(d.rpack_idx_off, std::vector<int64_t>(hs.rpack_idx_off.begin(), hs.rpack_idx_off.end() - 1));
         UP(d.rpack_inv_off, std::vector<int64_t>(hs.rpack_inv_off.begin(), hs.rpack_inv_off.end() - 1));
         UP(d.rpack_idx, hs.rpack_idx);
+        UP(d.rpack_went32, std::vector<float>(hs.rpack_ras.begin(), hs.rpack_ras.end()));
         const size_t total = hs.rpack_inv.size();
         if (prm.prec == CGS_FP32_BULK) {
             std::vector<float> f(total);
@@ -977,7 +1049,7 @@ cgs_status cgs_mesh_setup(cgs_ctx* ctx, const double* xyz, int64_t nv, const int
         m->d_dev = const_cast<DevMesh*>(dd);
     }
     // one solve slot and its work tables
-    m->sizes = MeshSizes{nv, ne, d.ntiles, hs.n_wsub, hs.nr, d.n_pack, d.nvb, d.nrng, d.n_rpack, d.nxseg};
+    m->sizes = MeshSizes{nv, ne, d.ntiles, hs.n_wsub, hs.nr, d.n_pack, d.nvb, d.nrng, d.n_rpack, d.nxseg, d.nhr};
     Engine& E = m->E;
     E.f64 = f64;
     E.prec = prm.prec;
@@ -986,6 +1058,7 @@ cgs_status cgs_mesh_setup(cgs_ctx* ctx, const double* xyz, int64_t nv, const int
     E.P.nslots = 1;
     E.P.max_m = d.max_m;
     E.P.any_nr = hs.nr > 0;
+    E.P.hyb_restrict = d.nhr > 0;
     {
         const MeshSizes sz = m->sizes;
         E.build = [sz](const Schedule& sch, std::vector<Work> (&tabs)[kWorkKinds]) {
@@ -1070,7 +1143,7 @@ cgs_status cgs_mesh_info(const cgs_mesh* m, cgs_mesh_info_t* info) {
 }
 
 cgs_status cgs_mesh_set_form(cgs_mesh* m, cgs_form form) {
-    if (!m || form < CGS_HYBRID || form > CGS_ADDITIVE) return fail(CGS_ERR_INVALID_ARG, "bad mesh or form");
+    if (!m || form < CGS_HYBRID || form > CGS_RAS) return fail(CGS_ERR_INVALID_ARG, "bad mesh or form");
     if (form != m->E.form && m->E.gexec) {   // the captured loop holds the old form
         cudaDeviceSynchronize();
         cudaGraphExecDestroy(m->E.gexec);
@@ -1795,6 +1868,7 @@ cudaError_t server_tables(cgs_server* sv, const std::vector<int>& ids, cgs_serve
     P.meshes = sv->reg_d;
     P.nslots = sv->max_slots;
     P.wait_limit = sv->E.P.wait_limit;
+    P.bar_limit = sv->E.P.bar_limit;
     P.tile_tma = sv->sch.tile_tma != 0;
     P.pdl = sv->sch.pdl != 0;
     P.interp_cells = sv->sch.interp_cells != 0;
@@ -1825,6 +1899,7 @@ cudaError_t server_tables(cgs_server* sv, const std::vector<int>& ids, cgs_serve
         P.nwork[kind] = (unsigned int)n;
     }
     P.any_xxt = P.nwork[kWorkXSeg] > 0;
+    P.hyb_restrict = hyb_restrict_ok(P, tabs);
     return cudaSuccess;
 }
 

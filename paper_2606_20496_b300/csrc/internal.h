@@ -36,6 +36,7 @@ struct HostSetup {
     std::vector<uint8_t> dir;          // nv, 1 = Dirichlet
     std::vector<double> invcnt;        // nv, 1 / (elements at the vertex)
     std::vector<double> wov;           // nv, 1 / (subdomains holding the vertex), 0 if none
+    std::vector<double> ras_w;         // sum_m, RAS prolongation weight of each entry of sub_idx
     // subdomains, in caller order
     std::vector<int64_t> sub_ptr;      // n_sub+1
     std::vector<int32_t> sub_idx;      // sum_m, ascending vertex ids per subdomain
@@ -46,17 +47,21 @@ struct HostSetup {
     std::vector<int32_t> wsub_idx;
     std::vector<int64_t> inv_ptr;      // n_wsub+1, offsets (entries) of the inverses
     std::vector<double> inv;           // cyclic diagonals (i, (i+d) mod m) at d*m + i, float64
+    std::vector<double> wsub_ras;      // RAS weights aligned with wsub_idx
+    std::vector<double> ap;            // A_p in the same layout (inexact local solves only)
     // lane packs (mixed forms): 32 subdomains of one size class, one per lane
     std::vector<int32_t> pack_m;       // n_pack, class size
     std::vector<int64_t> pack_idx_off; // n_pack+1, offsets into pack_idx (32*M per pack)
     std::vector<int64_t> pack_inv_off; // n_pack+1, offsets into pack_inv (32*lane_entries(M) per pack)
     std::vector<int32_t> pack_idx;     // [pack][k][lane] vertex id, -1 = padding
     std::vector<double> pack_inv;      // [pack][lane][lane_entries(M)] upper triangle, row-major, float64
+    std::vector<double> pack_ras;      // RAS weights aligned with pack_idx
     // row packs (small meshes): the same subdomains, 8 per pack, full rows
     std::vector<int32_t> rpack_m;
     std::vector<int64_t> rpack_idx_off, rpack_inv_off;
     std::vector<int32_t> rpack_idx;    // [pack][k][lane] vertex id of row k of lane's subdomain, -1 = padding
     std::vector<double> rpack_inv;     // [pack][lane][row_entries(M)] rows g, g+4, ... of the inverse
+    std::vector<double> rpack_ras;     // RAS weights aligned with rpack_idx
     // box coarse space
     int b[3] = {1, 1, 1};
     double lo[3] = {0, 0, 0}, H[3] = {1, 1, 1};
@@ -75,6 +80,16 @@ struct HostSetup {
     std::vector<int32_t> re_vert, re_cell;   // the same entries sorted by cell (restriction)
     std::vector<double> re_w;
     std::vector<int32_t> re_rng;       // (begin, end) entry ranges within one cell, <= kBoxRange each
+    // J~ = W Q^T J_L as explicit rows, aligned with vb_vert (the same
+    // interpolant as the box lists, the weights formed once in float64)
+    std::vector<int32_t> jt_ptr;       // nvb+1
+    std::vector<int32_t> jt_col;       // reduced columns, ascending per row
+    std::vector<double> jt_val;
+    // restriction of the hybrid step, r_r = J~^T r - (A J~)^T l, as explicit
+    // entries sorted by reduced column, then vertex (hybrid set-ups only)
+    std::vector<int32_t> hr_vert;
+    std::vector<double> hr_j, hr_g;    // J~_vc and (A J~)_vc
+    std::vector<int32_t> hr_rng;       // 4 per range: begin, end, column, 0 (<= kBoxRange entries)
     std::vector<int64_t> box_active;   // nr, lexicographic box-vertex ids
     int coarse = 1;                    // reduced solver: 1 dense A_r^{-1}, 2 XX^T
     int64_t ar_nnz = 0;                // nonzeros of A_r
@@ -141,6 +156,13 @@ struct DevMesh {
     const float* inv32 = nullptr;
     const __half* inv16 = nullptr;
     const float* inv16_scale = nullptr;// n_sub
+    // RAS prolongation weight of each entry of sub_idx (Sec. 3, R~_p)
+    const double* went64 = nullptr;
+    const float* went32 = nullptr;
+    // inexact local solves (cg_steps > 0): A_p in the layout of the inverses
+    int32_t cg_steps = 0;
+    const double* ap64 = nullptr;
+    const float* ap32 = nullptr;
     // lane packs (mixed forms): 32 subdomains of one size class M per pack,
     // lane l of the pack solves one; idx [k][32], entries float4 groups
     // [e/4][32][4] (float) or 8-entry groups [e/8][32][8] (half, per-lane scale)
@@ -149,6 +171,9 @@ struct DevMesh {
     const int64_t* pack_idx_off = nullptr; // n_pack
     const int64_t* pack_inv_off = nullptr; // n_pack (entries)
     const int32_t* pack_idx = nullptr;
+    const double* pack_inv64 = nullptr;    // FP64 form: groups [e/2][32][2]
+    const double* pack_went64 = nullptr;   // RAS weights [k][32], aligned with pack_idx
+    const float* pack_went32 = nullptr;
     const float* pack_inv32 = nullptr;
     const __half* pack_inv16 = nullptr;
     const float* pack_scale = nullptr;     // n_pack*32 (half entries)
@@ -162,8 +187,19 @@ struct DevMesh {
     const float* rpack_inv32 = nullptr;
     const __half* rpack_inv16 = nullptr;
     const float* rpack_scale = nullptr;
+    const float* rpack_went32 = nullptr;   // RAS weights, aligned with rpack_idx
     const double* wov64 = nullptr;     // nv
     const float* wov32 = nullptr;      // nv
+    // explicit rows of J~ (FP64 form), aligned with vb_vert
+    const int32_t* jt_ptr = nullptr;   // nvb + 1
+    const int32_t* jt_col = nullptr;
+    const double* jt_val = nullptr;
+    // restriction of the hybrid step r_r = J~^T r - (A J~)^T l (hybrid set-ups)
+    int64_t nhr = 0;                   // ranges
+    const int4* hr_rng = nullptr;      // (begin, end, column, 0), <= kBoxRange entries of one column
+    const int32_t* hr_vert = nullptr;
+    const double2* hr_jg64 = nullptr;  // (J~_vc, (A J~)_vc), FP64 form
+    const float2* hr_jg32 = nullptr;   // the same rounded to float, mixed forms
     int32_t xxt = 0;                   // 1: reduced solve by XX^T (the fields below), else dense
     int64_t nxseg = 0;                 // pass-1 segments
     const int4* xs_seg = nullptr;      // (column, begin, end, 0) of each segment of X's columns
@@ -193,6 +229,7 @@ enum WorkKind {
     kWorkBoxEnt,
     kWorkRowPack,
     kWorkXSeg,
+    kWorkHybR,
     kWorkKinds
 };
 
@@ -211,6 +248,8 @@ struct Plan {
     bool pdl = true;                       // launch with programmatic stream serialization
     bool interp_cells = false;             // interpolation by cell-sorted entries (dots left to the caller)
     bool any_xxt = false;                  // some mesh solves its reduced system by XX^T
+    bool hyb_restrict = false;             // every mesh with a reduced space has the hybrid
+                                           // restriction entries (no s = r - A l needed)
 };
 
 // Grid-wide barrier of the persistent PCG kernel (device memory, zeroed

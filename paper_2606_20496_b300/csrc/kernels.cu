@@ -43,6 +43,13 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
+template <typename T>
+__device__ __forceinline__ T warp_sum_t(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
 __device__ __forceinline__ bool is_done(const SolveScalars* S) {
     return S != nullptr && *(volatile const int*)&S->done;
 }
@@ -825,6 +832,19 @@ template <>
 __device__ __forceinline__ const double* overlap_weights<double>(const DevMesh& M) { return M.wov64; }
 template <>
 __device__ __forceinline__ const float* overlap_weights<float>(const DevMesh& M) { return M.wov32; }
+// RAS weights per entry of the warp-kernel index sets
+template <typename T>
+__device__ __forceinline__ const T* entry_weights(const DevMesh& M);
+template <>
+__device__ __forceinline__ const double* entry_weights<double>(const DevMesh& M) { return M.went64; }
+template <>
+__device__ __forceinline__ const float* entry_weights<float>(const DevMesh& M) { return M.went32; }
+// the weight of entry k (vertex v) of a subdomain: W_ov(v) (mode 1), the RAS
+// entry weight (mode 2) or 1
+template <typename T>
+__device__ __forceinline__ T out_weight(const T* wov, const T* went, int v, int k) {
+    return wov ? __ldg(&wov[v]) : went ? __ldg(&went[k]) : T(1);
+}
 
 template <typename T, typename Stor>
 __device__ __forceinline__ void local_warp_item(const DevMesh* __restrict__ meshes, const Work& w, Vecs V,
@@ -834,7 +854,8 @@ __device__ __forceinline__ void local_warp_item(const DevMesh* __restrict__ mesh
     T* out = outv + w.voff;
     const Stor* inv = inverse_store<Stor>(M);
     const float* scale = M.inv16_scale;
-    const T* wov = weighted ? overlap_weights<T>(M) : nullptr;
+    const T* wov = weighted == 1 ? overlap_weights<T>(M) : nullptr;
+    const T* went = weighted == 2 ? entry_weights<T>(M) : nullptr;
     const int lane = threadIdx.x & 31;
     for (int p = w.begin + (int)(threadIdx.x >> 5); p < w.end; p += kBlock / 32) {
         const int o = __ldg(&M.sub_ptr[p]);
@@ -870,7 +891,7 @@ __device__ __forceinline__ void local_warp_item(const DevMesh* __restrict__ mesh
                 const T xm = __shfl_sync(0xffffffffu, x, jm);
                 y += ap[d] * xp + am[d] * xm;
             }
-            if (h) atomicAdd(&out[v], wov ? y * __ldg(&wov[v]) : y);
+            if (h) atomicAdd(&out[v], y * out_weight(wov, went, v, o + lane));
         } else {
             // 33..64 dofs: lane holds rows lane and lane + 32
             const bool h1 = lane + 32 < m;
@@ -901,9 +922,96 @@ __device__ __forceinline__ void local_warp_item(const DevMesh* __restrict__ mesh
                     }
                 }
             }
-            atomicAdd(&out[v0], wov ? y0 * __ldg(&wov[v0]) : y0);
-            if (h1) atomicAdd(&out[v1], wov ? y1 * __ldg(&wov[v1]) : y1);
+            atomicAdd(&out[v0], y0 * out_weight(wov, went, v0, o + lane));
+            if (h1) atomicAdd(&out[v1], y1 * out_weight(wov, went, v1, o + lane + 32));
         }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Inexact local solves (Sec. 6): a fixed number of CG steps on A_p y = R_p r
+// from y = 0, one warp per subdomain (m_p <= 64; lane i holds entries i and
+// i + 32).  A_p is stored by cyclic diagonals like the inverses, so the
+// product A_p d uses the same coalesced diagonal reads and shuffles; each
+// step adds two warp sums (d.A_p d and the new residual norm).
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ const T* local_matrix_store(const DevMesh& M);
+template <>
+__device__ __forceinline__ const double* local_matrix_store<double>(const DevMesh& M) { return M.ap64; }
+template <>
+__device__ __forceinline__ const float* local_matrix_store<float>(const DevMesh& M) { return M.ap32; }
+
+// (y0, y1) = A (x0, x1) rows lane and lane + 32 of an m x m symmetric matrix
+// in cyclic diagonals at a + io (entry (i, (i+d) mod m) at d m + i)
+template <typename T>
+__device__ __forceinline__ void cyclic_matvec(const T* __restrict__ a, size_t io, int m, int lane, T x0, T x1,
+                                              T& y0, T& y1) {
+    const int nd = m / 2 + 1;
+    y0 = lane < m ? __ldg(&a[io + lane]) * x0 : T(0);
+    y1 = lane + 32 < m ? __ldg(&a[io + lane + 32]) * x1 : T(0);
+    for (int d = 1; d < nd; ++d) {
+        const size_t row = io + (size_t)d * m;
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+            const int i = lane + 32 * half;
+            int jp = i + d;
+            if (jp >= m) jp -= m;
+            int jm = i - d;
+            if (jm < 0) jm += m;
+            const T pa = __shfl_sync(0xffffffffu, x0, jp & 31), pb = __shfl_sync(0xffffffffu, x1, jp & 31);
+            const T ma = __shfl_sync(0xffffffffu, x0, jm & 31), mb = __shfl_sync(0xffffffffu, x1, jm & 31);
+            if (i < m) {
+                T acc = __ldg(&a[row + i]) * (jp < 32 ? pa : pb);
+                if (2 * d != m) acc = fma(__ldg(&a[row + jm]), jm < 32 ? ma : mb, acc);
+                if (half == 0)
+                    y0 += acc;
+                else
+                    y1 += acc;
+            }
+        }
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void local_cg_item(const DevMesh* __restrict__ meshes, const Work& w, Vecs V,
+                                              const T* __restrict__ rin, T* __restrict__ outv, int weighted) {
+    CGS_ITEM_PROLOGUE();
+    const T* r = rin + w.voff;
+    T* out = outv + w.voff;
+    const T* a = local_matrix_store<T>(M);
+    const T* wov = weighted == 1 ? overlap_weights<T>(M) : nullptr;
+    const T* went = weighted == 2 ? entry_weights<T>(M) : nullptr;
+    const int lane = threadIdx.x & 31;
+    const int steps = M.cg_steps;
+    for (int p = w.begin + (int)(threadIdx.x >> 5); p < w.end; p += kBlock / 32) {
+        const int o = __ldg(&M.sub_ptr[p]);
+        const int m = __ldg(&M.sub_ptr[p + 1]) - o;
+        if (m == 0 || m > 64) continue;
+        const size_t io = (size_t)__ldg(&M.inv_ptr[p]);
+        const bool h0 = lane < m, h1 = lane + 32 < m;
+        const int v0 = h0 ? __ldg(&M.sub_idx[o + lane]) : 0;
+        const int v1 = h1 ? __ldg(&M.sub_idx[o + lane + 32]) : 0;
+        T res0 = h0 ? __ldg(&r[v0]) : T(0), res1 = h1 ? __ldg(&r[v1]) : T(0);
+        T y0 = T(0), y1 = T(0), d0 = res0, d1 = res1;
+        T rr = warp_sum_t(fma(res0, res0, res1 * res1));
+        for (int it = 0; it < steps; ++it) {
+            T q0, q1;
+            cyclic_matvec(a, io, m, lane, d0, d1, q0, q1);
+            const T dq = warp_sum_t(fma(d0, q0, d1 * q1));
+            const T al = dq > T(0) ? rr / dq : T(0);
+            y0 = fma(al, d0, y0);
+            y1 = fma(al, d1, y1);
+            res0 = fma(-al, q0, res0);
+            res1 = fma(-al, q1, res1);
+            const T rn = warp_sum_t(fma(res0, res0, res1 * res1));
+            const T be = rr > T(0) ? rn / rr : T(0);
+            d0 = fma(be, d0, res0);
+            d1 = fma(be, d1, res1);
+            rr = rn;
+        }
+        if (h0) atomicAdd(&out[v0], y0 * out_weight(wov, went, v0, o + lane));
+        if (h1) atomicAdd(&out[v1], y1 * out_weight(wov, went, v1, o + lane + 32));
     }
 }
 
@@ -914,7 +1022,11 @@ __global__ void __launch_bounds__(kBlock) local_warp_kernel(const DevMesh* __res
                                                             int weighted) {
     const Work w_ = work[blockIdx.x];
     pdl_wait();
-    local_warp_item<T, Stor>(meshes, w_, V, rin, outv, weighted);
+    // a mesh set up for inexact local solves runs CG on A_p instead
+    if (std::is_same<T, Stor>::value && meshes[w_.mesh].cg_steps > 0)
+        local_cg_item<T>(meshes, w_, V, rin, outv, weighted);
+    else
+        local_warp_item<T, Stor>(meshes, w_, V, rin, outv, weighted);
 }
 
 // Subdomains with more than 64 dofs: the whole block on one subdomain, rows
@@ -926,7 +1038,8 @@ __device__ __forceinline__ void local_block_item(const DevMesh* __restrict__ mes
     const T* r = rin + w.voff;
     T* out = outv + w.voff;
     const Stor* inv = inverse_store<Stor>(M);
-    const T* wov = weighted ? overlap_weights<T>(M) : nullptr;
+    const T* wov = weighted == 1 ? overlap_weights<T>(M) : nullptr;
+    const T* went = weighted == 2 ? entry_weights<T>(M) : nullptr;
     for (int p = w.begin; p < w.end; ++p) {
         const int o = M.sub_ptr[p];
         const int m = M.sub_ptr[p + 1] - o;
@@ -937,7 +1050,7 @@ __device__ __forceinline__ void local_block_item(const DevMesh* __restrict__ mes
             T y = 0;
             for (int j = 0; j < m; ++j) y += diag_entry<T, Stor>(inv, io, m, i, j, sc) * __ldg(&r[M.sub_idx[o + j]]);
             const int v = M.sub_idx[o + i];
-            atomicAdd(&out[v], wov ? y * wov[v] : y);
+            atomicAdd(&out[v], y * out_weight(wov, went, v, o + i));
         }
     }
 }
@@ -970,6 +1083,12 @@ __device__ __forceinline__ uint4 ld_stream_u4(const uint4* p) {
     return v;
 }
 
+__device__ __forceinline__ double2 ld_stream_d2(const double2* p) {
+    double2 v;
+    asm("ld.global.nc.L1::no_allocate.v2.f64 {%0, %1}, [%2];" : "=d"(v.x), "=d"(v.y) : "l"(p));
+    return v;
+}
+
 // entries of one lane, group by group: float (4 per group) or half (8)
 struct LaneEntries32 {
     const float4* a;   // pack base, groups [g][32]
@@ -993,49 +1112,64 @@ struct LaneEntries16 {
     }
 };
 
-template <int Mc, class Entries>
-__device__ __forceinline__ void lane_solve(Entries A, const int32_t* __restrict__ idx, const float* __restrict__ r,
-                                           float* __restrict__ out, const float* __restrict__ wov, int lane) {
-    float x[Mc], y[Mc];
+// entries of one lane in the FP64 form: groups of two doubles
+struct LaneEntries64 {
+    const double2* a;   // pack base, groups [g][32]
+    int lane;
+    double2 cur;
+    __device__ __forceinline__ double get(int e) {
+        if ((e & 1) == 0) cur = ld_stream_d2(a + (e >> 1) * 32 + lane);
+        return (e & 1) ? cur.y : cur.x;
+    }
+};
+
+// wov: W_ov per vertex (hybrid), went: a weight per entry aligned with idx
+// (the RAS prolongation), or neither (additive)
+template <int Mc, typename T, class Entries>
+__device__ __forceinline__ void lane_solve(Entries A, const int32_t* __restrict__ idx, const T* __restrict__ r,
+                                           T* __restrict__ out, const T* __restrict__ wov, const T* __restrict__ went,
+                                           int lane) {
+    T x[Mc], y[Mc];
 #pragma unroll
     for (int k = 0; k < Mc; ++k) {
         const int v = __ldg(&idx[k * 32 + lane]);
-        x[k] = v >= 0 ? __ldg(&r[v]) : 0.0f;
-        y[k] = 0.0f;
+        x[k] = v >= 0 ? __ldg(&r[v]) : T(0);
+        y[k] = T(0);
     }
     int e = 0;
 #pragma unroll
     for (int i = 0; i < Mc; ++i) {
 #pragma unroll
         for (int j = i; j < Mc; ++j, ++e) {
-            const float a = A.get(e);
+            const T a = A.get(e);
             if (i == j) {
-                y[i] = fmaf(a, x[i], y[i]);
+                y[i] = fma(a, x[i], y[i]);
             } else {
-                y[i] = fmaf(a, x[j], y[i]);
-                y[j] = fmaf(a, x[i], y[j]);
+                y[i] = fma(a, x[j], y[i]);
+                y[j] = fma(a, x[i], y[j]);
             }
         }
     }
 #pragma unroll
     for (int k = 0; k < Mc; ++k) {
         const int v = __ldg(&idx[k * 32 + lane]);
-        if (v >= 0) atomicAdd(&out[v], wov ? y[k] * __ldg(&wov[v]) : y[k]);
+        if (v >= 0)
+            atomicAdd(&out[v], wov ? y[k] * __ldg(&wov[v]) : went ? y[k] * __ldg(&went[k * 32 + lane]) : y[k]);
     }
 }
 
-template <class Entries>
-__device__ __forceinline__ void lane_dispatch(int Mc, const Entries& A, const int32_t* idx, const float* r,
-                                              float* out, const float* wov, int lane) {
+template <typename T, class Entries>
+__device__ __forceinline__ void lane_dispatch(int Mc, const Entries& A, const int32_t* idx, const T* r, T* out,
+                                              const T* wov, const T* went, int lane) {
     switch (Mc) {
-        case 8: lane_solve<8>(A, idx, r, out, wov, lane); break;
-        case 12: lane_solve<12>(A, idx, r, out, wov, lane); break;
-        case 16: lane_solve<16>(A, idx, r, out, wov, lane); break;
-        case 18: lane_solve<18>(A, idx, r, out, wov, lane); break;
-        case 20: lane_solve<20>(A, idx, r, out, wov, lane); break;
-        case 24: lane_solve<24>(A, idx, r, out, wov, lane); break;
-        case 27: lane_solve<27>(A, idx, r, out, wov, lane); break;
-        default: lane_solve<32>(A, idx, r, out, wov, lane); break;
+        case 8: lane_solve<8, T>(A, idx, r, out, wov, went, lane); break;
+        case 12: lane_solve<12, T>(A, idx, r, out, wov, went, lane); break;
+        case 16: lane_solve<16, T>(A, idx, r, out, wov, went, lane); break;
+        case 18: lane_solve<18, T>(A, idx, r, out, wov, went, lane); break;
+        case 20: lane_solve<20, T>(A, idx, r, out, wov, went, lane); break;
+        case 24: lane_solve<24, T>(A, idx, r, out, wov, went, lane); break;
+        case 27: lane_solve<27, T>(A, idx, r, out, wov, went, lane); break;
+        default: lane_solve<32, T>(A, idx, r, out, wov, went, lane); break;
     }
 }
 
@@ -1046,19 +1180,21 @@ __device__ __forceinline__ void local_lane_item(const DevMesh* __restrict__ mesh
     CGS_ITEM_PROLOGUE();
     const float* r = rin + w.voff;
     float* out = outv + w.voff;
-    const float* wov = weighted ? M.wov32 : nullptr;
+    const float* wov = weighted == 1 ? M.wov32 : nullptr;
     const int lane = threadIdx.x & 31;
     for (int pk = w.begin + (int)(threadIdx.x >> 5); pk < w.end; pk += kBlock / 32) {
         const int Mc = __ldg(&M.pack_m[pk]);
-        const int32_t* idx = M.pack_idx + __ldg(&M.pack_idx_off[pk]);
+        const int64_t io = __ldg(&M.pack_idx_off[pk]);
+        const int32_t* idx = M.pack_idx + io;
+        const float* went = weighted == 2 ? M.pack_went32 + io : nullptr;
         const int64_t ao = __ldg(&M.pack_inv_off[pk]);
         if (std::is_same<Stor, float>::value) {
             LaneEntries32 A{reinterpret_cast<const float4*>(M.pack_inv32 + ao), lane, {}};
-            lane_dispatch(Mc, A, idx, r, out, wov, lane);
+            lane_dispatch(Mc, A, idx, r, out, wov, went, lane);
         } else {
             LaneEntries16 A{reinterpret_cast<const uint4*>(M.pack_inv16 + ao), lane,
                             __ldg(&M.pack_scale[(size_t)pk * 32 + lane]), {}};
-            lane_dispatch(Mc, A, idx, r, out, wov, lane);
+            lane_dispatch(Mc, A, idx, r, out, wov, went, lane);
         }
     }
 }
@@ -1073,6 +1209,32 @@ __global__ void __launch_bounds__(kBlock, 2) local_lane_kernel(const DevMesh* __
     local_lane_item<Stor>(meshes, w_, V, rin, outv, weighted);
 }
 
+// The FP64 form's lane packs (meshes with many small subdomains): the same
+// one-lane-per-subdomain product in float64.  A lane holds 2 M doubles of x
+// and y in registers, so one block per SM (up to 255 registers a thread);
+// the kernel is bound by the FP64 FMA rate, M^2 FMAs per subdomain.
+__global__ void __launch_bounds__(kBlock, 1) local_lane64_kernel(const DevMesh* __restrict__ meshes,
+                                                                 const Work* __restrict__ work, Vecs V,
+                                                                 const double* __restrict__ rin,
+                                                                 double* __restrict__ outv, int weighted) {
+    const Work w = work[blockIdx.x];
+    pdl_wait();
+    CGS_ITEM_PROLOGUE();
+    const double* r = rin + w.voff;
+    double* out = outv + w.voff;
+    const double* wov = weighted == 1 ? M.wov64 : nullptr;
+    const int lane = threadIdx.x & 31;
+    for (int pk = w.begin + (int)(threadIdx.x >> 5); pk < w.end; pk += kBlock / 32) {
+        const int Mc = __ldg(&M.pack_m[pk]);
+        const int64_t io = __ldg(&M.pack_idx_off[pk]);
+        const int32_t* idx = M.pack_idx + io;
+        const double* went = weighted == 2 ? M.pack_went64 + io : nullptr;
+        const int64_t ao = __ldg(&M.pack_inv_off[pk]);
+        LaneEntries64 A{reinterpret_cast<const double2*>(M.pack_inv64 + ao), lane, {}};
+        lane_dispatch<double>(Mc, A, idx, r, out, wov, went, lane);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Local solves of small meshes, four lanes per subdomain (row packs): a warp
 // takes 8 subdomains of one size class; lane 4 s + g keeps subdomain s's x
@@ -1083,7 +1245,8 @@ __global__ void __launch_bounds__(kBlock, 2) local_lane_kernel(const DevMesh* __
 // ---------------------------------------------------------------------------
 template <int Mc, class Entries>
 __device__ __forceinline__ void row_solve(Entries A, const int32_t* __restrict__ idx, const float* __restrict__ r,
-                                          float* __restrict__ out, const float* __restrict__ wov, int lane) {
+                                          float* __restrict__ out, const float* __restrict__ wov,
+                                          const float* __restrict__ went, int lane) {
     constexpr int R = row_pack_rows(Mc);
     const int g = lane % kRowLanes;
     float x[Mc], y[R];
@@ -1105,22 +1268,23 @@ __device__ __forceinline__ void row_solve(Entries A, const int32_t* __restrict__
         const int i = q * kRowLanes + g;
         if (i >= Mc) continue;
         const int v = __ldg(&idx[i * 32 + lane]);
-        if (v >= 0) atomicAdd(&out[v], wov ? y[q] * __ldg(&wov[v]) : y[q]);
+        if (v >= 0)
+            atomicAdd(&out[v], wov ? y[q] * __ldg(&wov[v]) : went ? y[q] * __ldg(&went[i * 32 + lane]) : y[q]);
     }
 }
 
 template <class Entries>
 __device__ __forceinline__ void row_dispatch(int Mc, const Entries& A, const int32_t* idx, const float* r,
-                                             float* out, const float* wov, int lane) {
+                                             float* out, const float* wov, const float* went, int lane) {
     switch (Mc) {
-        case 8: row_solve<8>(A, idx, r, out, wov, lane); break;
-        case 12: row_solve<12>(A, idx, r, out, wov, lane); break;
-        case 16: row_solve<16>(A, idx, r, out, wov, lane); break;
-        case 18: row_solve<18>(A, idx, r, out, wov, lane); break;
-        case 20: row_solve<20>(A, idx, r, out, wov, lane); break;
-        case 24: row_solve<24>(A, idx, r, out, wov, lane); break;
-        case 27: row_solve<27>(A, idx, r, out, wov, lane); break;
-        default: row_solve<32>(A, idx, r, out, wov, lane); break;
+        case 8: row_solve<8>(A, idx, r, out, wov, went, lane); break;
+        case 12: row_solve<12>(A, idx, r, out, wov, went, lane); break;
+        case 16: row_solve<16>(A, idx, r, out, wov, went, lane); break;
+        case 18: row_solve<18>(A, idx, r, out, wov, went, lane); break;
+        case 20: row_solve<20>(A, idx, r, out, wov, went, lane); break;
+        case 24: row_solve<24>(A, idx, r, out, wov, went, lane); break;
+        case 27: row_solve<27>(A, idx, r, out, wov, went, lane); break;
+        default: row_solve<32>(A, idx, r, out, wov, went, lane); break;
     }
 }
 
@@ -1132,19 +1296,21 @@ __device__ __forceinline__ void local_rowpack_item(const DevMesh* __restrict__ m
     CGS_ITEM_PROLOGUE();
     const float* r = rin + w.voff;
     float* out = outv + w.voff;
-    const float* wov = weighted ? M.wov32 : nullptr;
+    const float* wov = weighted == 1 ? M.wov32 : nullptr;
     const int lane = threadIdx.x & 31;
     for (int pk = w.begin + (int)(threadIdx.x >> 5); pk < w.end; pk += kBlock / 32) {
         const int Mc = __ldg(&M.rpack_m[pk]);
-        const int32_t* idx = M.rpack_idx + __ldg(&M.rpack_idx_off[pk]);
+        const int64_t io = __ldg(&M.rpack_idx_off[pk]);
+        const int32_t* idx = M.rpack_idx + io;
+        const float* went = weighted == 2 ? M.rpack_went32 + io : nullptr;
         const int64_t ao = __ldg(&M.rpack_inv_off[pk]);
         if (std::is_same<Stor, float>::value) {
             LaneEntries32 A{reinterpret_cast<const float4*>(M.rpack_inv32 + ao), lane, {}};
-            row_dispatch(Mc, A, idx, r, out, wov, lane);
+            row_dispatch(Mc, A, idx, r, out, wov, went, lane);
         } else {
             LaneEntries16 A{reinterpret_cast<const uint4*>(M.rpack_inv16 + ao), lane,
                             __ldg(&M.rpack_scale[(size_t)pk * 32 + lane]), {}};
-            row_dispatch(Mc, A, idx, r, out, wov, lane);
+            row_dispatch(Mc, A, idx, r, out, wov, went, lane);
         }
     }
 }
@@ -1336,6 +1502,139 @@ __global__ void __launch_bounds__(kBlock) restrict_kernel(const DevMesh* __restr
     const Work w_ = work[blockIdx.x];
     pdl_wait();
     restrict_item<T, Tin, kPairOut>(meshes, w_, V, sin, rrv);
+}
+
+// Restriction of the hybrid step without the residual update (Eq. asm2):
+// r_r = J~^T (r - A l) = J~^T r - (A J~)^T l, A symmetric, over explicit
+// entries (v, J~_vc, (A J~)_vc) sorted by reduced column c.  One warp per
+// range of one column (<= kBoxRange entries): each lane takes every 32nd
+// entry, four at a time with the loads first, the warp sums, and lane 0 adds
+// the total to r_r[c] once.  This replaces the inner operator apply s -= A l
+// (one pass over the element matrices) and the restriction of s.
+// T = double: float64 entries, r_r float64; T = float (mixed forms): float
+// entries and inputs, r_r a float pair (compensated atomic).
+__device__ __forceinline__ double2 hr_entry(const DevMesh& M, int i, double) { return __ldg(&M.hr_jg64[i]); }
+__device__ __forceinline__ float2 hr_entry(const DevMesh& M, int i, float) { return __ldg(&M.hr_jg32[i]); }
+
+template <typename T>
+__device__ __forceinline__ void restrict_hyb_item(const DevMesh* __restrict__ meshes, const Work& w, Vecs V,
+                                                  const T* __restrict__ rin, const T* __restrict__ lin,
+                                                  void* __restrict__ rrv) {
+    CGS_ITEM_PROLOGUE();
+    const int q = w.begin + (int)(threadIdx.x >> 5);
+    if (q >= w.end) return;   // whole warps leave
+    const T* r = rin + w.voff;
+    const T* l = lin + w.voff;
+    const int lane = threadIdx.x & 31;
+    const int4 rg = __ldg(&M.hr_rng[q]);
+    T acc = T(0);
+    for (int i0 = rg.x + lane; i0 < rg.y; i0 += 128) {
+        int v[4];
+        decltype(hr_entry(M, 0, T(0))) jg[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int i = i0 + 32 * k;
+            v[k] = i < rg.y ? __ldg(&M.hr_vert[i]) : -1;
+            if (i < rg.y) jg[k] = hr_entry(M, i, T(0));
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (v[k] < 0) continue;
+            acc = fma(jg[k].x, __ldg(&r[v[k]]), acc);
+            acc = fma(-jg[k].y, __ldg(&l[v[k]]), acc);
+        }
+    }
+    acc = warp_sum_t(acc);
+    if (lane == 0)
+        pool_add(static_cast<double*>(rrv) + w.roff, static_cast<float2*>(rrv) + w.roff, rg.z, one_sum(acc),
+                 std::integral_constant<bool, std::is_same<T, float>::value>());
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBlock) restrict_hyb_kernel(const DevMesh* __restrict__ meshes,
+                                                              const Work* __restrict__ work, Vecs V,
+                                                              const T* __restrict__ rin, const T* __restrict__ lin,
+                                                              void* __restrict__ rrv) {
+    const Work w_ = work[blockIdx.x];
+    pdl_wait();
+    restrict_hyb_item<T>(meshes, w_, V, rin, lin, rrv);
+}
+
+// z += J~ u_r by the explicit float64 rows of J~ (FP64 form): one thread per
+// box-list vertex, the row's (column, weight) pairs with u_r gathered from
+// L2; kDots also forms the PCG dots z.r, z.q and beta (as interp_add).
+template <int kDots>
+__device__ __forceinline__ void interp_rows_item(const DevMesh* __restrict__ meshes, const Work& w, Vecs V,
+                                                 const double* __restrict__ urv, double* __restrict__ zv) {
+    CGS_ITEM_PROLOGUE();
+    const double* ur = urv + w.roff;
+    double* z = zv + w.voff;
+    const double* __restrict__ r64 = V.r + w.voff;
+    const double* __restrict__ q64 = V.q + w.voff;
+    double zr = 0.0, zq = 0.0;
+    for (int64_t i0 = (int64_t)w.begin + threadIdx.x; i0 < w.end; i0 += 2 * (int64_t)blockDim.x) {
+        int v[2], p0[2], p1[2];
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const int64_t i = i0 + k * (int64_t)blockDim.x;
+            v[k] = -1;
+            p0[k] = p1[k] = 0;
+            if (i < w.end) {
+                v[k] = __ldg(&M.vb_vert[i]);
+                p0[k] = __ldg(&M.jt_ptr[i]);
+                p1[k] = __ldg(&M.jt_ptr[i + 1]);
+            }
+        }
+        double zo[2], rd[2], qd[2], val[2];
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const bool ok = v[k] >= 0;
+            zo[k] = ok ? z[v[k]] : 0.0;
+            rd[k] = (kDots && ok) ? r64[v[k]] : 0.0;
+            qd[k] = (kDots && ok) ? q64[v[k]] : 0.0;
+            val[k] = 0.0;
+        }
+#pragma unroll
+        for (int k = 0; k < 2; ++k)
+            for (int e = p0[k]; e < p1[k]; ++e) val[k] = fma(__ldg(&M.jt_val[e]), __ldg(&ur[__ldg(&M.jt_col[e])]), val[k]);
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            if (v[k] < 0) continue;
+            const double zi = zo[k] + val[k];
+            z[v[k]] = zi;
+            if (kDots) {
+                zr = fma(zi, rd[k], zr);
+                zq = fma(zi, qd[k], zq);
+            }
+        }
+    }
+    if (kDots == 0 || !S) return;
+    double val2[2] = {zr, zq}, tot[2];
+    pdl_trigger();   // the successor may launch during the reduction tail
+    if (slot_sum<2>(val2, V.partials + w.poff, w.idx, w.count, &S->ticket[3], tot) && threadIdx.x == 0) {
+        S->zr = tot[0];
+        S->zq = tot[1];
+        const double beta = -S->alpha * tot[1] / S->rho;
+        S->beta = beta;
+        S->beta2 = split_pair(beta);
+        S->rho = tot[0];
+        if (!(tot[0] > 0.0) || !isfinite(tot[0]) || !isfinite(beta)) {
+            S->status = CGS_ERR_BREAKDOWN;
+            S->done = 1;
+        }
+    }
+}
+
+template <int kDots>
+__global__ void __launch_bounds__(kBlock) interp_rows_kernel(const DevMesh* __restrict__ meshes,
+                                                             const Work* __restrict__ work, Vecs V,
+                                                             const double* __restrict__ urv,
+                                                             double* __restrict__ zv, int nslots,
+                                                             cudaGraphConditionalHandle cond, int set_cond) {
+    const Work w_ = work[blockIdx.x];
+    pdl_wait();
+    if (set_cond && blockIdx.x == 0) loop_condition(V.S, nslots, cond);
+    interp_rows_item<kDots>(meshes, w_, V, urv, zv);
 }
 
 // z += W Q^T J_L u_r over the cell-sorted box-list entries (the transpose of
@@ -2441,9 +2740,9 @@ void launch_apply28f_tiled(const Plan& P, const Vecs& V, const float* x, float* 
     }
 }
 
-void launch_local(const Plan& P, const Vecs& V, cgs_precision prec, const void* r, void* out, bool weighted,
+void launch_local(const Plan& P, const Vecs& V, cgs_precision prec, const void* r, void* out, int weighted,
                   cudaStream_t st) {
-    const int wt = weighted ? 1 : 0;
+    const int wt = weighted;
     // mixed forms: subdomains of at most kLaneMaxM dofs in lane packs, or in
     // row packs (small meshes)
     if (prec != CGS_FP64 && P.nwork[kWorkRowPack]) {
@@ -2466,8 +2765,11 @@ void launch_local(const Plan& P, const Vecs& V, cgs_precision prec, const void* 
             launch_pdl(P.pdl, local_lane_kernel<__half>, P.nwork[kWorkPack], kBlock, 0, st, P.meshes, P.work[kWorkPack],
                        V, rf, of, wt);
     }
-    // the rest (every subdomain in the FP64 form): a warp per subdomain of
-    // up to 64 dofs, a block per larger one
+    if (prec == CGS_FP64 && P.nwork[kWorkPack])
+        launch_pdl(P.pdl, local_lane64_kernel, P.nwork[kWorkPack], kBlock, 0, st, P.meshes, P.work[kWorkPack], V,
+                   static_cast<const double*>(r), static_cast<double*>(out), wt);
+    // the rest (in the FP64 form every subdomain outside lane packs): a warp
+    // per subdomain of up to 64 dofs, a block per larger one
     if (!P.nwork[kWorkSub]) return;
     const unsigned int n = P.nwork[kWorkSub];
     const Work* W = P.work[kWorkSub];
@@ -2510,6 +2812,18 @@ bool launch_local_restrict(const Plan& P, const Vecs& V, cgs_precision prec, con
     return true;
 }
 
+void launch_restrict_hybrid(const Plan& P, const Vecs& V, bool fp64, const void* r, const void* l, void* rr,
+                            cudaStream_t st) {
+    if (!P.nwork[kWorkHybR] || !P.any_nr) return;
+    const unsigned int n = P.nwork[kWorkHybR];
+    if (fp64)
+        launch_pdl(P.pdl, restrict_hyb_kernel<double>, n, kBlock, 0, st, P.meshes, P.work[kWorkHybR], V,
+                   static_cast<const double*>(r), static_cast<const double*>(l), rr);
+    else
+        launch_pdl(P.pdl, restrict_hyb_kernel<float>, n, kBlock, 0, st, P.meshes, P.work[kWorkHybR], V,
+                   static_cast<const float*>(r), static_cast<const float*>(l), rr);
+}
+
 void launch_restrict(const Plan& P, const Vecs& V, bool fp64, const void* s, bool s_is_double, void* rr,
                      bool pair_out, cudaStream_t st) {
     if (!P.nwork[kWorkBoxEnt] || !P.any_nr) return;
@@ -2531,6 +2845,17 @@ void launch_restrict(const Plan& P, const Vecs& V, bool fp64, const void* s, boo
 
 bool launch_interp_add(const Plan& P, const Vecs& V, bool fp64, const double* ur, const float* ur32, void* z,
                        bool dots, const cudaGraphConditionalHandle* cond, cudaStream_t st) {
+    if (fp64) {   // by the explicit float64 rows of J~, the dots fused
+        if (!P.nwork[kWorkBox] || !P.any_nr) return false;
+        const cudaGraphConditionalHandle h = cond ? *cond : 0;
+        if (dots)
+            launch_pdl(P.pdl, interp_rows_kernel<1>, P.nwork[kWorkBox], kBlock, 0, st, P.meshes, P.work[kWorkBox], V,
+                       ur, static_cast<double*>(z), P.nslots, h, cond ? 1 : 0);
+        else
+            launch_pdl(P.pdl, interp_rows_kernel<0>, P.nwork[kWorkBox], kBlock, 0, st, P.meshes, P.work[kWorkBox], V,
+                       ur, static_cast<double*>(z), P.nslots, h, cond ? 1 : 0);
+        return dots;
+    }
     if (P.interp_cells) {   // by cell-sorted entries; the dots are left to the caller
         if (!P.nwork[kWorkBoxEnt] || !P.any_nr) return false;
         const unsigned int n = P.nwork[kWorkBoxEnt];
@@ -2770,6 +3095,7 @@ void append_mesh_work(std::vector<Work> (&tabs)[kWorkKinds], int mesh, int slot,
     add(kWorkBox, z.nvb, sch.box_chunk);
     if (z.nr > 0) add(kWorkBoxEnt, z.nrng, kBlock / 32);
     if (z.nxseg > 0) add(kWorkXSeg, z.nxseg, kRowChunk);
+    if (z.nr > 0 && z.nhr > 0) add(kWorkHybR, z.nhr, kBlock / 32);
 }
 
 int64_t mesh_partial_slots(const MeshSizes& z, const Schedule& sch) {

@@ -27,13 +27,20 @@ void launch_apply64(const Plan& P, const Vecs& V, const double* x, double* y, do
                     cudaStream_t st);
 void launch_apply_pair_tiled(const Plan& P, const Vecs& V, cudaStream_t st);
 void launch_apply28f_tiled(const Plan& P, const Vecs& V, const float* x, float* y, float alpha, cudaStream_t st);
-void launch_local(const Plan& P, const Vecs& V, cgs_precision prec, const void* r, void* out, bool weighted,
+// out += sum_p R~_p^T A_p^{-1} R_p r, weighted: 0 none (additive), 1 W_ov per
+// vertex (hybrid), 2 the RAS weight per entry
+void launch_local(const Plan& P, const Vecs& V, cgs_precision prec, const void* r, void* out, int weighted,
                   cudaStream_t st);
 // Additive form, mixed precision: z += local solves of s and r_r += J^T W s
 // (float pairs) in one launch; false (nothing launched) unless every
 // subdomain is in packs and there is a reduced space.
 bool launch_local_restrict(const Plan& P, const Vecs& V, cgs_precision prec, const float* s, float* z, void* rr,
                            cudaStream_t st);
+// Hybrid step without s = r - A l: r_r += J~^T r - (A J~)^T l over the
+// mesh's explicit entries (float64, or float with a float-pair r_r in the
+// mixed forms); r and l in the bulk precision.  Needs P.hyb_restrict.
+void launch_restrict_hybrid(const Plan& P, const Vecs& V, bool fp64, const void* r, const void* l, void* rr,
+                            cudaStream_t st);
 // r_r += J^T W s.  pair_out: rr holds float pairs (mixed forms, float s)
 void launch_restrict(const Plan& P, const Vecs& V, bool fp64, const void* s, bool s_is_double, void* rr,
                      bool pair_out, cudaStream_t st);
@@ -95,6 +102,7 @@ void launch_fill_f(int64_t n, float* a, float v, cudaStream_t st);
 struct MeshSizes {
     int64_t nv, ne, ntiles, n_sub, nr, n_pack, nvb, nrng, n_rpack;   // n_sub: warp-kernel subdomains
     int64_t nxseg;                                                   // XX^T pass-1 segments (0: dense)
+    int64_t nhr;                                                     // hybrid restriction ranges
 };
 // Block sizes of the range-parallel kernels: vertices per block (vector
 // kernels) and subdomains per block (local solves), and how the tiled

@@ -89,28 +89,33 @@ extern "C" cgs_status cgs_apply_preconditioner_noalloc(cgs_mesh* mesh, const dou
         launch_precond_prep<double>(P, V, r, st);
     else
         launch_precond_prep<float>(P, V, r, st);
-    const bool weighted = mesh_form(mesh) == CGS_HYBRID;
+    const cgs_form form = mesh_form(mesh);
+    const bool weighted = form == CGS_HYBRID;
     // additive mixed form: the local solves and the restriction of s share
     // one launch when every subdomain is in packs (as in the regular call)
-    const bool restricted = !weighted && !f64 && d.nr &&
+    const bool restricted = form == CGS_ADDITIVE && !f64 && d.nr &&
                             launch_local_restrict(P, V, prec, static_cast<const float*>(V.s),
                                                   static_cast<float*>(V.z), V.rr, st);
-    if (!restricted) launch_local(P, V, prec, V.s, V.z, weighted, st);
-    if (weighted) {
+    if (!restricted) launch_local(P, V, prec, V.s, V.z, weighted ? 1 : form == CGS_RAS ? 2 : 0, st);
+    // hybrid: r_r = J~^T r - (A J~)^T l straight from r and l (as the regular
+    // call does when the mesh has the entries), else s = r - A l first
+    const bool hyb_direct = weighted && d.nr && P.hyb_restrict;
+    if (hyb_direct) launch_restrict_hybrid(P, V, f64, V.s, V.z, V.rr, st);
+    if (weighted && !hyb_direct) {
         if (f64)
             launch_apply64(P, V, static_cast<const double*>(V.z), static_cast<double*>(V.s), -1.0, false, st);
         else
             launch_apply28f_tiled(P, V, static_cast<const float*>(V.z), static_cast<float*>(V.s), -1.0f, st);
     }
     if (d.nr && f64) {
-        launch_restrict(P, V, true, V.s, true, V.rr, false, st);
+        if (!hyb_direct) launch_restrict(P, V, true, V.s, true, V.rr, false, st);
         launch_xxt_pass1(P, V, false, V.rr, st);   // XX^T meshes only
         launch_coarse(P, V, V.rr, V.ur, nullptr, st);
         launch_interp_add(P, V, true, V.ur, nullptr, V.z, false, nullptr, st);
     } else if (d.nr) {
         // r_r as float pairs, the pair product writes u_r rounded to float
         float* ur32 = reinterpret_cast<float*>(V.ur);
-        if (!restricted) launch_restrict(P, V, false, V.s, false, V.rr, true, st);
+        if (!restricted && !hyb_direct) launch_restrict(P, V, false, V.s, false, V.rr, true, st);
         launch_xxt_pass1(P, V, true, V.rr, st);    // XX^T meshes only
         launch_coarse_pair(P, V, reinterpret_cast<const float2*>(V.rr), nullptr, ur32, st);
         launch_interp_add(P, V, false, nullptr, ur32, V.z, false, nullptr, st);

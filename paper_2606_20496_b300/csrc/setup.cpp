@@ -390,8 +390,13 @@ cgs_status host_setup(const double* xyz, int64_t nv, const int32_t* conn, int64_
     }
     std::vector<std::vector<int32_t>> sub_sets(n_sub);
     std::vector<std::vector<double>> sub_inv(n_sub);
-    // the mixed forms solve subdomains of at most kLaneMaxM dofs one per lane
-    const bool lane_packs = prm.prec != CGS_FP64;
+    std::vector<std::vector<double>> sub_ap(prm.local_cg_steps > 0 ? n_sub : 0);   // A_p, cyclic diagonals
+    // subdomains of at most kLaneMaxM dofs are solved one per lane: always in
+    // the mixed forms, and in the FP64 form when there are enough of them to
+    // fill the GPU one lane each (otherwise a warp per subdomain)
+    // (inexact local solves run CG on A_p itself, one warp per subdomain)
+    const bool inexact = prm.local_cg_steps > 0;
+    const bool lane_packs = !inexact && (prm.prec != CGS_FP64 || n_sub >= kRowPackMaxSubs);
     bool not_spd = false, too_big = false;
 #pragma omp parallel
     {
@@ -453,6 +458,14 @@ cgs_status host_setup(const double* xyz, int64_t nv, const int32_t* conn, int64_
                 }
             }
             for (int i = 0; i < m; ++i) vpos[R[i]] = -1;
+            if (prm.local_cg_steps > 0) {
+                // A_p itself for the inexact solves: cyclic diagonals, as the inverse
+                const int nd = m / 2 + 1;
+                std::vector<double>& ap = sub_ap[p];
+                ap.resize((size_t)nd * m);
+                for (int d = 0; d < nd; ++d)
+                    for (int i = 0; i < m; ++i) ap[(size_t)d * m + i] = Ap[(size_t)i * m + (i + d) % m];
+            }
             std::vector<double> full((size_t)m * m);
             if (!spd_inverse(Ap.data(), m, full.data(), 1)) {
 #pragma omp atomic write
@@ -483,6 +496,39 @@ cgs_status host_setup(const double* xyz, int64_t nv, const int32_t* conn, int64_
         err = "a local matrix A_p is not SPD";
         return CGS_ERR_NOT_SPD;
     }
+    // RAS prolongation weights (Sec. 3, R~_p): an entry of R_p keeps its value
+    // only if the vertex lies on an element of the original (not grown)
+    // Omega_p, divided by the number of original subdomains holding the
+    // vertex (continuity of the nodes several subdomains store)
+    std::vector<std::vector<double>> sub_ras(n_sub);
+    {
+        auto part_of = [&](int64_t e) -> int32_t { return elem_part ? elem_part[e] : 0; };
+        std::vector<int32_t> own_mult(nv, 0);
+#pragma omp parallel for schedule(static)
+        for (int64_t v = 0; v < nv; ++v) {
+            int32_t seen[64];
+            int ns = 0;
+            for (int64_t t = v2e_ptr[v]; t < v2e_ptr[v + 1]; ++t) {
+                const int32_t q = part_of(v2e[t]);
+                bool dup = false;
+                for (int i = 0; i < ns; ++i) dup = dup || seen[i] == q;
+                if (!dup && ns < 64) seen[ns++] = q;
+            }
+            own_mult[v] = ns;
+        }
+#pragma omp parallel for schedule(dynamic, 64)
+        for (int64_t p = 0; p < n_sub; ++p) {
+            const std::vector<int32_t>& R = sub_sets[p];
+            std::vector<double>& w = sub_ras[p];
+            w.assign(R.size(), 0.0);
+            for (size_t k = 0; k < R.size(); ++k) {
+                const int32_t v = R[k];
+                bool own = false;
+                for (int64_t t = v2e_ptr[v]; t < v2e_ptr[v + 1] && !own; ++t) own = part_of(v2e[t]) == (int32_t)p;
+                w[k] = own && own_mult[v] > 0 ? 1.0 / own_mult[v] : 0.0;
+            }
+        }
+    }
     S.sub_ptr.assign(n_sub + 1, 0);
     S.max_m = 0;
     for (int64_t p = 0; p < n_sub; ++p) {
@@ -503,6 +549,12 @@ cgs_status host_setup(const double* xyz, int64_t nv, const int32_t* conn, int64_
         for (int32_t v : sub_sets[p]) mult[v]++;
     }
     for (int64_t v = 0; v < nv; ++v) S.wov[v] = mult[v] ? 1.0 / mult[v] : 0.0;
+    S.ras_w.resize(S.sum_m);
+    for (int64_t p = 0; p < n_sub; ++p) std::copy(sub_ras[p].begin(), sub_ras[p].end(), S.ras_w.begin() + S.sub_ptr[p]);
+    if (prm.local_cg_steps > 0 && S.max_m > 64) {
+        err = "inexact local solves (local_cg_steps > 0) need subdomains of at most 64 dofs";
+        return CGS_ERR_INVALID_ARG;
+    }
     auto in_lane = [&](int64_t p) {
         const size_t m = sub_sets[p].size();
         return lane_packs && m > 0 && m <= (size_t)kLaneMaxM;
@@ -521,11 +573,15 @@ cgs_status host_setup(const double* xyz, int64_t nv, const int32_t* conn, int64_
     }
     S.n_wsub = (int64_t)S.wsub_ptr.size() - 1;
     S.wsub_idx.resize(S.wsub_ptr.back());
+    S.wsub_ras.resize(S.wsub_ptr.back());
     S.inv.assign(S.inv_ptr.back(), 0.0);
+    S.ap.assign(prm.local_cg_steps > 0 ? S.inv_ptr.back() : 0, 0.0);
     for (int64_t p = 0, w = 0; p < n_sub; ++p) {
         if (in_lane(p)) continue;
         std::copy(sub_sets[p].begin(), sub_sets[p].end(), S.wsub_idx.begin() + S.wsub_ptr[w]);
+        std::copy(sub_ras[p].begin(), sub_ras[p].end(), S.wsub_ras.begin() + S.wsub_ptr[w]);
         std::copy(sub_inv[p].begin(), sub_inv[p].end(), S.inv.begin() + S.inv_ptr[w]);
+        if (prm.local_cg_steps > 0) std::copy(sub_ap[p].begin(), sub_ap[p].end(), S.ap.begin() + S.inv_ptr[w]);
         ++w;
     }
     // lane packs: per size class (ascending), 32 subdomains in caller order
@@ -543,12 +599,16 @@ cgs_status host_setup(const double* xyz, int64_t nv, const int32_t* conn, int64_
             const int64_t io = S.pack_idx_off[S.pack_idx_off.size() - 2];
             const int64_t ao = S.pack_inv_off[S.pack_inv_off.size() - 2];
             S.pack_idx.resize(S.pack_idx_off.back(), -1);
+            S.pack_ras.resize(S.pack_idx_off.back(), 0.0);
             S.pack_inv.resize(S.pack_inv_off.back(), 0.0);
             for (int l = 0; l < 32 && b + l < members.size(); ++l) {
                 const int64_t p = members[b + l];
                 const std::vector<int32_t>& R = sub_sets[p];
                 const int m = (int)R.size();
-                for (int k = 0; k < m; ++k) S.pack_idx[io + (int64_t)k * 32 + l] = R[k];
+                for (int k = 0; k < m; ++k) {
+                    S.pack_idx[io + (int64_t)k * 32 + l] = R[k];
+                    S.pack_ras[io + (int64_t)k * 32 + l] = sub_ras[p][k];
+                }
                 // the m x m triangle inside the c x c one (zero padding)
                 const std::vector<double>& tri = sub_inv[p];
                 size_t src = 0;
@@ -568,7 +628,7 @@ cgs_status host_setup(const double* xyz, int64_t nv, const int32_t* conn, int64_
     S.rpack_inv.clear();
     int64_t n_lane_subs = 0;
     for (int64_t p = 0; p < n_sub; ++p) n_lane_subs += in_lane(p) ? 1 : 0;
-    if (lane_packs && n_lane_subs > 0 && n_lane_subs < kRowPackMaxSubs) {
+    if (prm.prec != CGS_FP64 && n_lane_subs > 0 && n_lane_subs < kRowPackMaxSubs) {
         for (int c : kLaneClasses) {
             std::vector<int64_t> members;
             for (int64_t p = 0; p < n_sub; ++p)
@@ -581,6 +641,7 @@ cgs_status host_setup(const double* xyz, int64_t nv, const int32_t* conn, int64_
                 const int64_t io = S.rpack_idx_off[S.rpack_idx_off.size() - 2];
                 const int64_t ao = S.rpack_inv_off[S.rpack_inv_off.size() - 2];
                 S.rpack_idx.resize(S.rpack_idx_off.back(), -1);
+                S.rpack_ras.resize(S.rpack_idx_off.back(), 0.0);
                 S.rpack_inv.resize(S.rpack_inv_off.back(), 0.0);
                 for (int sidx = 0; sidx < per && b + sidx < members.size(); ++sidx) {
                     const int64_t p = members[b + sidx];
@@ -593,7 +654,10 @@ cgs_status host_setup(const double* xyz, int64_t nv, const int32_t* conn, int64_
                     };
                     for (int g = 0; g < kRowLanes; ++g) {
                         const int l = sidx * kRowLanes + g;
-                        for (int k = 0; k < m; ++k) S.rpack_idx[io + (int64_t)k * 32 + l] = Rp[k];
+                        for (int k = 0; k < m; ++k) {
+                            S.rpack_idx[io + (int64_t)k * 32 + l] = Rp[k];
+                            S.rpack_ras[io + (int64_t)k * 32 + l] = sub_ras[p][k];
+                        }
                         int64_t e = 0;
                         for (int r = 0; r < R; ++r)
                             for (int j = 0; j < c; ++j, ++e) {
@@ -607,6 +671,8 @@ cgs_status host_setup(const double* xyz, int64_t nv, const int32_t* conn, int64_
     }
     sub_sets.clear();
     sub_inv.clear();
+    sub_ap.clear();
+    sub_ras.clear();
 
     // ---- box grid and centroid cells ----------------------------------------
     double lo[3], hi[3];
@@ -783,6 +849,135 @@ cgs_status host_setup(const double* xyz, int64_t nv, const int32_t* conn, int64_
                 S.re_rng.push_back((int32_t)std::min(b, c + kBoxRange));
             }
             a = b;
+        }
+    }
+
+    // ---- J~ by explicit rows, and the hybrid step's restriction -------------
+    // Row v of J~ = W Q^T J_L: sum over the vertex's (cell, n_c / cnt_v)
+    // entries of the cell's trilinear weights at x_v, duplicate columns
+    // (corners shared by neighbouring cells) merged.
+    {
+        const size_t nvb = S.vb_vert.size();
+        std::vector<std::vector<std::pair<int32_t, double>>> rows(nvb);
+#pragma omp parallel for schedule(static)
+        for (int64_t i = 0; i < (int64_t)nvb; ++i) {
+            const int32_t v = S.vb_vert[i];
+            auto& row = rows[i];
+            for (int32_t e = S.vb_ptr[i]; e < S.vb_ptr[i + 1]; ++e) {
+                const int pc = S.vb_cell[e];
+                const int ci = pc & 1023, cj = (pc >> 10) & 1023, ck = pc >> 20;
+                const int cid = ci + bx * (cj + by * ck);
+                for (int m = 0; m < 8; ++m) {
+                    const int32_t c = S.cell_cols[(int64_t)cid * 8 + m];
+                    if (c < 0) continue;
+                    const double w = S.vb_w[e] * corner_weight(&xyz[(size_t)v * 3], ci, cj, ck, m);
+                    bool found = false;
+                    for (auto& cv : row)
+                        if (cv.first == c) {
+                            cv.second += w;
+                            found = true;
+                            break;
+                        }
+                    if (!found) row.emplace_back(c, w);
+                }
+            }
+            std::sort(row.begin(), row.end());
+        }
+        S.jt_ptr.assign(nvb + 1, 0);
+        for (size_t i = 0; i < nvb; ++i) S.jt_ptr[i + 1] = S.jt_ptr[i] + (int32_t)rows[i].size();
+        S.jt_col.resize(S.jt_ptr[nvb]);
+        S.jt_val.resize(S.jt_ptr[nvb]);
+        for (size_t i = 0; i < nvb; ++i)
+            for (size_t k = 0; k < rows[i].size(); ++k) {
+                S.jt_col[S.jt_ptr[i] + k] = rows[i][k].first;
+                S.jt_val[S.jt_ptr[i] + k] = rows[i][k].second;
+            }
+        // hybrid: r_r = J~^T (r - A l) = J~^T r - (A J~)^T l, so the step
+        // needs J~^T and G = A J~ (A symmetric) but never s = r - A l itself.
+        // Row v of G = sum over the elements e at v of sum_k A^e(v, k) J~_k
+        // (free k); entries kept where J~ or G is nonzero, then sorted by
+        // column (vertex order within a column).
+        S.hr_vert.clear();
+        S.hr_j.clear();
+        S.hr_g.clear();
+        S.hr_rng.clear();
+        if (prm.form == CGS_HYBRID && S.nr > 0) {
+            std::vector<int32_t> row_of(nv, -1);
+            for (size_t i = 0; i < nvb; ++i) row_of[S.vb_vert[i]] = (int32_t)i;
+            struct Ent {
+                int32_t v, c;
+                double j, g;
+            };
+            const int nth = omp_get_max_threads();
+            std::vector<std::vector<Ent>> buf(nth);
+#pragma omp parallel
+            {
+                const int th = omp_get_thread_num();
+                std::vector<double> gacc(S.nr, 0.0), jacc(S.nr, 0.0);
+                std::vector<uint8_t> mark(S.nr, 0);
+                std::vector<int32_t> touched;
+#pragma omp for schedule(static)
+                for (int64_t i = 0; i < (int64_t)nvb; ++i) {
+                    const int32_t v = S.vb_vert[i];
+                    touched.clear();
+                    auto touch = [&](int32_t c) {
+                        if (!mark[c]) {
+                            mark[c] = 1;
+                            touched.push_back(c);
+                        }
+                    };
+                    for (int32_t k = S.jt_ptr[i]; k < S.jt_ptr[i + 1]; ++k) {
+                        touch(S.jt_col[k]);
+                        jacc[S.jt_col[k]] += S.jt_val[k];
+                    }
+                    for (int64_t t = v2e_ptr[v]; t < v2e_ptr[v + 1]; ++t) {
+                        const int64_t e = v2e[t];
+                        int iv = 0;
+                        while (conn[e * 8 + iv] != v) ++iv;
+                        for (int k = 0; k < 8; ++k) {
+                            const int32_t u = conn[e * 8 + k];
+                            const int32_t ru = row_of[u];
+                            if (S.dir[u] || ru < 0) continue;
+                            const double a = Ae[(size_t)e * 64 + iv * 8 + k];
+                            for (int32_t q = S.jt_ptr[ru]; q < S.jt_ptr[ru + 1]; ++q) {
+                                touch(S.jt_col[q]);
+                                gacc[S.jt_col[q]] += a * S.jt_val[q];
+                            }
+                        }
+                    }
+                    std::sort(touched.begin(), touched.end());
+                    for (int32_t c : touched) {
+                        if (jacc[c] != 0.0 || gacc[c] != 0.0) buf[th].push_back({v, c, jacc[c], gacc[c]});
+                        jacc[c] = gacc[c] = 0.0;
+                        mark[c] = 0;
+                    }
+                }
+            }
+            // counting sort by column; the buffers hold increasing vertex
+            // ranges in thread order, so vertex order within a column stays
+            std::vector<int64_t> cptr(S.nr + 1, 0);
+            for (auto& b : buf)
+                for (const Ent& x : b) cptr[x.c + 1]++;
+            for (int64_t c = 0; c < S.nr; ++c) cptr[c + 1] += cptr[c];
+            const int64_t nh = cptr[S.nr];
+            S.hr_vert.resize(nh);
+            S.hr_j.resize(nh);
+            S.hr_g.resize(nh);
+            std::vector<int64_t> fill(cptr.begin(), cptr.end() - 1);
+            for (auto& b : buf)
+                for (const Ent& x : b) {
+                    const int64_t at = fill[x.c]++;
+                    S.hr_vert[at] = x.v;
+                    S.hr_j[at] = x.j;
+                    S.hr_g[at] = x.g;
+                }
+            for (int64_t c = 0; c < S.nr; ++c)
+                for (int64_t a = cptr[c]; a < cptr[c + 1]; a += kBoxRange) {
+                    S.hr_rng.push_back((int32_t)a);
+                    S.hr_rng.push_back((int32_t)std::min<int64_t>(cptr[c + 1], a + kBoxRange));
+                    S.hr_rng.push_back((int32_t)c);
+                    S.hr_rng.push_back(0);
+                }
         }
     }
 

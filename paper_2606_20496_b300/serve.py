@@ -135,7 +135,7 @@ def run_plain(ctx, h64, pool, t_arr, which, rtol, budget_s):
 
 
 def serve(rate=2000.0, seconds=10.0, pool_n=64, slots=256, iters_per_step=4, rtol=1e-8, prec="fp32",
-          plain=True, kmax=64, arena_mb=2048.0):
+          plain=True, kmax=64, arena_mb=2048.0, plain_budget_s=None):
     import torch
 
     from . import build, cgs
@@ -162,7 +162,8 @@ def serve(rate=2000.0, seconds=10.0, pool_n=64, slots=256, iters_per_step=4, rto
         for i in range(len(pool)):   # warm-up (graphs)
             b = torch.ones(pool[i].nv, dtype=torch.float64, device="cuda")
             cgs.cgs_solve(h64[i].handle, b, torch.empty_like(b), rtol=rtol)
-        out["fp64_plain_per_request"] = run_plain(ctx, h64, pool, t_arr, which, rtol, budget_s=3 * seconds)
+        out["fp64_plain_per_request"] = run_plain(ctx, h64, pool, t_arr, which, rtol,
+                                                  budget_s=plain_budget_s or 3 * seconds)
         for h in h64:
             h.free()
     cgs.cgs_destroy(ctx)

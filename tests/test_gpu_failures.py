@@ -64,7 +64,12 @@ def test_tile_wait_expiry_stops_the_solve(ctx, cube32, prec):
 @pytest.mark.parametrize("call", ["preconditioner", "noalloc", "inner", "outer"])
 def test_tile_wait_expiry_in_single_steps(ctx, cube32, call):
     m, b, P = cube32
-    with cgs.Mesh(ctx, m.xyz, m.conn, part=m.part, boxes=m.boxes, prec="fp32") as h:
+    # set up additive, then switched to hybrid: the hybrid step then forms
+    # s = r - A l with the (TMA-staged) inner apply, whose tile wait the
+    # limit of 0 makes expire (a hybrid set-up restricts r and l directly,
+    # with no wait in the preconditioner)
+    with cgs.Mesh(ctx, m.xyz, m.conn, part=m.part, boxes=m.boxes, prec="fp32", form="additive") as h:
+        cgs.cgs_mesh_set_form(h.handle, "hybrid")
         cgs.cgs_mesh_set_schedule(h.handle, tile_tma=1)
         r = dev(np.random.default_rng(3).standard_normal(m.nv))
         z = torch.empty_like(r)

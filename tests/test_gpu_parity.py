@@ -402,3 +402,49 @@ def test_full_cylinder_sampled(ctx):
         xg = np.where(dirm, 0.0, host(x))
         res = bb - np.where(dirm, 0.0, A @ xg)
         assert np.linalg.norm(res) / np.linalg.norm(bb) <= 1.5e-8
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_full_cylinder_against_stored_oracle_results(ctx, prec):
+    """The full-size cylinder in the launch configuration the benchmark times,
+    against FP64 oracle results stored by tests/golden/make_cylinder_golden.py
+    at 256 sampled free vertices: A b, the weighted local solves, M b (hybrid
+    and additive), and the PCG solve to rtol 1e-8 (the oracle needs 300
+    iterations).  FP64: 1e-12 for A b, 1e-11 for the preconditioner terms
+    (relative to the largest sampled value); FP32 bulk: 1e-5.  Solves: the
+    iteration count within one of the oracle's and the sampled solution within
+    1e-6 relative (both stop at relres 1e-8 along the same iteration)."""
+    import json
+    import os
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "cylinder_oracle.json")))
+    idx = np.array(g["idx"])
+    m, b = meshes.workload_cylinder()
+    dirm = O.dirichlet_mask(m.conn, m.nv)
+    b = np.where(dirm, 0.0, b)
+    tol = 1e-11 if prec == "fp64" else 1e-5
+    with cgs.Mesh(ctx, m.xyz, m.conn, part=m.part, boxes=m.boxes, prec=prec) as h:
+        cgs.cgs_mesh_tune(h.handle)
+        bd = dev(b)
+        out = torch.empty(m.nv, dtype=torch.float64, device="cuda")
+
+        def check(got, key, t):
+            ref = np.array(g[key])
+            assert np.abs(got[idx] - ref).max() <= t * np.abs(ref).max(), key
+
+        cgs.cgs_apply_A(h.handle, bd, out)
+        check(host(out), "apply_A", 1e-12)
+        cgs.cgs_apply_local(h.handle, bd, out, True)
+        check(host(out), "local_w", tol)
+        cgs.cgs_apply_preconditioner(h.handle, bd, out)
+        check(host(out), "m_hybrid", tol)
+        cgs.cgs_mesh_set_form(h.handle, "additive")
+        cgs.cgs_apply_preconditioner(h.handle, bd, out)
+        check(host(out), "m_additive", tol)
+        cgs.cgs_mesh_set_form(h.handle, "hybrid")
+        assert cgs.cgs_mesh_step_status(h.handle) == cgs.OK
+        st, its, rel = cgs.cgs_solve(h.handle, bd, out, rtol=1e-8, maxit=1000)
+        assert st == cgs.OK and rel[0] <= 1.5e-8
+        assert abs(int(its[0]) - g["solve"]["iters"]) <= 1
+        xs, xo = host(out)[idx], np.array(g["solve"]["x"])
+        assert np.linalg.norm(xs - xo) <= 1e-6 * np.linalg.norm(xo)

@@ -104,6 +104,8 @@ def test_admission_by_footprint(ctx):
     small = meshes.cube(5, perturb=0.1, seed=6)
     h = cgs.Mesh(ctx, m.xyz, m.conn, part=m.part, boxes=m.boxes, prec="fp32")
     hsm = cgs.Mesh(ctx, small.xyz, small.conn, part=small.part, boxes=small.boxes, prec="fp32")
+    oracle_of = {id(h): O.Problem(m.xyz, m.conn, m.part, m.boxes),
+                 id(hsm): O.Problem(small.xyz, small.conn, small.part, small.boxes)}
     pool_nv = 2 * ((m.nv + 31) // 32 * 32)
     server = cgs.cgs_server_create(ctx, max_slots=4, pool_nv=pool_nv, pool_nr=2 * h.info["n_r"], prec="fp32",
                                    rtol=1e-10)
@@ -143,7 +145,8 @@ def test_admission_by_footprint(ctx):
             xa, xb = x1.cpu().numpy(), x.cpu().numpy()
             assert np.linalg.norm(xb - xa) / np.linalg.norm(xa) <= 1e-8
             # against the oracle's solve of the same request
-            xo, its_o, _, ok = oracles[mi].solve(b.cpu().numpy(), rtol=rtol)
+            P = oracle_of[id(hh)]
+            xo, its_o, _, ok = P.solve(b.cpu().numpy(), rtol=1e-10)
             assert ok and abs(its_o - its) <= 1
             assert np.linalg.norm(xb - xo) / np.linalg.norm(xo) <= 1e-8
     finally:

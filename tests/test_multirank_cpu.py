@@ -39,11 +39,13 @@ def _rank(rank, world, port, out_dir):
     # reference arm: rank 0 only (the oracle timing replaced by a stub)
     called = []
 
-    def fake_oracle(budget_s=0.0, max_solves=None):
+    def fake_problem():
         called.append(rank)
-        return {"value": 2.0, "unit": bench.UNIT, "cores": 1, "kind": "oracle", "sample": "stub"}
+        return None, None, 0.0
 
-    bench.time_oracle = fake_oracle
+    bench.oracle_iters_per_solve = lambda: 5
+    bench.oracle_problem = fake_problem
+    bench.oracle_step = lambda P, b: 0.1          # 0.1 s per iteration, 5 per solve: 2 solves/s
     buf = io.StringIO()
     with contextlib.redirect_stdout(buf):
         bench.run_reference(types.SimpleNamespace(gpus=world, steps=3, warmup=0))
@@ -61,4 +63,4 @@ def test_two_gloo_ranks_max_time_and_rank0_reference(tmp_path):
     assert r[0]["called"] == [0] and r[1]["called"] == []
     assert r[1]["stdout"] == ""
     line = json.loads(r[0]["stdout"].strip())
-    assert line["impl"] == "reference" and line["value"] == 2.0 and line["n_gpus"] == 2
+    assert line["impl"] == "reference" and line["value"] == pytest.approx(2.0) and line["n_gpus"] == 2
