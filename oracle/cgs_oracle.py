@@ -410,18 +410,20 @@ class Problem:
         return self.interp(self.coarse_solve(self.restrict(r)))
 
     # -- preconditioners -------------------------------------------------------
-    def apply_M(self, r, form: str = "hybrid"):
+    def apply_M(self, r, form: str = "hybrid", inner: int = 0):
+        """M r; inner > 0 replaces every A_p^{-1} by that many CG steps on
+        A_p (the inexact local solves of Sec. 6)."""
         r = np.where(self.dir, 0.0, np.asarray(r, dtype=np.float64))
         if form == "hybrid":                    # Eqs. asm1, asm2
-            l = self.local_solves(r, weighted=True)
+            l = self.local_solves(r, weighted=True, inner=inner)
             s = r - self.apply_A(l)
             return l + self.box_correction(s)
         if form == "additive":                  # Eq. asm
-            return self.local_solves(r, weighted=False) + self.box_correction(r)
+            return self.local_solves(r, weighted=False, inner=inner) + self.box_correction(r)
         if form == "ras":                       # Eq. asm with the restricted R~_p (RAS)
-            return self.local_solves(r, weighted="ras") + self.box_correction(r)
+            return self.local_solves(r, weighted="ras", inner=inner) + self.box_correction(r)
         if form == "local":                     # ASM_1 alone
-            return self.local_solves(r, weighted=True)
+            return self.local_solves(r, weighted=True, inner=inner)
         if form == "box":                       # J A_r^{-1} J^T alone
             return self.box_correction(r)
         if form == "none":
@@ -429,11 +431,11 @@ class Problem:
         raise ValueError(form)
 
     # -- outer iteration -------------------------------------------------------
-    def solve(self, b, rtol: float = 1e-8, maxit: int = 500, form: str = "hybrid"):
+    def solve(self, b, rtol: float = 1e-8, maxit: int = 500, form: str = "hybrid", inner: int = 0):
         """Flexible PCG, x0 = 0, Polak-Ribiere beta; stops when the recursive
         residual satisfies ||r|| <= rtol ||b||.  Returns (x, iters, true relres);
         iters counts the products A p; see fcg for the return tuple."""
-        return fcg(self.apply_A, lambda r: self.apply_M(r, form),
+        return fcg(self.apply_A, lambda r: self.apply_M(r, form, inner),
                    np.where(self.dir, 0.0, np.asarray(b, dtype=np.float64)), rtol, maxit)
 
 

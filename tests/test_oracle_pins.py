@@ -779,6 +779,12 @@ def test_inexact_local_solves():
     full = P.local_solves(r, True, inner=max(P.groups))
     assert np.abs(full - exact).max() <= 1e-9 * np.abs(exact).max()
     assert np.abs(P.local_solves(r, True, inner=2) - exact).max() > 1e-3 * np.abs(exact).max()
+    # the same inner steps inside every form of M (Sec. 6): m_p steps give the
+    # exact preconditioner
+    k = max(P.groups)
+    for form in ("hybrid", "additive", "ras"):
+        ex = P.apply_M(r, form)
+        assert np.abs(P.apply_M(r, form, inner=k) - ex).max() <= 1e-9 * np.abs(ex).max()
 
 
 def test_schwarz_richardson_converges_at_the_spectral_radius():
