@@ -1,12 +1,18 @@
 #!/usr/bin/env python
 """Coarse-solve throughput of the two-level Schwarz PCG solver on one B300.
 
-Workload: the 32^3 smoothly deformed unit cube with randomly renumbered
-elements (35,937 vertices, 4,096 overlapping 2^3-element subdomains, 8^3 box
-coarse space), hybrid Schwarz (ASM_1 + ASM_2) inside flexible PCG to a
-relative residual of 1e-8.  One step = one complete coarse solve of one
-N(0,1) right-hand side.  The headline form is FP32 bulk / FP64 outer; the FP64
-plain form runs beside it for the iteration-count comparison.
+Headline workload: the hollow cylinder of 64 x 128 x 128 trilinear hexes
+(1,073,280 vertices; radial grading 1.05, inner-wall aspect ratio 1:100;
+131,072 overlapping 2^3-element subdomains; a 16^3 box coarse space with
+3,876 active vertices), hybrid Schwarz (ASM_1 + ASM_2) inside flexible PCG to
+a relative residual of 1e-8, in the plain FP64 form (every step in float64,
+the precision of the paper's Schwarz solves).  One step = one complete coarse
+solve of one N(0,1) right-hand side.  Beside it, on the same mesh: the FP32
+bulk and FP16 local forms (rate, iterations, difference from the FP64
+solution); the batched form (256 perturbed cubes x 4 right-hand sides in one
+graph) against the FP64 per-request path; and the serving form (a 10 s
+Poisson stream at 2,000 req/s over a 64-mesh pool) against the FP64
+per-request path.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -33,20 +39,26 @@ sys.path.insert(0, ROOT)
 METRIC = "coarse-solve apps/s & PCG iters to 1e-8 vs FP64 plain; p50/p99 serve latency"
 UNIT = "solves/s"
 RTOL = 1e-8
-L2_FLUSH_BYTES = 256 << 20
+# FP64 FMA issue rate of B300: 2 per clock per SM (148 SMs, 2032 MHz maximum
+# SM clock) -> 1.203 TFLOP/s; this repository's dependent-FMA probe measured
+# 1.10 TFLOP/s, the nominal figure is 1.25
+FP64_PEAK_TFLOPS = 2 * 2 * 148 * 2.032e9 / 1e12
+WORKLOAD = ("hollow_cylinder_1M: 64 x 128 x 128 trilinear hexes (1,073,280 vertices), radial grading 1.05, "
+            "inner-wall aspect 1:100, 131,072 2^3-element subdomains grown by one layer, 16^3 boxes "
+            "(3,876 active vertices, XX^T reduced solve); hybrid Schwarz (ASM_1+ASM_2) in flexible PCG to "
+            "rtol 1e-8, one N(0,1) RHS (seed 6) per step")
 
 
 def workload():
     from paper_2606_20496_b300 import meshes
-    return meshes.workload_cube32()
+    return meshes.workload_cylinder()
 
 
 def config_block(extra=None):
-    c = {"workload": "cube32_deformed_permuted: 32^3 trilinear hexes, 35,937 vertices, elements renumbered "
-                     "by a seeded permutation, 4,096 2^3-element subdomains grown by one layer, 8^3 boxes; "
-                     "hybrid Schwarz (ASM_1+ASM_2) in flexible PCG to rtol 1e-8, one N(0,1) RHS per step",
-         "form": "hybrid", "precision": "fp32 bulk (local solves, inner A, J, J^T), fp64 outer PCG and A_r^-1",
-         "rtol": RTOL, "l2": "flushed between steps (256 MB device write outside the timed events)"}
+    c = {"workload": WORKLOAD, "form": "hybrid",
+         "precision": "fp64 plain: every step in float64 (local solves, operator applies, J, J^T, XX^T, "
+                      "PCG vectors and dots)",
+         "rtol": RTOL, "l2": "inputs larger than L2: the mesh's resident data is 885 MB (126 MB L2), no flush"}
     if extra:
         c.update(extra)
     return c
@@ -108,7 +120,7 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------
-# algorithmic bytes per launch of each kernel class (HBM roofline)
+# algorithmic bytes and flops per launch of each kernel class
 # ---------------------------------------------------------------------------
 
 def algorithmic_bytes(info, prec, interp_cells=False):
@@ -124,7 +136,7 @@ def algorithmic_bytes(info, prec, interp_cells=False):
     nb = info["n_box_entries"]
     sb = 8 if prec == "fp64" else 4
     sl = {"fp64": 8, "fp32": 4, "fp16": 2}[prec]
-    packed = info["_packed_entries"]
+    packed = info["sum_sub_tri"]
     # reduced solve per launch: the dense inverse once, or one XX^T pass (X's
     # 8-byte values and 2-byte indices once, r_r or t gathered, t or u_r out)
     xnnz = info.get("xxt_nnz", 0)
@@ -164,6 +176,16 @@ def algorithmic_bytes(info, prec, interp_cells=False):
     }
 
 
+def algorithmic_flops(info, prec):
+    """Float64 flops per launch of the FP64-form kernels that the FP64 pipe
+    bounds (an FMA counts 2): the element matrix-vector product (64 FMAs per
+    element) and the local solves (m_p^2 FMAs per subdomain)."""
+    if prec != "fp64":
+        return {}
+    sum_m2 = 2 * info["sum_sub_tri"] - info["sum_sub_dofs"]
+    return {"apply_A64": 2 * 64 * info["ne"], "local": 2 * sum_m2}
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -172,59 +194,127 @@ def measured_peaks():
     return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0}, "fallback"
 
 
-def traffic_for(kernel_class):
+def traffic_for(kernel_class, workload_key):
     """dram read+write bytes per launch from a committed ncu summary, if one
-    exists for the current kernel source (kernels.cu; else None)."""
+    exists for this kernel class and workload, taken with the current kernel
+    source (else None)."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
     try:
         d = json.load(open(p))
-        ent = d.get("kernels", {}).get(kernel_class)
+        ent = d.get(workload_key, {}).get(kernel_class)
         if not ent:
             return None
         import hashlib
         h = hashlib.sha256(open(os.path.join(ROOT, "paper_2606_20496_b300", "csrc", "kernels.cu"), "rb").read())
-        h = h.hexdigest()[:16]
-        return ent["bytes_per_launch"] if ent.get("source_hash") == h else None
+        return ent["bytes_per_launch"] if ent.get("source_hash") == h.hexdigest()[:16] else None
     except Exception:
         return None
+
+
+def roofline_of(prof, info, prec, interp_cells, peaks, peak_kind, workload_key):
+    """Per-kernel achieved rates from the event profile, and the roofline
+    object of the dominant (most time) kernel: HBM-bound unless its FP64-ALU
+    fraction is the larger."""
+    algo = algorithmic_bytes(info, prec, interp_cells)
+    flops = algorithmic_flops(info, prec)
+    total = sum(t for t, n in prof.values()) or 1.0
+    per = {}
+    for k, (t, n) in prof.items():
+        if not n:
+            continue
+        us = 1e3 * t / n
+        e = {"share": round(t / total, 4), "launches": n, "avg_us": round(us, 2)}
+        if k in algo:
+            gbs = algo[k] / (us * 1e-6) / 1e9
+            e.update(achieved_gbs=round(gbs, 1), hbm_frac=round(gbs / peaks["hbm_gbs"], 3))
+        if k in flops:
+            tf = flops[k] / (us * 1e-6) / 1e12
+            e.update(achieved_fp64_tflops=round(tf, 3), fp64_frac=round(tf / FP64_PEAK_TFLOPS, 3))
+        per[k] = e
+    dom = max((k for k in per if k in algo), key=lambda k: per[k]["share"])
+    d = per[dom]
+    if d.get("fp64_frac", 0.0) > d["hbm_frac"]:
+        roof = {"bound": "alu", "kernel": dom, "achieved": d["achieved_fp64_tflops"], "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": d["fp64_frac"], "traffic": traffic_for(dom, workload_key),
+                "peak_source": "derived: 2 FP64 FMA per clock per SM x 148 SMs x 2032 MHz (probe measured 1.10)",
+                "algorithmic_flops_per_launch": flops[dom], "algorithmic_bytes_per_launch": algo[dom],
+                "hbm_frac": d["hbm_frac"], "avg_launch_us": d["avg_us"]}
+    else:
+        roof = {"bound": "hbm", "kernel": dom, "achieved": d["achieved_gbs"], "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "frac": d["hbm_frac"], "traffic": traffic_for(dom, workload_key),
+                "peak_source": f"{peak_kind} hbm_gbs", "algorithmic_bytes_per_launch": algo[dom],
+                "avg_launch_us": d["avg_us"]}
+    return roof, per
 
 
 # ---------------------------------------------------------------------------
 # the CPU oracle (reference arm and cpu_baseline)
 # ---------------------------------------------------------------------------
 
-def time_oracle(budget_s=15.0, max_solves=None):
-    """Time complete oracle solves in a fresh single-threaded interpreter
-    (BLAS/OpenMP pools pinned to one thread through the environment)."""
+def _oracle_env():
     env = dict(os.environ)
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
         env[k] = "1"
     env["CUDA_VISIBLE_DEVICES"] = ""
-    cmd = [sys.executable, os.path.abspath(__file__), "--oracle-sample", str(budget_s), str(max_solves or 0)]
-    res = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=budget_s * 4 + 300)
-    if res.returncode:
-        return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": "failed: " + res.stderr[-300:]}
-    return json.loads(res.stdout.strip().splitlines()[-1])
+    return env
 
 
-def oracle_sample(budget_s, max_solves):
+def oracle_iters_per_solve():
+    """The oracle's own iteration count for this workload (hybrid, rtol 1e-8),
+    stored by tests/golden/make_cylinder_golden.py from an oracle solve."""
+    p = os.path.join(ROOT, "tests", "golden", "cylinder_oracle.json")
+    return int(json.load(open(p))["solve"]["iters"])
+
+
+def start_oracle_sample(iters):
+    """Start the cpu_baseline sample in a fresh single-threaded interpreter
+    (it runs on the host cores while the GPU work proceeds)."""
+    cmd = [sys.executable, os.path.abspath(__file__), "--oracle-sample", str(iters)]
+    return subprocess.Popen(cmd, env=_oracle_env(), stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True)
+
+
+def finish_oracle_sample(proc, timeout=900):
+    try:
+        out, err = proc.communicate(timeout=timeout)
+    except subprocess.TimeoutExpired:
+        proc.kill()
+        return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": "timed out"}
+    if proc.returncode:
+        return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": "failed: " + err[-300:]}
+    return json.loads(out.strip().splitlines()[-1])
+
+
+def oracle_problem():
     from oracle import cgs_oracle as O
     m, b = workload()
+    t0 = time.perf_counter()
     P = O.Problem(m.xyz, m.conn, m.part, m.boxes)
-    times, iters = [], []
-    t_all = time.perf_counter()
-    while True:
-        t0 = time.perf_counter()
-        x, its, rel, ok = P.solve(b, rtol=RTOL)
-        times.append(time.perf_counter() - t0)
-        iters.append(its)
-        if time.perf_counter() - t_all >= budget_s or (max_solves and len(times) >= max_solves):
-            break
-    print(json.dumps({"value": len(times) / sum(times), "unit": UNIT, "cores": 1, "kind": "oracle",
-                      "sample": f"{len(times)} complete FP64 oracle solves of the same workload (numpy/scipy, "
-                                f"one thread, setup excluded), {sum(times):.1f} s; iters {iters[0]}"}))
+    return P, b, time.perf_counter() - t0
+
+
+def oracle_step(P, b):
+    """One preconditioned flexible-PCG iteration of the oracle (its solve
+    with maxit = 1: z = M r, q = A p, the x, r update, and the true-residual
+    product at the end); returns seconds."""
+    t0 = time.perf_counter()
+    P.solve(b, rtol=RTOL, maxit=1)
+    return time.perf_counter() - t0
+
+
+def oracle_sample(iters):
+    """cpu_baseline: the oracle on the full cylinder, a bounded sample of 6
+    iterations (about 20 s on one core; set-up excluded), scaled to solves/s
+    by the oracle's own iteration count per solve."""
+    P, b, setup_s = oracle_problem()
+    ts = [oracle_step(P, b) for _ in range(6)]
+    t = float(np.median(ts))
+    print(json.dumps({"value": 1.0 / (t * iters), "unit": UNIT, "cores": 1, "kind": "oracle",
+                      "sample": f"{len(ts)} preconditioned PCG iterations of the FP64 oracle (numpy/scipy, one "
+                                f"thread) on the same cylinder, median {t:.2f} s each, scaled by the oracle's "
+                                f"{iters} iterations per solve (tests/golden/cylinder_oracle.json); oracle "
+                                f"set-up {setup_s:.0f} s excluded"}))
 
 
 def max_over_ranks(dist, value: float, device: str) -> float:
@@ -244,17 +334,29 @@ def whole_job_rate(world: int, units_per_rank: int, ms_max: float) -> float:
 
 
 def run_reference(args):
+    """The oracle, as it stands, on the host cores: set-up untimed, then W + K
+    steps of one preconditioned PCG iteration each; value = solves/s, the
+    mean step time scaled by the oracle's iterations per solve."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    sample = time_oracle(budget_s=90.0, max_solves=max(1, args.steps))
-    line = {"impl": "reference", "metric": METRIC, "value": sample["value"], "unit": UNIT,
+    iters = oracle_iters_per_solve()
+    P, b, setup_s = oracle_problem()
+    for _ in range(args.warmup):
+        oracle_step(P, b)
+    ts = [oracle_step(P, b) for _ in range(args.steps)]
+    t = float(np.mean(ts))
+    value = 1.0 / (t * iters)
+    sample = (f"{args.steps} timed steps (after {args.warmup} warm-up) of one preconditioned PCG iteration of the "
+              f"FP64 oracle (numpy/scipy, one thread), mean {t:.2f} s, scaled by its {iters} iterations per solve; "
+              f"set-up {setup_s:.0f} s excluded")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1000.0 / sample["value"], "higher_is_better": True, "scaling": "weak",
+            "ms_per_step": 1000.0 / value, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": config_block({"precision": "fp64 (CPU oracle)"}),
-            "cpu_baseline": sample,
-            "e2e": {"value": sample["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
 
@@ -262,41 +364,19 @@ def run_reference(args):
 # our arm
 # ---------------------------------------------------------------------------
 
-def serve_probe(ctx, args):
-    """Continuous-batching server on a Poisson stream (this rank's replica):
-    pool meshes drawn like the serving workload (cubes and cylinders with
-    k^3 elements, k log-uniform in [8, 64], seed 3), FP32 bulk to 1e-8,
-    latency from arrival to completion on the wall clock."""
-    from paper_2606_20496_b300 import cgs, serve
-    import torch
-    pool = serve.make_pool(args.serve_pool)
-    hs = [cgs.Mesh(ctx, mm.xyz, mm.conn, part=mm.part, boxes=mm.boxes, prec="fp32") for mm in pool]
-    try:
-        # warm-up: every pool mesh once
-        serve.run_server(ctx, hs, pool, np.zeros(len(pool)), np.arange(len(pool)), min(256, len(pool)), 8,
-                         RTOL, "fp32", 2048.0)
-        torch.cuda.synchronize()
-        t_arr, which = serve.arrivals(args.serve_rate, args.serve_seconds, len(pool))
-        r = serve.run_server(ctx, hs, pool, t_arr, which, 256, 8, RTOL, "fp32", 2048.0)
-    finally:
-        for h in hs:
-            h.free()
-    return {"p50": r["p50_ms"], "p99": r["p99_ms"], "solves_per_s": r["solves_per_s"],
-            "offered_req_per_s": args.serve_rate, "requests": int(t_arr.size), "seconds": args.serve_seconds,
-            "workload": f"Poisson stream over {len(pool)} cube/cylinder meshes, k^3 elements, k log-uniform in "
-                        "[8, 64] (seed 3), one N(0,1) RHS per request, rtol 1e-8, FP32 bulk",
-            "server": {"slots": 256, "iters_per_step": 8, "arena_mb": 2048, "mean_active": r["mean_active_after_step"]}}
-
-
 def run_ours(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    # the CPU baseline runs on the host cores while the GPU work proceeds
+    # (started before the first CUDA call)
+    cpu_proc = start_oracle_sample(oracle_iters_per_solve()) if (rank == 0 and world == 1 and
+                                                                  args.cpu_baseline) else None
     import torch
 
     from paper_2606_20496_b300 import build as B
     from paper_2606_20496_b300 import cgs
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     dist = None
     if world > 1:
@@ -305,140 +385,137 @@ def run_ours(args):
     B.build()
     m, b = workload()
     ctx = cgs.cgs_create(local)
-    h32 = cgs.Mesh(ctx, m.xyz, m.conn, part=m.part, boxes=m.boxes, prec="fp32")
-    h64 = cgs.Mesh(ctx, m.xyz, m.conn, part=m.part, boxes=m.boxes, prec="fp64")
-    # the library's autotuner picks the block sizes on this mesh (untimed setup)
-    cgs.cgs_mesh_tune(h32.handle)
-    cgs.cgs_mesh_tune(h64.handle)
-    sched = cgs.cgs_mesh_get_schedule(h32.handle)
-    sched64 = cgs.cgs_mesh_get_schedule(h64.handle)
-    bd = torch.as_tensor(b, dtype=torch.float64, device="cuda")
-    x = torch.empty_like(bd)
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
+    bd = torch.as_tensor(b, dtype=torch.float64, device="cuda")
+    peaks, peak_kind = measured_peaks()
 
-    def timed(h, steps, warmup):
+    def timed(h, steps, warmup, clocks=False):
+        x = torch.empty_like(bd)
         for _ in range(warmup):
             cgs.cgs_solve(h.handle, bd, x, rtol=RTOL)
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
         its = []
-        n0 = cgs.cgs_mesh_info(h.handle)["kernel_launches"]
         torch.cuda.synchronize()
         if dist:
             dist.barrier()
-        wall0 = time.perf_counter()
+        sampler = ClockSampler(local) if clocks else None
+        if sampler:
+            sampler.__enter__()
         for s in range(steps):
-            flush.zero_()
             ev[s][0].record(stream)
             st, it, rel = cgs.cgs_solve(h.handle, bd, x, rtol=RTOL)
             ev[s][1].record(stream)
             its.append(int(it[0]))
             assert st == cgs.OK and rel[0] <= 1.5 * RTOL, (st, rel)
         torch.cuda.synchronize()
-        wall = time.perf_counter() - wall0
-        launches = cgs.cgs_mesh_info(h.handle)["kernel_launches"] - n0
+        if sampler:
+            sampler.__exit__(None, None, None)
         ms = max_over_ranks(dist, sum(a.elapsed_time(c) for a, c in ev), "cuda")
         if dist:
             dist.barrier()
-        return ms, its, launches, wall
+        return ms, its, x, (sampler.summary() if sampler else None)
 
-    with ClockSampler(local) as clk:
-        ms32, its32, launches32, wall32 = timed(h32, args.steps, args.warmup)
-    clocks = clk.summary()
-    ms64, its64, _, _ = timed(h64, args.steps, args.warmup)
-
-    # per-kernel event timing (separate pass, same workload and launches)
     def profile(h, n):
+        """Per-kernel-class CUDA-event times over n solves (host-driven loop,
+        events on the launching stream); also the kernels one solve launches."""
+        x = torch.empty_like(bd)
         cgs.cgs_profile_enable(h.handle, True)
         for _ in range(n):
-            flush.zero_()
             cgs.cgs_solve(h.handle, bd, x, rtol=RTOL)
         prof = cgs.cgs_profile_read(h.handle)
         cgs.cgs_profile_enable(h.handle, False)
-        return prof
+        return prof, sum(nl for _, nl in prof.values()) / n
 
-    nprof = min(args.steps, 50)
-    prof = profile(h32, nprof)
-    info = dict(h32.info)
-    info.update(cgs.cgs_mesh_info(h32.handle))
-    info["_packed_entries"] = info["sum_sub_tri"]
-    algo = algorithmic_bytes(info, "fp32", interp_cells=bool(sched.get("interp_cells")))
-    iters32 = int(np.median(its32))
-    # the persistent loop runs every phase of every iteration in one launch
-    # (interpolating by vertex)
-    per_iter = ["apply_A64", "pcg_xr", "local", "apply_A32", "restrict", "coarse", "interp"]
-    by_vertex = algorithmic_bytes(info, "fp32")
-    algo["loop"] = iters32 * sum(by_vertex[k] for k in per_iter)
-    total_ms = sum(t for t, n in prof.values())
-    dom = max((k for k in prof if k in algo and prof[k][1]), key=lambda k: prof[k][0])
-    dom_ms = prof[dom][0] / prof[dom][1]
-    achieved = algo[dom] / (dom_ms * 1e-3) / 1e9
-    peaks, peak_kind = measured_peaks()
-    traffic = traffic_for(dom)
-    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
-                "peak_source": f"{peak_kind} hbm_gbs", "algorithmic_bytes_per_launch": algo[dom],
-                "avg_launch_us": dom_ms * 1e3}
-    if dom == "loop":
-        roofline["note"] = (f"persistent loop: {iters32} iterations per launch, algorithmic bytes = iterations x "
-                            "(q = A p, x/r/p update, local solves, s -= A l, restriction, reduced solve, "
-                            "interpolation with the dots)")
-    shares = {k: {"share": round(t / total_ms, 4), "launches": n, "avg_us": round(1e3 * t / n, 2)}
-              for k, (t, n) in prof.items() if n}
-    # the same solves one launch per phase (per-phase attribution)
-    p0 = cgs.cgs_mesh_get_schedule(h32.handle)["persistent"]
-    cgs.cgs_mesh_set_schedule(h32.handle, persistent=0)
-    prof_s = profile(h32, nprof)
-    cgs.cgs_mesh_set_schedule(h32.handle, persistent=p0)
-    total_s = sum(t for t, n in prof_s.values())
-    shares_stepwise = {k: {"share": round(t / total_s, 4), "launches": n, "avg_us": round(1e3 * t / n, 2),
-                           "achieved_gbs": round(algo[k] / (t / n * 1e-3) / 1e9, 1) if k in algo else None}
-                       for k, (t, n) in prof_s.items() if n}
+    # ---- headline: FP64 plain form ------------------------------------------------
+    h64 = cgs.Mesh(ctx, m.xyz, m.conn, part=m.part, boxes=m.boxes, prec="fp64")
+    cgs.cgs_mesh_tune(h64.handle)
+    sched64 = cgs.cgs_mesh_get_schedule(h64.handle)
+    ms64, its64, x64, clocks = timed(h64, args.steps, args.warmup, clocks=True)
+    x64 = x64.clone()
+    prof64, launches_per_solve = profile(h64, 2)
+    info64 = dict(h64.info)
+    info64.update(cgs.cgs_mesh_info(h64.handle))
+    roofline, kernels64 = roofline_of(prof64, info64, "fp64", bool(sched64["interp_cells"]), peaks, peak_kind,
+                                      "hollow_cylinder_1M_fp64")
 
-    # end to end through the host-buffer entry point
+    # end to end through the host-buffer entry point (H2D of b and D2H of x in
+    # the timed region)
     bh = torch.empty(m.nv, dtype=torch.float64, pin_memory=True)
     bh.copy_(torch.as_tensor(b))
     xh = torch.empty(m.nv, dtype=torch.float64, pin_memory=True)
-    for _ in range(args.warmup):
-        cgs.cgs_solve_host(h32.handle, bh, xh, rtol=RTOL)
+    for _ in range(2):
+        cgs.cgs_solve_host(h64.handle, bh, xh, rtol=RTOL)
     torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
     e2e_ms = 0.0
-    for _ in range(args.steps):
-        flush.zero_()
-        torch.cuda.synchronize()
+    e2e_steps = max(3, args.steps // 2)
+    for _ in range(e2e_steps):
         t0 = time.perf_counter()
-        st, it, rel = cgs.cgs_solve_host(h32.handle, bh, xh, rtol=RTOL)
+        st, it, rel = cgs.cgs_solve_host(h64.handle, bh, xh, rtol=RTOL)
         e2e_ms += (time.perf_counter() - t0) * 1e3
         assert st == cgs.OK
     e2e_ms = max_over_ranks(dist, e2e_ms, "cuda")
-
-    serving = serve_probe(ctx, args) if args.serve_seconds > 0 else None
-
-    line = None
-    if rank == 0:
-        ms_per_step = ms32 / args.steps
-        value = whole_job_rate(world, args.steps, ms32)
-        cpu = time_oracle(budget_s=args.cpu_seconds) if world == 1 else None
-        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-                "config": config_block({"parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                                        "schedule": sched}),
-                "iters": {"fp32_bulk": int(np.median(its32)), "fp64_plain": int(np.median(its64)),
-                          "delta": int(np.median(its32)) - int(np.median(its64))},
-                "fp64_plain": {"value": whole_job_rate(world, args.steps, ms64), "unit": UNIT,
-                               "ms_per_step": ms64 / args.steps, "schedule": sched64},
-                "serve_latency_ms": serving,
-                "roofline": roofline, "kernel_shares": shares, "kernel_shares_stepwise": shares_stepwise,
-                "cpu_baseline": cpu,
-                "e2e": {"value": whole_job_rate(world, args.steps, e2e_ms), "unit": UNIT,
-                        "h2d_bytes_per_step": m.nv * 8, "d2h_bytes_per_step": m.nv * 8 + 16},
-                "gpu_launches": int(launches32), "clocks": clocks,
-                "impl": "ours"}
-        print(json.dumps(line))
-    h32.free()
     h64.free()
+
+    # ---- the reduced-precision forms on the same mesh --------------------------------
+    forms = {}
+    for prec in ("fp32", "fp16"):
+        h = cgs.Mesh(ctx, m.xyz, m.conn, part=m.part, boxes=m.boxes, prec=prec)
+        cgs.cgs_mesh_tune(h.handle)
+        sch = cgs.cgs_mesh_get_schedule(h.handle)
+        ms, its, x, _ = timed(h, args.steps, max(2, args.warmup // 2))
+        prof, _ = profile(h, 2)
+        info = dict(h.info)
+        info.update(cgs.cgs_mesh_info(h.handle))
+        roof, per = roofline_of(prof, info, prec, bool(sch["interp_cells"]), peaks, peak_kind,
+                                f"hollow_cylinder_1M_{prec}")
+        forms[prec] = {"value": whole_job_rate(world, args.steps, ms), "unit": UNIT,
+                       "ms_per_step": ms / args.steps, "iters": int(np.median(its)),
+                       "iters_delta_vs_fp64": int(np.median(its)) - int(np.median(its64)),
+                       "x_rel_diff_vs_fp64": float(torch.linalg.norm(x - x64) / torch.linalg.norm(x64)),
+                       "schedule": sch, "roofline": roof, "kernels": per}
+        h.free()
+
+    # ---- batched form (256 meshes x 4 right-hand sides in one graph) -----------------
+    batch = None
+    if args.batch:
+        from paper_2606_20496_b300 import run_batch
+        batch = run_batch.run(ctx, 256, 4, "fp32", RTOL, reps=3, plain=True, plain_budget_s=args.plain_seconds)
     cgs.cgs_destroy(ctx)
+
+    # ---- serving form ----------------------------------------------------------------
+    serving = None
+    if args.serve_seconds > 0:
+        from paper_2606_20496_b300 import serve
+        serving = serve.serve(rate=args.serve_rate, seconds=args.serve_seconds, pool_n=args.serve_pool, slots=256,
+                              iters_per_step=8, rtol=RTOL, prec="fp32", plain=True,
+                              plain_budget_s=args.plain_seconds)
+
+    if rank == 0:
+        value = whole_job_rate(world, args.steps, ms64)
+        cpu = finish_oracle_sample(cpu_proc) if cpu_proc else None
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms64 / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": config_block({"parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                                        "schedule": sched64}),
+                "iters": {"fp64_plain": int(np.median(its64)), "fp32_bulk": forms["fp32"]["iters"],
+                          "fp16_local": forms["fp16"]["iters"],
+                          "delta_fp32": forms["fp32"]["iters_delta_vs_fp64"],
+                          "delta_fp16": forms["fp16"]["iters_delta_vs_fp64"],
+                          "oracle": oracle_iters_per_solve()},
+                "fp32_bulk": forms["fp32"], "fp16_local": forms["fp16"],
+                "batch": batch, "serve": serving,
+                "roofline": roofline, "kernels": kernels64,
+                "cpu_baseline": cpu,
+                "e2e": {"value": whole_job_rate(world, e2e_steps, e2e_ms), "unit": UNIT,
+                        "h2d_bytes_per_step": m.nv * 8, "d2h_bytes_per_step": m.nv * 8 + 16},
+                "gpu_launches": int(round(launches_per_solve * args.steps)),
+                "gpu_launches_note": "kernels per solve counted in a profiled solve (the graph loop runs the same "
+                                     "kernels) x timed solves",
+                "clocks": clocks, "impl": "ours"}
+        print(json.dumps(line))
     if dist:
         dist.barrier()
         dist.destroy_process_group()
@@ -447,17 +524,20 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
-    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--serve-seconds", type=float, default=3.0, help="serving probe length (0: skip)")
+    ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--no-batch", dest="batch", action="store_false", help="skip the batched form")
+    ap.add_argument("--serve-seconds", type=float, default=10.0, help="serving stream length (0: skip)")
     ap.add_argument("--serve-rate", type=float, default=2000.0)
-    ap.add_argument("--serve-pool", type=int, default=32)
-    ap.add_argument("--oracle-sample", nargs=2, type=float, default=None, help=argparse.SUPPRESS)
+    ap.add_argument("--serve-pool", type=int, default=64)
+    ap.add_argument("--plain-seconds", type=float, default=10.0,
+                    help="time budget of each FP64 per-request comparison (batch, serving)")
+    ap.add_argument("--oracle-sample", type=int, default=None, help=argparse.SUPPRESS)
     args = ap.parse_args()
-    if args.oracle_sample:
-        oracle_sample(args.oracle_sample[0], int(args.oracle_sample[1]))
+    if args.oracle_sample is not None:
+        oracle_sample(args.oracle_sample)
         return
     if args.warmup < 3:
         args.warmup = 3

@@ -330,6 +330,32 @@ cgs_status cgs_solve(cgs_mesh* mesh, const double* b, double* x, int nrhs, doubl
 cgs_status cgs_solve_host(cgs_mesh* mesh, const double* b_host, double* x_host, int nrhs,
                           double rtol, int maxit, int* iters, double* relres, void* stream);
 
+/* ---- other outer iterations around the same preconditioner -----------------
+ * cgs_solve_wrapped: A x = b for one right-hand side with
+ *   CGS_METHOD_PCG         the flexible PCG of cgs_solve (restart ignored);
+ *   CGS_METHOD_RICHARDSON  Schwarz-Richardson, x += M (b - A x) from x = 0, the
+ *                          paper's alternative wrapper (Sec. 3); iters counts the
+ *                          updates of x;
+ *   CGS_METHOD_FGMRES      flexible GMRES(restart), right-preconditioned, x = 0
+ *                          first: the Arnoldi basis V of the residual space and the
+ *                          preconditioned directions Z = M V are kept, so M may vary
+ *                          between steps (inexact local solves, Sec. 6); the
+ *                          Hessenberg least-squares problem is solved by Givens
+ *                          rotations on the host; iters counts the products A z.
+ * M is the mesh's preconditioner (form and precision); vectors and
+ * arithmetic of the outer iteration are float64 on the device.  Stops when the
+ * residual norm (true for Richardson and at every GMRES restart, the
+ * least-squares estimate inside a cycle) is <= rtol ||b||.  b, x device
+ * vectors of length nv; iters and relres (the last residual norm / ||b||)
+ * host scalars, always written.  Synchronous; allocates (restart + 1 +
+ * restart) nv doubles for GMRES, 3 nv for Richardson, freed before it
+ * returns.  Returns NO_CONVERGENCE after maxit, BREAKDOWN on a non-finite
+ * value, TIMEOUT when a bounded device wait expired, INVALID_ARG for an
+ * unknown method or restart outside [1, 1024].                              */
+typedef enum { CGS_METHOD_PCG = 0, CGS_METHOD_RICHARDSON = 1, CGS_METHOD_FGMRES = 2 } cgs_method;
+cgs_status cgs_solve_wrapped(cgs_mesh* mesh, const double* b, double* x, cgs_method method, double rtol, int maxit,
+                             int restart, int* iters, double* relres, void* stream);
+
 /* ---- profiling --------------------------------------------------------------
  * cgs_profile_enable: when on, every kernel the mesh launches is bracketed by
  * CUDA events recorded on its launching stream (adds host cost per launch).

@@ -24,6 +24,7 @@ FORM = {"hybrid": 0, "additive": 1, "ras": 2}
 COARSE = {"auto": 0, "dense": 1, "xxt": 2}
 COARSE_OP = {"cellwise": 0, "galerkin": 1, "vertex": 2}
 OP = {"fp64": 0, "inner": 1, "outer": 2}
+METHOD = {"pcg": 0, "richardson": 1, "fgmres": 2}
 
 # every symbol include/cgs.h declares
 EXPORTS = (
@@ -31,7 +32,7 @@ EXPORTS = (
     "cgs_mesh_set_form", "cgs_mesh_export", "cgs_apply_A", "cgs_apply_A_prec", "cgs_mesh_step_status",
     "cgs_mesh_set_wait_limits", "cgs_apply_local", "cgs_restrict",
     "cgs_coarse_solve", "cgs_interp", "cgs_apply_preconditioner", "cgs_apply_preconditioner_noalloc",
-    "cgs_solve", "cgs_solve_host", "cgs_mesh_set_projection", "cgs_mesh_projection_size",
+    "cgs_solve", "cgs_solve_host", "cgs_solve_wrapped", "cgs_mesh_set_projection", "cgs_mesh_projection_size",
     "cgs_profile_enable", "cgs_profile_read", "cgs_batch_create", "cgs_batch_free", "cgs_batch_solve",
     "cgs_batch_launches", "cgs_solve_batched", "cgs_mesh_tune", "cgs_mesh_get_schedule", "cgs_mesh_set_schedule",
     "cgs_batch_tune",
@@ -104,6 +105,7 @@ def load(path: str = LIB_PATH):
         "cgs_apply_preconditioner_noalloc": ([P, P, P, P], I32),
         "cgs_solve": ([P, P, P, I32, D, I32, P, P, P], I32),
         "cgs_solve_host": ([P, P, P, I32, D, I32, P, P, P], I32),
+        "cgs_solve_wrapped": ([P, P, P, I32, D, I32, I32, C.POINTER(I32), C.POINTER(D), P], I32),
         "cgs_mesh_set_projection": ([P, I32], I32),
         "cgs_mesh_projection_size": ([P, C.POINTER(I32)], I32),
         "cgs_profile_enable": ([P, I32], I32),
@@ -301,6 +303,17 @@ def cgs_solve_host(mesh, b, x, nrhs=1, rtol=1e-8, maxit=1000, stream=None,
                                _ptr(relres), _stream(stream))
     _check(st, "cgs_solve_host", allow)
     return st, iters, relres
+
+
+def cgs_solve_wrapped(mesh, b, x, method="fgmres", rtol=1e-8, maxit=1000, restart=30, stream=None,
+                      allow=(ERR_NO_CONVERGENCE, ERR_BREAKDOWN)):
+    """Schwarz-Richardson, flexible GMRES(restart) or the PCG around the
+    mesh's preconditioner.  Returns (status, iters, relres)."""
+    it, rr = C.c_int(0), C.c_double(0.0)
+    st = load().cgs_solve_wrapped(mesh, _ptr(b), _ptr(x), METHOD[method], float(rtol), int(maxit), int(restart),
+                                  C.byref(it), C.byref(rr), _stream(stream))
+    _check(st, "cgs_solve_wrapped", allow)
+    return st, it.value, rr.value
 
 
 def cgs_mesh_set_projection(mesh, l: int):

@@ -292,10 +292,15 @@ void pcg_iteration(Engine& E, cudaStream_t st, const cudaGraphConditionalHandle*
     const Plan& P = E.P;
     const Vecs& V = E.V;
     if (E.f64) {
+        // the preconditioner reads its input without changing it unless the
+        // hybrid step forms s = r - A l in place: then s must be a copy of r,
+        // otherwise it is r itself (no copy written by the x, r update)
+        Vecs Vi = V;
+        if (P.hyb_restrict || E.form != CGS_HYBRID) Vi.s = V.r;
         K(CGS_K_APPLY_A64, launch_apply64(P, V, V.p, V.q, 1.0, true, st));
-        K(CGS_K_PCG_XR, (launch_pcg_update_xr<double, double>(P, V, V.q, st)));
-        if (!precond_body(E, V, st, true)) K(CGS_K_PCG_DOTS, (launch_pcg_dots<double, double>(P, V, V.q, st)));
-        K(CGS_K_PCG_P, (launch_pcg_update_p<double, double>(P, V, V.q, cond, st)));
+        K(CGS_K_PCG_XR, (launch_pcg_update_xr<double, double>(P, Vi, V.q, st)));
+        if (!precond_body(E, Vi, st, true)) K(CGS_K_PCG_DOTS, (launch_pcg_dots<double, double>(P, Vi, V.q, st)));
+        K(CGS_K_PCG_P, (launch_pcg_update_p<double, double>(P, Vi, V.q, cond, st)));
     } else {
         // p = z + beta p is formed by the apply and stored by the x, r update;
         // the interpolation (or the dots) closes the iteration and sets the

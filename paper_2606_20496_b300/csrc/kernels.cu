@@ -216,9 +216,12 @@ __device__ __forceinline__ void apply64_item(const DevMesh* __restrict__ meshes,
                 }
             }
         }
+        // (a product with alpha only when it is not 1: FP64 issue slots are
+        // what bounds this kernel on B300)
+        const bool scale = alpha != 1.0;
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
-            if (v[k] >= 0) atomicAdd(&y[v[k]], alpha * ye[k]);
+            if (v[k] >= 0) atomicAdd(&y[v[k]], scale ? alpha * ye[k] : ye[k]);
             if (kDot) energy = fma(xe[k], ye[k], energy);
         }
     }
@@ -2161,14 +2164,34 @@ __device__ __forceinline__ void pcg_update_xr_item(const DevMesh* __restrict__ m
     Tz* z = static_cast<Tz*>(V.z) + w.voff;
     Tz* s = static_cast<Tz*>(V.s) + w.voff;
     const double alpha = S->alpha;
+    // s is r itself when the preconditioner only reads its input
+    const bool copy_s = (const void*)s != (const void*)r;
     double acc = 0.0;
-    CGS_VERT_LOOP(i) {
-        x[i] = fma(alpha, p[i], x[i]);
-        const double ri = fma(-alpha, qval(q, i), r[i]);
-        r[i] = ri;
-        acc = fma(ri, ri, acc);
-        z[i] = Tz(0);
-        s[i] = (Tz)ri;
+    // four vertices per thread and round, every load issued before the stores
+    CGS_VERT_LOOP4(i0) {
+        double xi[4], pi[4], ri[4], qi[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int64_t i = i0 + k * (int64_t)blockDim.x;
+            if (i < w.end) {
+                xi[k] = x[i];
+                pi[k] = p[i];
+                ri[k] = r[i];
+                qi[k] = qval(q, i);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int64_t i = i0 + k * (int64_t)blockDim.x;
+            if (i < w.end) {
+                x[i] = fma(alpha, pi[k], xi[k]);
+                const double rn = fma(-alpha, qi[k], ri[k]);
+                r[i] = rn;
+                acc = fma(rn, rn, acc);
+                z[i] = Tz(0);
+                if (copy_s) s[i] = (Tz)rn;
+            }
+        }
     }
     const int64_t chunk = (M.nr + w.count - 1) / w.count;
     const int64_t r0 = (int64_t)w.idx * chunk, r1 = min((int64_t)M.nr, r0 + chunk);
@@ -2253,11 +2276,26 @@ __device__ __forceinline__ void pcg_update_p_item(const DevMesh* __restrict__ me
     float2* p2 = V.p2 ? V.p2 + w.voff : nullptr;
     Tq* q = qv + w.voff;
     const double beta = S->beta;
-    CGS_VERT_LOOP(i) {
-        const double pi = fma(beta, p[i], (double)z[i]);
-        p[i] = pi;
-        if (p2) p2[i] = split_pair(pi);
-        qzero(q, i);
+    CGS_VERT_LOOP4(i0) {
+        double pk[4], zk[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int64_t i = i0 + k * (int64_t)blockDim.x;
+            if (i < w.end) {
+                pk[k] = p[i];
+                zk[k] = (double)z[i];
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int64_t i = i0 + k * (int64_t)blockDim.x;
+            if (i < w.end) {
+                const double pi = fma(beta, pk[k], zk[k]);
+                p[i] = pi;
+                if (p2) p2[i] = split_pair(pi);
+                qzero(q, i);
+            }
+        }
     }
 }
 
