@@ -141,17 +141,25 @@ def algorithmic_bytes(info, prec, interp_cells=False):
     # 8-byte values and 2-byte indices once, r_r or t gathered, t or u_r out)
     xnnz = info.get("xxt_nnz", 0)
     coarse = xnnz * 10 + nr * 12 if info.get("coarse_solver") == 2 else nr * nr * 8 + nr * 12
+    nh = info.get("n_hyb_entries", 0)
+    nj = info.get("n_jt_entries", 0)
+    nvb = info.get("n_free", nv)
     if prec == "fp64":
         return {
             "apply_A64": E * (36 * 8 + 32) + nv * (8 + 16),
             "local": packed * sl + sm * 4 + nv * (8 + 2 * sb + sb),
-            "restrict": nb * 16 + nv * (32 + sb) + nr * 16,
+            # hybrid: (vertex, J~, A J~) entries, r and l gathered, r_r; else
+            # the cell-sorted restriction of s
+            "restrict": (nh * (4 + 16) + nv * 16 + nr * 8) if nh else nb * 16 + nv * (32 + sb) + nr * 16,
             "coarse": coarse + (nr * 4 if info.get("coarse_solver") != 2 else 0),
-            "interp": (nb * 16 + nv * (32 + 2 * sb) + nr * 8) if interp_cells
-            else nb * 16 + nv * (4 + 32 + 2 * sb + 16) + nr * 8,
-            "pcg_xr": nv * (8 * 6 + 2 * sb),
+            # explicit J~ rows (column, weight), z read and written, r and q
+            # read for the fused dots
+            "interp": nj * 12 + nvb * 8 + nv * 32 + nr * 8,
+            # x, p, r, q read; x, r, z written
+            "pcg_xr": nv * (4 * 8 + 3 * 8),
             "pcg_dots": nv * (sb + 16),
-            "pcg_p": nv * (sb + 24),
+            # z, p read; p, q written
+            "pcg_p": nv * 32,
         }
     return {
         # q = A p: hi/lo off-diagonals and 16-bit local indices per element;
@@ -161,8 +169,9 @@ def algorithmic_bytes(info, prec, interp_cells=False):
         "apply_A32": E * (28 * 4 + 16) + nv * (4 + 2 * 4),
         # upper triangles, vertex ids, W_ov; r gathered, z read and written
         "local": packed * sl + sm * 4 + nv * (4 + sb + 2 * sb),
-        # (vertex, cell, weight) entries; coordinates and s per vertex; r_r pairs
-        "restrict": nb * 12 + nv * (16 + sb) + nr * 8,
+        # hybrid: (vertex, J~, A J~) float entries, r and l gathered, r_r
+        # pairs; else (vertex, cell, weight) entries, coordinates and s
+        "restrict": (nh * (4 + 8) + nv * 8 + nr * 8) if nh else nb * 12 + nv * (16 + sb) + nr * 8,
         # per-vertex lists, coordinates, z read and written, r and q pairs
         # read (dots), q cleared
         "interp": (nb * 12 + nv * (16 + 2 * sb) + nr * 4) if interp_cells
@@ -177,13 +186,19 @@ def algorithmic_bytes(info, prec, interp_cells=False):
 
 
 def algorithmic_flops(info, prec):
-    """Float64 flops per launch of the FP64-form kernels that the FP64 pipe
-    bounds (an FMA counts 2): the element matrix-vector product (64 FMAs per
-    element) and the local solves (m_p^2 FMAs per subdomain)."""
+    """Float64 flops per launch of the FP64-form kernels (an FMA counts 2): the
+    element matrix-vector product (64 FMAs per element), the local solves
+    (m_p^2 FMAs per subdomain), the hybrid restriction (2 FMAs per entry) and
+    the interpolation by rows (1 FMA per entry, 2 per vertex for the dots)."""
     if prec != "fp64":
         return {}
     sum_m2 = 2 * info["sum_sub_tri"] - info["sum_sub_dofs"]
-    return {"apply_A64": 2 * 64 * info["ne"], "local": 2 * sum_m2}
+    out = {"apply_A64": 2 * 64 * info["ne"], "local": 2 * sum_m2}
+    if info.get("n_hyb_entries"):
+        out["restrict"] = 4 * info["n_hyb_entries"]
+    if info.get("n_jt_entries"):
+        out["interp"] = 2 * info["n_jt_entries"] + 4 * info.get("n_free", info["nv"])
+    return out
 
 
 def measured_peaks():

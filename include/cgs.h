@@ -127,6 +127,9 @@ typedef struct {
     int64_t xxt_nnz;       /* nonzeros of X (XX^T solver), else 0                    */
     int64_t ar_nnz;        /* nonzeros of A_r                                         */
     int32_t coarse_operator; /* the cgs_coarse_operator of the set-up                */
+    int64_t n_hyb_entries; /* entries (v, J~_vc, (A J~)_vc) of the hybrid restriction
+                              (0 unless the set-up was hybrid)                        */
+    int64_t n_jt_entries;  /* entries of the explicit rows of J~ (FP64 form)         */
 } cgs_mesh_info_t;
 
 /* Launch schedule of a mesh's kernels (cgs_mesh_get_schedule / _set_schedule):

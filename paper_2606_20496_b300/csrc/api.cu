@@ -608,8 +608,11 @@ cgs_status tune_engine(Engine& E, cudaStream_t st) {
             best.vert_chunk = vc;
         }
     }
-    // box-list vertices per interpolation block
-    if (P_any_nr(E)) {
+    // box-list vertices per interpolation block (mixed forms; the FP64
+    // form's interpolation by rows closes with the PCG dots, whose per-slot
+    // reduction a timing run without slot scalars cannot include, so it keeps
+    // the default of about seven blocks per SM)
+    if (P_any_nr(E) && !E.f64) {
         float best_box = 1e30f;
         for (int bc : {256, 512, 768, 1024, 2048}) {
             Schedule t = best;
@@ -625,8 +628,8 @@ cgs_status tune_engine(Engine& E, cudaStream_t st) {
         }
     }
     // interpolation by vertex with the dots fused, or by cells followed by
-    // the dots kernel
-    if (P_any_nr(E)) {
+    // the dots kernel (mixed forms; the FP64 form interpolates by rows)
+    if (P_any_nr(E) && !E.f64) {
         float best_ip = 1e30f;
         for (int ic = 0; ic < 2; ++ic) {
             Schedule t = best;
@@ -828,6 +831,7 @@ cgs_status cgs_mesh_setup(cgs_ctx* ctx, const double* xyz, int64_t nv, const int
             UP(d.vb_w64, hs.vb_w);
             UP(d.re_w64, hs.re_w);
             // explicit rows of J~ for the float64 interpolation
+            UP(d.jt_vert, hs.jt_vert);
             UP(d.jt_ptr, hs.jt_ptr);
             UP(d.jt_col, hs.jt_col);
             UP(d.jt_val, hs.jt_val);
@@ -1112,6 +1116,8 @@ cgs_status cgs_mesh_setup(cgs_ctx* ctx, const double* xyz, int64_t nv, const int
     m->info.ar_nnz = hs.ar_nnz;
     m->info.coarse_operator = prm.coarse_operator;
     m->info.xxt_nnz = (int64_t)hs.xc_idx.size();
+    m->info.n_hyb_entries = (int64_t)hs.hr_vert.size();
+    m->info.n_jt_entries = f64 ? hs.jt_nnz : 0;
     m->info.footprint_bytes = m->mem.bytes;
     m->info.setup_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     *out = m;

@@ -80,16 +80,19 @@ struct HostSetup {
     std::vector<int32_t> re_vert, re_cell;   // the same entries sorted by cell (restriction)
     std::vector<double> re_w;
     std::vector<int32_t> re_rng;       // (begin, end) entry ranges within one cell, <= kBoxRange each
-    // J~ = W Q^T J_L as explicit rows, aligned with vb_vert (the same
-    // interpolant as the box lists, the weights formed once in float64)
+    // J~ = W Q^T J_L as explicit rows (the same interpolant as the box
+    // lists, the weights formed once in float64), padded to multiples of 4
+    // entries and ordered by padded length, then vertex
+    std::vector<int32_t> jt_vert;      // nvb, the vertex of each row
     std::vector<int32_t> jt_ptr;       // nvb+1
-    std::vector<int32_t> jt_col;       // reduced columns, ascending per row
-    std::vector<double> jt_val;
+    std::vector<int32_t> jt_col;       // reduced columns, ascending per row (padding: column 0)
+    std::vector<double> jt_val;        // weights (padding: 0)
+    int64_t jt_nnz = 0;                // entries without the padding
     // restriction of the hybrid step, r_r = J~^T r - (A J~)^T l, as explicit
     // entries sorted by reduced column, then vertex (hybrid set-ups only)
     std::vector<int32_t> hr_vert;
     std::vector<double> hr_j, hr_g;    // J~_vc and (A J~)_vc
-    std::vector<int32_t> hr_rng;       // 4 per range: begin, end, column, 0 (<= kBoxRange entries)
+    std::vector<int32_t> hr_rng;       // 4 per range: begin, end, column, 0 (<= kHybRange entries)
     std::vector<int64_t> box_active;   // nr, lexicographic box-vertex ids
     int coarse = 1;                    // reduced solver: 1 dense A_r^{-1}, 2 XX^T
     int64_t ar_nnz = 0;                // nonzeros of A_r
@@ -190,13 +193,14 @@ struct DevMesh {
     const float* rpack_went32 = nullptr;   // RAS weights, aligned with rpack_idx
     const double* wov64 = nullptr;     // nv
     const float* wov32 = nullptr;      // nv
-    // explicit rows of J~ (FP64 form), aligned with vb_vert
+    // explicit rows of J~ (FP64 form): row vertices, offsets (multiples of 4)
+    const int32_t* jt_vert = nullptr;  // nvb
     const int32_t* jt_ptr = nullptr;   // nvb + 1
     const int32_t* jt_col = nullptr;
     const double* jt_val = nullptr;
     // restriction of the hybrid step r_r = J~^T r - (A J~)^T l (hybrid set-ups)
     int64_t nhr = 0;                   // ranges
-    const int4* hr_rng = nullptr;      // (begin, end, column, 0), <= kBoxRange entries of one column
+    const int4* hr_rng = nullptr;      // (begin, end, column, 0), <= kHybRange entries of one column
     const int32_t* hr_vert = nullptr;
     const double2* hr_jg64 = nullptr;  // (J~_vc, (A J~)_vc), FP64 form
     const float2* hr_jg32 = nullptr;   // the same rounded to float, mixed forms
@@ -324,6 +328,10 @@ inline int32_t pack_cell(int32_t c, int bx, int by) {
 constexpr int kRowChunk = 4;      // reduced rows per block (one warp each)
 constexpr int kXxtSeg = 256;      // entries of one column of X per pass-1 warp
 constexpr int kBoxRange = 256;    // restriction entries (of one cell) per warp
+// hybrid-restriction entries (of one reduced column) per warp: long ranges,
+// so the warp's closing sum (five float64 additions on all 32 lanes) is
+// small against its two FMAs per entry
+constexpr int kHybRange = 1024;
 
 // Vector pools of a set of slots, passed by value to every kernel.  A slot's
 // vector is pool + work.voff (vertex vectors) or pool + work.roff (reduced).

@@ -1215,7 +1215,9 @@ __global__ void __launch_bounds__(kBlock, 2) local_lane_kernel(const DevMesh* __
 // The FP64 form's lane packs (meshes with many small subdomains): the same
 // one-lane-per-subdomain product in float64.  A lane holds 2 M doubles of x
 // and y in registers, so one block per SM (up to 255 registers a thread);
-// the kernel is bound by the FP64 FMA rate, M^2 FMAs per subdomain.
+// the kernel is bound by the FP64 FMA rate, M^2 FMAs per subdomain.  (A
+// variant with x in shared memory and two blocks per SM spilled and ran
+// 16% slower on the cylinder.)
 __global__ void __launch_bounds__(kBlock, 1) local_lane64_kernel(const DevMesh* __restrict__ meshes,
                                                                  const Work* __restrict__ work, Vecs V,
                                                                  const double* __restrict__ rin,
@@ -1510,7 +1512,7 @@ __global__ void __launch_bounds__(kBlock) restrict_kernel(const DevMesh* __restr
 // Restriction of the hybrid step without the residual update (Eq. asm2):
 // r_r = J~^T (r - A l) = J~^T r - (A J~)^T l, A symmetric, over explicit
 // entries (v, J~_vc, (A J~)_vc) sorted by reduced column c.  One warp per
-// range of one column (<= kBoxRange entries): each lane takes every 32nd
+// range of one column (<= kHybRange entries): each lane takes every 32nd
 // entry, four at a time with the loads first, the warp sums, and lane 0 adds
 // the total to r_r[c] once.  This replaces the inner operator apply s -= A l
 // (one pass over the element matrices) and the restriction of s.
@@ -1564,28 +1566,31 @@ __global__ void __launch_bounds__(kBlock) restrict_hyb_kernel(const DevMesh* __r
 }
 
 // z += J~ u_r by the explicit float64 rows of J~ (FP64 form): one thread per
-// box-list vertex, the row's (column, weight) pairs with u_r gathered from
-// L2; kDots also forms the PCG dots z.r, z.q and beta (as interp_add).
+// row, rows ordered by length (so a warp's rows have the same length) and
+// padded to multiples of four entries, read as 16-byte groups; u_r gathered
+// from L2.  kDots also forms the PCG dots z.r, z.q and beta (as interp_add).
 template <int kDots>
 __device__ __forceinline__ void interp_rows_item(const DevMesh* __restrict__ meshes, const Work& w, Vecs V,
                                                  const double* __restrict__ urv, double* __restrict__ zv) {
     CGS_ITEM_PROLOGUE();
-    const double* ur = urv + w.roff;
-    double* z = zv + w.voff;
+    const double* __restrict__ ur = urv + w.roff;
+    double* __restrict__ z = zv + w.voff;
     const double* __restrict__ r64 = V.r + w.voff;
     const double* __restrict__ q64 = V.q + w.voff;
+    const int4* __restrict__ col4 = reinterpret_cast<const int4*>(M.jt_col);
+    const double2* __restrict__ val2 = reinterpret_cast<const double2*>(M.jt_val);
     double zr = 0.0, zq = 0.0;
-    for (int64_t i0 = (int64_t)w.begin + threadIdx.x; i0 < w.end; i0 += 2 * (int64_t)blockDim.x) {
-        int v[2], p0[2], p1[2];
+    for (int i0 = w.begin + (int)threadIdx.x; i0 < w.end; i0 += 2 * (int)blockDim.x) {
+        int v[2], g0[2], g1[2];
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
-            const int64_t i = i0 + k * (int64_t)blockDim.x;
+            const int i = i0 + k * (int)blockDim.x;
             v[k] = -1;
-            p0[k] = p1[k] = 0;
+            g0[k] = g1[k] = 0;
             if (i < w.end) {
-                v[k] = __ldg(&M.vb_vert[i]);
-                p0[k] = __ldg(&M.jt_ptr[i]);
-                p1[k] = __ldg(&M.jt_ptr[i + 1]);
+                v[k] = __ldg(&M.jt_vert[i]);
+                g0[k] = __ldg(&M.jt_ptr[i]) >> 2;
+                g1[k] = __ldg(&M.jt_ptr[i + 1]) >> 2;
             }
         }
         double zo[2], rd[2], qd[2], val[2];
@@ -1597,9 +1602,26 @@ __device__ __forceinline__ void interp_rows_item(const DevMesh* __restrict__ mes
             qd[k] = (kDots && ok) ? q64[v[k]] : 0.0;
             val[k] = 0.0;
         }
+        // both rows advance together, one group of four entries each per step
+        const int n = max(g1[0] - g0[0], g1[1] - g0[1]);
+        for (int t = 0; t < n; ++t) {
+            int4 c[2];
+            double2 a[2], b[2];
 #pragma unroll
-        for (int k = 0; k < 2; ++k)
-            for (int e = p0[k]; e < p1[k]; ++e) val[k] = fma(__ldg(&M.jt_val[e]), __ldg(&ur[__ldg(&M.jt_col[e])]), val[k]);
+            for (int k = 0; k < 2; ++k) {
+                const bool ok = g0[k] + t < g1[k];
+                c[k] = ok ? __ldg(&col4[g0[k] + t]) : make_int4(0, 0, 0, 0);
+                a[k] = ok ? __ldg(&val2[2 * (g0[k] + t)]) : make_double2(0.0, 0.0);
+                b[k] = ok ? __ldg(&val2[2 * (g0[k] + t) + 1]) : make_double2(0.0, 0.0);
+            }
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                val[k] = fma(a[k].x, __ldg(&ur[c[k].x]), val[k]);
+                val[k] = fma(a[k].y, __ldg(&ur[c[k].y]), val[k]);
+                val[k] = fma(b[k].x, __ldg(&ur[c[k].z]), val[k]);
+                val[k] = fma(b[k].y, __ldg(&ur[c[k].w]), val[k]);
+            }
+        }
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
             if (v[k] < 0) continue;
@@ -1612,9 +1634,9 @@ __device__ __forceinline__ void interp_rows_item(const DevMesh* __restrict__ mes
         }
     }
     if (kDots == 0 || !S) return;
-    double val2[2] = {zr, zq}, tot[2];
+    double val2s[2] = {zr, zq}, tot[2];
     pdl_trigger();   // the successor may launch during the reduction tail
-    if (slot_sum<2>(val2, V.partials + w.poff, w.idx, w.count, &S->ticket[3], tot) && threadIdx.x == 0) {
+    if (slot_sum<2>(val2s, V.partials + w.poff, w.idx, w.count, &S->ticket[3], tot) && threadIdx.x == 0) {
         S->zr = tot[0];
         S->zq = tot[1];
         const double beta = -S->alpha * tot[1] / S->rho;
@@ -2219,7 +2241,7 @@ __device__ __forceinline__ void pcg_update_xr_item(const DevMesh* __restrict__ m
 }
 
 template <typename Tz, typename Tq>
-__global__ void __launch_bounds__(kBlock) pcg_update_xr_kernel(const DevMesh* __restrict__ meshes,
+__global__ void __launch_bounds__(kBlock, 3) pcg_update_xr_kernel(const DevMesh* __restrict__ meshes,
                                                                const Work* __restrict__ work, Vecs V,
                                                                const Tq* __restrict__ qv) {
     const Work w_ = work[blockIdx.x];
@@ -2301,7 +2323,7 @@ __device__ __forceinline__ void pcg_update_p_item(const DevMesh* __restrict__ me
 
 
 template <typename Tz, typename Tq>
-__global__ void __launch_bounds__(kBlock) pcg_update_p_kernel(const DevMesh* __restrict__ meshes,
+__global__ void __launch_bounds__(kBlock, 4) pcg_update_p_kernel(const DevMesh* __restrict__ meshes,
                                                               const Work* __restrict__ work, Vecs V, Tq* qv,
                                                               int nslots, cudaGraphConditionalHandle cond,
                                                               int set_cond) {

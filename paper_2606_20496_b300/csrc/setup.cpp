@@ -883,15 +883,33 @@ cgs_status host_setup(const double* xyz, int64_t nv, const int32_t* conn, int64_
             }
             std::sort(row.begin(), row.end());
         }
-        S.jt_ptr.assign(nvb + 1, 0);
-        for (size_t i = 0; i < nvb; ++i) S.jt_ptr[i + 1] = S.jt_ptr[i] + (int32_t)rows[i].size();
-        S.jt_col.resize(S.jt_ptr[nvb]);
-        S.jt_val.resize(S.jt_ptr[nvb]);
-        for (size_t i = 0; i < nvb; ++i)
-            for (size_t k = 0; k < rows[i].size(); ++k) {
-                S.jt_col[S.jt_ptr[i] + k] = rows[i][k].first;
-                S.jt_val[S.jt_ptr[i] + k] = rows[i][k].second;
+        // the device copy (FP64 interpolation): rows padded to a multiple of
+        // four entries (weight 0, column 0) for 16-byte loads, and ordered by
+        // padded length, then vertex, so that the rows a warp takes have the
+        // same length
+        {
+            std::vector<int32_t> order(nvb);
+            std::iota(order.begin(), order.end(), 0);
+            auto plen = [&](int32_t i) { return (int32_t)((rows[i].size() + 3) / 4 * 4); };
+            std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return plen(a) < plen(b); });
+            S.jt_vert.resize(nvb);
+            S.jt_ptr.assign(nvb + 1, 0);
+            for (size_t q = 0; q < nvb; ++q) {
+                S.jt_vert[q] = S.vb_vert[order[q]];
+                S.jt_ptr[q + 1] = S.jt_ptr[q] + plen(order[q]);
             }
+            S.jt_nnz = 0;
+            for (const auto& row : rows) S.jt_nnz += (int64_t)row.size();
+            S.jt_col.assign(S.jt_ptr[nvb], 0);
+            S.jt_val.assign(S.jt_ptr[nvb], 0.0);
+            for (size_t q = 0; q < nvb; ++q) {
+                const auto& row = rows[order[q]];
+                for (size_t k = 0; k < row.size(); ++k) {
+                    S.jt_col[S.jt_ptr[q] + k] = row[k].first;
+                    S.jt_val[S.jt_ptr[q] + k] = row[k].second;
+                }
+            }
+        }
         // hybrid: r_r = J~^T (r - A l) = J~^T r - (A J~)^T l, so the step
         // needs J~^T and G = A J~ (A symmetric) but never s = r - A l itself.
         // Row v of G = sum over the elements e at v of sum_k A^e(v, k) J~_k
@@ -926,9 +944,9 @@ cgs_status host_setup(const double* xyz, int64_t nv, const int32_t* conn, int64_
                             touched.push_back(c);
                         }
                     };
-                    for (int32_t k = S.jt_ptr[i]; k < S.jt_ptr[i + 1]; ++k) {
-                        touch(S.jt_col[k]);
-                        jacc[S.jt_col[k]] += S.jt_val[k];
+                    for (const auto& cv : rows[i]) {
+                        touch(cv.first);
+                        jacc[cv.first] += cv.second;
                     }
                     for (int64_t t = v2e_ptr[v]; t < v2e_ptr[v + 1]; ++t) {
                         const int64_t e = v2e[t];
@@ -939,9 +957,9 @@ cgs_status host_setup(const double* xyz, int64_t nv, const int32_t* conn, int64_
                             const int32_t ru = row_of[u];
                             if (S.dir[u] || ru < 0) continue;
                             const double a = Ae[(size_t)e * 64 + iv * 8 + k];
-                            for (int32_t q = S.jt_ptr[ru]; q < S.jt_ptr[ru + 1]; ++q) {
-                                touch(S.jt_col[q]);
-                                gacc[S.jt_col[q]] += a * S.jt_val[q];
+                            for (const auto& cv : rows[ru]) {
+                                touch(cv.first);
+                                gacc[cv.first] += a * cv.second;
                             }
                         }
                     }
@@ -972,9 +990,9 @@ cgs_status host_setup(const double* xyz, int64_t nv, const int32_t* conn, int64_
                     S.hr_g[at] = x.g;
                 }
             for (int64_t c = 0; c < S.nr; ++c)
-                for (int64_t a = cptr[c]; a < cptr[c + 1]; a += kBoxRange) {
+                for (int64_t a = cptr[c]; a < cptr[c + 1]; a += kHybRange) {
                     S.hr_rng.push_back((int32_t)a);
-                    S.hr_rng.push_back((int32_t)std::min<int64_t>(cptr[c + 1], a + kBoxRange));
+                    S.hr_rng.push_back((int32_t)std::min<int64_t>(cptr[c + 1], a + kHybRange));
                     S.hr_rng.push_back((int32_t)c);
                     S.hr_rng.push_back(0);
                 }
