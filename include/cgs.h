@@ -6,10 +6,10 @@
  * overlapping Schwarz method of "Coarse Solvers for Exascale Solution of
  * Poisson Problems" (Ratnayaka, Fischer, Olson):
  *
- *   local part   l = sum_p R~_p^T A_p^{-1} R_p r            (Sec. 3, Eq. asm1)
+ *   local part   l = sum_p R~_p^T A_p^{-1} R_p r            (Sec. 3, Eq. (4))
  *   box part     B_C s = J~ A_r^{-1} J~^T s,  J~ = W Q^T J_L  (Sec. 4)
- *   hybrid       z = l + B_C (r - A l)                      (Eq. asm2)
- *   additive     z = sum_p R_p^T A_p^{-1} R_p r + B_C r     (Eq. asm)
+ *   hybrid       z = l + B_C (r - A l)                      (Eq. (5))
+ *   additive     z = sum_p R_p^T A_p^{-1} R_p r + B_C r     (Eq. (3))
  *
  * Conventions shared by every call
  *   - Meshes are trilinear hexahedra.  conn[8*e + k] is the vertex of local
@@ -63,9 +63,9 @@ typedef enum {
 } cgs_precision;
 
 typedef enum {
-    CGS_HYBRID = 0,      /* ASM_1 then ASM_2 (Eqs. asm1, asm2), W_ov-weighted local sum */
-    CGS_ADDITIVE = 1,    /* Eq. asm with R~_p = R_p (symmetric)                         */
-    CGS_RAS = 2          /* Eq. asm with the restricted prolongation R~_p (Sec. 3, RAS):
+    CGS_HYBRID = 0,      /* ASM_1 then ASM_2 (Eqs. (4), (5)), W_ov-weighted local sum */
+    CGS_ADDITIVE = 1,    /* Eq. (3) with R~_p = R_p (symmetric)                         */
+    CGS_RAS = 2          /* Eq. (3) with the restricted prolongation R~_p (Sec. 3, RAS):
                             a local solution keeps only the nodes of the original,
                             not grown, Omega_p, averaged where several original
                             subdomains store a node; not symmetric, so solve it
@@ -84,7 +84,7 @@ typedef enum {
 
 /* The reduced operator A_r and its interpolation (Sec. 4). */
 typedef enum {
-    CGS_COARSE_OP_CELLWISE = 0, /* cell-wise assembly of Eq. Aij (3^3 stencil) with the
+    CGS_COARSE_OP_CELLWISE = 0, /* cell-wise assembly of Eq. (12) (3^3 stencil) with the
                                    averaged interpolant W Q^T J_L (default)            */
     CGS_COARSE_OP_GALERKIN = 1, /* the same interpolant, A_r = J~^T A J~ (5^3 stencil) */
     CGS_COARSE_OP_VERTEX = 2    /* vertex-based J: each node interpolated in the box
@@ -99,7 +99,7 @@ typedef struct {
     cgs_precision prec;
     cgs_form form;
     cgs_coarse_solver coarse_solver;  /* 0 (zero-initialised params) = auto        */
-    cgs_coarse_operator coarse_operator; /* 0 = cell-wise (Eq. Aij)                  */
+    cgs_coarse_operator coarse_operator; /* 0 = cell-wise (Eq. (12))                  */
     int local_cg_steps;    /* 0: exact local solves (explicit A_p^{-1}); k > 0: inexact
                               local solves, k CG steps on each A_p from zero (Sec. 6),
                               one warp per subdomain; needs m_p <= 64 and the FP64 or
@@ -191,7 +191,7 @@ size_t cgs_ctx_bytes_in_use(const cgs_ctx* ctx);
  * Host work: element matrices (2x2x2 Gauss), Dirichlet set, grown subdomains
  * and the explicit inverses of A_p = R_p A R_p^T (Cholesky, float64), box
  * grid, centroid cells, active box vertices, the reduced operator A_r chosen
- * by params->coarse_operator (cell-wise assembly of Eq. Aij, Galerkin
+ * by params->coarse_operator (cell-wise assembly of Eq. (12), Galerkin
  * J~^T A J~, or vertex-based J^T A J; Sec. 4), and its reduced solver chosen
  * by params->coarse_solver (explicit dense inverse, or the XX^T factor X of
  * Sec. 2 in a nested-dissection order), all in float64; the mixed forms also
@@ -227,7 +227,7 @@ cgs_status cgs_apply_A(cgs_mesh* mesh, const double* x, double* y, void* stream)
 /* cgs_apply_A_prec: y = A x (Sec. 3) evaluated by one of the mesh's operator
  * kernels, for checking each precision form against its error bound:
  *   CGS_OP_FP64   the float64 operator (as cgs_apply_A);
- *   CGS_OP_INNER  the inner apply of the hybrid step (Eq. asm2, s = r - A l):
+ *   CGS_OP_INNER  the inner apply of the hybrid step (Eq. (5), s = r - A l):
  *                 x rounded to float32, 28 float32 off-diagonals per element,
  *                 float32 sums, then widened to float64;
  *   CGS_OP_OUTER  the outer operator of the PCG (q = A p): hi/lo float pairs
@@ -250,7 +250,7 @@ cgs_status cgs_mesh_step_status(cgs_mesh* mesh, void* stream);
  * waits, with its own limit, for the copy it started before it returns.
  * Synchronous.  INVALID_ARG for a negative limit.                            */
 cgs_status cgs_mesh_set_wait_limits(cgs_mesh* mesh, int tile_wait, int barrier_wait);
-/* cgs_apply_local: l = sum_p R_p^T A_p^{-1} R_p r (Eq. asm1), weighted by
+/* cgs_apply_local: l = sum_p R_p^T A_p^{-1} R_p r (Eq. (4)), weighted by
  * W_ov = 1/multiplicity when `weighted` != 0.  Mesh precision.              */
 cgs_status cgs_apply_local(cgs_mesh* mesh, const double* r, double* l, int weighted, void* stream);
 /* cgs_restrict: r_r = J_L^T Q W s (Sec. 4); s device nv, r_r device n_r.     */

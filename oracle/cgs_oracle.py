@@ -18,15 +18,15 @@ A u = b, Sec. 3):
 * the box coarse space (Sec. 4): bounding box split into b_x*b_y*b_z cells,
   each element assigned to the cell holding its centroid, element-local
   trilinear interpolant J_L, averaging W Q^T (Sec. 4, the centroid-assignment
-  paragraph), active-vertex compression, and A_r assembled cell-wise (Eq. Aij);
-* three coarse operators (Sec. 4): the cell-wise A_r of Eq. Aij (default),
+  paragraph), active-vertex compression, and A_r assembled cell-wise (Eq. (12));
+* three coarse operators (Sec. 4): the cell-wise A_r of Eq. (12) (default),
   the Galerkin J~^T A J~ of the averaged interpolant, and the vertex-based J
   (each node in the box cell holding it) with A_r = J^T A J;
 * the reduced solve exactly (Cholesky) and by XX^T (Sec. 2): A_r-conjugate
   basis vectors formed by Gram-Schmidt in the A_r inner product, in a
   nested-dissection order of the box lattice;
-* the preconditioners ASM (Eq. asm) and the hybrid ASM_1 + ASM_2 (Eqs. asm1,
-  asm2);
+* the preconditioners ASM (Eq. (3)) and the hybrid ASM_1 + ASM_2 (Eqs. (4)
+  and (5));
 * variants and wrappers for the next steps: restricted additive Schwarz
   (Sec. 3, R~_p without the grown part), inexact local solves by a fixed
   number of CG steps (Sec. 6), Schwarz-Richardson and flexible GMRES
@@ -223,7 +223,7 @@ class Problem:
             self.ras_w[m] = np.where(inown > 0, 1.0 / np.maximum(self.own_mult[I], 1.0), 0.0)
 
     def local_solves(self, r, weighted, inner: int = 0):
-        """sum_p R~_p^T A_p^{-1} R_p r (Eq. asm, asm1).  weighted: True scales
+        """sum_p R~_p^T A_p^{-1} R_p r (Eqs. (3), (4)).  weighted: True scales
         by W_ov = 1/multiplicity (R~_p = R_p); False adds plainly; "ras" uses
         the restricted prolongation.  inner > 0 replaces A_p^{-1} by that many
         CG steps on A_p from zero (an inexact local solve, Sec. 6)."""
@@ -307,7 +307,7 @@ class Problem:
             Jf = Jt[self.free]
             self.Ar = (Jf.T @ self.A @ Jf).toarray()
             return self._factor_Ar()
-        # A_r = sum_e J_e^T A^e J_e (Eq. Aij, cell-wise assembly)
+        # A_r = sum_e J_e^T A^e J_e (Eq. (12), cell-wise assembly)
         Jk = np.where((self.corner_col >= 0)[:, None, :], Je, 0.0)
         Ke = np.einsum("ekm,ekl,eln->emn", Jk, self.Ae, Jk)
         cc = np.where(self.corner_col >= 0, self.corner_col, 0)
@@ -414,13 +414,13 @@ class Problem:
         """M r; inner > 0 replaces every A_p^{-1} by that many CG steps on
         A_p (the inexact local solves of Sec. 6)."""
         r = np.where(self.dir, 0.0, np.asarray(r, dtype=np.float64))
-        if form == "hybrid":                    # Eqs. asm1, asm2
+        if form == "hybrid":                    # Eqs. (4), (5)
             l = self.local_solves(r, weighted=True, inner=inner)
             s = r - self.apply_A(l)
             return l + self.box_correction(s)
-        if form == "additive":                  # Eq. asm
+        if form == "additive":                  # Eq. (3)
             return self.local_solves(r, weighted=False, inner=inner) + self.box_correction(r)
-        if form == "ras":                       # Eq. asm with the restricted R~_p (RAS)
+        if form == "ras":                       # Eq. (3) with the restricted R~_p (RAS)
             return self.local_solves(r, weighted="ras", inner=inner) + self.box_correction(r)
         if form == "local":                     # ASM_1 alone
             return self.local_solves(r, weighted=True, inner=inner)

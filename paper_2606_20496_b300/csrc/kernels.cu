@@ -2,8 +2,8 @@
 //
 //   apply64               y += alpha Q^T A_L Q x, float64          (Sec. 3)
 //   apply_pair_tiled      q  = A p, float-pair outer operator      (Sec. 3)
-//   apply28f_tiled        s -= A l, float32 inner apply            (Eq. asm2)
-//   local_warp            out += W_ov sum_p R_p^T A_p^{-1} R_p r   (Eq. asm1)
+//   apply28f_tiled        s -= A l, float32 inner apply            (Eq. (5))
+//   local_warp            out += W_ov sum_p R_p^T A_p^{-1} R_p r   (Eq. (4))
 //   restrict              r_r += J_L^T Q W s                       (Sec. 4)
 //   coarse_gemv           u_r = A_r^{-1} r_r, float64              (Sec. 4)
 //   interp_add            z += W Q^T J_L u_r                       (Sec. 4)
@@ -459,6 +459,31 @@ struct SmemSlots {
     __device__ __forceinline__ float4 h(int g) const { return hi[g * kTileElems + e]; }
     __device__ __forceinline__ float4 l(int g) const { return lo[g * kTileElems + e]; }
 };
+// The tile in shared memory arriving group by group: group g (hi and lo,
+// 8 KiB) completes its own mbarrier, and the first read of a group waits
+// (bounded) for it, so the arithmetic starts as soon as group 0 is in.  An
+// expired wait stops the slot (CGS_ERR_TIMEOUT) and the thread goes on with
+// whatever the buffer holds; the block waits for every copy before it exits.
+constexpr uint32_t kGroupBytes = kTileElems * sizeof(float4);   // 4 KiB
+struct SmemWaitSlots {
+    const float4* hi;
+    const float4* lo;
+    int e;
+    uint64_t* bars;
+    SolveScalars* S;
+    int limit;
+    __device__ __forceinline__ float4 h(int g) const {
+        bool ok = false;
+        for (int i = 0; i < limit && !ok; ++i) ok = mbar_try_wait(&bars[g], 0);
+        if (!ok && S) {
+            atomicAdd(&S->timeouts, 1);
+            S->status = CGS_ERR_TIMEOUT;
+            S->done = 1;
+        }
+        return hi[g * kTileElems + e];
+    }
+    __device__ __forceinline__ float4 l(int g) const { return lo[g * kTileElems + e]; }
+};
 // read-only streaming load (not volatile: the compiler may hoist it)
 __device__ __forceinline__ float4 ld_stream(const float4* p) {
     float4 v;
@@ -560,7 +585,7 @@ __device__ __forceinline__ void apply_pair_tiled_item(const DevMesh* __restrict_
     float2* ys = ps + kTileVerts;
     float4* sh_hi = reinterpret_cast<float4*>(ys + kTileVerts);
     float4* sh_lo = sh_hi + kGroups * kTileElems;
-    __shared__ uint64_t bar;
+    __shared__ uint64_t gbar[kGroups];
     CGS_ITEM_PROLOGUE();
     const float2* p2 = V.p2 + w.voff;
     const float* zf = static_cast<const float*>(V.z) + w.voff;
@@ -573,10 +598,15 @@ __device__ __forceinline__ void apply_pair_tiled_item(const DevMesh* __restrict_
     const float4* ghi = reinterpret_cast<const float4*>(M.at_hi) + (size_t)t * kGroups * kTileElems;
     const float4* glo = reinterpret_cast<const float4*>(M.at_lo) + (size_t)t * kGroups * kTileElems;
     if (kTma && threadIdx.x == 0) {
-        mbar_init(&bar, 1);
-        mbar_expect_tx(&bar, 2 * kTileSlotBytes);
-        bulk_copy_g2s(sh_hi, ghi, kTileSlotBytes, &bar);
-        bulk_copy_g2s(sh_lo, glo, kTileSlotBytes, &bar);
+        // one mbarrier per group (hi and lo, 8 KiB): the groups arrive in order
+#pragma unroll
+        for (int g = 0; g < kGroups; ++g) mbar_init(&gbar[g], 1);
+#pragma unroll
+        for (int g = 0; g < kGroups; ++g) {
+            mbar_expect_tx(&gbar[g], 2 * kGroupBytes);
+            bulk_copy_g2s(sh_hi + g * kTileElems, ghi + g * kTileElems, kGroupBytes, &gbar[g]);
+            bulk_copy_g2s(sh_lo + g * kTileElems, glo + g * kTileElems, kGroupBytes, &gbar[g]);
+        }
     }
     const int e0 = __ldg(&M.tile_ptr[t]), net = __ldg(&M.tile_ptr[t + 1]) - e0;
     const int v0 = __ldg(&M.tile_vptr[t]), nvt = __ldg(&M.tile_vptr[t + 1]) - v0;
@@ -615,13 +645,11 @@ __device__ __forceinline__ void apply_pair_tiled_item(const DevMesh* __restrict_
         }
     }
     __syncthreads();
-    bool ok = true;
-    if (kTma) {
-        ok = __syncthreads_and(wait_tile(&bar, S, wait_limit)) != 0;   // one decision per block
-        if (ok && has_e) {
-            H = sh_hi[threadIdx.x];
-            L = sh_lo[threadIdx.x];
-        }
+    const bool ok = true;
+    const SmemWaitSlots tslots{sh_hi, sh_lo, (int)threadIdx.x, gbar, S, wait_limit};
+    if (kTma && has_e) {
+        H = tslots.h(0);
+        L = tslots.l(0);
     }
     float eh = 0.0f, el = 0.0f;   // this thread's share of p.Ap
     if (ok && has_e) {
@@ -636,7 +664,7 @@ __device__ __forceinline__ void apply_pair_tiled_item(const DevMesh* __restrict_
             yl[k] = 0.0f;
         }
         if (kTma)
-            element_pair(SmemSlots{sh_hi, sh_lo, (int)threadIdx.x}, H, L, xh, xl, yh, yl);
+            element_pair(tslots, H, L, xh, xl, yh, yl);
         else
             element_pair(GlobalSlots{ghi, glo, (int)threadIdx.x}, H, L, xh, xl, yh, yl);
 #pragma unroll
@@ -653,6 +681,14 @@ __device__ __forceinline__ void apply_pair_tiled_item(const DevMesh* __restrict_
         }
     }
     __syncthreads();
+    if (kTma && threadIdx.x == 0) {
+        // every copy has landed before the block may exit (they all have,
+        // unless a wait above gave up)
+#pragma unroll
+        for (int g = 0; g < kGroups; ++g)
+            for (int i = 0; i < kWaitLimit; ++i)
+                if (mbar_try_wait(&gbar[g], 0)) break;
+    }
     if (ok) {
         for (int i = threadIdx.x; i < nvt; i += kBlock) {
             const uint32_t raw = __ldg(&M.tile_verts[v0 + i]);
@@ -1509,7 +1545,7 @@ __global__ void __launch_bounds__(kBlock) restrict_kernel(const DevMesh* __restr
     restrict_item<T, Tin, kPairOut>(meshes, w_, V, sin, rrv);
 }
 
-// Restriction of the hybrid step without the residual update (Eq. asm2):
+// Restriction of the hybrid step without the residual update (Eq. (5)):
 // r_r = J~^T (r - A l) = J~^T r - (A J~)^T l, A symmetric, over explicit
 // entries (v, J~_vc, (A J~)_vc) sorted by reduced column c.  One warp per
 // range of one column (<= kHybRange entries): each lane takes every 32nd

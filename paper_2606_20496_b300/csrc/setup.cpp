@@ -15,7 +15,7 @@
 //                      (rows of Dirichlet vertices zero); active box vertices
 //                      are the corners of occupied cells with a nonzero column
 //                      (Sec. 4); A_r = sum_e J_e^T A^e J_e cell by cell
-//                      (Eq. Aij) and its inverse.
+//                      (Eq. (12)) and its inverse.
 //
 // The device keeps explicit inverses instead of sparse Cholesky factors (the
 // paper's CHOLMOD and XX^T): a GEMV with a 27..64-dof inverse is one coalesced
@@ -584,11 +584,15 @@ cgs_status host_setup(const double* xyz, int64_t nv, const int32_t* conn, int64_
         if (prm.local_cg_steps > 0) std::copy(sub_ap[p].begin(), sub_ap[p].end(), S.ap.begin() + S.inv_ptr[w]);
         ++w;
     }
-    // lane packs: per size class (ascending), 32 subdomains in caller order
+    // lane packs: per size class, the largest class first (blocks start
+    // roughly in order, so the last wave holds the cheapest packs), 32
+    // subdomains in caller order
     S.pack_m.clear();
     S.pack_idx_off.assign(1, 0);
     S.pack_inv_off.assign(1, 0);
-    for (int c : kLaneClasses) {
+    constexpr int kNumClasses = (int)(sizeof(kLaneClasses) / sizeof(kLaneClasses[0]));
+    for (int ci = kNumClasses - 1; ci >= 0; --ci) {
+        const int c = kLaneClasses[ci];
         std::vector<int64_t> members;
         for (int64_t p = 0; p < n_sub; ++p)
             if (in_lane(p) && lane_class((int)sub_sets[p].size()) == c) members.push_back(p);
@@ -1008,7 +1012,7 @@ cgs_status host_setup(const double* xyz, int64_t nv, const int32_t* conn, int64_
         return pa < pb;
     });
 
-    // ---- A_r = sum over cells of sum_e J_e^T A^e J_e  (Eq. Aij) --------------
+    // ---- A_r = sum over cells of sum_e J_e^T A^e J_e  (Eq. (12)) --------------
     // or, for the full-support operators, A_r = J^T A J assembled element by
     // element from the rows of J at the element's nodes
     if (S.nr > 0) {

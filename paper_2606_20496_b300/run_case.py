@@ -37,7 +37,7 @@ def main():
     ap.add_argument("--prec", default="fp32", choices=list(cgs.PREC))
     ap.add_argument("--form", default="hybrid", choices=list(cgs.FORM))
     ap.add_argument("--coarse-operator", default="cellwise", choices=list(cgs.COARSE_OP),
-                    help="A_r: cell-wise (Eq. Aij), galerkin (J~^T A J~) or vertex (vertex-based J^T A J)")
+                    help="A_r: cell-wise (Eq. (12)), galerkin (J~^T A J~) or vertex (vertex-based J^T A J)")
     ap.add_argument("--coarse", default="auto", choices=list(cgs.COARSE),
                     help="reduced solver: auto (XX^T above 1500 unknowns), dense or xxt")
     ap.add_argument("--solves", type=int, default=2)

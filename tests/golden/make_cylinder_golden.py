@@ -10,9 +10,9 @@ is why the results are stored instead of recomputed by each test.
 
 Stored (vertex indices drawn by default_rng(11) among the free vertices):
   apply_A      (A b)_v                         Sec. 3, A = Q^T A_L Q
-  local_w      (W_ov sum_p R_p^T A_p^{-1} R_p b)_v     Eq. asm1
-  m_hybrid     (M b)_v, hybrid ASM_1 + ASM_2   Eqs. asm1, asm2
-  m_additive   (M b)_v, additive               Eq. asm
+  local_w      (W_ov sum_p R_p^T A_p^{-1} R_p b)_v     Eq. (4)
+  m_hybrid     (M b)_v, hybrid ASM_1 + ASM_2   Eqs. (4), (5)
+  m_additive   (M b)_v, additive               Eq. (3)
   solve        flexible PCG on A x = b, hybrid, rtol 1e-8: iterations, true
                relative residual, x_v
 """
@@ -42,7 +42,7 @@ def main():
     t_setup = time.time() - t0
     b = np.where(P.dir, 0.0, b)
     idx = np.sort(np.random.default_rng(11).choice(P.free, NSAMPLE, replace=False))
-    out = {"citation": "Sec. 3 (A = Q^T A_L Q, Eq. asm1), Sec. 4 (box coarse space, Eq. asm2), flexible PCG; "
+    out = {"citation": "Sec. 3 (A = Q^T A_L Q, Eq. (4)), Sec. 4 (box coarse space, Eq. (5)), flexible PCG; "
                        "written by tests/golden/make_cylinder_golden.py from the FP64 oracle",
            "mesh": "hollow cylinder 64 x 128 x 128 hexes (workload_cylinder(), RHS seed 6), 16^3 boxes, "
                    "2^3-element subdomains grown by one layer",

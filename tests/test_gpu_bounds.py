@@ -2,7 +2,7 @@
 against the FP64 oracle (the bounds the design notes derive; u = 2^-24 is the
 float32 unit roundoff, gamma_k = k u / (1 - k u)).
 
-* Inner operator (Eq. asm2, s = r - A l, float32, difference form
+* Inner operator (Eq. (5), s = r - A l, float32, difference form
   y_i += a_ij (x_j - x_i)): with k_i = 7 n_i + 8, n_i the elements at vertex i,
       |dy_i| <= gamma_{k_i} sum_e sum_{j != i} |a^e_ij| (|x_j| + |x_i|).
 * Outer operator (q = A p, hi/lo float pairs, about 48 bits): the same sum of

@@ -10,8 +10,8 @@ variant is forced here and compared with the oracle on two meshes: cube32
 (137,280 vertices, 16,384 subdomains: lane packs by default, the layout the
 full-size cylinder runs).
 
-Bars, as for the default schedule (Sec. 3 Eq. asm1 for the local solves,
-Eqs. asm and asm2 for M r, flexible PCG around them):
+Bars, as for the default schedule (Sec. 3 Eq. (4) for the local solves,
+Eqs. (3) and (5) for M r, flexible PCG around them):
   local solves   every entry within the float bound gamma_{m+12} W sum_p
                  |A_p^{-1}||R_p r| (plus 2 u16 and the subnormal term in FP16)
   M r            relative max-norm difference <= 1e-5 (FP32) or 2e-3 (FP16)

@@ -44,7 +44,7 @@ def test_xxt_factors_equal_dense_inverse(driver, n, boxes, nr):
 
 
 def test_coarse_operators_match_oracle(tmp_path):
-    """The library's host set-up of A_r (cell-wise Eq. Aij, Galerkin J~^T A J~,
+    """The library's host set-up of A_r (cell-wise Eq. (12), Galerkin J~^T A J~,
     vertex-based J^T A J) against the oracle's on a perturbed cube: the same
     active box vertices, the same nonzero count, A_r^{-1} to 1e-13."""
     import numpy as np

@@ -282,7 +282,7 @@ def _vertex_based_J(P):
 
 def test_galerkin_equality_on_box_aligned_mesh():
     """When element planes align with box planes J_L is continuous and the
-    cell-wise assembly (Eq. Aij) equals the Galerkin A_r = J^T A J."""
+    cell-wise assembly (Eq. (12)) equals the Galerkin A_r = J^T A J."""
     m = meshes.cube(8, boxes=(4, 2, 4))
     P = O.Problem(m.xyz, m.conn, m.part, m.boxes)
     J = _vertex_based_J(P)
@@ -301,7 +301,7 @@ def test_boxes_equal_to_elements_give_exact_inverse():
 
 
 def test_hybrid_residual_is_orthogonal_to_coarse_space_when_galerkin():
-    """With A_r = J~^T A J~ the coarse step of Eq. asm2 is an A-orthogonal
+    """With A_r = J~^T A J~ the coarse step of Eq. (5) is an A-orthogonal
     projection: J~^T (r - A z) = 0 for z = M r (hybrid)."""
     m = meshes.cube(8, boxes=(2, 4, 2), perturb=0.0)
     P = O.Problem(m.xyz, m.conn, m.part, m.boxes)
@@ -364,7 +364,7 @@ def _cell_by_search(P, point):
 
 def _brute_force_coarse(P, m):
     """Cell of each element's centroid, the averaged interpolant J~ = W Q^T J_L
-    (dense, free rows, active columns) and A_r = sum_e J_e^T A^e J_e (Eq. Aij),
+    (dense, free rows, active columns) and A_r = sum_e J_e^T A^e J_e (Eq. (12)),
     element by element with Python loops (Sec. 4: each element belongs to the
     box cell holding its centroid, and interpolates trilinearly from that
     cell's eight corners, extrapolating where its vertices lie outside)."""
@@ -427,7 +427,7 @@ def test_element_cells_follow_the_centroid(perturbed4):
 @pytest.mark.parametrize("form", ["hybrid", "additive"])
 def test_preconditioner_matches_its_dense_formula(perturbed4, form):
     """M applied to every unit vector equals the matrix composed from dense
-    factors (Sec. 3, Eqs. asm, asm1, asm2; Sec. 4, J~ = W Q^T J_L):
+    factors (Sec. 3, Eqs. (3)-(5); Sec. 4, J~ = W Q^T J_L):
       additive  sum_p R_p^T A_p^{-1} R_p + J~ A_r^{-1} J~^T
       hybrid    M_1 + J~ A_r^{-1} J~^T (I - A M_1),  M_1 = W_ov sum_p R_p^T A_p^{-1} R_p
     with R_p the selection matrices of the subdomain index sets, W_ov their
@@ -696,7 +696,7 @@ def test_projected_sequence_converges_with_fewer_iterations(cube8_problem):
 
 def test_coarse_operators_coincide_on_box_aligned_mesh():
     """With element planes on box planes J_L is continuous: the cell-wise
-    A_r (Eq. Aij), the Galerkin J~^T A J~ and the vertex-based J^T A J agree."""
+    A_r (Eq. (12)), the Galerkin J~^T A J~ and the vertex-based J^T A J agree."""
     m = meshes.cube(8, boxes=(4, 2, 4))
     Ps = {op: O.Problem(m.xyz, m.conn, m.part, m.boxes, coarse_operator=op)
           for op in ("broken", "galerkin", "vertex")}
