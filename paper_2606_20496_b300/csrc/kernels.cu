@@ -459,31 +459,6 @@ struct SmemSlots {
     __device__ __forceinline__ float4 h(int g) const { return hi[g * kTileElems + e]; }
     __device__ __forceinline__ float4 l(int g) const { return lo[g * kTileElems + e]; }
 };
-// The tile in shared memory arriving group by group: group g (hi and lo,
-// 8 KiB) completes its own mbarrier, and the first read of a group waits
-// (bounded) for it, so the arithmetic starts as soon as group 0 is in.  An
-// expired wait stops the slot (CGS_ERR_TIMEOUT) and the thread goes on with
-// whatever the buffer holds; the block waits for every copy before it exits.
-constexpr uint32_t kGroupBytes = kTileElems * sizeof(float4);   // 4 KiB
-struct SmemWaitSlots {
-    const float4* hi;
-    const float4* lo;
-    int e;
-    uint64_t* bars;
-    SolveScalars* S;
-    int limit;
-    __device__ __forceinline__ float4 h(int g) const {
-        bool ok = false;
-        for (int i = 0; i < limit && !ok; ++i) ok = mbar_try_wait(&bars[g], 0);
-        if (!ok && S) {
-            atomicAdd(&S->timeouts, 1);
-            S->status = CGS_ERR_TIMEOUT;
-            S->done = 1;
-        }
-        return hi[g * kTileElems + e];
-    }
-    __device__ __forceinline__ float4 l(int g) const { return lo[g * kTileElems + e]; }
-};
 // read-only streaming load (not volatile: the compiler may hoist it)
 __device__ __forceinline__ float4 ld_stream(const float4* p) {
     float4 v;
@@ -585,7 +560,7 @@ __device__ __forceinline__ void apply_pair_tiled_item(const DevMesh* __restrict_
     float2* ys = ps + kTileVerts;
     float4* sh_hi = reinterpret_cast<float4*>(ys + kTileVerts);
     float4* sh_lo = sh_hi + kGroups * kTileElems;
-    __shared__ uint64_t gbar[kGroups];
+    __shared__ uint64_t bar;
     CGS_ITEM_PROLOGUE();
     const float2* p2 = V.p2 + w.voff;
     const float* zf = static_cast<const float*>(V.z) + w.voff;
@@ -598,15 +573,10 @@ __device__ __forceinline__ void apply_pair_tiled_item(const DevMesh* __restrict_
     const float4* ghi = reinterpret_cast<const float4*>(M.at_hi) + (size_t)t * kGroups * kTileElems;
     const float4* glo = reinterpret_cast<const float4*>(M.at_lo) + (size_t)t * kGroups * kTileElems;
     if (kTma && threadIdx.x == 0) {
-        // one mbarrier per group (hi and lo, 8 KiB): the groups arrive in order
-#pragma unroll
-        for (int g = 0; g < kGroups; ++g) mbar_init(&gbar[g], 1);
-#pragma unroll
-        for (int g = 0; g < kGroups; ++g) {
-            mbar_expect_tx(&gbar[g], 2 * kGroupBytes);
-            bulk_copy_g2s(sh_hi + g * kTileElems, ghi + g * kTileElems, kGroupBytes, &gbar[g]);
-            bulk_copy_g2s(sh_lo + g * kTileElems, glo + g * kTileElems, kGroupBytes, &gbar[g]);
-        }
+        mbar_init(&bar, 1);
+        mbar_expect_tx(&bar, 2 * kTileSlotBytes);
+        bulk_copy_g2s(sh_hi, ghi, kTileSlotBytes, &bar);
+        bulk_copy_g2s(sh_lo, glo, kTileSlotBytes, &bar);
     }
     const int e0 = __ldg(&M.tile_ptr[t]), net = __ldg(&M.tile_ptr[t + 1]) - e0;
     const int v0 = __ldg(&M.tile_vptr[t]), nvt = __ldg(&M.tile_vptr[t + 1]) - v0;
@@ -645,11 +615,13 @@ __device__ __forceinline__ void apply_pair_tiled_item(const DevMesh* __restrict_
         }
     }
     __syncthreads();
-    const bool ok = true;
-    const SmemWaitSlots tslots{sh_hi, sh_lo, (int)threadIdx.x, gbar, S, wait_limit};
-    if (kTma && has_e) {
-        H = tslots.h(0);
-        L = tslots.l(0);
+    bool ok = true;
+    if (kTma) {
+        ok = __syncthreads_and(wait_tile(&bar, S, wait_limit)) != 0;   // one decision per block
+        if (ok && has_e) {
+            H = sh_hi[threadIdx.x];
+            L = sh_lo[threadIdx.x];
+        }
     }
     float eh = 0.0f, el = 0.0f;   // this thread's share of p.Ap
     if (ok && has_e) {
@@ -664,7 +636,7 @@ __device__ __forceinline__ void apply_pair_tiled_item(const DevMesh* __restrict_
             yl[k] = 0.0f;
         }
         if (kTma)
-            element_pair(tslots, H, L, xh, xl, yh, yl);
+            element_pair(SmemSlots{sh_hi, sh_lo, (int)threadIdx.x}, H, L, xh, xl, yh, yl);
         else
             element_pair(GlobalSlots{ghi, glo, (int)threadIdx.x}, H, L, xh, xl, yh, yl);
 #pragma unroll
@@ -681,14 +653,6 @@ __device__ __forceinline__ void apply_pair_tiled_item(const DevMesh* __restrict_
         }
     }
     __syncthreads();
-    if (kTma && threadIdx.x == 0) {
-        // every copy has landed before the block may exit (they all have,
-        // unless a wait above gave up)
-#pragma unroll
-        for (int g = 0; g < kGroups; ++g)
-            for (int i = 0; i < kWaitLimit; ++i)
-                if (mbar_try_wait(&gbar[g], 0)) break;
-    }
     if (ok) {
         for (int i = threadIdx.x; i < nvt; i += kBlock) {
             const uint32_t raw = __ldg(&M.tile_verts[v0 + i]);
@@ -1568,21 +1532,39 @@ __device__ __forceinline__ void restrict_hyb_item(const DevMesh* __restrict__ me
     const T* l = lin + w.voff;
     const int lane = threadIdx.x & 31;
     const int4 rg = __ldg(&M.hr_rng[q]);
-    T acc = T(0);
-    for (int i0 = rg.x + lane; i0 < rg.y; i0 += 128) {
-        int v[4];
-        decltype(hr_entry(M, 0, T(0))) jg[4];
+    using JG = decltype(hr_entry(M, 0, T(0)));
+    // software pipeline over rounds of four entries per lane: the entry
+    // loads of round k + 1 are issued before the gathers of round k are
+    // used, so the two dependent round trips of consecutive rounds overlap
+    int v[4];
+    JG jg[4];
+    auto load_round = [&](int i0, int (&vv)[4], JG (&jj)[4]) {
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             const int i = i0 + 32 * k;
-            v[k] = i < rg.y ? __ldg(&M.hr_vert[i]) : -1;
-            if (i < rg.y) jg[k] = hr_entry(M, i, T(0));
+            vv[k] = i < rg.y ? __ldg(&M.hr_vert[i]) : -1;
+            if (i < rg.y) jj[k] = hr_entry(M, i, T(0));
         }
+    };
+    load_round(rg.x + lane, v, jg);
+    T acc = T(0);
+    for (int i0 = rg.x + lane; i0 < rg.y; i0 += 128) {
+        T rv[4], lv[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            if (v[k] < 0) continue;
-            acc = fma(jg[k].x, __ldg(&r[v[k]]), acc);
-            acc = fma(-jg[k].y, __ldg(&l[v[k]]), acc);
+            rv[k] = v[k] >= 0 ? __ldg(&r[v[k]]) : T(0);
+            lv[k] = v[k] >= 0 ? __ldg(&l[v[k]]) : T(0);
+        }
+        JG cur[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) cur[k] = jg[k];
+        const bool live[4] = {v[0] >= 0, v[1] >= 0, v[2] >= 0, v[3] >= 0};
+        load_round(i0 + 128, v, jg);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (!live[k]) continue;
+            acc = fma(cur[k].x, rv[k], acc);
+            acc = fma(-cur[k].y, lv[k], acc);
         }
     }
     acc = warp_sum_t(acc);
