@@ -238,3 +238,35 @@ def workload_batch(count: int = 256, seed: int = 2) -> list:
         m = cube(int(n), perturb=0.15, seed=[seed, i], part_mode="mixed", name=f"batch{i}_n{int(n)}")
         out.append((m, rhs(m.nv, [seed, i, 1], count=4)))
     return out
+
+
+# ---------------------------------------------------------------------------
+# The p-multigrid wrap: spectral elements of order N on the same hexahedra.
+# Its nodes are numbered differently by every implementation, so the
+# right-hand side is a function of the node coordinates, not a list.
+# ---------------------------------------------------------------------------
+
+def sem_rhs(coords: np.ndarray, seed: int = 9, waves: int = 24, kmax: float = 40.0) -> np.ndarray:
+    """f(x) = sum_m a_m sin(k_m . x + phi_m) at the points coords (n, 3):
+    ``waves`` plane waves with wave numbers up to ``kmax`` (smooth and rough
+    components together), amplitudes N(0,1), phases U(0, 2 pi), all drawn
+    from ``default_rng(seed)``."""
+    rng = np.random.default_rng(seed)
+    k = rng.uniform(-kmax, kmax, size=(waves, 3))
+    a = rng.standard_normal(waves)
+    phi = rng.uniform(0.0, 2.0 * np.pi, size=waves)
+    return np.sin(np.asarray(coords, dtype=np.float64) @ k.T + phi) @ a
+
+
+def workload_sem() -> tuple:
+    """The 32^3 smoothly deformed cube with spectral elements of order 7 and
+    the schedule 7 -> 3 -> 1 (11,390,625 nodes at order 7); the order-1 level
+    is the 35,937-vertex coarse problem with its 8^3 boxes."""
+    m, _ = workload_cube32()
+    return m, (7, 3)
+
+
+def workload_sem_small() -> tuple:
+    """The 8^3 perturbed cube at order 7, schedule 7 -> 3 -> 1 (185,193 nodes)."""
+    m, _ = workload_cube8()
+    return m, (7, 3)
