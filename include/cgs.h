@@ -451,6 +451,82 @@ cgs_status cgs_server_stats(const cgs_server* server, size_t* arena_bytes, size_
                             int* queued);
 int64_t cgs_server_launches(const cgs_server* server);
 
+/* ---- p-multigrid wrap: spectral-element levels around the coarse solve ----
+ * The coarse-grid solve is the N = 1 level of a p-multigrid preconditioner
+ * for the spectral-element (SEM) Poisson problem of order N (Sec. 1, Sec. 5).
+ * A cgs_pmg holds the SEM levels of orders N_0 > N_1 > ... > 1 on the
+ * hexahedral mesh of a cgs_mesh, and applies the preconditioner of Eq. (13),
+ * additive between levels,
+ *     z = M_{N0}^-1 r + J_1 (M_{N1}^-1 r_1 + J_2 (... + J_c M_c J_c^T ...)),
+ * r_{l+1} = J_{l+1}^T r_l, where
+ *   - M_N^-1 = W_N sum_e R_{N,e}^T A~_{N,e}^-1 R_{N,e} (Eq. (14)) is the
+ *     element-local additive Schwarz smoother: R_{N,e} takes the element's
+ *     own (N+1)^3 nodes, A~ is the separable approximation of the element
+ *     problem solved by fast diagonalisation, W_N = 1 / (elements holding
+ *     the node);
+ *   - J from an order to the next finer one is element-wise tensor-product
+ *     Lagrange interpolation between the GLL nodes, averaged over the copies
+ *     of each fine node (J = W_f Q_f^T I Q_c), and J^T its transpose;
+ *   - M_c, at order 1, is ONE application of the mesh's two-level Schwarz
+ *     preconditioner (cgs_apply_preconditioner, in the mesh's form and
+ *     precision): inside a Krylov method the coarse problem needs no exact
+ *     solve (Sec. 3, opening paragraph).
+ * The SEM operator of order N is A_N = Q^T A_L Q with A^e = Dhat^T G^e Dhat,
+ * GLL quadrature at the nodes and the trilinear map of each hexahedron; every
+ * node of a boundary face is Dirichlet.  All arithmetic is float64.
+ *
+ * Levels are numbered 0 (order orders[0]) to n_orders (order 1, whose nodes
+ * are the mesh vertices in the mesh's own numbering).  Vectors of level l are
+ * float64 DEVICE arrays over its global nodes; Dirichlet entries are ignored
+ * on input and written 0 on output.  The global numbering of level l < n_orders
+ * starts with the mesh vertices, then the nodes inside edges, faces and
+ * elements; cgs_pmg_node_map gives it per element.
+ *
+ * cgs_pmg_setup: `mesh` must have the default Dirichlet set (boundary-face
+ *   vertices) and must outlive the cgs_pmg; xyz (nv*3) and conn (ne*8,
+ *   lexicographic vertex order) are the HOST arrays the mesh was set up
+ *   from (checked against its sizes; copied).  orders: n_orders (1..4) values,
+ *   strictly decreasing, each in [2, 8] (e.g. {7, 3} for 7 -> 3 -> 1).
+ *   Device memory per element at order N (p = N + 1): 6 p^3 doubles of
+ *   geometric factors, p^3 int32 node numbers and 3 p (p + 1) doubles of
+ *   smoother factors, plus about four doubles per global node; it is not
+ *   counted against the context's budget.  INVALID_ARG on a bad argument, INVALID_MESH on a
+ *   non-positive Jacobian at a GLL node, OOM.  Synchronous.
+ * cgs_pmg_info: order, global nodes and free (non-Dirichlet) nodes of a level.
+ * cgs_pmg_node_map: HOST array of ne*(N+1)^3 global node numbers, element by
+ *   element, local node (i, j, k) at i + (N+1)(j + (N+1) k); for level
+ *   n_orders this is conn.
+ * cgs_pmg_node_coords: HOST array of n_nodes*3 node coordinates.
+ * cgs_pmg_apply_A: y = A_N x on level l < n_orders.
+ * cgs_pmg_smooth: z = M_N^-1 r (Eq. (14)) on level l < n_orders.
+ * cgs_pmg_restrict: rc = J^T rf from level l to level l + 1.
+ * cgs_pmg_prolong: uf = J uc from level l + 1 to level l.
+ * cgs_pmg_apply_preconditioner: z = M r of Eq. (13) on level 0.
+ * cgs_pmg_solve: A_{N0} x = b on level 0 by flexible GMRES(restart) with
+ *   that preconditioner (Sec. 5: GMRES on the pressure, p-multigrid
+ *   preconditioned), x = 0 first, stopping at ||b - A x|| <= rtol ||b||
+ *   (the least-squares estimate inside a cycle, the true residual at every
+ *   restart); iters = products A z, relres as in cgs_solve_wrapped.
+ *   Synchronous; allocates (2 restart + 5) vectors of level 0 for the call.
+ *   NO_CONVERGENCE after maxit, BREAKDOWN on a non-finite value, TIMEOUT
+ *   when a bounded device wait of the coarse preconditioner expired.
+ * The single-step calls are asynchronous on `stream` and use work vectors of
+ * the cgs_pmg (calls on one cgs_pmg must not overlap).                     */
+typedef struct cgs_pmg cgs_pmg;
+cgs_status cgs_pmg_setup(cgs_mesh* mesh, const double* xyz, int64_t nv, const int32_t* conn, int64_t ne,
+                         const int32_t* orders, int n_orders, cgs_pmg** out);
+cgs_status cgs_pmg_free(cgs_pmg* pmg);
+cgs_status cgs_pmg_info(const cgs_pmg* pmg, int level, int* order, int64_t* n_nodes, int64_t* n_free);
+cgs_status cgs_pmg_node_map(const cgs_pmg* pmg, int level, int32_t* l2g);
+cgs_status cgs_pmg_node_coords(const cgs_pmg* pmg, int level, double* xyz);
+cgs_status cgs_pmg_apply_A(cgs_pmg* pmg, int level, const double* x, double* y, void* stream);
+cgs_status cgs_pmg_smooth(cgs_pmg* pmg, int level, const double* r, double* z, void* stream);
+cgs_status cgs_pmg_restrict(cgs_pmg* pmg, int level, const double* rf, double* rc, void* stream);
+cgs_status cgs_pmg_prolong(cgs_pmg* pmg, int level, const double* uc, double* uf, void* stream);
+cgs_status cgs_pmg_apply_preconditioner(cgs_pmg* pmg, const double* r, double* z, void* stream);
+cgs_status cgs_pmg_solve(cgs_pmg* pmg, const double* b, double* x, double rtol, int maxit, int restart,
+                         int* iters, double* relres, void* stream);
+
 const char* cgs_status_string(cgs_status s);
 const char* cgs_last_error(void);
 

@@ -41,6 +41,8 @@ EXPORTS = (
     "cgs_server_stats",
     "cgs_server_launches", "cgs_status_string",
     "cgs_last_error",
+    "cgs_pmg_setup", "cgs_pmg_free", "cgs_pmg_info", "cgs_pmg_node_map", "cgs_pmg_node_coords", "cgs_pmg_apply_A",
+    "cgs_pmg_smooth", "cgs_pmg_restrict", "cgs_pmg_prolong", "cgs_pmg_apply_preconditioner", "cgs_pmg_solve",
 )
 KERNEL_CLASSES = ("apply_A64", "apply_A32", "local", "restrict", "coarse", "interp", "pcg_xr", "pcg_dots",
                   "pcg_p", "other", "loop")
@@ -128,6 +130,17 @@ def load(path: str = LIB_PATH):
         "cgs_batch_tune": ([P, P], I32),
         "cgs_mesh_get_schedule": ([P, C.POINTER(Schedule)], I32),
         "cgs_mesh_set_schedule": ([P, C.POINTER(Schedule)], I32),
+        "cgs_pmg_setup": ([P, P, I64, P, I64, P, I32, C.POINTER(P)], I32),
+        "cgs_pmg_free": ([P], I32),
+        "cgs_pmg_info": ([P, I32, C.POINTER(I32), C.POINTER(I64), C.POINTER(I64)], I32),
+        "cgs_pmg_node_map": ([P, I32, P], I32),
+        "cgs_pmg_node_coords": ([P, I32, P], I32),
+        "cgs_pmg_apply_A": ([P, I32, P, P, P], I32),
+        "cgs_pmg_smooth": ([P, I32, P, P, P], I32),
+        "cgs_pmg_restrict": ([P, I32, P, P, P], I32),
+        "cgs_pmg_prolong": ([P, I32, P, P, P], I32),
+        "cgs_pmg_apply_preconditioner": ([P, P, P, P], I32),
+        "cgs_pmg_solve": ([P, P, P, D, I32, I32, C.POINTER(I32), C.POINTER(D), P], I32),
         "cgs_status_string": ([I32], C.c_char_p),
         "cgs_last_error": ([], C.c_char_p),
     }
@@ -479,6 +492,94 @@ def cgs_poll(server, ticket):
 
 def cgs_server_launches(server) -> int:
     return int(load().cgs_server_launches(server))
+
+
+# ---- p-multigrid wrap -------------------------------------------------------
+
+def cgs_pmg_setup(mesh, xyz, conn, orders=(7, 3)):
+    xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+    conn = np.ascontiguousarray(conn, dtype=np.int32)
+    ords = np.ascontiguousarray(orders, dtype=np.int32)
+    out = C.c_void_p()
+    _check(load().cgs_pmg_setup(mesh, _ptr(xyz), xyz.shape[0], _ptr(conn), conn.shape[0], _ptr(ords), len(ords),
+                                C.byref(out)), "cgs_pmg_setup")
+    return out
+
+
+def cgs_pmg_free(pmg):
+    _check(load().cgs_pmg_free(pmg), "cgs_pmg_free")
+
+
+def cgs_pmg_info(pmg, level) -> dict:
+    o, n, f = C.c_int(0), C.c_int64(0), C.c_int64(0)
+    _check(load().cgs_pmg_info(pmg, level, C.byref(o), C.byref(n), C.byref(f)), "cgs_pmg_info")
+    return {"order": o.value, "n_nodes": n.value, "n_free": f.value}
+
+
+def cgs_pmg_node_map(pmg, level, ne) -> np.ndarray:
+    p = cgs_pmg_info(pmg, level)["order"] + 1
+    out = np.empty((ne, p, p, p), dtype=np.int32)
+    _check(load().cgs_pmg_node_map(pmg, level, _ptr(out)), "cgs_pmg_node_map")
+    return out
+
+
+def cgs_pmg_node_coords(pmg, level) -> np.ndarray:
+    out = np.empty((cgs_pmg_info(pmg, level)["n_nodes"], 3), dtype=np.float64)
+    _check(load().cgs_pmg_node_coords(pmg, level, _ptr(out)), "cgs_pmg_node_coords")
+    return out
+
+
+def cgs_pmg_apply_A(pmg, level, x, y, stream=None):
+    _check(load().cgs_pmg_apply_A(pmg, level, _ptr(x), _ptr(y), _stream(stream)), "cgs_pmg_apply_A")
+
+
+def cgs_pmg_smooth(pmg, level, r, z, stream=None):
+    _check(load().cgs_pmg_smooth(pmg, level, _ptr(r), _ptr(z), _stream(stream)), "cgs_pmg_smooth")
+
+
+def cgs_pmg_restrict(pmg, level, rf, rc, stream=None):
+    _check(load().cgs_pmg_restrict(pmg, level, _ptr(rf), _ptr(rc), _stream(stream)), "cgs_pmg_restrict")
+
+
+def cgs_pmg_prolong(pmg, level, uc, uf, stream=None):
+    _check(load().cgs_pmg_prolong(pmg, level, _ptr(uc), _ptr(uf), _stream(stream)), "cgs_pmg_prolong")
+
+
+def cgs_pmg_apply_preconditioner(pmg, r, z, stream=None):
+    _check(load().cgs_pmg_apply_preconditioner(pmg, _ptr(r), _ptr(z), _stream(stream)),
+           "cgs_pmg_apply_preconditioner")
+
+
+def cgs_pmg_solve(pmg, b, x, rtol=1e-8, maxit=500, restart=30, stream=None,
+                  allow=(ERR_NO_CONVERGENCE, ERR_BREAKDOWN)):
+    """Flexible GMRES on the finest level with the p-multigrid preconditioner.
+    Returns (status, iters, relres)."""
+    it, rr = C.c_int(0), C.c_double(0.0)
+    st = load().cgs_pmg_solve(pmg, _ptr(b), _ptr(x), float(rtol), int(maxit), int(restart), C.byref(it),
+                              C.byref(rr), _stream(stream))
+    _check(st, "cgs_pmg_solve", allow)
+    return st, it.value, rr.value
+
+
+class PMG:
+    """Owning handle around cgs_pmg_setup / cgs_pmg_free."""
+
+    def __init__(self, mesh, xyz, conn, orders=(7, 3)):
+        self.handle = cgs_pmg_setup(mesh.handle if isinstance(mesh, Mesh) else mesh, xyz, conn, orders)
+        self.orders = tuple(orders)
+        self.ne = int(np.asarray(conn).shape[0])
+        self.levels = [cgs_pmg_info(self.handle, l) for l in range(len(self.orders) + 1)]
+
+    def free(self):
+        if self.handle is not None:
+            cgs_pmg_free(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.free()
 
 
 class Mesh:

@@ -1,0 +1,30 @@
+// Flexible GMRES on the device around any operator and preconditioner given
+// as callbacks (wrappers.cu): used by cgs_solve_wrapped on a coarse mesh and
+// by cgs_pmg_solve on the finest spectral-element level.
+#pragma once
+
+#include <cstdint>
+#include <functional>
+
+#include <cuda_runtime.h>
+
+#include "../../include/cgs.h"
+
+namespace cgs {
+
+struct KrylovOps {
+    int64_t n = 0;                      // vector length
+    const uint8_t* dir = nullptr;       // device, n: Dirichlet entries (taken as zero in every dot)
+    std::function<cgs_status(const double* x, double* y)> apply_A;
+    std::function<cgs_status(const double* r, double* z)> apply_M;
+};
+
+// Right-preconditioned flexible GMRES(restart) from x = 0 on device vectors:
+// the Arnoldi basis V of the preconditioned directions Z = M V (classical
+// Gram-Schmidt applied twice), Givens rotations on the host, x += Z y at each
+// restart.  iters = products A z; relres = ||b - A x|| / ||b|| of the last
+// restart's residual.  Allocates its (2 restart + 5) n doubles per call.
+cgs_status fgmres_device(const KrylovOps& ops, const double* b, double* x, double rtol, int maxit, int restart,
+                         int* iters, double* relres, cudaStream_t st);
+
+}  // namespace cgs

@@ -17,6 +17,7 @@
 
 #include "internal.h"
 #include "kernels.h"
+#include "krylov.h"
 
 using namespace cgs;
 
@@ -73,6 +74,121 @@ cgs_status dots(Dots& D, const double* X, int k, int64_t n, const double* v, con
 
 }  // namespace
 
+namespace cgs {
+
+cgs_status fgmres_device(const KrylovOps& ops, const double* b, double* x, double rtol, int maxit, int restart,
+                         int* iters, double* relres, cudaStream_t st) {
+    *iters = 0;
+    *relres = 0.0;
+    const int64_t n = ops.n;
+    const uint8_t* dir = ops.dir;
+    const int kmax = restart + 1;
+    Buffers buf;
+    Dots D;
+    double *bm, *r, *one, *coef, *V, *Z, *w;
+    WRAP_CUDA(buf.alloc(&D.partial, proj_partial_entries(kmax)));
+    WRAP_CUDA(buf.alloc(&D.out, kmax + 1));
+    WRAP_CUDA(buf.alloc(&bm, n));
+    WRAP_CUDA(buf.alloc(&r, n));
+    WRAP_CUDA(buf.alloc(&one, 1));
+    WRAP_CUDA(buf.alloc(&coef, kmax));
+    WRAP_CUDA(buf.alloc(&V, (size_t)(restart + 1) * n));
+    WRAP_CUDA(buf.alloc(&Z, (size_t)restart * n));
+    WRAP_CUDA(buf.alloc(&w, n));
+    const double h_one = 1.0;
+    WRAP_CUDA(cudaMemcpyAsync(one, &h_one, sizeof(double), cudaMemcpyHostToDevice, st));
+    // b with its Dirichlet entries zeroed, x = 0
+    launch_proj_combine(n, b, dir, 0.0, one, 0, nullptr, bm, st);
+    WRAP_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n, st));
+    WRAP_OK(dots(D, nullptr, 0, n, bm, dir, st));
+    const double nb = std::sqrt(D.host[0]);
+    if (nb == 0.0) return CGS_OK;
+    const int m = restart;
+    std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), yv(m);
+    auto Hij = [&](int i, int j) -> double& { return H[(size_t)i * m + j]; };
+    int its = 0;
+    cgs_status result = CGS_ERR_NO_CONVERGENCE;
+    for (;;) {
+        // r = bm - A x
+        WRAP_OK(ops.apply_A(x, w));
+        launch_proj_combine(n, bm, dir, -1.0, one, 1, w, r, st);
+        WRAP_OK(dots(D, nullptr, 0, n, r, dir, st));
+        const double beta = std::sqrt(D.host[0]);
+        *relres = beta / nb;
+        *iters = its;
+        if (!std::isfinite(beta)) {
+            result = CGS_ERR_BREAKDOWN;
+            break;
+        }
+        if (beta <= rtol * nb) {
+            result = CGS_OK;
+            break;
+        }
+        if (its >= maxit) break;
+        launch_proj_combine(n, nullptr, dir, 1.0 / beta, one, 1, r, V, st);
+        std::fill(H.begin(), H.end(), 0.0);
+        std::fill(g.begin(), g.end(), 0.0);
+        g[0] = beta;
+        int used = 0;
+        bool breakdown = false;
+        for (int j = 0; j < m; ++j) {
+            double* Vj = V + (size_t)j * n;
+            double* Zj = Z + (size_t)j * n;
+            WRAP_OK(ops.apply_M(Vj, Zj));
+            WRAP_OK(ops.apply_A(Zj, w));
+            ++its;
+            // two Gram-Schmidt passes against V_0..V_j
+            for (int pass = 0; pass < 2; ++pass) {
+                WRAP_OK(dots(D, V, j + 1, n, w, dir, st));
+                for (int i = 0; i <= j; ++i) Hij(i, j) += D.host[i];
+                launch_proj_combine(n, w, dir, -1.0, D.out, j + 1, V, w, st);
+            }
+            WRAP_OK(dots(D, nullptr, 0, n, w, dir, st));
+            const double hn = std::sqrt(D.host[0]);
+            Hij(j + 1, j) = hn;
+            if (!std::isfinite(hn)) {
+                breakdown = true;
+                break;
+            }
+            // previous rotations on column j, then the new one
+            for (int i = 0; i < j; ++i) {
+                const double a = Hij(i, j), c = Hij(i + 1, j);
+                Hij(i, j) = cs[i] * a + sn[i] * c;
+                Hij(i + 1, j) = -sn[i] * a + cs[i] * c;
+            }
+            const double a = Hij(j, j), c = Hij(j + 1, j), rho = std::hypot(a, c);
+            cs[j] = rho > 0.0 ? a / rho : 1.0;
+            sn[j] = rho > 0.0 ? c / rho : 0.0;
+            Hij(j, j) = rho;
+            Hij(j + 1, j) = 0.0;
+            g[j + 1] = -sn[j] * g[j];
+            g[j] = cs[j] * g[j];
+            used = j + 1;
+            if (std::fabs(g[j + 1]) <= rtol * nb || its >= maxit || hn == 0.0) break;
+            launch_proj_combine(n, nullptr, dir, 1.0 / hn, one, 1, w, V + (size_t)(j + 1) * n, st);
+        }
+        if (breakdown) {
+            result = CGS_ERR_BREAKDOWN;
+            break;
+        }
+        // y = R^{-1} g by back substitution, x += Z y
+        for (int i = used - 1; i >= 0; --i) {
+            double s = g[i];
+            for (int k = i + 1; k < used; ++k) s -= Hij(i, k) * yv[k];
+            yv[i] = Hij(i, i) != 0.0 ? s / Hij(i, i) : 0.0;
+        }
+        WRAP_CUDA(cudaMemcpyAsync(coef, yv.data(), sizeof(double) * used, cudaMemcpyHostToDevice, st));
+        launch_proj_combine(n, x, dir, 1.0, coef, used, Z, x, st);
+    }
+    WRAP_CUDA(cudaStreamSynchronize(st));
+    WRAP_CUDA(cudaGetLastError());
+    if (result == CGS_ERR_NO_CONVERGENCE) set_last_error("maxit reached before the tolerance");
+    if (result == CGS_ERR_BREAKDOWN) set_last_error("non-finite value in the wrapped iteration");
+    return result;
+}
+
+}  // namespace cgs
+
 extern "C" cgs_status cgs_solve_wrapped(cgs_mesh* mesh, const double* b, double* x, cgs_method method, double rtol,
                                         int maxit, int restart, int* iters, double* relres, void* stream) {
     if (!mesh || !b || !x || !iters || !relres || maxit < 0 || !(rtol > 0.0)) {
@@ -94,38 +210,32 @@ extern "C" cgs_status cgs_solve_wrapped(cgs_mesh* mesh, const double* b, double*
     WRAP_CUDA(cudaSetDevice(mesh_device(mesh)));
     const int64_t n = mesh_dev(mesh).nv;
     const uint8_t* dir = mesh_dir(mesh);
-    const int kmax = method == CGS_METHOD_FGMRES ? restart + 1 : 1;
-    Buffers buf;
-    Dots D;
-    double *bm, *r, *y, *one, *coef, *V = nullptr, *Z = nullptr, *w = nullptr;
-    WRAP_CUDA(buf.alloc(&D.partial, proj_partial_entries(kmax)));
-    WRAP_CUDA(buf.alloc(&D.out, kmax + 1));
-    WRAP_CUDA(buf.alloc(&bm, n));
-    WRAP_CUDA(buf.alloc(&r, n));
-    WRAP_CUDA(buf.alloc(&y, n));
-    WRAP_CUDA(buf.alloc(&one, 1));
-    WRAP_CUDA(buf.alloc(&coef, kmax));
-    if (method == CGS_METHOD_FGMRES) {
-        WRAP_CUDA(buf.alloc(&V, (size_t)(restart + 1) * n));
-        WRAP_CUDA(buf.alloc(&Z, (size_t)restart * n));
-        WRAP_CUDA(buf.alloc(&w, n));
-    }
-    const double h_one = 1.0;
-    WRAP_CUDA(cudaMemcpyAsync(one, &h_one, sizeof(double), cudaMemcpyHostToDevice, st));
-    // b with its Dirichlet entries zeroed, x = 0
-    launch_proj_combine(n, b, dir, 0.0, one, 0, nullptr, bm, st);
-    WRAP_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n, st));
-    WRAP_OK(dots(D, nullptr, 0, n, bm, dir, st));
-    const double nb = std::sqrt(D.host[0]);
-    if (nb == 0.0) return CGS_OK;
-    // r = bm - A x
-    auto residual = [&]() -> cgs_status {
-        WRAP_OK(cgs_apply_A(mesh, x, y, st));
-        launch_proj_combine(n, bm, dir, -1.0, one, 1, y, r, st);
-        return CGS_OK;
-    };
     cgs_status result = CGS_ERR_NO_CONVERGENCE;
-    if (method == CGS_METHOD_RICHARDSON) {
+    if (method == CGS_METHOD_FGMRES) {
+        KrylovOps ops;
+        ops.n = n;
+        ops.dir = dir;
+        ops.apply_A = [&](const double* u, double* y) { return cgs_apply_A(mesh, u, y, stream); };
+        ops.apply_M = [&](const double* r, double* z) { return cgs_apply_preconditioner(mesh, r, z, stream); };
+        result = fgmres_device(ops, b, x, rtol, maxit, restart, iters, relres, st);
+        if (result != CGS_OK && result != CGS_ERR_NO_CONVERGENCE && result != CGS_ERR_BREAKDOWN) return result;
+    } else {
+        Buffers buf;
+        Dots D;
+        double *bm, *r, *y, *one;
+        WRAP_CUDA(buf.alloc(&D.partial, proj_partial_entries(1)));
+        WRAP_CUDA(buf.alloc(&D.out, 2));
+        WRAP_CUDA(buf.alloc(&bm, n));
+        WRAP_CUDA(buf.alloc(&r, n));
+        WRAP_CUDA(buf.alloc(&y, n));
+        WRAP_CUDA(buf.alloc(&one, 1));
+        const double h_one = 1.0;
+        WRAP_CUDA(cudaMemcpyAsync(one, &h_one, sizeof(double), cudaMemcpyHostToDevice, st));
+        launch_proj_combine(n, b, dir, 0.0, one, 0, nullptr, bm, st);
+        WRAP_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n, st));
+        WRAP_OK(dots(D, nullptr, 0, n, bm, dir, st));
+        const double nb = std::sqrt(D.host[0]);
+        if (nb == 0.0) return CGS_OK;
         // Schwarz-Richardson, undamped: x += M (b - A x) until the true
         // residual meets the tolerance; iters = updates of x
         WRAP_CUDA(cudaMemcpyAsync(r, bm, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
@@ -145,91 +255,14 @@ extern "C" cgs_status cgs_solve_wrapped(cgs_mesh* mesh, const double* b, double*
             if (k == maxit) break;
             WRAP_OK(cgs_apply_preconditioner(mesh, r, y, st));
             launch_vec_add(n, x, y, x, st);
-            WRAP_OK(residual());
+            WRAP_OK(cgs_apply_A(mesh, x, y, st));
+            launch_proj_combine(n, bm, dir, -1.0, one, 1, y, r, st);
         }
-    } else {
-        // flexible GMRES(restart): Arnoldi on the preconditioned directions
-        // Z_j = M V_j with classical Gram-Schmidt applied twice (each pass one
-        // multi-dot launch), Givens rotations on the host, x += Z y
-        const int m = restart;
-        std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), yv(m);
-        auto Hij = [&](int i, int j) -> double& { return H[(size_t)i * m + j]; };
-        int its = 0;
-        for (;;) {
-            WRAP_OK(residual());
-            WRAP_OK(dots(D, nullptr, 0, n, r, dir, st));
-            const double beta = std::sqrt(D.host[0]);
-            *relres = beta / nb;
-            *iters = its;
-            if (!std::isfinite(beta)) {
-                result = CGS_ERR_BREAKDOWN;
-                break;
-            }
-            if (beta <= rtol * nb) {
-                result = CGS_OK;
-                break;
-            }
-            if (its >= maxit) break;
-            const double inv_beta = 1.0 / beta;
-            launch_proj_combine(n, nullptr, dir, inv_beta, one, 1, r, V, st);
-            std::fill(H.begin(), H.end(), 0.0);
-            std::fill(g.begin(), g.end(), 0.0);
-            g[0] = beta;
-            int used = 0;
-            bool breakdown = false;
-            for (int j = 0; j < m; ++j) {
-                double* Vj = V + (size_t)j * n;
-                double* Zj = Z + (size_t)j * n;
-                WRAP_OK(cgs_apply_preconditioner(mesh, Vj, Zj, st));
-                WRAP_OK(cgs_apply_A(mesh, Zj, w, st));
-                ++its;
-                // two Gram-Schmidt passes against V_0..V_j
-                for (int pass = 0; pass < 2; ++pass) {
-                    WRAP_OK(dots(D, V, j + 1, n, w, dir, st));
-                    for (int i = 0; i <= j; ++i) Hij(i, j) += D.host[i];
-                    launch_proj_combine(n, w, dir, -1.0, D.out, j + 1, V, w, st);
-                }
-                WRAP_OK(dots(D, nullptr, 0, n, w, dir, st));
-                const double hn = std::sqrt(D.host[0]);
-                Hij(j + 1, j) = hn;
-                if (!std::isfinite(hn)) {
-                    breakdown = true;
-                    break;
-                }
-                // previous rotations on column j, then the new one
-                for (int i = 0; i < j; ++i) {
-                    const double a = Hij(i, j), c = Hij(i + 1, j);
-                    Hij(i, j) = cs[i] * a + sn[i] * c;
-                    Hij(i + 1, j) = -sn[i] * a + cs[i] * c;
-                }
-                const double a = Hij(j, j), c = Hij(j + 1, j), rho = std::hypot(a, c);
-                cs[j] = rho > 0.0 ? a / rho : 1.0;
-                sn[j] = rho > 0.0 ? c / rho : 0.0;
-                Hij(j, j) = rho;
-                Hij(j + 1, j) = 0.0;
-                g[j + 1] = -sn[j] * g[j];
-                g[j] = cs[j] * g[j];
-                used = j + 1;
-                if (std::fabs(g[j + 1]) <= rtol * nb || its >= maxit || hn == 0.0) break;
-                launch_proj_combine(n, nullptr, dir, 1.0 / hn, one, 1, w, V + (size_t)(j + 1) * n, st);
-            }
-            if (breakdown) {
-                result = CGS_ERR_BREAKDOWN;
-                break;
-            }
-            // y = R^{-1} g by back substitution, x += Z y
-            for (int i = used - 1; i >= 0; --i) {
-                double s = g[i];
-                for (int k = i + 1; k < used; ++k) s -= Hij(i, k) * yv[k];
-                yv[i] = Hij(i, i) != 0.0 ? s / Hij(i, i) : 0.0;
-            }
-            WRAP_CUDA(cudaMemcpyAsync(coef, yv.data(), sizeof(double) * used, cudaMemcpyHostToDevice, st));
-            launch_proj_combine(n, x, dir, 1.0, coef, used, Z, x, st);
-        }
-        // the final residual was formed at the top of the loop
+        WRAP_CUDA(cudaStreamSynchronize(st));
+        WRAP_CUDA(cudaGetLastError());
+        if (result == CGS_ERR_NO_CONVERGENCE) set_last_error("maxit reached before the tolerance");
+        if (result == CGS_ERR_BREAKDOWN) set_last_error("non-finite value in the wrapped iteration");
     }
-    WRAP_CUDA(cudaStreamSynchronize(st));
-    WRAP_CUDA(cudaGetLastError());
     // a bounded device wait that expired inside the single steps
     const cgs_status ws = cgs_mesh_step_status(mesh, stream);
     if (ws != CGS_OK) return ws;
