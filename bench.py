@@ -283,6 +283,13 @@ def oracle_iters_per_solve():
     return int(json.load(open(p))["solve"]["iters"])
 
 
+def pmg_oracle_iters():
+    """The oracle's GMRES products for the p-multigrid workload, stored by
+    tests/golden/make_pmg_golden.py (None when the file is absent)."""
+    p = os.path.join(ROOT, "tests", "golden", "pmg_oracle.json")
+    return int(json.load(open(p))["solve"]["iters"]) if os.path.exists(p) else None
+
+
 def start_oracle_sample(iters):
     """Start the cpu_baseline sample in a fresh single-threaded interpreter
     (it runs on the host cores while the GPU work proceeds)."""
@@ -492,6 +499,18 @@ def run_ours(args):
                        "schedule": sch, "roofline": roof, "kernels": per}
         h.free()
 
+    # ---- the p-multigrid wrap: order-7 SEM levels around the coarse solve -------------
+    pmg = None
+    if args.pmg:
+        from paper_2606_20496_b300 import run_pmg
+        pmg = run_pmg.run(ctx, solves=3)
+        pmg["iters_oracle"] = pmg_oracle_iters()
+        ax = pmg["steps"]["ax_N%d" % pmg["orders"][0]]
+        pmg["roofline"] = {"kernel": "sem_ax_kernel<%d>" % (pmg["orders"][0] + 1), "bound": "alu",
+                           "achieved": ax["tflops"], "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                           "frac": ax["fp64_frac"], "traffic": None,
+                           "peak_note": "FP64 FMA issue rate, 2 per clock per SM at 2032 MHz"}
+
     # ---- batched form (256 meshes x 4 right-hand sides in one graph) -----------------
     batch = None
     if args.batch:
@@ -521,7 +540,7 @@ def run_ours(args):
                           "delta_fp16": forms["fp16"]["iters_delta_vs_fp64"],
                           "oracle": oracle_iters_per_solve()},
                 "fp32_bulk": forms["fp32"], "fp16_local": forms["fp16"],
-                "batch": batch, "serve": serving,
+                "batch": batch, "serve": serving, "pmg": pmg,
                 "roofline": roofline, "kernels": kernels64,
                 "cpu_baseline": cpu,
                 "e2e": {"value": whole_job_rate(world, e2e_steps, e2e_ms), "unit": UNIT,
@@ -544,6 +563,7 @@ def main():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-batch", dest="batch", action="store_false", help="skip the batched form")
+    ap.add_argument("--no-pmg", dest="pmg", action="store_false", help="skip the p-multigrid wrap")
     ap.add_argument("--serve-seconds", type=float, default=10.0, help="serving stream length (0: skip)")
     ap.add_argument("--serve-rate", type=float, default=2000.0)
     ap.add_argument("--serve-pool", type=int, default=64)

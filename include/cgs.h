@@ -507,7 +507,9 @@ int64_t cgs_server_launches(const cgs_server* server);
  *   preconditioned), x = 0 first, stopping at ||b - A x|| <= rtol ||b||
  *   (the least-squares estimate inside a cycle, the true residual at every
  *   restart); iters = products A z, relres as in cgs_solve_wrapped.
- *   Synchronous; allocates (2 restart + 5) vectors of level 0 for the call.
+ *   Synchronous.  The first solve, and one with a larger restart than any
+ *   before, allocates the GMRES workspace (about 2 restart + 3 vectors of
+ *   level 0), which the cgs_pmg keeps until cgs_pmg_free.
  *   NO_CONVERGENCE after maxit, BREAKDOWN on a non-finite value, TIMEOUT
  *   when a bounded device wait of the coarse preconditioner expired.
  * The single-step calls are asynchronous on `stream` and use work vectors of

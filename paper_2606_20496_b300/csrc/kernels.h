@@ -20,6 +20,12 @@ void launch_proj_dots(const double* X, int k, int64_t n, const double* v, const 
 // out = base (Dirichlet entries zeroed; nullptr = 0) + s sum_{j<k} coef[j] Y_j
 void launch_proj_combine(int64_t n, const double* base, const uint8_t* dir, double s, const double* coef, int k,
                          const double* Y, double* out, cudaStream_t st);
+// w -= sum_{j<k} coef[j] X_j (coef on the device), Dirichlet entries of w
+// zero; then, with dots, out[j] = X_j . w (j < k) and out[k] = w . w of the
+// updated w (false, nothing launched, for k > 32), without dots out[0] =
+// w . w.  `partial` holds proj_partial_entries(k) doubles.  Two kernels.
+bool launch_gs_update(const double* X, int k, int64_t n, const double* coef, const uint8_t* dir, double* w,
+                      double* partial, double* out, bool dots, cudaStream_t st);
 void launch_vec_scale(int64_t n, double* a, double alpha, cudaStream_t st);
 void launch_vec_add(int64_t n, const double* a, const double* b, double* out, cudaStream_t st);
 

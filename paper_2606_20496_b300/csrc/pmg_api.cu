@@ -27,9 +27,13 @@ struct cgs_pmg {
     int32_t* l2g1 = nullptr;                       // order 1: conn, Dirichlet vertices encoded
     double* r1 = nullptr;
     double* z1 = nullptr;
+    bool f32 = false;                              // float smoothers and transfers
+    double* gmres_work = nullptr;                  // GMRES workspace, kept across solves
+    size_t gmres_doubles = 0;
     std::vector<void*> allocs;
     ~cgs_pmg() {
         for (void* p : allocs) cudaFree(p);
+        if (gmres_work) cudaFree(gmres_work);
     }
 };
 
@@ -69,42 +73,42 @@ cudaError_t upload(cgs_pmg* P, T** dst, const T* src, size_t n) {
 
 int n_levels(const cgs_pmg* P) { return (int)P->orders.size(); }
 
-// the next-coarser level's size, map and order-plus-one
-void next_level(const cgs_pmg* P, int l, int& pc, const int32_t*& l2g_c, int64_t& ng_c, double*& r_c,
-                double*& z_c) {
+// The next-coarser level of level l: nodes per direction, map, size, work
+// vectors and whether they are float (order 1: the mesh's float64 vectors).
+struct Next {
+    int pc;
+    const int32_t* l2g;
+    int64_t ng;
+    void* r;
+    void* z;
+    bool f32;
+    bool sem;    // a spectral-element level (else order 1)
+};
+Next next_level(const cgs_pmg* P, int l) {
     if (l + 1 < n_levels(P)) {
         const SemDevLevel& C = P->lev[l + 1];
-        pc = C.p;
-        l2g_c = C.l2g;
-        ng_c = C.ng;
-        r_c = C.r;
-        z_c = C.z;
-    } else {
-        pc = 2;
-        l2g_c = P->l2g1;
-        ng_c = P->nv;
-        r_c = P->r1;
-        z_c = P->z1;
+        return {C.p, C.l2g, C.ng, C.r, C.z, C.f32, true};
     }
+    return {2, P->l2g1, P->nv, P->r1, P->z1, false, false};
 }
 
-// z = M r on level l and below (Eq. (13)), z overwritten
-cgs_status pmg_level(cgs_pmg* P, int l, const double* r, double* z, cudaStream_t st) {
+size_t vec_bytes(int64_t n, bool f32) { return (size_t)n * (f32 ? sizeof(float) : sizeof(double)); }
+
+// z = M r on level l and below (Eq. (13)), z overwritten; the vectors of
+// level l are float when l > 0 and the level is f32
+cgs_status pmg_level(cgs_pmg* P, int l, const void* r, void* z, cudaStream_t st) {
     const SemDevLevel& L = P->lev[l];
-    PMG_CUDA(cudaMemsetAsync(z, 0, sizeof(double) * L.ng, st));
-    launch_sem_fdm(L, P->ne, r, z, st);
-    int pc;
-    const int32_t* l2g_c;
-    int64_t ng_c;
-    double *r_c, *z_c;
-    next_level(P, l, pc, l2g_c, ng_c, r_c, z_c);
-    PMG_CUDA(cudaMemsetAsync(r_c, 0, sizeof(double) * ng_c, st));
-    launch_sem_restrict(L, pc, l2g_c, P->ne, r, r_c, st);
-    if (l + 1 < n_levels(P))
-        PMG_OK(pmg_level(P, l + 1, r_c, z_c, st));
+    const bool vf = l > 0 && L.f32;
+    PMG_CUDA(cudaMemsetAsync(z, 0, vec_bytes(L.ng, vf), st));
+    launch_sem_fdm(L, P->ne, r, z, vf, st);
+    const Next c = next_level(P, l);
+    PMG_CUDA(cudaMemsetAsync(c.r, 0, vec_bytes(c.ng, c.f32), st));
+    launch_sem_restrict(L, c.pc, c.l2g, P->ne, r, c.r, vf, c.f32, st);
+    if (c.sem)
+        PMG_OK(pmg_level(P, l + 1, c.r, c.z, st));
     else
-        PMG_OK(cgs_apply_preconditioner(P->mesh, r_c, z_c, st));
-    launch_sem_prolong(L, pc, l2g_c, P->ne, z_c, z, st);
+        PMG_OK(cgs_apply_preconditioner(P->mesh, static_cast<const double*>(c.r), static_cast<double*>(c.z), st));
+    launch_sem_prolong(L, c.pc, c.l2g, P->ne, c.z, z, c.f32, vf, st);
     PMG_CUDA(cudaGetLastError());
     return CGS_OK;
 }
@@ -144,6 +148,10 @@ cgs_status cgs_pmg_setup(cgs_mesh* mesh, const double* xyz, int64_t nv, const in
     P->orders.assign(orders, orders + n_orders);
     P->xyz.assign(xyz, xyz + nv * 3);
     P->conn.assign(conn, conn + ne * 8);
+    // the smoothers and transfers follow the coarse mesh's precision: float64
+    // under the FP64 form, float under the mixed forms
+    const bool f32 = mesh_prec(mesh) != CGS_FP64;
+    P->f32 = f32;
     std::vector<SemHostLevel> H(n_orders);
     for (int l = 0; l < n_orders; ++l) {
         const std::string err = sem_build_level(orders[l], xyz, nv, conn, ne, H[l]);
@@ -177,9 +185,29 @@ cgs_status cgs_pmg_setup(cgs_mesh* mesh, const double* xyz, int64_t nv, const in
             xc = {-1.0, 1.0};
         lagrange_interp(xc, h.x, I);
         PMG_CUDA(upload(P.get(), &d.I_next, I.data(), I.size()));
+        d.f32 = f32;
+        if (f32) {
+            auto to_f = [](const std::vector<double>& v) { return std::vector<float>(v.begin(), v.end()); };
+            const std::vector<float> S32 = to_f(h.S), lam32 = to_f(h.lam), w32 = to_f(h.inv_mult), I32 = to_f(I);
+            PMG_CUDA(upload(P.get(), &d.S32, S32.data(), S32.size()));
+            PMG_CUDA(upload(P.get(), &d.lam32, lam32.data(), lam32.size()));
+            PMG_CUDA(upload(P.get(), &d.inv_mult32, w32.data(), w32.size()));
+            PMG_CUDA(upload(P.get(), &d.I_next32, I32.data(), I32.size()));
+        }
         if (l > 0) {
-            PMG_CUDA(upload<double>(P.get(), &d.r, nullptr, (size_t)h.ng));
-            PMG_CUDA(upload<double>(P.get(), &d.z, nullptr, (size_t)h.ng));
+            if (f32) {
+                float *r, *z;
+                PMG_CUDA(upload<float>(P.get(), &r, nullptr, (size_t)h.ng));
+                PMG_CUDA(upload<float>(P.get(), &z, nullptr, (size_t)h.ng));
+                d.r = r;
+                d.z = z;
+            } else {
+                double *r, *z;
+                PMG_CUDA(upload<double>(P.get(), &r, nullptr, (size_t)h.ng));
+                PMG_CUDA(upload<double>(P.get(), &z, nullptr, (size_t)h.ng));
+                d.r = r;
+                d.z = z;
+            }
         }
         P->host_l2g[l] = std::move(h.l2g);
         h = SemHostLevel();   // release the host copies level by level
@@ -254,7 +282,7 @@ cgs_status cgs_pmg_smooth(cgs_pmg* pmg, int level, const double* r, double* z, v
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const SemDevLevel& L = pmg->lev[level];
     PMG_CUDA(cudaMemsetAsync(z, 0, sizeof(double) * L.ng, st));
-    launch_sem_fdm(L, pmg->ne, r, z, st);
+    launch_sem_fdm(L, pmg->ne, r, z, false, st);
     PMG_CUDA(cudaGetLastError());
     return CGS_OK;
 }
@@ -262,13 +290,9 @@ cgs_status cgs_pmg_smooth(cgs_pmg* pmg, int level, const double* r, double* z, v
 cgs_status cgs_pmg_restrict(cgs_pmg* pmg, int level, const double* rf, double* rc, void* stream) {
     if (!pmg || !rf || !rc || level < 0 || level >= n_levels(pmg)) return pmg_fail(CGS_ERR_INVALID_ARG, "bad argument");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    int pc;
-    const int32_t* l2g_c;
-    int64_t ng_c;
-    double *r_c, *z_c;
-    next_level(pmg, level, pc, l2g_c, ng_c, r_c, z_c);
-    PMG_CUDA(cudaMemsetAsync(rc, 0, sizeof(double) * ng_c, st));
-    launch_sem_restrict(pmg->lev[level], pc, l2g_c, pmg->ne, rf, rc, st);
+    const Next c = next_level(pmg, level);
+    PMG_CUDA(cudaMemsetAsync(rc, 0, sizeof(double) * c.ng, st));
+    launch_sem_restrict(pmg->lev[level], c.pc, c.l2g, pmg->ne, rf, rc, false, false, st);
     PMG_CUDA(cudaGetLastError());
     return CGS_OK;
 }
@@ -276,14 +300,10 @@ cgs_status cgs_pmg_restrict(cgs_pmg* pmg, int level, const double* rf, double* r
 cgs_status cgs_pmg_prolong(cgs_pmg* pmg, int level, const double* uc, double* uf, void* stream) {
     if (!pmg || !uc || !uf || level < 0 || level >= n_levels(pmg)) return pmg_fail(CGS_ERR_INVALID_ARG, "bad argument");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    int pc;
-    const int32_t* l2g_c;
-    int64_t ng_c;
-    double *r_c, *z_c;
-    next_level(pmg, level, pc, l2g_c, ng_c, r_c, z_c);
+    const Next c = next_level(pmg, level);
     const SemDevLevel& L = pmg->lev[level];
     PMG_CUDA(cudaMemsetAsync(uf, 0, sizeof(double) * L.ng, st));
-    launch_sem_prolong(L, pc, l2g_c, pmg->ne, uc, uf, st);
+    launch_sem_prolong(L, c.pc, c.l2g, pmg->ne, uc, uf, false, false, st);
     PMG_CUDA(cudaGetLastError());
     return CGS_OK;
 }
@@ -303,6 +323,20 @@ cgs_status cgs_pmg_solve(cgs_pmg* pmg, const double* b, double* x, double rtol, 
     KrylovOps ops;
     ops.n = pmg->lev[0].ng;
     ops.dir = pmg->lev[0].dir;
+    // the workspace of the largest restart so far stays with the cgs_pmg
+    const size_t need = fgmres_work_doubles(ops.n, restart);
+    if (pmg->gmres_doubles < need) {
+        if (pmg->gmres_work) {
+            PMG_CUDA(cudaStreamSynchronize(st));
+            cudaFree(pmg->gmres_work);
+            pmg->gmres_work = nullptr;
+            pmg->gmres_doubles = 0;
+        }
+        PMG_CUDA(cudaMalloc(&pmg->gmres_work, need * sizeof(double)));
+        pmg->gmres_doubles = need;
+    }
+    ops.work = pmg->gmres_work;
+    ops.work_doubles = pmg->gmres_doubles;
     ops.apply_A = [&](const double* u, double* y) { return cgs_pmg_apply_A(pmg, 0, u, y, stream); };
     ops.apply_M = [&](const double* r, double* z) { return pmg_level(pmg, 0, r, z, st); };
     const cgs_status s = fgmres_device(ops, b, x, rtol, maxit, restart, iters, relres, st);

@@ -1,5 +1,5 @@
 // Kernels of the p-multigrid wrap's spectral-element levels (Sec. 1, Sec. 5,
-// Eqs. (13) and (14)), float64, one block of p x p threads per element:
+// Eqs. (13) and (14)), one block of p x p threads per element:
 // thread (i, j) holds the column k = 0..p-1 of its element in registers and
 // exchanges layers through shared memory for the contractions along i and j.
 //
@@ -10,8 +10,15 @@
 //
 // Element-local to global maps store a Dirichlet node g as -(g + 1): gathers
 // read zero there and scatters skip it, so Dirichlet entries are ignored on
-// input and never written.  Scatters are float64 atomic adds (the order of
-// the additions, and so the last bits, varies from run to run).
+// input and never written.  Scatters are atomic adds (the order of the
+// additions, and so the last bits, varies from run to run).
+//
+// The operator is float64 always (it forms the outer residual).  The
+// smoother and the transfers run in float64 under an FP64 coarse mesh and in
+// float under the mixed forms' meshes (the multilevel preconditioner needs no
+// more: the outer GMRES is flexible), with level vectors in float below the
+// finest level; the finest level's r and z, and the order-1 vectors handed to
+// the coarse preconditioner, stay float64.
 #include <cuda_runtime.h>
 
 #include "sem.h"
@@ -76,37 +83,44 @@ __global__ void __launch_bounds__(P * P) sem_ax_kernel(const int32_t* __restrict
     }
 }
 
-// z += W sum_e R_e^T S_e (lam_x + lam_y + lam_z)^-1 S_e^T R_e r
-template <int P>
-__global__ void __launch_bounds__(P * P) sem_fdm_kernel(const int32_t* __restrict__ l2g, const double* __restrict__ S,
-                                                       const double* __restrict__ lam,
-                                                       const double* __restrict__ inv_mult,
-                                                       const double* __restrict__ r, double* __restrict__ z) {
+__device__ __forceinline__ double mad(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float mad(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+template <class T, class V>
+__device__ __forceinline__ T load_as(const V* __restrict__ v, int32_t g) {
+    return g >= 0 ? (T)__ldg(&v[g]) : T(0);
+}
+
+// z += W sum_e R_e^T S_e (lam_x + lam_y + lam_z)^-1 S_e^T R_e r, arithmetic in
+// T (float64, or float for the mixed forms' preconditioner), vectors in V
+template <int P, class T, class V>
+__global__ void __launch_bounds__(P * P) sem_fdm_kernel(const int32_t* __restrict__ l2g, const T* __restrict__ S,
+                                                       const T* __restrict__ lam, const T* __restrict__ inv_mult,
+                                                       const V* __restrict__ r, V* __restrict__ z) {
     constexpr int P2 = P * P, P3 = P * P * P;
-    __shared__ double sS[3][P][P];     // S_d[node][mode]
-    __shared__ double sl[3][P];
-    __shared__ double sx[P][P][P];
+    __shared__ T sS[3][P][P];     // S_d[node][mode]
+    __shared__ T sl[3][P];
+    __shared__ T sx[P][P][P];
     const int e = blockIdx.x;
     const int i = threadIdx.x % P, j = threadIdx.x / P;
-    const double* Se = S + (size_t)e * 3 * P2;
+    const T* Se = S + (size_t)e * 3 * P2;
 #pragma unroll
     for (int d = 0; d < 3; ++d) sS[d][j][i] = __ldg(&Se[d * P2 + j * P + i]);
     if (threadIdx.x < 3 * P) sl[threadIdx.x / P][threadIdx.x % P] = __ldg(&lam[(size_t)e * 3 * P + threadIdx.x]);
     const int32_t* L = l2g + (size_t)e * P3;
     int32_t gk[P];
-    double a[P], b[P];
+    T a[P], b[P];
 #pragma unroll
     for (int k = 0; k < P; ++k) {
         gk[k] = __ldg(&L[k * P2 + j * P + i]);
-        a[k] = gather(r, gk[k]);
+        a[k] = load_as<T>(r, gk[k]);
     }
     __syncthreads();
     // S_z^T along k (registers)
 #pragma unroll
     for (int k = 0; k < P; ++k) {
-        double t = 0.0;
+        T t = 0;
 #pragma unroll
-        for (int m = 0; m < P; ++m) t = fma(sS[2][m][k], a[m], t);
+        for (int m = 0; m < P; ++m) t = mad(sS[2][m][k], a[m], t);
         b[k] = t;
     }
     // S_y^T along j
@@ -115,9 +129,9 @@ __global__ void __launch_bounds__(P * P) sem_fdm_kernel(const int32_t* __restric
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < P; ++k) {
-        double t = 0.0;
+        T t = 0;
 #pragma unroll
-        for (int m = 0; m < P; ++m) t = fma(sS[1][m][j], sx[k][m][i], t);
+        for (int m = 0; m < P; ++m) t = mad(sS[1][m][j], sx[k][m][i], t);
         a[k] = t;
     }
     __syncthreads();
@@ -127,9 +141,9 @@ __global__ void __launch_bounds__(P * P) sem_fdm_kernel(const int32_t* __restric
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < P; ++k) {
-        double t = 0.0;
+        T t = 0;
 #pragma unroll
-        for (int m = 0; m < P; ++m) t = fma(sS[0][m][i], sx[k][j][m], t);
+        for (int m = 0; m < P; ++m) t = mad(sS[0][m][i], sx[k][j][m], t);
         b[k] = t / (sl[0][i] + sl[1][j] + sl[2][k]);
     }
     __syncthreads();
@@ -139,9 +153,9 @@ __global__ void __launch_bounds__(P * P) sem_fdm_kernel(const int32_t* __restric
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < P; ++k) {
-        double t = 0.0;
+        T t = 0;
 #pragma unroll
-        for (int m = 0; m < P; ++m) t = fma(sS[0][i][m], sx[k][j][m], t);
+        for (int m = 0; m < P; ++m) t = mad(sS[0][i][m], sx[k][j][m], t);
         a[k] = t;
     }
     __syncthreads();
@@ -151,61 +165,61 @@ __global__ void __launch_bounds__(P * P) sem_fdm_kernel(const int32_t* __restric
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < P; ++k) {
-        double t = 0.0;
+        T t = 0;
 #pragma unroll
-        for (int m = 0; m < P; ++m) t = fma(sS[1][j][m], sx[k][m][i], t);
+        for (int m = 0; m < P; ++m) t = mad(sS[1][j][m], sx[k][m][i], t);
         b[k] = t;
     }
     // S_z along k, then W and the scatter
 #pragma unroll
     for (int k = 0; k < P; ++k) {
         if (gk[k] < 0) continue;
-        double t = 0.0;
+        T t = 0;
 #pragma unroll
-        for (int m = 0; m < P; ++m) t = fma(sS[2][k][m], b[m], t);
-        atomicAdd(&z[gk[k]], __ldg(&inv_mult[gk[k]]) * t);
+        for (int m = 0; m < P; ++m) t = mad(sS[2][k][m], b[m], t);
+        atomicAdd(&z[gk[k]], (V)(__ldg(&inv_mult[gk[k]]) * t));
     }
 }
 
 // r_c += Q_c^T I^T Q_f W_f r_f over one element: the fine block is p x p
 // threads, the coarse element has pc <= P nodes per direction
-template <int P>
+template <int P, class T, class VF, class VC>
 __global__ void __launch_bounds__(P * P) sem_restrict_kernel(const int32_t* __restrict__ l2g_f,
-                                                            const double* __restrict__ inv_mult_f,
-                                                            const double* __restrict__ Ig, int pc,
+                                                            const T* __restrict__ inv_mult_f,
+                                                            const T* __restrict__ Ig, int pc,
                                                             const int32_t* __restrict__ l2g_c,
-                                                            const double* __restrict__ rf, double* __restrict__ rc) {
+                                                            const VF* __restrict__ rf, VC* __restrict__ rc) {
     constexpr int P2 = P * P, P3 = P * P * P;
-    __shared__ double sI[P][P];        // sI[fine][coarse]
-    __shared__ double s1[P][P][P];     // [kc][j][i]
-    __shared__ double s2[P][P][P];     // [kc][jc][i]
+    __shared__ T sI[P][P];        // sI[fine][coarse]
+    __shared__ T s1[P][P][P];     // [kc][j][i]
+    __shared__ T s2[P][P][P];     // [kc][jc][i]
     const int e = blockIdx.x;
     const int i = threadIdx.x % P, j = threadIdx.x / P;
     if (i < pc) sI[j][i] = __ldg(&Ig[j * pc + i]);
     const int32_t* L = l2g_f + (size_t)e * P3;
-    double a[P];
+    T a[P];
 #pragma unroll
     for (int k = 0; k < P; ++k) {
         const int32_t g = __ldg(&L[k * P2 + j * P + i]);
-        a[k] = g >= 0 ? __ldg(&rf[g]) * __ldg(&inv_mult_f[g]) : 0.0;
+        a[k] = g >= 0 ? (T)__ldg(&rf[g]) * __ldg(&inv_mult_f[g]) : T(0);
     }
     __syncthreads();
     // I^T along k
 #pragma unroll
     for (int kc = 0; kc < P; ++kc) {
         if (kc >= pc) break;
-        double t = 0.0;
+        T t = 0;
 #pragma unroll
-        for (int k = 0; k < P; ++k) t = fma(sI[k][kc], a[k], t);
+        for (int k = 0; k < P; ++k) t = mad(sI[k][kc], a[k], t);
         s1[kc][j][i] = t;
     }
     __syncthreads();
     // I^T along j: thread (i, jc) for jc < pc
     if (j < pc) {
         for (int kc = 0; kc < pc; ++kc) {
-            double t = 0.0;
+            T t = 0;
 #pragma unroll
-            for (int m = 0; m < P; ++m) t = fma(sI[m][j], s1[kc][m][i], t);
+            for (int m = 0; m < P; ++m) t = mad(sI[m][j], s1[kc][m][i], t);
             s2[kc][j][i] = t;
         }
     }
@@ -215,26 +229,26 @@ __global__ void __launch_bounds__(P * P) sem_restrict_kernel(const int32_t* __re
         const int pc2 = pc * pc;
         const int32_t* Lc = l2g_c + (size_t)e * pc2 * pc;
         for (int kc = 0; kc < pc; ++kc) {
-            double t = 0.0;
+            T t = 0;
 #pragma unroll
-            for (int m = 0; m < P; ++m) t = fma(sI[m][i], s2[kc][j][m], t);
+            for (int m = 0; m < P; ++m) t = mad(sI[m][i], s2[kc][j][m], t);
             const int32_t g = __ldg(&Lc[kc * pc2 + j * pc + i]);
-            if (g >= 0) atomicAdd(&rc[g], t);
+            if (g >= 0) atomicAdd(&rc[g], (VC)t);
         }
     }
 }
 
 // z_f += W_f Q_f^T I Q_c u_c over one element
-template <int P>
+template <int P, class T, class VC, class VF>
 __global__ void __launch_bounds__(P * P) sem_prolong_kernel(const int32_t* __restrict__ l2g_f,
-                                                           const double* __restrict__ inv_mult_f,
-                                                           const double* __restrict__ Ig, int pc,
+                                                           const T* __restrict__ inv_mult_f,
+                                                           const T* __restrict__ Ig, int pc,
                                                            const int32_t* __restrict__ l2g_c,
-                                                           const double* __restrict__ uc, double* __restrict__ zf) {
+                                                           const VC* __restrict__ uc, VF* __restrict__ zf) {
     constexpr int P2 = P * P, P3 = P * P * P;
-    __shared__ double sI[P][P];        // sI[fine][coarse]
-    __shared__ double sc[P][P][P];     // coarse values [kc][jc][ic]
-    __shared__ double s1[P][P][P];     // [kc][jc][i]
+    __shared__ T sI[P][P];        // sI[fine][coarse]
+    __shared__ T sc[P][P][P];     // coarse values [kc][jc][ic]
+    __shared__ T s1[P][P][P];     // [kc][jc][i]
     const int e = blockIdx.x;
     const int i = threadIdx.x % P, j = threadIdx.x / P;
     if (i < pc) sI[j][i] = __ldg(&Ig[j * pc + i]);
@@ -242,25 +256,25 @@ __global__ void __launch_bounds__(P * P) sem_prolong_kernel(const int32_t* __res
     const int32_t* Lc = l2g_c + (size_t)e * pc2 * pc;
     for (int q = threadIdx.x; q < pc2 * pc; q += P2) {
         const int kc = q / pc2, jc = (q / pc) % pc, ic = q % pc;
-        sc[kc][jc][ic] = gather(uc, __ldg(&Lc[q]));
+        sc[kc][jc][ic] = load_as<T>(uc, __ldg(&Lc[q]));
     }
     __syncthreads();
     // I along i: thread (i, jc)
     if (j < pc) {
         for (int kc = 0; kc < pc; ++kc) {
-            double t = 0.0;
-            for (int m = 0; m < pc; ++m) t = fma(sI[i][m], sc[kc][j][m], t);
+            T t = 0;
+            for (int m = 0; m < pc; ++m) t = mad(sI[i][m], sc[kc][j][m], t);
             s1[kc][j][i] = t;
         }
     }
     __syncthreads();
     // I along j (registers over kc), then along k
-    double b[P];
+    T b[P];
 #pragma unroll
     for (int kc = 0; kc < P; ++kc) {
-        double t = 0.0;
+        T t = 0;
         if (kc < pc)
-            for (int m = 0; m < pc; ++m) t = fma(sI[j][m], s1[kc][m][i], t);
+            for (int m = 0; m < pc; ++m) t = mad(sI[j][m], s1[kc][m][i], t);
         b[kc] = t;
     }
     const int32_t* L = l2g_f + (size_t)e * P3;
@@ -268,11 +282,11 @@ __global__ void __launch_bounds__(P * P) sem_prolong_kernel(const int32_t* __res
     for (int k = 0; k < P; ++k) {
         const int32_t g = __ldg(&L[k * P2 + j * P + i]);
         if (g < 0) continue;
-        double t = 0.0;
+        T t = 0;
 #pragma unroll
         for (int m = 0; m < P; ++m)
-            if (m < pc) t = fma(sI[k][m], b[m], t);
-        atomicAdd(&zf[g], __ldg(&inv_mult_f[g]) * t);
+            if (m < pc) t = mad(sI[k][m], b[m], t);
+        atomicAdd(&zf[g], (VF)(__ldg(&inv_mult_f[g]) * t));
     }
 }
 
@@ -287,6 +301,18 @@ __global__ void __launch_bounds__(P * P) sem_prolong_kernel(const int32_t* __res
         case 9: KERNEL<9><<<grid, 81, 0, st>>>(__VA_ARGS__); break;                     \
         default: break;                                                                \
     }
+// one launch per supported p (orders 2..8)
+#define SEM_CASES(p, LAUNCH)                                                           \
+    switch (p) {                                                                       \
+        case 3: LAUNCH(3); break;                                                      \
+        case 4: LAUNCH(4); break;                                                      \
+        case 5: LAUNCH(5); break;                                                      \
+        case 6: LAUNCH(6); break;                                                      \
+        case 7: LAUNCH(7); break;                                                      \
+        case 8: LAUNCH(8); break;                                                      \
+        case 9: LAUNCH(9); break;                                                      \
+        default: break;                                                                \
+    }
 
 }  // namespace
 
@@ -296,24 +322,81 @@ void launch_sem_ax(const SemDevLevel& L, int64_t ne, const double* x, double* y,
     SEM_DISPATCH(L.p, sem_ax_kernel, L.l2g, L.G, L.D, x, y);
 }
 
-void launch_sem_fdm(const SemDevLevel& L, int64_t ne, const double* r, double* z, cudaStream_t st) {
-    if (ne == 0) return;
+namespace {
+
+template <class T, class V>
+void fdm_typed(const SemDevLevel& L, int64_t ne, const T* S, const T* lam, const T* w, const void* r, void* z,
+               cudaStream_t st) {
     const dim3 grid((unsigned)ne);
-    SEM_DISPATCH(L.p, sem_fdm_kernel, L.l2g, L.S, L.lam, L.inv_mult, r, z);
+    const V* rv = static_cast<const V*>(r);
+    V* zv = static_cast<V*>(z);
+#define SEM_FDM(p) sem_fdm_kernel<p, T, V><<<grid, p * p, 0, st>>>(L.l2g, S, lam, w, rv, zv)
+    SEM_CASES(L.p, SEM_FDM)
+#undef SEM_FDM
 }
 
-void launch_sem_restrict(const SemDevLevel& F, int pc, const int32_t* l2g_c, int64_t ne, const double* rf,
-                         double* rc, cudaStream_t st) {
+}  // namespace
+
+void launch_sem_fdm(const SemDevLevel& L, int64_t ne, const void* r, void* z, bool vec_f32, cudaStream_t st) {
     if (ne == 0) return;
-    const dim3 grid((unsigned)ne);
-    SEM_DISPATCH(F.p, sem_restrict_kernel, F.l2g, F.inv_mult, F.I_next, pc, l2g_c, rf, rc);
+    if (!L.f32)
+        fdm_typed<double, double>(L, ne, L.S, L.lam, L.inv_mult, r, z, st);
+    else if (vec_f32)
+        fdm_typed<float, float>(L, ne, L.S32, L.lam32, L.inv_mult32, r, z, st);
+    else
+        fdm_typed<float, double>(L, ne, L.S32, L.lam32, L.inv_mult32, r, z, st);
 }
 
-void launch_sem_prolong(const SemDevLevel& F, int pc, const int32_t* l2g_c, int64_t ne, const double* uc,
-                        double* zf, cudaStream_t st) {
-    if (ne == 0) return;
+namespace {
+
+template <class T, class VF, class VC>
+void transfer_typed(bool restrict_, const SemDevLevel& F, const T* w, const T* I, int pc, const int32_t* l2g_c,
+                    int64_t ne, const void* in, void* out, cudaStream_t st) {
     const dim3 grid((unsigned)ne);
-    SEM_DISPATCH(F.p, sem_prolong_kernel, F.l2g, F.inv_mult, F.I_next, pc, l2g_c, uc, zf);
+    if (restrict_) {
+        const VF* a = static_cast<const VF*>(in);
+        VC* b = static_cast<VC*>(out);
+#define SEM_R(p) sem_restrict_kernel<p, T, VF, VC><<<grid, p * p, 0, st>>>(F.l2g, w, I, pc, l2g_c, a, b)
+        SEM_CASES(F.p, SEM_R)
+#undef SEM_R
+    } else {
+        const VC* a = static_cast<const VC*>(in);
+        VF* b = static_cast<VF*>(out);
+#define SEM_P(p) sem_prolong_kernel<p, T, VC, VF><<<grid, p * p, 0, st>>>(F.l2g, w, I, pc, l2g_c, a, b)
+        SEM_CASES(F.p, SEM_P)
+#undef SEM_P
+    }
+}
+
+void transfer(bool restrict_, const SemDevLevel& F, int pc, const int32_t* l2g_c, int64_t ne, const void* in,
+              void* out, bool f_f32, bool c_f32, cudaStream_t st) {
+    if (ne == 0) return;
+    if (!F.f32) {
+        transfer_typed<double, double, double>(restrict_, F, F.inv_mult, F.I_next, pc, l2g_c, ne, in, out, st);
+        return;
+    }
+    const float* w = F.inv_mult32;
+    const float* I = F.I_next32;
+    if (!f_f32 && !c_f32)
+        transfer_typed<float, double, double>(restrict_, F, w, I, pc, l2g_c, ne, in, out, st);
+    else if (!f_f32 && c_f32)
+        transfer_typed<float, double, float>(restrict_, F, w, I, pc, l2g_c, ne, in, out, st);
+    else if (f_f32 && c_f32)
+        transfer_typed<float, float, float>(restrict_, F, w, I, pc, l2g_c, ne, in, out, st);
+    else
+        transfer_typed<float, float, double>(restrict_, F, w, I, pc, l2g_c, ne, in, out, st);
+}
+
+}  // namespace
+
+void launch_sem_restrict(const SemDevLevel& F, int pc, const int32_t* l2g_c, int64_t ne, const void* rf, void* rc,
+                         bool f_f32, bool c_f32, cudaStream_t st) {
+    transfer(true, F, pc, l2g_c, ne, rf, rc, f_f32, c_f32, st);
+}
+
+void launch_sem_prolong(const SemDevLevel& F, int pc, const int32_t* l2g_c, int64_t ne, const void* uc, void* zf,
+                        bool c_f32, bool f_f32, cudaStream_t st) {
+    transfer(false, F, pc, l2g_c, ne, uc, zf, f_f32, c_f32, st);
 }
 
 }  // namespace cgs

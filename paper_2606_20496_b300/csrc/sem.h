@@ -66,21 +66,28 @@ struct SemDevLevel {
     double* lam = nullptr;
     double* D = nullptr;
     double* I_next = nullptr;       // p x p_next interpolation to the next (coarser) level
-    double* r = nullptr;            // work vectors of this level (not used on level 0)
-    double* z = nullptr;
+    // float copies for the float smoother and transfers (f32 set)
+    bool f32 = false;
+    float* S32 = nullptr;
+    float* lam32 = nullptr;
+    float* inv_mult32 = nullptr;
+    float* I_next32 = nullptr;
+    void* r = nullptr;              // work vectors of this level (levels below the finest):
+    void* z = nullptr;              // float when f32, else float64
 };
 
-// Launchers (sem.cu).  Vectors are float64 over a level's global nodes;
-// Dirichlet entries are skipped on input and never written.
-// y += A_n x (y cleared by the caller)
+// Launchers (sem.cu).  Dirichlet entries are skipped on input and never
+// written.  Vector types: float64, or float where the flag says so (only
+// with L.f32 / F.f32).
+// y += A_n x (float64; y cleared by the caller)
 void launch_sem_ax(const SemDevLevel& L, int64_t ne, const double* x, double* y, cudaStream_t st);
 // z += W sum_e R_e^T A~_e^-1 R_e r (Eq. (14))
-void launch_sem_fdm(const SemDevLevel& L, int64_t ne, const double* r, double* z, cudaStream_t st);
+void launch_sem_fdm(const SemDevLevel& L, int64_t ne, const void* r, void* z, bool vec_f32, cudaStream_t st);
 // rc += J^T rf = Q_c^T I^T Q_f W_f rf; coarse l2g of pc^3 entries per element
-void launch_sem_restrict(const SemDevLevel& F, int pc, const int32_t* l2g_c, int64_t ne, const double* rf,
-                         double* rc, cudaStream_t st);
+void launch_sem_restrict(const SemDevLevel& F, int pc, const int32_t* l2g_c, int64_t ne, const void* rf, void* rc,
+                         bool f_f32, bool c_f32, cudaStream_t st);
 // zf += J uc = W_f Q_f^T I Q_c uc
-void launch_sem_prolong(const SemDevLevel& F, int pc, const int32_t* l2g_c, int64_t ne, const double* uc,
-                        double* zf, cudaStream_t st);
+void launch_sem_prolong(const SemDevLevel& F, int pc, const int32_t* l2g_c, int64_t ne, const void* uc, void* zf,
+                        bool c_f32, bool f_f32, cudaStream_t st);
 
 }  // namespace cgs

@@ -76,6 +76,14 @@ cgs_status dots(Dots& D, const double* X, int k, int64_t n, const double* v, con
 
 namespace cgs {
 
+size_t fgmres_work_doubles(int64_t n, int restart) {
+    const size_t kmax = (size_t)restart + 1;
+    // every piece rounded up to 32 doubles (256-byte alignment)
+    auto r32 = [](size_t x) { return (x + 31) / 32 * 32; };
+    return r32(proj_partial_entries((int)kmax)) + r32(kmax + 1) + 3 * r32((size_t)n) + r32(1) + r32(kmax) +
+           r32((size_t)(restart + 1) * n) + r32((size_t)restart * n);
+}
+
 cgs_status fgmres_device(const KrylovOps& ops, const double* b, double* x, double rtol, int maxit, int restart,
                          int* iters, double* relres, cudaStream_t st) {
     *iters = 0;
@@ -86,15 +94,33 @@ cgs_status fgmres_device(const KrylovOps& ops, const double* b, double* x, doubl
     Buffers buf;
     Dots D;
     double *bm, *r, *one, *coef, *V, *Z, *w;
-    WRAP_CUDA(buf.alloc(&D.partial, proj_partial_entries(kmax)));
-    WRAP_CUDA(buf.alloc(&D.out, kmax + 1));
-    WRAP_CUDA(buf.alloc(&bm, n));
-    WRAP_CUDA(buf.alloc(&r, n));
-    WRAP_CUDA(buf.alloc(&one, 1));
-    WRAP_CUDA(buf.alloc(&coef, kmax));
-    WRAP_CUDA(buf.alloc(&V, (size_t)(restart + 1) * n));
-    WRAP_CUDA(buf.alloc(&Z, (size_t)restart * n));
-    WRAP_CUDA(buf.alloc(&w, n));
+    if (ops.work && ops.work_doubles >= fgmres_work_doubles(n, restart)) {
+        auto r32 = [](size_t v) { return (v + 31) / 32 * 32; };
+        double* p = ops.work;
+        auto take = [&](double** q, size_t cnt) {
+            *q = p;
+            p += r32(cnt);
+        };
+        take(&D.partial, proj_partial_entries(kmax));
+        take(&D.out, kmax + 1);
+        take(&bm, n);
+        take(&r, n);
+        take(&w, n);
+        take(&one, 1);
+        take(&coef, kmax);
+        take(&V, (size_t)(restart + 1) * n);
+        take(&Z, (size_t)restart * n);
+    } else {
+        WRAP_CUDA(buf.alloc(&D.partial, proj_partial_entries(kmax)));
+        WRAP_CUDA(buf.alloc(&D.out, kmax + 1));
+        WRAP_CUDA(buf.alloc(&bm, n));
+        WRAP_CUDA(buf.alloc(&r, n));
+        WRAP_CUDA(buf.alloc(&one, 1));
+        WRAP_CUDA(buf.alloc(&coef, kmax));
+        WRAP_CUDA(buf.alloc(&V, (size_t)(restart + 1) * n));
+        WRAP_CUDA(buf.alloc(&Z, (size_t)restart * n));
+        WRAP_CUDA(buf.alloc(&w, n));
+    }
     const double h_one = 1.0;
     WRAP_CUDA(cudaMemcpyAsync(one, &h_one, sizeof(double), cudaMemcpyHostToDevice, st));
     // b with its Dirichlet entries zeroed, x = 0
@@ -137,14 +163,23 @@ cgs_status fgmres_device(const KrylovOps& ops, const double* b, double* x, doubl
             WRAP_OK(ops.apply_M(Vj, Zj));
             WRAP_OK(ops.apply_A(Zj, w));
             ++its;
-            // two Gram-Schmidt passes against V_0..V_j
+            // classical Gram-Schmidt against V_0..V_j, repeated once when the
+            // first pass cancels more than half of w's norm (the
+            // Daniel-Gragg-Kaufman-Stewart test, eta = 1/sqrt(2)); each pass is
+            // the dots (with ||w||^2 before) and the correction (with ||w||^2
+            // after)
+            double hn = 0.0;
             for (int pass = 0; pass < 2; ++pass) {
                 WRAP_OK(dots(D, V, j + 1, n, w, dir, st));
                 for (int i = 0; i <= j; ++i) Hij(i, j) += D.host[i];
-                launch_proj_combine(n, w, dir, -1.0, D.out, j + 1, V, w, st);
+                const double before = D.host[j + 1];
+                launch_gs_update(V, j + 1, n, D.out, dir, w, D.partial, D.out, false, st);
+                double after = 0.0;
+                WRAP_CUDA(cudaMemcpyAsync(&after, D.out, sizeof(double), cudaMemcpyDeviceToHost, st));
+                WRAP_CUDA(cudaStreamSynchronize(st));
+                hn = std::sqrt(after);
+                if (!(after < 0.5 * before)) break;
             }
-            WRAP_OK(dots(D, nullptr, 0, n, w, dir, st));
-            const double hn = std::sqrt(D.host[0]);
             Hij(j + 1, j) = hn;
             if (!std::isfinite(hn)) {
                 breakdown = true;

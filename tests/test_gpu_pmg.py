@@ -195,3 +195,33 @@ def test_single_level_schedule(ctx):
         z = torch.empty(f.ng, dtype=torch.float64, device="cuda")
         cgs.cgs_pmg_apply_preconditioner(g.handle, dev(to_gpu_numbering(r, f, gm, f.ng)), z)
         assert_close(local(host(z), gm), local(P.apply_M(r), f.l2g), 1e-11)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_float_smoothers_under_a_mixed_coarse_mesh(ctx, built, name):
+    """Under an FP32-bulk coarse mesh the smoothers and transfers run in float
+    (level vectors below the finest in float): every entry of M r within
+    2e-5 max|M r| of the FP64 oracle (float rounding of six contractions of
+    length p and of the FP32-bulk coarse sweep), GMRES within one product of
+    the oracle's FP64 count, and the true residual at the tolerance."""
+    m, _, _, P, maps = built(name)
+    orders = CASES[name][1]
+    f = P.fine
+    with cgs.Mesh(ctx, m.xyz, m.conn, part=m.part, boxes=m.boxes, prec="fp32") as h, \
+            cgs.PMG(h, m.xyz, m.conn, orders) as g:
+        gm = cgs.cgs_pmg_node_map(g.handle, 0, m.ne)
+        assert np.array_equal(gm, maps[0])
+        r = rand_level(P, 0, 70)
+        z = torch.empty(f.ng, dtype=torch.float64, device="cuda")
+        cgs.cgs_pmg_smooth(g.handle, 0, dev(to_gpu_numbering(r, f, gm, f.ng)), z)
+        assert_close(local(host(z), gm), local(P.smoothers[0].apply(r), f.l2g), 1e-5)
+        cgs.cgs_pmg_apply_preconditioner(g.handle, dev(to_gpu_numbering(r, f, gm, f.ng)), z)
+        assert_close(local(host(z), gm), local(P.apply_M(r), f.l2g), 2e-5)
+        b = np.where(f.dir, 0.0, meshes.sem_rhs(f.node_coords()))
+        _, its_or, _, _ = P.solve(b, rtol=1e-8, maxit=300, restart=30)
+        x = torch.empty(f.ng, dtype=torch.float64, device="cuda")
+        st, its, rel = cgs.cgs_pmg_solve(g.handle, dev(to_gpu_numbering(b, f, gm, f.ng)), x, rtol=1e-8)
+        assert st == cgs.OK and rel <= 1e-8 and abs(its - its_or) <= 1, (st, its, its_or)
+        xg = np.zeros(f.ng)
+        xg[f.l2g.ravel()] = local(host(x), gm).ravel()
+        assert np.linalg.norm(b - f.apply_A(xg)) <= 1.01e-8 * np.linalg.norm(b)
