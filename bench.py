@@ -10,9 +10,11 @@ the precision of the paper's Schwarz solves).  One step = one complete coarse
 solve of one N(0,1) right-hand side.  Beside it, on the same mesh: the FP32
 bulk and FP16 local forms (rate, iterations, difference from the FP64
 solution); the batched form (256 perturbed cubes x 4 right-hand sides in one
-graph) against the FP64 per-request path; and the serving form (a 10 s
-Poisson stream at 2,000 req/s over a 64-mesh pool) against the FP64
-per-request path.
+graph) against the FP64 per-request path; the serving form (a 10 s Poisson
+stream at 2,000 req/s over a 64-mesh pool) against the FP64 per-request
+path; and the p-multigrid wrap (GMRES on the order-7 spectral-element Poisson
+problem of the 32^3 deformed cube, 11.4 M nodes, schedule 7 -> 3 -> 1, with
+this solver as the order-1 level), with float64 and with float smoothers.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -209,7 +211,7 @@ def measured_peaks():
     return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0}, "fallback"
 
 
-def traffic_for(kernel_class, workload_key):
+def traffic_for(kernel_class, workload_key, source="kernels.cu"):
     """dram read+write bytes per launch from a committed ncu summary, if one
     exists for this kernel class and workload, taken with the current kernel
     source (else None)."""
@@ -222,7 +224,7 @@ def traffic_for(kernel_class, workload_key):
         if not ent:
             return None
         import hashlib
-        h = hashlib.sha256(open(os.path.join(ROOT, "paper_2606_20496_b300", "csrc", "kernels.cu"), "rb").read())
+        h = hashlib.sha256(open(os.path.join(ROOT, "paper_2606_20496_b300", "csrc", source), "rb").read())
         return ent["bytes_per_launch"] if ent.get("source_hash") == h.hexdigest()[:16] else None
     except Exception:
         return None
@@ -503,13 +505,15 @@ def run_ours(args):
     pmg = None
     if args.pmg:
         from paper_2606_20496_b300 import run_pmg
-        pmg = run_pmg.run(ctx, solves=3)
-        pmg["iters_oracle"] = pmg_oracle_iters()
-        ax = pmg["steps"]["ax_N%d" % pmg["orders"][0]]
-        pmg["roofline"] = {"kernel": "sem_ax_kernel<%d>" % (pmg["orders"][0] + 1), "bound": "alu",
-                           "achieved": ax["tflops"], "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                           "frac": ax["fp64_frac"], "traffic": None,
-                           "peak_note": "FP64 FMA issue rate, 2 per clock per SM at 2032 MHz"}
+        pmg = {"iters_oracle": pmg_oracle_iters()}
+        for prec in ("fp64", "fp32"):
+            r = run_pmg.run(ctx, solves=3, prec=prec)
+            ax = r["steps"]["ax_N%d" % r["orders"][0]]
+            r["roofline"] = {"kernel": "sem_ax_kernel<%d>" % (r["orders"][0] + 1), "bound": "alu",
+                             "achieved": ax["tflops"], "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                             "frac": ax["fp64_frac"], "traffic": traffic_for("sem_ax", "pmg_cube32_order7", "sem.cu"),
+                             "peak_note": "FP64 FMA issue rate, 2 per clock per SM at 2032 MHz"}
+            pmg["fp64_smoothers" if prec == "fp64" else "fp32_smoothers"] = r
 
     # ---- batched form (256 meshes x 4 right-hand sides in one graph) -----------------
     batch = None

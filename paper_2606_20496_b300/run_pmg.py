@@ -120,6 +120,33 @@ def run(ctx, small: bool = False, solves: int = 3, rtol: float = 1e-8, restart: 
     return out
 
 
+def profile_target(ctx, mode: str, prec: str, maxit: int, small: bool = False) -> dict:
+    """A short run for a profiler: `solve` = one GMRES solve of at most maxit
+    products (restart 30); `steps` = three launches each of the finest
+    level's operator and smoother."""
+    import torch
+
+    from . import cgs, meshes
+    m, orders = meshes.workload_sem_small() if small else meshes.workload_sem()
+    h = cgs.Mesh(ctx, m.xyz, m.conn, part=m.part, boxes=m.boxes, prec=prec)
+    g = cgs.PMG(h, m.xyz, m.conn, orders)
+    b = torch.as_tensor(meshes.sem_rhs(cgs.cgs_pmg_node_coords(g.handle, 0)), device="cuda")
+    y = torch.empty_like(b)
+    out = {"mode": mode, "prec": prec}
+    if mode == "solve":
+        st, its, rel = cgs.cgs_pmg_solve(g.handle, b, y, rtol=1e-12, maxit=maxit, restart=30)
+        out.update({"iters": its, "relres": rel})
+    else:
+        for _ in range(3):
+            cgs.cgs_pmg_apply_A(g.handle, 0, b, y)
+        for _ in range(3):
+            cgs.cgs_pmg_smooth(g.handle, 0, b, y)
+    torch.cuda.synchronize()
+    g.free()
+    h.free()
+    return out
+
+
 def main():
     from . import build, cgs
     ap = argparse.ArgumentParser()
@@ -127,10 +154,16 @@ def main():
     ap.add_argument("--solves", type=int, default=3)
     ap.add_argument("--prec", default="fp64",
                     help="coarse mesh precision; fp32/fp16 also run the smoothers and transfers in float")
+    ap.add_argument("--only", choices=("solve", "steps"), default=None,
+                    help="a short run for a profiler: one solve (--maxit products) or three launches per step")
+    ap.add_argument("--maxit", type=int, default=8)
     args = ap.parse_args()
     build.build()
     ctx = cgs.cgs_create(0)
-    print(json.dumps(run(ctx, args.small, args.solves, prec=args.prec)))
+    if args.only:
+        print(json.dumps(profile_target(ctx, args.only, args.prec, args.maxit, args.small)))
+    else:
+        print(json.dumps(run(ctx, args.small, args.solves, prec=args.prec)))
     cgs.cgs_destroy(ctx)
 
 
