@@ -802,6 +802,13 @@ cgs_status cgs_mesh_setup(cgs_ctx* ctx, const double* xyz, int64_t nv, const int
 
     UP(d.conn, hs.conn);
     UP(d.a36, hs.a36);
+    if (!hs.ell_ptr.empty()) {
+        d.nslice = (int64_t)hs.ell_ptr.size() - 1;
+        d.ell_w = hs.ell_w;
+        UP(d.ell_ptr, hs.ell_ptr);
+        UP(d.ell_col, hs.ell_col);
+        UP(d.ell_val, hs.ell_val);
+    }
     UP(d.cell, hs.cell);
     if (!f64) {
         d.ntiles = (int64_t)hs.tile_ptr.size() - 1;
@@ -1068,6 +1075,7 @@ cgs_status cgs_mesh_setup(cgs_ctx* ctx, const double* xyz, int64_t nv, const int
     E.P.max_m = d.max_m;
     E.P.any_nr = hs.nr > 0;
     E.P.hyb_restrict = d.nhr > 0;
+    E.P.ell = d.nslice > 0;
     {
         const MeshSizes sz = m->sizes;
         E.build = [sz](const Schedule& sch, std::vector<Work> (&tabs)[kWorkKinds]) {
@@ -1574,6 +1582,7 @@ cgs_status cgs_batch_create(cgs_ctx* ctx, cgs_mesh* const* meshes, int nmesh, in
         sizes[i] = m->sizes;
         E.P.max_m = std::max(E.P.max_m, m->d.max_m);
         E.P.any_nr = E.P.any_nr || m->d.nr > 0;
+        E.P.ell = (i == 0 || E.P.ell) && m->d.nslice > 0;
         B->max_nv = std::max(B->max_nv, m->d.nv);
         total_v += (int64_t)nrhs * m->d.nv;
         total_r += (int64_t)nrhs * m->d.nr;
@@ -1883,12 +1892,14 @@ cudaError_t server_tables(cgs_server* sv, const std::vector<int>& ids, cgs_serve
     P.tile_tma = sv->sch.tile_tma != 0;
     P.pdl = sv->sch.pdl != 0;
     P.interp_cells = sv->sch.interp_cells != 0;
+    P.ell = !ids.empty();
     for (int k : ids) {
         const cgs_server::SlotState& ss = sv->slots[k];
         const cgs_mesh* m = ss.req.mesh;
         append_mesh_work(tabs, ss.reg, k, ss.voff, ss.roff, ss.poff, m->sizes, sv->sch);
         P.max_m = std::max(P.max_m, m->d.max_m);
         P.any_nr = P.any_nr || m->d.nr > 0;
+        P.ell = P.ell && m->d.nslice > 0;
     }
     for (int kind = 0; kind < kWorkKinds; ++kind) {
         const size_t n = tabs[kind].size();

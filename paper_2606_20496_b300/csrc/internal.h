@@ -31,6 +31,14 @@ struct HostSetup {
     std::vector<int32_t> elem_order;   // device slot -> caller element id
     std::vector<int32_t> conn;         // ne*8, vertex id, or ~v for a Dirichlet vertex
     std::vector<double> a36;           // SoA [kUpper][ne] element matrices, float64
+    // the assembled free block of A (float64 form), sliced ELL: rows in
+    // slices of 32, every slice ell_w entries wide, entry k of row 32 s + lane
+    // at ell_ptr[s] + 32 k + lane = 32 ell_w s + 32 k + lane (column -1 and
+    // value 0 pad the shorter rows; Dirichlet rows are all padding)
+    int32_t ell_w = 0;
+    std::vector<int64_t> ell_ptr;      // nslice+1 (empty: element form only)
+    std::vector<int32_t> ell_col;
+    std::vector<double> ell_val;
     std::vector<float> a28;            // SoA [kOff][ne] off-diagonals rounded to float32
     std::vector<float> a28lo;          // SoA [kOff][ne] float32 remainders a - (double)a28
     std::vector<uint8_t> dir;          // nv, 1 = Dirichlet
@@ -124,6 +132,11 @@ struct DevMesh {
     const int32_t* conn = nullptr;     // ne*8 (int4 x2 per element)
     const uint8_t* dir = nullptr;      // nv, 1 = Dirichlet
     const double* a36 = nullptr;       // [36][ne]
+    int64_t nslice = 0;                // sliced-ELL rows of the assembled A (0: none)
+    int32_t ell_w = 0;                 // entries per row (every slice as wide)
+    const int64_t* ell_ptr = nullptr;
+    const int32_t* ell_col = nullptr;
+    const double* ell_val = nullptr;
     const double2* xyzw = nullptr;     // 2*nv: (x, y), (z, 1/count) per vertex, float64
     const float4* xyzwf = nullptr;     // nv: same, float32
     const int32_t* cell = nullptr;     // ne
@@ -234,6 +247,7 @@ enum WorkKind {
     kWorkRowPack,
     kWorkXSeg,
     kWorkHybR,
+    kWorkEll,
     kWorkKinds
 };
 
@@ -254,6 +268,8 @@ struct Plan {
     bool any_xxt = false;                  // some mesh solves its reduced system by XX^T
     bool hyb_restrict = false;             // every mesh with a reduced space has the hybrid
                                            // restriction entries (no s = r - A l needed)
+    bool ell = false;                      // every mesh has the assembled A (float64 form):
+                                           // the FP64 applies run by rows
 };
 
 // Grid-wide barrier of the persistent PCG kernel (device memory, zeroed
@@ -319,6 +335,7 @@ constexpr int row_entries(int M) { return (row_pack_rows(M) * M + 7) / 8 * 8; }
 // meshes with fewer lane subdomains than this also get row packs
 constexpr int64_t kRowPackMaxSubs = 9472;
 constexpr int kElemChunk = 256;   // elements per block
+constexpr int kEllChunk = 1024;   // rows of the assembled A per block (four per thread)
 // Box cells per axis, at most kMaxBoxes; the box lists store a cell as its
 // packed coordinates ci | cj << 10 | ck << 20.
 constexpr int kMaxBoxes = 1023;

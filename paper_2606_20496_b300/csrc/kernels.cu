@@ -1,6 +1,7 @@
 // CUDA kernels of the coarse-grid solve (sm_103a).
 //
 //   apply64               y += alpha Q^T A_L Q x, float64          (Sec. 3)
+//   apply_ell64           the same by rows of the assembled A (float64 form)
 //   apply_pair_tiled      q  = A p, float-pair outer operator      (Sec. 3)
 //   apply28f_tiled        s -= A l, float32 inner apply            (Eq. (5))
 //   local_warp            out += W_ov sum_p R_p^T A_p^{-1} R_p r   (Eq. (4))
@@ -239,6 +240,74 @@ __device__ __forceinline__ void apply64_item(const DevMesh* __restrict__ meshes,
             }
         }
     }
+}
+
+// read-once loads that do not allocate in L1
+__device__ __forceinline__ int32_t ld_stream_i32(const int32_t* p) {
+    int32_t v;
+    asm("ld.global.nc.L1::no_allocate.b32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ double ld_stream_f64(const double* p) {
+    double v;
+    asm("ld.global.nc.L1::no_allocate.f64 %0, [%1];" : "=d"(v) : "l"(p));
+    return v;
+}
+
+// y += alpha A x over the rows of the assembled free block (sliced ELL),
+// float64: each row's entries are read once, coalesced across the warp that
+// holds its slice, about 27 FP64 multiply-adds per row on hexahedral meshes
+// (the element form needs 64 per element).  Dirichlet rows are padding and
+// add zero to y; Dirichlet columns are not stored.  kDot: p.Ap = sum over
+// rows of x_i (A x)_i and alpha for the PCG.
+template <bool kDot>
+__device__ __forceinline__ void apply_ell64_item(const DevMesh* __restrict__ meshes, const Work& w, Vecs V,
+                                                 const double* __restrict__ xin, double* __restrict__ yout,
+                                                 double alpha) {
+    CGS_ITEM_PROLOGUE();
+    const double* x = xin + w.voff;
+    double* y = yout + w.voff;
+    double energy = 0.0;
+    const int W = M.ell_w;
+    for (int64_t i = (int64_t)w.begin + threadIdx.x; i < w.end; i += blockDim.x) {
+        const int64_t o0 = (i >> 5) * 32 * (int64_t)W + (i & 31);
+        double acc = 0.0;
+// the entries stream past L1 (read once), which keeps L1 for the gathers
+        // of x (each x_j is read by up to 27 rows); the loop unrolled over a
+        // hexahedral mesh's 27 entries keeps them all in flight
+#pragma unroll 27
+        for (int k = 0; k < W; ++k) {
+            const int32_t c = ld_stream_i32(&M.ell_col[o0 + 32 * k]);
+            const double a = ld_stream_f64(&M.ell_val[o0 + 32 * k]);
+            if (c >= 0) acc = fma(a, __ldg(&x[c]), acc);
+        }
+        y[i] = alpha == 1.0 ? y[i] + acc : fma(alpha, acc, y[i]);
+        if (kDot) energy = fma(__ldg(&x[i]), acc, energy);
+    }
+    if (kDot) {
+        double val[1] = {energy}, tot[1];
+        pdl_trigger();   // the successor may launch during the reduction tail
+        if (slot_sum<1>(val, V.partials + w.poff, w.idx, w.count, &S->ticket[0], tot) && threadIdx.x == 0) {
+            const double pq = tot[0];
+            S->pq = pq;
+            if (!(pq > 0.0) || !isfinite(pq)) {
+                S->status = CGS_ERR_BREAKDOWN;
+                S->done = 1;
+            } else {
+                S->alpha = S->rho / pq;
+            }
+        }
+    }
+}
+
+template <bool kDot>
+__global__ void __launch_bounds__(kBlock) apply_ell64_kernel(const DevMesh* __restrict__ meshes,
+                                                             const Work* __restrict__ work, Vecs V,
+                                                             const double* __restrict__ xin,
+                                                             double* __restrict__ yout, double alpha) {
+    const Work w_ = work[blockIdx.x];
+    pdl_wait();
+    apply_ell64_item<kDot>(meshes, w_, V, xin, yout, alpha);
 }
 
 template <bool kDot>
@@ -2771,6 +2840,16 @@ void launch_pdl(bool pdl, void (*kern)(KArgs...), unsigned int grid, unsigned in
 
 void launch_apply64(const Plan& P, const Vecs& V, const double* x, double* y, double alpha, bool dot,
                     cudaStream_t st) {
+    if (P.ell) {   // the assembled rows
+        if (!P.nwork[kWorkEll]) return;
+        if (dot)
+            launch_pdl(P.pdl, apply_ell64_kernel<true>, P.nwork[kWorkEll], kBlock, 0, st, P.meshes, P.work[kWorkEll],
+                       V, x, y, alpha);
+        else
+            launch_pdl(P.pdl, apply_ell64_kernel<false>, P.nwork[kWorkEll], kBlock, 0, st, P.meshes, P.work[kWorkEll],
+                       V, x, y, alpha);
+        return;
+    }
     if (!P.nwork[kWorkElem]) return;
     if (dot)
         launch_pdl(P.pdl, apply64_kernel<true>, P.nwork[kWorkElem], kBlock, 0, st, P.meshes, P.work[kWorkElem], V, x, y,
@@ -3174,6 +3253,7 @@ void append_mesh_work(std::vector<Work> (&tabs)[kWorkKinds], int mesh, int slot,
     if (z.nr > 0) add(kWorkBoxEnt, z.nrng, kBlock / 32);
     if (z.nxseg > 0) add(kWorkXSeg, z.nxseg, kRowChunk);
     if (z.nr > 0 && z.nhr > 0) add(kWorkHybR, z.nhr, kBlock / 32);
+    add(kWorkEll, z.nv, kEllChunk);
 }
 
 int64_t mesh_partial_slots(const MeshSizes& z, const Schedule& sch) {
@@ -3181,6 +3261,7 @@ int64_t mesh_partial_slots(const MeshSizes& z, const Schedule& sch) {
     c = std::max(c, z.ntiles);
     c = std::max(c, (z.nv + sch.vert_chunk - 1) / sch.vert_chunk);
     c = std::max(c, (z.nvb + sch.box_chunk - 1) / sch.box_chunk);
+    c = std::max(c, (z.nv + kEllChunk - 1) / kEllChunk);
     return 2 * std::max<int64_t>(c, 1);
 }
 

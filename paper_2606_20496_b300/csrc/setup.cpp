@@ -1206,6 +1206,84 @@ cgs_status host_setup(const double* xyz, int64_t nv, const int32_t* conn, int64_
                 }
             }
     }
+    // ---- the assembled free block of A, sliced ELL (float64 form) ----------
+    // B300 issues two FP64 multiply-adds per clock per SM, and the element
+    // form of q = A p spends 64 of them per element against about 27 per row
+    // of the assembled operator on hexahedral meshes: the FP64 form applies
+    // A row by row.  Each row sums its elements' contributions in v2e order.
+    if (prm.prec == CGS_FP64) {
+        constexpr int kMaxRow = 64;
+        // the entries of row v (caller vertex ids), ascending columns; false
+        // if the row has more than kMaxRow
+        auto row_of = [&](int64_t v, int32_t* cols, double* vals, int& cnt) {
+            cnt = 0;
+            if (S.dir[v]) return true;
+            for (int64_t t = v2e_ptr[v]; t < v2e_ptr[v + 1]; ++t) {
+                const int64_t e = v2e[t];
+                int a = 0;
+                while (a < 8 && conn[e * 8 + a] != v) ++a;
+                const double* A = &Ae[(size_t)e * 64];
+                for (int b = 0; b < 8; ++b) {
+                    const int32_t u = conn[e * 8 + b];
+                    if (S.dir[u]) continue;
+                    int q = 0;
+                    while (q < cnt && cols[q] != u) ++q;
+                    if (q == cnt) {
+                        if (cnt == kMaxRow) return false;
+                        cols[cnt] = u;
+                        vals[cnt] = 0.0;
+                        ++cnt;
+                    }
+                    vals[q] += A[a * 8 + b];
+                }
+            }
+            for (int i = 1; i < cnt; ++i)   // insertion sort by column
+                for (int j = i; j > 0 && cols[j - 1] > cols[j]; --j) {
+                    std::swap(cols[j - 1], cols[j]);
+                    std::swap(vals[j - 1], vals[j]);
+                }
+            return true;
+        };
+        const int64_t nsl = (nv + 31) / 32;
+        std::vector<int32_t> width(nsl, 0);
+        bool fits = true;
+#pragma omp parallel for schedule(static) reduction(&& : fits)
+        for (int64_t sl = 0; sl < nsl; ++sl) {
+            int32_t cols[kMaxRow];
+            double vals[kMaxRow];
+            int w = 0;
+            for (int64_t v = sl * 32; v < std::min<int64_t>(nv, sl * 32 + 32); ++v) {
+                int cnt = 0;
+                fits = fits && row_of(v, cols, vals, cnt);
+                w = std::max(w, cnt);
+            }
+            width[sl] = w;
+        }
+        if (fits) {
+            // one width for every slice (the widest row; shorter rows are
+            // padded), so that entry k of row i sits at a computable place
+            const int32_t wmax = nsl ? *std::max_element(width.begin(), width.end()) : 0;
+            S.ell_w = wmax;
+            S.ell_ptr.assign(nsl + 1, 0);
+            for (int64_t sl = 0; sl < nsl; ++sl) S.ell_ptr[sl + 1] = S.ell_ptr[sl] + 32 * (int64_t)wmax;
+            S.ell_col.assign(S.ell_ptr[nsl], -1);
+            S.ell_val.assign(S.ell_ptr[nsl], 0.0);
+#pragma omp parallel for schedule(static)
+            for (int64_t sl = 0; sl < nsl; ++sl) {
+                int32_t cols[kMaxRow];
+                double vals[kMaxRow];
+                for (int64_t v = sl * 32; v < std::min<int64_t>(nv, sl * 32 + 32); ++v) {
+                    int cnt = 0;
+                    row_of(v, cols, vals, cnt);
+                    for (int k = 0; k < cnt; ++k) {
+                        const int64_t o = S.ell_ptr[sl] + 32 * (int64_t)k + (v - sl * 32);
+                        S.ell_col[o] = cols[k];
+                        S.ell_val[o] = vals[k];
+                    }
+                }
+            }
+        }
+    }
     // ---- element tiles for block-local assembly --------------------------
     {
         std::vector<int32_t> stamp(nv, -1), loc(nv, 0), in_tile(nv, 0);
