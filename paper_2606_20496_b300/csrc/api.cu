@@ -302,12 +302,22 @@ void pcg_iteration(Engine& E, cudaStream_t st, const cudaGraphConditionalHandle*
         if (!precond_body(E, Vi, st, true)) K(CGS_K_PCG_DOTS, (launch_pcg_dots<double, double>(P, Vi, V.q, st)));
         K(CGS_K_PCG_P, (launch_pcg_update_p<double, double>(P, Vi, V.q, cond, st)));
     } else {
-        // p = z + beta p is formed by the apply and stored by the x, r update;
-        // the interpolation (or the dots) closes the iteration and sets the
-        // loop condition
-        K(CGS_K_APPLY_A64, launch_apply_pair_tiled(P, V, st));
-        K(CGS_K_PCG_XR, launch_pcg_update_xr_pair(P, V, st));
-        if (!precond_body(E, V, st, true, cond)) K(CGS_K_PCG_DOTS, launch_pcg_dots_pair(P, V, cond, st));
+        if (rows_outer(P)) {
+            // q = A p by rows of the assembled A (p stored by the previous
+            // iteration's p update), x and r, the preconditioner and the dots;
+            // the p update closes the iteration and sets the loop condition
+            K(CGS_K_APPLY_A64, launch_apply_outer(P, V, st));
+            K(CGS_K_PCG_XR, launch_pcg_update_xr_pair(P, V, st, false));
+            if (!precond_body(E, V, st, true, nullptr)) K(CGS_K_PCG_DOTS, launch_pcg_dots_pair(P, V, nullptr, st));
+            K(CGS_K_PCG_P, launch_pcg_update_p_pair(P, V, cond, st));
+        } else {
+            // p = z + beta p is formed by the tiled apply and stored by the x,
+            // r update; the interpolation (or the dots) closes the iteration
+            // and sets the loop condition
+            K(CGS_K_APPLY_A64, launch_apply_pair_tiled(P, V, st));
+            K(CGS_K_PCG_XR, launch_pcg_update_xr_pair(P, V, st));
+            if (!precond_body(E, V, st, true, cond)) K(CGS_K_PCG_DOTS, launch_pcg_dots_pair(P, V, cond, st));
+        }
     }
 }
 
@@ -657,7 +667,7 @@ cgs_status tune_engine(Engine& E, cudaStream_t st) {
             t.tile_tma = tma;
             if (set_schedule(E, t) != cudaSuccess) continue;
             const float ms = time_it([&]() {
-                launch_apply_pair_tiled(E.P, V, st);
+                launch_apply_outer(E.P, V, st);
                 launch_apply28f_tiled(E.P, V, static_cast<const float*>(V.z), static_cast<float*>(V.s), -1.0f, st);
             });
             if (ms < best_tile) {
@@ -807,7 +817,12 @@ cgs_status cgs_mesh_setup(cgs_ctx* ctx, const double* xyz, int64_t nv, const int
         d.ell_w = hs.ell_w;
         UP(d.ell_ptr, hs.ell_ptr);
         UP(d.ell_col, hs.ell_col);
-        UP(d.ell_val, hs.ell_val);
+        if (!hs.ell_val.empty()) UP(d.ell_val, hs.ell_val);
+        if (!hs.ell_pair.empty()) {
+            const float* pp = nullptr;
+            UP(pp, hs.ell_pair);
+            d.ell_pair = reinterpret_cast<const float2*>(pp);
+        }
     }
     UP(d.cell, hs.cell);
     if (!f64) {
@@ -1075,7 +1090,8 @@ cgs_status cgs_mesh_setup(cgs_ctx* ctx, const double* xyz, int64_t nv, const int
     E.P.max_m = d.max_m;
     E.P.any_nr = hs.nr > 0;
     E.P.hyb_restrict = d.nhr > 0;
-    E.P.ell = d.nslice > 0;
+    E.P.ell = d.nslice > 0 && d.ell_val;
+    E.P.ell_pair = d.nslice > 0 && d.ell_pair;
     {
         const MeshSizes sz = m->sizes;
         E.build = [sz](const Schedule& sch, std::vector<Work> (&tabs)[kWorkKinds]) {
@@ -1259,7 +1275,7 @@ cgs_status cgs_apply_A_prec(cgs_mesh* m, const double* x, double* y, int op, voi
         // x split into float pairs, y = A x in float-pair arithmetic
         K(CGS_K_OTHER, launch_split_pair(nv, x, V.p2, st));
         K(CGS_K_OTHER, launch_fill_d(nv, reinterpret_cast<double*>(V.q2), 0.0, st));
-        K(CGS_K_APPLY_A64, launch_apply_pair_tiled(E.P, V, st));
+        K(CGS_K_APPLY_A64, launch_apply_outer(E.P, V, st));
         K(CGS_K_OTHER, launch_pair_to_double(nv, V.q2, y, st));
     }
     return finish(st, false);
@@ -1582,7 +1598,8 @@ cgs_status cgs_batch_create(cgs_ctx* ctx, cgs_mesh* const* meshes, int nmesh, in
         sizes[i] = m->sizes;
         E.P.max_m = std::max(E.P.max_m, m->d.max_m);
         E.P.any_nr = E.P.any_nr || m->d.nr > 0;
-        E.P.ell = (i == 0 || E.P.ell) && m->d.nslice > 0;
+        E.P.ell = (i == 0 || E.P.ell) && m->d.nslice > 0 && m->d.ell_val;
+        E.P.ell_pair = (i == 0 || E.P.ell_pair) && m->d.nslice > 0 && m->d.ell_pair;
         B->max_nv = std::max(B->max_nv, m->d.nv);
         total_v += (int64_t)nrhs * m->d.nv;
         total_r += (int64_t)nrhs * m->d.nr;
@@ -1893,13 +1910,15 @@ cudaError_t server_tables(cgs_server* sv, const std::vector<int>& ids, cgs_serve
     P.pdl = sv->sch.pdl != 0;
     P.interp_cells = sv->sch.interp_cells != 0;
     P.ell = !ids.empty();
+    P.ell_pair = !ids.empty();
     for (int k : ids) {
         const cgs_server::SlotState& ss = sv->slots[k];
         const cgs_mesh* m = ss.req.mesh;
         append_mesh_work(tabs, ss.reg, k, ss.voff, ss.roff, ss.poff, m->sizes, sv->sch);
         P.max_m = std::max(P.max_m, m->d.max_m);
         P.any_nr = P.any_nr || m->d.nr > 0;
-        P.ell = P.ell && m->d.nslice > 0;
+        P.ell = P.ell && m->d.nslice > 0 && m->d.ell_val;
+        P.ell_pair = P.ell_pair && m->d.nslice > 0 && m->d.ell_pair;
     }
     for (int kind = 0; kind < kWorkKinds; ++kind) {
         const size_t n = tabs[kind].size();

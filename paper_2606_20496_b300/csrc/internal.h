@@ -38,7 +38,8 @@ struct HostSetup {
     int32_t ell_w = 0;
     std::vector<int64_t> ell_ptr;      // nslice+1 (empty: element form only)
     std::vector<int32_t> ell_col;
-    std::vector<double> ell_val;
+    std::vector<double> ell_val;       // float64 form
+    std::vector<float> ell_pair;       // mixed forms: (hi, lo) per entry
     std::vector<float> a28;            // SoA [kOff][ne] off-diagonals rounded to float32
     std::vector<float> a28lo;          // SoA [kOff][ne] float32 remainders a - (double)a28
     std::vector<uint8_t> dir;          // nv, 1 = Dirichlet
@@ -136,7 +137,8 @@ struct DevMesh {
     int32_t ell_w = 0;                 // entries per row (every slice as wide)
     const int64_t* ell_ptr = nullptr;
     const int32_t* ell_col = nullptr;
-    const double* ell_val = nullptr;
+    const double* ell_val = nullptr;   // float64 form
+    const float2* ell_pair = nullptr;  // mixed forms
     const double2* xyzw = nullptr;     // 2*nv: (x, y), (z, 1/count) per vertex, float64
     const float4* xyzwf = nullptr;     // nv: same, float32
     const int32_t* cell = nullptr;     // ne
@@ -268,8 +270,10 @@ struct Plan {
     bool any_xxt = false;                  // some mesh solves its reduced system by XX^T
     bool hyb_restrict = false;             // every mesh with a reduced space has the hybrid
                                            // restriction entries (no s = r - A l needed)
-    bool ell = false;                      // every mesh has the assembled A (float64 form):
+    bool ell = false;                      // every mesh has the assembled A in float64:
                                            // the FP64 applies run by rows
+    bool ell_pair = false;                 // every mesh has it in float pairs: the PCG's
+                                           // outer apply runs by rows (unless tile_tma)
 };
 
 // Grid-wide barrier of the persistent PCG kernel (device memory, zeroed

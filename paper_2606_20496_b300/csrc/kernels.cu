@@ -3,6 +3,7 @@
 //   apply64               y += alpha Q^T A_L Q x, float64          (Sec. 3)
 //   apply_ell64           the same by rows of the assembled A (float64 form)
 //   apply_pair_tiled      q  = A p, float-pair outer operator      (Sec. 3)
+//   apply_ell_pair        the same by rows of the assembled A (float pairs)
 //   apply28f_tiled        s -= A l, float32 inner apply            (Eq. (5))
 //   local_warp            out += W_ov sum_p R_p^T A_p^{-1} R_p r   (Eq. (4))
 //   restrict              r_r += J_L^T Q W s                       (Sec. 4)
@@ -251,6 +252,11 @@ __device__ __forceinline__ int32_t ld_stream_i32(const int32_t* p) {
 __device__ __forceinline__ double ld_stream_f64(const double* p) {
     double v;
     asm("ld.global.nc.L1::no_allocate.f64 %0, [%1];" : "=d"(v) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ float2 ld_stream_f2(const float2* p) {
+    float2 v;
+    asm("ld.global.nc.L1::no_allocate.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p));
     return v;
 }
 
@@ -767,6 +773,65 @@ __global__ void __launch_bounds__(kBlock, kTma ? 3 : 4) apply_pair_tiled_kernel(
     const Work w_ = work[blockIdx.x];
     pdl_wait();
     apply_pair_tiled_item<kTma>(meshes, w_, V, wait_limit);
+}
+
+// q = A p in float-pair arithmetic by rows of the assembled free block
+// (sliced ELL, (hi, lo) values): per entry one pair product and one pair
+// accumulation, about 27 per row on hexahedral meshes, written once per
+// row (no atomics).  p is this iteration's direction, stored by the p update
+// that ends the previous iteration.  Inside the PCG also sums p.Ap and
+// finalises alpha in the slot's last block; a single step (or a timing run)
+// only applies A.
+__device__ __forceinline__ void apply_ell_pair_item(const DevMesh* __restrict__ meshes, const Work& w, Vecs V) {
+    CGS_ITEM_PROLOGUE();
+    const bool pcg = S && !V.step;
+    const float2* p2 = V.p2 + w.voff;
+    float2* q2 = V.q2 + w.voff;
+    const int W = M.ell_w;
+    float eh = 0.0f, el = 0.0f;   // this thread's share of p.Ap
+    for (int64_t i = (int64_t)w.begin + threadIdx.x; i < w.end; i += blockDim.x) {
+        const int64_t o0 = (i >> 5) * 32 * (int64_t)W + (i & 31);
+        float yh = 0.0f, yl = 0.0f;
+#pragma unroll 27
+        for (int k = 0; k < W; ++k) {
+            const int32_t c = ld_stream_i32(&M.ell_col[o0 + 32 * k]);
+            const float2 a = ld_stream_f2(&M.ell_pair[o0 + 32 * k]);
+            if (c >= 0) {
+                const float2 x = __ldg(&p2[c]);
+                float ph, pl;
+                pair_mul(a.x, a.y, x.x, x.y, ph, pl);
+                pair_acc(yh, yl, ph, pl);
+            }
+        }
+        float h, l;
+        fast_two_sum(yh, yl, h, l);
+        q2[i] = make_float2(h, l);
+        if (pcg) pr_dot_acc(eh, el, __ldg(&p2[i]), make_float2(h, l));
+    }
+    if (!pcg) return;   // no PCG scalars (single steps, timing runs): no reduction
+    float vh[1] = {eh}, vl[1] = {el};
+    double tot[1];
+    pdl_trigger();   // the successor may launch during the reduction tail
+    if (slot_sum_pair<1>(vh, vl, V.partials + w.poff, w.idx, w.count, &S->ticket[0], tot) && threadIdx.x == 0) {
+        const double pq = tot[0];
+        S->pq = pq;
+        if (S->status == CGS_ERR_TIMEOUT) {
+            S->done = 1;
+        } else if (!(pq > 0.0) || !isfinite(pq)) {
+            S->status = CGS_ERR_BREAKDOWN;
+            S->done = 1;
+        } else {
+            S->alpha = S->rho / pq;
+            S->alpha2 = split_pair(S->alpha);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kBlock) apply_ell_pair_kernel(const DevMesh* __restrict__ meshes,
+                                                                const Work* __restrict__ work, Vecs V) {
+    const Work w_ = work[blockIdx.x];
+    pdl_wait();
+    apply_ell_pair_item(meshes, w_, V);
 }
 
 // y += alpha A x in float32 (inner apply s -= A l of the hybrid step); the
@@ -2514,7 +2579,11 @@ __global__ void __launch_bounds__(kBlock) pcg_first_dir_pair_kernel(const DevMes
 
 // x += alpha p, r -= alpha q, ||r||^2; z = 0, s = hi(r), r_r = 0.  The
 // slot's last block counts the iteration and applies the stopping test.
-__device__ __forceinline__ void pcg_update_xr_pair_item(const DevMesh* __restrict__ meshes, const Work& w, Vecs V) {
+// form_p: p = z + beta p is formed here and stored (the tiled apply formed
+// it on the fly); otherwise p is current already (the row apply needs it
+// stored before the apply, so the p update ends the previous iteration).
+__device__ __forceinline__ void pcg_update_xr_pair_item(const DevMesh* __restrict__ meshes, const Work& w, Vecs V,
+                                                        bool form_p = true) {
     CGS_ITEM_PROLOGUE();
     float2* __restrict__ x = as_pair(V.x) + w.voff;
     float2* __restrict__ r = as_pair(V.r) + w.voff;
@@ -2544,8 +2613,8 @@ __device__ __forceinline__ void pcg_update_xr_pair_item(const DevMesh* __restric
             const int64_t i = i0 + k * (int64_t)blockDim.x;
             if (i < w.end) {
                 // p = z + beta p: the same arithmetic as the operator apply's
-                const float2 pn = pr_fma(beta, pi[k], make_float2(zi[k], 0.0f));
-                p[i] = pn;
+                const float2 pn = form_p ? pr_fma(beta, pi[k], make_float2(zi[k], 0.0f)) : pi[k];
+                if (form_p) p[i] = pn;
                 x[i] = pr_fma(a, pn, xi[k]);
                 const float2 rn = pr_fma(na, qi[k], ri[k]);
                 r[i] = rn;
@@ -2581,10 +2650,45 @@ __device__ __forceinline__ void pcg_update_xr_pair_item(const DevMesh* __restric
     }
 }
 __global__ void __launch_bounds__(kBlock, 4) pcg_update_xr_pair_kernel(const DevMesh* __restrict__ meshes,
-                                                                    const Work* __restrict__ work, Vecs V) {
+                                                                    const Work* __restrict__ work, Vecs V,
+                                                                    int form_p) {
     const Work w_ = work[blockIdx.x];
     pdl_wait();
-    pcg_update_xr_pair_item(meshes, w_, V);
+    pcg_update_xr_pair_item(meshes, w_, V, form_p != 0);
+}
+
+// p = z + beta p in float pairs (the row apply's direction), ending the
+// iteration: block 0 also sets the loop condition.
+__device__ __forceinline__ void pcg_update_p_pair_item(const DevMesh* __restrict__ meshes, const Work& w, Vecs V) {
+    CGS_ITEM_PROLOGUE();
+    float2* __restrict__ p = V.p2 + w.voff;
+    const float* __restrict__ z = static_cast<const float*>(V.z) + w.voff;
+    const float2 beta = S->beta2;
+    CGS_VERT_LOOP4(i0) {
+        float2 pk[4];
+        float zk[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int64_t i = i0 + k * (int64_t)blockDim.x;
+            if (i < w.end) {
+                pk[k] = p[i];
+                zk[k] = z[i];
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int64_t i = i0 + k * (int64_t)blockDim.x;
+            if (i < w.end) p[i] = pr_fma(beta, pk[k], make_float2(zk[k], 0.0f));
+        }
+    }
+}
+__global__ void __launch_bounds__(kBlock, 4) pcg_update_p_pair_kernel(const DevMesh* __restrict__ meshes,
+                                                                   const Work* __restrict__ work, Vecs V, int nslots,
+                                                                   cudaGraphConditionalHandle cond, int set_cond) {
+    if (set_cond && blockIdx.x == 0) loop_condition(V.S, nslots, cond);
+    const Work w_ = work[blockIdx.x];
+    pdl_wait();
+    pcg_update_p_pair_item(meshes, w_, V);
 }
 
 // z.r and z.q; beta = -alpha (z.q) / rho, rho = z.r.
@@ -2730,7 +2834,7 @@ __global__ void __launch_bounds__(kBlock, 2) pcg_persistent_kernel(const DevMesh
         CGS_FOR_ITEMS(kWorkTile, k) apply_pair_tiled_item<false>(meshes, T.w[kWorkTile][k], V, wait_limit);
         CGS_SYNC_OR_LEAVE();
         // x, r, ||r||, stopping test; z = 0, s = hi(r), r_r = 0
-        CGS_FOR_ITEMS(kWorkVert, k) pcg_update_xr_pair_item(meshes, T.w[kWorkVert][k], V);
+        CGS_FOR_ITEMS(kWorkVert, k) pcg_update_xr_pair_item(meshes, T.w[kWorkVert][k], V, true);
         CGS_SYNC_OR_LEAVE();
         int running = 0;
         for (int i = threadIdx.x; i < nslots; i += blockDim.x) running |= !*(volatile const int*)&V.S[i].done;
@@ -2865,6 +2969,15 @@ void set_smem_attr(const void* fn, int bytes, bool& done) {
         cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
         done = true;
     }
+}
+
+bool rows_outer(const Plan& P) { return P.ell_pair && !P.tile_tma && P.nwork[kWorkEll] > 0; }
+
+void launch_apply_outer(const Plan& P, const Vecs& V, cudaStream_t st) {
+    if (rows_outer(P))
+        launch_pdl(P.pdl, apply_ell_pair_kernel, P.nwork[kWorkEll], kBlock, 0, st, P.meshes, P.work[kWorkEll], V);
+    else
+        launch_apply_pair_tiled(P, V, st);
 }
 
 void launch_apply_pair_tiled(const Plan& P, const Vecs& V, cudaStream_t st) {
@@ -3092,8 +3205,13 @@ void launch_pcg_first_dir_pair(const Plan& P, const Vecs& V, cudaStream_t st) {
     CGS_VLAUNCH(pcg_first_dir_pair_kernel);
 }
 
-void launch_pcg_update_xr_pair(const Plan& P, const Vecs& V, cudaStream_t st) {
-    CGS_VLAUNCH(pcg_update_xr_pair_kernel);
+void launch_pcg_update_xr_pair(const Plan& P, const Vecs& V, cudaStream_t st, bool form_p) {
+    CGS_VLAUNCH(pcg_update_xr_pair_kernel, form_p ? 1 : 0);
+}
+
+void launch_pcg_update_p_pair(const Plan& P, const Vecs& V, const cudaGraphConditionalHandle* cond,
+                              cudaStream_t st) {
+    CGS_VLAUNCH(pcg_update_p_pair_kernel, P.nslots, cond ? *cond : 0, cond ? 1 : 0);
 }
 
 void launch_pcg_dots_pair(const Plan& P, const Vecs& V, const cudaGraphConditionalHandle* cond, cudaStream_t st) {

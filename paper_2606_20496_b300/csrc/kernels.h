@@ -32,6 +32,10 @@ void launch_vec_add(int64_t n, const double* a, const double* b, double* out, cu
 void launch_apply64(const Plan& P, const Vecs& V, const double* x, double* y, double alpha, bool dot,
                     cudaStream_t st);
 void launch_apply_pair_tiled(const Plan& P, const Vecs& V, cudaStream_t st);
+// the PCG's outer apply of the mixed forms: by rows of the assembled A when
+// every mesh has them and the schedule does not ask for TMA-staged tiles
+bool rows_outer(const Plan& P);
+void launch_apply_outer(const Plan& P, const Vecs& V, cudaStream_t st);
 void launch_apply28f_tiled(const Plan& P, const Vecs& V, const float* x, float* y, float alpha, cudaStream_t st);
 // out += sum_p R~_p^T A_p^{-1} R_p r, weighted: 0 none (additive), 1 W_ov per
 // vertex (hybrid), 2 the RAS weight per entry
@@ -71,7 +75,10 @@ void launch_pair_to_double(int64_t n, const float2* a, double* b, cudaStream_t s
 void launch_pcg_init_pair(const Plan& P, const Vecs& V, double rtol, int maxit, cudaStream_t st);
 void launch_precond_prep_pair(const Plan& P, const Vecs& V, cudaStream_t st);
 void launch_pcg_first_dir_pair(const Plan& P, const Vecs& V, cudaStream_t st);
-void launch_pcg_update_xr_pair(const Plan& P, const Vecs& V, cudaStream_t st);
+void launch_pcg_update_xr_pair(const Plan& P, const Vecs& V, cudaStream_t st, bool form_p = true);
+// p = z + beta p in float pairs; sets the loop condition when cond is given
+void launch_pcg_update_p_pair(const Plan& P, const Vecs& V, const cudaGraphConditionalHandle* cond,
+                              cudaStream_t st);
 void launch_pcg_dots_pair(const Plan& P, const Vecs& V, const cudaGraphConditionalHandle* cond, cudaStream_t st);
 void launch_finalize_x_pair(const Plan& P, const Vecs& V, cudaStream_t st);
 

@@ -1206,12 +1206,15 @@ cgs_status host_setup(const double* xyz, int64_t nv, const int32_t* conn, int64_
                 }
             }
     }
-    // ---- the assembled free block of A, sliced ELL (float64 form) ----------
+    // ---- the assembled free block of A, sliced ELL --------------------------
     // B300 issues two FP64 multiply-adds per clock per SM, and the element
     // form of q = A p spends 64 of them per element against about 27 per row
     // of the assembled operator on hexahedral meshes: the FP64 form applies
-    // A row by row.  Each row sums its elements' contributions in v2e order.
-    if (prm.prec == CGS_FP64) {
+    // A row by row.  The mixed forms keep the rows as float pairs (hi + lo,
+    // about 48 bits) for the outer apply: 27 pair products per row instead of
+    // 28 difference-form pair updates of two rows per element.  Each row sums
+    // its elements' contributions in float64, in v2e order.
+    {
         constexpr int kMaxRow = 64;
         // the entries of row v (caller vertex ids), ascending columns; false
         // if the row has more than kMaxRow
@@ -1268,6 +1271,7 @@ cgs_status host_setup(const double* xyz, int64_t nv, const int32_t* conn, int64_
             for (int64_t sl = 0; sl < nsl; ++sl) S.ell_ptr[sl + 1] = S.ell_ptr[sl] + 32 * (int64_t)wmax;
             S.ell_col.assign(S.ell_ptr[nsl], -1);
             S.ell_val.assign(S.ell_ptr[nsl], 0.0);
+            const bool pairs = prm.prec != CGS_FP64;
 #pragma omp parallel for schedule(static)
             for (int64_t sl = 0; sl < nsl; ++sl) {
                 int32_t cols[kMaxRow];
@@ -1281,6 +1285,16 @@ cgs_status host_setup(const double* xyz, int64_t nv, const int32_t* conn, int64_
                         S.ell_val[o] = vals[k];
                     }
                 }
+            }
+            if (pairs) {   // float pairs instead of float64 values
+                S.ell_pair.assign(2 * S.ell_val.size(), 0.0f);
+#pragma omp parallel for schedule(static)
+                for (int64_t o = 0; o < (int64_t)S.ell_val.size(); ++o) {
+                    const float hi = (float)S.ell_val[o];
+                    S.ell_pair[2 * o] = hi;
+                    S.ell_pair[2 * o + 1] = (float)(S.ell_val[o] - (double)hi);
+                }
+                std::vector<double>().swap(S.ell_val);
             }
         }
     }
