@@ -557,6 +557,7 @@ cudaError_t set_schedule(Engine& E, const Schedule& sch) {
     E.tables.release();
     E.tables = fresh;
     P.tile_tma = sch.tile_tma != 0;
+    P.pack_chunk = sch.pack_chunk;
     P.pdl = sch.pdl != 0;
     P.interp_cells = sch.interp_cells != 0;
     P.any_xxt = P.nwork[kWorkXSeg] > 0;
@@ -1907,6 +1908,7 @@ cudaError_t server_tables(cgs_server* sv, const std::vector<int>& ids, cgs_serve
     P.wait_limit = sv->E.P.wait_limit;
     P.bar_limit = sv->E.P.bar_limit;
     P.tile_tma = sv->sch.tile_tma != 0;
+    P.pack_chunk = sv->sch.pack_chunk;
     P.pdl = sv->sch.pdl != 0;
     P.interp_cells = sv->sch.interp_cells != 0;
     P.ell = !ids.empty();

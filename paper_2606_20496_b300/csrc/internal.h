@@ -265,6 +265,7 @@ struct Plan {
     int wait_limit = 1 << 20;              // iteration limit of the element-tile (TMA) waits
     int bar_limit = 1 << 22;               // iteration limit of the persistent loop's grid-barrier waits
     bool tile_tma = false;                 // element tiles staged by TMA (else streamed by the threads)
+    int pack_chunk = 8;                    // lane packs per kWorkPack item (the schedule's)
     bool pdl = true;                       // launch with programmatic stream serialization
     bool interp_cells = false;             // interpolation by cell-sorted entries (dots left to the caller)
     bool any_xxt = false;                  // some mesh solves its reduced system by XX^T

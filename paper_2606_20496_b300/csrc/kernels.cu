@@ -1352,18 +1352,28 @@ __global__ void __launch_bounds__(kBlock, 2) local_lane_kernel(const DevMesh* __
 // the kernel is bound by the FP64 FMA rate, M^2 FMAs per subdomain.  (A
 // variant with x in shared memory and two blocks per SM spilled and ran
 // 16% slower on the cylinder.)
+// One block per SM, each pack of 32 subdomains handled by one warp; packs
+// are dealt so that block b takes the packs whose virtual index (item x
+// chunk + position) is b modulo the grid, its warps in turn: every SM gets
+// the same share of the (class-sorted, largest first) packs, to within one,
+// instead of the last of several waves of blocks running on part of the GPU.
 __global__ void __launch_bounds__(kBlock, 1) local_lane64_kernel(const DevMesh* __restrict__ meshes,
-                                                                 const Work* __restrict__ work, Vecs V,
-                                                                 const double* __restrict__ rin,
+                                                                 const Work* __restrict__ work, int nitems, int chunk,
+                                                                 Vecs V, const double* __restrict__ rin,
                                                                  double* __restrict__ outv, int weighted) {
-    const Work w = work[blockIdx.x];
     pdl_wait();
-    CGS_ITEM_PROLOGUE();
-    const double* r = rin + w.voff;
-    double* out = outv + w.voff;
-    const double* wov = weighted == 1 ? M.wov64 : nullptr;
-    const int lane = threadIdx.x & 31;
-    for (int pk = w.begin + (int)(threadIdx.x >> 5); pk < w.end; pk += kBlock / 32) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t nvirt = (int64_t)nitems * chunk;
+    for (int64_t v = blockIdx.x + (int64_t)gridDim.x * warp; v < nvirt; v += (int64_t)gridDim.x * (kBlock / 32)) {
+        const Work& w = work[v / chunk];
+        const int pk = w.begin + (int)(v % chunk);
+        if (pk >= w.end) continue;
+        SolveScalars* S = V.S ? V.S + w.slot : nullptr;
+        if (is_done(S)) continue;
+        const DevMesh& M = meshes[w.mesh];
+        const double* r = rin + w.voff;
+        double* out = outv + w.voff;
+        const double* wov = weighted == 1 ? M.wov64 : nullptr;
         const int Mc = __ldg(&M.pack_m[pk]);
         const int64_t io = __ldg(&M.pack_idx_off[pk]);
         const int32_t* idx = M.pack_idx + io;
@@ -3035,9 +3045,20 @@ void launch_local(const Plan& P, const Vecs& V, cgs_precision prec, const void* 
             launch_pdl(P.pdl, local_lane_kernel<__half>, P.nwork[kWorkPack], kBlock, 0, st, P.meshes, P.work[kWorkPack],
                        V, rf, of, wt);
     }
-    if (prec == CGS_FP64 && P.nwork[kWorkPack])
-        launch_pdl(P.pdl, local_lane64_kernel, P.nwork[kWorkPack], kBlock, 0, st, P.meshes, P.work[kWorkPack], V,
-                   static_cast<const double*>(r), static_cast<double*>(out), wt);
+    if (prec == CGS_FP64 && P.nwork[kWorkPack]) {
+        static int sms = 0;
+        if (!sms) {
+            int dev = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            sms = std::max(sms, 1);
+        }
+        const int64_t warps = (int64_t)P.nwork[kWorkPack] * P.pack_chunk;
+        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(sms, (warps + kBlock / 32 - 1) / (kBlock / 32)));
+        launch_pdl(P.pdl, local_lane64_kernel, grid, kBlock, 0, st, P.meshes, P.work[kWorkPack],
+                   (int)P.nwork[kWorkPack], P.pack_chunk, V, static_cast<const double*>(r), static_cast<double*>(out),
+                   wt);
+    }
     // the rest (in the FP64 form every subdomain outside lane packs): a warp
     // per subdomain of up to 64 dofs, a block per larger one
     if (!P.nwork[kWorkSub]) return;
