@@ -146,9 +146,12 @@ def algorithmic_bytes(info, prec, interp_cells=False):
     nh = info.get("n_hyb_entries", 0)
     nj = info.get("n_jt_entries", 0)
     nvb = info.get("n_free", nv)
+    # the row applies over the assembled A: column and value of every
+    # nonzero once, x (or p) gathered once, y read and written once
+    ell = info.get("ell_nnz", 0)
     if prec == "fp64":
         return {
-            "apply_A64": E * (36 * 8 + 32) + nv * (8 + 16),
+            "apply_A64": ell * (4 + 8) + nv * (8 + 16) if ell else E * (36 * 8 + 32) + nv * (8 + 16),
             "local": packed * sl + sm * 4 + nv * (8 + 2 * sb + sb),
             # hybrid: (vertex, J~, A J~) entries, r and l gathered, r_r; else
             # the cell-sorted restriction of s
@@ -164,9 +167,10 @@ def algorithmic_bytes(info, prec, interp_cells=False):
             "pcg_p": nv * 32,
         }
     return {
-        # q = A p: hi/lo off-diagonals and 16-bit local indices per element;
-        # p and z gathered (p = z + beta p on the fly), q written, once per vertex
-        "apply_A64": E * (28 * 8 + 16) + nv * (8 + sb + 8),
+        # q = A p: by rows, column and (hi, lo) value per nonzero, p gathered,
+        # q written; else hi/lo off-diagonals and 16-bit local indices per
+        # element, p and z gathered (p = z + beta p on the fly), q written
+        "apply_A64": ell * (4 + 8) + nv * (8 + 8) if ell else E * (28 * 8 + 16) + nv * (8 + sb + 8),
         # s -= A l: float off-diagonals and indices; l read, s read and written
         "apply_A32": E * (28 * 4 + 16) + nv * (4 + 2 * 4),
         # upper triangles, vertex ids, W_ov; r gathered, z read and written
@@ -179,23 +183,27 @@ def algorithmic_bytes(info, prec, interp_cells=False):
         "interp": (nb * 12 + nv * (16 + 2 * sb) + nr * 4) if interp_cells
         else nv * 8 + nb * 8 + nv * (16 + 2 * sb + 16 + 8) + nr * 4,
         "coarse": coarse,
-        # p, q, x, r read; p, x, r written; z read and cleared; s written
-        "pcg_xr": nv * (8 * 7 + 3 * sb),
+        # p, q, x, r read; x, r (and p without the row apply) written; z read
+        # and cleared; s written
+        "pcg_xr": nv * (8 * (6 if ell else 7) + 3 * sb),
         # z, r and q read, q cleared
         "pcg_dots": nv * (sb + 16 + 8),
-        "pcg_p": nv * (sb + 24),
+        # z read, p read and written (the row apply's p update)
+        "pcg_p": nv * (sb + 16),
     }
 
 
 def algorithmic_flops(info, prec):
     """Float64 flops per launch of the FP64-form kernels (an FMA counts 2): the
-    element matrix-vector product (64 FMAs per element), the local solves
-    (m_p^2 FMAs per subdomain), the hybrid restriction (2 FMAs per entry) and
-    the interpolation by rows (1 FMA per entry, 2 per vertex for the dots)."""
+    operator by rows (one FMA per nonzero and one per row for p.Ap; 64 FMAs
+    per element in the element form), the local solves (m_p^2 FMAs per
+    subdomain), the hybrid restriction (2 FMAs per entry) and the
+    interpolation by rows (1 FMA per entry, 2 per vertex for the dots)."""
     if prec != "fp64":
         return {}
     sum_m2 = 2 * info["sum_sub_tri"] - info["sum_sub_dofs"]
-    out = {"apply_A64": 2 * 64 * info["ne"], "local": 2 * sum_m2}
+    ell = info.get("ell_nnz", 0)
+    out = {"apply_A64": 2 * ell + 2 * info["nv"] if ell else 2 * 64 * info["ne"], "local": 2 * sum_m2}
     if info.get("n_hyb_entries"):
         out["restrict"] = 4 * info["n_hyb_entries"]
     if info.get("n_jt_entries"):

@@ -130,6 +130,10 @@ typedef struct {
     int64_t n_hyb_entries; /* entries (v, J~_vc, (A J~)_vc) of the hybrid restriction
                               (0 unless the set-up was hybrid)                        */
     int64_t n_jt_entries;  /* entries of the explicit rows of J~ (FP64 form)         */
+    int64_t ell_nnz;       /* nonzeros of the assembled free block of A kept for the
+                              row applies (0: the element form only)              */
+    int64_t ell_slots;     /* its stored entries, padding included (sliced ELL, every
+                              row as wide as the widest)                          */
 } cgs_mesh_info_t;
 
 /* Launch schedule of a mesh's kernels (cgs_mesh_get_schedule / _set_schedule):

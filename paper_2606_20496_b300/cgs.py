@@ -66,7 +66,8 @@ class MeshInfo(C.Structure):
                 ("footprint_bytes", C.c_size_t), ("setup_seconds", C.c_double),
                 ("kernel_launches", C.c_int64), ("n_box_entries", C.c_int64), ("n_lane_packs", C.c_int64),
                 ("loop", C.c_int32), ("coarse_solver", C.c_int32), ("xxt_nnz", C.c_int64), ("ar_nnz", C.c_int64),
-                ("coarse_operator", C.c_int32), ("n_hyb_entries", C.c_int64), ("n_jt_entries", C.c_int64)]
+                ("coarse_operator", C.c_int32), ("n_hyb_entries", C.c_int64), ("n_jt_entries", C.c_int64),
+                ("ell_nnz", C.c_int64), ("ell_slots", C.c_int64)]
 
 
 class Schedule(C.Structure):

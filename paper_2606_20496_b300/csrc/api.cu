@@ -1143,6 +1143,9 @@ cgs_status cgs_mesh_setup(cgs_ctx* ctx, const double* xyz, int64_t nv, const int
     m->info.xxt_nnz = (int64_t)hs.xc_idx.size();
     m->info.n_hyb_entries = (int64_t)hs.hr_vert.size();
     m->info.n_jt_entries = f64 ? hs.jt_nnz : 0;
+    m->info.ell_slots = (int64_t)hs.ell_col.size();
+    m->info.ell_nnz = 0;
+    for (int32_t c : hs.ell_col) m->info.ell_nnz += c >= 0;
     m->info.footprint_bytes = m->mem.bytes;
     m->info.setup_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     *out = m;
