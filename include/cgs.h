@@ -106,6 +106,10 @@ typedef struct {
                               FP32-bulk form (INVALID_ARG otherwise).  The
                               preconditioner then varies with r, which the flexible
                               PCG and cgs_solve_wrapped's flexible GMRES allow    */
+    int fault_negate_subdomain; /* testing aid, 0 in normal use: k > 0 negates the local
+                              matrix A_p of subdomain k - 1 (caller numbering) before
+                              its inverse is formed, so that the set-up takes its
+                              not-SPD path and returns CGS_ERR_NOT_SPD              */
 } cgs_params;
 
 typedef struct {

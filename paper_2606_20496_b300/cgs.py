@@ -57,7 +57,7 @@ class CGSError(RuntimeError):
 class Params(C.Structure):
     _fields_ = [("box", C.c_int * 3), ("box_margin", C.c_double), ("overlap_layers", C.c_int),
                 ("prec", C.c_int), ("form", C.c_int), ("coarse_solver", C.c_int), ("coarse_operator", C.c_int),
-                ("local_cg_steps", C.c_int)]
+                ("local_cg_steps", C.c_int), ("fault_negate_subdomain", C.c_int)]
 
 
 class MeshInfo(C.Structure):
@@ -212,7 +212,8 @@ def cgs_ctx_bytes_in_use(ctx) -> int:
 
 
 def cgs_mesh_setup(ctx, xyz, conn, dirichlet=None, elem_part=None, boxes=(4, 4, 4), margin=0.0, overlap=1,
-                   prec="fp64", form="hybrid", coarse="auto", coarse_operator="cellwise", local_cg_steps=0):
+                   prec="fp64", form="hybrid", coarse="auto", coarse_operator="cellwise", local_cg_steps=0,
+                   fault_negate_subdomain=0):
     xyz = np.ascontiguousarray(xyz, dtype=np.float64)
     conn = np.ascontiguousarray(conn, dtype=np.int32)
     d = None if dirichlet is None else np.ascontiguousarray(dirichlet, dtype=np.uint8)
@@ -220,7 +221,7 @@ def cgs_mesh_setup(ctx, xyz, conn, dirichlet=None, elem_part=None, boxes=(4, 4, 
     prm = Params((C.c_int * 3)(*[int(b) for b in boxes]), float(margin), int(overlap), PREC[prec], FORM[form],
                  COARSE[coarse] if isinstance(coarse, str) else int(coarse),
                  COARSE_OP[coarse_operator] if isinstance(coarse_operator, str) else int(coarse_operator),
-                 int(local_cg_steps))
+                 int(local_cg_steps), int(fault_negate_subdomain))
     mesh = C.c_void_p()
     st = load().cgs_mesh_setup(ctx, _ptr(xyz), xyz.shape[0], _ptr(conn), conn.shape[0], _ptr(d), _ptr(part),
                                C.byref(prm), C.byref(mesh))

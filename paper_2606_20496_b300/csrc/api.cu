@@ -757,6 +757,7 @@ cgs_status cgs_mesh_setup(cgs_ctx* ctx, const double* xyz, int64_t nv, const int
     if (prm.local_cg_steps < 0 || prm.local_cg_steps > 1024 ||
         (prm.local_cg_steps > 0 && prm.prec == CGS_FP16_LOCAL))
         return fail(CGS_ERR_INVALID_ARG, "local_cg_steps must be in [0, 1024], and 0 in the FP16-local form");
+    if (prm.fault_negate_subdomain < 0) return fail(CGS_ERR_INVALID_ARG, "fault_negate_subdomain must be >= 0");
     CGS_CUDA(cudaSetDevice(ctx->device));
     HostSetup hs;
     std::string err;

@@ -466,6 +466,8 @@ cgs_status host_setup(const double* xyz, int64_t nv, const int32_t* conn, int64_
                 for (int d = 0; d < nd; ++d)
                     for (int i = 0; i < m; ++i) ap[(size_t)d * m + i] = Ap[(size_t)i * m + (i + d) % m];
             }
+            if (prm.fault_negate_subdomain == (int)p + 1)   // testing aid: a non-SPD block
+                for (double& a : Ap) a = -a;
             std::vector<double> full((size_t)m * m);
             if (!spd_inverse(Ap.data(), m, full.data(), 1)) {
 #pragma omp atomic write

@@ -131,3 +131,21 @@ def test_nan_rhs_reports_breakdown(ctx, cube32, prec):
         assert st == cgs.ERR_BREAKDOWN
         st, its, rel = cgs.cgs_solve(h.handle, dev(b), x, rtol=1e-8)
         assert st == cgs.OK and rel[0] <= 1.5e-8
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_non_spd_local_block_is_reported(ctx, prec):
+    """A local matrix negated on the host (the set-up's testing aid) makes its
+    inverse fail: CGS_ERR_NOT_SPD, and a normal set-up of the same mesh
+    afterwards works."""
+    m, _ = meshes.workload_cube8()
+    with pytest.raises(cgs.CGSError) as ei:
+        cgs.cgs_mesh_setup(ctx, m.xyz, m.conn, elem_part=m.part, boxes=m.boxes, prec=prec,
+                           fault_negate_subdomain=5)
+    assert ei.value.status == cgs.ERR_NOT_SPD
+    with pytest.raises(cgs.CGSError) as ei:
+        cgs.cgs_mesh_setup(ctx, m.xyz, m.conn, elem_part=m.part, boxes=m.boxes, prec=prec,
+                           fault_negate_subdomain=-1)
+    assert ei.value.status == cgs.ERR_INVALID_ARG
+    h = cgs.cgs_mesh_setup(ctx, m.xyz, m.conn, elem_part=m.part, boxes=m.boxes, prec=prec)
+    cgs.cgs_mesh_free(h)
