@@ -517,10 +517,19 @@ def run_ours(args):
         for prec in ("fp64", "fp32"):
             r = run_pmg.run(ctx, solves=3, prec=prec)
             ax = r["steps"]["ax_N%d" % r["orders"][0]]
-            r["roofline"] = {"kernel": "sem_ax_kernel<%d>" % (r["orders"][0] + 1), "bound": "alu",
-                             "achieved": ax["tflops"], "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                             "frac": ax["fp64_frac"], "traffic": traffic_for("sem_ax", "pmg_cube32_order7", "sem.cu"),
-                             "peak_note": "FP64 FMA issue rate, 2 per clock per SM at 2032 MHz"}
+            if prec == "fp64":
+                r["roofline"] = {"kernel": "sem_ax_kernel<%d>" % (r["orders"][0] + 1), "bound": "alu",
+                                 "achieved": ax["tflops"], "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                                 "frac": ax["fp64_frac"],
+                                 "traffic": traffic_for("sem_ax", "pmg_cube32_order7", "sem.cu"),
+                                 "peak_note": "FP64 FMA issue rate, 2 per clock per SM at 2032 MHz"}
+            else:
+                r["roofline"] = {"kernel": "sem_ax_pair_kernel<%d>" % (r["orders"][0] + 1), "bound": "alu",
+                                 "achieved": ax["tops"], "peak": run_pmg.FP32_PEAK_TOPS,
+                                 "unit": "T FP32 instructions/s", "frac": ax["fp32_frac"],
+                                 "traffic": traffic_for("sem_ax_pair", "pmg_cube32_order7", "sem.cu"),
+                                 "peak_note": "FP32 issue rate, 128 lanes per clock per SM at 2032 MHz; "
+                                              "instructions counted per node of the pair arithmetic"}
             pmg["fp64_smoothers" if prec == "fp64" else "fp32_smoothers"] = r
 
     # ---- batched form (256 meshes x 4 right-hand sides in one graph) -----------------

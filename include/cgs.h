@@ -481,7 +481,10 @@ int64_t cgs_server_launches(const cgs_server* server);
  *     solve (Sec. 3, opening paragraph).
  * The SEM operator of order N is A_N = Q^T A_L Q with A^e = Dhat^T G^e Dhat,
  * GLL quadrature at the nodes and the trilinear map of each hexahedron; every
- * node of a boundary face is Dirichlet.  All arithmetic is float64.
+ * node of a boundary face is Dirichlet.  Precision follows the mesh: all
+ * float64 under an FP64 mesh; under the mixed forms the operator runs in
+ * float-pair arithmetic (about 48 bits) and the smoothers and transfers in
+ * float (vectors of the API and GMRES stay float64).
  *
  * Levels are numbered 0 (order orders[0]) to n_orders (order 1, whose nodes
  * are the mesh vertices in the mesh's own numbering).  Vectors of level l are

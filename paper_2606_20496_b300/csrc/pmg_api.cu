@@ -171,7 +171,21 @@ cgs_status cgs_pmg_setup(cgs_mesh* mesh, const double* xyz, int64_t nv, const in
         std::vector<int32_t> enc(h.l2g.size());
         for (size_t q = 0; q < enc.size(); ++q) enc[q] = h.dir[h.l2g[q]] ? -(h.l2g[q] + 1) : h.l2g[q];
         PMG_CUDA(upload(P.get(), &d.l2g, enc.data(), enc.size()));
-        PMG_CUDA(upload(P.get(), &d.G, h.G.data(), h.G.size()));
+        if (f32) {   // the operator in float pairs: the metric and D as (hi, lo)
+            auto pairs = [](const std::vector<double>& v) {
+                std::vector<float2> out(v.size());
+                for (size_t q = 0; q < v.size(); ++q) {
+                    const float hi = (float)v[q];
+                    out[q] = make_float2(hi, (float)(v[q] - (double)hi));
+                }
+                return out;
+            };
+            const std::vector<float2> Gp = pairs(h.G), Dp = pairs(h.D);
+            PMG_CUDA(upload(P.get(), &d.Gp, Gp.data(), Gp.size()));
+            PMG_CUDA(upload(P.get(), &d.Dp, Dp.data(), Dp.size()));
+        } else {
+            PMG_CUDA(upload(P.get(), &d.G, h.G.data(), h.G.size()));
+        }
         PMG_CUDA(upload(P.get(), &d.dir, h.dir.data(), h.dir.size()));
         PMG_CUDA(upload(P.get(), &d.inv_mult, h.inv_mult.data(), h.inv_mult.size()));
         PMG_CUDA(upload(P.get(), &d.S, h.S.data(), h.S.size()));

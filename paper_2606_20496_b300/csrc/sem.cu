@@ -13,12 +13,14 @@
 // input and never written.  Scatters are atomic adds (the order of the
 // additions, and so the last bits, varies from run to run).
 //
-// The operator is float64 always (it forms the outer residual).  The
-// smoother and the transfers run in float64 under an FP64 coarse mesh and in
-// float under the mixed forms' meshes (the multilevel preconditioner needs no
-// more: the outer GMRES is flexible), with level vectors in float below the
-// finest level; the finest level's r and z, and the order-1 vectors handed to
-// the coarse preconditioner, stay float64.
+// Precision follows the coarse mesh.  Under an FP64 mesh everything is
+// float64.  Under the mixed forms' meshes the operator runs in float-pair
+// arithmetic (about 48 bits: GMRES's residual, like the coarse solver's
+// outer operator), and the smoother and the transfers in float (the
+// multilevel preconditioner needs no more: the outer GMRES is flexible),
+// with level vectors in float below the finest level; the finest level's
+// vectors, and the order-1 vectors handed to the coarse preconditioner, stay
+// float64.
 #include <cuda_runtime.h>
 
 #include "sem.h"
@@ -80,6 +82,109 @@ __global__ void __launch_bounds__(P * P) sem_ax_kernel(const int32_t* __restrict
             v = fma(sD[m][k], wt[m], v);
         }
         if (gk[k] >= 0) atomicAdd(&y[gk[k]], v);
+    }
+}
+
+// Float-pair ("double-float") arithmetic of the mixed forms' operator: a
+// value is hi + lo (about 48 bits); products by the FMA-based two-product,
+// sums by Knuth's two-sum (published error-free transformations).
+__device__ __forceinline__ void two_sum_f(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+// (a.x + a.y)(b.x + b.y) ~= ph + pl (the lo * lo term dropped)
+__device__ __forceinline__ void pmul(float2 a, float2 b, float& ph, float& pl) {
+    ph = __fmul_rn(a.x, b.x);
+    pl = __fmaf_rn(a.x, b.x, -ph);
+    pl = __fmaf_rn(a.x, b.y, pl);
+    pl = __fmaf_rn(a.y, b.x, pl);
+}
+// (yh, yl) += a b, the low word left unnormalised
+__device__ __forceinline__ void pmad(float2 a, float2 b, float& yh, float& yl) {
+    float ph, pl, s, e;
+    pmul(a, b, ph, pl);
+    two_sum_f(yh, ph, s, e);
+    yh = s;
+    yl = __fadd_rn(yl, __fadd_rn(e, pl));
+}
+__device__ __forceinline__ float2 pnorm(float h, float l) {
+    const float s = __fadd_rn(h, l);
+    return make_float2(s, __fsub_rn(l, __fsub_rn(s, h)));
+}
+__device__ __forceinline__ float2 psplit(double x) {
+    const float h = __double2float_rn(x);
+    return make_float2(h, __double2float_rn(x - (double)h));
+}
+
+// y += A_n x with the metric and D as float pairs and every product and sum
+// in pair arithmetic on the FP32 pipes (about 2^-44 of the sum of the
+// terms' magnitudes), x read and y accumulated in float64: the operator of
+// the mixed forms, where float64 arithmetic (two FMAs per clock per SM on
+// B300) would bound the whole solve.
+template <int P>
+__global__ void __launch_bounds__(P * P) sem_ax_pair_kernel(const int32_t* __restrict__ l2g,
+                                                           const float2* __restrict__ G,
+                                                           const float2* __restrict__ Dg,
+                                                           const double* __restrict__ x, double* __restrict__ y) {
+    constexpr int P2 = P * P, P3 = P * P * P;
+    __shared__ float2 sD[P][P];
+    __shared__ float2 su[P][P][P];
+    __shared__ float2 sr[P][P][P];
+    __shared__ float2 ss[P][P][P];
+    const int e = blockIdx.x;
+    const int i = threadIdx.x % P, j = threadIdx.x / P;
+    sD[j][i] = Dg[j * P + i];
+    const int32_t* L = l2g + (size_t)e * P3;
+    int32_t gk[P];
+    float2 uk[P];
+#pragma unroll
+    for (int k = 0; k < P; ++k) {
+        gk[k] = __ldg(&L[k * P2 + j * P + i]);
+        uk[k] = gk[k] >= 0 ? psplit(__ldg(&x[gk[k]])) : make_float2(0.0f, 0.0f);
+        su[k][j][i] = uk[k];
+    }
+    __syncthreads();
+    const float2* Ge = G + (size_t)e * 6 * P3;
+    float2 wt[P];
+#pragma unroll
+    for (int k = 0; k < P; ++k) {
+        float rh = 0.f, rl = 0.f, sh = 0.f, sl = 0.f, th = 0.f, tl = 0.f;
+#pragma unroll
+        for (int m = 0; m < P; ++m) {
+            pmad(sD[i][m], su[k][j][m], rh, rl);
+            pmad(sD[j][m], su[k][m][i], sh, sl);
+            pmad(sD[k][m], uk[m], th, tl);
+        }
+        const float2 ur = pnorm(rh, rl), us = pnorm(sh, sl), ut = pnorm(th, tl);
+        const int node = k * P2 + j * P + i;
+        const float2 g00 = __ldg(&Ge[node]), g01 = __ldg(&Ge[P3 + node]), g02 = __ldg(&Ge[2 * P3 + node]);
+        const float2 g11 = __ldg(&Ge[3 * P3 + node]), g12 = __ldg(&Ge[4 * P3 + node]), g22 = __ldg(&Ge[5 * P3 + node]);
+        float ah = 0.f, al = 0.f, bh = 0.f, bl = 0.f, ch = 0.f, cl = 0.f;
+        pmad(g00, ur, ah, al);
+        pmad(g01, us, ah, al);
+        pmad(g02, ut, ah, al);
+        pmad(g01, ur, bh, bl);
+        pmad(g11, us, bh, bl);
+        pmad(g12, ut, bh, bl);
+        pmad(g02, ur, ch, cl);
+        pmad(g12, us, ch, cl);
+        pmad(g22, ut, ch, cl);
+        sr[k][j][i] = pnorm(ah, al);
+        ss[k][j][i] = pnorm(bh, bl);
+        wt[k] = pnorm(ch, cl);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < P; ++k) {
+        float vh = 0.f, vl = 0.f;
+#pragma unroll
+        for (int m = 0; m < P; ++m) {
+            pmad(sD[m][i], sr[k][j][m], vh, vl);
+            pmad(sD[m][j], ss[k][m][i], vh, vl);
+            pmad(sD[m][k], wt[m], vh, vl);
+        }
+        if (gk[k] >= 0) atomicAdd(&y[gk[k]], (double)vh + (double)vl);
     }
 }
 
@@ -319,7 +424,11 @@ __global__ void __launch_bounds__(P * P) sem_prolong_kernel(const int32_t* __res
 void launch_sem_ax(const SemDevLevel& L, int64_t ne, const double* x, double* y, cudaStream_t st) {
     if (ne == 0) return;
     const dim3 grid((unsigned)ne);
-    SEM_DISPATCH(L.p, sem_ax_kernel, L.l2g, L.G, L.D, x, y);
+    if (L.Gp) {
+        SEM_DISPATCH(L.p, sem_ax_pair_kernel, L.l2g, L.Gp, L.Dp, x, y);
+    } else {
+        SEM_DISPATCH(L.p, sem_ax_kernel, L.l2g, L.G, L.D, x, y);
+    }
 }
 
 namespace {

@@ -72,6 +72,8 @@ struct SemDevLevel {
     float* lam32 = nullptr;
     float* inv_mult32 = nullptr;
     float* I_next32 = nullptr;
+    float2* Gp = nullptr;           // metric as (hi, lo) pairs: the pair operator (f32 set)
+    float2* Dp = nullptr;           // D as pairs
     void* r = nullptr;              // work vectors of this level (levels below the finest):
     void* z = nullptr;              // float when f32, else float64
 };

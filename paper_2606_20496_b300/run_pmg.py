@@ -18,6 +18,12 @@ import numpy as np
 
 # FP64 FMA issue rate of B300: 2 per clock per SM, 148 SMs, 2032 MHz
 FP64_PEAK_TFLOPS = 2 * 2 * 148 * 2.032e9 / 1e12
+# FP32 instruction issue rate: 128 lanes per clock per SM
+FP32_PEAK_TOPS = 128 * 148 * 2.032e9 / 1e12
+# FP32 instructions per node of the float-pair operator: 57 pair
+# multiply-adds of 12 instructions (two-product 4, two-sum 6, 2 adds) and six
+# renormalisations of 3
+PAIR_OPS_PER_NODE = 57 * 12 + 6 * 3
 
 
 def sem_flops_bytes(p: int, ne: int, ng: int, ng_c: int = 0, pc: int = 0) -> dict:
@@ -103,6 +109,10 @@ def run(ctx, small: bool = False, solves: int = 3, rtol: float = 1e-8, restart: 
                 "ms": v, "tflops": fb[k]["flops"] / (v * 1e-3) / 1e12,
                 "fp64_frac": fb[k]["flops"] / (v * 1e-3) / 1e12 / FP64_PEAK_TFLOPS,
                 "gbs": fb[k]["bytes"] / (v * 1e-3) / 1e9, "flops": fb[k]["flops"], "bytes": fb[k]["bytes"]}
+        if prec != "fp64":   # the operator in float pairs: FP32 instructions
+            ops = m.ne * p ** 3 * PAIR_OPS_PER_NODE
+            steps[f"ax_N{orders[l]}"].update({"pair_ops": ops, "tops": ops / (t["ax"] * 1e-3) / 1e12,
+                                               "fp32_frac": ops / (t["ax"] * 1e-3) / 1e12 / FP32_PEAK_TOPS})
     r = torch.randn(n0, dtype=torch.float64, device="cuda")
     z = torch.empty_like(r)
     m_ms = events(lambda: cgs.cgs_pmg_apply_preconditioner(g.handle, r, z), 10)

@@ -199,7 +199,8 @@ def test_single_level_schedule(ctx):
 
 @pytest.mark.parametrize("name", list(CASES))
 def test_float_smoothers_under_a_mixed_coarse_mesh(ctx, built, name):
-    """Under an FP32-bulk coarse mesh the smoothers and transfers run in float
+    """Under an FP32-bulk coarse mesh the operator runs in float pairs (within
+    1e-11 of its largest entry) and the smoothers and transfers in float
     (level vectors below the finest in float): every entry of M r within
     2e-5 max|M r| of the FP64 oracle (float rounding of six contractions of
     length p and of the FP32-bulk coarse sweep), GMRES within one product of
@@ -211,6 +212,13 @@ def test_float_smoothers_under_a_mixed_coarse_mesh(ctx, built, name):
             cgs.PMG(h, m.xyz, m.conn, orders) as g:
         gm = cgs.cgs_pmg_node_map(g.handle, 0, m.ne)
         assert np.array_equal(gm, maps[0])
+        # the operator in float-pair arithmetic (about 48 bits)
+        for l in range(len(orders)):
+            lev = P.levels[l]
+            u = rand_level(P, l, 80 + l)
+            y = torch.empty(lev.ng, dtype=torch.float64, device="cuda")
+            cgs.cgs_pmg_apply_A(g.handle, l, dev(to_gpu_numbering(u, lev, maps[l], lev.ng)), y)
+            assert_close(local(host(y), maps[l]), local(lev.apply_A(u), lev.l2g), 1e-11)
         r = rand_level(P, 0, 70)
         z = torch.empty(f.ng, dtype=torch.float64, device="cuda")
         cgs.cgs_pmg_smooth(g.handle, 0, dev(to_gpu_numbering(r, f, gm, f.ng)), z)
