@@ -1038,20 +1038,38 @@ __device__ __forceinline__ void local_warp_item(const DevMesh* __restrict__ mesh
             const T x1 = h1 ? __ldg(&r[v1]) : T(0);
             T y0 = stage<T, Stor>(inv, io + lane, sc) * x0;
             T y1 = h1 ? stage<T, Stor>(inv, io + lane + 32, sc) * x1 : T(0);
-            for (int d = 1; d < nd; ++d) {
-                const size_t row = io + (size_t)d * m;
+            // eight diagonals at a time: their (up to) 32 entries per lane are
+            // loaded before the shuffles and multiply-adds that use them
+            for (int d0 = 1; d0 < nd; d0 += 8) {
+                T ep[2][8], em[2][8];
 #pragma unroll
-                for (int half = 0; half < 2; ++half) {
-                    const int i = lane + 32 * half;
-                    int jp = i + d;
-                    if (jp >= m) jp -= m;
-                    int jm = i - d;
-                    if (jm < 0) jm += m;
-                    const T pa = __shfl_sync(0xffffffffu, x0, jp & 31), pb = __shfl_sync(0xffffffffu, x1, jp & 31);
-                    const T ma = __shfl_sync(0xffffffffu, x0, jm & 31), mb = __shfl_sync(0xffffffffu, x1, jm & 31);
-                    if (i < m) {
-                        T acc = stage<T, Stor>(inv, row + i, sc) * (jp < 32 ? pa : pb);
-                        if (2 * d != m) acc += stage<T, Stor>(inv, row + jm, sc) * (jm < 32 ? ma : mb);
+                for (int g = 0; g < 8; ++g) {
+                    const int d = d0 + g;
+                    const size_t row = io + (size_t)d * m;
+#pragma unroll
+                    for (int half = 0; half < 2; ++half) {
+                        const int i = lane + 32 * half;
+                        int jm = i - d;
+                        if (jm < 0) jm += m;
+                        const bool ok = d < nd && i < m;
+                        ep[half][g] = ok ? stage<T, Stor>(inv, row + i, sc) : T(0);
+                        em[half][g] = (ok && 2 * d != m) ? stage<T, Stor>(inv, row + jm, sc) : T(0);
+                    }
+                }
+#pragma unroll
+                for (int g = 0; g < 8; ++g) {
+                    const int d = d0 + g;
+                    if (d >= nd) break;
+#pragma unroll
+                    for (int half = 0; half < 2; ++half) {
+                        const int i = lane + 32 * half;
+                        int jp = i + d;
+                        if (jp >= m) jp -= m;
+                        int jm = i - d;
+                        if (jm < 0) jm += m;
+                        const T pa = __shfl_sync(0xffffffffu, x0, jp & 31), pb = __shfl_sync(0xffffffffu, x1, jp & 31);
+                        const T ma = __shfl_sync(0xffffffffu, x0, jm & 31), mb = __shfl_sync(0xffffffffu, x1, jm & 31);
+                        const T acc = ep[half][g] * (jp < 32 ? pa : pb) + em[half][g] * (jm < 32 ? ma : mb);
                         if (half == 0)
                             y0 += acc;
                         else
