@@ -93,7 +93,7 @@ struct Engine {
     // persistent loop (mixed forms, schedule.persistent): its grid barrier
     // and the resident block count
     GridBar* bar = nullptr;
-    int pblocks = 0;
+    int pblocks_of[2] = {0, 0};   // persistent-loop blocks without / with packs above 32 dofs
     // launch accounting and the optional event profiler
     int64_t launches = 0;
     bool prof = false;
@@ -274,8 +274,9 @@ bool precond_body(Engine& E, const Vecs& V, cudaStream_t st, bool dots = false,
         K(CGS_K_LOCAL, launch_local(P, V, E.prec, V.s, V.z, 2, st));
     } else {
         // the restriction of s fused with the local solves when every
-        // subdomain is in packs
-        if (!E.f64 && !P.nwork[kWorkSub] && P.any_nr && P.nwork[kWorkBoxEnt]) {
+        // subdomain is in packs of at most 32 dofs (the conditions under
+        // which launch_local_restrict launches)
+        if (!E.f64 && !P.nwork[kWorkSub] && !P.lane_big && P.any_nr && P.nwork[kWorkBoxEnt]) {
             K(CGS_K_LOCAL, launch_local_restrict(P, V, E.prec, static_cast<const float*>(V.s),
                                                  static_cast<float*>(V.z), V.rr, st));
             return box_correction(E, V, dots, st, true, cond);
@@ -394,11 +395,18 @@ cgs_status build_loop_graph(Engine& E) {
 // Whether the engine runs its iterations in the persistent loop (mixed forms
 // only): by the schedule, or (auto) when the element tiles of a launch fit
 // about two per resident block.
+// Resident blocks of the persistent loop for the engine's current plan (the
+// variant with packs above 32 dofs holds one block per SM), cached.
+int pblocks(Engine& E) {
+    int& b = E.pblocks_of[E.P.lane_big ? 1 : 0];
+    if (!b) b = persistent_blocks(E.prec, E.P.lane_big);
+    return b;
+}
+
 bool use_persistent(Engine& E, const Schedule& sch) {
     // the persistent loop runs the dense reduced product only
     if (E.f64 || sch.persistent == 0 || E.P.any_xxt) return false;
-    if (!E.pblocks) E.pblocks = persistent_blocks(E.prec);
-    if (E.pblocks <= 0) return false;
+    if (pblocks(E) <= 0) return false;
     return sch.persistent == 1;
 }
 
@@ -408,10 +416,9 @@ cudaError_t persistent_launch(Engine& E, int max_iters, cudaStream_t st) {
         cudaError_t e = cudaMalloc(&E.bar, sizeof(GridBar));
         if (e != cudaSuccess) return e;
     }
-    if (!E.pblocks) E.pblocks = persistent_blocks(E.prec);
     cudaError_t e = cudaMemsetAsync(E.bar, 0, sizeof(GridBar), st);
     if (e != cudaSuccess) return e;
-    K(CGS_K_LOOP, e = launch_pcg_persistent(E.P, E.V, E.prec, E.form == CGS_HYBRID, E.bar, max_iters, E.pblocks, st));
+    K(CGS_K_LOOP, e = launch_pcg_persistent(E.P, E.V, E.prec, E.form == CGS_HYBRID, E.bar, max_iters, pblocks(E), st));
     return e;
 }
 
@@ -789,6 +796,8 @@ cgs_status cgs_mesh_setup(cgs_ctx* ctx, const double* xyz, int64_t nv, const int
     d.ne = ne;
     d.n_sub = hs.n_wsub;
     d.n_pack = (int64_t)hs.pack_m.size();
+    for (int c : hs.pack_m) d.max_pack_m = std::max(d.max_pack_m, c);
+    for (int c : hs.rpack_m) d.max_pack_m = std::max(d.max_pack_m, c);
     d.nr = hs.nr;
     for (int k = 0; k < 3; ++k) {
         d.b[k] = hs.b[k];
@@ -1092,6 +1101,7 @@ cgs_status cgs_mesh_setup(cgs_ctx* ctx, const double* xyz, int64_t nv, const int
     E.P.max_m = d.max_m;
     E.P.any_nr = hs.nr > 0;
     E.P.hyb_restrict = d.nhr > 0;
+    E.P.lane_big = d.max_pack_m > 32;
     E.P.ell = d.nslice > 0 && d.ell_val;
     E.P.ell_pair = d.nslice > 0 && d.ell_pair;
     {
@@ -1603,6 +1613,7 @@ cgs_status cgs_batch_create(cgs_ctx* ctx, cgs_mesh* const* meshes, int nmesh, in
         sizes[i] = m->sizes;
         E.P.max_m = std::max(E.P.max_m, m->d.max_m);
         E.P.any_nr = E.P.any_nr || m->d.nr > 0;
+        E.P.lane_big = E.P.lane_big || m->d.max_pack_m > 32;
         E.P.ell = (i == 0 || E.P.ell) && m->d.nslice > 0 && m->d.ell_val;
         E.P.ell_pair = (i == 0 || E.P.ell_pair) && m->d.nslice > 0 && m->d.ell_pair;
         B->max_nv = std::max(B->max_nv, m->d.nv);
@@ -1923,6 +1934,7 @@ cudaError_t server_tables(cgs_server* sv, const std::vector<int>& ids, cgs_serve
         append_mesh_work(tabs, ss.reg, k, ss.voff, ss.roff, ss.poff, m->sizes, sv->sch);
         P.max_m = std::max(P.max_m, m->d.max_m);
         P.any_nr = P.any_nr || m->d.nr > 0;
+        P.lane_big = P.lane_big || m->d.max_pack_m > 32;
         P.ell = P.ell && m->d.nslice > 0 && m->d.ell_val;
         P.ell_pair = P.ell_pair && m->d.nslice > 0 && m->d.ell_pair;
     }

@@ -133,6 +133,7 @@ struct DevMesh {
     const int32_t* conn = nullptr;     // ne*8 (int4 x2 per element)
     const uint8_t* dir = nullptr;      // nv, 1 = Dirichlet
     const double* a36 = nullptr;       // [36][ne]
+    int max_pack_m = 0;                // largest lane- or row-pack class
     int64_t nslice = 0;                // sliced-ELL rows of the assembled A (0: none)
     int32_t ell_w = 0;                 // entries per row (every slice as wide)
     const int64_t* ell_ptr = nullptr;
@@ -271,6 +272,7 @@ struct Plan {
     bool any_xxt = false;                  // some mesh solves its reduced system by XX^T
     bool hyb_restrict = false;             // every mesh with a reduced space has the hybrid
                                            // restriction entries (no s = r - A l needed)
+    bool lane_big = false;                 // some mesh has lane or row packs of more than 32 dofs
     bool ell = false;                      // every mesh has the assembled A in float64:
                                            // the FP64 applies run by rows
     bool ell_pair = false;                 // every mesh has it in float pairs: the PCG's
@@ -323,8 +325,9 @@ struct Work {
 
 // Lane packs of the mixed-form local solves: subdomains with at most
 // kLaneMaxM dofs, padded to the next size class, 32 of one class per pack.
-constexpr int kLaneMaxM = 32;
-constexpr int kLaneClasses[] = {8, 12, 16, 18, 20, 24, 27, 32};
+constexpr int kLaneMaxM = 32;        // FP64 form (a lane keeps 2M doubles in registers)
+constexpr int kLaneMaxMixed = 64;    // mixed forms: classes above 32 run in kernels of their own
+constexpr int kLaneClasses[] = {8, 12, 16, 18, 20, 24, 27, 32, 40, 48, 56, 64};
 inline int lane_class(int m) {
     for (int c : kLaneClasses)
         if (m <= c) return c;

@@ -1313,23 +1313,39 @@ __device__ __forceinline__ void lane_solve(Entries A, const int32_t* __restrict_
     }
 }
 
-template <typename T, class Entries>
+// the size classes of up to 32 dofs (kBig false) or above (kBig true, the
+// mixed forms only: a lane keeps 2 x 64 floats in registers, so these run in
+// kernels of their own with one block per SM, leaving the small classes'
+// occupancy alone); a class of the other group does nothing
+template <bool kBig, typename T, class Entries>
 __device__ __forceinline__ void lane_dispatch(int Mc, const Entries& A, const int32_t* idx, const T* r, T* out,
                                               const T* wov, const T* went, int lane) {
-    switch (Mc) {
-        case 8: lane_solve<8, T>(A, idx, r, out, wov, went, lane); break;
-        case 12: lane_solve<12, T>(A, idx, r, out, wov, went, lane); break;
-        case 16: lane_solve<16, T>(A, idx, r, out, wov, went, lane); break;
-        case 18: lane_solve<18, T>(A, idx, r, out, wov, went, lane); break;
-        case 20: lane_solve<20, T>(A, idx, r, out, wov, went, lane); break;
-        case 24: lane_solve<24, T>(A, idx, r, out, wov, went, lane); break;
-        case 27: lane_solve<27, T>(A, idx, r, out, wov, went, lane); break;
-        default: lane_solve<32, T>(A, idx, r, out, wov, went, lane); break;
+    if (!kBig) {
+        switch (Mc) {
+            case 8: lane_solve<8, T>(A, idx, r, out, wov, went, lane); break;
+            case 12: lane_solve<12, T>(A, idx, r, out, wov, went, lane); break;
+            case 16: lane_solve<16, T>(A, idx, r, out, wov, went, lane); break;
+            case 18: lane_solve<18, T>(A, idx, r, out, wov, went, lane); break;
+            case 20: lane_solve<20, T>(A, idx, r, out, wov, went, lane); break;
+            case 24: lane_solve<24, T>(A, idx, r, out, wov, went, lane); break;
+            case 27: lane_solve<27, T>(A, idx, r, out, wov, went, lane); break;
+            case 32: lane_solve<32, T>(A, idx, r, out, wov, went, lane); break;
+            default: break;
+        }
+    } else {
+        switch (Mc) {
+            case 40: lane_solve<40, T>(A, idx, r, out, wov, went, lane); break;
+            case 48: lane_solve<48, T>(A, idx, r, out, wov, went, lane); break;
+            case 56: lane_solve<56, T>(A, idx, r, out, wov, went, lane); break;
+            case 64: lane_solve<64, T>(A, idx, r, out, wov, went, lane); break;
+            default: break;
+        }
     }
 }
 
-// out += W_ov sum_p R_p^T A_p^{-1} R_p r over the lane packs (float r, out).
-template <typename Stor>
+// out += W_ov sum_p R_p^T A_p^{-1} R_p r over the lane packs (float r, out)
+// of the small classes, or (kBig) of the classes above 32 dofs.
+template <typename Stor, bool kBig = false>
 __device__ __forceinline__ void local_lane_item(const DevMesh* __restrict__ meshes, const Work& w, Vecs V,
                                                 const float* __restrict__ rin, float* __restrict__ outv, int weighted) {
     CGS_ITEM_PROLOGUE();
@@ -1345,11 +1361,11 @@ __device__ __forceinline__ void local_lane_item(const DevMesh* __restrict__ mesh
         const int64_t ao = __ldg(&M.pack_inv_off[pk]);
         if (std::is_same<Stor, float>::value) {
             LaneEntries32 A{reinterpret_cast<const float4*>(M.pack_inv32 + ao), lane, {}};
-            lane_dispatch(Mc, A, idx, r, out, wov, went, lane);
+            lane_dispatch<kBig>(Mc, A, idx, r, out, wov, went, lane);
         } else {
             LaneEntries16 A{reinterpret_cast<const uint4*>(M.pack_inv16 + ao), lane,
                             __ldg(&M.pack_scale[(size_t)pk * 32 + lane]), {}};
-            lane_dispatch(Mc, A, idx, r, out, wov, went, lane);
+            lane_dispatch<kBig>(Mc, A, idx, r, out, wov, went, lane);
         }
     }
 }
@@ -1362,6 +1378,17 @@ __global__ void __launch_bounds__(kBlock, 2) local_lane_kernel(const DevMesh* __
     const Work w_ = work[blockIdx.x];
     pdl_wait();
     local_lane_item<Stor>(meshes, w_, V, rin, outv, weighted);
+}
+
+// the classes above 32 dofs (mixed forms): one block of 8 warps per SM
+template <typename Stor>
+__global__ void __launch_bounds__(kBlock, 1) local_lane_big_kernel(const DevMesh* __restrict__ meshes,
+                                                               const Work* __restrict__ work, Vecs V,
+                                                               const float* __restrict__ rin,
+                                                               float* __restrict__ outv, int weighted) {
+    const Work w_ = work[blockIdx.x];
+    pdl_wait();
+    local_lane_item<Stor, true>(meshes, w_, V, rin, outv, weighted);
 }
 
 // The FP64 form's lane packs (meshes with many small subdomains): the same
@@ -1398,7 +1425,7 @@ __global__ void __launch_bounds__(kBlock, 1) local_lane64_kernel(const DevMesh* 
         const double* went = weighted == 2 ? M.pack_went64 + io : nullptr;
         const int64_t ao = __ldg(&M.pack_inv_off[pk]);
         LaneEntries64 A{reinterpret_cast<const double2*>(M.pack_inv64 + ao), lane, {}};
-        lane_dispatch<double>(Mc, A, idx, r, out, wov, went, lane);
+        lane_dispatch<false, double>(Mc, A, idx, r, out, wov, went, lane);
     }
 }
 
@@ -1440,23 +1467,35 @@ __device__ __forceinline__ void row_solve(Entries A, const int32_t* __restrict__
     }
 }
 
-template <class Entries>
+template <bool kBig, class Entries>
 __device__ __forceinline__ void row_dispatch(int Mc, const Entries& A, const int32_t* idx, const float* r,
                                              float* out, const float* wov, const float* went, int lane) {
-    switch (Mc) {
-        case 8: row_solve<8>(A, idx, r, out, wov, went, lane); break;
-        case 12: row_solve<12>(A, idx, r, out, wov, went, lane); break;
-        case 16: row_solve<16>(A, idx, r, out, wov, went, lane); break;
-        case 18: row_solve<18>(A, idx, r, out, wov, went, lane); break;
-        case 20: row_solve<20>(A, idx, r, out, wov, went, lane); break;
-        case 24: row_solve<24>(A, idx, r, out, wov, went, lane); break;
-        case 27: row_solve<27>(A, idx, r, out, wov, went, lane); break;
-        default: row_solve<32>(A, idx, r, out, wov, went, lane); break;
+    if (!kBig) {
+        switch (Mc) {
+            case 8: row_solve<8>(A, idx, r, out, wov, went, lane); break;
+            case 12: row_solve<12>(A, idx, r, out, wov, went, lane); break;
+            case 16: row_solve<16>(A, idx, r, out, wov, went, lane); break;
+            case 18: row_solve<18>(A, idx, r, out, wov, went, lane); break;
+            case 20: row_solve<20>(A, idx, r, out, wov, went, lane); break;
+            case 24: row_solve<24>(A, idx, r, out, wov, went, lane); break;
+            case 27: row_solve<27>(A, idx, r, out, wov, went, lane); break;
+            case 32: row_solve<32>(A, idx, r, out, wov, went, lane); break;
+            default: break;
+        }
+    } else {
+        switch (Mc) {
+            case 40: row_solve<40>(A, idx, r, out, wov, went, lane); break;
+            case 48: row_solve<48>(A, idx, r, out, wov, went, lane); break;
+            case 56: row_solve<56>(A, idx, r, out, wov, went, lane); break;
+            case 64: row_solve<64>(A, idx, r, out, wov, went, lane); break;
+            default: break;
+        }
     }
 }
 
-// out += W_ov sum_p R_p^T A_p^{-1} R_p r over the row packs (float r, out).
-template <typename Stor>
+// out += W_ov sum_p R_p^T A_p^{-1} R_p r over the row packs (float r, out)
+// of the small classes, or (kBig) of the classes above 32 dofs.
+template <typename Stor, bool kBig = false>
 __device__ __forceinline__ void local_rowpack_item(const DevMesh* __restrict__ meshes, const Work& w, Vecs V,
                                                    const float* __restrict__ rin, float* __restrict__ outv,
                                                    int weighted) {
@@ -1473,11 +1512,11 @@ __device__ __forceinline__ void local_rowpack_item(const DevMesh* __restrict__ m
         const int64_t ao = __ldg(&M.rpack_inv_off[pk]);
         if (std::is_same<Stor, float>::value) {
             LaneEntries32 A{reinterpret_cast<const float4*>(M.rpack_inv32 + ao), lane, {}};
-            row_dispatch(Mc, A, idx, r, out, wov, went, lane);
+            row_dispatch<kBig>(Mc, A, idx, r, out, wov, went, lane);
         } else {
             LaneEntries16 A{reinterpret_cast<const uint4*>(M.rpack_inv16 + ao), lane,
                             __ldg(&M.rpack_scale[(size_t)pk * 32 + lane]), {}};
-            row_dispatch(Mc, A, idx, r, out, wov, went, lane);
+            row_dispatch<kBig>(Mc, A, idx, r, out, wov, went, lane);
         }
     }
 }
@@ -1489,6 +1528,17 @@ __global__ void __launch_bounds__(kBlock) local_rowpack_kernel(const DevMesh* __
     const Work w_ = work[blockIdx.x];
     pdl_wait();
     local_rowpack_item<Stor>(meshes, w_, V, rin, outv, weighted);
+}
+
+// the classes above 32 dofs (mixed forms)
+template <typename Stor>
+__global__ void __launch_bounds__(kBlock, 1) local_rowpack_big_kernel(const DevMesh* __restrict__ meshes,
+                                                               const Work* __restrict__ work, Vecs V,
+                                                               const float* __restrict__ rin,
+                                                               float* __restrict__ outv, int weighted) {
+    const Work w_ = work[blockIdx.x];
+    pdl_wait();
+    local_rowpack_item<Stor, true>(meshes, w_, V, rin, outv, weighted);
 }
 
 // ---------------------------------------------------------------------------
@@ -2850,8 +2900,10 @@ __device__ void abort_slots(SolveScalars* S, int nslots) {
         return;                            \
     }
 
-template <typename Stor>
-__global__ void __launch_bounds__(kBlock, 2) pcg_persistent_kernel(const DevMesh* __restrict__ meshes, LoopTables T,
+// kBig: some mesh has packs above 32 dofs, run here too (a lane then holds
+// up to 2 x 64 floats, so one block per SM)
+template <typename Stor, bool kBig>
+__global__ void __launch_bounds__(kBlock, kBig ? 1 : 2) pcg_persistent_kernel(const DevMesh* __restrict__ meshes, LoopTables T,
                                                                    Vecs V, GridBar* bar, int nslots, int hybrid,
                                                                    int any_nr, int big_subs, int max_iters,
                                                                    int wait_limit, int bar_limit) {
@@ -2870,6 +2922,11 @@ __global__ void __launch_bounds__(kBlock, 2) pcg_persistent_kernel(const DevMesh
         // z = M r
         CGS_FOR_ITEMS(kWorkPack, k) local_lane_item<Stor>(meshes, T.w[kWorkPack][k], V, s, z, hybrid);
         CGS_FOR_ITEMS(kWorkRowPack, k) local_rowpack_item<Stor>(meshes, T.w[kWorkRowPack][k], V, s, z, hybrid);
+        if (kBig) {
+            CGS_FOR_ITEMS(kWorkPack, k) local_lane_item<Stor, true>(meshes, T.w[kWorkPack][k], V, s, z, hybrid);
+            CGS_FOR_ITEMS(kWorkRowPack, k)
+                local_rowpack_item<Stor, true>(meshes, T.w[kWorkRowPack][k], V, s, z, hybrid);
+        }
         CGS_FOR_ITEMS(kWorkSub, k) local_warp_item<float, Stor>(meshes, T.w[kWorkSub][k], V, s, z, hybrid);
         if (big_subs)
             CGS_FOR_ITEMS(kWorkSub, k) local_block_item<float, Stor>(meshes, T.w[kWorkSub][k], V, s, z, hybrid);
@@ -3041,8 +3098,9 @@ void launch_apply28f_tiled(const Plan& P, const Vecs& V, const float* x, float* 
 void launch_local(const Plan& P, const Vecs& V, cgs_precision prec, const void* r, void* out, int weighted,
                   cudaStream_t st) {
     const int wt = weighted;
-    // mixed forms: subdomains of at most kLaneMaxM dofs in lane packs, or in
-    // row packs (small meshes)
+    // mixed forms: subdomains of at most kLaneMaxMixed dofs in lane packs, or
+    // in row packs (small meshes); the classes above 32 dofs in kernels of
+    // their own
     if (prec != CGS_FP64 && P.nwork[kWorkRowPack]) {
         const float* rf = static_cast<const float*>(r);
         float* of = static_cast<float*>(out);
@@ -3052,6 +3110,14 @@ void launch_local(const Plan& P, const Vecs& V, cgs_precision prec, const void* 
         else
             launch_pdl(P.pdl, local_rowpack_kernel<__half>, P.nwork[kWorkRowPack], kBlock, 0, st, P.meshes,
                        P.work[kWorkRowPack], V, rf, of, wt);
+        if (P.lane_big) {
+            if (prec == CGS_FP32_BULK)
+                launch_pdl(P.pdl, local_rowpack_big_kernel<float>, P.nwork[kWorkRowPack], kBlock, 0, st, P.meshes,
+                           P.work[kWorkRowPack], V, rf, of, wt);
+            else
+                launch_pdl(P.pdl, local_rowpack_big_kernel<__half>, P.nwork[kWorkRowPack], kBlock, 0, st, P.meshes,
+                           P.work[kWorkRowPack], V, rf, of, wt);
+        }
     }
     if (prec != CGS_FP64 && P.nwork[kWorkPack]) {
         const float* rf = static_cast<const float*>(r);
@@ -3062,6 +3128,14 @@ void launch_local(const Plan& P, const Vecs& V, cgs_precision prec, const void* 
         else
             launch_pdl(P.pdl, local_lane_kernel<__half>, P.nwork[kWorkPack], kBlock, 0, st, P.meshes, P.work[kWorkPack],
                        V, rf, of, wt);
+        if (P.lane_big) {
+            if (prec == CGS_FP32_BULK)
+                launch_pdl(P.pdl, local_lane_big_kernel<float>, P.nwork[kWorkPack], kBlock, 0, st, P.meshes,
+                           P.work[kWorkPack], V, rf, of, wt);
+            else
+                launch_pdl(P.pdl, local_lane_big_kernel<__half>, P.nwork[kWorkPack], kBlock, 0, st, P.meshes,
+                           P.work[kWorkPack], V, rf, of, wt);
+        }
     }
     if (prec == CGS_FP64 && P.nwork[kWorkPack]) {
         static int sms = 0;
@@ -3106,8 +3180,9 @@ void launch_local(const Plan& P, const Vecs& V, cgs_precision prec, const void* 
 
 bool launch_local_restrict(const Plan& P, const Vecs& V, cgs_precision prec, const float* s, float* z, void* rr,
                            cudaStream_t st) {
-    // only when every subdomain is in packs (no warp-list launch needed)
-    if (prec == CGS_FP64 || P.nwork[kWorkSub] || !P.any_nr || !P.nwork[kWorkBoxEnt]) return false;
+    // only when every subdomain is in packs of at most 32 dofs (no warp-list
+    // or large-class launch needed)
+    if (prec == CGS_FP64 || P.nwork[kWorkSub] || P.lane_big || !P.any_nr || !P.nwork[kWorkBoxEnt]) return false;
     const bool rowp = P.nwork[kWorkRowPack] > 0;
     const unsigned int nl = rowp ? P.nwork[kWorkRowPack] : P.nwork[kWorkPack];
     const Work* wl = rowp ? P.work[kWorkRowPack] : P.work[kWorkPack];
@@ -3324,15 +3399,18 @@ void launch_pcg_update_p(const Plan& P, const Vecs& V, Tq* q, const cudaGraphCon
 
 // Blocks of the persistent loop that fit on the device at once (the
 // cooperative launch requires all of them resident).
-int persistent_blocks(cgs_precision prec) {
+static const void* persistent_fn(cgs_precision prec, bool big) {
+    if (prec == CGS_FP16_LOCAL)
+        return big ? (const void*)pcg_persistent_kernel<__half, true> : (const void*)pcg_persistent_kernel<__half, false>;
+    return big ? (const void*)pcg_persistent_kernel<float, true> : (const void*)pcg_persistent_kernel<float, false>;
+}
+
+int persistent_blocks(cgs_precision prec, bool big) {
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int smem = (int)(2 * kTileVerts * sizeof(float2));
-    if (prec == CGS_FP16_LOCAL)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pcg_persistent_kernel<__half>, kBlock, smem);
-    else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pcg_persistent_kernel<float>, kBlock, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persistent_fn(prec, big), kBlock, smem);
     return per_sm * sms;
 }
 
@@ -3349,9 +3427,7 @@ cudaError_t launch_pcg_persistent(const Plan& P, const Vecs& V, cgs_precision pr
     const DevMesh* meshes = P.meshes;
     void* args[] = {(void*)&meshes, &T, &Vv, &bar, &nslots, &hyb, &any_nr, &big, &max_iters, &wait_limit, &bar_limit};
     const int smem = (int)(2 * kTileVerts * sizeof(float2));
-    const void* fn = prec == CGS_FP16_LOCAL ? (const void*)pcg_persistent_kernel<__half>
-                                            : (const void*)pcg_persistent_kernel<float>;
-    return cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(kBlock), args, smem, st);
+    return cudaLaunchCooperativeKernel(persistent_fn(prec, P.lane_big), dim3(blocks), dim3(kBlock), args, smem, st);
 }
 
 void launch_resid_norm(const Plan& P, const Vecs& V, cudaStream_t st) {

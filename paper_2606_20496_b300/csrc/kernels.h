@@ -99,8 +99,8 @@ void launch_pcg_update_p(const Plan& P, const Vecs& V, Tq* q, const cudaGraphCon
                          cudaStream_t st);
 // Persistent PCG loop of the mixed forms: up to max_iters iterations over
 // every slot of the plan in one cooperative launch of `blocks` blocks (at
-// most persistent_blocks(prec)); bar must be zero on entry.
-int persistent_blocks(cgs_precision prec);
+// most persistent_blocks(prec, P.lane_big)); bar must be zero on entry.
+int persistent_blocks(cgs_precision prec, bool big);
 cudaError_t launch_pcg_persistent(const Plan& P, const Vecs& V, cgs_precision prec, bool hybrid, GridBar* bar,
                                   int max_iters, int blocks, cudaStream_t st);
 void launch_resid_norm(const Plan& P, const Vecs& V, cudaStream_t st);

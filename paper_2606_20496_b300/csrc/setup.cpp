@@ -391,12 +391,14 @@ cgs_status host_setup(const double* xyz, int64_t nv, const int32_t* conn, int64_
     std::vector<std::vector<int32_t>> sub_sets(n_sub);
     std::vector<std::vector<double>> sub_inv(n_sub);
     std::vector<std::vector<double>> sub_ap(prm.local_cg_steps > 0 ? n_sub : 0);   // A_p, cyclic diagonals
-    // subdomains of at most kLaneMaxM dofs are solved one per lane: always in
-    // the mixed forms, and in the FP64 form when there are enough of them to
-    // fill the GPU one lane each (otherwise a warp per subdomain)
+    // subdomains of at most kLaneMaxM dofs (kLaneMaxMixed in the mixed forms)
+    // are solved one per lane: always in the mixed forms, and in the FP64 form
+    // when there are enough of them to fill the GPU one lane each (otherwise
+    // a warp per subdomain)
     // (inexact local solves run CG on A_p itself, one warp per subdomain)
     const bool inexact = prm.local_cg_steps > 0;
     const bool lane_packs = !inexact && (prm.prec != CGS_FP64 || n_sub >= kRowPackMaxSubs);
+    const int lane_max = prm.prec == CGS_FP64 ? kLaneMaxM : kLaneMaxMixed;
     bool not_spd = false, too_big = false;
 #pragma omp parallel
     {
@@ -475,7 +477,7 @@ cgs_status host_setup(const double* xyz, int64_t nv, const int32_t* conn, int64_
                 continue;
             }
             std::vector<double>& pk = sub_inv[p];
-            if (lane_packs && m <= kLaneMaxM) {
+            if (lane_packs && m <= lane_max) {
                 // upper triangle, row-major (lane packs)
                 pk.resize((size_t)m * (m + 1) / 2);
                 size_t e = 0;
@@ -559,7 +561,7 @@ cgs_status host_setup(const double* xyz, int64_t nv, const int32_t* conn, int64_
     }
     auto in_lane = [&](int64_t p) {
         const size_t m = sub_sets[p].size();
-        return lane_packs && m > 0 && m <= (size_t)kLaneMaxM;
+        return lane_packs && m > 0 && m <= (size_t)lane_max;
     };
     // warp-kernel subdomains, caller order
     S.wsub_ptr.assign(1, 0);

@@ -5,10 +5,12 @@ mesh's schedule: lane packs (one lane per subdomain) or row packs (four lanes
 per subdomain) for the local solves, TMA-staged or thread-streamed element
 tiles for both operator applies, interpolation by vertex (dots fused) or by
 cell-sorted entries, and one launch per phase or the persistent loop.  Each
-variant is forced here and compared with the oracle on two meshes: cube32
-(4,096 subdomains: row packs by default) and the halved hollow cylinder
+variant is forced here and compared with the oracle on three meshes: cube32
+(4,096 subdomains: row packs by default), the halved hollow cylinder
 (137,280 vertices, 16,384 subdomains: lane packs by default, the layout the
-full-size cylinder runs).
+full-size cylinder runs) and a perturbed 13^3 cube cut into 3- and
+2-element segments (125 subdomains of 27 to 64 dofs: the size classes above
+32 dofs, which run in kernels of their own).
 
 Bars, as for the default schedule (Sec. 3 Eq. (4) for the local solves,
 Eqs. (3) and (5) for M r, flexible PCG around them):
@@ -28,7 +30,11 @@ from oracle import cgs_oracle as O  # noqa: E402
 from paper_2606_20496_b300 import cgs, meshes  # noqa: E402
 
 U32, U16 = 2.0 ** -24, 2.0 ** -11
-MESHES = {"cube32": meshes.workload_cube32, "cyl2": lambda: meshes.workload_cylinder(scale=2)}
+MESHES = {"cube32": meshes.workload_cube32, "cyl2": lambda: meshes.workload_cylinder(scale=2),
+          # 3- and 2-element segments: subdomains of 27 to 64 dofs, the
+          # larger classes (40, 48, 64) in packs of their own
+          "cube13_mixed": lambda: (lambda m: (m, meshes.rhs(m.nv, 13)))(
+              meshes.cube(13, perturb=0.15, seed=[2, 13], part_mode="mixed", name="cube13_mixed"))}
 # schedule fields forced by each variant (the rest keep the set-up defaults)
 VARIANTS = {
     "lane_packs": dict(row_packs=0),
