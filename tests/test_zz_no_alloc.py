@@ -55,6 +55,27 @@ def test_noalloc_matches_regular_preconditioner_twice(ctx, prec, form, coarse):
             assert _rel_inf(a, b) <= TOL[prec], (call, _rel_inf(a, b))
 
 
+@pytest.mark.parametrize("prec,form", [("fp32", "hybrid"), ("fp32", "additive"), ("fp16", "additive")])
+def test_noalloc_with_subdomains_of_up_to_64_dofs(ctx, prec, form):
+    """3- and 2-element segments: packs of the classes above 32 dofs, which
+    the additive form's fused local-solve-and-restriction launch does not
+    take (the entry point falls back to separate launches)."""
+    m = meshes.cube(13, perturb=0.15, seed=[2, 13], part_mode="mixed", name="cube13_mixed")
+    rng = np.random.default_rng(22)
+    with cgs.Mesh(ctx, m.xyz, m.conn, part=m.part, boxes=m.boxes, prec=prec, form=form) as h:
+        assert h.info["max_sub_dofs"] > 32
+        for call in range(2):
+            r = torch.as_tensor(rng.standard_normal(m.nv), dtype=torch.float64, device="cuda")
+            z_ref = torch.empty_like(r)
+            z_new = torch.full_like(r, np.nan)
+            cgs.cgs_apply_preconditioner(h.handle, r, z_ref)
+            cgs.cgs_apply_preconditioner_noalloc(h.handle, r, z_new)
+            torch.cuda.synchronize()
+            a, b = z_new.cpu().numpy(), z_ref.cpu().numpy()
+            assert np.isfinite(a).all() and np.abs(b).max() > 0
+            assert _rel_inf(a, b) <= TOL[prec], (call, _rel_inf(a, b))
+
+
 def test_noalloc_rejects_meshes_beyond_its_limit(ctx):
     m, _ = meshes.workload_cylinder(scale=2)        # 137,280 vertices > the 131,072 limit
     assert m.nv > cgs.NOALLOC_MAX_NV
