@@ -111,6 +111,23 @@ def test_apply_local(mesh_of, name, weighted):
     assert rel_inf(host(out), P.local_solves(r, weighted)) <= 1e-11
 
 
+@pytest.mark.parametrize("weighted", [True, False])
+def test_fp64_lane_packs_against_oracle(ctx, weighted):
+    """The FP64 form's lane packs (one lane per subdomain, the triangle walked
+    by diagonals), used from 9,472 subdomains on: the halved cylinder (16,384
+    subdomains of 2^3 elements, classes 18 to 27) entry by entry against the
+    oracle's local solves (Sec. 3, Eq. (4)) at 1e-11."""
+    m, _ = meshes.workload_cylinder(scale=2)
+    P = O.Problem(m.xyz, m.conn, m.part, m.boxes)
+    r = np.where(P.dir, 0.0, np.random.default_rng(5).standard_normal(m.nv))
+    with cgs.Mesh(ctx, m.xyz, m.conn, part=m.part, boxes=m.boxes, prec="fp64") as h:
+        assert h.info["n_sub"] == 16384 and h.info["n_lane_packs"] == 16384 // 32
+        out = torch.empty(m.nv, dtype=torch.float64, device="cuda")
+        cgs.cgs_apply_local(h.handle, dev(r), out, weighted)
+        assert cgs.cgs_mesh_step_status(h.handle) == cgs.OK
+        assert rel_inf(host(out), P.local_solves(r, weighted)) <= 1e-11
+
+
 @pytest.mark.parametrize("name", NAMES)
 def test_box_steps(mesh_of, name):
     m, b, P, h = mesh_of(name)
