@@ -16,7 +16,9 @@
 // On B300 these kernels are bound by the float64 pipe (two fused
 // multiply-adds per clock per SM, about one per 8 bytes of HBM traffic), not
 // by HBM: every loop therefore does exactly the multiply-adds it needs (no
-// padded rows), and a row loop stops at k with a uniform branch.
+// padded rows), and a row loop stops at k with a uniform branch.  Each thread
+// takes two entries per step with all their loads issued first, so that the
+// pipe is not left waiting on one entry's loads.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -30,6 +32,7 @@ namespace {
 constexpr int kProjBlock = 256;
 constexpr int kProjGrid = 592;   // four blocks per SM of a 148-SM part
 constexpr int kProjGroup = 8;    // kept vectors per pass over v
+constexpr int kProjU = 2;        // elements per thread and step of the dots and updates
 
 // v[i] with a Dirichlet entry read as zero; both loads are issued together
 __device__ __forceinline__ double masked(const double* v, const uint8_t* dir, int64_t i) {
@@ -63,13 +66,24 @@ __global__ void __launch_bounds__(kProjBlock) proj_dots_partial(const double* __
         double acc[kProjGroup];
 #pragma unroll
         for (int g = 0; g < kProjGroup; ++g) acc[g] = 0.0;
-        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += S) {
-            const double vi = masked(v, dir, i);
+        // kProjU elements per thread and step: that many loads in flight
+        for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += kProjU * S) {
+            double vi[kProjU];
+#pragma unroll
+            for (int u = 0; u < kProjU; ++u) {
+                const int64_t i = i0 + u * S;
+                vi[u] = i < n ? masked(v, dir, i) : 0.0;
+            }
 #pragma unroll
             for (int g = 0; g < kProjGroup; ++g) {
                 if (g >= G) break;
                 const int j = j0 + g;
-                acc[g] = fma(j < k ? __ldg(&X[(size_t)j * n + i]) : vi, vi, acc[g]);
+#pragma unroll
+                for (int u = 0; u < kProjU; ++u) {
+                    const int64_t i = i0 + u * S;
+                    const double a = i >= n ? 0.0 : j < k ? __ldg(&X[(size_t)j * n + i]) : vi[u];
+                    acc[g] = fma(a, vi[u], acc[g]);
+                }
             }
         }
 #pragma unroll
@@ -131,14 +145,10 @@ __global__ void __launch_bounds__(kProjBlock) vec_add(int64_t n, const double* _
         out[i] = a[i] + b[i];
 }
 
-// w[i] -= sum_{j<k} coef[j] X_j[i] (Dirichlet entries of w read as zero and
-// written as zero); partial[b * (k + 1) + j] = block b's share of X_j . w
-// (j < k) and w . w (j = k) of the updated w.  KMAX >= k accumulators in
-// registers.
 // w[i] -= sum_{j<k} coef[j] X_j[i] (a Dirichlet entry of w is written zero);
 // then, with DOTS, partial[b * (k + 1) + j] = block b's share of X_j . w
-// (j < k) and of w . w (j = k) for the updated w; without DOTS only w . w,
-// in partial[b].
+// (j < k) and of w . w (j = k) for the updated w (KMAX >= k accumulators in
+// registers); without DOTS only w . w, in partial[b].
 template <int KMAX, bool DOTS>
 __global__ void __launch_bounds__(kProjBlock) gs_update_partial(const double* __restrict__ X, int k, int64_t n,
                                                                 const double* __restrict__ coef,
@@ -153,21 +163,38 @@ __global__ void __launch_bounds__(kProjBlock) gs_update_partial(const double* __
     for (int j = 0; j < (DOTS ? KMAX : 1); ++j) acc[j] = 0.0;
     double nrm = 0.0;
     const int64_t S = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += S) {
-        const bool d = dir && __ldg(&dir[i]);
-        double wi = w[i];
-#pragma unroll 4
-        for (int j = 0; j < k; ++j) wi = fma(-sc[j], __ldg(&X[(size_t)j * n + i]), wi);
-        if (d) wi = 0.0;
-        w[i] = wi;
-        if (DOTS) {
+    // kProjU elements per thread and step: that many loads in flight
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += kProjU * S) {
+        double wi[kProjU];
 #pragma unroll
-            for (int j = 0; j < KMAX; ++j) {
-                if (j >= k) break;
-                acc[j] = fma(__ldg(&X[(size_t)j * n + i]), wi, acc[j]);
+        for (int u = 0; u < kProjU; ++u) {
+            const int64_t i = i0 + u * S;
+            wi[u] = i < n ? w[i] : 0.0;
+        }
+#pragma unroll 2
+        for (int j = 0; j < k; ++j) {
+            const double c = sc[j];
+#pragma unroll
+            for (int u = 0; u < kProjU; ++u) {
+                const int64_t i = i0 + u * S;
+                wi[u] = fma(-c, i < n ? __ldg(&X[(size_t)j * n + i]) : 0.0, wi[u]);
             }
         }
-        nrm = fma(wi, wi, nrm);
+#pragma unroll
+        for (int u = 0; u < kProjU; ++u) {
+            const int64_t i = i0 + u * S;
+            if (i >= n) continue;
+            if (dir && __ldg(&dir[i])) wi[u] = 0.0;
+            w[i] = wi[u];
+            if (DOTS) {
+#pragma unroll
+                for (int j = 0; j < KMAX; ++j) {
+                    if (j >= k) break;
+                    acc[j] = fma(__ldg(&X[(size_t)j * n + i]), wi[u], acc[j]);
+                }
+            }
+            nrm = fma(wi[u], wi[u], nrm);
+        }
     }
     if (DOTS) {
 #pragma unroll
