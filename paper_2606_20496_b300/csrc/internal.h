@@ -49,8 +49,9 @@ struct HostSetup {
     // subdomains, in caller order
     std::vector<int64_t> sub_ptr;      // n_sub+1
     std::vector<int32_t> sub_idx;      // sum_m, ascending vertex ids per subdomain
-    // subdomains solved by the warp kernels (all of them in the FP64 form,
-    // those with more than kLaneMaxM dofs in the mixed forms), caller order
+    // subdomains solved by the warp kernels (all of them in the FP64 form on
+    // small meshes, else those with more than kLaneMaxM dofs in the FP64 form
+    // and more than kLaneMaxMixed in the mixed forms), caller order
     int64_t n_wsub = 0, max_wm = 0;
     std::vector<int64_t> wsub_ptr;     // n_wsub+1
     std::vector<int32_t> wsub_idx;
@@ -58,7 +59,8 @@ struct HostSetup {
     std::vector<double> inv;           // cyclic diagonals (i, (i+d) mod m) at d*m + i, float64
     std::vector<double> wsub_ras;      // RAS weights aligned with wsub_idx
     std::vector<double> ap;            // A_p in the same layout (inexact local solves only)
-    // lane packs (mixed forms): 32 subdomains of one size class, one per lane
+    // lane packs (mixed forms; FP64 form on large meshes): 32 subdomains of
+    // one size class, one per lane
     std::vector<int32_t> pack_m;       // n_pack, class size
     std::vector<int64_t> pack_idx_off; // n_pack+1, offsets into pack_idx (32*M per pack)
     std::vector<int64_t> pack_inv_off; // n_pack+1, offsets into pack_inv (32*lane_entries(M) per pack)
@@ -166,8 +168,8 @@ struct DevMesh {
     const float* re_w32 = nullptr;
     int64_t nrng = 0;
     const int2* re_rng = nullptr;      // nrng (begin, end) ranges of one cell's entries
-    // subdomains of the warp kernels (n_sub of them: all in the FP64 form,
-    // those with more than kLaneMaxM dofs in the mixed forms)
+    // subdomains of the warp kernels (n_sub of them: all in the FP64 form on
+    // small meshes, else those above the lane packs' size limit)
     const int32_t* sub_ptr = nullptr;  // n_sub+1 (int32 offsets into sub_idx)
     const int32_t* sub_idx = nullptr;
     const int64_t* inv_ptr = nullptr;  // n_sub+1
