@@ -59,7 +59,7 @@ cgs_status cuda_status(cudaError_t e, const char* where) {
 // Scalars the host needs: out[0..k] of a dot-product launch.
 struct Dots {
     double* partial = nullptr;   // proj_partial_entries(kmax) doubles
-    double* out = nullptr;       // kmax + 1 doubles (device)
+    double* out = nullptr;       // kmax + 2 doubles (device): the dots, then one more slot
     std::vector<double> host;
 };
 
@@ -80,7 +80,7 @@ size_t fgmres_work_doubles(int64_t n, int restart) {
     const size_t kmax = (size_t)restart + 1;
     // every piece rounded up to 32 doubles (256-byte alignment)
     auto r32 = [](size_t x) { return (x + 31) / 32 * 32; };
-    return r32(proj_partial_entries((int)kmax)) + r32(kmax + 1) + 3 * r32((size_t)n) + r32(1) + r32(kmax) +
+    return r32(proj_partial_entries((int)kmax)) + r32(kmax + 2) + 3 * r32((size_t)n) + r32(1) + r32(kmax) +
            r32((size_t)(restart + 1) * n) + r32((size_t)restart * n);
 }
 
@@ -102,7 +102,7 @@ cgs_status fgmres_device(const KrylovOps& ops, const double* b, double* x, doubl
             p += r32(cnt);
         };
         take(&D.partial, proj_partial_entries(kmax));
-        take(&D.out, kmax + 1);
+        take(&D.out, kmax + 2);
         take(&bm, n);
         take(&r, n);
         take(&w, n);
@@ -112,7 +112,7 @@ cgs_status fgmres_device(const KrylovOps& ops, const double* b, double* x, doubl
         take(&Z, (size_t)restart * n);
     } else {
         WRAP_CUDA(buf.alloc(&D.partial, proj_partial_entries(kmax)));
-        WRAP_CUDA(buf.alloc(&D.out, kmax + 1));
+        WRAP_CUDA(buf.alloc(&D.out, kmax + 2));
         WRAP_CUDA(buf.alloc(&bm, n));
         WRAP_CUDA(buf.alloc(&r, n));
         WRAP_CUDA(buf.alloc(&one, 1));
@@ -168,15 +168,18 @@ cgs_status fgmres_device(const KrylovOps& ops, const double* b, double* x, doubl
             // Daniel-Gragg-Kaufman-Stewart test, eta = 1/sqrt(2)); each pass is
             // the dots (with ||w||^2 before) and the correction (with ||w||^2
             // after)
+            // (the dots stay on the device as the correction's coefficients;
+            // they and ||w||^2 after come back in one copy, one wait per pass)
             double hn = 0.0;
             for (int pass = 0; pass < 2; ++pass) {
-                WRAP_OK(dots(D, V, j + 1, n, w, dir, st));
-                for (int i = 0; i <= j; ++i) Hij(i, j) += D.host[i];
-                const double before = D.host[j + 1];
-                launch_gs_update(V, j + 1, n, D.out, dir, w, D.partial, D.out, false, st);
-                double after = 0.0;
-                WRAP_CUDA(cudaMemcpyAsync(&after, D.out, sizeof(double), cudaMemcpyDeviceToHost, st));
+                launch_proj_dots(V, j + 1, n, w, dir, D.partial, D.out, st);
+                launch_gs_update(V, j + 1, n, D.out, dir, w, D.partial, D.out + (j + 2), false, st);
+                D.host.resize(j + 3);
+                WRAP_CUDA(cudaMemcpyAsync(D.host.data(), D.out, sizeof(double) * (j + 3), cudaMemcpyDeviceToHost,
+                                          st));
                 WRAP_CUDA(cudaStreamSynchronize(st));
+                for (int i = 0; i <= j; ++i) Hij(i, j) += D.host[i];
+                const double before = D.host[j + 1], after = D.host[j + 2];
                 hn = std::sqrt(after);
                 if (!(after < 0.5 * before)) break;
             }
