@@ -9,6 +9,9 @@ drivers under tests/host/.
 - The three coarse operators (ar_check.cpp) against the oracle's.
 - The lane packs of the mixed forms (pack_check.cpp) against the oracle's
   local inverses, size classes up to 64 dofs.
+- The spectral-element levels of the p-multigrid wrap (sem_check.cpp):
+  GLL rule, D, numbering, metric, Dirichlet nodes, multiplicities and the
+  element smoothers against the SEM oracle.
 """
 import os
 import re
@@ -160,3 +163,89 @@ def test_lane_packs_hold_the_oracles_local_inverses(tmp_path):
             assert not got[mm:, :].any() and not got[:, mm:].any()
     assert len(seen) == sum(len(ps) for ps, *_ in P.groups.values())
     assert {40, 48, 64} <= classes
+
+
+@pytest.mark.parametrize("case", ["cube3_n7", "cyl16_n4"])
+def test_sem_level_matches_oracle(tmp_path, case):
+    """The spectral-element set-up of the p-multigrid wrap (host C++, Sec. 1
+    and Eq. (14)) against the oracle's (numpy), on a perturbed 3^3 cube at
+    order 7 and the 16-fold reduced hollow cylinder (periodic around) at
+    order 4: the GLL nodes and D, the node numbering (the same partition of
+    element-local nodes into global nodes), the metric w det J J^-1 J^-T at
+    every node, the Dirichlet nodes and multiplicities, and the element
+    smoother (the fast-diagonalisation inverse of each element applied to
+    random vectors) to 1e-12."""
+    import numpy as np
+
+    from oracle import sem_oracle as SO
+    from paper_2606_20496_b300 import meshes
+    gxx = shutil.which("g++")
+    if gxx is None:
+        pytest.skip("no host C++ compiler")
+    exe = str(tmp_path / "sem_check")
+    res = subprocess.run([gxx, "-std=c++17", "-O2", "-fopenmp", "-I", CSRC, "-I", os.path.join(ROOT, "include"),
+                          "-I", "/usr/local/cuda/include", "-o", exe,
+                          os.path.join(ROOT, "tests", "host", "sem_check.cpp"), os.path.join(CSRC, "sem_setup.cpp")],
+                         capture_output=True, text=True)
+    assert res.returncode == 0, res.stderr[-3000:]
+    if case == "cube3_n7":
+        m, n = meshes.cube(3, perturb=0.15, seed=11, name="cube3"), 7
+    else:
+        m, _ = meshes.workload_cylinder(scale=16)
+        n = 4
+    src = tmp_path / "mesh.txt"
+    with open(src, "w") as f:
+        f.write(f"{n} {m.nv} {m.ne}\n")
+        f.write(" ".join("%.17g" % v for v in np.asarray(m.xyz).ravel()) + "\n")
+        f.write(" ".join(str(int(v)) for v in np.asarray(m.conn).ravel()) + "\n")
+    dump = tmp_path / "sem.txt"
+    out = subprocess.run([exe, str(src), str(dump)], capture_output=True, text=True, timeout=300)
+    assert out.returncode == 0, out.stdout + out.stderr
+    lines = open(dump).read().split("\n")
+    p, ng, nfree = map(int, lines[0].split())
+    x = np.array(lines[1].split(), dtype=float)
+    D = np.array(lines[2].split(), dtype=float).reshape(p, p)
+    p3, ne = p ** 3, m.ne
+    l2g = np.empty((ne, p3), dtype=np.int64)
+    G = np.empty((ne, 6, p3))
+    S = np.empty((ne, 3, p, p))
+    lam = np.empty((ne, 3, p))
+    pos = 3
+    for e in range(ne):
+        l2g[e] = np.array(lines[pos].split(), dtype=np.int64)
+        G[e] = np.array(lines[pos + 1].split(), dtype=float).reshape(6, p3)
+        S[e] = np.array(lines[pos + 2].split(), dtype=float).reshape(3, p, p)
+        lam[e] = np.array(lines[pos + 3].split(), dtype=float).reshape(3, p)
+        pos += 4
+    tail = np.array([ln.split() for ln in lines[pos:pos + ng]], dtype=float)
+    dirc, inv_mult = tail[:, 0].astype(bool), tail[:, 1]
+
+    lev = SO.Level(m.xyz, m.conn, n)
+    assert p == lev.p and ng == lev.ng and nfree == int((~lev.dir).sum())
+    assert np.abs(x - lev.x).max() <= 1e-14
+    assert np.abs(D - lev.D).max() <= 1e-12 * np.abs(lev.D).max()
+    # numbering: one oracle node per library node and the other way round
+    lo = lev.l2g.reshape(ne, p3)
+    fwd = {}
+    for a, b in zip(l2g.ravel(), lo.ravel()):
+        assert fwd.setdefault(int(a), int(b)) == int(b)
+    assert len(fwd) == ng and len(set(fwd.values())) == ng
+    o_of = np.array([fwd[g] for g in range(ng)])
+    assert np.array_equal(dirc, lev.dir[o_of])
+    assert np.abs(inv_mult - 1.0 / lev.mult[o_of]).max() <= 1e-15
+    # metric, entries 00 01 02 11 12 22 at node (k, j, i)
+    Go = lev.G.reshape(ne, p3, 3, 3)
+    for c, (a, b) in enumerate([(0, 0), (0, 1), (0, 2), (1, 1), (1, 2), (2, 2)]):
+        assert np.abs(G[:, c] - Go[:, :, a, b]).max() <= 1e-12 * np.abs(Go).max(), (a, b)
+    # the element smoother: the library's S and eigenvalues in the oracle's
+    # fast-diagonalisation apply against the oracle's own
+    sm = SO.Smoother(lev)
+    mine = SO.Smoother.__new__(SO.Smoother)
+    mine.lev, mine.S, mine.lam = lev, S, lam
+    rng = np.random.default_rng(4)
+    for _ in range(2):
+        rL = rng.standard_normal((ne, p, p, p))
+        want = sm.local_solve(rL)
+        got = mine.local_solve(rL)
+        assert np.isfinite(got).all()
+        assert np.abs(got - want).max() <= 1e-12 * np.abs(want).max()
