@@ -9,6 +9,9 @@ drivers under tests/host/.
 - The three coarse operators (ar_check.cpp) against the oracle's.
 - The lane packs of the mixed forms (pack_check.cpp) against the oracle's
   local inverses, size classes up to 64 dofs.
+- The assembled rows of A (ell_check.cpp), float64 and float pairs, against
+  the oracle's assembled operator, with and without an outflow Dirichlet
+  set.
 - The spectral-element levels of the p-multigrid wrap (sem_check.cpp):
   GLL rule, D, numbering, metric, Dirichlet nodes, multiplicities and the
   element smoothers against the SEM oracle.
@@ -249,3 +252,72 @@ def test_sem_level_matches_oracle(tmp_path, case):
         got = mine.local_solve(rL)
         assert np.isfinite(got).all()
         assert np.abs(got - want).max() <= 1e-12 * np.abs(want).max()
+
+
+@pytest.mark.parametrize("case", ["cube8", "cube8_outflow", "cyl8"])
+def test_assembled_rows_match_oracle(tmp_path, case):
+    """The sliced-ELL rows of the assembled free block A = Q^T A_L Q (Sec. 3)
+    built by the library's host set-up: per vertex, the same columns as the
+    oracle's assembled operator (none for a Dirichlet vertex), float64 values
+    to 1e-14 of the row's largest, and the mixed forms' float pairs equal to
+    them to 2^-46 (hi the rounded value, |lo| at most half an ulp of hi)."""
+    import numpy as np
+
+    from oracle import cgs_oracle as O
+    from paper_2606_20496_b300 import meshes
+    gxx = shutil.which("g++")
+    if gxx is None:
+        pytest.skip("no host C++ compiler")
+    exe = str(tmp_path / "ell_check")
+    res = subprocess.run([gxx, "-std=c++17", "-O2", "-fopenmp", "-I", CSRC, "-I", os.path.join(ROOT, "include"),
+                          "-I", "/usr/local/cuda/include", "-o", exe,
+                          os.path.join(ROOT, "tests", "host", "ell_check.cpp"), os.path.join(CSRC, "setup.cpp")],
+                         capture_output=True, text=True)
+    assert res.returncode == 0, res.stderr[-3000:]
+    m, _ = meshes.workload_cylinder(scale=8) if case == "cyl8" else meshes.workload_cube8()
+    d = meshes.outflow_dirichlet(m) if case.endswith("outflow") else None
+    src = tmp_path / "mesh.txt"
+    with open(src, "w") as f:
+        f.write(f"{m.nv} {m.ne} {m.boxes[0]} {m.boxes[1]} {m.boxes[2]} {0 if d is None else 1}\n")
+        f.write(" ".join("%.17g" % v for v in np.asarray(m.xyz).ravel()) + "\n")
+        f.write(" ".join(str(int(v)) for v in np.asarray(m.conn).ravel()) + "\n")
+        f.write(" ".join(str(int(v)) for v in np.asarray(m.part).ravel()) + "\n")
+        if d is not None:
+            f.write(" ".join(str(int(v)) for v in np.asarray(d).astype(int)) + "\n")
+    dump = tmp_path / "ell.txt"
+    out = subprocess.run([exe, str(src), str(dump)], capture_output=True, text=True, timeout=300)
+    assert out.returncode == 0, out.stdout + out.stderr
+    P = O.Problem(m.xyz, m.conn, m.part, m.boxes, dirichlet=None if d is None else d.astype(bool))
+    A = P.A.tocsr()
+    lines = open(dump).read().split("\n")
+    pos = 0
+    for pairs in (False, True):
+        w, nsl = map(int, lines[pos].split())
+        pos += 1
+        assert nsl == (m.nv + 31) // 32 and w >= 1
+        for v in range(m.nv):
+            t = lines[pos].split()
+            pos += 1
+            if P.dir[v]:
+                assert not t
+                continue
+            step = 3 if pairs else 2
+            cols = np.array(t[0::step], dtype=np.int64)
+            if pairs:
+                hi = np.array(t[1::3], dtype=np.float32).astype(np.float64)
+                lo = np.array(t[2::3], dtype=np.float32).astype(np.float64)
+                vals = hi + lo
+            else:
+                vals = np.array(t[1::2], dtype=float)
+            fv = P.free_pos[v]
+            lo_, hi_ = A.indptr[fv], A.indptr[fv + 1]
+            want_cols = P.free[A.indices[lo_:hi_]]         # vertex ids of the row's columns
+            order = np.argsort(want_cols)
+            assert np.array_equal(cols, want_cols[order]), v
+            want = A.data[lo_:hi_][order]
+            scale = np.abs(want).max()
+            assert np.abs(vals - want).max() <= (2.0 ** -46 if pairs else 1e-14) * scale, v
+            if pairs:
+                assert np.array_equal(hi.astype(np.float32), want.astype(np.float32)) or \
+                    np.abs(hi - want).max() <= 2.0 ** -24 * scale
+                assert np.all(np.abs(lo) <= np.abs(np.spacing(hi.astype(np.float32)).astype(np.float64)))
