@@ -12,6 +12,8 @@ drivers under tests/host/.
 - The assembled rows of A (ell_check.cpp), float64 and float pairs, against
   the oracle's assembled operator, with and without an outflow Dirichlet
   set.
+- The explicit rows of J~ and the hybrid restriction's (J~, A J~) entries
+  (jt_check.cpp) against the oracle's interpolation and operator.
 - The spectral-element levels of the p-multigrid wrap (sem_check.cpp):
   GLL rule, D, numbering, metric, Dirichlet nodes, multiplicities and the
   element smoothers against the SEM oracle.
@@ -321,3 +323,66 @@ def test_assembled_rows_match_oracle(tmp_path, case):
                 assert np.array_equal(hi.astype(np.float32), want.astype(np.float32)) or \
                     np.abs(hi - want).max() <= 2.0 ** -24 * scale
                 assert np.all(np.abs(lo) <= np.abs(np.spacing(hi.astype(np.float32)).astype(np.float64)))
+
+
+@pytest.mark.parametrize("case", ["cube8", "cyl8"])
+def test_interpolation_rows_and_hybrid_entries_match_oracle(tmp_path, case):
+    """The explicit rows of J~ = W Q^T J_L (Sec. 4) and the hybrid
+    restriction's entries (J~_vc, (A J~)_vc) (Eq. (5) without the residual
+    update) built by the library's host set-up in the FP64 form, against the
+    oracle's interpolation and operator applied to unit vectors of the
+    reduced space: every nonzero present once, values to 1e-13."""
+    import numpy as np
+
+    from oracle import cgs_oracle as O
+    from paper_2606_20496_b300 import meshes
+    gxx = shutil.which("g++")
+    if gxx is None:
+        pytest.skip("no host C++ compiler")
+    exe = str(tmp_path / "jt_check")
+    res = subprocess.run([gxx, "-std=c++17", "-O2", "-fopenmp", "-I", CSRC, "-I", os.path.join(ROOT, "include"),
+                          "-I", "/usr/local/cuda/include", "-o", exe,
+                          os.path.join(ROOT, "tests", "host", "jt_check.cpp"), os.path.join(CSRC, "setup.cpp")],
+                         capture_output=True, text=True)
+    assert res.returncode == 0, res.stderr[-3000:]
+    m, _ = meshes.workload_cylinder(scale=8) if case == "cyl8" else meshes.workload_cube8()
+    src = tmp_path / "mesh.txt"
+    with open(src, "w") as f:
+        f.write(f"{m.nv} {m.ne} {m.boxes[0]} {m.boxes[1]} {m.boxes[2]}\n")
+        f.write(" ".join("%.17g" % v for v in np.asarray(m.xyz).ravel()) + "\n")
+        f.write(" ".join(str(int(v)) for v in np.asarray(m.conn).ravel()) + "\n")
+        f.write(" ".join(str(int(v)) for v in np.asarray(m.part).ravel()) + "\n")
+    dump = tmp_path / "jt.txt"
+    out = subprocess.run([exe, str(src), str(dump)], capture_output=True, text=True, timeout=300)
+    assert out.returncode == 0, out.stdout + out.stderr
+    P = O.Problem(m.xyz, m.conn, m.part, m.boxes)
+    # the oracle's J~ and A J~, column by column
+    J = np.stack([P.interp(np.eye(P.nr)[c]) for c in range(P.nr)], axis=1)       # (nv, nr)
+    AJ = np.stack([P.apply_A(J[:, c]) for c in range(P.nr)], axis=1)
+    lines = open(dump).read().split("\n")
+    nr, nrows, _ = map(int, lines[0].split())
+    assert nr == P.nr
+    sj, sg = np.abs(J).max(), np.abs(AJ).max()
+    got = np.zeros_like(J)
+    rows_seen = set()
+    for ln in lines[1:1 + nrows]:
+        t = ln.split()
+        v = int(t[0])
+        assert v not in rows_seen and not P.dir[v]
+        rows_seen.add(v)
+        for c, val in zip(t[1::2], t[2::2]):
+            assert got[v, int(c)] == 0.0
+            got[v, int(c)] = float(val)
+    assert np.abs(got - J).max() <= 1e-13 * sj
+    gj, gg = np.zeros_like(J), np.zeros_like(AJ)
+    seen = set()
+    for ln in lines[1 + nrows:]:
+        if not ln.strip():
+            continue
+        v, c, jv, av = ln.split()
+        key = (int(v), int(c))
+        assert key not in seen
+        seen.add(key)
+        gj[key], gg[key] = float(jv), float(av)
+    assert np.abs(gj - J).max() <= 1e-13 * sj
+    assert np.abs(gg - AJ).max() <= 1e-13 * sg
